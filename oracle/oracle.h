@@ -1,0 +1,146 @@
+/*
+ * oracle.h -- FP64 CPU oracle for the per-macroparticle photon-emission step of
+ * Wan, Lv, Jia, Sang & Xie, "Photon emission by bremsstrahlung and nonlinear
+ * Compton scattering in the interaction of ultraintense laser and plasmas"
+ * (arXiv:1612.07592).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This directory is the independent reference the
+ * CUDA library is checked against.  Only the test suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library.
+ *
+ * Everything is plain scalar C99 in double precision, one particle at a time,
+ * in the order the method states its steps:
+ *   fields at (x^n, t^n) -> Boris push -> quantum parameter eta (Sec. 2.1)
+ *   -> nonlinear-Compton optical depth (Sec. 2.2, "same as EPOCH")
+ *   -> bremsstrahlung direct MC collision (Sec. 2.2, Eq. 4, Eq. 1)
+ *   -> position update.
+ *
+ * Units: time in 1/omega_L, length in c/omega_L, momentum u = p/(m c),
+ * fields in m c omega_L / e, energies in m c^2.
+ */
+#ifndef PE_ORACLE_H
+#define PE_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* ---- special functions (integral representations, own quadrature) -------- */
+double or_bessel_k(double nu, double x);          /* K_nu(x)                    */
+double or_int_k53(double x);                      /* int_x^inf K_{5/3}(t) dt    */
+/* Quantum-synchrotron emissivity F(eta, chi) (Sokolov-Ternov form used by
+ * Kirk 2009 / Ridgers 2014, which the paper's NCS module follows).            */
+double or_ncs_F(double eta, double chi);
+/* integral of F over chi in (0, eta/2): the radiated power shape (Larmor pin) */
+double or_ncs_power_integral(double eta);
+/* h(eta) = int_0^{eta/2} F/chi dchi, by direct quadrature (no table)          */
+double or_ncs_h_direct(double eta);
+
+/* ---- bremsstrahlung: Tsai screened DCS, Eq. (1) ---------------------------- */
+double or_coulomb_f(double Z);
+/* d sigma / d y per atom in units of alpha r_e^2; y = k/E, E = gamma m c^2.
+ * complete != 0 forces the screening variables to zero (complete screening).
+ * Not clamped: returns the raw bracket value.                                 */
+double or_brems_dcs_raw(double Z, double gamma, double y, int complete);
+/* sigma_Z(gamma) = int_{ycut}^{ymax} dsigma/dy dy (clamped integrand >= 0),
+ * ycut = photon_min/gamma, ymax = 1 - 1/gamma; units alpha r_e^2.            */
+double or_brems_sigma_direct(double Z, double gamma, double photon_min);
+
+/* ---- tables ---------------------------------------------------------------- */
+typedef struct {
+    int n_eta, n_y;           /* NCS rows (log eta) x columns (log y)          */
+    double eta_min, eta_max;
+    double y_min, y_max;      /* CDF abscissa y = 2 delta / (3 eta (1-delta))  */
+    int n_E, n_s;             /* brems rows (log gamma) x columns (s in [0,1]) */
+    double gamma_min, gamma_max;
+    double photon_min;        /* hard-photon cut in m c^2 (Sec. 3: 0.511 MeV)  */
+} or_table_params;
+
+typedef struct or_tables or_tables;
+or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z);
+void or_tables_free(or_tables* t);
+/* which: 0 = h(eta_i) [n_eta], 1 = NCS CDF [n_eta*n_y], 2 = classical CDF [n_y],
+ *        3 = sigma_Z(gamma_i) [n_E] for Z index iz, 4 = brems CDF [n_E*n_s].
+ * Returns the number of doubles written, or -1.                               */
+int64_t or_tables_export(const or_tables* t, int which, int iz, double* out, int64_t cap);
+/* classical-limit total int_0^inf (int_y^inf K53) dy as integrated (5 pi/3)  */
+double or_tables_classical_total(const or_tables* t);
+
+/* inverse-CDF samplers exactly as the step uses them (exposed for tests)      */
+double or_sample_ncs_delta(const or_tables* t, double eta, double R, int* below);
+double or_sample_brems_y(const or_tables* t, int iz, double gamma, double R);
+double or_ncs_h_interp(const or_tables* t, double eta, int* range_flag);
+double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* above);
+
+/* ---- run description ------------------------------------------------------- */
+enum { OR_LP_Y = 0, OR_CP = 1 };
+enum { OR_PLANE_1D = 0, OR_GAUSS_2D = 1, OR_CONST = 2 };
+enum { OR_REST = 0, OR_MAXWELL_JUTTNER = 1, OR_BEAM = 2 };
+
+typedef struct {
+    double a0, lambda_m;
+    int polarisation, geometry;
+    double w0_m, focus_x_m;
+    double flat_s, ramp_periods;
+    double E_const[3], B_const[3];       /* OR_CONST only (normalised units)    */
+    double Z, charge_state, ne_over_nc;
+    double slab_x0_m, slab_thick_m, y_half_m;
+    double dt_over_T;
+    int init_dist;
+    double T_mev;                        /* Maxwell-Juttner temperature         */
+    double beam_gamma;                   /* OR_BEAM: u = (sqrt(g^2-1), 0, 0)    */
+    uint64_t seed;
+    uint32_t run_id;
+    int enable_ncs, enable_brems;
+    int box_enable; double box_x_m[2];   /* absorbing box in x                  */
+    int iz;                              /* index of Z in the table set         */
+} or_run_params;
+
+/* photon record, 32 bytes */
+typedef struct {
+    float x, y, energy, kx, ky, kz;
+    uint32_t step;
+    uint32_t id_mech;                    /* particle id | (mechanism << 31)      */
+} or_photon;
+
+/* tally words (uint64) */
+enum {
+    ORT_N_NCS_STORED = 0, ORT_N_NCS_BELOW = 1, ORT_N_BR_STORED = 2, ORT_N_BR_BELOW = 3,
+    ORT_N_PHOTONS = 4, ORT_N_ETA_ABOVE = 5, ORT_N_ETA_BELOW = 6, ORT_N_GAMMA_ABOVE = 7,
+    ORT_N_KILLED = 8, ORT_KILLED_STEPS = 9, ORT_N_CLAMP = 10, ORT_N_HIST_OVER = 11,
+    ORT_E_NCS_STORED = 16, ORT_E_NCS_BELOW = 18, ORT_E_BR_STORED = 20, ORT_E_BR_BELOW = 22,
+    ORT_E_RECOIL_NCS = 24, ORT_E_RECOIL_BR = 26,
+    ORT_WORDS = 32
+};
+#define OR_HIST_E_BINS 512
+#define OR_HIST_T_BINS 180
+#define OR_HIST_WORDS (2 * OR_HIST_E_BINS + 2 * OR_HIST_T_BINS)
+
+/* Initial state of the listed particles (x, y, ux, uy, uz, tau per particle). */
+int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
+            double* state);
+/* Advance the listed particles from step0 for n_steps.  state is in/out (6
+ * doubles per particle).  Photons of these particles are written in particle
+ * order to photons[0..cap); *n_photons receives the true count.  hist and
+ * tally are accumulated (not cleared).  Returns 0 on success.                 */
+int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
+           int64_t step0, int64_t n_steps, double* state,
+           or_photon* photons, int64_t cap, int64_t* n_photons,
+           uint64_t* hist, uint64_t* tally, int n_threads);
+
+/* normalised helpers (exposed for unit pins) */
+double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */
+double or_critical_density(double lambda_m);  /* n_c in m^-3                   */
+void or_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]);
+double or_eta(const double u[3], const double E[3], const double B[3], double E_S);
+void or_boris(double u[3], const double E[3], const double B[3], double dt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

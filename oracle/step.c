@@ -1,0 +1,443 @@
+/*
+ * step.c -- oracle particle step.  TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * One particle at a time, FP64, in the order of the method:
+ *   E, B at (x^n, t^n)                         prescribed laser (Sec. 3 setup)
+ *   Boris push u^{n-1/2} -> u^{n+1/2}           "particle pusher" (Sec. 2.2)
+ *   eta from u^{n+1/2} and E, B                 Sec. 2.1 (quantum parameter)
+ *   NCS optical depth tau -= dN/dt dt; emit at tau <= 0     Sec. 2.2 (EPOCH)
+ *   brems: P = 1 - exp(-n sigma v dt), event iff R1 < P      Eq. (4)
+ *          photon energy from sigma(y,E) = sigma(E) R2, k along v  Sec. 2.2
+ *   photons below m c^2 are created but not stored           Sec. 3
+ *   x^{n+1} = x^n + dt u^{n+1/2} / gamma
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 */
+#define C_ALPHA 7.2973525693e-3
+#define C_RE 2.8179403262e-15          /* classical electron radius, m  */
+#define C_MEC2_MEV 0.51099895000       /* m_e c^2, MeV                  */
+#define C_HBARC_MEVM 197.3269804e-15   /* hbar c, MeV m                 */
+#define C_LIGHT 299792458.0
+#define HIST_EMAX_MEV 10000.0          /* top of the energy histogram   */
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from its published definition (Salmon et al., SC'11):      */
+/* 10 rounds of two 32x32->64 multiplies (M0 = 0xD2511F53, M1 = 0xCD9E8D57), */
+/* key bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between rounds. */
+/* ------------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* purposes of the per-particle Philox streams */
+enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4 };
+
+static void draw(const or_run_params* r, int64_t id, uint32_t step, uint32_t purpose, uint32_t w[4]) {
+    uint32_t ctr[4] = {(uint32_t)id, r->run_id, step, purpose};
+    uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
+    or_philox4x32_10(ctr, key, w);
+}
+static uint64_t word64(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | (uint64_t)lo; }
+/* uniform in (0,1) with 53 random bits */
+static double u53(uint64_t v) { return ((double)(v >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+/* uniform in (0,1) with 32 random bits */
+static double u32(uint32_t v) { return ((double)v + 0.5) * (1.0 / 4294967296.0); }
+
+/* ------------------------------------------------------------------------- */
+/* Units                                                                     */
+/* ------------------------------------------------------------------------- */
+double or_schwinger_field(double lambda_m) {
+    /* E_S = m^2 c^3 / (e hbar) in units of m c omega / e  =  m c^2 / (hbar omega) */
+    double hbar_omega_mev = 2.0 * M_PI * C_HBARC_MEVM / lambda_m;
+    return C_MEC2_MEV / hbar_omega_mev;
+}
+double or_critical_density(double lambda_m) {
+    /* n_c = eps0 m omega^2 / e^2 = pi / (r_e lambda^2) */
+    return M_PI / (C_RE * lambda_m * lambda_m);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Prescribed laser fields.  The pulse is defined through its vector         */
+/* potential A(phi) with phi = t - x, so E and B carry no DC part:           */
+/*   g(phi): sin^2 ramp over ramp_periods, flat top flat_s, cos^2 ramp;      */
+/*   LP:  A = a0 g sin(phi) y^;   CP: A = a0 g (sin(phi) y^ - cos(phi) z^);  */
+/*   E = -dA/dt, B = curl A = x^ cross E for the plane wave.                 */
+/* The 2D focus multiplies the transverse profile sqrt(w0/w) exp(-y^2/w^2)   */
+/* and adds the paraxial curvature and Gouy phase plus the first-order       */
+/* longitudinal components required by div E = 0 and div B = 0.              */
+/* ------------------------------------------------------------------------- */
+static void envelope(const or_run_params* r, double phi, double* g, double* dg) {
+    double pr = 2.0 * M_PI * r->ramp_periods;
+    double pf = 2.0 * M_PI * r->flat_s * C_LIGHT / r->lambda_m;
+    if (phi <= 0.0 || phi >= 2.0 * pr + pf) { *g = 0.0; *dg = 0.0; return; }
+    if (phi < pr) {
+        double s = sin(0.5 * M_PI * phi / pr);
+        *g = s * s;
+        *dg = (0.5 * M_PI / pr) * sin(M_PI * phi / pr);
+        return;
+    }
+    if (phi <= pr + pf) { *g = 1.0; *dg = 0.0; return; }
+    double q = phi - pr - pf;
+    double c = cos(0.5 * M_PI * q / pr);
+    *g = c * c;
+    *dg = -(0.5 * M_PI / pr) * sin(M_PI * q / pr);
+}
+
+void or_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]) {
+    E[0] = E[1] = E[2] = 0.0;
+    B[0] = B[1] = B[2] = 0.0;
+    if (r->geometry == OR_CONST) {
+        for (int k = 0; k < 3; ++k) { E[k] = r->E_const[k]; B[k] = r->B_const[k]; }
+        return;
+    }
+    double phi = t - x;
+    double g, dg;
+    envelope(r, phi, &g, &dg);
+    if (g == 0.0 && dg == 0.0) return;
+    double a0 = r->a0;
+    double S = 1.0, theta = phi, inv_R = 0.0, inv_w2 = 0.0;
+    if (r->geometry == OR_GAUSS_2D) {
+        double kl = 2.0 * M_PI / r->lambda_m;         /* lengths -> c/omega     */
+        double w0 = r->w0_m * kl;
+        double zr = 0.5 * w0 * w0;
+        double xi = x - r->focus_x_m * kl;
+        double w2 = w0 * w0 * (1.0 + xi * xi / (zr * zr));
+        inv_w2 = 1.0 / w2;
+        inv_R = xi / (xi * xi + zr * zr);
+        S = sqrt(w0 / sqrt(w2)) * exp(-y * y * inv_w2);
+        theta = phi - 0.5 * y * y * inv_R + 0.5 * atan(xi / zr);
+    }
+    double st = sin(theta), ct = cos(theta);
+    /* y-polarised component: E_y = B_z = -a0 S (g' sin + g cos) */
+    double ey = -a0 * S * (dg * st + g * ct);
+    E[1] = ey;
+    B[2] = ey;
+    if (r->geometry == OR_GAUSS_2D)
+        E[0] = a0 * g * S * (y * inv_R * ct + 2.0 * y * inv_w2 * st);
+    if (r->polarisation == OR_CP) {
+        /* z-polarised component, a quarter period behind: E_z = -B_y */
+        double ez = a0 * S * (dg * ct - g * st);
+        E[2] = ez;
+        B[1] = -ez;
+        if (r->geometry == OR_GAUSS_2D)
+            B[0] = a0 * g * S * (2.0 * y * inv_w2 * ct - y * inv_R * st);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Boris push for charge -e, mass m (normalised: du/dt = -(E + u x B/gamma)) */
+/* ------------------------------------------------------------------------- */
+void or_boris(double u[3], const double E[3], const double B[3], double dt) {
+    double h = 0.5 * dt;
+    double um[3] = {u[0] - h * E[0], u[1] - h * E[1], u[2] - h * E[2]};
+    double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    double tv[3] = {-h * B[0] / gm, -h * B[1] / gm, -h * B[2] / gm};
+    double t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+    double sv[3] = {2.0 * tv[0] / (1.0 + t2), 2.0 * tv[1] / (1.0 + t2), 2.0 * tv[2] / (1.0 + t2)};
+    double up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]),
+                    um[1] + (um[2] * tv[0] - um[0] * tv[2]),
+                    um[2] + (um[0] * tv[1] - um[1] * tv[0])};
+    double uq[3] = {um[0] + (up[1] * sv[2] - up[2] * sv[1]),
+                    um[1] + (up[2] * sv[0] - up[0] * sv[2]),
+                    um[2] + (up[0] * sv[1] - up[1] * sv[0])};
+    u[0] = uq[0] - h * E[0];
+    u[1] = uq[1] - h * E[1];
+    u[2] = uq[2] - h * E[2];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Quantum parameter (Sec. 2.1; garbled there, read as the standard          */
+/* invariant):  eta E_S = sqrt( (gamma E + u x B)^2 - (u.E)^2 ).             */
+/* Evaluated through an exact rewriting that avoids cancellation for         */
+/* electrons riding a wave along x:  with dB = B - x^ x E and                */
+/* V = (gamma - u_x) E + u x dB, one has gamma E + u x B = V + x^ (u.E), so   */
+/* the invariant equals |V|^2 + 2 V_x (u.E).  gamma - u_x is formed as       */
+/* (1 + u_y^2 + u_z^2)/(gamma + u_x) when u_x > 0.                           */
+/* ------------------------------------------------------------------------- */
+double or_eta(const double u[3], const double E[3], const double B[3], double E_S) {
+    double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double gm = (u[0] > 0.0) ? (1.0 + u[1] * u[1] + u[2] * u[2]) / (gamma + u[0]) : gamma - u[0];
+    double dB[3] = {B[0], B[1] + E[2], B[2] - E[1]};
+    double V[3] = {gm * E[0] + (u[1] * dB[2] - u[2] * dB[1]),
+                   gm * E[1] + (u[2] * dB[0] - u[0] * dB[2]),
+                   gm * E[2] + (u[0] * dB[1] - u[1] * dB[0])};
+    double uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+    double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2] + 2.0 * V[0] * uE;
+    return q > 0.0 ? sqrt(q) / E_S : 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 128-bit fixed-point energy tally: value = hi + lo * 2^-64                 */
+/* ------------------------------------------------------------------------- */
+static void fx_add(uint64_t* w, double v) {
+    if (!(v > 0.0)) return;
+    double ip = floor(v);
+    double fr = v - ip;
+    uint64_t lo = (uint64_t)(fr * 18446744073709551616.0);
+    uint64_t old = w[0];
+    w[0] = old + lo;
+    if (w[0] < old) w[1] += 1;
+    w[1] += (uint64_t)ip;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Run context                                                               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double dt, E_S, C_ncs, K_br, x0, x1, yh, box0, box1, log_emax;
+    double photon_min;
+} run_ctx;
+
+static void make_ctx(const or_tables* t, const or_run_params* r, run_ctx* c, double photon_min) {
+    double kl = 2.0 * M_PI / r->lambda_m;              /* 1/m -> c/omega units */
+    c->dt = r->dt_over_T * 2.0 * M_PI;
+    c->E_S = or_schwinger_field(r->lambda_m);
+    /* dN/dt = sqrt(3) alpha /(2 pi) * (m c^2/hbar) * (eta/gamma) h(eta); in 1/omega units */
+    c->C_ncs = sqrt(3.0) * C_ALPHA / (2.0 * M_PI) * c->E_S;
+    /* x_b = n_i sigma beta c dt; sigma in alpha r_e^2, c dt in metres */
+    double n_i = r->ne_over_nc * or_critical_density(r->lambda_m) / r->charge_state;
+    c->K_br = n_i * C_ALPHA * C_RE * C_RE * (c->dt / kl);
+    c->x0 = r->slab_x0_m * kl;
+    c->x1 = (r->slab_x0_m + r->slab_thick_m) * kl;
+    c->yh = r->y_half_m * kl;
+    c->box0 = r->box_x_m[0] * kl;
+    c->box1 = r->box_x_m[1] * kl;
+    c->log_emax = log(HIST_EMAX_MEV / C_MEC2_MEV);
+    c->photon_min = photon_min;
+    (void)t;
+}
+
+/* table params are needed for photon_min; fetch through the export API */
+extern double or__photon_min(const or_tables* t);
+
+int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids, double* st) {
+    run_ctx c;
+    make_ctx(t, r, &c, or__photon_min(t));
+    double theta = r->T_mev / C_MEC2_MEV;
+    for (int64_t k = 0; k < n_ids; ++k) {
+        int64_t id = ids[k];
+        uint32_t w[4];
+        double* s = st + 6 * k;
+        draw(r, id, 0, PUR_POS, w);
+        s[0] = c.x0 + (c.x1 - c.x0) * u32(w[0]);
+        s[1] = (r->geometry == OR_GAUSS_2D) ? -c.yh + 2.0 * c.yh * u32(w[1]) : 0.0;
+        s[2] = s[3] = s[4] = 0.0;
+        if (r->init_dist == OR_MAXWELL_JUTTNER) {
+            /* Sobol (1976) rejection for the Maxwell-Juttner momentum magnitude */
+            double um = 0.0;
+            for (uint32_t round = 0; round < 64; ++round) {
+                uint32_t m[4];
+                draw(r, id, 0, PUR_MJ + round, m);
+                double X1 = u32(m[0]), X2 = u32(m[1]), X3 = u32(m[2]), X4 = u32(m[3]);
+                double uu = -theta * log(X1 * X2 * X3);
+                double ee = -theta * log(X1 * X2 * X3 * X4);
+                if (ee * ee - uu * uu > 1.0) { um = uu; break; }
+            }
+            /* isotropic direction from the position draw's last two words */
+            double X5 = u32(w[2]), X6 = u32(w[3]);
+            double sn = 2.0 * sqrt(X5 * (1.0 - X5));
+            s[2] = um * (2.0 * X5 - 1.0);
+            s[3] = um * sn * cos(2.0 * M_PI * X6);
+            s[4] = um * sn * sin(2.0 * M_PI * X6);
+        } else if (r->init_dist == OR_BEAM) {
+            s[2] = sqrt(r->beam_gamma * r->beam_gamma - 1.0);
+        }
+        draw(r, id, 0, PUR_TAU0, w);
+        s[5] = -log(u53(word64(w[0], w[1])));
+    }
+    return 0;
+}
+
+typedef struct { or_photon* v; int64_t n, cap; } plist;
+static void plist_push(plist* l, const or_photon* p) {
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 8;
+        l->v = (or_photon*)realloc(l->v, sizeof(or_photon) * l->cap);
+    }
+    l->v[l->n++] = *p;
+}
+
+static void record(const run_ctx* c, double x, double y, double ew, const double k[3], uint32_t step,
+                   int64_t id, int mech, plist* pl, uint64_t* hist, uint64_t* tally) {
+    or_photon p;
+    p.x = (float)x; p.y = (float)y; p.energy = (float)ew;
+    p.kx = (float)k[0]; p.ky = (float)k[1]; p.kz = (float)k[2];
+    p.step = step;
+    p.id_mech = (uint32_t)id | ((uint32_t)mech << 31);
+    plist_push(pl, &p);
+    int eb = (int)floor((double)OR_HIST_E_BINS * log(ew) / c->log_emax);
+    if (eb >= OR_HIST_E_BINS) { eb = OR_HIST_E_BINS - 1; tally[ORT_N_HIST_OVER]++; }
+    if (eb < 0) eb = 0;
+    double th = atan2(k[1], k[0]);
+    int tb = (int)floor((th + M_PI) / (2.0 * M_PI) * (double)OR_HIST_T_BINS);
+    if (tb < 0) tb = 0;
+    if (tb >= OR_HIST_T_BINS) tb = OR_HIST_T_BINS - 1;
+    hist[mech * OR_HIST_E_BINS + eb]++;
+    hist[2 * OR_HIST_E_BINS + mech * OR_HIST_T_BINS + tb]++;
+}
+
+/* energy-conserving recoil along u: gamma' = gamma - w, u' = u^ sqrt(gamma'^2 - 1) */
+static void recoil(double u[3], double gamma, double w, double khat[3]) {
+    double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (um > 0.0) { khat[0] = u[0] / um; khat[1] = u[1] / um; khat[2] = u[2] / um; }
+    else { khat[0] = 1.0; khat[1] = 0.0; khat[2] = 0.0; }
+    double g2 = gamma - w;
+    double un = (g2 > 1.0) ? sqrt(g2 * g2 - 1.0) : 0.0;
+    u[0] = khat[0] * un; u[1] = khat[1] * un; u[2] = khat[2] * un;
+}
+
+static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c, int64_t id,
+                    int64_t step0, int64_t n_steps, double* s, plist* pl, uint64_t* hist, uint64_t* tally) {
+    double x = s[0], y = s[1];
+    double u[3] = {s[2], s[3], s[4]};
+    double tau = s[5];
+    for (int64_t n = step0; n < step0 + n_steps; ++n) {
+        if (isnan(x)) break;
+        double tn = (double)n * c->dt;
+        double E[3], B[3];
+        or_fields(r, x, y, tn, E, B);
+        or_boris(u, E, B, c->dt);
+        double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (r->enable_ncs) {
+            double eta = or_eta(u, E, B, c->E_S);
+            int fl;
+            double h = or_ncs_h_interp(t, eta, &fl);
+            if (fl == 1) tally[ORT_N_ETA_ABOVE]++;
+            tau -= c->C_ncs * (eta / gamma) * h * c->dt;
+            if (tau <= 0.0) {
+                uint32_t w[4];
+                draw(r, id, (uint32_t)n, PUR_NCS, w);
+                int below;
+                double delta = or_sample_ncs_delta(t, eta, u53(word64(w[0], w[1])), &below);
+                if (below) tally[ORT_N_ETA_BELOW]++;
+                double ew = delta * gamma;
+                if (ew > gamma - 1.0) { ew = gamma - 1.0; tally[ORT_N_CLAMP]++; }
+                double k[3];
+                recoil(u, gamma, ew, k);
+                double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                fx_add(tally + ORT_E_RECOIL_NCS, gamma - gn);
+                if (ew >= c->photon_min) {
+                    tally[ORT_N_NCS_STORED]++;
+                    tally[ORT_N_PHOTONS]++;
+                    fx_add(tally + ORT_E_NCS_STORED, ew);
+                    record(c, x, y, ew, k, (uint32_t)n, id, 0, pl, hist, tally);
+                } else {
+                    tally[ORT_N_NCS_BELOW]++;
+                    fx_add(tally + ORT_E_NCS_BELOW, ew);
+                }
+                gamma = gn;
+                tau = -log(u53(word64(w[2], w[3])));
+            }
+        }
+        if (r->enable_brems) {
+            int in_slab = (x >= c->x0 && x <= c->x1);
+            if (r->geometry == OR_GAUSS_2D && fabs(y) > c->yh) in_slab = 0;
+            if (in_slab && gamma > 1.0 + c->photon_min) {
+                int above;
+                double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
+                if (above) tally[ORT_N_GAMMA_ABOVE]++;
+                double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double xb = c->K_br * sig * (um / gamma);
+                double P = -expm1(-xb);
+                uint32_t w[4];
+                draw(r, id, (uint32_t)n, PUR_BREMS, w);
+                uint64_t U = word64(w[0], w[1]);
+                uint64_t thr = (uint64_t)floor(P * 18446744073709551616.0);
+                if (P >= 1.0) thr = UINT64_MAX;
+                if (U < thr) {
+                    double yy = or_sample_brems_y(t, r->iz, gamma, u53(word64(w[2], w[3])));
+                    double ew = yy * gamma;
+                    double k[3];
+                    recoil(u, gamma, ew, k);
+                    double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    fx_add(tally + ORT_E_RECOIL_BR, gamma - gn);
+                    if (ew >= c->photon_min) {
+                        tally[ORT_N_BR_STORED]++;
+                        tally[ORT_N_PHOTONS]++;
+                        fx_add(tally + ORT_E_BR_STORED, ew);
+                        record(c, x, y, ew, k, (uint32_t)n, id, 1, pl, hist, tally);
+                    } else {
+                        tally[ORT_N_BR_BELOW]++;
+                        fx_add(tally + ORT_E_BR_BELOW, ew);
+                    }
+                    gamma = gn;
+                }
+            }
+        }
+        x += c->dt * u[0] / gamma;
+        if (r->geometry == OR_GAUSS_2D) y += c->dt * u[1] / gamma;
+        if (r->box_enable && (x < c->box0 || x > c->box1)) {
+            x = NAN;
+            tally[ORT_N_KILLED]++;
+            tally[ORT_KILLED_STEPS] += (uint64_t)(n + 1);
+        }
+    }
+    s[0] = x; s[1] = y; s[2] = u[0]; s[3] = u[1]; s[4] = u[2]; s[5] = tau;
+}
+
+int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
+           int64_t step0, int64_t n_steps, double* state,
+           or_photon* photons, int64_t cap, int64_t* n_photons,
+           uint64_t* hist, uint64_t* tally, int n_threads) {
+    if (!t || !r || n_ids < 0 || n_steps < 0) return -1;
+    run_ctx c;
+    make_ctx(t, r, &c, or__photon_min(t));
+    plist* lists = (plist*)calloc(n_ids > 0 ? n_ids : 1, sizeof(plist));
+    int nt = n_threads > 0 ? n_threads : 1;
+    uint64_t* th_hist = (uint64_t*)calloc((size_t)nt * OR_HIST_WORDS, sizeof(uint64_t));
+    uint64_t* th_tally = (uint64_t*)calloc((size_t)nt * ORT_WORDS, sizeof(uint64_t));
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
+    for (int64_t k = 0; k < n_ids; ++k) {
+        int me = 0;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+#endif
+        run_one(t, r, &c, ids[k], step0, n_steps, state + 6 * k, &lists[k],
+                th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS);
+    }
+    for (int k = 0; k < nt; ++k) {
+        const uint64_t* th = th_tally + (size_t)k * ORT_WORDS;
+        for (int i = 0; i < OR_HIST_WORDS; ++i) hist[i] += th_hist[(size_t)k * OR_HIST_WORDS + i];
+        for (int i = 0; i < ORT_E_NCS_STORED; ++i) tally[i] += th[i];
+        /* 128-bit fixed-point pairs (lo, hi) */
+        for (int i = ORT_E_NCS_STORED; i <= ORT_E_RECOIL_BR; i += 2) {
+            uint64_t old = tally[i];
+            tally[i] = old + th[i];
+            if (tally[i] < old) tally[i + 1] += 1;
+            tally[i + 1] += th[i + 1];
+        }
+    }
+    int64_t total = 0;
+    for (int64_t k = 0; k < n_ids; ++k) {
+        for (int64_t j = 0; j < lists[k].n; ++j) {
+            if (total < cap) photons[total] = lists[k].v[j];
+            ++total;
+        }
+        free(lists[k].v);
+    }
+    *n_photons = total;
+    free(lists); free(th_hist); free(th_tally);
+    return 0;
+}
