@@ -1,0 +1,210 @@
+/*
+ * pe.h -- C ABI of the GB300 photon-emission step library (libpe.so).
+ *
+ * The library advances laser-driven electrons through the per-macroparticle
+ * emission step of Wan, Lv, Jia, Sang & Xie, arXiv:1612.07592 ("Photon
+ * emission by bremsstrahlung and nonlinear Compton scattering in the
+ * interaction of ultraintense laser and plasmas"), in the paper's own test
+ * mode (Sec. 2.2: field solver and weighting off, "only particle pusher and
+ * bremsstrahlung MC module", here with the NCS module as well) under
+ * prescribed laser fields with the paper's setup (Sec. 3).
+ *
+ * Per particle and step:
+ *   E, B at (x^n, t^n)                       prescribed pulse (Sec. 3)
+ *   Boris push u^{n-1/2} -> u^{n+1/2}         particle pusher (Sec. 2.2)
+ *   eta = sqrt((gamma E + u x B)^2 - (u.E)^2) / E_S       (Sec. 2.1)
+ *   NCS: tau -= dN/dt dt against the tabulated quantum-synchrotron rate;
+ *        tau <= 0 -> photon energy by inverse CDF, recoil, new tau (Sec. 2.2)
+ *   brems: P = 1 - exp(-n_i sigma(E) v dt) (Eq. 4, sign as intended), event
+ *        iff a 64-bit uniform is below P 2^64; photon energy from
+ *        sigma(y, E) = sigma(E) R2 (text after Eq. 4) with the screened Tsai
+ *        cross section of Eq. (1); photon along v
+ *   photons below m c^2 are created but only tallied (Sec. 3)
+ *   x^{n+1} = x^n + dt u^{n+1/2} / gamma
+ *
+ * Units inside the library: time 1/omega_L, length c/omega_L, u = p/(m c),
+ * fields m c omega_L / e, energies m c^2.  Parameters are SI unless stated.
+ *
+ * Conventions.  Every call returns pe_status; no exception crosses the ABI.
+ * On an error pe_last_error() (thread-local) describes it.  The library owns
+ * the opaque handles and the device copies of the tables; the caller owns
+ * every particle, photon, histogram and tally buffer (device memory, e.g.
+ * torch tensors) and keeps them alive until pe_destroy().  Streams are passed
+ * as void* (cudaStream_t).  All work is asynchronous on the run's stream
+ * except pe_create_tables, pe_tally and the export calls, which synchronise.
+ */
+#ifndef PE_H
+#define PE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PE_OK = 0,
+    PE_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad enum)     */
+    PE_ERR_CUDA = 2,         /* a CUDA runtime call failed                              */
+    PE_ERR_NOMEM = 3,        /* the library could not allocate its own device memory    */
+    PE_ERR_BUFFER_FULL = 4,  /* photon buffer overflowed; counts stay exact             */
+    PE_ERR_TABLE_RANGE = 5,  /* reserved: out-of-table values are counted, not fatal    */
+    PE_ERR_TIMEOUT = 6,      /* reserved for bounded device waits                       */
+    PE_ERR_STATE = 7         /* call out of order (e.g. mixed precisions in one batch)  */
+} pe_status;
+
+enum { PE_LP_Y = 0, PE_CP = 1 };                          /* polarisation                */
+enum { PE_PLANE_1D = 0, PE_GAUSS_2D = 1, PE_CONST = 2 };  /* field geometry              */
+enum { PE_F64 = 0, PE_F32 = 1 };                          /* arithmetic of the step      */
+enum { PE_REST = 0, PE_MAXWELL_JUTTNER = 1, PE_BEAM = 2, PE_CALLER = 3 };  /* initial state */
+
+#define PE_HIST_E_BINS 512    /* log bins of photon energy over [0.511 MeV, 10 GeV]      */
+#define PE_HIST_T_BINS 180    /* bins of theta = atan2(k_y, k_x) over [-pi, pi)          */
+#define PE_HIST_WORDS (2 * PE_HIST_E_BINS + 2 * PE_HIST_T_BINS)
+#define PE_TALLY_WORDS 32
+#define PE_MAX_BATCH 64       /* runs in one batched launch                              */
+
+/* tally word indices (uint64).  Energies are 128-bit fixed point in m c^2:
+ * value = word[i+1] + word[i] * 2^-64, summed exactly (order independent).   */
+enum {
+    PE_T_N_NCS_STORED = 0, PE_T_N_NCS_BELOW = 1, PE_T_N_BR_STORED = 2, PE_T_N_BR_BELOW = 3,
+    PE_T_N_PHOTONS = 4,      /* photons appended (true count, also beyond capacity)       */
+    PE_T_N_ETA_ABOVE = 5,    /* particle-steps with eta above the table (row clamped)      */
+    PE_T_N_ETA_BELOW = 6,    /* NCS emissions sampled from the classical (eta->0) row      */
+    PE_T_N_GAMMA_ABOVE = 7,  /* brems tests with gamma above the table (row clamped)       */
+    PE_T_N_KILLED = 8, PE_T_KILLED_STEPS = 9, PE_T_N_CLAMP = 10, PE_T_N_HIST_OVER = 11,
+    PE_T_E_NCS_STORED = 16, PE_T_E_NCS_BELOW = 18, PE_T_E_BR_STORED = 20, PE_T_E_BR_BELOW = 22,
+    PE_T_E_RECOIL_NCS = 24, PE_T_E_RECOIL_BR = 26
+};
+
+/* Sampling-table description (Sec. 2.2).
+ * NCS: h(eta) and the photon-energy CDF on n_eta log-spaced eta in
+ *   [eta_min, eta_max] x n_y log-spaced y in [y_min, y_max], where
+ *   y = 2 delta / (3 eta (1 - delta)) and delta = photon energy / electron energy.
+ * Brems: sigma_Z(gamma) and the CDF of sigma(y, E) = sigma(E) R2 on n_E
+ *   log-spaced gamma in [gamma_min, gamma_max] x n_s points s in [0, 1] with
+ *   y = y_cut (y_max / y_cut)^s, y_cut = photon_min_mc2 / gamma, y_max = 1 - 1/gamma.
+ * One brems table per entry of Z[0..n_Z).                                     */
+typedef struct {
+    int n_eta, n_y;
+    double eta_min, eta_max, y_min, y_max;
+    int n_E, n_s;
+    double gamma_min, gamma_max;
+    double photon_min_mc2;           /* hard-photon cut, m c^2 (Sec. 3: 1.0)        */
+    int n_Z;
+    const double* Z;                 /* host array, copied                          */
+} pe_table_params;
+
+/* One run (one laser-target configuration, Sec. 3). */
+typedef struct {
+    double a0, lambda_m;             /* peak normalised vector potential per component, wavelength */
+    int polarisation, geometry;      /* PE_LP_Y | PE_CP ; PE_PLANE_1D | PE_GAUSS_2D | PE_CONST     */
+    double w0_m, focus_x_m;          /* PE_GAUSS_2D waist and focal plane                           */
+    double flat_s, ramp_periods;     /* flat top (Sec. 3: 30 fs) and sin^2 ramps in periods          */
+    double E_const[3], B_const[3];   /* PE_CONST fields, normalised units                           */
+    double Z, charge_state, ne_over_nc;          /* target: atomic number, ion charge, n_e / n_c   */
+    double slab_x0_m, slab_thick_m, y_half_m;    /* slab [x0, x0+thick] (and |y| <= y_half in 2D)  */
+    double dt_over_T;                /* time step in laser periods                                  */
+    int precision;                   /* PE_F64 | PE_F32                                             */
+    int init_dist;                   /* PE_REST | PE_MAXWELL_JUTTNER | PE_BEAM | PE_CALLER          */
+    double T_mev, beam_gamma;        /* Maxwell-Juttner temperature; PE_BEAM Lorentz factor         */
+    uint64_t seed;                   /* Philox key                                                  */
+    uint32_t run_id;                 /* Philox counter word 1                                       */
+    int enable_ncs, enable_brems;
+    int box_enable;                  /* absorbing boundary in x (Sec. 3), default off               */
+    double box_x_m[2];
+} pe_run_params;
+
+/* Caller-owned device buffers of one run.
+ *   x, y, ux, uy, uz : n elements, float (PE_F32) or double (PE_F64); y is
+ *                      only read/written for PE_GAUSS_2D but must be valid.
+ *   tau              : n doubles (optical depth; always FP64).
+ *   photons          : photon_capacity records of 32 bytes
+ *                      {float x, y, energy, kx, ky, kz; uint32 step; uint32 id | mech << 31}
+ *   hist             : PE_HIST_WORDS uint64 (zeroed by pe_init_particles)
+ *   tally            : PE_TALLY_WORDS uint64 (zeroed by pe_init_particles)
+ *   events           : optional (may be NULL), n uint64 per-particle event
+ *                      fingerprints, zeroed by pe_init_particles: low 32 bits =
+ *                      NCS emissions | brems emissions << 16, high 32 bits =
+ *                      sum over emissions of (step + 1) * (1, or 0x9E3779B1 for
+ *                      brems) mod 2^32.  Used to compare event lists.
+ * Pointers must be 16-byte aligned.                                            */
+typedef struct {
+    void *x, *y, *ux, *uy, *uz, *tau;
+    void* photons;
+    int64_t photon_capacity;
+    void* hist;
+    void* tally;
+    void* events;
+} pe_buffers;
+
+/* Launch shape of the persistent FP32 kernel (the autotuner's knobs).
+ * block: threads per CTA (multiple of 32, <= 1024); ctas_per_sm: CTAs per SM
+ * in the grid; steps_per_launch: steps done per launch with the state held in
+ * registers (1 = state round-trips memory every step).  Zeros pick defaults. */
+typedef struct {
+    int block, ctas_per_sm, steps_per_launch;
+} pe_launch_config;
+
+/* Host copy of a run's results. */
+typedef struct {
+    uint64_t tally[PE_TALLY_WORDS];
+    uint64_t hist[PE_HIST_WORDS];
+    int64_t n_particles, steps_done;
+    int64_t photons_stored;          /* min(true count, capacity)                   */
+    double live_particle_steps;      /* sum over particles of steps advanced alive  */
+    double e_ncs_stored, e_ncs_below, e_br_stored, e_br_below, e_recoil_ncs, e_recoil_br;  /* m c^2 */
+} pe_tally_out;
+
+typedef struct pe_tables pe_tables;
+typedef struct pe_run pe_run;
+
+/* Build the NCS and brems tables on the host in FP64 (Sec. 2.2; Eq. 1 with
+ * Tsai's screening functions) and upload FP64 and FP32 copies to the current
+ * device.  Synchronous.  Errors: PE_ERR_ARG, PE_ERR_NOMEM, PE_ERR_CUDA.     */
+pe_status pe_create_tables(const pe_table_params* params, pe_tables** out);
+pe_status pe_destroy_tables(pe_tables* tables);
+
+/* Copy one table to host memory: which = 0 h(eta) [n_eta], 1 NCS CDF
+ * [n_eta*n_y], 2 classical CDF [n_y], 3 sigma_Z [n_E] (iz), 4 brems CDF
+ * [n_E*n_s] (iz).  *n_out receives the element count; cap too small -> ARG. */
+pe_status pe_tables_export(const pe_tables* tables, int which, int iz, double* host_out,
+                           int64_t cap, int64_t* n_out);
+
+/* Bind buffers to a new run and, unless init_dist == PE_CALLER, draw the
+ * initial positions (uniform in the slab) and momenta (rest, Maxwell-Juttner
+ * by Sobol's rejection, or a beam along +x) from the particle's Philox
+ * stream; always draws the initial optical depth tau = -ln U.  Zeroes hist,
+ * tally and the photon count.  Asynchronous on cuda_stream.  The run refers
+ * to tables, which must outlive it.  Z must be one of the table set's Z.
+ * Errors: PE_ERR_ARG (null, n < 0, n >= 2^31, Z not in tables, misaligned).  */
+pe_status pe_init_particles(const pe_tables* tables, const pe_run_params* params, int64_t n,
+                            const pe_buffers* buffers, void* cuda_stream, pe_run** out);
+
+/* Advance runs by n_steps.  n_runs == 1: PE_F64 runs use the plain kernel
+ * (one launch per step); PE_F32 runs use the persistent kernel.  n_runs > 1
+ * (<= PE_MAX_BATCH): all runs must be PE_F32 and share the first run's
+ * stream; they advance together in one persistent launch per
+ * steps_per_launch steps.  Asynchronous.  cfg may be NULL.                  */
+pe_status pe_step(pe_run* const* runs, int n_runs, int64_t n_steps);
+pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg);
+
+/* Synchronise the run's stream and copy tally, histograms and counters to
+ * *out.  Returns PE_ERR_BUFFER_FULL (after filling *out) if more photons
+ * were produced than the buffer holds; the counts stay exact.               */
+pe_status pe_tally(pe_run* run, pe_tally_out* out);
+
+pe_status pe_destroy(pe_run* run);
+
+/* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
+ * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */
+double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);
+
+/* Number of kernel launches the library has issued (all runs, this process). */
+int64_t pe_launch_count(void);
+
+const char* pe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -113,7 +113,8 @@ def lib():
             L.or_init.restype = C.c_int
             L.or_run.argtypes = [C.c_void_p, C.POINTER(RunParams), C.POINTER(C.c_int64), C.c_int64,
                                  C.c_int64, C.c_int64, dp, C.c_void_p, C.c_int64,
-                                 C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int]
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                 C.POINTER(C.c_uint64), C.c_int]
             L.or_run.restype = C.c_int
             L.or_fields.argtypes = [C.POINTER(RunParams), C.c_double, C.c_double, C.c_double, dp, dp]
             L.or_eta.argtypes = [dp, dp, dp, C.c_double]
@@ -221,8 +222,11 @@ def init(tables: Tables, run: RunParams, ids) -> np.ndarray:
 
 
 def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
-        capacity: int = 1 << 20, threads: int | None = None):
-    """Advance ``state`` (n x 6, in place) and return (photons, hist, tally)."""
+        capacity: int = 1 << 20, threads: int | None = None, events=None):
+    """Advance ``state`` (n x 6, in place); return (photons, true photon count, hist, tally).
+
+    ``events`` (optional uint64 array, one per particle) accumulates each particle's
+    event fingerprint (see oracle.h)."""
     ids = np.ascontiguousarray(ids, dtype=np.int64)
     assert state.dtype == np.float64 and state.flags.c_contiguous and state.shape == (len(ids), 6)
     photons = np.zeros(capacity, dtype=PHOTON_DTYPE)
@@ -233,7 +237,8 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
     rc = lib().or_run(tables._h, C.byref(run), ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids),
                       step0, n_steps, _dp(state), photons.ctypes.data_as(C.c_void_p), capacity,
                       C.byref(n_ph), hist.ctypes.data_as(C.POINTER(C.c_uint64)),
-                      tally.ctypes.data_as(C.POINTER(C.c_uint64)), nt)
+                      tally.ctypes.data_as(C.POINTER(C.c_uint64)),
+                      events.ctypes.data_as(C.POINTER(C.c_uint64)) if events is not None else None, nt)
     if rc != 0:
         raise RuntimeError("or_run failed")
     return photons[:min(n_ph.value, capacity)], n_ph.value, hist, tally

@@ -131,7 +131,10 @@ int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int6
 int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
            int64_t step0, int64_t n_steps, double* state,
            or_photon* photons, int64_t cap, int64_t* n_photons,
-           uint64_t* hist, uint64_t* tally, int n_threads);
+           uint64_t* hist, uint64_t* tally, uint64_t* events, int n_threads);
+/* events (nullable): per particle, low 32 bits = NCS count | brems count << 16,
+ * high 32 bits = sum over emissions of (step + 1) * (1 or 0x9E3779B1 for brems)
+ * mod 2^32 -- a fingerprint of the particle's event list.                     */
 
 /* normalised helpers (exposed for unit pins) */
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */

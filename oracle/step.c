@@ -308,8 +308,17 @@ static void recoil(double u[3], double gamma, double w, double khat[3]) {
     u[0] = khat[0] * un; u[1] = khat[1] * un; u[2] = khat[2] * un;
 }
 
+static void note_event(uint64_t* ev, int64_t n, int mech) {
+    if (!ev) return;
+    uint32_t cnt = (uint32_t)(*ev & 0xffffffffu), hs = (uint32_t)(*ev >> 32);
+    cnt += mech ? 0x10000u : 1u;
+    hs += (uint32_t)(n + 1) * (mech ? 0x9E3779B1u : 1u);
+    *ev = ((uint64_t)hs << 32) | cnt;
+}
+
 static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c, int64_t id,
-                    int64_t step0, int64_t n_steps, double* s, plist* pl, uint64_t* hist, uint64_t* tally) {
+                    int64_t step0, int64_t n_steps, double* s, plist* pl, uint64_t* hist, uint64_t* tally,
+                    uint64_t* ev) {
     double x = s[0], y = s[1];
     double u[3] = {s[2], s[3], s[4]};
     double tau = s[5];
@@ -336,6 +345,7 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
                 if (ew > gamma - 1.0) { ew = gamma - 1.0; tally[ORT_N_CLAMP]++; }
                 double k[3];
                 recoil(u, gamma, ew, k);
+                note_event(ev, n, 0);
                 double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 fx_add(tally + ORT_E_RECOIL_NCS, gamma - gn);
                 if (ew >= c->photon_min) {
@@ -371,6 +381,7 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
                     double ew = yy * gamma;
                     double k[3];
                     recoil(u, gamma, ew, k);
+                    note_event(ev, n, 1);
                     double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                     fx_add(tally + ORT_E_RECOIL_BR, gamma - gn);
                     if (ew >= c->photon_min) {
@@ -400,7 +411,7 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
 int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
            int64_t step0, int64_t n_steps, double* state,
            or_photon* photons, int64_t cap, int64_t* n_photons,
-           uint64_t* hist, uint64_t* tally, int n_threads) {
+           uint64_t* hist, uint64_t* tally, uint64_t* events, int n_threads) {
     if (!t || !r || n_ids < 0 || n_steps < 0) return -1;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
@@ -415,7 +426,8 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
         me = omp_get_thread_num();
 #endif
         run_one(t, r, &c, ids[k], step0, n_steps, state + 6 * k, &lists[k],
-                th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS);
+                th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS,
+                events ? events + k : NULL);
     }
     for (int k = 0; k < nt; ++k) {
         const uint64_t* th = th_tally + (size_t)k * ORT_WORDS;

@@ -1,0 +1,268 @@
+"""GB300 photon-emission step (arXiv:1612.07592, Wan et al.) -- Python binding.
+
+A thin ctypes layer over ``libpe.so`` (the C ABI in ``include/pe.h``): the same
+entry points with the same names, plus a small ``Run`` helper that allocates
+the caller-owned buffers as torch CUDA tensors.  Every step of the physics runs
+in the library's CUDA kernels; this module only marshals arguments.  Importing
+it needs no GPU; calling into the library needs the compiled ``libpe.so`` and a
+CUDA device, and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpe.so")
+
+PE_OK, PE_ERR_ARG, PE_ERR_CUDA, PE_ERR_NOMEM, PE_ERR_BUFFER_FULL, PE_ERR_TABLE_RANGE, PE_ERR_TIMEOUT, PE_ERR_STATE = range(8)
+PE_LP_Y, PE_CP = 0, 1
+PE_PLANE_1D, PE_GAUSS_2D, PE_CONST = 0, 1, 2
+PE_F64, PE_F32 = 0, 1
+PE_REST, PE_MAXWELL_JUTTNER, PE_BEAM, PE_CALLER = 0, 1, 2, 3
+HIST_E_BINS, HIST_T_BINS = 512, 180
+HIST_WORDS = 2 * HIST_E_BINS + 2 * HIST_T_BINS
+TALLY_WORDS = 32
+MAX_BATCH = 64
+T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4, N_ETA_ABOVE=5,
+         N_ETA_BELOW=6, N_GAMMA_ABOVE=7, N_KILLED=8, KILLED_STEPS=9, N_CLAMP=10, N_HIST_OVER=11,
+         E_NCS_STORED=16, E_NCS_BELOW=18, E_BR_STORED=20, E_BR_BELOW=22, E_RECOIL_NCS=24, E_RECOIL_BR=26)
+PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
+                         ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
+EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
+            "pe_step_ex", "pe_tally", "pe_destroy", "pe_a0_from_intensity", "pe_launch_count", "pe_last_error"]
+
+
+class PeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pe status {status}: {msg}")
+        self.status = status
+
+
+class TableParams(C.Structure):
+    _fields_ = [("n_eta", C.c_int), ("n_y", C.c_int), ("eta_min", C.c_double), ("eta_max", C.c_double),
+                ("y_min", C.c_double), ("y_max", C.c_double), ("n_E", C.c_int), ("n_s", C.c_int),
+                ("gamma_min", C.c_double), ("gamma_max", C.c_double), ("photon_min_mc2", C.c_double),
+                ("n_Z", C.c_int), ("Z", C.POINTER(C.c_double))]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("a0", C.c_double), ("lambda_m", C.c_double), ("polarisation", C.c_int), ("geometry", C.c_int),
+                ("w0_m", C.c_double), ("focus_x_m", C.c_double), ("flat_s", C.c_double),
+                ("ramp_periods", C.c_double), ("E_const", C.c_double * 3), ("B_const", C.c_double * 3),
+                ("Z", C.c_double), ("charge_state", C.c_double), ("ne_over_nc", C.c_double),
+                ("slab_x0_m", C.c_double), ("slab_thick_m", C.c_double), ("y_half_m", C.c_double),
+                ("dt_over_T", C.c_double), ("precision", C.c_int), ("init_dist", C.c_int),
+                ("T_mev", C.c_double), ("beam_gamma", C.c_double), ("seed", C.c_uint64),
+                ("run_id", C.c_uint32), ("enable_ncs", C.c_int), ("enable_brems", C.c_int),
+                ("box_enable", C.c_int), ("box_x_m", C.c_double * 2)]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
+                ("uz", C.c_void_p), ("tau", C.c_void_p), ("photons", C.c_void_p),
+                ("photon_capacity", C.c_int64), ("hist", C.c_void_p), ("tally", C.c_void_p),
+                ("events", C.c_void_p)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("block", C.c_int), ("ctas_per_sm", C.c_int), ("steps_per_launch", C.c_int)]
+
+
+class TallyOut(C.Structure):
+    _fields_ = [("tally", C.c_uint64 * TALLY_WORDS), ("hist", C.c_uint64 * HIST_WORDS),
+                ("n_particles", C.c_int64), ("steps_done", C.c_int64), ("photons_stored", C.c_int64),
+                ("live_particle_steps", C.c_double), ("e_ncs_stored", C.c_double), ("e_ncs_below", C.c_double),
+                ("e_br_stored", C.c_double), ("e_br_below", C.c_double), ("e_recoil_ncs", C.c_double),
+                ("e_recoil_br", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libpe.so.  Raises if the library has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            vp = C.c_void_p
+            L.pe_create_tables.argtypes = [C.POINTER(TableParams), C.POINTER(vp)]
+            L.pe_destroy_tables.argtypes = [vp]
+            L.pe_tables_export.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int64,
+                                           C.POINTER(C.c_int64)]
+            L.pe_init_particles.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), vp,
+                                            C.POINTER(vp)]
+            L.pe_step.argtypes = [C.POINTER(vp), C.c_int, C.c_int64]
+            L.pe_step_ex.argtypes = [C.POINTER(vp), C.c_int, C.c_int64, C.POINTER(LaunchConfig)]
+            L.pe_tally.argtypes = [vp, C.POINTER(TallyOut)]
+            L.pe_destroy.argtypes = [vp]
+            L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.pe_a0_from_intensity.restype = C.c_double
+            L.pe_launch_count.restype = C.c_int64
+            L.pe_last_error.restype = C.c_char_p
+            for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
+                         "pe_step", "pe_step_ex", "pe_tally", "pe_destroy"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, allow=()):
+    if status != PE_OK and status not in allow:
+        raise PeError(status, lib().pe_last_error().decode())
+    return status
+
+
+# ---------------------------------------------------------------- C ABI ----
+def table_params(**kw):
+    d = dict(n_eta=128, n_y=128, eta_min=1e-4, eta_max=1e2, y_min=1e-6, y_max=1e2, n_E=128, n_s=128,
+             gamma_min=2.0, gamma_max=1e6, photon_min_mc2=1.0)
+    Z = kw.pop("Z", (13.0, 79.0))
+    d.update(kw)
+    return d, tuple(float(z) for z in Z)
+
+
+def pe_create_tables(params: dict, Z) -> int:
+    z = (C.c_double * len(Z))(*Z)
+    p = TableParams(**params, n_Z=len(Z), Z=z)
+    h = C.c_void_p()
+    _check(lib().pe_create_tables(C.byref(p), C.byref(h)))
+    return h.value
+
+
+def pe_destroy_tables(h: int):
+    _check(lib().pe_destroy_tables(h))
+
+
+def pe_tables_export(h: int, which: int, iz: int = 0) -> np.ndarray:
+    n = C.c_int64(0)
+    dummy = (C.c_double * 1)()
+    lib().pe_tables_export(h, which, iz, dummy, 0, C.byref(n))
+    out = np.empty(max(n.value, 1), dtype=np.float64)
+    _check(lib().pe_tables_export(h, which, iz, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+    return out[:n.value]
+
+
+def run_params(**kw) -> RunParams:
+    d = dict(a0=27.0, lambda_m=1e-6, polarisation=0, geometry=0, w0_m=3e-6, focus_x_m=2e-6, flat_s=30e-15,
+             ramp_periods=1.0, Z=13.0, charge_state=11.0, ne_over_nc=50.0, slab_x0_m=2e-6, slab_thick_m=1e-6,
+             y_half_m=3e-6, dt_over_T=0.01, precision=PE_F64, init_dist=PE_REST, T_mev=1.0, beam_gamma=1.0,
+             seed=0, run_id=0, enable_ncs=1, enable_brems=1, box_enable=0)
+    E = kw.pop("E_const", (0.0, 0.0, 0.0))
+    B = kw.pop("B_const", (0.0, 0.0, 0.0))
+    box = kw.pop("box_x_m", (0.0, 0.0))
+    kw.pop("iz", None)
+    d.update(kw)
+    r = RunParams(**d)
+    r.E_const = (C.c_double * 3)(*E)
+    r.B_const = (C.c_double * 3)(*B)
+    r.box_x_m = (C.c_double * 2)(*box)
+    return r
+
+
+def pe_init_particles(tables: int, params: RunParams, n: int, buffers: Buffers, stream: int) -> int:
+    h = C.c_void_p()
+    _check(lib().pe_init_particles(tables, C.byref(params), n, C.byref(buffers), stream, C.byref(h)))
+    return h.value
+
+
+def pe_step(runs, n_steps: int):
+    arr = (C.c_void_p * len(runs))(*runs)
+    _check(lib().pe_step(arr, len(runs), n_steps))
+
+
+def pe_step_ex(runs, n_steps: int, block: int = 0, ctas_per_sm: int = 0, steps_per_launch: int = 0):
+    arr = (C.c_void_p * len(runs))(*runs)
+    cfg = LaunchConfig(block, ctas_per_sm, steps_per_launch)
+    _check(lib().pe_step_ex(arr, len(runs), n_steps, C.byref(cfg)))
+
+
+def pe_tally(run: int) -> TallyOut:
+    out = TallyOut()
+    st = _check(lib().pe_tally(run, C.byref(out)), allow=(PE_ERR_BUFFER_FULL,))
+    out.status = st
+    return out
+
+
+def pe_destroy(run: int):
+    _check(lib().pe_destroy(run))
+
+
+def pe_a0_from_intensity(I_wcm2: float, lambda_m: float = 1e-6, polarisation: int = PE_LP_Y) -> float:
+    return lib().pe_a0_from_intensity(I_wcm2, lambda_m, polarisation)
+
+
+def pe_launch_count() -> int:
+    return lib().pe_launch_count()
+
+
+# ------------------------------------------------------- torch-side helper ----
+class Run:
+    """One run with caller-owned buffers allocated as torch CUDA tensors."""
+
+    def __init__(self, tables: int, params: RunParams, n: int, capacity: int = 1 << 20, stream=None,
+                 device="cuda", events: bool = False):
+        import torch
+        self.torch = torch
+        dt = torch.float32 if params.precision == PE_F32 else torch.float64
+        dev = torch.device(device)
+        m = max(int(n), 1)
+        self.n = int(n)
+        self.x = torch.zeros(m, dtype=dt, device=dev)
+        self.y = torch.zeros(m, dtype=dt, device=dev)
+        self.ux = torch.zeros(m, dtype=dt, device=dev)
+        self.uy = torch.zeros(m, dtype=dt, device=dev)
+        self.uz = torch.zeros(m, dtype=dt, device=dev)
+        self.tau = torch.zeros(m, dtype=torch.float64, device=dev)
+        self.capacity = int(capacity)
+        self.photons = torch.zeros(max(self.capacity, 1) * 8, dtype=torch.int32, device=dev)
+        self.hist = torch.zeros(HIST_WORDS, dtype=torch.int64, device=dev)
+        self.tally = torch.zeros(TALLY_WORDS, dtype=torch.int64, device=dev)
+        self.events = torch.zeros(m, dtype=torch.int64, device=dev) if events else None
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.params = params
+        b = Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),
+                    self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
+                    self.hist.data_ptr(), self.tally.data_ptr(),
+                    self.events.data_ptr() if events else None)
+        self.handle = pe_init_particles(tables, params, self.n, b, self.stream.cuda_stream)
+
+    def state(self) -> np.ndarray:
+        """Host copy (n x 6, float64): x, y, ux, uy, uz, tau."""
+        cols = [self.x, self.y, self.ux, self.uy, self.uz, self.tau]
+        return np.stack([c[:self.n].double().cpu().numpy() for c in cols], axis=1)
+
+    def photon_records(self, count: int | None = None) -> np.ndarray:
+        out = self.tally_out() if count is None else None
+        k = count if count is not None else out.photons_stored
+        raw = self.photons[: k * 8].cpu().numpy()
+        return raw.view(PHOTON_DTYPE)
+
+    def event_words(self) -> np.ndarray:
+        return self.events[:self.n].cpu().numpy().view(np.uint64)
+
+    def tally_out(self) -> TallyOut:
+        return pe_tally(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fixed_to_float(tally, idx: int) -> float:
+    return float(int(tally[idx + 1]) & 0xFFFFFFFFFFFFFFFF) + float(int(tally[idx]) & 0xFFFFFFFFFFFFFFFF) / 2.0 ** 64

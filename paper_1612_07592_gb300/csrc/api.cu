@@ -1,0 +1,365 @@
+// api.cu -- the C ABI declared in include/pe.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace pe;
+
+struct pe_tables {
+    HostTables host;
+    TablesDev dev;
+    void* dmem = nullptr;
+    int device = 0;
+};
+
+struct pe_run {
+    RunDev dev;
+    pe_run_params params;
+    pe_buffers buf;
+    const pe_tables* tables = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t steps_done = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+pe_status fail(pe_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+pe_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(PE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// largest value <= dt with 11 significant bits, so n * dt_hi is exact in float for n < 2^13
+void split_dt(double dt, double* hi, double* lo) {
+    int e;
+    double m = std::frexp(dt, &e);
+    double mh = std::floor(std::ldexp(m, 11));
+    *hi = std::ldexp(mh, e - 11);
+    *lo = dt - *hi;
+}
+
+}  // namespace
+
+extern "C" const char* pe_last_error(void) { return g_err.c_str(); }
+extern "C" int64_t pe_launch_count(void) { return g_launches.load(); }
+
+extern "C" double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation) {
+    double a = 0.855 * (lambda_m * 1e6) * std::sqrt(I_wcm2 / 1e18);
+    return polarisation == PE_CP ? a / std::sqrt(2.0) : a;
+}
+
+extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out) {
+    if (!p || !out) return fail(PE_ERR_ARG, "pe_create_tables: null argument");
+    *out = nullptr;
+    if (p->n_eta < 2 || p->n_y < 2 || p->n_E < 2 || p->n_s < 2 || p->n_eta > 4096 || p->n_y > 4096 ||
+        p->n_E > 4096 || p->n_s > 4096)
+        return fail(PE_ERR_ARG, "pe_create_tables: table sizes must be in [2, 4096]");
+    if (!(p->eta_min > 0 && p->eta_max > p->eta_min && p->y_min > 0 && p->y_max > p->y_min &&
+          p->gamma_min > 1 && p->gamma_max > p->gamma_min && p->photon_min_mc2 > 0))
+        return fail(PE_ERR_ARG, "pe_create_tables: ranges must be positive and increasing (gamma_min > 1)");
+    if (p->n_Z < 1 || p->n_Z > 16 || !p->Z) return fail(PE_ERR_ARG, "pe_create_tables: need 1..16 values of Z");
+    for (int i = 0; i < p->n_Z; ++i)
+        if (!(p->Z[i] >= 1.0 && p->Z[i] <= 120.0)) return fail(PE_ERR_ARG, "pe_create_tables: Z out of [1, 120]");
+
+    pe_tables* t = new pe_tables();
+    std::string err;
+    if (!build_host_tables(*p, t->host, &err)) {
+        delete t;
+        return fail(PE_ERR_ARG, "pe_create_tables: " + err);
+    }
+    cudaGetDevice(&t->device);
+    const HostTables& H = t->host;
+    size_t n_h = H.h.size(), n_c = H.cdf.size(), n_sg = H.sigma.size(), n_b = H.bcdf.size();
+    size_t n_all = n_h + n_c + n_sg + n_b;
+    size_t bytes = n_all * (sizeof(double) + sizeof(float)) + 64;
+    cudaError_t e = cudaMalloc(&t->dmem, bytes);
+    if (e != cudaSuccess) {
+        delete t;
+        return fail(PE_ERR_NOMEM, std::string("pe_create_tables: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    std::vector<double> all64;
+    all64.reserve(n_all);
+    all64.insert(all64.end(), H.h.begin(), H.h.end());
+    all64.insert(all64.end(), H.cdf.begin(), H.cdf.end());
+    all64.insert(all64.end(), H.sigma.begin(), H.sigma.end());
+    all64.insert(all64.end(), H.bcdf.begin(), H.bcdf.end());
+    std::vector<float> all32(all64.begin(), all64.end());
+    double* d64 = static_cast<double*>(t->dmem);
+    float* d32 = reinterpret_cast<float*>(d64 + n_all);
+    e = cudaMemcpy(d64, all64.data(), n_all * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d32, all32.data(), n_all * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(t->dmem);
+        delete t;
+        return cuda_fail(e, "pe_create_tables: cudaMemcpy");
+    }
+    TablesDev& D = t->dev;
+    D.h64 = d64; D.cdf64 = d64 + n_h; D.sig64 = D.cdf64 + n_c; D.bcdf64 = D.sig64 + n_sg;
+    D.h32 = d32; D.cdf32 = d32 + n_h; D.sig32 = D.cdf32 + n_c; D.bcdf32 = D.sig32 + n_sg;
+    D.n_eta = p->n_eta; D.n_y = p->n_y; D.n_E = p->n_E; D.n_s = p->n_s; D.n_Z = p->n_Z;
+    D.eta_min = p->eta_min;
+    D.ln_eta_min = std::log(p->eta_min);
+    D.inv_dln_eta = (p->n_eta - 1) / (std::log(p->eta_max) - std::log(p->eta_min));
+    D.ln_y_min = std::log(p->y_min);
+    D.dln_y = (std::log(p->y_max) - std::log(p->y_min)) / (p->n_y - 1);
+    D.y_min = p->y_min; D.y_max = p->y_max;
+    D.ln_g_min = std::log(p->gamma_min);
+    D.inv_dln_g = (p->n_E - 1) / (std::log(p->gamma_max) - std::log(p->gamma_min));
+    D.photon_min = p->photon_min_mc2;
+    D.h_classical = 5.0 * kPi / 3.0;
+    *out = t;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_destroy_tables(pe_tables* t) {
+    if (!t) return fail(PE_ERR_ARG, "pe_destroy_tables: null");
+    if (t->dmem) cudaFree(t->dmem);
+    delete t;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_tables_export(const pe_tables* t, int which, int iz, double* out, int64_t cap,
+                                      int64_t* n_out) {
+    if (!t || !out) return fail(PE_ERR_ARG, "pe_tables_export: null argument");
+    const HostTables& H = t->host;
+    const pe_table_params& p = H.p;
+    const double* src = nullptr;
+    int64_t n = 0;
+    if ((which == 3 || which == 4) && (iz < 0 || iz >= p.n_Z)) return fail(PE_ERR_ARG, "pe_tables_export: bad iz");
+    switch (which) {
+        case 0: src = H.h.data(); n = p.n_eta; break;
+        case 1: src = H.cdf.data(); n = (int64_t)p.n_eta * p.n_y; break;
+        case 2: src = H.cdf.data() + (size_t)p.n_eta * p.n_y; n = p.n_y; break;
+        case 3: src = H.sigma.data() + (size_t)iz * p.n_E; n = p.n_E; break;
+        case 4: src = H.bcdf.data() + (size_t)iz * p.n_E * p.n_s; n = (int64_t)p.n_E * p.n_s; break;
+        default: return fail(PE_ERR_ARG, "pe_tables_export: which must be 0..4");
+    }
+    if (n_out) *n_out = n;
+    if (cap < n) return fail(PE_ERR_ARG, "pe_tables_export: output too small");
+    std::memcpy(out, src, sizeof(double) * n);
+    return PE_OK;
+}
+
+extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* rp, int64_t n,
+                                       const pe_buffers* b, void* stream, pe_run** out) {
+    if (!t || !rp || !b || !out) return fail(PE_ERR_ARG, "pe_init_particles: null argument");
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_init_particles: n must be in [0, 2^31)");
+    if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_init_particles: precision");
+    if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_CONST) return fail(PE_ERR_ARG, "pe_init_particles: geometry");
+    if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP) return fail(PE_ERR_ARG, "pe_init_particles: polarisation");
+    if (rp->init_dist < PE_REST || rp->init_dist > PE_CALLER) return fail(PE_ERR_ARG, "pe_init_particles: init_dist");
+    if (!(rp->lambda_m > 0 && rp->dt_over_T > 0 && rp->charge_state > 0 && rp->ne_over_nc >= 0 &&
+          rp->ramp_periods > 0 && rp->flat_s >= 0))
+        return fail(PE_ERR_ARG, "pe_init_particles: lambda, dt, charge state, ramp must be positive");
+    if (rp->geometry == PE_GAUSS_2D && !(rp->w0_m > 0)) return fail(PE_ERR_ARG, "pe_init_particles: w0");
+    if (rp->init_dist == PE_MAXWELL_JUTTNER && !(rp->T_mev > 0)) return fail(PE_ERR_ARG, "pe_init_particles: T_mev");
+    if (rp->init_dist == PE_BEAM && !(rp->beam_gamma >= 1)) return fail(PE_ERR_ARG, "pe_init_particles: beam_gamma");
+    if (n > 0) {
+        if (!b->x || !b->y || !b->ux || !b->uy || !b->uz || !b->tau || !b->hist || !b->tally)
+            return fail(PE_ERR_ARG, "pe_init_particles: null buffer");
+        const void* ps[] = {b->x, b->y, b->ux, b->uy, b->uz, b->tau, b->hist, b->tally};
+        for (const void* q : ps)
+            if (!aligned16(q)) return fail(PE_ERR_ARG, "pe_init_particles: buffers must be 16-byte aligned");
+    }
+    if (!b->hist || !b->tally) return fail(PE_ERR_ARG, "pe_init_particles: null hist/tally");
+    if (b->events && !aligned16(b->events)) return fail(PE_ERR_ARG, "pe_init_particles: events misaligned");
+    if (b->photon_capacity < 0 || (b->photon_capacity > 0 && (!b->photons || !aligned16(b->photons))))
+        return fail(PE_ERR_ARG, "pe_init_particles: photon buffer");
+    int iz = -1;
+    for (int k = 0; k < t->host.p.n_Z; ++k)
+        if (std::fabs(t->host.Z[k] - rp->Z) < 1e-9) iz = k;
+    if (iz < 0) return fail(PE_ERR_ARG, "pe_init_particles: Z is not in the table set");
+
+    pe_run* r = new pe_run();
+    r->params = *rp;
+    r->buf = *b;
+    r->tables = t;
+    r->stream = static_cast<cudaStream_t>(stream);
+    RunDev& d = r->dev;
+    std::memset(&d, 0, sizeof(d));
+    d.x = b->x; d.y = b->y; d.ux = b->ux; d.uy = b->uy; d.uz = b->uz;
+    d.tau = static_cast<double*>(b->tau);
+    d.photons = static_cast<uint8_t*>(b->photons);
+    d.hist = static_cast<unsigned long long*>(b->hist);
+    d.tally = static_cast<unsigned long long*>(b->tally);
+    d.events = static_cast<unsigned long long*>(b->events);
+    d.n = n;
+    d.capacity = b->photon_capacity;
+    d.step0 = 0;
+    const double kl = 2.0 * kPi / rp->lambda_m;
+    d.dt = rp->dt_over_T * 2.0 * kPi;
+    split_dt(d.dt, &d.dt_hi, &d.dt_lo);
+    d.E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
+    d.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * d.E_S * d.dt;
+    double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
+    double n_i = rp->ne_over_nc * n_c / rp->charge_state;
+    d.K_br = n_i * kAlpha * kRe * kRe * (d.dt / kl);
+    d.x0 = rp->slab_x0_m * kl;
+    d.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
+    d.yh = rp->y_half_m * kl;
+    d.box0 = rp->box_x_m[0] * kl;
+    d.box1 = rp->box_x_m[1] * kl;
+    d.inv_log_emax = 1.0 / std::log(kHistEmaxMeV / kMec2MeV);
+    d.a0 = rp->a0;
+    d.w0 = rp->w0_m * kl;
+    d.zr = 0.5 * d.w0 * d.w0;
+    d.xf = rp->focus_x_m * kl;
+    d.phi_r = 2.0 * kPi * rp->ramp_periods;
+    d.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
+    for (int k = 0; k < 3; ++k) { d.E_const[k] = rp->E_const[k]; d.B_const[k] = rp->B_const[k]; }
+    d.geometry = rp->geometry;
+    d.polarisation = rp->polarisation;
+    d.enable_ncs = rp->enable_ncs;
+    d.enable_brems = rp->enable_brems;
+    d.box_enable = rp->box_enable;
+    d.iz = iz;
+    d.run_id = rp->run_id;
+    d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
+    d.seed_hi = (uint32_t)(rp->seed >> 32);
+
+    cudaError_t e = cudaMemsetAsync(b->hist, 0, sizeof(uint64_t) * PE_HIST_WORDS, r->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->tally, 0, sizeof(uint64_t) * PE_TALLY_WORDS, r->stream);
+    if (e == cudaSuccess && b->events && n > 0) e = cudaMemsetAsync(b->events, 0, sizeof(uint64_t) * n, r->stream);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(e, "pe_init_particles: cudaMemsetAsync");
+    }
+    double theta = rp->T_mev / kMec2MeV;
+    double beam_u = rp->init_dist == PE_BEAM ? std::sqrt(rp->beam_gamma * rp->beam_gamma - 1.0) : 0.0;
+    if (n > 0) {
+        launch_init(t->dev, d, rp->precision, rp->init_dist, theta, beam_u, r->stream);
+        g_launches++;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            delete r;
+            return cuda_fail(e, "pe_init_particles: k_init");
+        }
+    }
+    *out = r;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg) {
+    if (!runs || n_runs < 1 || n_runs > PE_MAX_BATCH) return fail(PE_ERR_ARG, "pe_step: need 1..64 runs");
+    if (n_steps < 0) return fail(PE_ERR_ARG, "pe_step: n_steps < 0");
+    for (int k = 0; k < n_runs; ++k)
+        if (!runs[k]) return fail(PE_ERR_ARG, "pe_step: null run");
+    const pe_tables* t = runs[0]->tables;
+    int prec = runs[0]->params.precision;
+    for (int k = 1; k < n_runs; ++k) {
+        if (runs[k]->tables != t) return fail(PE_ERR_STATE, "pe_step: runs of a batch must share one table set");
+        if (runs[k]->params.precision != prec) return fail(PE_ERR_STATE, "pe_step: runs of a batch must share precision");
+    }
+    for (int k = 0; k < n_runs; ++k)
+        if (runs[k]->steps_done + n_steps >= (int64_t(1) << 32))
+            return fail(PE_ERR_ARG, "pe_step: step index would exceed 2^32");
+    if (n_steps == 0) return PE_OK;
+    cudaStream_t s = runs[0]->stream;
+
+    if (n_runs == 1 && prec == PE_F64 && !(cfg && cfg->steps_per_launch > 0)) {
+        pe_run* r = runs[0];
+        RunDev d = r->dev;
+        for (int64_t k = 0; k < n_steps; ++k) {
+            d.step0 = r->steps_done + k;
+            launch_step_plain_f64(t->dev, d, s);
+            g_launches++;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "pe_step: k_step_plain");
+        r->steps_done += n_steps;
+        return PE_OK;
+    }
+
+    int block = (cfg && cfg->block > 0) ? cfg->block : 256;
+    if (block % 32 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be a multiple of 32, <= 256");
+    int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 2048);
+    int dev;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem = persistent_smem_bytes(t->dev, prec);
+    int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : persistent_occupancy(prec, block, smem);
+    if (per_sm < 1) per_sm = 1;
+    BatchDev b;   // host staging; passed by value to the kernel
+    std::memset(&b, 0, sizeof(b));
+    b.n_runs = n_runs;
+    b.tile = block;
+    b.tile_start[0] = 0;
+    for (int k = 0; k < n_runs; ++k) {
+        b.runs[k] = runs[k]->dev;
+        b.tile_start[k + 1] = b.tile_start[k] + (runs[k]->dev.n + block - 1) / block;
+    }
+    int64_t n_tiles = b.tile_start[n_runs];
+    if (n_tiles == 0) {
+        for (int k = 0; k < n_runs; ++k) runs[k]->steps_done += n_steps;
+        return PE_OK;
+    }
+    int grid_cap = sms * per_sm;
+    int grid = (int)std::min<int64_t>(n_tiles, grid_cap);
+    for (int64_t done = 0; done < n_steps; done += K) {
+        int k_now = (int)std::min<int64_t>(K, n_steps - done);
+        for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
+        if (prec == PE_F32)
+            launch_step_persistent_f32(t->dev, b, k_now, grid, block, s);
+        else
+            launch_step_persistent_f64(t->dev, b, k_now, grid, block, s);
+        g_launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pe_step: k_step_persistent");
+    for (int k = 0; k < n_runs; ++k) runs[k]->steps_done += n_steps;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_step(pe_run* const* runs, int n_runs, int64_t n_steps) {
+    return pe_step_ex(runs, n_runs, n_steps, nullptr);
+}
+
+static double fx_value(const uint64_t* w, int i) {
+    return (double)w[i + 1] + (double)w[i] * 0x1.0p-64;
+}
+
+extern "C" pe_status pe_tally(pe_run* r, pe_tally_out* out) {
+    if (!r || !out) return fail(PE_ERR_ARG, "pe_tally: null argument");
+    cudaError_t e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_tally: stream");
+    e = cudaMemcpy(out->tally, r->buf.tally, sizeof(out->tally), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out->hist, r->buf.hist, sizeof(out->hist), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_tally: copy");
+    out->n_particles = r->dev.n;
+    out->steps_done = r->steps_done;
+    uint64_t np = out->tally[PE_T_N_PHOTONS];
+    out->photons_stored = (int64_t)std::min<uint64_t>(np, (uint64_t)r->buf.photon_capacity);
+    double killed = (double)out->tally[PE_T_N_KILLED];
+    out->live_particle_steps = ((double)r->dev.n - killed) * (double)r->steps_done + (double)out->tally[PE_T_KILLED_STEPS];
+    out->e_ncs_stored = fx_value(out->tally, PE_T_E_NCS_STORED);
+    out->e_ncs_below = fx_value(out->tally, PE_T_E_NCS_BELOW);
+    out->e_br_stored = fx_value(out->tally, PE_T_E_BR_STORED);
+    out->e_br_below = fx_value(out->tally, PE_T_E_BR_BELOW);
+    out->e_recoil_ncs = fx_value(out->tally, PE_T_E_RECOIL_NCS);
+    out->e_recoil_br = fx_value(out->tally, PE_T_E_RECOIL_BR);
+    if (np > (uint64_t)r->buf.photon_capacity)
+        return fail(PE_ERR_BUFFER_FULL, "pe_tally: photon buffer overflowed (counts are exact)");
+    return PE_OK;
+}
+
+extern "C" pe_status pe_destroy(pe_run* r) {
+    if (!r) return fail(PE_ERR_ARG, "pe_destroy: null");
+    delete r;
+    return PE_OK;
+}

@@ -1,0 +1,99 @@
+// internal.h -- descriptors shared by the host API and the kernels of libpe.
+// Everything here is passed to kernels by value (kernel parameters up to
+// 32 KB), so a launch needs no device-side descriptor copies and can be
+// captured in a CUDA graph as is.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pe.h"
+
+namespace pe {
+
+// physical constants (CODATA 2018)
+constexpr double kAlpha = 7.2973525693e-3;
+constexpr double kRe = 2.8179403262e-15;        // classical electron radius [m]
+constexpr double kMec2MeV = 0.51099895000;      // m_e c^2 [MeV]
+constexpr double kHbarcMeVm = 197.3269804e-15;  // hbar c [MeV m]
+constexpr double kC = 299792458.0;              // [m/s]
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kHistEmaxMeV = 10000.0;        // top edge of the energy histogram
+
+// Device view of one table set.  f32 and f64 copies of every table.
+struct TablesDev {
+    const float* h32;   const double* h64;      // [n_eta]
+    const float* cdf32; const double* cdf64;    // [(n_eta + 1) * n_y]; row n_eta = classical limit
+    const float* sig32; const double* sig64;    // [n_Z * n_E]
+    const float* bcdf32; const double* bcdf64;  // [n_Z * n_E * n_s]
+    int n_eta, n_y, n_E, n_s, n_Z;
+    double eta_min, ln_eta_min, inv_dln_eta;    // row position = (ln eta - ln eta_min) * inv
+    double ln_y_min, dln_y, y_min, y_max;
+    double ln_g_min, inv_dln_g;
+    double photon_min;
+    double h_classical;                         // 5 pi / 3
+};
+
+// Device view of one run.
+struct RunDev {
+    // state (float or double per precision; tau always double)
+    void *x, *y, *ux, *uy, *uz;
+    double* tau;
+    uint8_t* photons;
+    unsigned long long* hist;
+    unsigned long long* tally;
+    unsigned long long* events;   // optional per-particle event fingerprints
+    int64_t n;
+    int64_t capacity;
+    int64_t step0;            // step index of the first step of this launch
+    // step
+    double dt, dt_hi, dt_lo;  // dt split so that n * dt_hi is exact in float for n < 2^13
+    double E_S, ncs_coef;     // ncs_coef = sqrt(3) alpha / (2 pi) * E_S * dt
+    double K_br;              // n_i alpha r_e^2 (c dt): x_b = K_br * sigma[alpha r_e^2] * beta
+    double x0, x1, yh;        // slab (normalised)
+    double box0, box1;
+    double inv_log_emax;      // 1 / ln(E_hist_max / m c^2)
+    // fields
+    double a0, w0, zr, xf, phi_r, phi_f;
+    double E_const[3], B_const[3];
+    int geometry, polarisation;
+    int enable_ncs, enable_brems, box_enable;
+    int iz;                   // brems table index
+    uint32_t run_id;
+    uint32_t seed_lo, seed_hi;
+};
+
+// Batched launch: runs and their tile prefix.
+struct BatchDev {
+    int n_runs;
+    int tile;                           // particles per tile
+    int64_t tile_start[PE_MAX_BATCH + 1];
+    RunDev runs[PE_MAX_BATCH];
+};
+
+// host-side table build (tables.cpp)
+struct HostTables {
+    pe_table_params p;
+    std::vector<double> Z;
+    std::vector<double> h;       // n_eta
+    std::vector<double> cdf;     // (n_eta + 1) * n_y, last row classical
+    std::vector<double> sigma;   // n_Z * n_E
+    std::vector<double> bcdf;    // n_Z * n_E * n_s
+    double classical_total = 0;
+};
+bool build_host_tables(const pe_table_params& p, HostTables& out, std::string* err);
+
+// kernels.cu
+void launch_init(const TablesDev& t, const RunDev& r, int precision, int init_dist, double theta,
+                 double beam_u, cudaStream_t s);
+void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s);
+void launch_step_persistent_f32(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+                                cudaStream_t s);
+void launch_step_persistent_f64(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+                                cudaStream_t s);
+int persistent_smem_bytes(const TablesDev& t, int precision);
+int persistent_occupancy(int precision, int block, int smem);
+
+}  // namespace pe

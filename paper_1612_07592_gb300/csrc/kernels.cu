@@ -1,0 +1,407 @@
+// kernels.cu -- the emission-step kernels for sm_103a.
+//
+//  k_init            one thread per particle: initial position, momentum and
+//                    optical depth from the particle's Philox stream.
+//  k_step_plain      FP64, one thread per particle, one step per launch,
+//                    tables read from global memory, histograms and tallies
+//                    by global atomics (the plain per-run path).
+//  k_step_persistent grid-stride over tiles of one or many runs, K steps per
+//                    launch with the particle state in registers, the rate
+//                    tables (h(eta), sigma_Z(gamma)) staged in shared memory,
+//                    photon append by warp-aggregated atomics, histograms and
+//                    tallies accumulated in shared memory and flushed once per
+//                    run per CTA.  Instantiated for float (fast path) and double.
+//
+// Step order per particle (Sec. 2.2): fields at (x^n, t^n) -> Boris push ->
+// eta -> NCS optical depth (emission at tau <= 0) -> brems test (Eq. 4) ->
+// position update.  Both emissions may fire in one step; brems sees the
+// momentum after the NCS recoil.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "physics.cuh"
+
+namespace pe {
+
+// ---------------------------------------------------------------------------
+// accumulation helpers
+// ---------------------------------------------------------------------------
+// 128-bit fixed-point add of v >= 0 (m c^2) into (lo, hi): exact, order-free
+__device__ __forceinline__ void fx_add(unsigned long long* w, double v) {
+    if (!(v > 0.0)) return;
+    double ip = floor(v);
+    unsigned long long lo = __double2ull_rz((v - ip) * 0x1.0p64);
+    unsigned long long old = atomicAdd(w, lo);
+    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    unsigned long long hi = (unsigned long long)ip + carry;
+    if (hi) atomicAdd(w + 1, hi);
+}
+
+struct Photon {
+    float x, y, e, kx, ky, kz;
+    uint32_t step, id_mech;
+};
+
+template <typename R>
+__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
+                                         R kx, R ky, double inv_log_emax) {
+    int eb = (int)m_floor((R)PE_HIST_E_BINS * m_log_acc(e) * (R)inv_log_emax);
+    if (eb >= PE_HIST_E_BINS) { eb = PE_HIST_E_BINS - 1; atomicAdd(tally + PE_T_N_HIST_OVER, 1ull); }
+    if (eb < 0) eb = 0;
+    R th = m_atan2(ky, kx);
+    int tb = (int)m_floor((th + (R)kPi) / (R)(2.0 * kPi) * (R)PE_HIST_T_BINS);
+    if (tb < 0) tb = 0;
+    if (tb >= PE_HIST_T_BINS) tb = PE_HIST_T_BINS - 1;
+    atomicAdd(hist + mech * PE_HIST_E_BINS + eb, 1ull);
+    atomicAdd(hist + 2 * PE_HIST_E_BINS + mech * PE_HIST_T_BINS + tb, 1ull);
+}
+
+// warp-aggregated append of at most one photon per lane; all 32 lanes call it
+__device__ __forceinline__ void warp_append(const RunDev& r, bool on, const Photon& p) {
+    unsigned mask = __ballot_sync(0xffffffffu, on);
+    if (mask == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(r.tally + PE_T_N_PHOTONS, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (on) {
+        unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+        if (slot < (unsigned long long)r.capacity) {
+            float4* dst = reinterpret_cast<float4*>(r.photons + slot * 32);
+            dst[0] = make_float4(p.x, p.y, p.e, p.kx);
+            dst[1] = make_float4(p.ky, p.kz, __uint_as_float(p.step), __uint_as_float(p.id_mech));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one step of one particle
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Particle {
+    R x, y, u[3];
+    double tau;
+    uint32_t ev_cnt, ev_hash;   // event fingerprint (only kept when r.events != nullptr)
+};
+template <typename R>
+__device__ __forceinline__ void note_event(Particle<R>& P, int64_t n, int mech) {
+    P.ev_cnt += mech ? 0x10000u : 1u;
+    P.ev_hash += (uint32_t)(n + 1) * (mech ? 0x9E3779B1u : 1u);
+}
+
+template <typename R>
+struct StepOut {
+    bool ncs, br;      // a stored photon of this mechanism
+    Photon pn, pb;
+};
+
+template <typename R>
+__device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, const R* h_tab, const R* sig_tab,
+                                         const R* cdf, const R* bcdf_z, uint32_t id, int64_t n,
+                                         Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
+                                         unsigned long long* tally) {
+    out.ncs = out.br = false;
+    const R dt = (R)r.dt;
+    R E[3], B[3];
+    fields<R>(r, P.x, P.y, n, E, B);
+    boris<R>(P.u, E, B, dt);
+    R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    const R xn = P.x, yn = P.y;
+
+    if (r.enable_ncs) {
+        R eta = eta_of<R>(P.u, gamma, E, B, (R)(1.0 / r.E_S));
+        int fl;
+        R h = h_of_eta<R>(t, h_tab, eta, fl);
+        if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
+        // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
+        P.tau -= (double)((R)r.ncs_coef * (eta / gamma) * h);
+        if (P.tau <= 0.0) {
+            uint4 w = draw(r, id, (uint32_t)n, PUR_NCS);
+            bool below;
+            R delta = sample_ncs_delta<R>(t, cdf, eta, uni_r<R>(w64(w.x, w.y)), below);
+            if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
+            R ew = delta * gamma;
+            if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
+            R k[3];
+            recoil<R>(P.u, gamma, ew, k);
+            note_event<R>(P, n, 0);
+            R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+            fx_add(tally + PE_T_E_RECOIL_NCS, (double)(gamma - gn));
+            if (ew >= (R)t.photon_min) {
+                atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
+                fx_add(tally + PE_T_E_NCS_STORED, (double)ew);
+                hist_add<R>(hist, tally, 0, ew, k[0], k[1], r.inv_log_emax);
+                out.ncs = true;
+                out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2],
+                                (uint32_t)n, id};
+            } else {
+                atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
+                fx_add(tally + PE_T_E_NCS_BELOW, (double)ew);
+            }
+            gamma = gn;
+            P.tau = -log(uni53(w64(w.z, w.w)));
+        }
+    }
+
+    if (r.enable_brems) {
+        bool in_slab = (xn >= (R)r.x0 && xn <= (R)r.x1);
+        if (r.geometry == PE_GAUSS_2D && fabs(yn) > (R)r.yh) in_slab = false;
+        if (in_slab && gamma > (R)1 + (R)t.photon_min) {
+            bool above;
+            R sig = sigma_of<R>(t, sig_tab, gamma, above);
+            if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
+            R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+            R xb = (R)r.K_br * sig * (um / gamma);
+            R Pbr = -m_expm1(-xb);
+            uint4 w = draw(r, id, (uint32_t)n, PUR_BREMS);
+            if (w64(w.x, w.y) < threshold64(Pbr)) {
+                R yy = sample_brems_y<R>(t, bcdf_z, gamma, uni_r<R>(w64(w.z, w.w)));
+                R ew = yy * gamma;
+                R k[3];
+                recoil<R>(P.u, gamma, ew, k);
+                note_event<R>(P, n, 1);
+                R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+                fx_add(tally + PE_T_E_RECOIL_BR, (double)(gamma - gn));
+                if (ew >= (R)t.photon_min) {
+                    atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
+                    fx_add(tally + PE_T_E_BR_STORED, (double)ew);
+                    hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.inv_log_emax);
+                    out.br = true;
+                    out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2],
+                                    (uint32_t)n, id | 0x80000000u};
+                } else {
+                    atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
+                    fx_add(tally + PE_T_E_BR_BELOW, (double)ew);
+                }
+                gamma = gn;
+            }
+        }
+    }
+
+    P.x = xn + dt * P.u[0] / gamma;
+    if (r.geometry == PE_GAUSS_2D) P.y = yn + dt * P.u[1] / gamma;
+    if (r.box_enable && (P.x < (R)r.box0 || P.x > (R)r.box1)) {
+        P.x = (R)NAN;
+        atomicAdd(tally + PE_T_N_KILLED, 1ull);
+        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)(n + 1));
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_particle(const RunDev& r, int64_t i, Particle<R>& P) {
+    P.x = ((const R*)r.x)[i];
+    P.y = (r.geometry == PE_GAUSS_2D) ? ((const R*)r.y)[i] : (R)0;
+    P.u[0] = ((const R*)r.ux)[i];
+    P.u[1] = ((const R*)r.uy)[i];
+    P.u[2] = ((const R*)r.uz)[i];
+    P.tau = r.tau[i];
+    if (r.events) {
+        unsigned long long e = r.events[i];
+        P.ev_cnt = (uint32_t)e;
+        P.ev_hash = (uint32_t)(e >> 32);
+    } else {
+        P.ev_cnt = P.ev_hash = 0;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store_particle(const RunDev& r, int64_t i, const Particle<R>& P) {
+    ((R*)r.x)[i] = P.x;
+    if (r.geometry == PE_GAUSS_2D) ((R*)r.y)[i] = P.y;
+    ((R*)r.ux)[i] = P.u[0];
+    ((R*)r.uy)[i] = P.u[1];
+    ((R*)r.uz)[i] = P.u[2];
+    r.tau[i] = P.tau;
+    if (r.events) r.events[i] = ((unsigned long long)P.ev_hash << 32) | P.ev_cnt;
+}
+
+// ---------------------------------------------------------------------------
+// plain FP64 kernel: one step, one particle per thread
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDev r) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = i < r.n;
+    Particle<double> P;
+    StepOut<double> out;
+    out.ncs = out.br = false;
+    if (active) {
+        load_particle<double>(r, i, P);
+        active = !isnan(P.x);
+    }
+    if (active) {
+        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E, t.cdf64,
+                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, r.step0, P, out, r.hist, r.tally);
+        store_particle<double>(r, i, P);
+    }
+    warp_append(r, out.ncs, out.pn);
+    warp_append(r, out.br, out.pb);
+}
+
+// ---------------------------------------------------------------------------
+// persistent kernel: grid-stride over tiles of all runs, K steps per launch
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_tally, const RunDev& r) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < PE_HIST_WORDS; k += blockDim.x) {
+        unsigned long long v = s_hist[k];
+        if (v) { atomicAdd(r.hist + k, v); s_hist[k] = 0; }
+    }
+    if (threadIdx.x < PE_T_E_NCS_STORED) {
+        unsigned long long v = s_tally[threadIdx.x];
+        if (v) { atomicAdd(r.tally + threadIdx.x, v); s_tally[threadIdx.x] = 0; }
+    } else if (threadIdx.x < PE_TALLY_WORDS && ((threadIdx.x - PE_T_E_NCS_STORED) & 1) == 0 &&
+               threadIdx.x <= PE_T_E_RECOIL_BR) {
+        int k = threadIdx.x;
+        unsigned long long lo = s_tally[k], hi = s_tally[k + 1];
+        if (lo || hi) {
+            unsigned long long old = atomicAdd(r.tally + k, lo);
+            if (old + lo < old) hi += 1;
+            if (hi) atomicAdd(r.tally + k + 1, hi);
+            s_tally[k] = 0;
+            s_tally[k + 1] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b, int steps) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
+    R* s_h = reinterpret_cast<R*>(s_tally + PE_TALLY_WORDS);
+    R* s_sig = s_h + t.n_eta;
+    const R* g_h = (sizeof(R) == 4) ? (const R*)t.h32 : (const R*)t.h64;
+    const R* g_sig = (sizeof(R) == 4) ? (const R*)t.sig32 : (const R*)t.sig64;
+    const R* g_cdf = (sizeof(R) == 4) ? (const R*)t.cdf32 : (const R*)t.cdf64;
+    const R* g_bcdf = (sizeof(R) == 4) ? (const R*)t.bcdf32 : (const R*)t.bcdf64;
+
+    for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
+    for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = g_h[k];
+    for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = g_sig[k];
+    __syncthreads();
+
+    const int64_t n_tiles = b.tile_start[b.n_runs];
+    int cur = -1;
+    int run_idx = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        while (run_idx + 1 < b.n_runs && b.tile_start[run_idx + 1] <= tile) ++run_idx;
+        if (run_idx != cur) {
+            if (cur >= 0) flush_shared<R>(s_hist, s_tally, b.runs[cur]);
+            cur = run_idx;
+        }
+        const RunDev& r = b.runs[run_idx];
+        int64_t i = (tile - b.tile_start[run_idx]) * b.tile + threadIdx.x;
+        bool active = i < r.n;
+        Particle<R> P;
+        if (active) {
+            load_particle<R>(r, i, P);
+            active = !isnan(P.x);
+        }
+        const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
+        const R* bcdf_z = g_bcdf + (size_t)r.iz * t.n_E * t.n_s;
+        for (int s = 0; s < steps; ++s) {
+            StepOut<R> out;
+            out.ncs = out.br = false;
+            if (active) {
+                step_one<R>(t, r, s_h, sig_z, g_cdf, bcdf_z, (uint32_t)i, r.step0 + s, P, out, s_hist, s_tally);
+                if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
+            }
+            warp_append(r, out.ncs, out.pn);
+            warp_append(r, out.br, out.pb);
+        }
+        if (active) store_particle<R>(r, i, P);
+    }
+    if (cur >= 0) flush_shared<R>(s_hist, s_tally, b.runs[cur]);
+}
+
+// ---------------------------------------------------------------------------
+// init kernel
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_init(RunDev r, int init_dist, double theta, double beam_u, double x0,
+                                              double x1, double yh, int two_d) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    uint32_t id = (uint32_t)i;
+    uint4 w = draw(r, id, 0, PUR_TAU0);
+    r.tau[i] = -log(uni53(w64(w.x, w.y)));
+    if (init_dist == PE_CALLER) return;
+    uint4 p = draw(r, id, 0, PUR_POS);
+    double x = x0 + (x1 - x0) * uni32(p.x);
+    double y = two_d ? -yh + 2.0 * yh * uni32(p.y) : 0.0;
+    double u0 = 0, u1 = 0, u2 = 0;
+    if (init_dist == PE_MAXWELL_JUTTNER) {
+        // Sobol (1976) rejection sampling of the Maxwell-Juttner momentum magnitude
+        double um = 0.0;
+        for (uint32_t round = 0; round < 64; ++round) {
+            uint4 m = draw(r, id, 0, PUR_MJ + round);
+            double X1 = uni32(m.x), X2 = uni32(m.y), X3 = uni32(m.z), X4 = uni32(m.w);
+            double uu = -theta * log(X1 * X2 * X3);
+            double ee = -theta * log(X1 * X2 * X3 * X4);
+            if (ee * ee - uu * uu > 1.0) { um = uu; break; }
+        }
+        double X5 = uni32(p.z), X6 = uni32(p.w);
+        double sn = 2.0 * sqrt(X5 * (1.0 - X5));
+        double sphi, cphi;
+        sincos(2.0 * kPi * X6, &sphi, &cphi);
+        u0 = um * (2.0 * X5 - 1.0);
+        u1 = um * sn * cphi;
+        u2 = um * sn * sphi;
+    } else if (init_dist == PE_BEAM) {
+        u0 = beam_u;
+    }
+    ((R*)r.x)[i] = (R)x;
+    ((R*)r.y)[i] = (R)y;
+    ((R*)r.ux)[i] = (R)u0;
+    ((R*)r.uy)[i] = (R)u1;
+    ((R*)r.uz)[i] = (R)u2;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_init(const TablesDev&, const RunDev& r, int precision, int init_dist, double theta, double beam_u,
+                 cudaStream_t s) {
+    if (r.n == 0) return;
+    int grid = (int)((r.n + 255) / 256);
+    int two_d = r.geometry == PE_GAUSS_2D;
+    if (precision == PE_F32)
+        k_init<float><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u, r.x0, r.x1, r.yh, two_d);
+    else
+        k_init<double><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u, r.x0, r.x1, r.yh, two_d);
+}
+
+void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s) {
+    if (r.n == 0) return;
+    int grid = (int)((r.n + 255) / 256);
+    k_step_plain<<<grid, 256, 0, s>>>(t, r);
+}
+
+int persistent_smem_bytes(const TablesDev& t, int precision) {
+    size_t rs = precision == PE_F32 ? 4 : 8;
+    return (int)(8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + rs * (t.n_eta + (size_t)t.n_Z * t.n_E));
+}
+
+int persistent_occupancy(int precision, int block, int smem) {
+    int occ = 0;
+    cudaError_t e = precision == PE_F32
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float>, block, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<double>, block, smem);
+    return e == cudaSuccess ? occ : 1;
+}
+
+void launch_step_persistent_f32(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+                                cudaStream_t s) {
+    int smem = persistent_smem_bytes(t, PE_F32);
+    k_step_persistent<float><<<grid, block, smem, s>>>(t, b, steps);
+}
+void launch_step_persistent_f64(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+                                cudaStream_t s) {
+    int smem = persistent_smem_bytes(t, PE_F64);
+    k_step_persistent<double><<<grid, block, smem, s>>>(t, b, steps);
+}
+
+}  // namespace pe

@@ -1,0 +1,273 @@
+// physics.cuh -- per-particle arithmetic of the emission step, templated on
+// the floating type R (float for the fast path, double for the plain path).
+// Each function cites the part of the method it implements.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pe {
+
+// ---- math wrappers (CUDA's own functions for both types) --------------------
+__device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float m_exp(float v) { return expf(v); }
+__device__ __forceinline__ double m_exp(double v) { return exp(v); }
+__device__ __forceinline__ float m_log(float v) { return __logf(v); }
+__device__ __forceinline__ double m_log(double v) { return log(v); }
+__device__ __forceinline__ float m_log_acc(float v) { return logf(v); }
+__device__ __forceinline__ double m_log_acc(double v) { return log(v); }
+__device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
+__device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
+__device__ __forceinline__ float m_atan(float v) { return atanf(v); }
+__device__ __forceinline__ double m_atan(double v) { return atan(v); }
+__device__ __forceinline__ void m_sincos(float v, float* s, float* c) { sincosf(v, s, c); }
+__device__ __forceinline__ void m_sincos(double v, double* s, double* c) { sincos(v, s, c); }
+__device__ __forceinline__ float m_atan2(float a, float b) { return atan2f(a, b); }
+__device__ __forceinline__ double m_atan2(double a, double b) { return atan2(a, b); }
+__device__ __forceinline__ float m_floor(float v) { return floorf(v); }
+__device__ __forceinline__ double m_floor(double v) { return floor(v); }
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------
+// Counter (particle id, run id, step, purpose), key (seed lo, seed hi).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4 };
+
+__device__ __forceinline__ uint4 draw(const RunDev& r, uint32_t id, uint32_t step, uint32_t purpose) {
+    return philox4x32_10(make_uint4(id, r.run_id, step, purpose), r.seed_lo, r.seed_hi);
+}
+__device__ __forceinline__ uint64_t w64(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
+// uniform in (0,1): 53 random bits (double), 24 random bits (float)
+__device__ __forceinline__ double uni53(uint64_t v) { return ((double)(v >> 11) + 0.5) * 0x1.0p-53; }
+__device__ __forceinline__ double uni32(uint32_t v) { return ((double)v + 0.5) * 0x1.0p-32; }
+template <typename R> __device__ __forceinline__ R uni_r(uint64_t v);
+template <> __device__ __forceinline__ double uni_r<double>(uint64_t v) { return uni53(v); }
+template <> __device__ __forceinline__ float uni_r<float>(uint64_t v) {
+    return ((float)(uint32_t)(v >> 40) + 0.5f) * 0x1.0p-24f;
+}
+// floor(P 2^64) for P in [0, 1): the 64-bit threshold of the brems test (Eq. 4)
+__device__ __forceinline__ uint64_t threshold64(float P) { return __float2ull_rz(P * 0x1.0p64f); }
+__device__ __forceinline__ uint64_t threshold64(double P) {
+    return P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+}
+
+// ---- prescribed laser fields (Sec. 3 setup) ------------------------------------
+// Pulse through its vector potential A(phi), phi = t - x: sin^2 ramps of
+// phi_r and a flat top phi_f; E = -dA/dt, B = x^ cross E for the plane wave.
+template <typename R>
+__device__ __forceinline__ void envelope(const RunDev& r, R phi, R& g, R& dg) {
+    const R pr = (R)r.phi_r, pf = (R)r.phi_f;
+    const R k = (R)(0.5 * kPi) / pr;
+    if (!(phi > (R)0) || phi >= (R)2 * pr + pf) { g = 0; dg = 0; return; }
+    if (phi < pr) {
+        R s, c;
+        m_sincos(k * phi, &s, &c);
+        g = s * s;
+        dg = k * (R)2 * s * c;
+        return;
+    }
+    if (phi <= pr + pf) { g = 1; dg = 0; return; }
+    R s, c;
+    m_sincos(k * (phi - pr - pf), &s, &c);
+    g = c * c;
+    dg = -k * (R)2 * s * c;
+}
+
+// phase t^n - x with t^n = n dt: in float, n * dt_hi is exact (dt_hi has 11
+// significant bits, n < 2^13), and the small remainder n * dt_lo is added.
+template <typename R> __device__ __forceinline__ R phase(const RunDev& r, int64_t n, R x);
+template <> __device__ __forceinline__ double phase<double>(const RunDev& r, int64_t n, double x) {
+    return (double)n * r.dt - x;
+}
+template <> __device__ __forceinline__ float phase<float>(const RunDev& r, int64_t n, float x) {
+    float nf = (float)n;
+    return fmaf(nf, (float)r.dt_lo, nf * (float)r.dt_hi - x);
+}
+
+template <typename R>
+__device__ __forceinline__ void fields(const RunDev& r, R x, R y, int64_t n, R E[3], R B[3]) {
+    E[0] = E[1] = E[2] = 0;
+    B[0] = B[1] = B[2] = 0;
+    if (r.geometry == PE_CONST) {
+        for (int k = 0; k < 3; ++k) { E[k] = (R)r.E_const[k]; B[k] = (R)r.B_const[k]; }
+        return;
+    }
+    R phi = phase<R>(r, n, x);
+    R g, dg;
+    envelope<R>(r, phi, g, dg);
+    if (g == (R)0 && dg == (R)0) return;
+    const R a0 = (R)r.a0;
+    R S = 1, theta = phi, inv_R = 0, inv_w2 = 0;
+    if (r.geometry == PE_GAUSS_2D) {
+        // paraxial 2D focus: amplitude sqrt(w0/w) exp(-y^2/w^2), curvature and Gouy phase
+        const R w0 = (R)r.w0, zr = (R)r.zr;
+        R xi = x - (R)r.xf;
+        R w2 = w0 * w0 * ((R)1 + xi * xi / (zr * zr));
+        inv_w2 = (R)1 / w2;
+        inv_R = xi / (xi * xi + zr * zr);
+        S = m_sqrt(w0 / m_sqrt(w2)) * m_exp(-y * y * inv_w2);
+        theta = phi - (R)0.5 * y * y * inv_R + (R)0.5 * m_atan(xi / zr);
+    }
+    R st, ct;
+    m_sincos(theta, &st, &ct);
+    R ey = -a0 * S * (dg * st + g * ct);
+    E[1] = ey;
+    B[2] = ey;
+    if (r.geometry == PE_GAUSS_2D) E[0] = a0 * g * S * (y * inv_R * ct + (R)2 * y * inv_w2 * st);
+    if (r.polarisation == PE_CP) {
+        R ez = a0 * S * (dg * ct - g * st);
+        E[2] = ez;
+        B[1] = -ez;
+        if (r.geometry == PE_GAUSS_2D) B[0] = a0 * g * S * ((R)2 * y * inv_w2 * ct - y * inv_R * st);
+    }
+}
+
+// ---- Boris push, charge -e (particle pusher, Sec. 2.2) -------------------------
+template <typename R>
+__device__ __forceinline__ void boris(R u[3], const R E[3], const R B[3], R dt) {
+    const R h = (R)0.5 * dt;
+    R um0 = u[0] - h * E[0], um1 = u[1] - h * E[1], um2 = u[2] - h * E[2];
+    R ig = (R)1 / m_sqrt((R)1 + um0 * um0 + um1 * um1 + um2 * um2);
+    R t0 = -h * B[0] * ig, t1 = -h * B[1] * ig, t2 = -h * B[2] * ig;
+    R f = (R)2 / ((R)1 + t0 * t0 + t1 * t1 + t2 * t2);
+    R s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    R p0 = um0 + (um1 * t2 - um2 * t1);
+    R p1 = um1 + (um2 * t0 - um0 * t2);
+    R p2 = um2 + (um0 * t1 - um1 * t0);
+    u[0] = um0 + (p1 * s2 - p2 * s1) - h * E[0];
+    u[1] = um1 + (p2 * s0 - p0 * s2) - h * E[1];
+    u[2] = um2 + (p0 * s1 - p1 * s0) - h * E[2];
+}
+
+// ---- quantum parameter (Sec. 2.1) ------------------------------------------------
+// eta E_S = sqrt((gamma E + u x B)^2 - (u.E)^2), rewritten without the
+// cancellation of electrons riding a wave along x: with dB = B - x^ cross E
+// and V = (gamma - u_x) E + u x dB, the radicand is |V|^2 + 2 V_x (u.E).
+template <typename R>
+__device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R B[3], R inv_ES) {
+    R gm = (u[0] > (R)0) ? ((R)1 + u[1] * u[1] + u[2] * u[2]) / (gamma + u[0]) : gamma - u[0];
+    R d0 = B[0], d1 = B[1] + E[2], d2 = B[2] - E[1];
+    R V0 = gm * E[0] + (u[1] * d2 - u[2] * d1);
+    R V1 = gm * E[1] + (u[2] * d0 - u[0] * d2);
+    R V2 = gm * E[2] + (u[0] * d1 - u[1] * d0);
+    R uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+    R q = V0 * V0 + V1 * V1 + V2 * V2 + (R)2 * V0 * uE;
+    return q > (R)0 ? m_sqrt(q) * inv_ES : (R)0;
+}
+
+// ---- table lookups (rows linear in log eta / log gamma) -----------------------
+template <typename R>
+__device__ __forceinline__ void row_pos(R v, double lnlo, double inv, int n, int& i, R& w, int& flag) {
+    R tp = (m_log(v) - (R)lnlo) * (R)inv;
+    flag = 0;
+    if (tp >= (R)(n - 1)) { i = n - 2; w = 1; flag = 1; return; }
+    if (!(tp >= (R)0)) { i = 0; w = 0; flag = -1; return; }
+    int k = (int)tp;
+    if (k > n - 2) k = n - 2;
+    i = k;
+    w = tp - (R)k;
+}
+
+// h(eta) by row interpolation; below the table: classical limit 5 pi / 3
+template <typename R>
+__device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int& flag) {
+    if (!(eta >= (R)t.eta_min)) { flag = -1; return (R)t.h_classical; }
+    int i; R w;
+    row_pos<R>(eta, t.ln_eta_min, t.inv_dln_eta, t.n_eta, i, w, flag);
+    return ((R)1 - w) * h[i] + w * h[i + 1];
+}
+
+// inverse of the row-interpolated CDF: largest j with c_j <= R, linear between nodes
+template <typename R>
+__device__ __forceinline__ R invert_rows(const R* ra, const R* rb, R w, int n, R Rv, int& j_out) {
+    R c0 = ((R)1 - w) * ra[0] + w * rb[0];
+    if (Rv < c0) { j_out = -1; return Rv / c0; }
+    R cn = ((R)1 - w) * ra[n - 1] + w * rb[n - 1];
+    if (Rv >= cn) { j_out = n - 1; return (R)0; }
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        R cm = ((R)1 - w) * ra[mid] + w * rb[mid];
+        if (cm <= Rv) lo = mid; else hi = mid;
+    }
+    R cl = ((R)1 - w) * ra[lo] + w * rb[lo];
+    R ch = ((R)1 - w) * ra[hi] + w * rb[hi];
+    j_out = lo;
+    return ch > cl ? (Rv - cl) / (ch - cl) : (R)0;
+}
+
+// NCS photon energy fraction delta for given eta and uniform Rv (Sec. 2.2)
+template <typename R>
+__device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, R eta, R Rv, bool& below) {
+    const R *ra, *rb;
+    R w;
+    below = false;
+    if (!(eta >= (R)t.eta_min)) {
+        ra = rb = cdf + (size_t)t.n_eta * t.n_y;
+        w = 0;
+        below = true;
+    } else {
+        int i, fl;
+        row_pos<R>(eta, t.ln_eta_min, t.inv_dln_eta, t.n_eta, i, w, fl);
+        ra = cdf + (size_t)i * t.n_y;
+        rb = ra + t.n_y;
+    }
+    int j;
+    R fr = invert_rows<R>(ra, rb, w, t.n_y, Rv, j);
+    R y;
+    if (j < 0) y = (R)t.y_min * fr * fr * fr;            // CDF ~ y^(1/3) below the grid
+    else if (j >= t.n_y - 1) y = (R)t.y_max;
+    else y = m_exp((R)t.ln_y_min + ((R)j + fr) * (R)t.dln_y);
+    R q = (R)3 * eta * y;
+    return q / ((R)2 + q);
+}
+
+// sigma_Z(gamma) by row interpolation in log gamma
+template <typename R>
+__device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma, bool& above) {
+    int i, fl; R w;
+    row_pos<R>(gamma, t.ln_g_min, t.inv_dln_g, t.n_E, i, w, fl);
+    above = (fl == 1);
+    return ((R)1 - w) * sig[i] + w * sig[i + 1];
+}
+
+// brems photon energy fraction y from sigma(y, E) = sigma(E) R2 (text after Eq. 4)
+template <typename R>
+__device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z, R gamma, R Rv) {
+    int i, fl; R w;
+    row_pos<R>(gamma, t.ln_g_min, t.inv_dln_g, t.n_E, i, w, fl);
+    const R* ra = bcdf_z + (size_t)i * t.n_s;
+    const R* rb = ra + t.n_s;
+    int j;
+    R fr = invert_rows<R>(ra, rb, w, t.n_s, Rv, j);
+    R s;
+    if (j < 0) s = 0;
+    else if (j >= t.n_s - 1) s = 1;
+    else s = ((R)j + fr) / (R)(t.n_s - 1);
+    R ycut = (R)t.photon_min / gamma, ymax = (R)1 - (R)1 / gamma;
+    return ycut * m_exp(s * m_log(ymax / ycut));
+}
+
+// energy-conserving recoil along u (photon direction k = v/|v|, Sec. 2.2)
+template <typename R>
+__device__ __forceinline__ void recoil(R u[3], R gamma, R w, R k[3]) {
+    R um = m_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (um > (R)0) { R iu = (R)1 / um; k[0] = u[0] * iu; k[1] = u[1] * iu; k[2] = u[2] * iu; }
+    else { k[0] = 1; k[1] = 0; k[2] = 0; }
+    R g2 = gamma - w;
+    R un = g2 > (R)1 ? m_sqrt(g2 * g2 - (R)1) : (R)0;
+    u[0] = k[0] * un; u[1] = k[1] * un; u[2] = k[2] * un;
+}
+
+}  // namespace pe

@@ -1,0 +1,93 @@
+"""CPU checks of the library boundary: it builds, loads, exports every symbol the
+header declares, the ctypes mirrors match the C struct layouts, the product
+path never reaches the oracle, and compute calls fail loudly without a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1612_07592_gb300 as pe
+from paper_1612_07592_gb300 import build as pe_build
+from paper_1612_07592_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pe.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return pe_build.build()
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:[a-z_]+\s+\*?\s*|const char\*\s+)(pe_[a-z0-9_]+)\s*\(", src, re.M)))
+
+
+def test_header_symbols_exported(libpath):
+    names = _declared()
+    assert "pe_step" in names and "pe_init_particles" in names and len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pe_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = C.CDLL(libpath)
+    for n in names:
+        getattr(L, n)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pe.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pe_table_params),'
+                    ' sizeof(pe_run_params), sizeof(pe_buffers), sizeof(pe_launch_config), sizeof(pe_tally_out),'
+                    ' offsetof(pe_run_params, seed), offsetof(pe_tally_out, live_particle_steps));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
+    want = [C.sizeof(pe.TableParams), C.sizeof(pe.RunParams), C.sizeof(pe.Buffers), C.sizeof(pe.LaunchConfig),
+            C.sizeof(pe.TallyOut), pe.RunParams.seed.offset, pe.TallyOut.live_particle_steps.offset]
+    assert got == want
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_1612_07592_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b", txt.replace("test oracle", "")), f
+
+
+def test_compute_fails_loudly_without_gpu(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    tp, Z = pe.table_params(n_eta=4, n_y=4, n_E=4, n_s=4, Z=(13.0,))
+    with pytest.raises(pe.PeError) as e:
+        pe.pe_create_tables(tp, Z)
+    assert e.value.status in (pe.PE_ERR_NOMEM, pe.PE_ERR_CUDA)
+
+
+def test_argument_errors_are_reported(libpath):
+    tp, Z = pe.table_params(n_eta=1, Z=(13.0,))
+    with pytest.raises(pe.PeError) as e:
+        pe.pe_create_tables(tp, Z)
+    assert e.value.status == pe.PE_ERR_ARG
+    assert pe.pe_a0_from_intensity(1e21) == pytest.approx(0.855 * 1000 ** 0.5)
+    assert pe.pe_a0_from_intensity(1e24) == pytest.approx(855.0, rel=1e-3)
+
+
+def test_workloads():
+    c4 = W.config4()
+    n = c4["n"]
+    assert len(n) == 64 and n.min() >= 1e4 and n.max() <= 4e6
+    assert 1.5e7 < n.sum() < 2.6e7
+    assert abs(W.a0_of(1e21) - 27.04) < 0.01 and abs(W.a0_of(1e24) - 855.0) < 0.1
+    c5 = W.config5(n_requests=50)
+    arr = [q["arrival_s"] for q in c5["requests"]]
+    assert np.all(np.diff(arr) > 0)
+    assert W.config2()["n"] == 1_000_000 and W.config3()["n"] == 30_000_000
