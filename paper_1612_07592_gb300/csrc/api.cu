@@ -293,6 +293,8 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int smem = persistent_smem_bytes(t->dev, prec);
+    if (smem > 200 * 1024)
+        return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
     int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : persistent_occupancy(prec, block, smem);
     if (per_sm < 1) per_sm = 1;
     BatchDev b;   // host staging; passed by value to the kernel

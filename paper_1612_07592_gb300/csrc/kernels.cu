@@ -396,11 +396,15 @@ int persistent_occupancy(int precision, int block, int smem) {
 void launch_step_persistent_f32(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
                                 cudaStream_t s) {
     int smem = persistent_smem_bytes(t, PE_F32);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_step_persistent<float><<<grid, block, smem, s>>>(t, b, steps);
 }
 void launch_step_persistent_f64(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
                                 cudaStream_t s) {
     int smem = persistent_smem_bytes(t, PE_F64);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_step_persistent<double><<<grid, block, smem, s>>>(t, b, steps);
 }
 
