@@ -1,0 +1,408 @@
+"""Benchmark: emitting particle-steps/s of the photon-emission step on GB300.
+
+Workload (default): the 1D Au configuration -- LP plane wave a0 = 270
+(1e23 W/cm^2), Au 51+ slab 1 um thick at n_e = 50 n_c, 1e6 electrons with a
+Maxwell-Juttner T = 1 MeV start, dt = T/100, 4000 steps, 256 x 256 tables.
+One benchmark step = that whole job: all 1e6 electrons advanced through all
+4000 steps of the hot path from the resident initial state (FP32 persistent
+kernel, state in registers across the steps of a launch).
+
+Lines printed (rank 0): one JSON object with the contract keys plus
+  roofline      the dominant kernel (k_step_persistent<float>) against the FP32 pipe
+  roofline_hbm  the one-step-per-launch form on a state larger than L2 against HBM
+  fp64_plain    the plain FP64 path (one launch per step) on the same job
+  cpu_baseline  the FP64 oracle on the host cores on a bounded sample
+  e2e           the same metric through the public API with host buffers
+`--impl reference` times the oracle alone on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "emitting particle-steps/s at 1 GB300 (FP32/batched vs FP64 plain); % HBM roofline; p99"
+UNIT = "particle-steps/s"
+# Algorithmic FP32 operations of one particle-step of the 1D LP case (fields, Boris push,
+# eta, rate lookup, optical depth, compensated position update; a mul+add pair counts 2).
+FLOP_PER_PSTEP_1D = 132
+# Algorithmic bytes of one particle-step when the state round-trips memory every step:
+# read + write of x, ux, uy, uz (f32) and tau (f64) in 1D; + y in 2D.
+BYTES_PER_PSTEP_1D = 48
+BYTES_PER_PSTEP_2D = 56
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def hbm_peak_gbs(d):
+    for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "hbm"):
+        if k in d and isinstance(d[k], (int, float)):
+            return float(d[k])
+    for v in d.values():
+        if isinstance(v, dict):
+            for k in ("hbm_gbs", "gbs"):
+                if k in v:
+                    return float(v[k])
+    return 6800.0
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+_ORACLE_TABLES = {}
+
+
+def cpu_baseline(cfg, n_sample, steps, threads):
+    """FP64 oracle (test infrastructure) on a strided id sample of the same workload."""
+    import oracle as O
+    tp = {("photon_min" if k == "photon_min_mc2" else k): v for k, v in cfg["tables"].items()}
+    key = (tuple(sorted(tp.items())), tuple(cfg["Z"]))
+    if key not in _ORACLE_TABLES:
+        _ORACLE_TABLES[key] = O.Tables(O.table_params(**tp), list(cfg["Z"]))
+    ot = _ORACLE_TABLES[key]
+    run = dict(cfg["run"])
+    run["iz"] = list(cfg["Z"]).index(run["Z"])
+    rp = O.run_params(**run)
+    ids = np.arange(0, cfg["n"], max(cfg["n"] // n_sample, 1))[:n_sample]
+    st = O.init(ot, rp, ids)
+    t0 = time.perf_counter()
+    O.run(ot, rp, ids, st, 0, steps, capacity=1 << 20, threads=threads)
+    dt = time.perf_counter() - t0
+    return len(ids) * steps / dt, len(ids), dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--steps-per-launch", type=int, default=0)
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
+    ap.add_argument("--particles", type=int, default=0, help="override N (profiling runs only)")
+    ap.add_argument("--job-steps", type=int, default=0, help="override steps per job (profiling runs only)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    from paper_1612_07592_gb300 import workloads as W
+    cfg = W.config2()
+    if args.particles:
+        cfg["n"] = args.particles
+    if args.job_steps:
+        cfg["steps"] = args.job_steps
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        threads = os.cpu_count() or 1
+        W_, K = args.warmup, args.steps
+        n_sample = max(2000, 40_000 // max(1, 16 // threads))
+        vals = []
+        for k in range(W_ + K):
+            v, ns, dt = cpu_baseline(cfg, n_sample // 8 if k < W_ else n_sample, cfg["steps"], threads)
+            if k >= W_:
+                vals.append((v, dt))
+        value = statistics.median(v for v, _ in vals)
+        ms = 1e3 * cfg["n"] * cfg["steps"] / value
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W_,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": cfg["name"], "particles": cfg["n"], "job_steps": cfg["steps"]},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": f"{n_sample} of {cfg['n']} electrons (strided ids) x {cfg['steps']} steps per timed step"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_1612_07592_gb300 as pe
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n, S = cfg["n"], cfg["steps"]
+    tables = pe.pe_create_tables(cfg["tables"], cfg["Z"])
+    stream = torch.cuda.Stream()
+    # each rank runs its own job on its own Philox run id (weak scaling: no data exchange)
+    run = dict(cfg["run"], run_id=rank)
+    launch = dict(block=args.block, ctas_per_sm=args.ctas_per_sm, steps_per_launch=args.steps_per_launch)
+    cap = 1 << 24
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=cap, stream=stream)
+    torch.cuda.synchronize()
+    init_state = [t.clone() for t in (r.x, r.y, r.ux, r.uy, r.uz, r.tau)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def reset(run_obj, state):
+        with torch.cuda.stream(stream):
+            for dst, src in zip((run_obj.x, run_obj.y, run_obj.ux, run_obj.uy, run_obj.uz, run_obj.tau), state):
+                dst.copy_(src)
+            run_obj.hist.zero_()
+            run_obj.tally.zero_()
+            flush.fill_(1.0)       # evict L2 (256 MB > 129 MB) between timed jobs
+
+    def one_job(run_obj):
+        # rebind the run so its step counter restarts at 0 with the reset state
+        pe.pe_step_ex([run_obj.handle], S, **launch)
+
+    # fresh run handles per job restart the step index at 0 (the laser pulse timing)
+    def fresh_handle(run_obj):
+        b = pe.Buffers(run_obj.x.data_ptr(), run_obj.y.data_ptr(), run_obj.ux.data_ptr(), run_obj.uy.data_ptr(),
+                       run_obj.uz.data_ptr(), run_obj.tau.data_ptr(), run_obj.photons.data_ptr(), cap,
+                       run_obj.hist.data_ptr(), run_obj.tally.data_ptr(), None)
+        p = pe.run_params(precision=pe.PE_F32, **dict(run, init_dist=pe.PE_CALLER))
+        old = run_obj.handle
+        run_obj.handle = pe.pe_init_particles(tables, p, n, b, stream.cuda_stream)
+        pe.pe_destroy(old)
+
+    times = []
+    for k in range(args.warmup + args.steps):
+        reset(r, init_state)
+        fresh_handle(r)
+        # PE_CALLER redraws tau from the same Philox stream: identical to the resident start
+        stream.synchronize()
+        if k == args.warmup:
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            launches = 0
+            clocks = ClockSampler(local).__enter__()
+            wall0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = pe.pe_launch_count()
+        e0.record(stream)
+        one_job(r)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+            launches += pe.pe_launch_count() - l0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks.__exit__()
+    out = r.tally_out()
+    ms = float(np.mean(times))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pst = out.live_particle_steps
+    value = pst * world / (ms * 1e-3)
+
+    pk, pk_kind = peaks()
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": cfg["name"], "particles_per_gpu": n, "job_steps": S,
+                      "precision": "fp32 push/emission, fp64 optical depth, 128-bit fixed-point tallies",
+                      "kernel": "k_step_persistent<float>",
+                      "steps_per_launch": args.steps_per_launch or min(S, 2048),
+                      "block": args.block or 256, "l2": "flushed between timed jobs (256 MB write)",
+                      "parallelism": f"dp{world} (independent jobs per GPU)"},
+           "gpu_launches": int(launches),
+           "clocks": clocks.summary(),
+           "wall_s_timed_region": wall}
+    # roofline of the dominant kernel: FP32 pipe (state held in registers across steps)
+    sm_clock = (res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
+    ach = FLOP_PER_PSTEP_1D * pst / (ms * 1e-3) / 1e12
+    res["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                       "traffic": None, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                       "flop_per_particle_step": FLOP_PER_PSTEP_1D}
+
+    if rank == 0 and not args.skip_extras:
+        res["roofline_hbm"] = hbm_form(pe, tables, cfg, stream, hbm_peak_gbs(pk), pk_kind)
+        res["fp64_plain"] = fp64_plain(pe, tables, cfg, stream, flush)
+        res["e2e"] = e2e(pe, tables, cfg, stream)
+    if rank == 0 and not args.skip_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"{ns} of {n} electrons (strided ids) x {S} steps, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(res))
+    r.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def hbm_form(pe, tables, cfg, stream, peak_gbs, peak_kind):
+    """One step per launch (state round-trips HBM every step) on 3e7 electrons of the same
+    1D physics (1.44 GB of state per step, > L2): per-launch time by CUDA events."""
+    import torch
+    n = 30_000_000
+    run = dict(cfg["run"], run_id=7)
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=1 << 20, stream=stream)
+    pe.pe_step_ex([r.handle], 200, steps_per_launch=200)       # bring the pulse onto the slab
+    stream.synchronize()
+    for _ in range(3):
+        pe.pe_step_ex([r.handle], 1, steps_per_launch=1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    K = 20
+    ev[0].record(stream)
+    pe.pe_step_ex([r.handle], K, steps_per_launch=1)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / K
+    gbs = BYTES_PER_PSTEP_1D * n / (ms * 1e-3) / 1e9
+    r.close()
+    return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+            "traffic": None, "peak_kind": peak_kind, "particles": n, "bytes_per_particle_step": BYTES_PER_PSTEP_1D,
+            "ms_per_launch": ms, "particle_steps_per_s": n / (ms * 1e-3), "kernel": "k_step_persistent<float>, K=1"}
+
+
+def fp64_plain(pe, tables, cfg, stream, flush):
+    """The plain FP64 path (one launch per step, tables in global memory) on the same job."""
+    import torch
+    run = dict(cfg["run"], run_id=0)
+    n, S = cfg["n"], cfg["steps"]
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F64, **run), n, capacity=1 << 24, stream=stream)
+        flush.fill_(1.0)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pe.pe_step([r.handle], S)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = r.tally_out()
+    r.close()
+    return {"value": out.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms,
+            "kernel": "k_step_plain (fp64, one launch per step)", "steps": 1, "warmup": 0}
+
+
+def e2e(pe, tables, cfg, stream):
+    """Same job through the public API from pinned host buffers: H2D of the initial state,
+    pe_init_particles (caller state) + pe_step + pe_tally, D2H of the final state and photons."""
+    import torch
+    n, S = cfg["n"], cfg["steps"]
+    run = dict(cfg["run"], run_id=0)
+    with torch.cuda.stream(stream):
+        src = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=16, stream=stream)
+    stream.synchronize()
+    host_in = [t[:n].cpu().pin_memory() for t in (src.x, src.ux, src.uy, src.uz)]
+    src.close()
+    cap = 1 << 22
+    bufs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(5)]
+    tau = torch.empty(n, dtype=torch.float64, device="cuda")
+    photons = torch.empty(cap * 8, dtype=torch.int32, device="cuda")
+    hist = torch.empty(pe.HIST_WORDS, dtype=torch.int64, device="cuda")
+    tally = torch.empty(pe.TALLY_WORDS, dtype=torch.int64, device="cuda")
+    host_out = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(4)]
+    host_tau = torch.empty(n, dtype=torch.float64).pin_memory()
+    host_ph = torch.empty(cap * 8, dtype=torch.int32).pin_memory()
+    times, h2d, d2h = [], 0, 0
+    for k in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for d, h in zip((bufs[0], bufs[2], bufs[3], bufs[4]), host_in):
+                d.copy_(h, non_blocking=True)
+        b = pe.Buffers(bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[2].data_ptr(), bufs[3].data_ptr(),
+                       bufs[4].data_ptr(), tau.data_ptr(), photons.data_ptr(), cap, hist.data_ptr(),
+                       tally.data_ptr(), None)
+        h = pe.pe_init_particles(tables, pe.run_params(precision=pe.PE_F32, **dict(run, init_dist=pe.PE_CALLER)),
+                                 n, b, stream.cuda_stream)
+        pe.pe_step([h], S)
+        out = pe.pe_tally(h)
+        nst = int(out.photons_stored)
+        with torch.cuda.stream(stream):
+            for hh, d in zip(host_out, (bufs[0], bufs[2], bufs[3], bufs[4])):
+                hh.copy_(d, non_blocking=True)
+            host_tau.copy_(tau, non_blocking=True)
+            host_ph[: nst * 8].copy_(photons[: nst * 8], non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        pe.pe_destroy(h)
+        times.append(dt)
+        h2d = 4 * 4 * n
+        d2h = 4 * 4 * n + 8 * n + 32 * nst + 8 * (pe.HIST_WORDS + pe.TALLY_WORDS)
+        pst = out.live_particle_steps
+    dt = statistics.median(times[1:])
+    return {"value": pst / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "s_per_job": dt, "path": "pinned host -> pe_init_particles(PE_CALLER) + pe_step + pe_tally -> pinned host"}
+
+
+if __name__ == "__main__":
+    main()

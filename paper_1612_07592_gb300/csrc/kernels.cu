@@ -82,6 +82,7 @@ __device__ __forceinline__ void warp_append(const RunDev& r, bool on, const Phot
 template <typename R>
 struct Particle {
     R x, y, u[3];
+    R x_lo, y_lo;               // compensation of the float position update (0 in double)
     double tau;
     uint32_t ev_cnt, ev_hash;   // event fingerprint (only kept when r.events != nullptr)
 };
@@ -105,7 +106,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, co
     out.ncs = out.br = false;
     const R dt = (R)r.dt;
     R E[3], B[3];
-    fields<R>(r, P.x, P.y, n, E, B);
+    fields<R>(r, P.x, P.x_lo, P.y, n, E, B);
     boris<R>(P.u, E, B, dt);
     R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
     const R xn = P.x, yn = P.y;
@@ -180,8 +181,8 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, co
         }
     }
 
-    P.x = xn + dt * P.u[0] / gamma;
-    if (r.geometry == PE_GAUSS_2D) P.y = yn + dt * P.u[1] / gamma;
+    advance(P.x, P.x_lo, dt * P.u[0] / gamma);
+    if (r.geometry == PE_GAUSS_2D) advance(P.y, P.y_lo, dt * P.u[1] / gamma);
     if (r.box_enable && (P.x < (R)r.box0 || P.x > (R)r.box1)) {
         P.x = (R)NAN;
         atomicAdd(tally + PE_T_N_KILLED, 1ull);
@@ -193,6 +194,8 @@ template <typename R>
 __device__ __forceinline__ void load_particle(const RunDev& r, int64_t i, Particle<R>& P) {
     P.x = ((const R*)r.x)[i];
     P.y = (r.geometry == PE_GAUSS_2D) ? ((const R*)r.y)[i] : (R)0;
+    P.x_lo = 0;
+    P.y_lo = 0;
     P.u[0] = ((const R*)r.ux)[i];
     P.u[1] = ((const R*)r.uy)[i];
     P.u[2] = ((const R*)r.uz)[i];
@@ -207,8 +210,8 @@ __device__ __forceinline__ void load_particle(const RunDev& r, int64_t i, Partic
 }
 template <typename R>
 __device__ __forceinline__ void store_particle(const RunDev& r, int64_t i, const Particle<R>& P) {
-    ((R*)r.x)[i] = P.x;
-    if (r.geometry == PE_GAUSS_2D) ((R*)r.y)[i] = P.y;
+    ((R*)r.x)[i] = P.x + P.x_lo;
+    if (r.geometry == PE_GAUSS_2D) ((R*)r.y)[i] = P.y + P.y_lo;
     ((R*)r.ux)[i] = P.u[0];
     ((R*)r.uy)[i] = P.u[1];
     ((R*)r.uz)[i] = P.u[2];

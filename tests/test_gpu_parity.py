@@ -19,10 +19,11 @@ from paper_1612_07592_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 F64_RTOL = 1e-9
-# FP32 state error where events match: the phase t - x carries the rounding of an
-# FP32 position (|x| up to ~300 c/omega, ulp ~3e-5) into the field; over ~1e3 steps
-# the accumulated relative error of u, x stays below ~1e-4 (measured).
-F32_RTOL = 3e-4
+# FP32 state error where events match, relative to the trajectory's momentum scale
+# max(|u|, a0) (the quiver amplitude; |u| itself passes near zero at the nodes of the
+# vector potential).  Positions are advanced with compensated (double-float) adds, so
+# the remaining error is the FP32 rounding of u and of the fields, ~1e-7 per step.
+F32_RTOL = 1e-5
 
 _TAB = {}
 
@@ -114,7 +115,8 @@ def test_init_matches_oracle(kind):
         r = pe.Run(lt, pe.run_params(precision=prec, **run), n)
         st = r.state()
         if prec == pe.PE_F64:
-            np.testing.assert_allclose(st, st_o, rtol=1e-14, atol=1e-300)
+            # rounding order (FMA contraction) leaves ~1e-15 absolute on coordinates near zero
+            np.testing.assert_allclose(st, st_o, rtol=1e-14, atol=1e-13)
         else:
             np.testing.assert_array_equal(st[:, :5], st_o[:, :5].astype(np.float32).astype(np.float64))
             np.testing.assert_allclose(st[:, 5], st_o[:, 5], rtol=1e-14)
@@ -199,7 +201,7 @@ def test_f32_parity(case):
     frac = match.mean()
     g = np.sqrt(1 + (st[:, 2:5] ** 2).sum(1))
     go = np.sqrt(1 + (st_o[:, 2:5] ** 2).sum(1))
-    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), 1.0)
+    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), max(run["a0"], 1.0))
     err_u = (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u)[match]
     err_x = (np.abs(st[:, 0:2] - st_o[:, 0:2]).max(1) / np.maximum(np.abs(st_o[:, 0:2]).max(1), 1.0))[match]
     print(f"{case}: event match {frac:.4f}, max rel err u {err_u.max():.2e} x {err_x.max():.2e}, "
@@ -219,7 +221,7 @@ def test_f32_spectrum_chi2():
     run = W.base_run(a0=270.0, init_dist=1, T_mev=1.0, **W.AU)
     Z = (13.0, 79.0)
     lt, ot = tables(_tp(48), Z)
-    n, steps = 4000, 1200
+    n, steps = 24000, 1200
     _, _, _, hist_o, _, _ = run_oracle(ot, dict(run, seed=101), Z, np.arange(n), steps)
     r, out = run_gpu(lt, dict(run, seed=202), n, steps, pe.PE_F32)
     h1 = np.frombuffer(bytes(out.hist), dtype=np.uint64)[:512].astype(float)
@@ -357,7 +359,7 @@ def test_config2_full_size_sampled():
     st_o, _, _, _, _, ev_o = run_oracle(ot, c["run"], Z, ids, steps)
     match = ev[ids] == ev_o
     assert match.mean() > 0.9
-    scale = np.maximum(np.abs(st_o[:, 2:5]).max(1), 1.0)
+    scale = np.maximum(np.abs(st_o[:, 2:5]).max(1), c["run"]["a0"])
     err = np.abs(st[ids, 2:5] - st_o[:, 2:5]).max(1) / scale
     assert err[match].max() < F32_RTOL
     r.close()
