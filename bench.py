@@ -37,9 +37,10 @@ UNIT = "particle-steps/s"
 # eta, rate lookup, optical depth, compensated position update; a mul+add pair counts 2).
 FLOP_PER_PSTEP_1D = 132
 # Algorithmic bytes of one particle-step when the state round-trips memory every step:
-# read + write of x, ux, uy, uz (f32) and tau (f64) in 1D; + y in 2D.
-BYTES_PER_PSTEP_1D = 48
-BYTES_PER_PSTEP_2D = 56
+# read + write of x (float pair, 8 B), ux, uy, uz (f32) and tau (float pair, 8 B) in 1D;
+# + y (float pair) in 2D.
+BYTES_PER_PSTEP_1D = 56
+BYTES_PER_PSTEP_2D = 72
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
@@ -361,15 +362,15 @@ def e2e(pe, tables, cfg, stream):
     with torch.cuda.stream(stream):
         src = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=16, stream=stream)
     stream.synchronize()
-    host_in = [t[:n].cpu().pin_memory() for t in (src.x, src.ux, src.uy, src.uz)]
+    host_in = [t[:n].cpu().pin_memory() for t in (src.x, src.ux, src.uy, src.uz)]   # x: float pairs
     src.close()
     cap = 1 << 22
-    bufs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(5)]
+    bufs = [torch.empty(n, dtype=torch.float64 if k < 2 else torch.float32, device="cuda") for k in range(5)]
     tau = torch.empty(n, dtype=torch.float64, device="cuda")
     photons = torch.empty(cap * 8, dtype=torch.int32, device="cuda")
     hist = torch.empty(pe.HIST_WORDS, dtype=torch.int64, device="cuda")
     tally = torch.empty(pe.TALLY_WORDS, dtype=torch.int64, device="cuda")
-    host_out = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(4)]
+    host_out = [torch.empty(n, dtype=torch.float64 if k == 0 else torch.float32).pin_memory() for k in range(4)]
     host_tau = torch.empty(n, dtype=torch.float64).pin_memory()
     host_ph = torch.empty(cap * 8, dtype=torch.int32).pin_memory()
     times, h2d, d2h = [], 0, 0
@@ -396,8 +397,8 @@ def e2e(pe, tables, cfg, stream):
         dt = time.perf_counter() - t0
         pe.pe_destroy(h)
         times.append(dt)
-        h2d = 4 * 4 * n
-        d2h = 4 * 4 * n + 8 * n + 32 * nst + 8 * (pe.HIST_WORDS + pe.TALLY_WORDS)
+        h2d = (8 + 3 * 4) * n
+        d2h = (8 + 3 * 4 + 8) * n + 32 * nst + 8 * (pe.HIST_WORDS + pe.TALLY_WORDS)
         pst = out.live_particle_steps
     dt = statistics.median(times[1:])
     return {"value": pst / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

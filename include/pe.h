@@ -115,9 +115,15 @@ typedef struct {
 } pe_run_params;
 
 /* Caller-owned device buffers of one run.
- *   x, y, ux, uy, uz : n elements, float (PE_F32) or double (PE_F64); y is
- *                      only read/written for PE_GAUSS_2D but must be valid.
- *   tau              : n doubles (optical depth; always FP64).
+ *   x, y             : n positions, 8 bytes each: a double for PE_F64; for
+ *                      PE_F32 a pair of floats (hi, lo) whose sum is the
+ *                      position, advanced by compensated adds so the laser
+ *                      phase t - x keeps ~1e-12 accuracy; y is only read and
+ *                      written for PE_GAUSS_2D but must be valid.
+ *   ux, uy, uz       : n momenta, float (PE_F32) or double (PE_F64).
+ *   tau              : n optical depths, 8 bytes each: a double for PE_F64; for
+ *                      PE_F32 a pair of floats (hi, lo) whose sum is the value,
+ *                      kept exact to ~2^-48 by compensated subtraction.
  *   photons          : photon_capacity records of 32 bytes
  *                      {float x, y, energy, kx, ky, kz; uint32 step; uint32 id | mech << 31}
  *   hist             : PE_HIST_WORDS uint64 (zeroed by pe_init_particles)

@@ -216,8 +216,10 @@ class Run:
         dev = torch.device(device)
         m = max(int(n), 1)
         self.n = int(n)
-        self.x = torch.zeros(m, dtype=dt, device=dev)
-        self.y = torch.zeros(m, dtype=dt, device=dev)
+        # positions and optical depths take 8 bytes per particle in both precisions
+        # (FP32 runs store float pairs hi + lo there)
+        self.x = torch.zeros(m, dtype=torch.float64, device=dev)
+        self.y = torch.zeros(m, dtype=torch.float64, device=dev)
         self.ux = torch.zeros(m, dtype=dt, device=dev)
         self.uy = torch.zeros(m, dtype=dt, device=dev)
         self.uz = torch.zeros(m, dtype=dt, device=dev)
@@ -236,9 +238,18 @@ class Run:
         self.handle = pe_init_particles(tables, params, self.n, b, self.stream.cuda_stream)
 
     def state(self) -> np.ndarray:
-        """Host copy (n x 6, float64): x, y, ux, uy, uz, tau."""
-        cols = [self.x, self.y, self.ux, self.uy, self.uz, self.tau]
-        return np.stack([c[:self.n].double().cpu().numpy() for c in cols], axis=1)
+        """Host copy (n x 6, float64): x, y, ux, uy, uz, tau.
+
+        In FP32 runs positions and optical depths are stored as float pairs (hi, lo)
+        whose sum is the value."""
+        def pair(t):
+            if self.params.precision == PE_F32:
+                p = t[:self.n].view(self.torch.float32).reshape(-1, 2).double().cpu().numpy()
+                return p[:, 0] + p[:, 1]
+            return t[:self.n].cpu().numpy()
+        cols = [pair(self.x), pair(self.y)]
+        cols += [c[:self.n].double().cpu().numpy() for c in (self.ux, self.uy, self.uz)]
+        return np.stack(cols + [pair(self.tau)], axis=1)
 
     def photon_records(self, count: int | None = None) -> np.ndarray:
         out = self.tally_out() if count is None else None

@@ -111,16 +111,20 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     D.h64 = d64; D.cdf64 = d64 + n_h; D.sig64 = D.cdf64 + n_c; D.bcdf64 = D.sig64 + n_sg;
     D.h32 = d32; D.cdf32 = d32 + n_h; D.sig32 = D.cdf32 + n_c; D.bcdf32 = D.sig32 + n_sg;
     D.n_eta = p->n_eta; D.n_y = p->n_y; D.n_E = p->n_E; D.n_s = p->n_s; D.n_Z = p->n_Z;
-    D.eta_min = p->eta_min;
-    D.ln_eta_min = std::log(p->eta_min);
-    D.inv_dln_eta = (p->n_eta - 1) / (std::log(p->eta_max) - std::log(p->eta_min));
-    D.ln_y_min = std::log(p->y_min);
-    D.dln_y = (std::log(p->y_max) - std::log(p->y_min)) / (p->n_y - 1);
-    D.y_min = p->y_min; D.y_max = p->y_max;
-    D.ln_g_min = std::log(p->gamma_min);
-    D.inv_dln_g = (p->n_E - 1) / (std::log(p->gamma_max) - std::log(p->gamma_min));
-    D.photon_min = p->photon_min_mc2;
-    D.h_classical = 5.0 * kPi / 3.0;
+    TabC<double>& C = D.cd;
+    C.eta_min = p->eta_min;
+    C.ln_eta_min = std::log(p->eta_min);
+    C.inv_dln_eta = (p->n_eta - 1) / (std::log(p->eta_max) - std::log(p->eta_min));
+    C.ln_y_min = std::log(p->y_min);
+    C.dln_y = (std::log(p->y_max) - std::log(p->y_min)) / (p->n_y - 1);
+    C.y_min = p->y_min; C.y_max = p->y_max;
+    C.ln_g_min = std::log(p->gamma_min);
+    C.inv_dln_g = (p->n_E - 1) / (std::log(p->gamma_max) - std::log(p->gamma_min));
+    C.photon_min = p->photon_min_mc2;
+    C.h_classical = 5.0 * kPi / 3.0;
+    const double* cs = &C.eta_min;
+    float* cfp = &D.cf.eta_min;
+    for (size_t k = 0; k < sizeof(TabC<double>) / sizeof(double); ++k) cfp[k] = (float)cs[k];
     *out = t;
     return PE_OK;
 }
@@ -193,7 +197,7 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     RunDev& d = r->dev;
     std::memset(&d, 0, sizeof(d));
     d.x = b->x; d.y = b->y; d.ux = b->ux; d.uy = b->uy; d.uz = b->uz;
-    d.tau = static_cast<double*>(b->tau);
+    d.tau = b->tau;
     d.photons = static_cast<uint8_t*>(b->photons);
     d.hist = static_cast<unsigned long long*>(b->hist);
     d.tally = static_cast<unsigned long long*>(b->tally);
@@ -201,27 +205,30 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     d.n = n;
     d.capacity = b->photon_capacity;
     d.step0 = 0;
+    StepC<double>& c = d.c;
     const double kl = 2.0 * kPi / rp->lambda_m;
-    d.dt = rp->dt_over_T * 2.0 * kPi;
-    split_dt(d.dt, &d.dt_hi, &d.dt_lo);
-    d.E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
-    d.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * d.E_S * d.dt;
+    c.dt = rp->dt_over_T * 2.0 * kPi;
+    split_dt(c.dt, &c.dt_hi, &c.dt_lo);
+    const double E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
+    c.inv_ES = 1.0 / E_S;
+    c.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * E_S * c.dt;
     double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
     double n_i = rp->ne_over_nc * n_c / rp->charge_state;
-    d.K_br = n_i * kAlpha * kRe * kRe * (d.dt / kl);
-    d.x0 = rp->slab_x0_m * kl;
-    d.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
-    d.yh = rp->y_half_m * kl;
-    d.box0 = rp->box_x_m[0] * kl;
-    d.box1 = rp->box_x_m[1] * kl;
-    d.inv_log_emax = 1.0 / std::log(kHistEmaxMeV / kMec2MeV);
-    d.a0 = rp->a0;
-    d.w0 = rp->w0_m * kl;
-    d.zr = 0.5 * d.w0 * d.w0;
-    d.xf = rp->focus_x_m * kl;
-    d.phi_r = 2.0 * kPi * rp->ramp_periods;
-    d.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
-    for (int k = 0; k < 3; ++k) { d.E_const[k] = rp->E_const[k]; d.B_const[k] = rp->B_const[k]; }
+    c.K_br = n_i * kAlpha * kRe * kRe * (c.dt / kl);
+    c.x0 = rp->slab_x0_m * kl;
+    c.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
+    c.yh = rp->y_half_m * kl;
+    c.box0 = rp->box_x_m[0] * kl;
+    c.box1 = rp->box_x_m[1] * kl;
+    c.inv_log_emax = 1.0 / std::log(kHistEmaxMeV / kMec2MeV);
+    c.a0 = rp->a0;
+    c.w0 = rp->w0_m * kl;
+    c.zr = 0.5 * c.w0 * c.w0;
+    c.xf = rp->focus_x_m * kl;
+    c.phi_r = 2.0 * kPi * rp->ramp_periods;
+    c.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
+    c.k_env = 0.5 * kPi / c.phi_r;
+    for (int k = 0; k < 3; ++k) { c.E_const[k] = rp->E_const[k]; c.B_const[k] = rp->B_const[k]; }
     d.geometry = rp->geometry;
     d.polarisation = rp->polarisation;
     d.enable_ncs = rp->enable_ncs;
@@ -242,7 +249,7 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     double theta = rp->T_mev / kMec2MeV;
     double beam_u = rp->init_dist == PE_BEAM ? std::sqrt(rp->beam_gamma * rp->beam_gamma - 1.0) : 0.0;
     if (n > 0) {
-        launch_init(t->dev, d, rp->precision, rp->init_dist, theta, beam_u, r->stream);
+        launch_init(d, rp->precision, rp->init_dist, theta, beam_u, r->stream);
         g_launches++;
         e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -297,30 +304,41 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
         return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
     int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : persistent_occupancy(prec, block, smem);
     if (per_sm < 1) per_sm = 1;
-    BatchDev b;   // host staging; passed by value to the kernel
-    std::memset(&b, 0, sizeof(b));
-    b.n_runs = n_runs;
-    b.tile = block;
-    b.tile_start[0] = 0;
-    for (int k = 0; k < n_runs; ++k) {
-        b.runs[k] = runs[k]->dev;
-        b.tile_start[k + 1] = b.tile_start[k] + (runs[k]->dev.n + block - 1) / block;
-    }
-    int64_t n_tiles = b.tile_start[n_runs];
+    int64_t tile_start[PE_MAX_BATCH + 1];
+    tile_start[0] = 0;
+    for (int k = 0; k < n_runs; ++k) tile_start[k + 1] = tile_start[k] + (runs[k]->dev.n + block - 1) / block;
+    int64_t n_tiles = tile_start[n_runs];
     if (n_tiles == 0) {
         for (int k = 0; k < n_runs; ++k) runs[k]->steps_done += n_steps;
         return PE_OK;
     }
-    int grid_cap = sms * per_sm;
-    int grid = (int)std::min<int64_t>(n_tiles, grid_cap);
-    for (int64_t done = 0; done < n_steps; done += K) {
-        int k_now = (int)std::min<int64_t>(K, n_steps - done);
-        for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
-        if (prec == PE_F32)
+    int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
+    if (prec == PE_F32) {
+        BatchDevT<float> b;   // host staging; passed by value to the kernel
+        std::memset(&b, 0, sizeof(b));
+        b.n_runs = n_runs;
+        b.tile = block;
+        for (int k = 0; k <= n_runs; ++k) b.tile_start[k] = tile_start[k];
+        for (int k = 0; k < n_runs; ++k) b.runs[k] = to_float(runs[k]->dev);
+        for (int64_t done = 0; done < n_steps; done += K) {
+            int k_now = (int)std::min<int64_t>(K, n_steps - done);
+            for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
             launch_step_persistent_f32(t->dev, b, k_now, grid, block, s);
-        else
+            g_launches++;
+        }
+    } else {
+        BatchDevT<double> b;
+        std::memset(&b, 0, sizeof(b));
+        b.n_runs = n_runs;
+        b.tile = block;
+        for (int k = 0; k <= n_runs; ++k) b.tile_start[k] = tile_start[k];
+        for (int k = 0; k < n_runs; ++k) b.runs[k] = runs[k]->dev;
+        for (int64_t done = 0; done < n_steps; done += K) {
+            int k_now = (int)std::min<int64_t>(K, n_steps - done);
+            for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
             launch_step_persistent_f64(t->dev, b, k_now, grid, block, s);
-        g_launches++;
+            g_launches++;
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pe_step: k_step_persistent");

@@ -22,6 +22,17 @@ constexpr double kC = 299792458.0;              // [m/s]
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kHistEmaxMeV = 10000.0;        // top edge of the energy histogram
 
+// Table constants in the arithmetic of the step (float copies for the FP32 path,
+// so no double->float conversion runs per step).
+template <typename R>
+struct TabC {
+    R eta_min, ln_eta_min, inv_dln_eta;   // row position = (ln eta - ln eta_min) * inv
+    R ln_y_min, dln_y, y_min, y_max;
+    R ln_g_min, inv_dln_g;
+    R photon_min;
+    R h_classical;                        // 5 pi / 3
+};
+
 // Device view of one table set.  f32 and f64 copies of every table.
 struct TablesDev {
     const float* h32;   const double* h64;      // [n_eta]
@@ -29,49 +40,67 @@ struct TablesDev {
     const float* sig32; const double* sig64;    // [n_Z * n_E]
     const float* bcdf32; const double* bcdf64;  // [n_Z * n_E * n_s]
     int n_eta, n_y, n_E, n_s, n_Z;
-    double eta_min, ln_eta_min, inv_dln_eta;    // row position = (ln eta - ln eta_min) * inv
-    double ln_y_min, dln_y, y_min, y_max;
-    double ln_g_min, inv_dln_g;
-    double photon_min;
-    double h_classical;                         // 5 pi / 3
+    TabC<float> cf;
+    TabC<double> cd;
 };
 
-// Device view of one run.
-struct RunDev {
-    // state (float or double per precision; tau always double)
+// Per-step constants of one run, in the arithmetic of the step.
+template <typename R>
+struct StepC {
+    R dt, dt_hi, dt_lo;       // dt split so that n * dt_hi is exact in float for n < 2^13
+    R inv_ES, ncs_coef;       // ncs_coef = sqrt(3) alpha / (2 pi) * E_S * dt
+    R K_br;                   // n_i alpha r_e^2 (c dt): x_b = K_br * sigma[alpha r_e^2] * beta
+    R x0, x1, yh;             // slab (normalised)
+    R box0, box1;
+    R inv_log_emax;           // 1 / ln(E_hist_max / m c^2)
+    R a0, w0, zr, xf, phi_r, phi_f, k_env;   // fields; k_env = pi / (2 phi_r)
+    R E_const[3], B_const[3];
+};
+
+// Device view of one run.  Optical depth: double for PE_F64, a float pair
+// (hi, lo) with value hi + lo for PE_F32; 8 bytes per particle either way.
+template <typename R>
+struct RunDevT {
     void *x, *y, *ux, *uy, *uz;
-    double* tau;
+    void* tau;
     uint8_t* photons;
     unsigned long long* hist;
     unsigned long long* tally;
     unsigned long long* events;   // optional per-particle event fingerprints
     int64_t n;
     int64_t capacity;
-    int64_t step0;            // step index of the first step of this launch
-    // step
-    double dt, dt_hi, dt_lo;  // dt split so that n * dt_hi is exact in float for n < 2^13
-    double E_S, ncs_coef;     // ncs_coef = sqrt(3) alpha / (2 pi) * E_S * dt
-    double K_br;              // n_i alpha r_e^2 (c dt): x_b = K_br * sigma[alpha r_e^2] * beta
-    double x0, x1, yh;        // slab (normalised)
-    double box0, box1;
-    double inv_log_emax;      // 1 / ln(E_hist_max / m c^2)
-    // fields
-    double a0, w0, zr, xf, phi_r, phi_f;
-    double E_const[3], B_const[3];
+    int64_t step0;                // step index of the first step of this launch
+    StepC<R> c;
     int geometry, polarisation;
     int enable_ncs, enable_brems, box_enable;
-    int iz;                   // brems table index
+    int iz;                       // brems table index
     uint32_t run_id;
     uint32_t seed_lo, seed_hi;
 };
+using RunDev = RunDevT<double>;
 
 // Batched launch: runs and their tile prefix.
-struct BatchDev {
+template <typename R>
+struct BatchDevT {
     int n_runs;
     int tile;                           // particles per tile
     int64_t tile_start[PE_MAX_BATCH + 1];
-    RunDev runs[PE_MAX_BATCH];
+    RunDevT<R> runs[PE_MAX_BATCH];
 };
+
+inline RunDevT<float> to_float(const RunDevT<double>& d) {
+    RunDevT<float> f;
+    f.x = d.x; f.y = d.y; f.ux = d.ux; f.uy = d.uy; f.uz = d.uz; f.tau = d.tau;
+    f.photons = d.photons; f.hist = d.hist; f.tally = d.tally; f.events = d.events;
+    f.n = d.n; f.capacity = d.capacity; f.step0 = d.step0;
+    const double* src = &d.c.dt;
+    float* dst = &f.c.dt;
+    for (size_t k = 0; k < sizeof(StepC<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
+    f.geometry = d.geometry; f.polarisation = d.polarisation;
+    f.enable_ncs = d.enable_ncs; f.enable_brems = d.enable_brems; f.box_enable = d.box_enable;
+    f.iz = d.iz; f.run_id = d.run_id; f.seed_lo = d.seed_lo; f.seed_hi = d.seed_hi;
+    return f;
+}
 
 // host-side table build (tables.cpp)
 struct HostTables {
@@ -86,12 +115,11 @@ struct HostTables {
 bool build_host_tables(const pe_table_params& p, HostTables& out, std::string* err);
 
 // kernels.cu
-void launch_init(const TablesDev& t, const RunDev& r, int precision, int init_dist, double theta,
-                 double beam_u, cudaStream_t s);
+void launch_init(const RunDev& r, int precision, int init_dist, double theta, double beam_u, cudaStream_t s);
 void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s);
-void launch_step_persistent_f32(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
                                 cudaStream_t s);
-void launch_step_persistent_f64(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
                                 cudaStream_t s);
 int persistent_smem_bytes(const TablesDev& t, int precision);
 int persistent_occupancy(int precision, int block, int smem);

@@ -45,8 +45,8 @@ struct Photon {
 
 template <typename R>
 __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
-                                         R kx, R ky, double inv_log_emax) {
-    int eb = (int)m_floor((R)PE_HIST_E_BINS * m_log_acc(e) * (R)inv_log_emax);
+                                         R kx, R ky, R inv_log_emax) {
+    int eb = (int)m_floor((R)PE_HIST_E_BINS * m_log_acc(e) * inv_log_emax);
     if (eb >= PE_HIST_E_BINS) { eb = PE_HIST_E_BINS - 1; atomicAdd(tally + PE_T_N_HIST_OVER, 1ull); }
     if (eb < 0) eb = 0;
     R th = m_atan2(ky, kx);
@@ -58,7 +58,8 @@ __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long
 }
 
 // warp-aggregated append of at most one photon per lane; all 32 lanes call it
-__device__ __forceinline__ void warp_append(const RunDev& r, bool on, const Photon& p) {
+template <typename R>
+__device__ __forceinline__ void warp_append(const RunDevT<R>& r, bool on, const Photon& p) {
     unsigned mask = __ballot_sync(0xffffffffu, on);
     if (mask == 0) return;
     int lane = threadIdx.x & 31;
@@ -83,13 +84,29 @@ template <typename R>
 struct Particle {
     R x, y, u[3];
     R x_lo, y_lo;               // compensation of the float position update (0 in double)
-    double tau;
+    R tau, tau_lo;              // optical depth; float path keeps it as the pair tau + tau_lo
     uint32_t ev_cnt, ev_hash;   // event fingerprint (only kept when r.events != nullptr)
 };
 template <typename R>
-__device__ __forceinline__ void note_event(Particle<R>& P, int64_t n, int mech) {
+__device__ __forceinline__ void note_event(Particle<R>& P, uint32_t n, int mech) {
     P.ev_cnt += mech ? 0x10000u : 1u;
-    P.ev_hash += (uint32_t)(n + 1) * (mech ? 0x9E3779B1u : 1u);
+    P.ev_hash += (n + 1u) * (mech ? 0x9E3779B1u : 1u);
+}
+// optical depth arithmetic: tau -= d (compensated in float), emission test, reset
+__device__ __forceinline__ void tau_sub(Particle<double>& P, double d) { P.tau -= d; }
+__device__ __forceinline__ void tau_sub(Particle<float>& P, float d) {
+    float s = P.tau - d;
+    float bb = s - P.tau;
+    float e = (P.tau - (s - bb)) + (-d - bb);
+    P.tau = s;
+    P.tau_lo += e;
+}
+template <typename R>
+__device__ __forceinline__ bool tau_crossed(const Particle<R>& P) { return P.tau + P.tau_lo <= (R)0; }
+__device__ __forceinline__ void tau_set(Particle<double>& P, double v) { P.tau = v; P.tau_lo = 0; }
+__device__ __forceinline__ void tau_set(Particle<float>& P, double v) {
+    P.tau = (float)v;
+    P.tau_lo = (float)(v - (double)P.tau);
 }
 
 template <typename R>
@@ -99,12 +116,14 @@ struct StepOut {
 };
 
 template <typename R>
-__device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, const R* h_tab, const R* sig_tab,
-                                         const R* cdf, const R* bcdf_z, uint32_t id, int64_t n,
+__device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
+                                         const double* bcdf_z, uint32_t id, uint32_t n,
                                          Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
                                          unsigned long long* tally) {
     out.ncs = out.br = false;
-    const R dt = (R)r.dt;
+    const StepC<R>& c = r.c;
+    const R photon_min = tabc<R>(t).photon_min;
+    const R dt = c.dt;
     R E[3], B[3];
     fields<R>(r, P.x, P.x_lo, P.y, n, E, B);
     boris<R>(P.u, E, B, dt);
@@ -112,16 +131,17 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, co
     const R xn = P.x, yn = P.y;
 
     if (r.enable_ncs) {
-        R eta = eta_of<R>(P.u, gamma, E, B, (R)(1.0 / r.E_S));
+        R eta = eta_of<R>(P.u, gamma, E, B, c.inv_ES);
         int fl;
         R h = h_of_eta<R>(t, h_tab, eta, fl);
         if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
-        P.tau -= (double)((R)r.ncs_coef * (eta / gamma) * h);
-        if (P.tau <= 0.0) {
-            uint4 w = draw(r, id, (uint32_t)n, PUR_NCS);
+        tau_sub(P, c.ncs_coef * (eta / gamma) * h);
+        if (tau_crossed(P)) {
+            uint4 w = draw(r, id, n, PUR_NCS);
             bool below;
-            R delta = sample_ncs_delta<R>(t, cdf, eta, uni_r<R>(w64(w.x, w.y)), below);
+            // rare branch: the inverse CDF runs in FP64 on the FP64 table with a 53-bit uniform
+            R delta = (R)sample_ncs_delta<double>(t, t.cdf64, (double)eta, uni53(w64(w.x, w.y)), below);
             if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
             R ew = delta * gamma;
             if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
@@ -130,48 +150,47 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, co
             note_event<R>(P, n, 0);
             R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
             fx_add(tally + PE_T_E_RECOIL_NCS, (double)(gamma - gn));
-            if (ew >= (R)t.photon_min) {
+            if (ew >= photon_min) {
                 atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
                 fx_add(tally + PE_T_E_NCS_STORED, (double)ew);
-                hist_add<R>(hist, tally, 0, ew, k[0], k[1], r.inv_log_emax);
+                hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
                 out.ncs = true;
-                out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2],
-                                (uint32_t)n, id};
+                out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
             } else {
                 atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
                 fx_add(tally + PE_T_E_NCS_BELOW, (double)ew);
             }
             gamma = gn;
-            P.tau = -log(uni53(w64(w.z, w.w)));
+            tau_set(P, -log(uni53(w64(w.z, w.w))));
         }
     }
 
     if (r.enable_brems) {
-        bool in_slab = (xn >= (R)r.x0 && xn <= (R)r.x1);
-        if (r.geometry == PE_GAUSS_2D && fabs(yn) > (R)r.yh) in_slab = false;
-        if (in_slab && gamma > (R)1 + (R)t.photon_min) {
+        bool in_slab = (xn >= c.x0 && xn <= c.x1);
+        if (r.geometry == PE_GAUSS_2D && fabs(yn) > c.yh) in_slab = false;
+        if (in_slab && gamma > (R)1 + photon_min) {
             bool above;
             R sig = sigma_of<R>(t, sig_tab, gamma, above);
             if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
             R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            R xb = (R)r.K_br * sig * (um / gamma);
+            R xb = c.K_br * sig * (um / gamma);
             R Pbr = -m_expm1(-xb);
-            uint4 w = draw(r, id, (uint32_t)n, PUR_BREMS);
-            if (w64(w.x, w.y) < threshold64(Pbr)) {
-                R yy = sample_brems_y<R>(t, bcdf_z, gamma, uni_r<R>(w64(w.z, w.w)));
+            uint4 w = draw(r, id, n, PUR_BREMS);
+            if (below_threshold(Pbr, w.x, w.y)) {
+                R yy = (R)sample_brems_y<double>(t, bcdf_z, (double)gamma, uni53(w64(w.z, w.w)));
                 R ew = yy * gamma;
                 R k[3];
                 recoil<R>(P.u, gamma, ew, k);
                 note_event<R>(P, n, 1);
                 R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
                 fx_add(tally + PE_T_E_RECOIL_BR, (double)(gamma - gn));
-                if (ew >= (R)t.photon_min) {
+                if (ew >= photon_min) {
                     atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
                     fx_add(tally + PE_T_E_BR_STORED, (double)ew);
-                    hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.inv_log_emax);
+                    hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
                     out.br = true;
-                    out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2],
-                                    (uint32_t)n, id | 0x80000000u};
+                    out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n,
+                                    id | 0x80000000u};
                 } else {
                     atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
                     fx_add(tally + PE_T_E_BR_BELOW, (double)ew);
@@ -183,23 +202,69 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDev& r, co
 
     advance(P.x, P.x_lo, dt * P.u[0] / gamma);
     if (r.geometry == PE_GAUSS_2D) advance(P.y, P.y_lo, dt * P.u[1] / gamma);
-    if (r.box_enable && (P.x < (R)r.box0 || P.x > (R)r.box1)) {
+    if (r.box_enable && (P.x < c.box0 || P.x > c.box1)) {
         P.x = (R)NAN;
         atomicAdd(tally + PE_T_N_KILLED, 1ull);
-        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)(n + 1));
+        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)n + 1ull);
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_particle(const RunDev& r, int64_t i, Particle<R>& P) {
-    P.x = ((const R*)r.x)[i];
-    P.y = (r.geometry == PE_GAUSS_2D) ? ((const R*)r.y)[i] : (R)0;
+__device__ __forceinline__ void load_tau(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
+    P.tau = ((const double*)r.tau)[i];
+    P.tau_lo = 0;
+}
+__device__ __forceinline__ void load_tau(const RunDevT<float>& r, int64_t i, Particle<float>& P) {
+    float2 v = ((const float2*)r.tau)[i];
+    P.tau = v.x;
+    P.tau_lo = v.y;
+}
+__device__ __forceinline__ void store_tau(const RunDevT<double>& r, int64_t i, const Particle<double>& P) {
+    ((double*)r.tau)[i] = P.tau;
+}
+__device__ __forceinline__ void store_tau(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
+    float s = P.tau + P.tau_lo;                 // renormalise the pair
+    ((float2*)r.tau)[i] = make_float2(s, P.tau_lo - (s - P.tau));
+}
+
+__device__ __forceinline__ void load_pos(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
+    P.x = ((const double*)r.x)[i];
+    P.y = (r.geometry == PE_GAUSS_2D) ? ((const double*)r.y)[i] : 0.0;
     P.x_lo = 0;
     P.y_lo = 0;
+}
+__device__ __forceinline__ void load_pos(const RunDevT<float>& r, int64_t i, Particle<float>& P) {
+    float2 v = ((const float2*)r.x)[i];
+    P.x = v.x;
+    P.x_lo = v.y;
+    if (r.geometry == PE_GAUSS_2D) {
+        float2 q = ((const float2*)r.y)[i];
+        P.y = q.x;
+        P.y_lo = q.y;
+    } else {
+        P.y = 0;
+        P.y_lo = 0;
+    }
+}
+__device__ __forceinline__ float2 renorm(float hi, float lo) {
+    float s = hi + lo;
+    return make_float2(s, lo - (s - hi));
+}
+__device__ __forceinline__ void store_pos(const RunDevT<double>& r, int64_t i, const Particle<double>& P) {
+    ((double*)r.x)[i] = P.x;
+    if (r.geometry == PE_GAUSS_2D) ((double*)r.y)[i] = P.y;
+}
+__device__ __forceinline__ void store_pos(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
+    ((float2*)r.x)[i] = isnan(P.x) ? make_float2(P.x, 0.0f) : renorm(P.x, P.x_lo);
+    if (r.geometry == PE_GAUSS_2D) ((float2*)r.y)[i] = renorm(P.y, P.y_lo);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_particle(const RunDevT<R>& r, int64_t i, Particle<R>& P) {
+    load_pos(r, i, P);
     P.u[0] = ((const R*)r.ux)[i];
     P.u[1] = ((const R*)r.uy)[i];
     P.u[2] = ((const R*)r.uz)[i];
-    P.tau = r.tau[i];
+    load_tau(r, i, P);
     if (r.events) {
         unsigned long long e = r.events[i];
         P.ev_cnt = (uint32_t)e;
@@ -209,20 +274,19 @@ __device__ __forceinline__ void load_particle(const RunDev& r, int64_t i, Partic
     }
 }
 template <typename R>
-__device__ __forceinline__ void store_particle(const RunDev& r, int64_t i, const Particle<R>& P) {
-    ((R*)r.x)[i] = P.x + P.x_lo;
-    if (r.geometry == PE_GAUSS_2D) ((R*)r.y)[i] = P.y + P.y_lo;
+__device__ __forceinline__ void store_particle(const RunDevT<R>& r, int64_t i, const Particle<R>& P) {
+    store_pos(r, i, P);
     ((R*)r.ux)[i] = P.u[0];
     ((R*)r.uy)[i] = P.u[1];
     ((R*)r.uz)[i] = P.u[2];
-    r.tau[i] = P.tau;
+    store_tau(r, i, P);
     if (r.events) r.events[i] = ((unsigned long long)P.ev_hash << 32) | P.ev_cnt;
 }
 
 // ---------------------------------------------------------------------------
 // plain FP64 kernel: one step, one particle per thread
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDev r) {
+__global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double> r) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < r.n;
     Particle<double> P;
@@ -233,8 +297,9 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDev r) {
         active = !isnan(P.x);
     }
     if (active) {
-        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E, t.cdf64,
-                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, r.step0, P, out, r.hist, r.tally);
+        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E,
+                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, (uint32_t)r.step0, P, out, r.hist,
+                         r.tally);
         store_particle<double>(r, i, P);
     }
     warp_append(r, out.ncs, out.pn);
@@ -245,7 +310,7 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDev r) {
 // persistent kernel: grid-stride over tiles of all runs, K steps per launch
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_tally, const RunDev& r) {
+__device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_tally, const RunDevT<R>& r) {
     __syncthreads();
     for (int k = threadIdx.x; k < PE_HIST_WORDS; k += blockDim.x) {
         unsigned long long v = s_hist[k];
@@ -270,7 +335,7 @@ __device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_t
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b, int steps) {
+__global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
@@ -278,8 +343,6 @@ __global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b
     R* s_sig = s_h + t.n_eta;
     const R* g_h = (sizeof(R) == 4) ? (const R*)t.h32 : (const R*)t.h64;
     const R* g_sig = (sizeof(R) == 4) ? (const R*)t.sig32 : (const R*)t.sig64;
-    const R* g_cdf = (sizeof(R) == 4) ? (const R*)t.cdf32 : (const R*)t.cdf64;
-    const R* g_bcdf = (sizeof(R) == 4) ? (const R*)t.bcdf32 : (const R*)t.bcdf64;
 
     for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
     for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = g_h[k];
@@ -295,7 +358,7 @@ __global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b
             if (cur >= 0) flush_shared<R>(s_hist, s_tally, b.runs[cur]);
             cur = run_idx;
         }
-        const RunDev& r = b.runs[run_idx];
+        const RunDevT<R>& r = b.runs[run_idx];
         int64_t i = (tile - b.tile_start[run_idx]) * b.tile + threadIdx.x;
         bool active = i < r.n;
         Particle<R> P;
@@ -304,12 +367,13 @@ __global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b
             active = !isnan(P.x);
         }
         const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
-        const R* bcdf_z = g_bcdf + (size_t)r.iz * t.n_E * t.n_s;
+        const double* bcdf_z = t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s;
         for (int s = 0; s < steps; ++s) {
             StepOut<R> out;
             out.ncs = out.br = false;
             if (active) {
-                step_one<R>(t, r, s_h, sig_z, g_cdf, bcdf_z, (uint32_t)i, r.step0 + s, P, out, s_hist, s_tally);
+                step_one<R>(t, r, s_h, sig_z, bcdf_z, (uint32_t)i, (uint32_t)(r.step0 + s), P, out, s_hist,
+                            s_tally);
                 if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
             }
             warp_append(r, out.ncs, out.pn);
@@ -324,17 +388,23 @@ __global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDev b
 // init kernel
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_init(RunDev r, int init_dist, double theta, double beam_u, double x0,
-                                              double x1, double yh, int two_d) {
+__global__ void __launch_bounds__(256) k_init(RunDevT<double> r, int init_dist, double theta, double beam_u) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r.n) return;
     uint32_t id = (uint32_t)i;
     uint4 w = draw(r, id, 0, PUR_TAU0);
-    r.tau[i] = -log(uni53(w64(w.x, w.y)));
+    double tau0 = -log(uni53(w64(w.x, w.y)));
+    if (sizeof(R) == 4) {
+        float hi = (float)tau0;
+        ((float2*)r.tau)[i] = make_float2(hi, (float)(tau0 - (double)hi));
+    } else {
+        ((double*)r.tau)[i] = tau0;
+    }
     if (init_dist == PE_CALLER) return;
     uint4 p = draw(r, id, 0, PUR_POS);
-    double x = x0 + (x1 - x0) * uni32(p.x);
-    double y = two_d ? -yh + 2.0 * yh * uni32(p.y) : 0.0;
+    const StepC<double>& c = r.c;
+    double x = c.x0 + (c.x1 - c.x0) * uni32(p.x);
+    double y = (r.geometry == PE_GAUSS_2D) ? -c.yh + 2.0 * c.yh * uni32(p.y) : 0.0;
     double u0 = 0, u1 = 0, u2 = 0;
     if (init_dist == PE_MAXWELL_JUTTNER) {
         // Sobol (1976) rejection sampling of the Maxwell-Juttner momentum magnitude
@@ -356,8 +426,14 @@ __global__ void __launch_bounds__(256) k_init(RunDev r, int init_dist, double th
     } else if (init_dist == PE_BEAM) {
         u0 = beam_u;
     }
-    ((R*)r.x)[i] = (R)x;
-    ((R*)r.y)[i] = (R)y;
+    if (sizeof(R) == 4) {
+        float xh = (float)x, yh = (float)y;
+        ((float2*)r.x)[i] = make_float2(xh, (float)(x - (double)xh));
+        ((float2*)r.y)[i] = make_float2(yh, (float)(y - (double)yh));
+    } else {
+        ((double*)r.x)[i] = x;
+        ((double*)r.y)[i] = y;
+    }
     ((R*)r.ux)[i] = (R)u0;
     ((R*)r.uy)[i] = (R)u1;
     ((R*)r.uz)[i] = (R)u2;
@@ -366,15 +442,13 @@ __global__ void __launch_bounds__(256) k_init(RunDev r, int init_dist, double th
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_init(const TablesDev&, const RunDev& r, int precision, int init_dist, double theta, double beam_u,
-                 cudaStream_t s) {
+void launch_init(const RunDev& r, int precision, int init_dist, double theta, double beam_u, cudaStream_t s) {
     if (r.n == 0) return;
     int grid = (int)((r.n + 255) / 256);
-    int two_d = r.geometry == PE_GAUSS_2D;
     if (precision == PE_F32)
-        k_init<float><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u, r.x0, r.x1, r.yh, two_d);
+        k_init<float><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u);
     else
-        k_init<double><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u, r.x0, r.x1, r.yh, two_d);
+        k_init<double><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u);
 }
 
 void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s) {
@@ -396,14 +470,14 @@ int persistent_occupancy(int precision, int block, int smem) {
     return e == cudaSuccess ? occ : 1;
 }
 
-void launch_step_persistent_f32(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
                                 cudaStream_t s) {
     int smem = persistent_smem_bytes(t, PE_F32);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_step_persistent<float><<<grid, block, smem, s>>>(t, b, steps);
 }
-void launch_step_persistent_f64(const TablesDev& t, const BatchDev& b, int steps, int grid, int block,
+void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
                                 cudaStream_t s) {
     int smem = persistent_smem_bytes(t, PE_F64);
     if (smem > 48 * 1024)

@@ -1,6 +1,8 @@
 // physics.cuh -- per-particle arithmetic of the emission step, templated on
 // the floating type R (float for the fast path, double for the plain path).
-// Each function cites the part of the method it implements.
+// Every constant a step reads is stored in R, so the float path issues no
+// FP64 instruction per step.  Each function cites the part of the method it
+// implements.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,6 +31,10 @@ __device__ __forceinline__ double m_atan2(double a, double b) { return atan2(a, 
 __device__ __forceinline__ float m_floor(float v) { return floorf(v); }
 __device__ __forceinline__ double m_floor(double v) { return floor(v); }
 
+template <typename R> __device__ __forceinline__ const TabC<R>& tabc(const TablesDev& t);
+template <> __device__ __forceinline__ const TabC<float>& tabc<float>(const TablesDev& t) { return t.cf; }
+template <> __device__ __forceinline__ const TabC<double>& tabc<double>(const TablesDev& t) { return t.cd; }
+
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------
 // Counter (particle id, run id, step, purpose), key (seed lo, seed hi).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -44,61 +50,67 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4 };
 
-__device__ __forceinline__ uint4 draw(const RunDev& r, uint32_t id, uint32_t step, uint32_t purpose) {
+template <typename R>
+__device__ __forceinline__ uint4 draw(const RunDevT<R>& r, uint32_t id, uint32_t step, uint32_t purpose) {
     return philox4x32_10(make_uint4(id, r.run_id, step, purpose), r.seed_lo, r.seed_hi);
 }
 __device__ __forceinline__ uint64_t w64(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
-// uniform in (0,1): 53 random bits (double), 24 random bits (float)
+// uniforms in (0,1) with 53 and 32 random bits
 __device__ __forceinline__ double uni53(uint64_t v) { return ((double)(v >> 11) + 0.5) * 0x1.0p-53; }
 __device__ __forceinline__ double uni32(uint32_t v) { return ((double)v + 0.5) * 0x1.0p-32; }
-template <typename R> __device__ __forceinline__ R uni_r(uint64_t v);
-template <> __device__ __forceinline__ double uni_r<double>(uint64_t v) { return uni53(v); }
-template <> __device__ __forceinline__ float uni_r<float>(uint64_t v) {
-    return ((float)(uint32_t)(v >> 40) + 0.5f) * 0x1.0p-24f;
+
+// Brems test of Eq. (4): event iff the 64-bit uniform (hi:lo) is below floor(P 2^64).
+__device__ __forceinline__ bool below_threshold(double P, uint32_t lo, uint32_t hi) {
+    uint64_t T = P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+    return w64(lo, hi) < T;
 }
-// floor(P 2^64) for P in [0, 1): the 64-bit threshold of the brems test (Eq. 4)
-__device__ __forceinline__ uint64_t threshold64(float P) { return __float2ull_rz(P * 0x1.0p64f); }
-__device__ __forceinline__ uint64_t threshold64(double P) {
-    return P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+// float P: floor(P 2^64) = th 2^32 + floor(frac(P 2^32) 2^32), both parts exact in
+// float, so the comparison runs on 32-bit integers.
+__device__ __forceinline__ bool below_threshold(float P, uint32_t lo, uint32_t hi) {
+    if (!(P > 0.0f)) return false;
+    if (P >= 1.0f) return true;
+    float p32 = P * 0x1.0p32f;
+    float fth = floorf(p32);
+    uint32_t th = (uint32_t)fth;
+    if (hi != th) return hi < th;
+    uint32_t tl = (uint32_t)floorf((p32 - fth) * 0x1.0p32f);
+    return lo < tl;
 }
 
 // ---- prescribed laser fields (Sec. 3 setup) ------------------------------------
 // Pulse through its vector potential A(phi), phi = t - x: sin^2 ramps of
 // phi_r and a flat top phi_f; E = -dA/dt, B = x^ cross E for the plane wave.
 template <typename R>
-__device__ __forceinline__ void envelope(const RunDev& r, R phi, R& g, R& dg) {
-    const R pr = (R)r.phi_r, pf = (R)r.phi_f;
-    const R k = (R)(0.5 * kPi) / pr;
+__device__ __forceinline__ void envelope(const StepC<R>& c, R phi, R& g, R& dg) {
+    const R pr = c.phi_r, pf = c.phi_f, k = c.k_env;
     if (!(phi > (R)0) || phi >= (R)2 * pr + pf) { g = 0; dg = 0; return; }
     if (phi < pr) {
-        R s, c;
-        m_sincos(k * phi, &s, &c);
+        R s, cc;
+        m_sincos(k * phi, &s, &cc);
         g = s * s;
-        dg = k * (R)2 * s * c;
+        dg = k * (R)2 * s * cc;
         return;
     }
     if (phi <= pr + pf) { g = 1; dg = 0; return; }
-    R s, c;
-    m_sincos(k * (phi - pr - pf), &s, &c);
-    g = c * c;
-    dg = -k * (R)2 * s * c;
+    R s, cc;
+    m_sincos(k * (phi - pr - pf), &s, &cc);
+    g = cc * cc;
+    dg = -k * (R)2 * s * cc;
 }
 
 // phase t^n - x with t^n = n dt.  In float, n * dt_hi is exact (dt_hi has 11
 // significant bits, n < 2^13), the small remainder n * dt_lo is added, and the
 // position enters as the unevaluated sum x + x_lo kept by the compensated update.
-template <typename R> __device__ __forceinline__ R phase(const RunDev& r, int64_t n, R x, R x_lo);
-template <> __device__ __forceinline__ double phase<double>(const RunDev& r, int64_t n, double x, double) {
-    return (double)n * r.dt - x;
+__device__ __forceinline__ double phase(const StepC<double>& c, uint32_t n, double x, double) {
+    return (double)n * c.dt - x;
 }
-template <> __device__ __forceinline__ float phase<float>(const RunDev& r, int64_t n, float x, float x_lo) {
+__device__ __forceinline__ float phase(const StepC<float>& c, uint32_t n, float x, float x_lo) {
     float nf = (float)n;
-    return fmaf(nf, (float)r.dt_lo, nf * (float)r.dt_hi - x) - x_lo;
+    return fmaf(nf, c.dt_lo, nf * c.dt_hi - x) - x_lo;
 }
 
-// position update x += d.  In float the rounding error of every add is kept in
-// x_lo (Knuth's TwoSum), so positions stay exact to ~1e-12 over any number of
-// steps done in registers; in double the plain add is used.
+// x += d.  In float the rounding error of every add is kept in x_lo (Knuth's
+// TwoSum), so positions stay exact to ~1e-12 over the steps done in registers.
 __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
     float s = x + d;
     float bb = s - x;
@@ -109,23 +121,24 @@ __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
 __device__ __forceinline__ void advance(double& x, double&, double d) { x += d; }
 
 template <typename R>
-__device__ __forceinline__ void fields(const RunDev& r, R x, R x_lo, R y, int64_t n, R E[3], R B[3]) {
+__device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, uint32_t n, R E[3], R B[3]) {
+    const StepC<R>& c = r.c;
     E[0] = E[1] = E[2] = 0;
     B[0] = B[1] = B[2] = 0;
     if (r.geometry == PE_CONST) {
-        for (int k = 0; k < 3; ++k) { E[k] = (R)r.E_const[k]; B[k] = (R)r.B_const[k]; }
+        for (int k = 0; k < 3; ++k) { E[k] = c.E_const[k]; B[k] = c.B_const[k]; }
         return;
     }
-    R phi = phase<R>(r, n, x, x_lo);
+    R phi = phase(c, n, x, x_lo);
     R g, dg;
-    envelope<R>(r, phi, g, dg);
+    envelope<R>(c, phi, g, dg);
     if (g == (R)0 && dg == (R)0) return;
-    const R a0 = (R)r.a0;
+    const R a0 = c.a0;
     R S = 1, theta = phi, inv_R = 0, inv_w2 = 0;
     if (r.geometry == PE_GAUSS_2D) {
         // paraxial 2D focus: amplitude sqrt(w0/w) exp(-y^2/w^2), curvature and Gouy phase
-        const R w0 = (R)r.w0, zr = (R)r.zr;
-        R xi = x - (R)r.xf;
+        const R w0 = c.w0, zr = c.zr;
+        R xi = x - c.xf;
         R w2 = w0 * w0 * ((R)1 + xi * xi / (zr * zr));
         inv_w2 = (R)1 / w2;
         inv_R = xi / (xi * xi + zr * zr);
@@ -181,8 +194,8 @@ __device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R
 
 // ---- table lookups (rows linear in log eta / log gamma) -----------------------
 template <typename R>
-__device__ __forceinline__ void row_pos(R v, double lnlo, double inv, int n, int& i, R& w, int& flag) {
-    R tp = (m_log(v) - (R)lnlo) * (R)inv;
+__device__ __forceinline__ void row_pos(R v, R lnlo, R inv, int n, int& i, R& w, int& flag) {
+    R tp = (m_log(v) - lnlo) * inv;
     flag = 0;
     if (tp >= (R)(n - 1)) { i = n - 2; w = 1; flag = 1; return; }
     if (!(tp >= (R)0)) { i = 0; w = 0; flag = -1; return; }
@@ -195,9 +208,10 @@ __device__ __forceinline__ void row_pos(R v, double lnlo, double inv, int n, int
 // h(eta) by row interpolation; below the table: classical limit 5 pi / 3
 template <typename R>
 __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int& flag) {
-    if (!(eta >= (R)t.eta_min)) { flag = -1; return (R)t.h_classical; }
+    const TabC<R>& c = tabc<R>(t);
+    if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
     int i; R w;
-    row_pos<R>(eta, t.ln_eta_min, t.inv_dln_eta, t.n_eta, i, w, flag);
+    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, t.n_eta, i, w, flag);
     return ((R)1 - w) * h[i] + w * h[i + 1];
 }
 
@@ -223,25 +237,26 @@ __device__ __forceinline__ R invert_rows(const R* ra, const R* rb, R w, int n, R
 // NCS photon energy fraction delta for given eta and uniform Rv (Sec. 2.2)
 template <typename R>
 __device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, R eta, R Rv, bool& below) {
+    const TabC<R>& c = tabc<R>(t);
     const R *ra, *rb;
     R w;
     below = false;
-    if (!(eta >= (R)t.eta_min)) {
+    if (!(eta >= c.eta_min)) {
         ra = rb = cdf + (size_t)t.n_eta * t.n_y;
         w = 0;
         below = true;
     } else {
         int i, fl;
-        row_pos<R>(eta, t.ln_eta_min, t.inv_dln_eta, t.n_eta, i, w, fl);
+        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, t.n_eta, i, w, fl);
         ra = cdf + (size_t)i * t.n_y;
         rb = ra + t.n_y;
     }
     int j;
     R fr = invert_rows<R>(ra, rb, w, t.n_y, Rv, j);
     R y;
-    if (j < 0) y = (R)t.y_min * fr * fr * fr;            // CDF ~ y^(1/3) below the grid
-    else if (j >= t.n_y - 1) y = (R)t.y_max;
-    else y = m_exp((R)t.ln_y_min + ((R)j + fr) * (R)t.dln_y);
+    if (j < 0) y = c.y_min * fr * fr * fr;            // CDF ~ y^(1/3) below the grid
+    else if (j >= t.n_y - 1) y = c.y_max;
+    else y = m_exp(c.ln_y_min + ((R)j + fr) * c.dln_y);
     R q = (R)3 * eta * y;
     return q / ((R)2 + q);
 }
@@ -249,8 +264,9 @@ __device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, 
 // sigma_Z(gamma) by row interpolation in log gamma
 template <typename R>
 __device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma, bool& above) {
+    const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, t.ln_g_min, t.inv_dln_g, t.n_E, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, t.n_E, i, w, fl);
     above = (fl == 1);
     return ((R)1 - w) * sig[i] + w * sig[i + 1];
 }
@@ -258,8 +274,9 @@ __device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma,
 // brems photon energy fraction y from sigma(y, E) = sigma(E) R2 (text after Eq. 4)
 template <typename R>
 __device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z, R gamma, R Rv) {
+    const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, t.ln_g_min, t.inv_dln_g, t.n_E, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, t.n_E, i, w, fl);
     const R* ra = bcdf_z + (size_t)i * t.n_s;
     const R* rb = ra + t.n_s;
     int j;
@@ -268,7 +285,7 @@ __device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z,
     if (j < 0) s = 0;
     else if (j >= t.n_s - 1) s = 1;
     else s = ((R)j + fr) / (R)(t.n_s - 1);
-    R ycut = (R)t.photon_min / gamma, ymax = (R)1 - (R)1 / gamma;
+    R ycut = c.photon_min / gamma, ymax = (R)1 - (R)1 / gamma;
     return ycut * m_exp(s * m_log(ymax / ycut));
 }
 
