@@ -122,6 +122,8 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     C.inv_dln_g = (p->n_E - 1) / (std::log(p->gamma_max) - std::log(p->gamma_min));
     C.photon_min = p->photon_min_mc2;
     C.h_classical = 5.0 * kPi / 3.0;
+    C.eta_last = p->n_eta - 1;
+    C.g_last = p->n_E - 1;
     const double* cs = &C.eta_min;
     float* cfp = &D.cf.eta_min;
     for (size_t k = 0; k < sizeof(TabC<double>) / sizeof(double); ++k) cfp[k] = (float)cs[k];

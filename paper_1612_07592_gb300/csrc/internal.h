@@ -31,6 +31,7 @@ struct TabC {
     R ln_g_min, inv_dln_g;
     R photon_min;
     R h_classical;                        // 5 pi / 3
+    R eta_last, g_last;                   // n_eta - 1 and n_E - 1 (last row position)
 };
 
 // Device view of one table set.  f32 and f64 copies of every table.

@@ -117,7 +117,7 @@ struct StepOut {
 
 template <typename R>
 __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
-                                         const double* bcdf_z, uint32_t id, uint32_t n,
+                                         const double* bcdf_z, uint32_t id, uint32_t n, R nf,
                                          Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
                                          unsigned long long* tally) {
     out.ncs = out.br = false;
@@ -125,7 +125,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
     const R photon_min = tabc<R>(t).photon_min;
     const R dt = c.dt;
     R E[3], B[3];
-    fields<R>(r, P.x, P.x_lo, P.y, n, E, B);
+    fields<R>(r, P.x, P.x_lo, P.y, nf, E, B);
     boris<R>(P.u, E, B, dt);
     R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
     const R xn = P.x, yn = P.y;
@@ -222,8 +222,7 @@ __device__ __forceinline__ void store_tau(const RunDevT<double>& r, int64_t i, c
     ((double*)r.tau)[i] = P.tau;
 }
 __device__ __forceinline__ void store_tau(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
-    float s = P.tau + P.tau_lo;                 // renormalise the pair
-    ((float2*)r.tau)[i] = make_float2(s, P.tau_lo - (s - P.tau));
+    ((float2*)r.tau)[i] = make_float2(P.tau, P.tau_lo);
 }
 
 __device__ __forceinline__ void load_pos(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
@@ -245,17 +244,14 @@ __device__ __forceinline__ void load_pos(const RunDevT<float>& r, int64_t i, Par
         P.y_lo = 0;
     }
 }
-__device__ __forceinline__ float2 renorm(float hi, float lo) {
-    float s = hi + lo;
-    return make_float2(s, lo - (s - hi));
-}
 __device__ __forceinline__ void store_pos(const RunDevT<double>& r, int64_t i, const Particle<double>& P) {
     ((double*)r.x)[i] = P.x;
     if (r.geometry == PE_GAUSS_2D) ((double*)r.y)[i] = P.y;
 }
+// pairs are stored exactly as held in registers, so a launch boundary changes nothing
 __device__ __forceinline__ void store_pos(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
-    ((float2*)r.x)[i] = isnan(P.x) ? make_float2(P.x, 0.0f) : renorm(P.x, P.x_lo);
-    if (r.geometry == PE_GAUSS_2D) ((float2*)r.y)[i] = renorm(P.y, P.y_lo);
+    ((float2*)r.x)[i] = make_float2(P.x, P.x_lo);
+    if (r.geometry == PE_GAUSS_2D) ((float2*)r.y)[i] = make_float2(P.y, P.y_lo);
 }
 
 template <typename R>
@@ -298,8 +294,8 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
     }
     if (active) {
         step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E,
-                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, (uint32_t)r.step0, P, out, r.hist,
-                         r.tally);
+                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, (uint32_t)r.step0,
+                         (double)r.step0, P, out, r.hist, r.tally);
         store_particle<double>(r, i, P);
     }
     warp_append(r, out.ncs, out.pn);
@@ -335,7 +331,7 @@ __device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_t
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
+__global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
@@ -368,11 +364,13 @@ __global__ void __launch_bounds__(256) k_step_persistent(TablesDev t, BatchDevT<
         }
         const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
         const double* bcdf_z = t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s;
-        for (int s = 0; s < steps; ++s) {
+        const uint32_t n0 = (uint32_t)r.step0;
+        R nf = (R)n0;                      // step index as a float, advanced by exact +1
+        for (int s = 0; s < steps; ++s, nf += (R)1) {
             StepOut<R> out;
             out.ncs = out.br = false;
             if (active) {
-                step_one<R>(t, r, s_h, sig_z, bcdf_z, (uint32_t)i, (uint32_t)(r.step0 + s), P, out, s_hist,
+                step_one<R>(t, r, s_h, sig_z, bcdf_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist,
                             s_tally);
                 if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
             }

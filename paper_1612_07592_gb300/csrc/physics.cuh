@@ -101,11 +101,11 @@ __device__ __forceinline__ void envelope(const StepC<R>& c, R phi, R& g, R& dg) 
 // phase t^n - x with t^n = n dt.  In float, n * dt_hi is exact (dt_hi has 11
 // significant bits, n < 2^13), the small remainder n * dt_lo is added, and the
 // position enters as the unevaluated sum x + x_lo kept by the compensated update.
-__device__ __forceinline__ double phase(const StepC<double>& c, uint32_t n, double x, double) {
-    return (double)n * c.dt - x;
+// nf is the step index n held as a float (exact for n < 2^24).
+__device__ __forceinline__ double phase(const StepC<double>& c, double nf, double x, double) {
+    return nf * c.dt - x;
 }
-__device__ __forceinline__ float phase(const StepC<float>& c, uint32_t n, float x, float x_lo) {
-    float nf = (float)n;
+__device__ __forceinline__ float phase(const StepC<float>& c, float nf, float x, float x_lo) {
     return fmaf(nf, c.dt_lo, nf * c.dt_hi - x) - x_lo;
 }
 
@@ -121,7 +121,7 @@ __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
 __device__ __forceinline__ void advance(double& x, double&, double d) { x += d; }
 
 template <typename R>
-__device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, uint32_t n, R E[3], R B[3]) {
+__device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R nf, R E[3], R B[3]) {
     const StepC<R>& c = r.c;
     E[0] = E[1] = E[2] = 0;
     B[0] = B[1] = B[2] = 0;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, ui
         for (int k = 0; k < 3; ++k) { E[k] = c.E_const[k]; B[k] = c.B_const[k]; }
         return;
     }
-    R phi = phase(c, n, x, x_lo);
+    R phi = phase(c, nf, x, x_lo);
     R g, dg;
     envelope<R>(c, phi, g, dg);
     if (g == (R)0 && dg == (R)0) return;
@@ -193,16 +193,20 @@ __device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R
 }
 
 // ---- table lookups (rows linear in log eta / log gamma) -----------------------
+// row index of a position 0 <= f < 2^23 that is already an integer-valued float,
+// without an int/float conversion instruction (add 2^23, read the mantissa bits)
+__device__ __forceinline__ int row_index(float f) { return __float_as_int(f + 0x1.0p23f) - 0x4B000000; }
+__device__ __forceinline__ int row_index(double f) { return (int)f; }
+
 template <typename R>
-__device__ __forceinline__ void row_pos(R v, R lnlo, R inv, int n, int& i, R& w, int& flag) {
+__device__ __forceinline__ void row_pos(R v, R lnlo, R inv, R last, int& i, R& w, int& flag) {
     R tp = (m_log(v) - lnlo) * inv;
     flag = 0;
-    if (tp >= (R)(n - 1)) { i = n - 2; w = 1; flag = 1; return; }
+    if (tp >= last) { i = row_index(last - (R)1); w = 1; flag = 1; return; }
     if (!(tp >= (R)0)) { i = 0; w = 0; flag = -1; return; }
-    int k = (int)tp;
-    if (k > n - 2) k = n - 2;
-    i = k;
-    w = tp - (R)k;
+    R f = m_floor(tp);
+    i = row_index(f);
+    w = tp - f;
 }
 
 // h(eta) by row interpolation; below the table: classical limit 5 pi / 3
@@ -211,7 +215,7 @@ __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int
     const TabC<R>& c = tabc<R>(t);
     if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
     int i; R w;
-    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, t.n_eta, i, w, flag);
+    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, i, w, flag);
     return ((R)1 - w) * h[i] + w * h[i + 1];
 }
 
@@ -247,7 +251,7 @@ __device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, 
         below = true;
     } else {
         int i, fl;
-        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, t.n_eta, i, w, fl);
+        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, i, w, fl);
         ra = cdf + (size_t)i * t.n_y;
         rb = ra + t.n_y;
     }
@@ -266,7 +270,7 @@ template <typename R>
 __device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma, bool& above) {
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, t.n_E, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, i, w, fl);
     above = (fl == 1);
     return ((R)1 - w) * sig[i] + w * sig[i + 1];
 }
@@ -276,7 +280,7 @@ template <typename R>
 __device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z, R gamma, R Rv) {
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, t.n_E, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, i, w, fl);
     const R* ra = bcdf_z + (size_t)i * t.n_s;
     const R* rb = ra + t.n_s;
     int j;
