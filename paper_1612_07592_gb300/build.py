@@ -14,7 +14,7 @@ SOURCES = ["api.cu", "kernels.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # single-precision division and square root at 2-ulp accuracy in the kernels (the FP64
-# arithmetic is unaffected); the FP32 error budget against the oracle includes this
+# arithmetic is unaffected); the stated FP32 error budget includes this
 KERNEL_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 
