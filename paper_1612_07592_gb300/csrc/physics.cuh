@@ -24,7 +24,34 @@ __device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
 __device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
 __device__ __forceinline__ float m_atan(float v) { return atanf(v); }
 __device__ __forceinline__ double m_atan(double v) { return atan(v); }
-__device__ __forceinline__ void m_sincos(float v, float* s, float* c) { sincosf(v, s, c); }
+// Single-precision sine and cosine without int/float conversion instructions:
+// Cody-Waite reduction by pi/2 (quadrant by magic-number rounding, two-part
+// constant with fused multiply-adds), then the Taylor series of sin and cos on
+// [-pi/4, pi/4] (truncation error below 2e-10, so the result is accurate to a
+// few float ulps).  Valid for |v| < 2^22.
+__device__ __forceinline__ void m_sincos(float v, float* s_out, float* c_out) {
+    const float kMagic = 0x1.8p23f;                       // 1.5 * 2^23
+    float t = fmaf(v, 0.636619772367581343f, kMagic);     // v * 2/pi rounded to an integer
+    int q = __float_as_int(t);                            // quadrant in the low bits
+    float k = t - kMagic;
+    float r = fmaf(-k, 1.57079637050628662f, v);          // pi/2 = 1.5707963705... + (-4.37e-8)
+    r = fmaf(-k, -4.37113900018624283e-8f, r);
+    float r2 = r * r;
+    float sp = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);  //  1/9!, -1/7!
+    sp = fmaf(r2, sp, 8.33333333e-3f);                      //  1/5!
+    sp = fmaf(r2, sp, -1.66666667e-1f);                     // -1/3!
+    float sn = fmaf(r * r2, sp, r);
+    float cp = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);  // -1/10!, 1/8!
+    cp = fmaf(r2, cp, -1.38888889e-3f);                     // -1/6!
+    cp = fmaf(r2, cp, 4.16666667e-2f);                      //  1/4!
+    cp = fmaf(r2, cp, -0.5f);                               // -1/2!
+    float cs = fmaf(r2, cp, 1.0f);
+    // rotate by the quadrant: (sin, cos) of v = rotation of (sn, cs) by q * pi/2
+    float a = (q & 1) ? cs : sn;
+    float b = (q & 1) ? sn : cs;
+    *s_out = (q & 2) ? -a : a;
+    *c_out = ((q + 1) & 2) ? -b : b;
+}
 __device__ __forceinline__ void m_sincos(double v, double* s, double* c) { sincos(v, s, c); }
 __device__ __forceinline__ float m_atan2(float a, float b) { return atan2f(a, b); }
 __device__ __forceinline__ double m_atan2(double a, double b) { return atan2(a, b); }
@@ -193,20 +220,28 @@ __device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R
 }
 
 // ---- table lookups (rows linear in log eta / log gamma) -----------------------
-// row index of a position 0 <= f < 2^23 that is already an integer-valued float,
-// without an int/float conversion instruction (add 2^23, read the mantissa bits)
-__device__ __forceinline__ int row_index(float f) { return __float_as_int(f + 0x1.0p23f) - 0x4B000000; }
-__device__ __forceinline__ int row_index(double f) { return (int)f; }
+// Row of a position 0 <= tp < 2^22 without int/float conversion instructions: the
+// nearest integer to tp - 1/2 is read off the mantissa after adding 1.5 * 2^23 (where
+// floats are spaced by 1).  This is floor(tp), or floor(tp) - 1 with weight 1 when tp
+// is an exact integer; both give the same interpolated value.
+__device__ __forceinline__ void split_pos(float tp, int& i, float& w) {
+    float t = (tp - 0.5f) + 0x1.8p23f;
+    i = __float_as_int(t) - 0x4B400000;
+    w = tp - (t - 0x1.8p23f);
+}
+__device__ __forceinline__ void split_pos(double tp, int& i, double& w) {
+    double f = floor(tp);
+    i = (int)f;
+    w = tp - f;
+}
 
 template <typename R>
-__device__ __forceinline__ void row_pos(R v, R lnlo, R inv, R last, int& i, R& w, int& flag) {
+__device__ __forceinline__ void row_pos(R v, R lnlo, R inv, R last, int n, int& i, R& w, int& flag) {
     R tp = (m_log(v) - lnlo) * inv;
     flag = 0;
-    if (tp >= last) { i = row_index(last - (R)1); w = 1; flag = 1; return; }
+    if (tp >= last) { i = n - 2; w = 1; flag = 1; return; }
     if (!(tp >= (R)0)) { i = 0; w = 0; flag = -1; return; }
-    R f = m_floor(tp);
-    i = row_index(f);
-    w = tp - f;
+    split_pos(tp, i, w);
 }
 
 // h(eta) by row interpolation; below the table: classical limit 5 pi / 3
@@ -215,7 +250,7 @@ __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int
     const TabC<R>& c = tabc<R>(t);
     if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
     int i; R w;
-    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, i, w, flag);
+    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, flag);
     return ((R)1 - w) * h[i] + w * h[i + 1];
 }
 
@@ -251,7 +286,7 @@ __device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, 
         below = true;
     } else {
         int i, fl;
-        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, i, w, fl);
+        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, fl);
         ra = cdf + (size_t)i * t.n_y;
         rb = ra + t.n_y;
     }
@@ -270,7 +305,7 @@ template <typename R>
 __device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma, bool& above) {
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
     above = (fl == 1);
     return ((R)1 - w) * sig[i] + w * sig[i + 1];
 }
@@ -280,7 +315,7 @@ template <typename R>
 __device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z, R gamma, R Rv) {
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
-    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, i, w, fl);
+    row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
     const R* ra = bcdf_z + (size_t)i * t.n_s;
     const R* rb = ra + t.n_s;
     int j;
