@@ -85,7 +85,7 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     const HostTables& H = t->host;
     size_t n_h = H.h.size(), n_c = H.cdf.size(), n_sg = H.sigma.size(), n_b = H.bcdf.size();
     size_t n_all = n_h + n_c + n_sg + n_b;
-    size_t bytes = n_all * (sizeof(double) + sizeof(float)) + 64;
+    size_t bytes = n_all * (sizeof(double) + 2 * sizeof(float)) + 64;
     cudaError_t e = cudaMalloc(&t->dmem, bytes);
     if (e != cudaSuccess) {
         delete t;
@@ -98,10 +98,14 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     all64.insert(all64.end(), H.sigma.begin(), H.sigma.end());
     all64.insert(all64.end(), H.bcdf.begin(), H.bcdf.end());
     std::vector<float> all32(all64.begin(), all64.end());
+    std::vector<float> all32lo(n_all);
+    for (size_t k = 0; k < n_all; ++k) all32lo[k] = (float)(all64[k] - (double)all32[k]);
     double* d64 = static_cast<double*>(t->dmem);
     float* d32 = reinterpret_cast<float*>(d64 + n_all);
+    float* d32lo = d32 + n_all;
     e = cudaMemcpy(d64, all64.data(), n_all * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d32, all32.data(), n_all * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d32lo, all32lo.data(), n_all * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(t->dmem);
         delete t;
@@ -110,6 +114,8 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     TablesDev& D = t->dev;
     D.h64 = d64; D.cdf64 = d64 + n_h; D.sig64 = D.cdf64 + n_c; D.bcdf64 = D.sig64 + n_sg;
     D.h32 = d32; D.cdf32 = d32 + n_h; D.sig32 = D.cdf32 + n_c; D.bcdf32 = D.sig32 + n_sg;
+    D.cdf32lo = d32lo + n_h;
+    D.bcdf32lo = d32lo + n_h + n_c + n_sg;
     D.n_eta = p->n_eta; D.n_y = p->n_y; D.n_E = p->n_E; D.n_s = p->n_s; D.n_Z = p->n_Z;
     TabC<double>& C = D.cd;
     C.eta_min = p->eta_min;
@@ -124,6 +130,7 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     C.h_classical = 5.0 * kPi / 3.0;
     C.eta_last = p->n_eta - 1;
     C.g_last = p->n_E - 1;
+    C.s_step = 1.0 / (p->n_s - 1);
     const double* cs = &C.eta_min;
     float* cfp = &D.cf.eta_min;
     for (size_t k = 0; k < sizeof(TabC<double>) / sizeof(double); ++k) cfp[k] = (float)cs[k];

@@ -32,6 +32,7 @@ struct TabC {
     R photon_min;
     R h_classical;                        // 5 pi / 3
     R eta_last, g_last;                   // n_eta - 1 and n_E - 1 (last row position)
+    R s_step;                             // 1 / (n_s - 1)
 };
 
 // Device view of one table set.  f32 and f64 copies of every table.
@@ -40,6 +41,8 @@ struct TablesDev {
     const float* cdf32; const double* cdf64;    // [(n_eta + 1) * n_y]; row n_eta = classical limit
     const float* sig32; const double* sig64;    // [n_Z * n_E]
     const float* bcdf32; const double* bcdf64;  // [n_Z * n_E * n_s]
+    const float* cdf32lo;                       // float-pair remainders: value = cdf32 + cdf32lo
+    const float* bcdf32lo;
     int n_eta, n_y, n_E, n_s, n_Z;
     TabC<float> cf;
     TabC<double> cd;

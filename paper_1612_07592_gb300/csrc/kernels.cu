@@ -21,6 +21,7 @@
 
 #include "internal.h"
 #include "physics.cuh"
+#include "rare_f32.cuh"
 
 namespace pe {
 
@@ -42,20 +43,6 @@ struct Photon {
     float x, y, e, kx, ky, kz;
     uint32_t step, id_mech;
 };
-
-template <typename R>
-__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
-                                         R kx, R ky, R inv_log_emax) {
-    int eb = (int)m_floor((R)PE_HIST_E_BINS * m_log_acc(e) * inv_log_emax);
-    if (eb >= PE_HIST_E_BINS) { eb = PE_HIST_E_BINS - 1; atomicAdd(tally + PE_T_N_HIST_OVER, 1ull); }
-    if (eb < 0) eb = 0;
-    R th = m_atan2(ky, kx);
-    int tb = (int)m_floor((th + (R)kPi) / (R)(2.0 * kPi) * (R)PE_HIST_T_BINS);
-    if (tb < 0) tb = 0;
-    if (tb >= PE_HIST_T_BINS) tb = PE_HIST_T_BINS - 1;
-    atomicAdd(hist + mech * PE_HIST_E_BINS + eb, 1ull);
-    atomicAdd(hist + 2 * PE_HIST_E_BINS + mech * PE_HIST_T_BINS + tb, 1ull);
-}
 
 // warp-aggregated append of at most one photon per lane; all 32 lanes call it
 template <typename R>
@@ -103,11 +90,58 @@ __device__ __forceinline__ void tau_sub(Particle<float>& P, float d) {
 }
 template <typename R>
 __device__ __forceinline__ bool tau_crossed(const Particle<R>& P) { return P.tau + P.tau_lo <= (R)0; }
-__device__ __forceinline__ void tau_set(Particle<double>& P, double v) { P.tau = v; P.tau_lo = 0; }
-__device__ __forceinline__ void tau_set(Particle<float>& P, double v) {
-    P.tau = (float)v;
-    P.tau_lo = (float)(v - (double)P.tau);
+// rare-branch arithmetic by precision: the FP64 path in double, the FP32 path in
+// float pairs and integers (no FP64 or conversion instructions, see rare_f32.cuh)
+__device__ __forceinline__ void tau_draw(Particle<double>& P, uint4 w) {
+    P.tau = -log(uni53(w64(w.z, w.w)));
+    P.tau_lo = 0;
 }
+__device__ __forceinline__ void tau_draw(Particle<float>& P, uint4 w) {
+    P.tau = tau_draw_f32(w.z, w.w);
+    P.tau_lo = 0;
+}
+__device__ __forceinline__ double sample_delta(const TablesDev& t, double eta, uint4 w, bool& below) {
+    return sample_ncs_delta<double>(t, t.cdf64, eta, uni53(w64(w.x, w.y)), below);
+}
+__device__ __forceinline__ float sample_delta(const TablesDev& t, float eta, uint4 w, bool& below) {
+    return sample_ncs_delta_f32(t, eta, w.x, w.y, below);
+}
+__device__ __forceinline__ double sample_y(const TablesDev& t, int iz, double gamma, uint4 w) {
+    return sample_brems_y<double>(t, t.bcdf64 + (size_t)iz * t.n_E * t.n_s, gamma, uni53(w64(w.z, w.w)));
+}
+__device__ __forceinline__ float sample_y(const TablesDev& t, int iz, float gamma, uint4 w) {
+    return sample_brems_y_f32(t, iz, gamma, w.z, w.w);
+}
+__device__ __forceinline__ void fx_add_r(unsigned long long* p, double v) { fx_add(p, v); }
+__device__ __forceinline__ void fx_add_r(unsigned long long* p, float v) { fx_add_f32(p, v); }
+__device__ __forceinline__ bool brems_event(double P, uint4 w) { return below_threshold(P, w.x, w.y); }
+__device__ __forceinline__ bool brems_event(float P, uint4 w) { return below_threshold_f32(P, w.x, w.y); }
+__device__ __forceinline__ void hist_bins(double e, double kx, double ky, double inv_log_emax, int& eb, int& tb,
+                                          bool& over) {
+    eb = (int)floor((double)PE_HIST_E_BINS * log(e) * inv_log_emax);
+    over = eb >= PE_HIST_E_BINS;
+    if (over) eb = PE_HIST_E_BINS - 1;
+    if (eb < 0) eb = 0;
+    tb = (int)floor((atan2(ky, kx) + kPi) / (2.0 * kPi) * (double)PE_HIST_T_BINS);
+    if (tb < 0) tb = 0;
+    if (tb >= PE_HIST_T_BINS) tb = PE_HIST_T_BINS - 1;
+}
+__device__ __forceinline__ void hist_bins(float e, float kx, float ky, float inv_log_emax, int& eb, int& tb,
+                                          bool& over) {
+    hist_bins_f32(e, kx, ky, inv_log_emax, eb, tb, over);
+}
+
+template <typename R>
+__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
+                                         R kx, R ky, R inv_log_emax) {
+    int eb, tb;
+    bool over;
+    hist_bins(e, kx, ky, inv_log_emax, eb, tb, over);
+    if (over) atomicAdd(tally + PE_T_N_HIST_OVER, 1ull);
+    atomicAdd(hist + mech * PE_HIST_E_BINS + eb, 1ull);
+    atomicAdd(hist + 2 * PE_HIST_E_BINS + mech * PE_HIST_T_BINS + tb, 1ull);
+}
+
 
 template <typename R>
 struct StepOut {
@@ -117,7 +151,7 @@ struct StepOut {
 
 template <typename R>
 __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
-                                         const double* bcdf_z, uint32_t id, uint32_t n, R nf,
+                                         uint32_t id, uint32_t n, R nf,
                                          Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
                                          unsigned long long* tally) {
     out.ncs = out.br = false;
@@ -140,8 +174,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if (tau_crossed(P)) {
             uint4 w = draw(r, id, n, PUR_NCS);
             bool below;
-            // rare branch: the inverse CDF runs in FP64 on the FP64 table with a 53-bit uniform
-            R delta = (R)sample_ncs_delta<double>(t, t.cdf64, (double)eta, uni53(w64(w.x, w.y)), below);
+            R delta = sample_delta(t, eta, w, below);
             if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
             R ew = delta * gamma;
             if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
@@ -149,19 +182,19 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
             recoil<R>(P.u, gamma, ew, k);
             note_event<R>(P, n, 0);
             R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            fx_add(tally + PE_T_E_RECOIL_NCS, (double)(gamma - gn));
+            fx_add_r(tally + PE_T_E_RECOIL_NCS, gamma - gn);
             if (ew >= photon_min) {
                 atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
-                fx_add(tally + PE_T_E_NCS_STORED, (double)ew);
+                fx_add_r(tally + PE_T_E_NCS_STORED, ew);
                 hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
                 out.ncs = true;
                 out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
             } else {
                 atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
-                fx_add(tally + PE_T_E_NCS_BELOW, (double)ew);
+                fx_add_r(tally + PE_T_E_NCS_BELOW, ew);
             }
             gamma = gn;
-            tau_set(P, -log(uni53(w64(w.z, w.w))));
+            tau_draw(P, w);
         }
     }
 
@@ -176,24 +209,24 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
             R xb = c.K_br * sig * (um / gamma);
             R Pbr = -m_expm1(-xb);
             uint4 w = draw(r, id, n, PUR_BREMS);
-            if (below_threshold(Pbr, w.x, w.y)) {
-                R yy = (R)sample_brems_y<double>(t, bcdf_z, (double)gamma, uni53(w64(w.z, w.w)));
+            if (brems_event(Pbr, w)) {
+                R yy = sample_y(t, r.iz, gamma, w);
                 R ew = yy * gamma;
                 R k[3];
                 recoil<R>(P.u, gamma, ew, k);
                 note_event<R>(P, n, 1);
                 R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-                fx_add(tally + PE_T_E_RECOIL_BR, (double)(gamma - gn));
+                fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
                 if (ew >= photon_min) {
                     atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
-                    fx_add(tally + PE_T_E_BR_STORED, (double)ew);
+                    fx_add_r(tally + PE_T_E_BR_STORED, ew);
                     hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
                     out.br = true;
                     out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n,
                                     id | 0x80000000u};
                 } else {
                     atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
-                    fx_add(tally + PE_T_E_BR_BELOW, (double)ew);
+                    fx_add_r(tally + PE_T_E_BR_BELOW, ew);
                 }
                 gamma = gn;
             }
@@ -293,8 +326,7 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
         active = !isnan(P.x);
     }
     if (active) {
-        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E,
-                         t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s, (uint32_t)i, (uint32_t)r.step0,
+        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E, (uint32_t)i, (uint32_t)r.step0,
                          (double)r.step0, P, out, r.hist, r.tally);
         store_particle<double>(r, i, P);
     }
@@ -330,9 +362,13 @@ __device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_t
     __syncthreads();
 }
 
-template <typename R>
+// kSingle: one run, its descriptor read straight from the kernel parameters
+// (constant-bank operands); otherwise the current run's descriptor is copied to
+// shared memory once per tile, so no step reads an indexed kernel parameter.
+template <typename R, bool kSingle>
 __global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RunDevT<R> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
     R* s_h = reinterpret_cast<R*>(s_tally + PE_TALLY_WORDS);
@@ -349,12 +385,20 @@ __global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDe
     int cur = -1;
     int run_idx = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        while (run_idx + 1 < b.n_runs && b.tile_start[run_idx + 1] <= tile) ++run_idx;
-        if (run_idx != cur) {
-            if (cur >= 0) flush_shared<R>(s_hist, s_tally, b.runs[cur]);
-            cur = run_idx;
+        if (!kSingle) {
+            while (run_idx + 1 < b.n_runs && b.tile_start[run_idx + 1] <= tile) ++run_idx;
+            if (run_idx != cur) {
+                if (cur >= 0) flush_shared<R>(s_hist, s_tally, s_run);
+                constexpr int kWords = sizeof(RunDevT<R>) / 4;
+                static_assert(kWords <= 256, "run descriptor larger than one word per thread");
+                if (threadIdx.x < kWords)
+                    reinterpret_cast<uint32_t*>(&s_run)[threadIdx.x] =
+                        reinterpret_cast<const uint32_t*>(&b.runs[run_idx])[threadIdx.x];
+                __syncthreads();
+                cur = run_idx;
+            }
         }
-        const RunDevT<R>& r = b.runs[run_idx];
+        const RunDevT<R>& r = kSingle ? b.runs[0] : s_run;
         int64_t i = (tile - b.tile_start[run_idx]) * b.tile + threadIdx.x;
         bool active = i < r.n;
         Particle<R> P;
@@ -363,23 +407,26 @@ __global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDe
             active = !isnan(P.x);
         }
         const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
-        const double* bcdf_z = t.bcdf64 + (size_t)r.iz * t.n_E * t.n_s;
         const uint32_t n0 = (uint32_t)r.step0;
         R nf = (R)n0;                      // step index as a float, advanced by exact +1
         for (int s = 0; s < steps; ++s, nf += (R)1) {
             StepOut<R> out;
             out.ncs = out.br = false;
             if (active) {
-                step_one<R>(t, r, s_h, sig_z, bcdf_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist,
-                            s_tally);
+                step_one<R>(t, r, s_h, sig_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
                 if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
             }
             warp_append(r, out.ncs, out.pn);
             warp_append(r, out.br, out.pb);
         }
         if (active) store_particle<R>(r, i, P);
+        cur = kSingle ? 0 : cur;
     }
-    if (cur >= 0) flush_shared<R>(s_hist, s_tally, b.runs[cur]);
+    if (kSingle) {
+        if (gridDim.x > 0 && n_tiles > 0) flush_shared<R>(s_hist, s_tally, b.runs[0]);
+    } else if (cur >= 0) {
+        flush_shared<R>(s_hist, s_tally, s_run);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -463,24 +510,32 @@ int persistent_smem_bytes(const TablesDev& t, int precision) {
 int persistent_occupancy(int precision, int block, int smem) {
     int occ = 0;
     cudaError_t e = precision == PE_F32
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float>, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<double>, block, smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false>, block, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<double, false>, block, smem);
     return e == cudaSuccess ? occ : 1;
+}
+
+template <typename R>
+static void launch_persistent(const TablesDev& t, const BatchDevT<R>& b, int steps, int grid, int block,
+                              cudaStream_t s, int smem) {
+    if (b.n_runs == 1) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_step_persistent<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_step_persistent<R, true><<<grid, block, smem, s>>>(t, b, steps);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_step_persistent<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_step_persistent<R, false><<<grid, block, smem, s>>>(t, b, steps);
+    }
 }
 
 void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
                                 cudaStream_t s) {
-    int smem = persistent_smem_bytes(t, PE_F32);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_step_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_step_persistent<float><<<grid, block, smem, s>>>(t, b, steps);
+    launch_persistent<float>(t, b, steps, grid, block, s, persistent_smem_bytes(t, PE_F32));
 }
 void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
                                 cudaStream_t s) {
-    int smem = persistent_smem_bytes(t, PE_F64);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_step_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_step_persistent<double><<<grid, block, smem, s>>>(t, b, steps);
+    launch_persistent<double>(t, b, steps, grid, block, s, persistent_smem_bytes(t, PE_F64));
 }
 
 }  // namespace pe
