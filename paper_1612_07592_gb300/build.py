@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe.so")
-SOURCES = ["api.cu", "kernels.cu", "tables.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "kernels_f32.cu", "kernels_f64.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # single-precision division and square root at 2-ulp accuracy in the kernels (the FP64
@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, src + ".o")
-        extra = KERNEL_FLAGS if src == "kernels.cu" else []
+        extra = KERNEL_FLAGS if src.startswith("kernels") else []
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, *FLAGS, "-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj] + ARCH

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "physics.cuh"
 
 using namespace pe;
 
@@ -311,42 +312,47 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
     int smem = persistent_smem_bytes(t->dev, prec);
     if (smem > 200 * 1024)
         return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
-    int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : persistent_occupancy(prec, block, smem);
+    int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : (prec == PE_F32 ? persistent_occupancy_f32(block, smem) : persistent_occupancy_f64(block, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t tile_start[PE_MAX_BATCH + 1];
-    tile_start[0] = 0;
-    for (int k = 0; k < n_runs; ++k) tile_start[k + 1] = tile_start[k] + (runs[k]->dev.n + block - 1) / block;
-    int64_t n_tiles = tile_start[n_runs];
-    if (n_tiles == 0) {
-        for (int k = 0; k < n_runs; ++k) runs[k]->steps_done += n_steps;
-        return PE_OK;
-    }
-    int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
-    if (prec == PE_F32) {
-        BatchDevT<float> b;   // host staging; passed by value to the kernel
-        std::memset(&b, 0, sizeof(b));
-        b.n_runs = n_runs;
-        b.tile = block;
-        for (int k = 0; k <= n_runs; ++k) b.tile_start[k] = tile_start[k];
-        for (int k = 0; k < n_runs; ++k) b.runs[k] = to_float(runs[k]->dev);
-        for (int64_t done = 0; done < n_steps; done += K) {
-            int k_now = (int)std::min<int64_t>(K, n_steps - done);
-            for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
-            launch_step_persistent_f32(t->dev, b, k_now, grid, block, s);
-            g_launches++;
-        }
-    } else {
-        BatchDevT<double> b;
-        std::memset(&b, 0, sizeof(b));
-        b.n_runs = n_runs;
-        b.tile = block;
-        for (int k = 0; k <= n_runs; ++k) b.tile_start[k] = tile_start[k];
-        for (int k = 0; k < n_runs; ++k) b.runs[k] = runs[k]->dev;
-        for (int64_t done = 0; done < n_steps; done += K) {
-            int k_now = (int)std::min<int64_t>(K, n_steps - done);
-            for (int k = 0; k < n_runs; ++k) b.runs[k].step0 = runs[k]->steps_done + done;
-            launch_step_persistent_f64(t->dev, b, k_now, grid, block, s);
-            g_launches++;
+    // one launch per field kind present in the batch (each kernel is specialised on it)
+    for (int fk = 0; fk <= 4; ++fk) {
+        int idx[PE_MAX_BATCH];
+        int m = 0;
+        for (int k = 0; k < n_runs; ++k)
+            if (field_kind(runs[k]->dev.geometry, runs[k]->dev.polarisation) == fk) idx[m++] = k;
+        if (m == 0) continue;
+        int64_t tile_start[PE_MAX_BATCH + 1];
+        tile_start[0] = 0;
+        for (int k = 0; k < m; ++k) tile_start[k + 1] = tile_start[k] + (runs[idx[k]]->dev.n + block - 1) / block;
+        int64_t n_tiles = tile_start[m];
+        if (n_tiles == 0) continue;
+        int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
+        if (prec == PE_F32) {
+            BatchDevT<float> b;   // host staging; passed by value to the kernel
+            std::memset(&b, 0, sizeof(b));
+            b.n_runs = m;
+            b.tile = block;
+            for (int k = 0; k <= m; ++k) b.tile_start[k] = tile_start[k];
+            for (int k = 0; k < m; ++k) b.runs[k] = to_float(runs[idx[k]]->dev);
+            for (int64_t done = 0; done < n_steps; done += K) {
+                int k_now = (int)std::min<int64_t>(K, n_steps - done);
+                for (int k = 0; k < m; ++k) b.runs[k].step0 = runs[idx[k]]->steps_done + done;
+                launch_step_persistent_f32(t->dev, b, k_now, grid, block, s);
+                g_launches++;
+            }
+        } else {
+            BatchDevT<double> b;
+            std::memset(&b, 0, sizeof(b));
+            b.n_runs = m;
+            b.tile = block;
+            for (int k = 0; k <= m; ++k) b.tile_start[k] = tile_start[k];
+            for (int k = 0; k < m; ++k) b.runs[k] = runs[idx[k]]->dev;
+            for (int64_t done = 0; done < n_steps; done += K) {
+                int k_now = (int)std::min<int64_t>(K, n_steps - done);
+                for (int k = 0; k < m; ++k) b.runs[k].step0 = runs[idx[k]]->steps_done + done;
+                launch_step_persistent_f64(t->dev, b, k_now, grid, block, s);
+                g_launches++;
+            }
         }
     }
     cudaError_t e = cudaGetLastError();

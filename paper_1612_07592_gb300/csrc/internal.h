@@ -126,6 +126,7 @@ void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, i
 void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
                                 cudaStream_t s);
 int persistent_smem_bytes(const TablesDev& t, int precision);
-int persistent_occupancy(int precision, int block, int smem);
+int persistent_occupancy_f32(int block, int smem);
+int persistent_occupancy_f64(int block, int smem);
 
 }  // namespace pe

@@ -1,316 +1,8 @@
-// kernels.cu -- the emission-step kernels for sm_103a.
-//
-//  k_init            one thread per particle: initial position, momentum and
-//                    optical depth from the particle's Philox stream.
-//  k_step_plain      FP64, one thread per particle, one step per launch,
-//                    tables read from global memory, histograms and tallies
-//                    by global atomics (the plain per-run path).
-//  k_step_persistent grid-stride over tiles of one or many runs, K steps per
-//                    launch with the particle state in registers, the rate
-//                    tables (h(eta), sigma_Z(gamma)) staged in shared memory,
-//                    photon append by warp-aggregated atomics, histograms and
-//                    tallies accumulated in shared memory and flushed once per
-//                    run per CTA.  Instantiated for float (fast path) and double.
-//
-// Step order per particle (Sec. 2.2): fields at (x^n, t^n) -> Boris push ->
-// eta -> NCS optical depth (emission at tau <= 0) -> brems test (Eq. 4) ->
-// position update.  Both emissions may fire in one step; brems sees the
-// momentum after the NCS recoil.
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "internal.h"
-#include "physics.cuh"
-#include "rare_f32.cuh"
+// kernels.cu -- launchers of the init and plain FP64 kernels and the precision-
+// specific persistent kernels (instantiated in kernels_f32.cu / kernels_f64.cu).
+#include "kernels.cuh"
 
 namespace pe {
-
-// ---------------------------------------------------------------------------
-// accumulation helpers
-// ---------------------------------------------------------------------------
-// 128-bit fixed-point add of v >= 0 (m c^2) into (lo, hi): exact, order-free
-__device__ __forceinline__ void fx_add(unsigned long long* w, double v) {
-    if (!(v > 0.0)) return;
-    double ip = floor(v);
-    unsigned long long lo = __double2ull_rz((v - ip) * 0x1.0p64);
-    unsigned long long old = atomicAdd(w, lo);
-    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    unsigned long long hi = (unsigned long long)ip + carry;
-    if (hi) atomicAdd(w + 1, hi);
-}
-
-struct Photon {
-    float x, y, e, kx, ky, kz;
-    uint32_t step, id_mech;
-};
-
-// warp-aggregated append of at most one photon per lane; all 32 lanes call it
-template <typename R>
-__device__ __forceinline__ void warp_append(const RunDevT<R>& r, bool on, const Photon& p) {
-    unsigned mask = __ballot_sync(0xffffffffu, on);
-    if (mask == 0) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(r.tally + PE_T_N_PHOTONS, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (on) {
-        unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-        if (slot < (unsigned long long)r.capacity) {
-            float4* dst = reinterpret_cast<float4*>(r.photons + slot * 32);
-            dst[0] = make_float4(p.x, p.y, p.e, p.kx);
-            dst[1] = make_float4(p.ky, p.kz, __uint_as_float(p.step), __uint_as_float(p.id_mech));
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// one step of one particle
-// ---------------------------------------------------------------------------
-template <typename R>
-struct Particle {
-    R x, y, u[3];
-    R x_lo, y_lo;               // compensation of the float position update (0 in double)
-    R tau, tau_lo;              // optical depth; float path keeps it as the pair tau + tau_lo
-    uint32_t ev_cnt, ev_hash;   // event fingerprint (only kept when r.events != nullptr)
-};
-template <typename R>
-__device__ __forceinline__ void note_event(Particle<R>& P, uint32_t n, int mech) {
-    P.ev_cnt += mech ? 0x10000u : 1u;
-    P.ev_hash += (n + 1u) * (mech ? 0x9E3779B1u : 1u);
-}
-// optical depth arithmetic: tau -= d (compensated in float), emission test, reset
-__device__ __forceinline__ void tau_sub(Particle<double>& P, double d) { P.tau -= d; }
-__device__ __forceinline__ void tau_sub(Particle<float>& P, float d) {
-    float s = P.tau - d;
-    float bb = s - P.tau;
-    float e = (P.tau - (s - bb)) + (-d - bb);
-    P.tau = s;
-    P.tau_lo += e;
-}
-template <typename R>
-__device__ __forceinline__ bool tau_crossed(const Particle<R>& P) { return P.tau + P.tau_lo <= (R)0; }
-// rare-branch arithmetic by precision: the FP64 path in double, the FP32 path in
-// float pairs and integers (no FP64 or conversion instructions, see rare_f32.cuh)
-__device__ __forceinline__ void tau_draw(Particle<double>& P, uint4 w) {
-    P.tau = -log(uni53(w64(w.z, w.w)));
-    P.tau_lo = 0;
-}
-__device__ __forceinline__ void tau_draw(Particle<float>& P, uint4 w) {
-    P.tau = tau_draw_f32(w.z, w.w);
-    P.tau_lo = 0;
-}
-__device__ __forceinline__ double sample_delta(const TablesDev& t, double eta, uint4 w, bool& below) {
-    return sample_ncs_delta<double>(t, t.cdf64, eta, uni53(w64(w.x, w.y)), below);
-}
-__device__ __forceinline__ float sample_delta(const TablesDev& t, float eta, uint4 w, bool& below) {
-    return sample_ncs_delta_f32(t, eta, w.x, w.y, below);
-}
-__device__ __forceinline__ double sample_y(const TablesDev& t, int iz, double gamma, uint4 w) {
-    return sample_brems_y<double>(t, t.bcdf64 + (size_t)iz * t.n_E * t.n_s, gamma, uni53(w64(w.z, w.w)));
-}
-__device__ __forceinline__ float sample_y(const TablesDev& t, int iz, float gamma, uint4 w) {
-    return sample_brems_y_f32(t, iz, gamma, w.z, w.w);
-}
-__device__ __forceinline__ void fx_add_r(unsigned long long* p, double v) { fx_add(p, v); }
-__device__ __forceinline__ void fx_add_r(unsigned long long* p, float v) { fx_add_f32(p, v); }
-__device__ __forceinline__ bool brems_event(double P, uint4 w) { return below_threshold(P, w.x, w.y); }
-__device__ __forceinline__ bool brems_event(float P, uint4 w) { return below_threshold_f32(P, w.x, w.y); }
-__device__ __forceinline__ void hist_bins(double e, double kx, double ky, double inv_log_emax, int& eb, int& tb,
-                                          bool& over) {
-    eb = (int)floor((double)PE_HIST_E_BINS * log(e) * inv_log_emax);
-    over = eb >= PE_HIST_E_BINS;
-    if (over) eb = PE_HIST_E_BINS - 1;
-    if (eb < 0) eb = 0;
-    tb = (int)floor((atan2(ky, kx) + kPi) / (2.0 * kPi) * (double)PE_HIST_T_BINS);
-    if (tb < 0) tb = 0;
-    if (tb >= PE_HIST_T_BINS) tb = PE_HIST_T_BINS - 1;
-}
-__device__ __forceinline__ void hist_bins(float e, float kx, float ky, float inv_log_emax, int& eb, int& tb,
-                                          bool& over) {
-    hist_bins_f32(e, kx, ky, inv_log_emax, eb, tb, over);
-}
-
-template <typename R>
-__device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
-                                         R kx, R ky, R inv_log_emax) {
-    int eb, tb;
-    bool over;
-    hist_bins(e, kx, ky, inv_log_emax, eb, tb, over);
-    if (over) atomicAdd(tally + PE_T_N_HIST_OVER, 1ull);
-    atomicAdd(hist + mech * PE_HIST_E_BINS + eb, 1ull);
-    atomicAdd(hist + 2 * PE_HIST_E_BINS + mech * PE_HIST_T_BINS + tb, 1ull);
-}
-
-
-template <typename R>
-struct StepOut {
-    bool ncs, br;      // a stored photon of this mechanism
-    Photon pn, pb;
-};
-
-template <typename R>
-__device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
-                                         uint32_t id, uint32_t n, R nf,
-                                         Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
-                                         unsigned long long* tally) {
-    out.ncs = out.br = false;
-    const StepC<R>& c = r.c;
-    const R photon_min = tabc<R>(t).photon_min;
-    const R dt = c.dt;
-    R E[3], B[3];
-    fields<R>(r, P.x, P.x_lo, P.y, nf, E, B);
-    boris<R>(P.u, E, B, dt);
-    R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-    const R xn = P.x, yn = P.y;
-
-    if (r.enable_ncs) {
-        R eta = eta_of<R>(P.u, gamma, E, B, c.inv_ES);
-        int fl;
-        R h = h_of_eta<R>(t, h_tab, eta, fl);
-        if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
-        // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
-        tau_sub(P, c.ncs_coef * (eta / gamma) * h);
-        if (tau_crossed(P)) {
-            uint4 w = draw(r, id, n, PUR_NCS);
-            bool below;
-            R delta = sample_delta(t, eta, w, below);
-            if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
-            R ew = delta * gamma;
-            if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
-            R k[3];
-            recoil<R>(P.u, gamma, ew, k);
-            note_event<R>(P, n, 0);
-            R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            fx_add_r(tally + PE_T_E_RECOIL_NCS, gamma - gn);
-            if (ew >= photon_min) {
-                atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
-                fx_add_r(tally + PE_T_E_NCS_STORED, ew);
-                hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
-                out.ncs = true;
-                out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
-            } else {
-                atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
-                fx_add_r(tally + PE_T_E_NCS_BELOW, ew);
-            }
-            gamma = gn;
-            tau_draw(P, w);
-        }
-    }
-
-    if (r.enable_brems) {
-        bool in_slab = (xn >= c.x0 && xn <= c.x1);
-        if (r.geometry == PE_GAUSS_2D && fabs(yn) > c.yh) in_slab = false;
-        if (in_slab && gamma > (R)1 + photon_min) {
-            bool above;
-            R sig = sigma_of<R>(t, sig_tab, gamma, above);
-            if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
-            R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            R xb = c.K_br * sig * (um / gamma);
-            R Pbr = -m_expm1(-xb);
-            uint4 w = draw(r, id, n, PUR_BREMS);
-            if (brems_event(Pbr, w)) {
-                R yy = sample_y(t, r.iz, gamma, w);
-                R ew = yy * gamma;
-                R k[3];
-                recoil<R>(P.u, gamma, ew, k);
-                note_event<R>(P, n, 1);
-                R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-                fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
-                if (ew >= photon_min) {
-                    atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
-                    fx_add_r(tally + PE_T_E_BR_STORED, ew);
-                    hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
-                    out.br = true;
-                    out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n,
-                                    id | 0x80000000u};
-                } else {
-                    atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
-                    fx_add_r(tally + PE_T_E_BR_BELOW, ew);
-                }
-                gamma = gn;
-            }
-        }
-    }
-
-    advance(P.x, P.x_lo, dt * P.u[0] / gamma);
-    if (r.geometry == PE_GAUSS_2D) advance(P.y, P.y_lo, dt * P.u[1] / gamma);
-    if (r.box_enable && (P.x < c.box0 || P.x > c.box1)) {
-        P.x = (R)NAN;
-        atomicAdd(tally + PE_T_N_KILLED, 1ull);
-        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)n + 1ull);
-    }
-}
-
-__device__ __forceinline__ void load_tau(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
-    P.tau = ((const double*)r.tau)[i];
-    P.tau_lo = 0;
-}
-__device__ __forceinline__ void load_tau(const RunDevT<float>& r, int64_t i, Particle<float>& P) {
-    float2 v = ((const float2*)r.tau)[i];
-    P.tau = v.x;
-    P.tau_lo = v.y;
-}
-__device__ __forceinline__ void store_tau(const RunDevT<double>& r, int64_t i, const Particle<double>& P) {
-    ((double*)r.tau)[i] = P.tau;
-}
-__device__ __forceinline__ void store_tau(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
-    ((float2*)r.tau)[i] = make_float2(P.tau, P.tau_lo);
-}
-
-__device__ __forceinline__ void load_pos(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
-    P.x = ((const double*)r.x)[i];
-    P.y = (r.geometry == PE_GAUSS_2D) ? ((const double*)r.y)[i] : 0.0;
-    P.x_lo = 0;
-    P.y_lo = 0;
-}
-__device__ __forceinline__ void load_pos(const RunDevT<float>& r, int64_t i, Particle<float>& P) {
-    float2 v = ((const float2*)r.x)[i];
-    P.x = v.x;
-    P.x_lo = v.y;
-    if (r.geometry == PE_GAUSS_2D) {
-        float2 q = ((const float2*)r.y)[i];
-        P.y = q.x;
-        P.y_lo = q.y;
-    } else {
-        P.y = 0;
-        P.y_lo = 0;
-    }
-}
-__device__ __forceinline__ void store_pos(const RunDevT<double>& r, int64_t i, const Particle<double>& P) {
-    ((double*)r.x)[i] = P.x;
-    if (r.geometry == PE_GAUSS_2D) ((double*)r.y)[i] = P.y;
-}
-// pairs are stored exactly as held in registers, so a launch boundary changes nothing
-__device__ __forceinline__ void store_pos(const RunDevT<float>& r, int64_t i, const Particle<float>& P) {
-    ((float2*)r.x)[i] = make_float2(P.x, P.x_lo);
-    if (r.geometry == PE_GAUSS_2D) ((float2*)r.y)[i] = make_float2(P.y, P.y_lo);
-}
-
-template <typename R>
-__device__ __forceinline__ void load_particle(const RunDevT<R>& r, int64_t i, Particle<R>& P) {
-    load_pos(r, i, P);
-    P.u[0] = ((const R*)r.ux)[i];
-    P.u[1] = ((const R*)r.uy)[i];
-    P.u[2] = ((const R*)r.uz)[i];
-    load_tau(r, i, P);
-    if (r.events) {
-        unsigned long long e = r.events[i];
-        P.ev_cnt = (uint32_t)e;
-        P.ev_hash = (uint32_t)(e >> 32);
-    } else {
-        P.ev_cnt = P.ev_hash = 0;
-    }
-}
-template <typename R>
-__device__ __forceinline__ void store_particle(const RunDevT<R>& r, int64_t i, const Particle<R>& P) {
-    store_pos(r, i, P);
-    ((R*)r.ux)[i] = P.u[0];
-    ((R*)r.uy)[i] = P.u[1];
-    ((R*)r.uz)[i] = P.u[2];
-    store_tau(r, i, P);
-    if (r.events) r.events[i] = ((unsigned long long)P.ev_hash << 32) | P.ev_cnt;
-}
 
 // ---------------------------------------------------------------------------
 // plain FP64 kernel: one step, one particle per thread
@@ -326,106 +18,20 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
         active = !isnan(P.x);
     }
     if (active) {
-        step_one<double>(t, r, t.h64, t.sig64 + (size_t)r.iz * t.n_E, (uint32_t)i, (uint32_t)r.step0,
-                         (double)r.step0, P, out, r.hist, r.tally);
+        const double* sig = t.sig64 + (size_t)r.iz * t.n_E;
+        const uint32_t n = (uint32_t)r.step0;
+        switch (field_kind(r.geometry, r.polarisation)) {
+            case FK_PLANE_LP: step_one<double, FK_PLANE_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_PLANE_CP: step_one<double, FK_PLANE_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_GAUSS_LP: step_one<double, FK_GAUSS_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_GAUSS_CP: step_one<double, FK_GAUSS_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            default: step_one<double, FK_CONST>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+        }
         store_particle<double>(r, i, P);
     }
-    warp_append(r, out.ncs, out.pn);
-    warp_append(r, out.br, out.pb);
-}
-
-// ---------------------------------------------------------------------------
-// persistent kernel: grid-stride over tiles of all runs, K steps per launch
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_tally, const RunDevT<R>& r) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < PE_HIST_WORDS; k += blockDim.x) {
-        unsigned long long v = s_hist[k];
-        if (v) { atomicAdd(r.hist + k, v); s_hist[k] = 0; }
-    }
-    if (threadIdx.x < PE_T_E_NCS_STORED) {
-        unsigned long long v = s_tally[threadIdx.x];
-        if (v) { atomicAdd(r.tally + threadIdx.x, v); s_tally[threadIdx.x] = 0; }
-    } else if (threadIdx.x < PE_TALLY_WORDS && ((threadIdx.x - PE_T_E_NCS_STORED) & 1) == 0 &&
-               threadIdx.x <= PE_T_E_RECOIL_BR) {
-        int k = threadIdx.x;
-        unsigned long long lo = s_tally[k], hi = s_tally[k + 1];
-        if (lo || hi) {
-            unsigned long long old = atomicAdd(r.tally + k, lo);
-            if (old + lo < old) hi += 1;
-            if (hi) atomicAdd(r.tally + k + 1, hi);
-            s_tally[k] = 0;
-            s_tally[k + 1] = 0;
-        }
-    }
-    __syncthreads();
-}
-
-// kSingle: one run, its descriptor read straight from the kernel parameters
-// (constant-bank operands); otherwise the current run's descriptor is copied to
-// shared memory once per tile, so no step reads an indexed kernel parameter.
-template <typename R, bool kSingle>
-__global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ RunDevT<R> s_run;
-    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
-    unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
-    R* s_h = reinterpret_cast<R*>(s_tally + PE_TALLY_WORDS);
-    R* s_sig = s_h + t.n_eta;
-    const R* g_h = (sizeof(R) == 4) ? (const R*)t.h32 : (const R*)t.h64;
-    const R* g_sig = (sizeof(R) == 4) ? (const R*)t.sig32 : (const R*)t.sig64;
-
-    for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
-    for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = g_h[k];
-    for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = g_sig[k];
-    __syncthreads();
-
-    const int64_t n_tiles = b.tile_start[b.n_runs];
-    int cur = -1;
-    int run_idx = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        if (!kSingle) {
-            while (run_idx + 1 < b.n_runs && b.tile_start[run_idx + 1] <= tile) ++run_idx;
-            if (run_idx != cur) {
-                if (cur >= 0) flush_shared<R>(s_hist, s_tally, s_run);
-                constexpr int kWords = sizeof(RunDevT<R>) / 4;
-                static_assert(kWords <= 256, "run descriptor larger than one word per thread");
-                if (threadIdx.x < kWords)
-                    reinterpret_cast<uint32_t*>(&s_run)[threadIdx.x] =
-                        reinterpret_cast<const uint32_t*>(&b.runs[run_idx])[threadIdx.x];
-                __syncthreads();
-                cur = run_idx;
-            }
-        }
-        const RunDevT<R>& r = kSingle ? b.runs[0] : s_run;
-        int64_t i = (tile - b.tile_start[run_idx]) * b.tile + threadIdx.x;
-        bool active = i < r.n;
-        Particle<R> P;
-        if (active) {
-            load_particle<R>(r, i, P);
-            active = !isnan(P.x);
-        }
-        const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
-        const uint32_t n0 = (uint32_t)r.step0;
-        R nf = (R)n0;                      // step index as a float, advanced by exact +1
-        for (int s = 0; s < steps; ++s, nf += (R)1) {
-            StepOut<R> out;
-            out.ncs = out.br = false;
-            if (active) {
-                step_one<R>(t, r, s_h, sig_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
-                if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
-            }
-            warp_append(r, out.ncs, out.pn);
-            warp_append(r, out.br, out.pb);
-        }
-        if (active) store_particle<R>(r, i, P);
-        cur = kSingle ? 0 : cur;
-    }
-    if (kSingle) {
-        if (gridDim.x > 0 && n_tiles > 0) flush_shared<R>(s_hist, s_tally, b.runs[0]);
-    } else if (cur >= 0) {
-        flush_shared<R>(s_hist, s_tally, s_run);
+    if (__any_sync(0xffffffffu, out.ncs || out.br)) {
+        warp_append(r, out.ncs, out.pn);
+        warp_append(r, out.br, out.pb);
     }
 }
 
@@ -505,37 +111,6 @@ void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s) 
 int persistent_smem_bytes(const TablesDev& t, int precision) {
     size_t rs = precision == PE_F32 ? 4 : 8;
     return (int)(8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + rs * (t.n_eta + (size_t)t.n_Z * t.n_E));
-}
-
-int persistent_occupancy(int precision, int block, int smem) {
-    int occ = 0;
-    cudaError_t e = precision == PE_F32
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false>, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<double, false>, block, smem);
-    return e == cudaSuccess ? occ : 1;
-}
-
-template <typename R>
-static void launch_persistent(const TablesDev& t, const BatchDevT<R>& b, int steps, int grid, int block,
-                              cudaStream_t s, int smem) {
-    if (b.n_runs == 1) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_step_persistent<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_step_persistent<R, true><<<grid, block, smem, s>>>(t, b, steps);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_step_persistent<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_step_persistent<R, false><<<grid, block, smem, s>>>(t, b, steps);
-    }
-}
-
-void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
-                                cudaStream_t s) {
-    launch_persistent<float>(t, b, steps, grid, block, s, persistent_smem_bytes(t, PE_F32));
-}
-void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
-                                cudaStream_t s) {
-    launch_persistent<double>(t, b, steps, grid, block, s, persistent_smem_bytes(t, PE_F64));
 }
 
 }  // namespace pe

@@ -1,0 +1,44 @@
+// kernels_f32.cu -- instantiations of the persistent kernel for float.
+#include "kernels.cuh"
+
+namespace pe {
+
+template <bool kSingle, int G>
+static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block, cudaStream_t s,
+                       int smem) {
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step_persistent<float, kSingle, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_step_persistent<float, kSingle, G><<<grid, block, smem, s>>>(t, b, steps);
+}
+
+void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
+                                cudaStream_t s) {
+    int smem = persistent_smem_bytes(t, PE_F32);
+    // all runs of b share one field kind (the caller groups a batch by kind)
+    const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
+    if (b.n_runs == 1) {
+        switch (fk) {
+            case FK_PLANE_LP: launch_one<true, FK_PLANE_LP>(t, b, steps, grid, block, s, smem); break;
+            case FK_PLANE_CP: launch_one<true, FK_PLANE_CP>(t, b, steps, grid, block, s, smem); break;
+            case FK_GAUSS_LP: launch_one<true, FK_GAUSS_LP>(t, b, steps, grid, block, s, smem); break;
+            case FK_GAUSS_CP: launch_one<true, FK_GAUSS_CP>(t, b, steps, grid, block, s, smem); break;
+            default: launch_one<true, FK_CONST>(t, b, steps, grid, block, s, smem); break;
+        }
+        return;
+    }
+    switch (fk) {
+        case FK_PLANE_LP: launch_one<false, FK_PLANE_LP>(t, b, steps, grid, block, s, smem); break;
+        case FK_PLANE_CP: launch_one<false, FK_PLANE_CP>(t, b, steps, grid, block, s, smem); break;
+        case FK_GAUSS_LP: launch_one<false, FK_GAUSS_LP>(t, b, steps, grid, block, s, smem); break;
+        case FK_GAUSS_CP: launch_one<false, FK_GAUSS_CP>(t, b, steps, grid, block, s, smem); break;
+        default: launch_one<false, FK_CONST>(t, b, steps, grid, block, s, smem); break;
+    }
+}
+
+int persistent_occupancy_f32(int block, int smem) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false, FK_PLANE_LP>, block, smem);
+    return e == cudaSuccess ? occ : 1;
+}
+
+}  // namespace pe

@@ -147,12 +147,21 @@ __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
 }
 __device__ __forceinline__ void advance(double& x, double&, double d) { x += d; }
 
-template <typename R>
+// Field kind of a run, a compile-time parameter of the step so that each geometry
+// and polarisation gets its own straight-line code.
+enum { FK_PLANE_LP = 0, FK_PLANE_CP = 1, FK_GAUSS_LP = 2, FK_GAUSS_CP = 3, FK_CONST = 4 };
+__host__ __device__ __forceinline__ int field_kind(int geometry, int polarisation) {
+    if (geometry == PE_CONST) return FK_CONST;
+    int cp = polarisation == PE_CP ? 1 : 0;
+    return (geometry == PE_GAUSS_2D ? 2 : 0) + cp;
+}
+
+template <typename R, int G>
 __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R nf, R E[3], R B[3]) {
     const StepC<R>& c = r.c;
     E[0] = E[1] = E[2] = 0;
     B[0] = B[1] = B[2] = 0;
-    if (r.geometry == PE_CONST) {
+    if (G == FK_CONST) {
         for (int k = 0; k < 3; ++k) { E[k] = c.E_const[k]; B[k] = c.B_const[k]; }
         return;
     }
@@ -162,7 +171,7 @@ __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R 
     if (g == (R)0 && dg == (R)0) return;
     const R a0 = c.a0;
     R S = 1, theta = phi, inv_R = 0, inv_w2 = 0;
-    if (r.geometry == PE_GAUSS_2D) {
+    if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) {
         // paraxial 2D focus: amplitude sqrt(w0/w) exp(-y^2/w^2), curvature and Gouy phase
         const R w0 = c.w0, zr = c.zr;
         R xi = x - c.xf;
@@ -177,12 +186,12 @@ __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R 
     R ey = -a0 * S * (dg * st + g * ct);
     E[1] = ey;
     B[2] = ey;
-    if (r.geometry == PE_GAUSS_2D) E[0] = a0 * g * S * (y * inv_R * ct + (R)2 * y * inv_w2 * st);
-    if (r.polarisation == PE_CP) {
+    if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) E[0] = a0 * g * S * (y * inv_R * ct + (R)2 * y * inv_w2 * st);
+    if (G == FK_PLANE_CP || G == FK_GAUSS_CP) {
         R ez = a0 * S * (dg * ct - g * st);
         E[2] = ez;
         B[1] = -ez;
-        if (r.geometry == PE_GAUSS_2D) B[0] = a0 * g * S * ((R)2 * y * inv_w2 * ct - y * inv_R * st);
+        if (G == FK_GAUSS_CP) B[0] = a0 * g * S * ((R)2 * y * inv_w2 * ct - y * inv_R * st);
     }
 }
 
@@ -207,9 +216,13 @@ __device__ __forceinline__ void boris(R u[3], const R E[3], const R B[3], R dt) 
 // eta E_S = sqrt((gamma E + u x B)^2 - (u.E)^2), rewritten without the
 // cancellation of electrons riding a wave along x: with dB = B - x^ cross E
 // and V = (gamma - u_x) E + u x dB, the radicand is |V|^2 + 2 V_x (u.E).
-template <typename R>
+// For the plane wave (B = x^ cross E, E_x = 0) dB and V_x vanish and the radicand is
+// exactly (gamma - u_x)^2 |E|^2.
+template <typename R, int G>
 __device__ __forceinline__ R eta_of(const R u[3], R gamma, const R E[3], const R B[3], R inv_ES) {
     R gm = (u[0] > (R)0) ? ((R)1 + u[1] * u[1] + u[2] * u[2]) / (gamma + u[0]) : gamma - u[0];
+    if (G == FK_PLANE_LP) return gm * fabs(E[1]) * inv_ES;
+    if (G == FK_PLANE_CP) return gm * m_sqrt(E[1] * E[1] + E[2] * E[2]) * inv_ES;
     R d0 = B[0], d1 = B[1] + E[2], d2 = B[2] - E[1];
     R V0 = gm * E[0] + (u[1] * d2 - u[2] * d1);
     R V1 = gm * E[1] + (u[2] * d0 - u[0] * d2);

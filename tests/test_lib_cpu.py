@@ -59,7 +59,7 @@ def test_product_never_imports_oracle():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
-                assert not re.search(r"^\s*(import|from)\s+oracle\b|oracle/|liboracle|or_[a-z_]+\(", txt, re.M), f
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|oracle/|liboracle|\bor_[a-z_]+\(", txt, re.M), f
 
 
 def test_compute_fails_loudly_without_gpu(libpath):
