@@ -43,6 +43,10 @@ BYTES_PER_PSTEP_1D = 56
 BYTES_PER_PSTEP_2D = 72
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per electron and launch of the dominant kernel, from the ncu
+# capture in profiles/k_step_persistent_f32__1d-au-a270-mj-2e5x400__full.md (5.88 MB for
+# 2e5 electrons); None once the kernel changes after that capture.
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.4
 
 
 def peaks():
@@ -286,8 +290,9 @@ def main():
     sm_clock = (res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
     fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
     ach = FLOP_PER_PSTEP_1D * pst / (ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC_BYTES_PER_ELECTRON * n if NCU_TRAFFIC_BYTES_PER_ELECTRON else None
     res["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                       "traffic": None, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                       "traffic": traffic, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                        "flop_per_particle_step": FLOP_PER_PSTEP_1D}
 
     if rank == 0 and not args.skip_extras:
