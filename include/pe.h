@@ -194,6 +194,20 @@ pe_status pe_init_particles(const pe_tables* tables, const pe_run_params* params
 pe_status pe_step(pe_run* const* runs, int n_runs, int64_t n_steps);
 pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg);
 
+/* A CUDA graph of the batched persistent launches that advance runs by
+ * steps_per_replay steps (one kernel node per launch: per field kind present
+ * and per steps_per_launch chunk).  pe_graph_launch replays it on the first
+ * run's stream, first setting each node's step index to where the runs are,
+ * so every replay continues the runs; results are identical to pe_step_ex
+ * with the same configuration.  All runs must share tables and precision
+ * (PE_F32 or PE_F64); the runs must not be stepped by other calls while the
+ * graph exists.  The graph refers to the runs, which must outlive it. */
+typedef struct pe_graph pe_graph;
+pe_status pe_graph_create(pe_run* const* runs, int n_runs, int64_t steps_per_replay, const pe_launch_config* cfg,
+                          pe_graph** out);
+pe_status pe_graph_launch(pe_graph* graph);
+pe_status pe_graph_destroy(pe_graph* graph);
+
 /* Synchronise the run's stream and copy tally, histograms and counters to
  * *out.  Returns PE_ERR_BUFFER_FULL (after filling *out) if more photons
  * were produced than the buffer holds; the counts stay exact.               */

@@ -33,7 +33,8 @@ T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4
 PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
                          ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
 EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
-            "pe_step_ex", "pe_tally", "pe_destroy", "pe_a0_from_intensity", "pe_launch_count", "pe_last_error"]
+            "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch", "pe_graph_destroy",
+            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error"]
 
 
 class PeError(RuntimeError):
@@ -103,13 +104,17 @@ def lib():
             L.pe_step.argtypes = [C.POINTER(vp), C.c_int, C.c_int64]
             L.pe_step_ex.argtypes = [C.POINTER(vp), C.c_int, C.c_int64, C.POINTER(LaunchConfig)]
             L.pe_tally.argtypes = [vp, C.POINTER(TallyOut)]
+            L.pe_graph_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int64, C.POINTER(LaunchConfig), C.POINTER(vp)]
+            L.pe_graph_launch.argtypes = [vp]
+            L.pe_graph_destroy.argtypes = [vp]
             L.pe_destroy.argtypes = [vp]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
             L.pe_last_error.restype = C.c_char_p
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
-                         "pe_step", "pe_step_ex", "pe_tally", "pe_destroy"):
+                         "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
+                         "pe_graph_destroy"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -185,6 +190,23 @@ def pe_step_ex(runs, n_steps: int, block: int = 0, ctas_per_sm: int = 0, steps_p
     _check(lib().pe_step_ex(arr, len(runs), n_steps, C.byref(cfg)))
 
 
+def pe_graph_create(runs, steps_per_replay: int, block: int = 0, ctas_per_sm: int = 0,
+                    steps_per_launch: int = 0) -> int:
+    arr = (C.c_void_p * len(runs))(*runs)
+    cfg = LaunchConfig(block, ctas_per_sm, steps_per_launch)
+    h = C.c_void_p()
+    _check(lib().pe_graph_create(arr, len(runs), steps_per_replay, C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def pe_graph_launch(graph: int):
+    _check(lib().pe_graph_launch(graph))
+
+
+def pe_graph_destroy(graph: int):
+    _check(lib().pe_graph_destroy(graph))
+
+
 def pe_tally(run: int) -> TallyOut:
     out = TallyOut()
     st = _check(lib().pe_tally(run, C.byref(out)), allow=(PE_ERR_BUFFER_FULL,))
@@ -236,6 +258,28 @@ class Run:
                     self.hist.data_ptr(), self.tally.data_ptr(),
                     self.events.data_ptr() if events else None)
         self.handle = pe_init_particles(tables, params, self.n, b, self.stream.cuda_stream)
+
+    def rebind(self, tables: int, precision_params: RunParams | None = None):
+        """Replace the run handle by a fresh one on the same buffers (caller-provided state,
+        optical depths redrawn, step index 0, tallies cleared)."""
+        p = precision_params if precision_params is not None else self.params
+        q = RunParams.from_buffer_copy(p)
+        q.init_dist = PE_CALLER
+        b = Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),
+                    self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
+                    self.hist.data_ptr(), self.tally.data_ptr(),
+                    self.events.data_ptr() if self.events is not None else None)
+        old = self.handle
+        self.handle = pe_init_particles(tables, q, self.n, b, self.stream.cuda_stream)
+        if old:
+            pe_destroy(old)
+
+    def snapshot(self):
+        return [t.clone() for t in (self.x, self.y, self.ux, self.uy, self.uz, self.tau)]
+
+    def restore(self, snap):
+        for dst, src in zip((self.x, self.y, self.ux, self.uy, self.uz, self.tau), snap):
+            dst.copy_(src)
 
     def state(self) -> np.ndarray:
         """Host copy (n x 6, float64): x, y, ux, uy, uz, tau.

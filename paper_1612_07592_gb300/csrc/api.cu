@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -271,20 +273,110 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     return PE_OK;
 }
 
-extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg) {
+// One persistent launch of a step call: the runs of one field kind, one chunk of
+// at most steps_per_launch steps starting `offset` steps into the call.
+struct PlanLaunch {
+    int prec = PE_F32, grid = 0, block = 0, smem = 0, steps = 0;
+    int64_t offset = 0;
+    std::vector<int> idx;                       // positions in the runs array
+    std::unique_ptr<BatchDevT<float>> bf;
+    std::unique_ptr<BatchDevT<double>> bd;
+};
+struct Plan {
+    std::vector<PlanLaunch> launches;
+};
+
+static void set_step0(PlanLaunch& L, pe_run* const* runs, int64_t base_extra) {
+    for (size_t k = 0; k < L.idx.size(); ++k) {
+        int64_t s0 = runs[L.idx[k]]->steps_done + base_extra + L.offset;
+        if (L.prec == PE_F32) L.bf->runs[k].step0 = s0; else L.bd->runs[k].step0 = s0;
+    }
+}
+
+// persistent launches (grouped by field kind, chunked by steps_per_launch)
+static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg,
+                            Plan& plan) {
+    const pe_tables* t = runs[0]->tables;
+    int prec = runs[0]->params.precision;
+    int block = (cfg && cfg->block > 0) ? cfg->block : 256;
+    if (block % 32 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be a multiple of 32, <= 256");
+    int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 2048);
+    if (K < 1) K = 1;
+    int dev;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem = persistent_smem_bytes(t->dev, prec);
+    if (smem > 200 * 1024)
+        return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
+    int per_sm = (cfg && cfg->ctas_per_sm > 0)
+                     ? cfg->ctas_per_sm
+                     : (prec == PE_F32 ? persistent_occupancy_f32(block, smem) : persistent_occupancy_f64(block, smem));
+    if (per_sm < 1) per_sm = 1;
+    for (int fk = 0; fk <= 4; ++fk) {
+        std::vector<int> idx;
+        for (int k = 0; k < n_runs; ++k)
+            if (field_kind(runs[k]->dev.geometry, runs[k]->dev.polarisation) == fk) idx.push_back(k);
+        if (idx.empty()) continue;
+        int m = (int)idx.size();
+        int64_t tile_start[PE_MAX_BATCH + 1];
+        tile_start[0] = 0;
+        for (int k = 0; k < m; ++k) tile_start[k + 1] = tile_start[k] + (runs[idx[k]]->dev.n + block - 1) / block;
+        int64_t n_tiles = tile_start[m];
+        if (n_tiles == 0) continue;
+        int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
+        for (int64_t done = 0; done < n_steps; done += K) {
+            PlanLaunch L;
+            L.prec = prec;
+            L.grid = grid;
+            L.block = block;
+            L.smem = smem;
+            L.steps = (int)std::min<int64_t>(K, n_steps - done);
+            L.offset = done;
+            L.idx = idx;
+            if (prec == PE_F32) {
+                L.bf.reset(new BatchDevT<float>());
+                std::memset(L.bf.get(), 0, sizeof(BatchDevT<float>));
+                L.bf->n_runs = m;
+                L.bf->tile = block;
+                for (int k = 0; k <= m; ++k) L.bf->tile_start[k] = tile_start[k];
+                for (int k = 0; k < m; ++k) L.bf->runs[k] = to_float(runs[idx[k]]->dev);
+            } else {
+                L.bd.reset(new BatchDevT<double>());
+                std::memset(L.bd.get(), 0, sizeof(BatchDevT<double>));
+                L.bd->n_runs = m;
+                L.bd->tile = block;
+                for (int k = 0; k <= m; ++k) L.bd->tile_start[k] = tile_start[k];
+                for (int k = 0; k < m; ++k) L.bd->runs[k] = runs[idx[k]]->dev;
+            }
+            plan.launches.push_back(std::move(L));
+        }
+    }
+    return PE_OK;
+}
+
+static pe_status check_batch(pe_run* const* runs, int n_runs, int64_t n_steps) {
     if (!runs || n_runs < 1 || n_runs > PE_MAX_BATCH) return fail(PE_ERR_ARG, "pe_step: need 1..64 runs");
     if (n_steps < 0) return fail(PE_ERR_ARG, "pe_step: n_steps < 0");
     for (int k = 0; k < n_runs; ++k)
         if (!runs[k]) return fail(PE_ERR_ARG, "pe_step: null run");
-    const pe_tables* t = runs[0]->tables;
-    int prec = runs[0]->params.precision;
     for (int k = 1; k < n_runs; ++k) {
-        if (runs[k]->tables != t) return fail(PE_ERR_STATE, "pe_step: runs of a batch must share one table set");
-        if (runs[k]->params.precision != prec) return fail(PE_ERR_STATE, "pe_step: runs of a batch must share precision");
+        if (runs[k]->tables != runs[0]->tables)
+            return fail(PE_ERR_STATE, "pe_step: runs of a batch must share one table set");
+        if (runs[k]->params.precision != runs[0]->params.precision)
+            return fail(PE_ERR_STATE, "pe_step: runs of a batch must share precision");
     }
     for (int k = 0; k < n_runs; ++k)
         if (runs[k]->steps_done + n_steps >= (int64_t(1) << 32))
             return fail(PE_ERR_ARG, "pe_step: step index would exceed 2^32");
+    return PE_OK;
+}
+
+extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg) {
+    pe_status st0 = check_batch(runs, n_runs, n_steps);
+    if (st0 != PE_OK) return st0;
+    const pe_tables* t = runs[0]->tables;
+    int prec = runs[0]->params.precision;
     if (n_steps == 0) return PE_OK;
     cudaStream_t s = runs[0]->stream;
 
@@ -302,58 +394,17 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
         return PE_OK;
     }
 
-    int block = (cfg && cfg->block > 0) ? cfg->block : 256;
-    if (block % 32 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be a multiple of 32, <= 256");
-    int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 2048);
-    int dev;
-    cudaGetDevice(&dev);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int smem = persistent_smem_bytes(t->dev, prec);
-    if (smem > 200 * 1024)
-        return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
-    int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : (prec == PE_F32 ? persistent_occupancy_f32(block, smem) : persistent_occupancy_f64(block, smem));
-    if (per_sm < 1) per_sm = 1;
-    // one launch per field kind present in the batch (each kernel is specialised on it)
-    for (int fk = 0; fk <= 4; ++fk) {
-        int idx[PE_MAX_BATCH];
-        int m = 0;
-        for (int k = 0; k < n_runs; ++k)
-            if (field_kind(runs[k]->dev.geometry, runs[k]->dev.polarisation) == fk) idx[m++] = k;
-        if (m == 0) continue;
-        int64_t tile_start[PE_MAX_BATCH + 1];
-        tile_start[0] = 0;
-        for (int k = 0; k < m; ++k) tile_start[k + 1] = tile_start[k] + (runs[idx[k]]->dev.n + block - 1) / block;
-        int64_t n_tiles = tile_start[m];
-        if (n_tiles == 0) continue;
-        int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
-        if (prec == PE_F32) {
-            BatchDevT<float> b;   // host staging; passed by value to the kernel
-            std::memset(&b, 0, sizeof(b));
-            b.n_runs = m;
-            b.tile = block;
-            for (int k = 0; k <= m; ++k) b.tile_start[k] = tile_start[k];
-            for (int k = 0; k < m; ++k) b.runs[k] = to_float(runs[idx[k]]->dev);
-            for (int64_t done = 0; done < n_steps; done += K) {
-                int k_now = (int)std::min<int64_t>(K, n_steps - done);
-                for (int k = 0; k < m; ++k) b.runs[k].step0 = runs[idx[k]]->steps_done + done;
-                launch_step_persistent_f32(t->dev, b, k_now, grid, block, s);
-                g_launches++;
-            }
-        } else {
-            BatchDevT<double> b;
-            std::memset(&b, 0, sizeof(b));
-            b.n_runs = m;
-            b.tile = block;
-            for (int k = 0; k <= m; ++k) b.tile_start[k] = tile_start[k];
-            for (int k = 0; k < m; ++k) b.runs[k] = runs[idx[k]]->dev;
-            for (int64_t done = 0; done < n_steps; done += K) {
-                int k_now = (int)std::min<int64_t>(K, n_steps - done);
-                for (int k = 0; k < m; ++k) b.runs[k].step0 = runs[idx[k]]->steps_done + done;
-                launch_step_persistent_f64(t->dev, b, k_now, grid, block, s);
-                g_launches++;
-            }
-        }
+    Plan plan;
+    pe_status st = build_plan(runs, n_runs, n_steps, cfg, plan);
+    (void)prec;
+    if (st != PE_OK) return st;
+    for (PlanLaunch& L : plan.launches) {
+        set_step0(L, runs, 0);
+        if (L.prec == PE_F32)
+            launch_step_persistent_f32(t->dev, *L.bf, L.steps, L.grid, L.block, s);
+        else
+            launch_step_persistent_f64(t->dev, *L.bd, L.steps, L.grid, L.block, s);
+        g_launches++;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pe_step: k_step_persistent");
@@ -396,5 +447,93 @@ extern "C" pe_status pe_tally(pe_run* r, pe_tally_out* out) {
 extern "C" pe_status pe_destroy(pe_run* r) {
     if (!r) return fail(PE_ERR_ARG, "pe_destroy: null");
     delete r;
+    return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of the batched persistent launches
+// ---------------------------------------------------------------------------
+struct pe_graph {
+    std::vector<pe_run*> runs;
+    int64_t steps = 0;
+    Plan plan;
+    std::vector<cudaGraphNode_t> nodes;
+    std::vector<cudaKernelNodeParams> params;
+    std::vector<std::array<void*, 3>> args;
+    std::vector<int> step_args;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+extern "C" pe_status pe_graph_create(pe_run* const* runs, int n_runs, int64_t steps_per_replay,
+                                     const pe_launch_config* cfg, pe_graph** out) {
+    if (!out) return fail(PE_ERR_ARG, "pe_graph_create: null out");
+    *out = nullptr;
+    pe_status st = check_batch(runs, n_runs, steps_per_replay);
+    if (st != PE_OK) return st;
+    if (steps_per_replay < 1) return fail(PE_ERR_ARG, "pe_graph_create: steps_per_replay must be >= 1");
+    pe_graph* g = new pe_graph();
+    g->runs.assign(runs, runs + n_runs);
+    g->steps = steps_per_replay;
+    g->stream = runs[0]->stream;
+    st = build_plan(runs, n_runs, steps_per_replay, cfg, g->plan);
+    if (st != PE_OK) { delete g; return st; }
+    const pe_tables* t = runs[0]->tables;
+    cudaError_t e = cudaGraphCreate(&g->graph, 0);
+    size_t nl = g->plan.launches.size();
+    g->nodes.resize(nl);
+    g->params.resize(nl);
+    g->args.resize(nl);
+    g->step_args.resize(nl);
+    for (size_t k = 0; k < nl && e == cudaSuccess; ++k) {
+        PlanLaunch& L = g->plan.launches[k];
+        set_step0(L, runs, 0);
+        g->step_args[k] = L.steps;
+        void* batch = L.prec == PE_F32 ? (void*)L.bf.get() : (void*)L.bd.get();
+        g->args[k] = {(void*)&t->dev, batch, (void*)&g->step_args[k]};
+        cudaKernelNodeParams& p = g->params[k];
+        std::memset(&p, 0, sizeof(p));
+        p.func = const_cast<void*>(L.prec == PE_F32 ? persistent_kernel_f32(*L.bf, L.smem)
+                                                    : persistent_kernel_f64(*L.bd, L.smem));
+        p.gridDim = dim3(L.grid);
+        p.blockDim = dim3(L.block);
+        p.sharedMemBytes = L.smem;
+        p.kernelParams = g->args[k].data();
+        e = cudaGraphAddKernelNode(&g->nodes[k], g->graph, k ? &g->nodes[k - 1] : nullptr, k ? 1 : 0, &p);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "pe_graph_create");
+    }
+    *out = g;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_graph_launch(pe_graph* g) {
+    if (!g) return fail(PE_ERR_ARG, "pe_graph_launch: null");
+    for (pe_run* r : g->runs)
+        if (r->steps_done + g->steps >= (int64_t(1) << 32))
+            return fail(PE_ERR_ARG, "pe_graph_launch: step index would exceed 2^32");
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < g->plan.launches.size() && e == cudaSuccess; ++k) {
+        set_step0(g->plan.launches[k], g->runs.data(), 0);
+        e = cudaGraphExecKernelNodeSetParams(g->exec, g->nodes[k], &g->params[k]);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_graph_launch");
+    g_launches += (int64_t)g->plan.launches.size();
+    for (pe_run* r : g->runs) r->steps_done += g->steps;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_graph_destroy(pe_graph* g) {
+    if (!g) return fail(PE_ERR_ARG, "pe_graph_destroy: null");
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
     return PE_OK;
 }

@@ -35,6 +35,31 @@ void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, i
     }
 }
 
+// the kernel a launch of these runs uses (for graph nodes); sets the shared-memory attribute
+const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem) {
+    const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
+    const void* f = nullptr;
+    if (b.n_runs == 1) {
+        switch (fk) {
+            case FK_PLANE_LP: f = (const void*)k_step_persistent<float, true, FK_PLANE_LP>; break;
+            case FK_PLANE_CP: f = (const void*)k_step_persistent<float, true, FK_PLANE_CP>; break;
+            case FK_GAUSS_LP: f = (const void*)k_step_persistent<float, true, FK_GAUSS_LP>; break;
+            case FK_GAUSS_CP: f = (const void*)k_step_persistent<float, true, FK_GAUSS_CP>; break;
+            default: f = (const void*)k_step_persistent<float, true, FK_CONST>; break;
+        }
+    } else {
+        switch (fk) {
+            case FK_PLANE_LP: f = (const void*)k_step_persistent<float, false, FK_PLANE_LP>; break;
+            case FK_PLANE_CP: f = (const void*)k_step_persistent<float, false, FK_PLANE_CP>; break;
+            case FK_GAUSS_LP: f = (const void*)k_step_persistent<float, false, FK_GAUSS_LP>; break;
+            case FK_GAUSS_CP: f = (const void*)k_step_persistent<float, false, FK_GAUSS_CP>; break;
+            default: f = (const void*)k_step_persistent<float, false, FK_CONST>; break;
+        }
+    }
+    if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return f;
+}
+
 int persistent_occupancy_f32(int block, int smem) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false, FK_PLANE_LP>, block, smem);

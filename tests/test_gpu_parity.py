@@ -389,3 +389,82 @@ def test_config2_full_size_sampled():
     assert np.quantile(err, 0.95) < F32_ILL_P95
     assert err.max() < F32_ILL_MAX
     r.close()
+
+
+# ------------------------------------------------------- graph, autotune ----
+def test_graph_equals_direct_steps():
+    Z = (13.0, 79.0)
+    lt, _ = tables(_tp(48), Z)
+    runs = [W.base_run(a0=270.0, init_dist=1, seed=1, run_id=0, **W.AU),
+            W.base_run(a0=27.0, seed=2, run_id=1),
+            W.base_run(a0=855.0, polarisation=1, geometry=1, slab_thick_m=2e-6, seed=3, run_id=2, **W.AU)]
+    sizes = [700, 300, 400]
+    direct = [pe.Run(lt, pe.run_params(precision=pe.PE_F32, **rk), n, events=True) for rk, n in zip(runs, sizes)]
+    pe.pe_step_ex([d.handle for d in direct], 400, block=128, steps_per_launch=50)
+    graphed = [pe.Run(lt, pe.run_params(precision=pe.PE_F32, **rk), n, events=True) for rk, n in zip(runs, sizes)]
+    g = pe.pe_graph_create([r.handle for r in graphed], 100, block=128, steps_per_launch=50)
+    for _ in range(4):
+        pe.pe_graph_launch(g)
+    pe.pe_graph_destroy(g)
+    for a, b in zip(direct, graphed):
+        np.testing.assert_array_equal(a.state(), b.state())
+        np.testing.assert_array_equal(a.event_words(), b.event_words())
+        ta, tb = a.tally_out(), b.tally_out()
+        assert bytes(ta.tally) == bytes(tb.tally) and bytes(ta.hist) == bytes(tb.hist)
+        assert tb.steps_done == 400
+
+
+def test_autotune_picks_a_shape():
+    from paper_1612_07592_gb300 import autotune
+    lt, _ = tables(_tp(48), (13.0, 79.0))
+    rs = [pe.Run(lt, pe.run_params(precision=pe.PE_F32, **W.base_run(a0=270.0, init_dist=1, seed=9, **W.AU)), 5000)]
+    space = dict(block=(128, 256), ctas_per_sm=(2, 4), steps_per_launch=(50, 200))
+    cfg, res = autotune.tune(lt, rs, 200, space=space, use_cache=False)
+    assert len(res) == 8 and all(ms > 0 for _, ms in res)
+    assert cfg in [c for c, _ in res]
+    # the runs are restored: stepping them now equals a fresh run
+    fresh = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **W.base_run(a0=270.0, init_dist=1, seed=9, **W.AU)), 5000)
+    pe.pe_step([rs[0].handle], 100)
+    pe.pe_step([fresh.handle], 100)
+    np.testing.assert_array_equal(rs[0].state(), fresh.state())
+
+
+# ----------------------------------------------------------------- serving ----
+def test_serving_alone_equals_mix():
+    from paper_1612_07592_gb300.serve import Request, Server
+    Z = (13.0, 79.0)
+    lt, _ = tables(_tp(48), Z)
+    kinds = [W.base_run(a0=270.0, init_dist=1, seed=11, run_id=0, **W.AU),
+             W.base_run(a0=100.0, seed=12, run_id=1),
+             W.base_run(a0=855.0, polarisation=1, geometry=1, slab_thick_m=2e-6, seed=13, run_id=2, **W.AU),
+             W.base_run(a0=60.0, seed=14, run_id=3, **W.AU)]
+    sizes, steps = [900, 300, 500, 257], [700, 450, 333, 600]
+    alone = []
+    for rk, n, s in zip(kinds, sizes, steps):
+        r = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **rk), n, capacity=1 << 16, events=True)
+        pe.pe_step([r.handle], s)
+        alone.append((r.state(), r.event_words(), bytes(r.tally_out().tally), bytes(r.tally_out().hist)))
+        r.close()
+    reqs = [Request(arrival_s=0.01 * k, n=n, steps=s, run=rk, capacity=1 << 16)
+            for k, (rk, n, s) in enumerate(zip(kinds, sizes, steps))]
+    srv = Server(lt, steps_per_iteration=128, keep_results=True)
+    stats = srv.run_trace(reqs, realtime=False)
+    assert stats.summary()["requests"] == 4 and stats.max_resident >= 2
+    for q, (st, ev, tal, hist) in zip(reqs, alone):
+        np.testing.assert_array_equal(q.state, st)
+        np.testing.assert_array_equal(q.events, ev)
+        assert bytes(q.tally.tally) == tal and bytes(q.tally.hist) == hist
+
+
+def test_serving_admits_by_memory():
+    from paper_1612_07592_gb300.serve import Request, Server
+    lt, _ = tables(_tp(33), (13.0, 79.0))
+    reqs = [Request(arrival_s=0.0, n=1000, steps=200, run=W.base_run(a0=50.0, seed=k, run_id=k)) for k in range(5)]
+    need = Server.bytes_needed(reqs[0])
+    budget = 2 * need + (1 << 20) + 1                    # room for two requests above the reserve
+    srv = Server(lt, steps_per_iteration=100, memory_reserve_bytes=1 << 20,
+                 mem_get_info=lambda: (budget - srv.resident_bytes, 1 << 40))
+    stats = srv.run_trace(reqs, realtime=False)
+    s = stats.summary()
+    assert s["requests"] == 5 and stats.max_resident == 2
+    assert s["particle_steps"] == 5 * 1000 * 200
