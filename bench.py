@@ -299,6 +299,9 @@ def main():
         res["roofline_hbm"] = hbm_form(pe, tables, cfg, stream, hbm_peak_gbs(pk), pk_kind)
         res["fp64_plain"] = fp64_plain(pe, tables, cfg, stream, flush)
         res["e2e"] = e2e(pe, tables, cfg, stream)
+        res["workloads"] = {"batch64_graph": batch64(pe, stream, flush),
+                            "gauss2d_cp_a855_3e7x2000": gauss2d(pe, stream, flush),
+                            "serving_poisson50hz": serving(pe, stream)}
     if rank == 0 and not args.skip_cpu_baseline:
         threads = os.cpu_count() or 1
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
@@ -356,6 +359,103 @@ def fp64_plain(pe, tables, cfg, stream, flush):
     r.close()
     return {"value": out.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms,
             "kernel": "k_step_plain (fp64, one launch per step)", "steps": 1, "warmup": 0}
+
+
+def batch64(pe, stream, flush):
+    """64 runs of uneven size (Al/Au, 1e21..1e24 W/cm^2, 1000 steps) advanced together by a CUDA
+    graph of batched persistent launches, launch shape chosen by the autotuner."""
+    import torch
+    from paper_1612_07592_gb300 import autotune
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.config4()
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    runs = []
+    with torch.cuda.stream(stream):
+        for rk, n in zip(c["runs"], c["n"]):
+            runs.append(pe.Run(tables, pe.run_params(precision=pe.PE_F32, **rk), int(n),
+                               capacity=int(min(2 * n, 1 << 23)), stream=stream))
+    stream.synchronize()
+    cfg, trials = autotune.tune(tables, runs, 200, space=dict(block=(128, 256), ctas_per_sm=(2, 3, 4),
+                                                                 steps_per_launch=(200,)), use_cache=False)
+    cfg = dict(cfg, steps_per_launch=500)
+    snaps = [r.snapshot() for r in runs]
+    times = []
+    for k in range(3):
+        with torch.cuda.stream(stream):
+            for r, sn in zip(runs, snaps):
+                r.restore(sn)
+            flush.fill_(1.0)
+        for r in runs:
+            r.rebind(tables)
+        g = pe.pe_graph_create([r.handle for r in runs], c["steps"], **cfg)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.pe_graph_launch(g)
+        e1.record(stream)
+        e1.synchronize()
+        pe.pe_graph_destroy(g)
+        if k:
+            times.append(e0.elapsed_time(e1))
+    pst = sum(r.tally_out().live_particle_steps for r in runs)
+    for r in runs:
+        r.close()
+    pe.pe_destroy_tables(tables)
+    ms = float(np.mean(times))
+    return {"value": pst / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "runs": 64, "electrons": int(c["n"].sum()),
+            "steps": c["steps"], "launch": cfg, "autotune_trials": len(trials)}
+
+
+def gauss2d(pe, stream, flush):
+    """2D paraxial Gaussian focus, CP a0 = 855 per component, Au 2 um slab: 3e7 electrons at rest,
+    2000 steps, photon buffer 2e8 records; FP32 path, state in registers per launch."""
+    import torch
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.config3()
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **c["run"]), c["n"], capacity=c["capacity"],
+                   stream=stream)
+    stream.synchronize()
+    snap = r.snapshot()
+    times = []
+    for k in range(3):
+        with torch.cuda.stream(stream):
+            r.restore(snap)
+            flush.fill_(1.0)
+        r.rebind(tables)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.pe_step([r.handle], c["steps"])
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            times.append(e0.elapsed_time(e1))
+    out = r.tally_out()
+    ms = float(np.mean(times))
+    res = {"value": out.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": c["n"],
+           "steps": c["steps"], "photons": int(out.tally[pe.T["N_PHOTONS"]]),
+           "ncs_stored": int(out.tally[pe.T["N_NCS_STORED"]]), "brems_stored": int(out.tally[pe.T["N_BR_STORED"]])}
+    r.close()
+    pe.pe_destroy_tables(tables)
+    return res
+
+
+def serving(pe, stream, n_requests=60):
+    """Continuous batching of a Poisson trace (50 requests/s; geometry of the 2D case, intensity
+    and target drawn per request, 1e4..1e7 electrons, 500..4000 steps), first n_requests arrivals
+    served in real time: p50/p99 latency (arrival to results on the host) and throughput."""
+    from paper_1612_07592_gb300 import workloads as W
+    from paper_1612_07592_gb300.serve import Server, requests_from_workload
+    c = W.config5(50.0, n_requests)
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    reqs = requests_from_workload(c)
+    srv = Server(tables, steps_per_iteration=500, stream=stream)
+    st = srv.run_trace(reqs, realtime=True).summary()
+    pe.pe_destroy_tables(tables)
+    st.update({"unit": UNIT, "offered_rate_hz": 50.0, "trace": f"first {n_requests} of config-5 Poisson arrivals"})
+    return st
 
 
 def e2e(pe, tables, cfg, stream):
