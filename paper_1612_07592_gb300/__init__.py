@@ -16,7 +16,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpe.so")
+# PE_LIB_PATH selects another build of the same library (e.g. a variant compiled with other flags)
+LIB_PATH = os.environ.get("PE_LIB_PATH") or os.path.join(HERE, "libpe.so")
 
 PE_OK, PE_ERR_ARG, PE_ERR_CUDA, PE_ERR_NOMEM, PE_ERR_BUFFER_FULL, PE_ERR_TABLE_RANGE, PE_ERR_TIMEOUT, PE_ERR_STATE = range(8)
 PE_LP_Y, PE_CP = 0, 1

@@ -23,17 +23,22 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, lib: str | None = None, out_dir: str | None = None,
+          defines: tuple = ()) -> str:
+    """Compile the sources into `lib` (default: libpe.so beside the package).  `defines`
+    are extra -D macros (e.g. PE_MIN_CTAS=3) for variant builds."""
+    LIB_ = lib or LIB
+    OUT = out_dir or OUT_DIR
+    os.makedirs(OUT, exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "pe.h")]
     newest = max(os.path.getmtime(p) for p in deps)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(LIB_) and os.path.getmtime(LIB_) >= newest:
+        return LIB_
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, src + ".o")
-        extra = KERNEL_FLAGS if src.startswith("kernels") else []
+        obj = os.path.join(OUT, src + ".o")
+        extra = (KERNEL_FLAGS if src.startswith("kernels") else []) + ["-D" + d for d in defines]
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, *FLAGS, "-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj] + ARCH
@@ -44,10 +49,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = LIB_ + f".{os.getpid()}.tmp"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_)
+    return LIB_
 
 
 if __name__ == "__main__":

@@ -368,8 +368,11 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 // straight from the kernel parameters (constant-bank operands); otherwise the
 // current run's descriptor is copied to shared memory once per tile, so no step
 // reads an indexed kernel parameter.
+#ifndef PE_MIN_CTAS
+#define PE_MIN_CTAS 4   // resident CTAs of 256 threads per SM the register budget is sized for
+#endif
 template <typename R, bool kSingle, int G>
-__global__ void __launch_bounds__(256, 4) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
+__global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<R> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);

@@ -53,6 +53,26 @@ __device__ __forceinline__ void m_sincos(float v, float* s_out, float* c_out) {
     *c_out = ((q + 1) & 2) ? -b : b;
 }
 __device__ __forceinline__ void m_sincos(double v, double* s, double* c) { sincos(v, s, c); }
+
+// sin and cos of 0 <= v <= pi/2 (the envelope ramps) by their Taylor series about
+// pi/4 in the offset d = v - pi/4, |d| <= pi/4: no range reduction needed
+__device__ __forceinline__ void ramp_sincos(float v, float* s_out, float* c_out) {
+    float d = v - 0.785398163397448310f;
+    float d2 = d * d;
+    float sp = fmaf(d2, 2.75573192e-6f, -1.98412698e-4f);
+    sp = fmaf(d2, sp, 8.33333333e-3f);
+    sp = fmaf(d2, sp, -1.66666667e-1f);
+    float sd = fmaf(d * d2, sp, d);                       // sin d
+    float cp = fmaf(d2, -2.75573192e-7f, 2.48015873e-5f);
+    cp = fmaf(d2, cp, -1.38888889e-3f);
+    cp = fmaf(d2, cp, 4.16666667e-2f);
+    cp = fmaf(d2, cp, -0.5f);
+    float cd = fmaf(d2, cp, 1.0f);                        // cos d
+    const float r = 0.707106781186547524f;                // sin(pi/4) = cos(pi/4)
+    *s_out = r * (cd + sd);
+    *c_out = r * (cd - sd);
+}
+__device__ __forceinline__ void ramp_sincos(double v, double* s, double* c) { sincos(v, s, c); }
 __device__ __forceinline__ float m_atan2(float a, float b) { return atan2f(a, b); }
 __device__ __forceinline__ double m_atan2(double a, double b) { return atan2(a, b); }
 __device__ __forceinline__ float m_floor(float v) { return floorf(v); }
@@ -113,14 +133,14 @@ __device__ __forceinline__ void envelope(const StepC<R>& c, R phi, R& g, R& dg) 
     if (!(phi > (R)0) || phi >= (R)2 * pr + pf) { g = 0; dg = 0; return; }
     if (phi < pr) {
         R s, cc;
-        m_sincos(k * phi, &s, &cc);
+        ramp_sincos(k * phi, &s, &cc);
         g = s * s;
         dg = k * (R)2 * s * cc;
         return;
     }
     if (phi <= pr + pf) { g = 1; dg = 0; return; }
     R s, cc;
-    m_sincos(k * (phi - pr - pf), &s, &cc);
+    ramp_sincos(k * (phi - pr - pf), &s, &cc);
     g = cc * cc;
     dg = -k * (R)2 * s * cc;
 }
