@@ -146,7 +146,8 @@ typedef struct {
 /* Launch shape of the persistent FP32 kernel (the autotuner's knobs).
  * block: threads per CTA (multiple of 32, <= 1024); ctas_per_sm: CTAs per SM
  * in the grid; steps_per_launch: steps done per launch with the state held in
- * registers (1 = state round-trips memory every step).  Zeros pick defaults. */
+ * registers (1 = state round-trips memory every step).  Zeros pick defaults:
+ * 256 threads, twice the CTAs that fit on an SM, min(steps, 2048) steps.       */
 typedef struct {
     int block, ctas_per_sm, steps_per_launch;
 } pe_launch_config;
