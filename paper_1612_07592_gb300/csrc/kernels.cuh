@@ -354,7 +354,7 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
         out.ncs = out.br = false;
         if (active) {
             step_one<R, G>(t, r, s_h, sig_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
-            if (isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
+            if (r.box_enable && isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
         }
         if (__any_sync(0xffffffffu, out.ncs || out.br)) {
             warp_append(r, out.ncs, out.pn);

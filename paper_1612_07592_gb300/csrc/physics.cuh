@@ -145,6 +145,23 @@ __device__ __forceinline__ void envelope(const StepC<R>& c, R phi, R& g, R& dg) 
     dg = -k * (R)2 * s * cc;
 }
 
+// Float version without branches (lanes of a warp sit in different parts of the
+// pulse): one ramp sine/cosine serves both ramps, the falling ramp through
+// cos^2(k q) = sin^2(pi/2 - k q), and selects pick the region.
+__device__ __forceinline__ void envelope_sel(const StepC<float>& c, float phi, float& g, float& dg) {
+    const float pr = c.phi_r, pf = c.phi_f, k = c.k_env;
+    const bool up = phi < pr;
+    float arg = up ? k * phi : 1.57079632679489662f - k * (phi - pr - pf);
+    arg = fminf(fmaxf(arg, 0.0f), 1.57079632679489662f);
+    float s, cc;
+    ramp_sincos(arg, &s, &cc);
+    const float two_s_c = 2.0f * s * cc;
+    const bool flat = !up && phi <= pr + pf;
+    const bool out = !(phi > 0.0f) || phi >= 2.0f * pr + pf;
+    g = out ? 0.0f : (flat ? 1.0f : s * s);
+    dg = (out || flat) ? 0.0f : (up ? k * two_s_c : -k * two_s_c);
+}
+
 // phase t^n - x with t^n = n dt.  In float, n * dt_hi is exact (dt_hi has 11
 // significant bits, n < 2^13), the small remainder n * dt_lo is added, and the
 // position enters as the unevaluated sum x + x_lo kept by the compensated update.
@@ -187,8 +204,12 @@ __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R 
     }
     R phi = phase(c, nf, x, x_lo);
     R g, dg;
-    envelope<R>(c, phi, g, dg);
-    if (g == (R)0 && dg == (R)0) return;
+    if constexpr (sizeof(R) == 4) {
+        envelope_sel(c, phi, g, dg);      // no early exit either: zero fields fall out of g = dg = 0
+    } else {
+        envelope<R>(c, phi, g, dg);
+        if (g == (R)0 && dg == (R)0) return;
+    }
     const R a0 = c.a0;
     R S = 1, theta = phi, inv_R = 0, inv_w2 = 0;
     if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) {
@@ -281,10 +302,25 @@ __device__ __forceinline__ void row_pos(R v, R lnlo, R inv, R last, int n, int& 
 template <typename R>
 __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int& flag) {
     const TabC<R>& c = tabc<R>(t);
-    if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
-    int i; R w;
-    row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, flag);
-    return ((R)1 - w) * h[i] + w * h[i + 1];
+    if constexpr (sizeof(R) == 4) {
+        // clamps and selects instead of branches; flag = 1 above the table
+        float tp = (m_log(eta) - c.ln_eta_min) * c.inv_dln_eta;
+        flag = tp >= c.eta_last ? 1 : 0;
+        float tpc = fminf(fmaxf(tp, 0.0f), c.eta_last);
+        int i;
+        float w;
+        split_pos(tpc, i, w);
+        const bool top = i > t.n_eta - 2;
+        i = top ? t.n_eta - 2 : i;
+        w = top ? 1.0f : w;
+        float v = (1.0f - w) * h[i] + w * h[i + 1];
+        return (eta >= c.eta_min) ? v : c.h_classical;
+    } else {
+        if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
+        int i; R w;
+        row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, flag);
+        return ((R)1 - w) * h[i] + w * h[i + 1];
+    }
 }
 
 // inverse of the row-interpolated CDF: largest j with c_j <= R, linear between nodes
