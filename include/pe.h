@@ -178,8 +178,9 @@ pe_status pe_tables_export(const pe_tables* tables, int which, int iz, double* h
                            int64_t cap, int64_t* n_out);
 
 /* Bind buffers to a new run and, unless init_dist == PE_CALLER, draw the
- * initial positions (uniform in the slab) and momenta (rest, Maxwell-Juttner
- * by Sobol's rejection, or a beam along +x) from the particle's Philox
+ * initial positions (uniform in the slab; a beam starts at the slab's front
+ * face) and momenta (rest, Maxwell-Juttner by Sobol's rejection, or a beam
+ * along +x) from the particle's Philox
  * stream; always draws the initial optical depth tau = -ln U.  Zeroes hist,
  * tally and the photon count.  Asynchronous on cuda_stream.  The run refers
  * to tables, which must outlive it.  Z must be one of the table set's Z.

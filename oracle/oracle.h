@@ -93,7 +93,7 @@ typedef struct {
     double dt_over_T;
     int init_dist;
     double T_mev;                        /* Maxwell-Juttner temperature         */
-    double beam_gamma;                   /* OR_BEAM: u = (sqrt(g^2-1), 0, 0)    */
+    double beam_gamma;                   /* OR_BEAM: u = (sqrt(g^2-1), 0, 0) at x = slab front */
     uint64_t seed;
     uint32_t run_id;
     int enable_ncs, enable_brems;

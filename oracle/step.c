@@ -241,7 +241,8 @@ int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int6
         uint32_t w[4];
         double* s = st + 6 * k;
         draw(r, id, 0, PUR_POS, w);
-        s[0] = c.x0 + (c.x1 - c.x0) * u32(w[0]);
+        /* a beam enters at the front face of the slab (Sec. 2.2 bunch benchmark) */
+        s[0] = (r->init_dist == OR_BEAM) ? c.x0 : c.x0 + (c.x1 - c.x0) * u32(w[0]);
         s[1] = (r->geometry == OR_GAUSS_2D) ? -c.yh + 2.0 * c.yh * u32(w[1]) : 0.0;
         s[2] = s[3] = s[4] = 0.0;
         if (r->init_dist == OR_MAXWELL_JUTTNER) {

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(256) k_init(RunDevT<double> r, int init_dist, 
     if (init_dist == PE_CALLER) return;
     uint4 p = draw(r, id, 0, PUR_POS);
     const StepC<double>& c = r.c;
-    double x = c.x0 + (c.x1 - c.x0) * uni32(p.x);
+    // a beam enters at the front face of the slab
+    double x = (init_dist == PE_BEAM) ? c.x0 : c.x0 + (c.x1 - c.x0) * uni32(p.x);
     double y = (r.geometry == PE_GAUSS_2D) ? -c.yh + 2.0 * c.yh * uni32(p.y) : 0.0;
     double u0 = 0, u1 = 0, u2 = 0;
     if (init_dist == PE_MAXWELL_JUTTNER) {

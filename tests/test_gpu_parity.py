@@ -146,6 +146,8 @@ CASES = {
     # dense fields-off target: brems-dominated (Sec. 2.2 benchmark mode)
     "beam-au-brems": (dict(a0=0.0, init_dist=2, beam_gamma=2000.0, ne_over_nc=2e4, slab_x0_m=-1e-3,
                            slab_thick_m=2e-3, enable_ncs=0, seed=9, **W.AU), 500, 800),
+    # the paper's bunch benchmark: 100 MeV into 5 mm of fully ionised Au, fields off (Sec. 2.2)
+    "bunch-100mev-au-5mm": (dict(W.bunch(100.0, "Au")["run"]), 300, 5000),
 }
 
 

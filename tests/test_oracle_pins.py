@@ -522,3 +522,35 @@ def test_config2_time_step_is_ill_conditioned():
         worst.append((np.abs(a[:, 2:5] - b[:, 2:5]).max(1) / scale).max())
     assert worst[0] > 1e-5
     assert worst[1] < worst[0] / 4
+
+
+@pytest.mark.parametrize("E0,target", [(1000.0, "Au"), (1000.0, "Al"), (100.0, "Au")])
+def test_bunch_energy_loss_radiation_length(E0, target):
+    """Sec. 2.2 benchmark (fields off, pusher + brems only): a 1 GeV bunch through 5 mm of target
+    loses energy by bremsstrahlung at the radiation-length rate, <E>/E0 ~ exp(-L/X0) (Tsai complete
+    screening, PDG X0), to a few per cent.  A 100 MeV bunch slows into the regime of incomplete
+    screening and of a hard-photon cut that is no longer negligible, so it loses less than that law."""
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.bunch(E0, target, n=2000)
+    X0_gcm2, rho = (6.46, 19.3) if target == "Au" else (24.01, 2.70)
+    L_over_X0 = 0.5 / (X0_gcm2 / rho)
+    p = O.table_params(n_eta=2, n_y=4, n_E=96, n_s=64, gamma_min=2.0, gamma_max=1e5)
+    t = O.Tables(p, [13.0, 79.0])
+    run = dict(c["run"]); run["iz"] = 1 if target == "Au" else 0
+    r = O.run_params(**run)
+    ids = np.arange(c["n"])
+    st = O.init(t, r, ids)
+    assert np.all(st[:, 0] == 0.0)
+    ph, n, hist, tally = O.run(t, r, ids, st, 0, c["steps"], capacity=1 << 20)
+    g0 = E0 / 0.51099895 + 1.0
+    g = np.sqrt(1 + (st[:, 2:5] ** 2).sum(1))
+    ratio = (g - 1).mean() / (g0 - 1)
+    law = math.exp(-L_over_X0)
+    if E0 >= 1000.0:
+        assert abs(ratio / law - 1) < 0.06, (ratio, law)
+    else:
+        assert law < ratio < 1.3 * law, (ratio, law)
+    # energy bookkeeping: electron loss = photon energy (stored, above the cut)
+    emitted = O.fixed_to_float(tally, O.T["E_BR_STORED"])
+    lost = (g0 - g).sum()
+    assert abs(emitted / lost - 1) < 1e-9
