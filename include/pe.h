@@ -144,7 +144,9 @@ typedef struct {
 } pe_buffers;
 
 /* Launch shape of the persistent FP32 kernel (the autotuner's knobs).
- * block: threads per CTA (multiple of 32, <= 1024); ctas_per_sm: CTAs per SM
+ * block: electrons per tile and threads per CTA (64, 128, 192 or 256; the FP32
+ * plane-wave kernel covers a tile with block/2 threads, two electrons each);
+ * ctas_per_sm: CTAs per SM
  * in the grid; steps_per_launch: steps done per launch with the state held in
  * registers (1 = state round-trips memory every step).  Zeros pick defaults:
  * 256 threads, twice the CTAs that fit on an SM, min(steps, 2048) steps.       */

@@ -299,7 +299,7 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
     const pe_tables* t = runs[0]->tables;
     int prec = runs[0]->params.precision;
     int block = (cfg && cfg->block > 0) ? cfg->block : 256;
-    if (block % 32 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be a multiple of 32, <= 256");
+    if (block % 64 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be 64, 128, 192 or 256");
     int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 2048);
     if (K < 1) K = 1;
     int dev;
@@ -496,10 +496,11 @@ extern "C" pe_status pe_graph_create(pe_run* const* runs, int n_runs, int64_t st
         g->args[k] = {(void*)&t->dev, batch, (void*)&g->step_args[k]};
         cudaKernelNodeParams& p = g->params[k];
         std::memset(&p, 0, sizeof(p));
-        p.func = const_cast<void*>(L.prec == PE_F32 ? persistent_kernel_f32(*L.bf, L.smem)
-                                                    : persistent_kernel_f64(*L.bd, L.smem));
+        int threads = L.block;
+        p.func = const_cast<void*>(L.prec == PE_F32 ? persistent_kernel_f32(*L.bf, L.smem, L.block, &threads)
+                                                    : persistent_kernel_f64(*L.bd, L.smem, L.block, &threads));
         p.gridDim = dim3(L.grid);
-        p.blockDim = dim3(L.block);
+        p.blockDim = dim3(threads);
         p.sharedMemBytes = L.smem;
         p.kernelParams = g->args[k].data();
         e = cudaGraphAddKernelNode(&g->nodes[k], g->graph, k ? &g->nodes[k - 1] : nullptr, k ? 1 : 0, &p);

@@ -127,8 +127,8 @@ void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, 
                                 cudaStream_t s);
 int persistent_smem_bytes(const TablesDev& t, int precision);
 int persistent_occupancy_f32(int block, int smem);
-const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem);
-const void* persistent_kernel_f64(const BatchDevT<double>& b, int smem);
+const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem, int block, int* threads);
+const void* persistent_kernel_f64(const BatchDevT<double>& b, int smem, int block, int* threads);
 int persistent_occupancy_f64(int block, int smem);
 
 }  // namespace pe

@@ -150,6 +150,87 @@ struct StepOut {
     Photon pn, pb;
 };
 
+// NCS emission at a crossing of the optical depth (Sec. 2.2): photon energy by
+// inverse CDF, recoil along u, tallies, new optical depth.  gamma is updated.
+template <typename R>
+__device__ __forceinline__ void ncs_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                         Particle<R>& P, R& gamma, R eta, R xn, R yn, bool& stored, Photon& ph,
+                                         unsigned long long* hist, unsigned long long* tally) {
+    const StepC<R>& c = r.c;
+    const R photon_min = tabc<R>(t).photon_min;
+    uint4 w = draw(r, id, n, PUR_NCS);
+    bool below;
+    R delta = sample_delta(t, eta, w, below);
+    if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
+    R ew = delta * gamma;
+    if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
+    R k[3];
+    recoil<R>(P.u, gamma, ew, k);
+    note_event<R>(P, n, 0);
+    R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    fx_add_r(tally + PE_T_E_RECOIL_NCS, gamma - gn);
+    if (ew >= photon_min) {
+        atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
+        fx_add_r(tally + PE_T_E_NCS_STORED, ew);
+        hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
+        stored = true;
+        ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
+    } else {
+        atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
+        fx_add_r(tally + PE_T_E_NCS_BELOW, ew);
+    }
+    gamma = gn;
+    tau_draw(P, w);
+}
+
+// Bremsstrahlung direct MC collision (Eq. 4 and the text after it) for an
+// electron in the slab: event test, photon energy, recoil.  gamma is updated.
+template <typename R>
+__device__ __forceinline__ void brems_collide(const TablesDev& t, const RunDevT<R>& r, const R* sig_tab,
+                                              uint32_t id, uint32_t n, Particle<R>& P, R& gamma, R xn, R yn,
+                                              bool& stored, Photon& ph, unsigned long long* hist,
+                                              unsigned long long* tally) {
+    const StepC<R>& c = r.c;
+    const R photon_min = tabc<R>(t).photon_min;
+    bool above;
+    R sig = sigma_of<R>(t, sig_tab, gamma, above);
+    if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
+    R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    R xb = c.K_br * sig * (um / gamma);
+    R Pbr = -m_expm1(-xb);
+    uint4 w = draw(r, id, n, PUR_BREMS);
+    if (brems_event(Pbr, w)) {
+        R yy = sample_y(t, r.iz, gamma, w);
+        R ew = yy * gamma;
+        R k[3];
+        recoil<R>(P.u, gamma, ew, k);
+        note_event<R>(P, n, 1);
+        R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+        fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
+        if (ew >= photon_min) {
+            atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
+            fx_add_r(tally + PE_T_E_BR_STORED, ew);
+            hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
+            stored = true;
+            ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
+        } else {
+            atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
+            fx_add_r(tally + PE_T_E_BR_BELOW, ew);
+        }
+        gamma = gn;
+    }
+}
+
+// absorbing boundary in x (Sec. 3): the electron is removed (x = NaN)
+template <typename R>
+__device__ __forceinline__ void box_check(const RunDevT<R>& r, Particle<R>& P, uint32_t n, unsigned long long* tally) {
+    if (r.box_enable && (P.x < r.c.box0 || P.x > r.c.box1)) {
+        P.x = (R)NAN;
+        atomicAdd(tally + PE_T_N_KILLED, 1ull);
+        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)n + 1ull);
+    }
+}
+
 template <typename R, int G>
 __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
                                          uint32_t id, uint32_t n, R nf,
@@ -172,75 +253,19 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
         tau_sub(P, c.ncs_coef * (eta / gamma) * h);
-        if (tau_crossed(P)) {
-            uint4 w = draw(r, id, n, PUR_NCS);
-            bool below;
-            R delta = sample_delta(t, eta, w, below);
-            if (below) atomicAdd(tally + PE_T_N_ETA_BELOW, 1ull);
-            R ew = delta * gamma;
-            if (ew > gamma - (R)1) { ew = gamma - (R)1; atomicAdd(tally + PE_T_N_CLAMP, 1ull); }
-            R k[3];
-            recoil<R>(P.u, gamma, ew, k);
-            note_event<R>(P, n, 0);
-            R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            fx_add_r(tally + PE_T_E_RECOIL_NCS, gamma - gn);
-            if (ew >= photon_min) {
-                atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
-                fx_add_r(tally + PE_T_E_NCS_STORED, ew);
-                hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
-                out.ncs = true;
-                out.pn = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
-            } else {
-                atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
-                fx_add_r(tally + PE_T_E_NCS_BELOW, ew);
-            }
-            gamma = gn;
-            tau_draw(P, w);
-        }
+        if (tau_crossed(P)) ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, out.ncs, out.pn, hist, tally);
     }
 
     if (r.enable_brems) {
         bool in_slab = (xn >= c.x0 && xn <= c.x1);
         if ((G == FK_GAUSS_LP || G == FK_GAUSS_CP) && fabs(yn) > c.yh) in_slab = false;
-        if (in_slab && gamma > (R)1 + photon_min) {
-            bool above;
-            R sig = sigma_of<R>(t, sig_tab, gamma, above);
-            if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
-            R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-            R xb = c.K_br * sig * (um / gamma);
-            R Pbr = -m_expm1(-xb);
-            uint4 w = draw(r, id, n, PUR_BREMS);
-            if (brems_event(Pbr, w)) {
-                R yy = sample_y(t, r.iz, gamma, w);
-                R ew = yy * gamma;
-                R k[3];
-                recoil<R>(P.u, gamma, ew, k);
-                note_event<R>(P, n, 1);
-                R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-                fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
-                if (ew >= photon_min) {
-                    atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
-                    fx_add_r(tally + PE_T_E_BR_STORED, ew);
-                    hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
-                    out.br = true;
-                    out.pb = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n,
-                                    id | 0x80000000u};
-                } else {
-                    atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
-                    fx_add_r(tally + PE_T_E_BR_BELOW, ew);
-                }
-                gamma = gn;
-            }
-        }
+        if (in_slab && gamma > (R)1 + photon_min)
+            brems_collide<R>(t, r, sig_tab, id, n, P, gamma, xn, yn, out.br, out.pb, hist, tally);
     }
 
     advance(P.x, P.x_lo, dt * P.u[0] / gamma);
     if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) advance(P.y, P.y_lo, dt * P.u[1] / gamma);
-    if (r.box_enable && (P.x < c.box0 || P.x > c.box1)) {
-        P.x = (R)NAN;
-        atomicAdd(tally + PE_T_N_KILLED, 1ull);
-        atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)n + 1ull);
-    }
+    box_check<R>(r, P, n, tally);
 }
 
 __device__ __forceinline__ void load_tau(const RunDevT<double>& r, int64_t i, Particle<double>& P) {

@@ -1,14 +1,31 @@
 // kernels_f32.cu -- instantiations of the persistent kernel for float.
 #include "kernels.cuh"
+#include "pair_f32.cuh"
 
 namespace pe {
+
+// The 1D plane-wave kinds use the paired kernel (two electrons per thread, block/2
+// threads per tile of `block` electrons); the others one electron per thread.
+template <bool kSingle, int G>
+static const void* kernel_of(int block, int& threads) {
+    if (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+        threads = block / 2;
+        return (const void*)k_step_pair<kSingle, G>;
+    }
+    threads = block;
+    return (const void*)k_step_persistent<float, kSingle, G>;
+}
 
 template <bool kSingle, int G>
 static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block, cudaStream_t s,
                        int smem) {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_step_persistent<float, kSingle, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_step_persistent<float, kSingle, G><<<grid, block, smem, s>>>(t, b, steps);
+    int threads;
+    const void* f = kernel_of<kSingle, G>(block, threads);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (G == FK_PLANE_LP || G == FK_PLANE_CP)
+        k_step_pair<kSingle, (G == FK_PLANE_CP ? FK_PLANE_CP : FK_PLANE_LP)><<<grid, threads, smem, s>>>(t, b, steps);
+    else
+        k_step_persistent<float, kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
 }
 
 void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
@@ -35,28 +52,31 @@ void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, i
     }
 }
 
-// the kernel a launch of these runs uses (for graph nodes); sets the shared-memory attribute
-const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem) {
+// the kernel a launch of these runs uses and its threads per CTA (for graph nodes);
+// sets the shared-memory attribute
+const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem, int block, int* threads) {
     const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
     const void* f = nullptr;
+    int th = block;
     if (b.n_runs == 1) {
         switch (fk) {
-            case FK_PLANE_LP: f = (const void*)k_step_persistent<float, true, FK_PLANE_LP>; break;
-            case FK_PLANE_CP: f = (const void*)k_step_persistent<float, true, FK_PLANE_CP>; break;
-            case FK_GAUSS_LP: f = (const void*)k_step_persistent<float, true, FK_GAUSS_LP>; break;
-            case FK_GAUSS_CP: f = (const void*)k_step_persistent<float, true, FK_GAUSS_CP>; break;
-            default: f = (const void*)k_step_persistent<float, true, FK_CONST>; break;
+            case FK_PLANE_LP: f = kernel_of<true, FK_PLANE_LP>(block, th); break;
+            case FK_PLANE_CP: f = kernel_of<true, FK_PLANE_CP>(block, th); break;
+            case FK_GAUSS_LP: f = kernel_of<true, FK_GAUSS_LP>(block, th); break;
+            case FK_GAUSS_CP: f = kernel_of<true, FK_GAUSS_CP>(block, th); break;
+            default: f = kernel_of<true, FK_CONST>(block, th); break;
         }
     } else {
         switch (fk) {
-            case FK_PLANE_LP: f = (const void*)k_step_persistent<float, false, FK_PLANE_LP>; break;
-            case FK_PLANE_CP: f = (const void*)k_step_persistent<float, false, FK_PLANE_CP>; break;
-            case FK_GAUSS_LP: f = (const void*)k_step_persistent<float, false, FK_GAUSS_LP>; break;
-            case FK_GAUSS_CP: f = (const void*)k_step_persistent<float, false, FK_GAUSS_CP>; break;
-            default: f = (const void*)k_step_persistent<float, false, FK_CONST>; break;
+            case FK_PLANE_LP: f = kernel_of<false, FK_PLANE_LP>(block, th); break;
+            case FK_PLANE_CP: f = kernel_of<false, FK_PLANE_CP>(block, th); break;
+            case FK_GAUSS_LP: f = kernel_of<false, FK_GAUSS_LP>(block, th); break;
+            case FK_GAUSS_CP: f = kernel_of<false, FK_GAUSS_CP>(block, th); break;
+            default: f = kernel_of<false, FK_CONST>(block, th); break;
         }
     }
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    *threads = th;
     return f;
 }
 

@@ -36,7 +36,8 @@ void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, 
 }
 
 // the kernel a launch of these runs uses (for graph nodes); sets the shared-memory attribute
-const void* persistent_kernel_f64(const BatchDevT<double>& b, int smem) {
+const void* persistent_kernel_f64(const BatchDevT<double>& b, int smem, int block, int* threads) {
+    *threads = block;
     const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
     const void* f = nullptr;
     if (b.n_runs == 1) {

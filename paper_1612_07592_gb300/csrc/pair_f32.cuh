@@ -1,0 +1,321 @@
+// pair_f32.cuh -- the FP32 step for the 1D plane-wave field kinds with two
+// electrons per thread.  Blackwell issues paired single-precision arithmetic
+// (FFMA2/FADD2/FMUL2: two FP32 results per instruction), so the common path of
+// the step -- fields, Boris push, eta, rate lookup, optical depth, position --
+// runs on float2 values holding the two electrons, with the operations of the
+// one-electron float step in the same order.  Emissions, the
+// bremsstrahlung test in the slab and the absorbing boundary leave the packed
+// path and run the one-electron code for the electron concerned.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace pe {
+
+// ---- paired arithmetic -----------------------------------------------------------
+__device__ __forceinline__ float2 P2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one paired instruction: (-1) b + a
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, P2(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f)); }
+// per-electron operations (no paired form)
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
+__device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__logf(a.x), __logf(a.y)); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
+    return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+__device__ __forceinline__ float2 clamp2(float2 a, float lo, float hi) {
+    return make_float2(fminf(fmaxf(a.x, lo), hi), fminf(fmaxf(a.y, lo), hi));
+}
+__device__ __forceinline__ float comp(float2 a, int k) { return k ? a.y : a.x; }
+__device__ __forceinline__ void set_comp(float2& a, int k, float v) { if (k) a.y = v; else a.x = v; }
+
+// TwoSum on pairs: (s, e) with s + e = a + b exactly
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = add2(a, b);
+    float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// ramp sine/cosine of the envelope (Taylor series about pi/4), paired
+__device__ __forceinline__ void ramp_sincos2(float2 v, float2& s_out, float2& c_out) {
+    float2 d = sub2(v, P2(0.785398163397448310f));
+    float2 d2 = mul2(d, d);
+    float2 sp = fma2(d2, P2(2.75573192e-6f), P2(-1.98412698e-4f));
+    sp = fma2(d2, sp, P2(8.33333333e-3f));
+    sp = fma2(d2, sp, P2(-1.66666667e-1f));
+    float2 sd = fma2(mul2(d, d2), sp, d);
+    float2 cp = fma2(d2, P2(-2.75573192e-7f), P2(2.48015873e-5f));
+    cp = fma2(d2, cp, P2(-1.38888889e-3f));
+    cp = fma2(d2, cp, P2(4.16666667e-2f));
+    cp = fma2(d2, cp, P2(-0.5f));
+    float2 cd = fma2(d2, cp, P2(1.0f));
+    const float2 r = P2(0.707106781186547524f);
+    s_out = mul2(r, add2(cd, sd));
+    c_out = mul2(r, sub2(cd, sd));
+}
+
+// sine and cosine (Cody-Waite reduction by pi/2, Taylor series), paired
+__device__ __forceinline__ void sincos2(float2 v, float2& s_out, float2& c_out) {
+    const float kMagic = 0x1.8p23f;
+    float2 t = fma2(v, P2(0.636619772367581343f), P2(kMagic));
+    int qx = __float_as_int(t.x), qy = __float_as_int(t.y);
+    float2 k = sub2(t, P2(kMagic));
+    float2 r = fma2(neg2(k), P2(1.57079637050628662f), v);
+    r = fma2(neg2(k), P2(-4.37113900018624283e-8f), r);
+    float2 r2 = mul2(r, r);
+    float2 sp = fma2(r2, P2(2.75573192e-6f), P2(-1.98412698e-4f));
+    sp = fma2(r2, sp, P2(8.33333333e-3f));
+    sp = fma2(r2, sp, P2(-1.66666667e-1f));
+    float2 sn = fma2(mul2(r, r2), sp, r);
+    float2 cp = fma2(r2, P2(-2.75573192e-7f), P2(2.48015873e-5f));
+    cp = fma2(r2, cp, P2(-1.38888889e-3f));
+    cp = fma2(r2, cp, P2(4.16666667e-2f));
+    cp = fma2(r2, cp, P2(-0.5f));
+    float2 cs = fma2(r2, cp, P2(1.0f));
+    float2 a = sel2(qx & 1, qy & 1, cs, sn);
+    float2 b = sel2(qx & 1, qy & 1, sn, cs);
+    s_out = sel2(qx & 2, qy & 2, neg2(a), a);
+    c_out = sel2((qx + 1) & 2, (qy + 1) & 2, neg2(b), b);
+}
+
+// two electrons; per-electron activity, optical-depth pairs and event fingerprints
+struct Pair {
+    float2 x, x_lo, u0, u1, u2, tau, tau_lo;
+    uint32_t ev_cnt[2], ev_hash[2];
+    bool act[2];
+};
+
+__device__ __forceinline__ Particle<float> unpack(const Pair& Q, int k) {
+    Particle<float> P;
+    P.x = comp(Q.x, k); P.x_lo = comp(Q.x_lo, k);
+    P.y = 0.0f; P.y_lo = 0.0f;
+    P.u[0] = comp(Q.u0, k); P.u[1] = comp(Q.u1, k); P.u[2] = comp(Q.u2, k);
+    P.tau = comp(Q.tau, k); P.tau_lo = comp(Q.tau_lo, k);
+    P.ev_cnt = Q.ev_cnt[k]; P.ev_hash = Q.ev_hash[k];
+    return P;
+}
+__device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P) {
+    set_comp(Q.x, k, P.x); set_comp(Q.x_lo, k, P.x_lo);
+    set_comp(Q.u0, k, P.u[0]); set_comp(Q.u1, k, P.u[1]); set_comp(Q.u2, k, P.u[2]);
+    set_comp(Q.tau, k, P.tau); set_comp(Q.tau_lo, k, P.tau_lo);
+    Q.ev_cnt[k] = P.ev_cnt; Q.ev_hash[k] = P.ev_hash;
+}
+
+// one step of two electrons (plane wave, G = FK_PLANE_LP or FK_PLANE_CP)
+template <int G>
+__device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
+                                          const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
+                                          bool st_ncs[2], Photon pn[2], bool st_br[2], Photon pb[2],
+                                          unsigned long long* hist, unsigned long long* tally) {
+    const StepC<float>& c = r.c;
+    const TabC<float>& tc = t.cf;
+    const float2 dt = P2(c.dt), h = P2(0.5f * c.dt);
+    // fields at (x^n, t^n): phase, envelope, carrier
+    const float2 nf2 = P2(nf);
+    float2 phi = fma2(nf2, P2(c.dt_lo), sub2(mul2(nf2, P2(c.dt_hi)), Q.x));
+    phi = sub2(phi, Q.x_lo);
+    const bool upx = phi.x < c.phi_r, upy = phi.y < c.phi_r;
+    float2 arg = sel2(upx, upy, mul2(P2(c.k_env), phi),
+                      sub2(P2(1.57079632679489662f), mul2(P2(c.k_env), sub2(sub2(phi, P2(c.phi_r)), P2(c.phi_f)))));
+    arg = clamp2(arg, 0.0f, 1.57079632679489662f);
+    float2 rs, rc;
+    ramp_sincos2(arg, rs, rc);
+    const float2 two_sc = mul2(mul2(P2(2.0f), rs), rc);
+    const bool flx = !upx && phi.x <= c.phi_r + c.phi_f, fly = !upy && phi.y <= c.phi_r + c.phi_f;
+    const bool oux = !(phi.x > 0.0f) || phi.x >= 2.0f * c.phi_r + c.phi_f;
+    const bool ouy = !(phi.y > 0.0f) || phi.y >= 2.0f * c.phi_r + c.phi_f;
+    float2 g = sel2(oux, ouy, P2(0.0f), sel2(flx, fly, P2(1.0f), mul2(rs, rs)));
+    float2 kts = mul2(P2(c.k_env), two_sc);
+    float2 dg = sel2(oux || flx, ouy || fly, P2(0.0f), sel2(upx, upy, kts, neg2(kts)));
+    float2 st, ct;
+    sincos2(phi, st, ct);
+    const float2 ma0 = P2(-c.a0);
+    float2 ey = mul2(ma0, fma2(dg, st, mul2(g, ct)));          // -a0 (g' sin + g cos)
+    float2 ez = P2(0.0f);
+    if (G == FK_PLANE_CP) ez = mul2(P2(c.a0), sub2(mul2(dg, ct), mul2(g, st)));   // a0 (g' cos - g sin)
+    // Boris push with E = (0, ey, ez), B = (0, -ez, ey)
+    float2 um0 = Q.u0;
+    float2 um1 = sub2(Q.u1, mul2(h, ey));
+    float2 um2 = (G == FK_PLANE_CP) ? sub2(Q.u2, mul2(h, ez)) : Q.u2;
+    float2 q = fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f))));
+    float2 ig = div2(P2(1.0f), sqrt2(q));
+    float2 t1 = (G == FK_PLANE_CP) ? mul2(mul2(h, ez), ig) : P2(0.0f);   // -h B_y / gamma
+    float2 t2 = mul2(neg2(mul2(h, ey)), ig);                           // -h B_z / gamma
+    float2 f = div2(P2(2.0f), fma2(t2, t2, fma2(t1, t1, P2(1.0f))));
+    float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
+    float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
+    float2 p1 = sub2(um1, mul2(um0, t2));
+    float2 p2 = add2(um2, mul2(um0, t1));
+    Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
+    Q.u1 = sub2(sub2(um1, mul2(p0, s2)), mul2(h, ey));
+    Q.u2 = (G == FK_PLANE_CP) ? sub2(add2(um2, mul2(p0, s1)), mul2(h, ez)) : um2;
+    float2 gamma = sqrt2(fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, fma2(Q.u0, Q.u0, P2(1.0f)))));
+    const float2 xn = Q.x;
+    float gam[2] = {gamma.x, gamma.y};
+
+    if (r.enable_ncs) {
+        // eta = (gamma - u_x) |E| / E_S for the plane wave
+        float2 up = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, P2(1.0f)));
+        float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, div2(up, add2(gamma, Q.u0)), sub2(gamma, Q.u0));
+        float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
+        float2 eta = mul2(mul2(gm, Emag), P2(c.inv_ES));
+        // h(eta): row interpolation in log eta, classical limit below the table
+        float2 tp = mul2(sub2(log2v(eta), P2(tc.ln_eta_min)), P2(tc.inv_dln_eta));
+        const bool abx = tp.x >= tc.eta_last, aby = tp.y >= tc.eta_last;
+        float2 tpc = clamp2(tp, 0.0f, tc.eta_last);
+        float2 tt = add2(sub2(tpc, P2(0.5f)), P2(0x1.8p23f));
+        int ix = __float_as_int(tt.x) - 0x4B400000, iy = __float_as_int(tt.y) - 0x4B400000;
+        float2 w = sub2(tpc, sub2(tt, P2(0x1.8p23f)));
+        const bool topx = ix > t.n_eta - 2, topy = iy > t.n_eta - 2;
+        ix = topx ? t.n_eta - 2 : ix;
+        iy = topy ? t.n_eta - 2 : iy;
+        w = sel2(topx, topy, P2(1.0f), w);
+        float2 h0 = make_float2(h_tab[ix], h_tab[iy]), h1 = make_float2(h_tab[ix + 1], h_tab[iy + 1]);
+        float2 hv = add2(mul2(sub2(P2(1.0f), w), h0), mul2(w, h1));
+        hv = sel2(eta.x >= tc.eta_min, eta.y >= tc.eta_min, hv, P2(tc.h_classical));
+        if (Q.act[0] && abx) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
+        if (Q.act[1] && aby) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
+        // tau -= ncs_coef (eta / gamma) h(eta), compensated
+        float2 dtau = mul2(mul2(P2(c.ncs_coef), div2(eta, gamma)), hv);
+        float2 s, e;
+        two_sum2(Q.tau, neg2(dtau), s, e);
+        Q.tau = s;
+        Q.tau_lo = add2(Q.tau_lo, e);
+        float2 tsum = add2(Q.tau, Q.tau_lo);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (Q.act[k] && comp(tsum, k) <= 0.0f) {
+                Particle<float> P = unpack(Q, k);
+                ncs_emit<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, st_ncs[k], pn[k], hist,
+                                tally);
+                repack(Q, k, P);
+            }
+        }
+    }
+
+    if (r.enable_brems) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float x = comp(xn, k);
+            if (Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min) {
+                Particle<float> P = unpack(Q, k);
+                brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist, tally);
+                repack(Q, k, P);
+            }
+        }
+    }
+
+    // x^{n+1} = x^n + dt u_x / gamma, compensated
+    float2 d = div2(mul2(dt, Q.u0), make_float2(gam[0], gam[1]));
+    float2 s, e;
+    two_sum2(Q.x, d, s, e);
+    Q.x = s;
+    Q.x_lo = add2(Q.x_lo, e);
+    if (r.box_enable) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!Q.act[k]) continue;
+            Particle<float> P = unpack(Q, k);
+            box_check<float>(r, P, n, tally);
+            repack(Q, k, P);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pair& Q, int k) {
+    Particle<float> P;
+    load_particle<float>(r, i, P);
+    repack(Q, k, P);
+    Q.act[k] = !isnan(P.x);
+}
+
+// K steps of the two electrons i0 = base + tid and i1 = base + tid + blockDim
+template <int G>
+__device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
+                                                const float* sig_z, int64_t i0, int64_t i1, int steps,
+                                                unsigned long long* s_hist, unsigned long long* s_tally) {
+    Pair Q;
+    Q.x = Q.x_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
+    Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
+    Q.act[0] = Q.act[1] = false;
+    if (i0 < r.n) load_one(r, i0, Q, 0);
+    if (i1 < r.n) load_one(r, i1, Q, 1);
+    const bool live0 = i0 < r.n, live1 = i1 < r.n;
+    const uint32_t id[2] = {(uint32_t)i0, (uint32_t)i1};
+    const uint32_t n0 = (uint32_t)r.step0;
+    float nf = (float)n0;
+    for (int s = 0; s < steps; ++s, nf += 1.0f) {
+        bool st_ncs[2] = {false, false}, st_br[2] = {false, false};
+        Photon pn[2], pb[2];
+        if (Q.act[0] || Q.act[1]) {
+            step_pair<G>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally);
+            if (r.box_enable) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (Q.act[k] && isnan(comp(Q.x, k))) {
+                        Q.act[k] = false;
+                        store_particle<float>(r, k ? i1 : i0, unpack(Q, k));
+                    }
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, st_ncs[0] || st_br[0] || st_ncs[1] || st_br[1])) {
+            warp_append(r, st_ncs[0], pn[0]);
+            warp_append(r, st_br[0], pb[0]);
+            warp_append(r, st_ncs[1], pn[1]);
+            warp_append(r, st_br[1], pb[1]);
+        }
+    }
+    if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
+    if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
+}
+
+// Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
+template <bool kSingle, int G>
+__global__ void __launch_bounds__(128, 4) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RunDevT<float> s_run;
+    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
+    float* s_h = reinterpret_cast<float*>(s_tally + PE_TALLY_WORDS);
+    float* s_sig = s_h + t.n_eta;
+
+    for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
+    for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = t.h32[k];
+    for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = t.sig32[k];
+    __syncthreads();
+
+    const int64_t n_tiles = b.tile_start[b.n_runs];
+    int cur = -1;
+    int run_idx = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (!kSingle) {
+            while (run_idx + 1 < b.n_runs && b.tile_start[run_idx + 1] <= tile) ++run_idx;
+            if (run_idx != cur) {
+                if (cur >= 0) flush_shared<float>(s_hist, s_tally, s_run);
+                constexpr int kWords = sizeof(RunDevT<float>) / 4;
+                for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+                    reinterpret_cast<uint32_t*>(&s_run)[w] = reinterpret_cast<const uint32_t*>(&b.runs[run_idx])[w];
+                __syncthreads();
+                cur = run_idx;
+            }
+        }
+        const RunDevT<float>& r = kSingle ? b.runs[0] : s_run;
+        const int64_t base = (tile - b.tile_start[run_idx]) * b.tile;
+        const int64_t i0 = base + threadIdx.x, i1 = base + threadIdx.x + blockDim.x;
+        tile_steps_pair<G>(t, r, s_h, s_sig + (size_t)r.iz * t.n_E, i0, i1, steps, s_hist, s_tally);
+    }
+    if (kSingle) {
+        if (n_tiles > 0) flush_shared<float>(s_hist, s_tally, b.runs[0]);
+    } else if (cur >= 0) {
+        flush_shared<float>(s_hist, s_tally, s_run);
+    }
+}
+
+}  // namespace pe
