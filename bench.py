@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the ncu
 # capture in profiles/k_step_persistent_f32__1d-au-a270-mj-2e5x400__full.md (5.88 MB for
 # 2e5 electrons); None once the kernel changes after that capture.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.4
+NCU_TRAFFIC_BYTES_PER_ELECTRON = None
 
 
 def peaks():
@@ -279,14 +279,14 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": cfg["name"], "particles_per_gpu": n, "job_steps": S,
                       "precision": "fp32 push/emission, fp64 optical depth, 128-bit fixed-point tallies",
-                      "kernel": "k_step_persistent<float>",
-                      "steps_per_launch": args.steps_per_launch or min(S, 2048),
+                      "kernel": "k_step_pair (FP32 persistent, two electrons per thread)",
+                      "steps_per_launch": args.steps_per_launch or min(S, 4096),
                       "block": args.block or 256, "l2": "flushed between timed jobs (256 MB write)",
                       "parallelism": f"dp{world} (independent jobs per GPU)"},
            "gpu_launches": int(launches),
            "clocks": clocks.summary(),
            "wall_s_timed_region": wall}
-    # roofline of the dominant kernel: FP32 pipe (state held in registers across steps)
+    # roofline of the dominant kernel (k_step_pair): FP32 pipe (state held in registers across steps)
     sm_clock = (res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
     fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
     ach = FLOP_PER_PSTEP_1D * pst / (ms * 1e-3) / 1e12
@@ -315,29 +315,33 @@ def main():
 
 
 def hbm_form(pe, tables, cfg, stream, peak_gbs, peak_kind):
-    """One step per launch (state round-trips HBM every step) on 3e7 electrons of the same
-    1D physics (1.44 GB of state per step, > L2): per-launch time by CUDA events."""
+    """One step per launch (the state round-trips HBM every step, as when fields come from a
+    grid) on 3e7 electrons of the same 1D physics (1.08 GB of state, > L2), over the whole
+    4000-step job: mean per-launch time by CUDA events."""
     import torch
     n = 30_000_000
     run = dict(cfg["run"], run_id=7)
     with torch.cuda.stream(stream):
         r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=1 << 20, stream=stream)
-    pe.pe_step_ex([r.handle], 200, steps_per_launch=200)       # bring the pulse onto the slab
     stream.synchronize()
-    for _ in range(3):
+    for _ in range(3):                                           # warm-up launches
         pe.pe_step_ex([r.handle], 1, steps_per_launch=1)
+    r.rebind(tables)
+    stream.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    K = 20
+    K = cfg["steps"]
     ev[0].record(stream)
     pe.pe_step_ex([r.handle], K, steps_per_launch=1)
     ev[1].record(stream)
     ev[1].synchronize()
+    pst = r.tally_out().live_particle_steps
     ms = ev[0].elapsed_time(ev[1]) / K
-    gbs = BYTES_PER_PSTEP_1D * n / (ms * 1e-3) / 1e9
+    gbs = BYTES_PER_PSTEP_1D * pst / K / (ms * 1e-3) / 1e9
     r.close()
     return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
             "traffic": None, "peak_kind": peak_kind, "particles": n, "bytes_per_particle_step": BYTES_PER_PSTEP_1D,
-            "ms_per_launch": ms, "particle_steps_per_s": n / (ms * 1e-3), "kernel": "k_step_persistent<float>, K=1"}
+            "ms_per_launch": ms, "launches": K, "particle_steps_per_s": pst / K / (ms * 1e-3),
+            "kernel": "k_step_pair (FP32, 1D plane wave), one step per launch"}
 
 
 def fp64_plain(pe, tables, cfg, stream, flush):

@@ -149,7 +149,8 @@ typedef struct {
  * ctas_per_sm: CTAs per SM
  * in the grid; steps_per_launch: steps done per launch with the state held in
  * registers (1 = state round-trips memory every step).  Zeros pick defaults:
- * 256 threads, twice the CTAs that fit on an SM, min(steps, 2048) steps.       */
+ * 256 electrons per tile, twice the CTAs that fit on an SM, min(steps, 4096)
+ * steps per launch.                                                            */
 typedef struct {
     int block, ctas_per_sm, steps_per_launch;
 } pe_launch_config;

@@ -300,7 +300,7 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
     int prec = runs[0]->params.precision;
     int block = (cfg && cfg->block > 0) ? cfg->block : 256;
     if (block % 64 || block > 256) return fail(PE_ERR_ARG, "pe_step: block must be 64, 128, 192 or 256");
-    int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 2048);
+    int K = (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : (int)std::min<int64_t>(n_steps, 4096);
     if (K < 1) K = 1;
     int dev;
     cudaGetDevice(&dev);

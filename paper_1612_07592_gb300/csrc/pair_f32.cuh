@@ -276,9 +276,12 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
 }
 
+#ifndef PE_PAIR_MIN_CTAS
+#define PE_PAIR_MIN_CTAS 5   // resident CTAs of 128 threads per SM the register budget is sized for (96 registers)
+#endif
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
 template <bool kSingle, int G>
-__global__ void __launch_bounds__(128, 4) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
+__global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<float> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
