@@ -324,9 +324,13 @@ def hbm_form(pe, tables, cfg, stream, peak_gbs, peak_kind):
     with torch.cuda.stream(stream):
         r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=1 << 20, stream=stream)
     stream.synchronize()
+    snap = r.snapshot()
     for _ in range(3):                                           # warm-up launches
         pe.pe_step_ex([r.handle], 1, steps_per_launch=1)
+    with torch.cuda.stream(stream):
+        r.restore(snap)
     r.rebind(tables)
+    del snap
     stream.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     K = cfg["steps"]
