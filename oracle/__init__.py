@@ -70,7 +70,8 @@ class RunParams(C.Structure):
                 ("dt_over_T", C.c_double), ("init_dist", C.c_int), ("T_mev", C.c_double),
                 ("beam_gamma", C.c_double), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("enable_ncs", C.c_int), ("enable_brems", C.c_int), ("box_enable", C.c_int),
-                ("box_x_m", C.c_double * 2), ("iz", C.c_int)]
+                ("box_x_m", C.c_double * 2), ("iz", C.c_int), ("reflect_r", C.c_double),
+                ("mirror_x_m", C.c_double), ("brems_method", C.c_int)]
 
 
 def lib():
@@ -109,10 +110,11 @@ def lib():
             L.or_ncs_h_interp.restype = C.c_double
             L.or_brems_sigma_interp.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int)]
             L.or_brems_sigma_interp.restype = C.c_double
-            L.or_init.argtypes = [C.c_void_p, C.POINTER(RunParams), C.POINTER(C.c_int64), C.c_int64, dp]
+            u32p = C.POINTER(C.c_uint32)
+            L.or_init.argtypes = [C.c_void_p, C.POINTER(RunParams), C.POINTER(C.c_int64), C.c_int64, dp, u32p]
             L.or_init.restype = C.c_int
             L.or_run.argtypes = [C.c_void_p, C.POINTER(RunParams), C.POINTER(C.c_int64), C.c_int64,
-                                 C.c_int64, C.c_int64, dp, C.c_void_p, C.c_int64,
+                                 C.c_int64, C.c_int64, dp, u32p, C.c_void_p, C.c_int64,
                                  C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                  C.POINTER(C.c_uint64), C.c_int]
             L.or_run.restype = C.c_int
@@ -120,6 +122,8 @@ def lib():
             L.or_eta.argtypes = [dp, dp, dp, C.c_double]
             L.or_eta.restype = C.c_double
             L.or_boris.argtypes = [dp, dp, dp, C.c_double]
+            L.or_null_x_hat.argtypes = [C.c_void_p, C.POINTER(RunParams)]
+            L.or_null_x_hat.restype = C.c_double
             _lib = L
     return _lib
 
@@ -212,21 +216,33 @@ class Tables:
         return v, f.value
 
 
-def init(tables: Tables, run: RunParams, ids) -> np.ndarray:
+def _wait_ptr(run: RunParams, wait, n: int):
+    if wait is None:
+        if run.brems_method == 1 and n > 0:
+            raise ValueError("the null-collision method needs a wait array (uint32, one per particle)")
+        return None
+    assert wait.dtype == np.uint32 and wait.flags.c_contiguous and wait.shape == (n,)
+    return wait.ctypes.data_as(C.POINTER(C.c_uint32))
+
+
+def init(tables: Tables, run: RunParams, ids, wait=None) -> np.ndarray:
+    """Initial state (n x 6).  For the null-collision brems method ``wait`` (uint32,
+    one per particle) receives the steps to each particle's first candidate."""
     ids = np.ascontiguousarray(ids, dtype=np.int64)
     st = np.zeros((len(ids), 6), dtype=np.float64)
-    rc = lib().or_init(tables._h, C.byref(run), ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids), _dp(st))
+    rc = lib().or_init(tables._h, C.byref(run), ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids), _dp(st),
+                       _wait_ptr(run, wait, len(ids)))
     if rc != 0:
         raise RuntimeError("or_init failed")
     return st
 
 
 def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
-        capacity: int = 1 << 20, threads: int | None = None, events=None):
+        capacity: int = 1 << 20, threads: int | None = None, events=None, wait=None):
     """Advance ``state`` (n x 6, in place); return (photons, true photon count, hist, tally).
 
     ``events`` (optional uint64 array, one per particle) accumulates each particle's
-    event fingerprint (see oracle.h)."""
+    event fingerprint (see oracle.h); ``wait`` is the null-collision wait array (in/out)."""
     ids = np.ascontiguousarray(ids, dtype=np.int64)
     assert state.dtype == np.float64 and state.flags.c_contiguous and state.shape == (len(ids), 6)
     photons = np.zeros(capacity, dtype=PHOTON_DTYPE)
@@ -235,7 +251,8 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
     n_ph = C.c_int64(0)
     nt = threads if threads else (os.cpu_count() or 1)
     rc = lib().or_run(tables._h, C.byref(run), ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids),
-                      step0, n_steps, _dp(state), photons.ctypes.data_as(C.c_void_p), capacity,
+                      step0, n_steps, _dp(state), _wait_ptr(run, wait, len(ids)),
+                      photons.ctypes.data_as(C.c_void_p), capacity,
                       C.byref(n_ph), hist.ctypes.data_as(C.POINTER(C.c_uint64)),
                       tally.ctypes.data_as(C.POINTER(C.c_uint64)),
                       events.ctypes.data_as(C.POINTER(C.c_uint64)) if events is not None else None, nt)
@@ -247,6 +264,11 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
 def fixed_to_float(tally: np.ndarray, idx: int) -> float:
     """Value of a 128-bit fixed-point tally pair (lo, hi) in m c^2."""
     return float(int(tally[idx + 1])) + float(int(tally[idx])) / 2.0 ** 64
+
+
+def null_x_hat(tables: Tables, run: RunParams) -> float:
+    """Majorant optical depth per step of the null-collision method."""
+    return lib().or_null_x_hat(tables._h, C.byref(run))
 
 
 def fields(run: RunParams, x: float, y: float, t: float):

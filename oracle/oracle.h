@@ -99,7 +99,14 @@ typedef struct {
     int enable_ncs, enable_brems;
     int box_enable; double box_x_m[2];   /* absorbing box in x                  */
     int iz;                              /* index of Z in the table set         */
+    /* reflected wave (OR_PLANE_1D): the incident pulse plus its mirror image in
+     * the plane x = mirror_x_m with amplitude coefficient reflect_r (0 = none) */
+    double reflect_r, mirror_x_m;
+    int brems_method;                    /* OR_BREMS_DIRECT | OR_BREMS_NULL     */
 } or_run_params;
+enum { OR_BREMS_DIRECT = 0, OR_BREMS_NULL = 1 };
+/* wait value meaning "no further candidate collision in this run"            */
+#define OR_WAIT_NEVER 0xFFFFFFFFu
 
 /* photon record, 32 bytes */
 typedef struct {
@@ -121,15 +128,17 @@ enum {
 #define OR_HIST_T_BINS 180
 #define OR_HIST_WORDS (2 * OR_HIST_E_BINS + 2 * OR_HIST_T_BINS)
 
-/* Initial state of the listed particles (x, y, ux, uy, uz, tau per particle). */
+/* Initial state of the listed particles (x, y, ux, uy, uz, tau per particle).
+ * wait (one per particle) receives the steps to the first candidate collision
+ * of the null-collision brems method; it may be NULL for OR_BREMS_DIRECT.    */
 int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
-            double* state);
+            double* state, uint32_t* wait);
 /* Advance the listed particles from step0 for n_steps.  state is in/out (6
  * doubles per particle).  Photons of these particles are written in particle
  * order to photons[0..cap); *n_photons receives the true count.  hist and
  * tally are accumulated (not cleared).  Returns 0 on success.                 */
 int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
-           int64_t step0, int64_t n_steps, double* state,
+           int64_t step0, int64_t n_steps, double* state, uint32_t* wait,
            or_photon* photons, int64_t cap, int64_t* n_photons,
            uint64_t* hist, uint64_t* tally, uint64_t* events, int n_threads);
 /* events (nullable): per particle, low 32 bits = NCS count | brems count << 16,
@@ -140,6 +149,8 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */
 double or_critical_density(double lambda_m);  /* n_c in m^-3                   */
 void or_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]);
+/* majorant of the null-collision method: x_hat = n_i max_gamma(sigma_Z) c dt  */
+double or_null_x_hat(const or_tables* t, const or_run_params* r);
 double or_eta(const double u[3], const double E[3], const double B[3], double E_S);
 void or_boris(double u[3], const double E[3], const double B[3], double dt);
 

@@ -52,7 +52,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /* purposes of the per-particle Philox streams */
-enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4 };
+enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4, PUR_WAIT = 256 };
 
 static void draw(const or_run_params* r, int64_t id, uint32_t step, uint32_t purpose, uint32_t w[4]) {
     uint32_t ctr[4] = {(uint32_t)id, r->run_id, step, purpose};
@@ -105,7 +105,7 @@ static void envelope(const or_run_params* r, double phi, double* g, double* dg) 
     *dg = -(0.5 * M_PI / pr) * sin(M_PI * q / pr);
 }
 
-void or_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]) {
+static void incident_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]) {
     E[0] = E[1] = E[2] = 0.0;
     B[0] = B[1] = B[2] = 0.0;
     if (r->geometry == OR_CONST) {
@@ -144,6 +144,37 @@ void or_fields(const or_run_params* r, double x, double y, double t, double E[3]
         if (r->geometry == OR_GAUSS_2D)
             B[0] = a0 * g * S * (2.0 * y * inv_w2 * ct - y * inv_R * st);
     }
+}
+
+static void add_reflected(const or_run_params* r, double x, double t, double E[3], double B[3]);
+void or_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]) {
+    incident_fields(r, x, y, t, E, B);
+    if (r->geometry == OR_PLANE_1D && r->reflect_r != 0.0) add_reflected(r, x, t, E, B);
+}
+
+/* Transverse E of the 1D plane pulse at phase p (the y and z components above). */
+static void plane_e(const or_run_params* r, double p, double* ey, double* ez) {
+    double g, dg;
+    envelope(r, p, &g, &dg);
+    double st = sin(p), ct = cos(p);
+    *ey = -r->a0 * (dg * st + g * ct);
+    *ez = (r->polarisation == OR_CP) ? r->a0 * (dg * ct - g * st) : 0.0;
+}
+
+/* Reflected wave: the mirror image of the incident vector potential in the
+ * plane x = x_m, A_r(t, x) = -r A(t + x - 2 x_m).  It travels along -x, so
+ * E_r = -r e(psi) with psi = t + x - 2 x_m and B_r = -x^ cross E_r; for r = 1
+ * the transverse E vanishes on the mirror plane at all times.                */
+static void add_reflected(const or_run_params* r, double x, double t, double E[3], double B[3]) {
+    double kl = 2.0 * M_PI / r->lambda_m;
+    double psi = t + x - 2.0 * r->mirror_x_m * kl;
+    double ey, ez;
+    plane_e(r, psi, &ey, &ez);
+    double ery = -r->reflect_r * ey, erz = -r->reflect_r * ez;
+    E[1] += ery;
+    E[2] += erz;
+    B[1] += erz;
+    B[2] -= ery;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -203,11 +234,39 @@ static void fx_add(uint64_t* w, double v) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Null-collision bremsstrahlung (the speed-up the paper names for the MC    */
+/* collision, Sec. 4; method of Skullerud 1968).  Candidate collisions come  */
+/* from a majorant process that ignores position and energy: per step a      */
+/* candidate with probability P_hat = 1 - exp(-x_hat), x_hat = n_i c dt times */
+/* the largest tabulated sigma_Z (beta <= 1 and the slab indicator <= 1).    */
+/* The steps between candidates are geometric, drawn as floor(-ln U/x_hat).  */
+/* A candidate becomes a collision with probability P/P_hat, P the Eq. 4     */
+/* probability of the step, so a collision happens in a step with            */
+/* probability P exactly, as in the direct method.                           */
+/* ------------------------------------------------------------------------- */
+extern double or__sigma_max(const or_tables* t, int iz);
+double or_null_x_hat(const or_tables* t, const or_run_params* r) {
+    double kl = 2.0 * M_PI / r->lambda_m;
+    double dt = r->dt_over_T * 2.0 * M_PI;
+    double n_i = r->ne_over_nc * or_critical_density(r->lambda_m) / r->charge_state;
+    double smax = or__sigma_max(t, r->iz);
+    return n_i * C_ALPHA * C_RE * C_RE * (dt / kl) * smax;
+}
+/* steps to the next candidate: floor(-ln U / x_hat), OR_WAIT_NEVER when that
+ * does not fit in 32 bits (or x_hat = 0)                                    */
+static uint32_t wait_draw(double x_hat, uint64_t v) {
+    double q = -log(u53(v)) / x_hat;
+    if (!(q < 4294967295.0)) return OR_WAIT_NEVER;
+    return (uint32_t)floor(q);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Run context                                                               */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     double dt, E_S, C_ncs, K_br, x0, x1, yh, box0, box1, log_emax;
     double photon_min;
+    double x_hat, P_hat;          /* null-collision majorant (brems_method NULL) */
 } run_ctx;
 
 static void make_ctx(const or_tables* t, const or_run_params* r, run_ctx* c, double photon_min) {
@@ -226,13 +285,16 @@ static void make_ctx(const or_tables* t, const or_run_params* r, run_ctx* c, dou
     c->box1 = r->box_x_m[1] * kl;
     c->log_emax = log(HIST_EMAX_MEV / C_MEC2_MEV);
     c->photon_min = photon_min;
-    (void)t;
+    c->x_hat = or_null_x_hat(t, r);
+    c->P_hat = -expm1(-c->x_hat);
 }
 
 /* table params are needed for photon_min; fetch through the export API */
 extern double or__photon_min(const or_tables* t);
 
-int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids, double* st) {
+int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids, double* st,
+            uint32_t* wait) {
+    if (r->brems_method == OR_BREMS_NULL && !wait && n_ids > 0) return -1;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
     double theta = r->T_mev / C_MEC2_MEV;
@@ -267,6 +329,10 @@ int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int6
         }
         draw(r, id, 0, PUR_TAU0, w);
         s[5] = -log(u53(word64(w[0], w[1])));
+        if (r->brems_method == OR_BREMS_NULL) {
+            draw(r, id, 0, PUR_WAIT, w);
+            wait[k] = wait_draw(c.x_hat, word64(w[0], w[1]));
+        }
     }
     return 0;
 }
@@ -318,8 +384,8 @@ static void note_event(uint64_t* ev, int64_t n, int mech) {
 }
 
 static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c, int64_t id,
-                    int64_t step0, int64_t n_steps, double* s, plist* pl, uint64_t* hist, uint64_t* tally,
-                    uint64_t* ev) {
+                    int64_t step0, int64_t n_steps, double* s, uint32_t* wait, plist* pl, uint64_t* hist,
+                    uint64_t* tally, uint64_t* ev) {
     double x = s[0], y = s[1];
     double u[3] = {s[2], s[3], s[4]};
     double tau = s[5];
@@ -365,18 +431,27 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
         if (r->enable_brems) {
             int in_slab = (x >= c->x0 && x <= c->x1);
             if (r->geometry == OR_GAUSS_2D && fabs(y) > c->yh) in_slab = 0;
-            if (in_slab && gamma > 1.0 + c->photon_min) {
-                int above;
-                double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
-                if (above) tally[ORT_N_GAMMA_ABOVE]++;
-                double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                double xb = c->K_br * sig * (um / gamma);
-                double P = -expm1(-xb);
+            int nullc = (r->brems_method == OR_BREMS_NULL);
+            /* direct method: every step in the slab is a test (Eq. 4); null
+             * collisions: only the candidate steps of the majorant process  */
+            int test = nullc ? (*wait == 0) : (in_slab && gamma > 1.0 + c->photon_min);
+            if (nullc && !test && *wait != OR_WAIT_NEVER) --*wait;
+            if (test) {
+                double P = 0.0;                  /* Eq. 4 probability of this step */
+                if (in_slab && gamma > 1.0 + c->photon_min) {
+                    int above;
+                    double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
+                    if (above) tally[ORT_N_GAMMA_ABOVE]++;
+                    double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    double xb = c->K_br * sig * (um / gamma);
+                    P = -expm1(-xb);
+                }
+                double p_acc = nullc ? P / c->P_hat : P;
                 uint32_t w[4];
                 draw(r, id, (uint32_t)n, PUR_BREMS, w);
                 uint64_t U = word64(w[0], w[1]);
-                uint64_t thr = (uint64_t)floor(P * 18446744073709551616.0);
-                if (P >= 1.0) thr = UINT64_MAX;
+                uint64_t thr = (uint64_t)floor(p_acc * 18446744073709551616.0);
+                if (p_acc >= 1.0) thr = UINT64_MAX;
                 if (U < thr) {
                     double yy = or_sample_brems_y(t, r->iz, gamma, u53(word64(w[2], w[3])));
                     double ew = yy * gamma;
@@ -396,6 +471,10 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
                     }
                     gamma = gn;
                 }
+                if (nullc) {
+                    draw(r, id, (uint32_t)n + 1u, PUR_WAIT, w);
+                    *wait = wait_draw(c->x_hat, word64(w[0], w[1]));
+                }
             }
         }
         x += c->dt * u[0] / gamma;
@@ -410,10 +489,11 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
 }
 
 int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64_t n_ids,
-           int64_t step0, int64_t n_steps, double* state,
+           int64_t step0, int64_t n_steps, double* state, uint32_t* wait,
            or_photon* photons, int64_t cap, int64_t* n_photons,
            uint64_t* hist, uint64_t* tally, uint64_t* events, int n_threads) {
     if (!t || !r || n_ids < 0 || n_steps < 0) return -1;
+    if (r->brems_method == OR_BREMS_NULL && !wait && n_ids > 0) return -1;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
     plist* lists = (plist*)calloc(n_ids > 0 ? n_ids : 1, sizeof(plist));
@@ -426,7 +506,7 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
 #ifdef _OPENMP
         me = omp_get_thread_num();
 #endif
-        run_one(t, r, &c, ids[k], step0, n_steps, state + 6 * k, &lists[k],
+        run_one(t, r, &c, ids[k], step0, n_steps, state + 6 * k, wait ? wait + k : NULL, &lists[k],
                 th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS,
                 events ? events + k : NULL);
     }

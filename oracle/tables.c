@@ -322,6 +322,13 @@ void or_tables_free(or_tables* t) {
 
 double or_tables_classical_total(const or_tables* t) { return t->cl_total; }
 double or__photon_min(const or_tables* t) { return t->p.photon_min; }
+/* largest tabulated sigma_Z of table iz (the interpolant never exceeds it) */
+double or__sigma_max(const or_tables* t, int iz) {
+    const double* s = t->sigma + (int64_t)iz * t->p.n_E;
+    double m = 0.0;
+    for (int i = 0; i < t->p.n_E; ++i) if (s[i] > m) m = s[i];
+    return m;
+}
 
 int64_t or_tables_export(const or_tables* t, int which, int iz, double* out, int64_t cap) {
     const or_table_params* p = &t->p;
