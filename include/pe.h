@@ -56,6 +56,8 @@ enum { PE_LP_Y = 0, PE_CP = 1 };                          /* polarisation       
 enum { PE_PLANE_1D = 0, PE_GAUSS_2D = 1, PE_CONST = 2 };  /* field geometry              */
 enum { PE_F64 = 0, PE_F32 = 1 };                          /* arithmetic of the step      */
 enum { PE_REST = 0, PE_MAXWELL_JUTTNER = 1, PE_BEAM = 2, PE_CALLER = 3 };  /* initial state */
+enum { PE_BREMS_DIRECT = 0, PE_BREMS_NULL = 1 };          /* bremsstrahlung MC method    */
+#define PE_WAIT_NEVER 0xFFFFFFFFu   /* brems_wait value: no further candidate in this run */
 
 #define PE_HIST_E_BINS 512    /* log bins of photon energy over [0.511 MeV, 10 GeV]      */
 #define PE_HIST_T_BINS 180    /* bins of theta = atan2(k_y, k_x) over [-pi, pi)          */
@@ -112,6 +114,24 @@ typedef struct {
     int enable_ncs, enable_brems;
     int box_enable;                  /* absorbing boundary in x (Sec. 3), default off               */
     double box_x_m[2];
+    /* Reflected wave (PE_PLANE_1D only): the incident pulse plus its mirror
+     * image in the plane x = mirror_x_m, A_r(t, x) = -reflect_r A(t + x - 2 x_m),
+     * a fixed stand-in for the reflecting plasma surface of Sec. 3.  The image
+     * travels along -x; for reflect_r = 1 the transverse E vanishes on the plane.
+     * The fields are not cut at the plane.  reflect_r in [0, 1], 0 = no
+     * reflected wave.                                                           */
+    double reflect_r, mirror_x_m;
+    /* PE_BREMS_DIRECT: the test of Eq. 4 in every step in the slab.
+     * PE_BREMS_NULL: null collisions (the speed-up Sec. 4 names for the MC
+     * collision): candidates from a majorant process with
+     * x_hat = n_i c dt max_gamma sigma_Z per step, independent of position and
+     * energy; the steps between candidates are geometric, floor(-ln U / x_hat),
+     * kept per particle in pe_buffers.brems_wait; a candidate is a collision
+     * with probability P / (1 - exp(-x_hat)), P the Eq. 4 probability of the
+     * step, so collisions have the law of the direct method.  Philox purposes:
+     * 0 at the candidate step (acceptance, photon energy), 256 at step 0 (first
+     * wait) and at candidate step + 1 (next wait).                               */
+    int brems_method;
 } pe_run_params;
 
 /* Caller-owned device buffers of one run.
@@ -133,6 +153,10 @@ typedef struct {
  *                      NCS emissions | brems emissions << 16, high 32 bits =
  *                      sum over emissions of (step + 1) * (1, or 0x9E3779B1 for
  *                      brems) mod 2^32.  Used to compare event lists.
+ *   brems_wait       : n uint32, steps to each particle's next candidate
+ *                      collision (PE_WAIT_NEVER: none); written by
+ *                      pe_init_particles, required for PE_BREMS_NULL, ignored
+ *                      (may be NULL) for PE_BREMS_DIRECT.
  * Pointers must be 16-byte aligned.                                            */
 typedef struct {
     void *x, *y, *ux, *uy, *uz, *tau;
@@ -141,6 +165,7 @@ typedef struct {
     void* hist;
     void* tally;
     void* events;
+    void* brems_wait;
 } pe_buffers;
 
 /* Launch shape of the persistent FP32 kernel (the autotuner's knobs).
@@ -184,10 +209,13 @@ pe_status pe_tables_export(const pe_tables* tables, int which, int iz, double* h
  * initial positions (uniform in the slab; a beam starts at the slab's front
  * face) and momenta (rest, Maxwell-Juttner by Sobol's rejection, or a beam
  * along +x) from the particle's Philox
- * stream; always draws the initial optical depth tau = -ln U.  Zeroes hist,
+ * stream; always draws the initial optical depth tau = -ln U and, for
+ * PE_BREMS_NULL, the first candidate wait.  Zeroes hist,
  * tally and the photon count.  Asynchronous on cuda_stream.  The run refers
  * to tables, which must outlive it.  Z must be one of the table set's Z.
- * Errors: PE_ERR_ARG (null, n < 0, n >= 2^31, Z not in tables, misaligned).  */
+ * Errors: PE_ERR_ARG (null, n < 0, n >= 2^31, Z not in tables, misaligned,
+ * reflect_r outside [0, 1] or set for a geometry other than PE_PLANE_1D,
+ * unknown brems_method, PE_BREMS_NULL without brems_wait).                   */
 pe_status pe_init_particles(const pe_tables* tables, const pe_run_params* params, int64_t n,
                             const pe_buffers* buffers, void* cuda_stream, pe_run** out);
 

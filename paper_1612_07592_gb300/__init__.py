@@ -24,6 +24,8 @@ PE_LP_Y, PE_CP = 0, 1
 PE_PLANE_1D, PE_GAUSS_2D, PE_CONST = 0, 1, 2
 PE_F64, PE_F32 = 0, 1
 PE_REST, PE_MAXWELL_JUTTNER, PE_BEAM, PE_CALLER = 0, 1, 2, 3
+PE_BREMS_DIRECT, PE_BREMS_NULL = 0, 1
+PE_WAIT_NEVER = 0xFFFFFFFF
 HIST_E_BINS, HIST_T_BINS = 512, 180
 HIST_WORDS = 2 * HIST_E_BINS + 2 * HIST_T_BINS
 TALLY_WORDS = 32
@@ -60,14 +62,15 @@ class RunParams(C.Structure):
                 ("dt_over_T", C.c_double), ("precision", C.c_int), ("init_dist", C.c_int),
                 ("T_mev", C.c_double), ("beam_gamma", C.c_double), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("enable_ncs", C.c_int), ("enable_brems", C.c_int),
-                ("box_enable", C.c_int), ("box_x_m", C.c_double * 2)]
+                ("box_enable", C.c_int), ("box_x_m", C.c_double * 2), ("reflect_r", C.c_double),
+                ("mirror_x_m", C.c_double), ("brems_method", C.c_int)]
 
 
 class Buffers(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
                 ("uz", C.c_void_p), ("tau", C.c_void_p), ("photons", C.c_void_p),
                 ("photon_capacity", C.c_int64), ("hist", C.c_void_p), ("tally", C.c_void_p),
-                ("events", C.c_void_p)]
+                ("events", C.c_void_p), ("brems_wait", C.c_void_p)]
 
 
 class LaunchConfig(C.Structure):
@@ -252,13 +255,18 @@ class Run:
         self.hist = torch.zeros(HIST_WORDS, dtype=torch.int64, device=dev)
         self.tally = torch.zeros(TALLY_WORDS, dtype=torch.int64, device=dev)
         self.events = torch.zeros(m, dtype=torch.int64, device=dev) if events else None
+        # null-collision brems: steps to each particle's next candidate (uint32 words)
+        self.wait = torch.zeros(m, dtype=torch.int32, device=dev) if params.brems_method == PE_BREMS_NULL else None
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self.params = params
-        b = Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),
-                    self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
-                    self.hist.data_ptr(), self.tally.data_ptr(),
-                    self.events.data_ptr() if events else None)
-        self.handle = pe_init_particles(tables, params, self.n, b, self.stream.cuda_stream)
+        self.handle = pe_init_particles(tables, params, self.n, self._buffers(), self.stream.cuda_stream)
+
+    def _buffers(self) -> Buffers:
+        return Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),
+                       self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
+                       self.hist.data_ptr(), self.tally.data_ptr(),
+                       self.events.data_ptr() if self.events is not None else None,
+                       self.wait.data_ptr() if self.wait is not None else None)
 
     def rebind(self, tables: int, precision_params: RunParams | None = None):
         """Replace the run handle by a fresh one on the same buffers (caller-provided state,
@@ -266,20 +274,20 @@ class Run:
         p = precision_params if precision_params is not None else self.params
         q = RunParams.from_buffer_copy(p)
         q.init_dist = PE_CALLER
-        b = Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),
-                    self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
-                    self.hist.data_ptr(), self.tally.data_ptr(),
-                    self.events.data_ptr() if self.events is not None else None)
         old = self.handle
-        self.handle = pe_init_particles(tables, q, self.n, b, self.stream.cuda_stream)
+        self.handle = pe_init_particles(tables, q, self.n, self._buffers(), self.stream.cuda_stream)
         if old:
             pe_destroy(old)
 
+    def _state_tensors(self):
+        ts = [self.x, self.y, self.ux, self.uy, self.uz, self.tau]
+        return ts + ([self.wait] if self.wait is not None else [])
+
     def snapshot(self):
-        return [t.clone() for t in (self.x, self.y, self.ux, self.uy, self.uz, self.tau)]
+        return [t.clone() for t in self._state_tensors()]
 
     def restore(self, snap):
-        for dst, src in zip((self.x, self.y, self.ux, self.uy, self.uz, self.tau), snap):
+        for dst, src in zip(self._state_tensors(), snap):
             dst.copy_(src)
 
     def state(self) -> np.ndarray:
@@ -304,6 +312,10 @@ class Run:
 
     def event_words(self) -> np.ndarray:
         return self.events[:self.n].cpu().numpy().view(np.uint64)
+
+    def wait_words(self) -> np.ndarray:
+        """Null-collision waits (uint32, PE_WAIT_NEVER = no further candidate)."""
+        return self.wait[:self.n].cpu().numpy().view(np.uint32)
 
     def tally_out(self) -> TallyOut:
         return pe_tally(self.handle)

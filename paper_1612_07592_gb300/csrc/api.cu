@@ -185,6 +185,13 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     if (rp->geometry == PE_GAUSS_2D && !(rp->w0_m > 0)) return fail(PE_ERR_ARG, "pe_init_particles: w0");
     if (rp->init_dist == PE_MAXWELL_JUTTNER && !(rp->T_mev > 0)) return fail(PE_ERR_ARG, "pe_init_particles: T_mev");
     if (rp->init_dist == PE_BEAM && !(rp->beam_gamma >= 1)) return fail(PE_ERR_ARG, "pe_init_particles: beam_gamma");
+    if (!(rp->reflect_r >= 0 && rp->reflect_r <= 1)) return fail(PE_ERR_ARG, "pe_init_particles: reflect_r must be in [0, 1]");
+    if (rp->reflect_r > 0 && rp->geometry != PE_PLANE_1D)
+        return fail(PE_ERR_ARG, "pe_init_particles: a reflected wave needs geometry PE_PLANE_1D");
+    if (rp->brems_method != PE_BREMS_DIRECT && rp->brems_method != PE_BREMS_NULL)
+        return fail(PE_ERR_ARG, "pe_init_particles: brems_method");
+    if (rp->brems_method == PE_BREMS_NULL && n > 0 && (!b->brems_wait || !aligned16(b->brems_wait)))
+        return fail(PE_ERR_ARG, "pe_init_particles: PE_BREMS_NULL needs a 16-byte aligned brems_wait buffer");
     if (n > 0) {
         if (!b->x || !b->y || !b->ux || !b->uy || !b->uz || !b->tau || !b->hist || !b->tally)
             return fail(PE_ERR_ARG, "pe_init_particles: null buffer");
@@ -241,6 +248,18 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     c.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
     c.k_env = 0.5 * kPi / c.phi_r;
     for (int k = 0; k < 3; ++k) { c.E_const[k] = rp->E_const[k]; c.B_const[k] = rp->B_const[k]; }
+    c.refl_r = rp->reflect_r;
+    const double xm2 = 2.0 * rp->mirror_x_m * kl;
+    c.xm2_hi = (double)(float)xm2;                 // an exact float, remainder below
+    c.xm2_lo = xm2 - c.xm2_hi;
+    // null collisions: majorant from the largest tabulated sigma_Z (beta <= 1)
+    double smax = 0;
+    for (int i = 0; i < t->host.p.n_E; ++i) smax = std::max(smax, t->host.sigma[(size_t)iz * t->host.p.n_E + i]);
+    d.x_hat = c.K_br * smax;
+    c.P_hat = -std::expm1(-d.x_hat);
+    d.brems_method = rp->brems_method;
+    d.wait = rp->brems_method == PE_BREMS_NULL ? static_cast<uint32_t*>(b->brems_wait) : nullptr;
+    d.fk = field_kind(rp->geometry, rp->polarisation, rp->reflect_r > 0);
     d.geometry = rp->geometry;
     d.polarisation = rp->polarisation;
     d.enable_ncs = rp->enable_ncs;
@@ -315,10 +334,10 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
                      ? cfg->ctas_per_sm
                      : 2 * (prec == PE_F32 ? persistent_occupancy_f32(block, smem) : persistent_occupancy_f64(block, smem));
     if (per_sm < 1) per_sm = 1;
-    for (int fk = 0; fk <= 4; ++fk) {
+    for (int fk = 0; fk < kFieldKinds; ++fk) {
         std::vector<int> idx;
         for (int k = 0; k < n_runs; ++k)
-            if (field_kind(runs[k]->dev.geometry, runs[k]->dev.polarisation) == fk) idx.push_back(k);
+            if (runs[k]->dev.fk == fk) idx.push_back(k);
         if (idx.empty()) continue;
         int m = (int)idx.size();
         int64_t tile_start[PE_MAX_BATCH + 1];

@@ -59,6 +59,9 @@ struct StepC {
     R inv_log_emax;           // 1 / ln(E_hist_max / m c^2)
     R a0, w0, zr, xf, phi_r, phi_f, k_env;   // fields; k_env = pi / (2 phi_r)
     R E_const[3], B_const[3];
+    R refl_r;                 // reflected wave amplitude coefficient
+    R xm2_hi, xm2_lo;         // 2 x_m (mirror plane) as hi + lo: in float an exact pair
+    R P_hat;                  // null collisions: candidate probability 1 - exp(-x_hat) per step
 };
 
 // Device view of one run.  Optical depth: double for PE_F64, a float pair
@@ -80,6 +83,10 @@ struct RunDevT {
     int iz;                       // brems table index
     uint32_t run_id;
     uint32_t seed_lo, seed_hi;
+    int fk;                       // field kind (physics.cuh)
+    int brems_method;             // PE_BREMS_DIRECT | PE_BREMS_NULL
+    uint32_t* wait;               // null collisions: steps to the next candidate
+    double x_hat;                 // null collisions: majorant optical depth per step (both precisions)
 };
 using RunDev = RunDevT<double>;
 
@@ -103,6 +110,7 @@ inline RunDevT<float> to_float(const RunDevT<double>& d) {
     f.geometry = d.geometry; f.polarisation = d.polarisation;
     f.enable_ncs = d.enable_ncs; f.enable_brems = d.enable_brems; f.box_enable = d.box_enable;
     f.iz = d.iz; f.run_id = d.run_id; f.seed_lo = d.seed_lo; f.seed_hi = d.seed_hi;
+    f.fk = d.fk; f.brems_method = d.brems_method; f.wait = d.wait; f.x_hat = d.x_hat;
     return f;
 }
 

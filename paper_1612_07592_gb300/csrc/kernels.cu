@@ -20,11 +20,13 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
     if (active) {
         const double* sig = t.sig64 + (size_t)r.iz * t.n_E;
         const uint32_t n = (uint32_t)r.step0;
-        switch (field_kind(r.geometry, r.polarisation)) {
+        switch (r.fk) {
             case FK_PLANE_LP: step_one<double, FK_PLANE_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
             case FK_PLANE_CP: step_one<double, FK_PLANE_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
             case FK_GAUSS_LP: step_one<double, FK_GAUSS_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
             case FK_GAUSS_CP: step_one<double, FK_GAUSS_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_REFL_LP: step_one<double, FK_REFL_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_REFL_CP: step_one<double, FK_REFL_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
             default: step_one<double, FK_CONST>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
         }
         store_particle<double>(r, i, P);
@@ -50,6 +52,10 @@ __global__ void __launch_bounds__(256) k_init(RunDevT<double> r, int init_dist, 
         ((float2*)r.tau)[i] = make_float2(hi, (float)(tau0 - (double)hi));
     } else {
         ((double*)r.tau)[i] = tau0;
+    }
+    if (r.wait) {
+        uint4 v = draw(r, id, 0, PUR_WAIT);
+        r.wait[i] = wait_draw(r.x_hat, v.x, v.y);
     }
     if (init_dist == PE_CALLER) return;
     uint4 p = draw(r, id, 0, PUR_POS);

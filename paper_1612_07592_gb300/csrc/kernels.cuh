@@ -74,6 +74,7 @@ struct Particle {
     R x_lo, y_lo;               // compensation of the float position update (0 in double)
     R tau, tau_lo;              // optical depth; float path keeps it as the pair tau + tau_lo
     uint32_t ev_cnt, ev_hash;   // event fingerprint (only kept when r.events != nullptr)
+    uint32_t wait;              // null collisions: steps to the next candidate
 };
 template <typename R>
 __device__ __forceinline__ void note_event(Particle<R>& P, uint32_t n, int mech) {
@@ -183,6 +184,46 @@ __device__ __forceinline__ void ncs_emit(const TablesDev& t, const RunDevT<R>& r
     tau_draw(P, w);
 }
 
+// Probability of a brems collision in this step, Eq. (4): P = 1 - exp(-x_b) with
+// x_b = n_i sigma_Z(gamma) beta c dt, for an electron in the slab.
+template <typename R>
+__device__ __forceinline__ R brems_prob(const TablesDev& t, const RunDevT<R>& r, const R* sig_tab,
+                                        const Particle<R>& P, R gamma, unsigned long long* tally) {
+    bool above;
+    R sig = sigma_of<R>(t, sig_tab, gamma, above);
+    if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
+    R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    R xb = r.c.K_br * sig * (um / gamma);
+    return -m_expm1(-xb);
+}
+
+// Brems photon (text after Eq. 4): y from sigma(y, E) = sigma(E) R2, k^ = v^,
+// recoil, tallies.  gamma is updated.
+template <typename R>
+__device__ __forceinline__ void brems_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                           Particle<R>& P, R& gamma, R xn, R yn, uint4 w, bool& stored, Photon& ph,
+                                           unsigned long long* hist, unsigned long long* tally) {
+    const R photon_min = tabc<R>(t).photon_min;
+    R yy = sample_y(t, r.iz, gamma, w);
+    R ew = yy * gamma;
+    R k[3];
+    recoil<R>(P.u, gamma, ew, k);
+    note_event<R>(P, n, 1);
+    R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
+    if (ew >= photon_min) {
+        atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
+        fx_add_r(tally + PE_T_E_BR_STORED, ew);
+        hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.c.inv_log_emax);
+        stored = true;
+        ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
+    } else {
+        atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
+        fx_add_r(tally + PE_T_E_BR_BELOW, ew);
+    }
+    gamma = gn;
+}
+
 // Bremsstrahlung direct MC collision (Eq. 4 and the text after it) for an
 // electron in the slab: event test, photon energy, recoil.  gamma is updated.
 template <typename R>
@@ -190,35 +231,34 @@ __device__ __forceinline__ void brems_collide(const TablesDev& t, const RunDevT<
                                               uint32_t id, uint32_t n, Particle<R>& P, R& gamma, R xn, R yn,
                                               bool& stored, Photon& ph, unsigned long long* hist,
                                               unsigned long long* tally) {
-    const StepC<R>& c = r.c;
-    const R photon_min = tabc<R>(t).photon_min;
-    bool above;
-    R sig = sigma_of<R>(t, sig_tab, gamma, above);
-    if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
-    R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-    R xb = c.K_br * sig * (um / gamma);
-    R Pbr = -m_expm1(-xb);
+    R Pbr = brems_prob<R>(t, r, sig_tab, P, gamma, tally);
     uint4 w = draw(r, id, n, PUR_BREMS);
-    if (brems_event(Pbr, w)) {
-        R yy = sample_y(t, r.iz, gamma, w);
-        R ew = yy * gamma;
-        R k[3];
-        recoil<R>(P.u, gamma, ew, k);
-        note_event<R>(P, n, 1);
-        R gn = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-        fx_add_r(tally + PE_T_E_RECOIL_BR, gamma - gn);
-        if (ew >= photon_min) {
-            atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
-            fx_add_r(tally + PE_T_E_BR_STORED, ew);
-            hist_add<R>(hist, tally, 1, ew, k[0], k[1], c.inv_log_emax);
-            stored = true;
-            ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
-        } else {
-            atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
-            fx_add_r(tally + PE_T_E_BR_BELOW, ew);
-        }
-        gamma = gn;
-    }
+    if (brems_event(Pbr, w)) brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, stored, ph, hist, tally);
+}
+
+// steps to the next candidate of the majorant process, floor(-ln U / x_hat), in
+// double in both precisions (once per candidate; the 32-bit count must not move
+// by a step against the FP64 reference)
+__device__ __forceinline__ uint32_t wait_draw(double x_hat, uint32_t lo, uint32_t hi) {
+    double q = -log(uni53(w64(lo, hi))) / x_hat;
+    if (!(q < 4294967295.0)) return PE_WAIT_NEVER;
+    return (uint32_t)floor(q);
+}
+
+// Null-collision candidate (majorant process, see pe.h): a collision with
+// probability P / P_hat (P of Eq. 4, 0 outside the slab), then the next wait.
+template <typename R>
+__device__ __forceinline__ void brems_candidate(const TablesDev& t, const RunDevT<R>& r, const R* sig_tab,
+                                                uint32_t id, uint32_t n, Particle<R>& P, R& gamma, bool in_slab,
+                                                R xn, R yn, bool& stored, Photon& ph, unsigned long long* hist,
+                                                unsigned long long* tally) {
+    R p_acc = 0;
+    if (in_slab && gamma > (R)1 + tabc<R>(t).photon_min)
+        p_acc = brems_prob<R>(t, r, sig_tab, P, gamma, tally) / r.c.P_hat;
+    uint4 w = draw(r, id, n, PUR_BREMS);
+    if (brems_event(p_acc, w)) brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, stored, ph, hist, tally);
+    uint4 v = draw(r, id, n + 1u, PUR_WAIT);
+    P.wait = wait_draw(r.x_hat, v.x, v.y);
 }
 
 // absorbing boundary in x (Sec. 3): the electron is removed (x = NaN)
@@ -259,8 +299,14 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
     if (r.enable_brems) {
         bool in_slab = (xn >= c.x0 && xn <= c.x1);
         if ((G == FK_GAUSS_LP || G == FK_GAUSS_CP) && fabs(yn) > c.yh) in_slab = false;
-        if (in_slab && gamma > (R)1 + photon_min)
+        if (r.brems_method == PE_BREMS_NULL) {
+            if (P.wait == 0u)
+                brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, out.br, out.pb, hist, tally);
+            else if (P.wait != PE_WAIT_NEVER)
+                --P.wait;
+        } else if (in_slab && gamma > (R)1 + photon_min) {
             brems_collide<R>(t, r, sig_tab, id, n, P, gamma, xn, yn, out.br, out.pb, hist, tally);
+        }
     }
 
     advance(P.x, P.x_lo, dt * P.u[0] / gamma);
@@ -320,6 +366,7 @@ __device__ __forceinline__ void load_particle(const RunDevT<R>& r, int64_t i, Pa
     P.u[1] = ((const R*)r.uy)[i];
     P.u[2] = ((const R*)r.uz)[i];
     load_tau(r, i, P);
+    P.wait = r.wait ? r.wait[i] : PE_WAIT_NEVER;
     if (r.events) {
         unsigned long long e = r.events[i];
         P.ev_cnt = (uint32_t)e;
@@ -335,6 +382,7 @@ __device__ __forceinline__ void store_particle(const RunDevT<R>& r, int64_t i, c
     ((R*)r.uy)[i] = P.u[1];
     ((R*)r.uz)[i] = P.u[2];
     store_tau(r, i, P);
+    if (r.wait) r.wait[i] = P.wait;
     if (r.events) r.events[i] = ((unsigned long long)P.ev_hash << 32) | P.ev_cnt;
 }
 

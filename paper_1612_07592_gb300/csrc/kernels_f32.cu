@@ -8,12 +8,13 @@ namespace pe {
 // threads per tile of `block` electrons); the others one electron per thread.
 template <bool kSingle, int G>
 static const void* kernel_of(int block, int& threads) {
-    if (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
         threads = block / 2;
         return (const void*)k_step_pair<kSingle, G>;
+    } else {
+        threads = block;
+        return (const void*)k_step_persistent<float, kSingle, G>;
     }
-    threads = block;
-    return (const void*)k_step_persistent<float, kSingle, G>;
 }
 
 template <bool kSingle, int G>
@@ -22,59 +23,31 @@ static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps,
     int threads;
     const void* f = kernel_of<kSingle, G>(block, threads);
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (G == FK_PLANE_LP || G == FK_PLANE_CP)
-        k_step_pair<kSingle, (G == FK_PLANE_CP ? FK_PLANE_CP : FK_PLANE_LP)><<<grid, threads, smem, s>>>(t, b, steps);
+    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP)
+        k_step_pair<kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
     else
         k_step_persistent<float, kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
 }
 
 void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
                                 cudaStream_t s) {
-    int smem = persistent_smem_bytes(t, PE_F32);
+    const int smem = persistent_smem_bytes(t, PE_F32);
     // all runs of b share one field kind (the caller groups a batch by kind)
-    const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
-    if (b.n_runs == 1) {
-        switch (fk) {
-            case FK_PLANE_LP: launch_one<true, FK_PLANE_LP>(t, b, steps, grid, block, s, smem); break;
-            case FK_PLANE_CP: launch_one<true, FK_PLANE_CP>(t, b, steps, grid, block, s, smem); break;
-            case FK_GAUSS_LP: launch_one<true, FK_GAUSS_LP>(t, b, steps, grid, block, s, smem); break;
-            case FK_GAUSS_CP: launch_one<true, FK_GAUSS_CP>(t, b, steps, grid, block, s, smem); break;
-            default: launch_one<true, FK_CONST>(t, b, steps, grid, block, s, smem); break;
-        }
-        return;
-    }
-    switch (fk) {
-        case FK_PLANE_LP: launch_one<false, FK_PLANE_LP>(t, b, steps, grid, block, s, smem); break;
-        case FK_PLANE_CP: launch_one<false, FK_PLANE_CP>(t, b, steps, grid, block, s, smem); break;
-        case FK_GAUSS_LP: launch_one<false, FK_GAUSS_LP>(t, b, steps, grid, block, s, smem); break;
-        case FK_GAUSS_CP: launch_one<false, FK_GAUSS_CP>(t, b, steps, grid, block, s, smem); break;
-        default: launch_one<false, FK_CONST>(t, b, steps, grid, block, s, smem); break;
-    }
+    with_field_kind(b.runs[0].fk, [&](auto g) {
+        if (b.n_runs == 1) launch_one<true, decltype(g)::value>(t, b, steps, grid, block, s, smem);
+        else launch_one<false, decltype(g)::value>(t, b, steps, grid, block, s, smem);
+    });
 }
 
 // the kernel a launch of these runs uses and its threads per CTA (for graph nodes);
 // sets the shared-memory attribute
 const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem, int block, int* threads) {
-    const int fk = field_kind(b.runs[0].geometry, b.runs[0].polarisation);
     const void* f = nullptr;
     int th = block;
-    if (b.n_runs == 1) {
-        switch (fk) {
-            case FK_PLANE_LP: f = kernel_of<true, FK_PLANE_LP>(block, th); break;
-            case FK_PLANE_CP: f = kernel_of<true, FK_PLANE_CP>(block, th); break;
-            case FK_GAUSS_LP: f = kernel_of<true, FK_GAUSS_LP>(block, th); break;
-            case FK_GAUSS_CP: f = kernel_of<true, FK_GAUSS_CP>(block, th); break;
-            default: f = kernel_of<true, FK_CONST>(block, th); break;
-        }
-    } else {
-        switch (fk) {
-            case FK_PLANE_LP: f = kernel_of<false, FK_PLANE_LP>(block, th); break;
-            case FK_PLANE_CP: f = kernel_of<false, FK_PLANE_CP>(block, th); break;
-            case FK_GAUSS_LP: f = kernel_of<false, FK_GAUSS_LP>(block, th); break;
-            case FK_GAUSS_CP: f = kernel_of<false, FK_GAUSS_CP>(block, th); break;
-            default: f = kernel_of<false, FK_CONST>(block, th); break;
-        }
-    }
+    with_field_kind(b.runs[0].fk, [&](auto g) {
+        f = b.n_runs == 1 ? kernel_of<true, decltype(g)::value>(block, th)
+                          : kernel_of<false, decltype(g)::value>(block, th);
+    });
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     *threads = th;
     return f;

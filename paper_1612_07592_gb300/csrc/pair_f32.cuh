@@ -88,6 +88,7 @@ __device__ __forceinline__ void sincos2(float2 v, float2& s_out, float2& c_out) 
 struct Pair {
     float2 x, x_lo, u0, u1, u2, tau, tau_lo;
     uint32_t ev_cnt[2], ev_hash[2];
+    uint32_t wait[2];
     bool act[2];
 };
 
@@ -98,6 +99,7 @@ __device__ __forceinline__ Particle<float> unpack(const Pair& Q, int k) {
     P.u[0] = comp(Q.u0, k); P.u[1] = comp(Q.u1, k); P.u[2] = comp(Q.u2, k);
     P.tau = comp(Q.tau, k); P.tau_lo = comp(Q.tau_lo, k);
     P.ev_cnt = Q.ev_cnt[k]; P.ev_hash = Q.ev_hash[k];
+    P.wait = Q.wait[k];
     return P;
 }
 __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P) {
@@ -105,6 +107,7 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
     set_comp(Q.u0, k, P.u[0]); set_comp(Q.u1, k, P.u[1]); set_comp(Q.u2, k, P.u[2]);
     set_comp(Q.tau, k, P.tau); set_comp(Q.tau_lo, k, P.tau_lo);
     Q.ev_cnt[k] = P.ev_cnt; Q.ev_hash[k] = P.ev_hash;
+    Q.wait[k] = P.wait;
 }
 
 // one step of two electrons (plane wave, G = FK_PLANE_LP or FK_PLANE_CP)
@@ -200,13 +203,30 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     }
 
     if (r.enable_brems) {
+        if (r.brems_method == PE_BREMS_NULL) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float x = comp(xn, k);
-            if (Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min) {
-                Particle<float> P = unpack(Q, k);
-                brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist, tally);
-                repack(Q, k, P);
+            for (int k = 0; k < 2; ++k) {
+                if (!Q.act[k]) continue;
+                if (Q.wait[k] == 0u) {
+                    const float x = comp(xn, k);
+                    Particle<float> P = unpack(Q, k);
+                    brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], x >= c.x0 && x <= c.x1, x, 0.0f,
+                                           st_br[k], pb[k], hist, tally);
+                    repack(Q, k, P);
+                } else if (Q.wait[k] != PE_WAIT_NEVER) {
+                    --Q.wait[k];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float x = comp(xn, k);
+                if (Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min) {
+                    Particle<float> P = unpack(Q, k);
+                    brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist,
+                                         tally);
+                    repack(Q, k, P);
+                }
             }
         }
     }
@@ -243,6 +263,7 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     Pair Q;
     Q.x = Q.x_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
     Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
+    Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
     Q.act[0] = Q.act[1] = false;
     if (i0 < r.n) load_one(r, i0, Q, 0);
     if (i1 < r.n) load_one(r, i1, Q, 1);

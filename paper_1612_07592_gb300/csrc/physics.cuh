@@ -5,6 +5,7 @@
 // implements.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 #include "internal.h"
@@ -95,7 +96,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     }
     return c;
 }
-enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4 };
+enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4, PUR_WAIT = 256 };
 
 template <typename R>
 __device__ __forceinline__ uint4 draw(const RunDevT<R>& r, uint32_t id, uint32_t step, uint32_t purpose) {
@@ -184,13 +185,53 @@ __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
 }
 __device__ __forceinline__ void advance(double& x, double&, double d) { x += d; }
 
+// phase of the reflected wave t^n + x - 2 x_m, with the same care as phase():
+// n * dt_hi - 2 x_m,hi rounds once, then x, then the small remainders.
+__device__ __forceinline__ double phase_refl(const StepC<double>& c, double nf, double x, double) {
+    return nf * c.dt + x - (c.xm2_hi + c.xm2_lo);
+}
+__device__ __forceinline__ float phase_refl(const StepC<float>& c, float nf, float x, float x_lo) {
+    float a = fmaf(nf, c.dt_hi, -c.xm2_hi);
+    return (a + x) + fmaf(nf, c.dt_lo, x_lo - c.xm2_lo);
+}
+
 // Field kind of a run, a compile-time parameter of the step so that each geometry
 // and polarisation gets its own straight-line code.
-enum { FK_PLANE_LP = 0, FK_PLANE_CP = 1, FK_GAUSS_LP = 2, FK_GAUSS_CP = 3, FK_CONST = 4 };
-__host__ __device__ __forceinline__ int field_kind(int geometry, int polarisation) {
+enum { FK_PLANE_LP = 0, FK_PLANE_CP = 1, FK_GAUSS_LP = 2, FK_GAUSS_CP = 3, FK_CONST = 4, FK_REFL_LP = 5,
+       FK_REFL_CP = 6 };
+constexpr int kFieldKinds = 7;
+__host__ __device__ __forceinline__ int field_kind(int geometry, int polarisation, bool reflected) {
     if (geometry == PE_CONST) return FK_CONST;
     int cp = polarisation == PE_CP ? 1 : 0;
+    if (geometry == PE_PLANE_1D && reflected) return FK_REFL_LP + cp;
     return (geometry == PE_GAUSS_2D ? 2 : 0) + cp;
+}
+
+// host dispatch of a runtime field kind to f(std::integral_constant<int, G>{})
+template <typename F>
+inline void with_field_kind(int fk, F&& f) {
+    switch (fk) {
+        case FK_PLANE_LP: f(std::integral_constant<int, FK_PLANE_LP>{}); break;
+        case FK_PLANE_CP: f(std::integral_constant<int, FK_PLANE_CP>{}); break;
+        case FK_GAUSS_LP: f(std::integral_constant<int, FK_GAUSS_LP>{}); break;
+        case FK_GAUSS_CP: f(std::integral_constant<int, FK_GAUSS_CP>{}); break;
+        case FK_REFL_LP: f(std::integral_constant<int, FK_REFL_LP>{}); break;
+        case FK_REFL_CP: f(std::integral_constant<int, FK_REFL_CP>{}); break;
+        default: f(std::integral_constant<int, FK_CONST>{}); break;
+    }
+}
+
+// transverse E of the 1D plane pulse at phase p: E_y = -a0 (g' sin p + g cos p),
+// and for CP E_z = a0 (g' cos p - g sin p)
+template <typename R, bool kCP>
+__device__ __forceinline__ void plane_e(const StepC<R>& c, R p, R& ey, R& ez) {
+    R g, dg;
+    if constexpr (sizeof(R) == 4) envelope_sel(c, p, g, dg);
+    else envelope<R>(c, p, g, dg);
+    R st, ct;
+    m_sincos(p, &st, &ct);
+    ey = -c.a0 * (dg * st + g * ct);
+    ez = kCP ? c.a0 * (dg * ct - g * st) : (R)0;
 }
 
 template <typename R, int G>
@@ -200,6 +241,20 @@ __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R 
     B[0] = B[1] = B[2] = 0;
     if (G == FK_CONST) {
         for (int k = 0; k < 3; ++k) { E[k] = c.E_const[k]; B[k] = c.B_const[k]; }
+        return;
+    }
+    if (G == FK_REFL_LP || G == FK_REFL_CP) {
+        // incident pulse (B = x^ cross E) plus the mirror image -r e(psi) moving
+        // along -x (B = -x^ cross E)
+        constexpr bool kCP = G == FK_REFL_CP;
+        R ey, ez, fy, fz;
+        plane_e<R, kCP>(c, phase(c, nf, x, x_lo), ey, ez);
+        plane_e<R, kCP>(c, phase_refl(c, nf, x, x_lo), fy, fz);
+        const R ry = -c.refl_r * fy, rz = -c.refl_r * fz;
+        E[1] = ey + ry;
+        E[2] = ez + rz;
+        B[1] = rz - ez;
+        B[2] = ey - ry;
         return;
     }
     R phi = phase(c, nf, x, x_lo);

@@ -63,11 +63,15 @@ def orun(run: dict, Z):
     return O.run_params(**d)
 
 
-def run_oracle(ot, run, Z, ids, steps, step0=0, state=None):
+def run_oracle(ot, run, Z, ids, steps, step0=0, state=None, wait=None):
+    """Oracle run; for the null-collision method ``wait`` (uint32 per particle) carries the
+    candidate waits (filled at init when ``state`` is None)."""
     rp = orun(run, Z)
-    st = O.init(ot, rp, ids) if state is None else state
+    if wait is None and rp.brems_method == pe.PE_BREMS_NULL:
+        wait = np.zeros(len(ids), dtype=np.uint32)
+    st = O.init(ot, rp, ids, wait=wait) if state is None else state
     ev = np.zeros(len(ids), dtype=np.uint64)
-    ph, nph, hist, tally = O.run(ot, rp, ids, st, step0, steps, capacity=1 << 22, events=ev)
+    ph, nph, hist, tally = O.run(ot, rp, ids, st, step0, steps, capacity=1 << 22, events=ev, wait=wait)
     return st, ph, nph, hist, tally, ev
 
 
@@ -148,6 +152,18 @@ CASES = {
                            slab_thick_m=2e-3, enable_ncs=0, seed=9, **W.AU), 500, 800),
     # the paper's bunch benchmark: 100 MeV into 5 mm of fully ionised Au, fields off (Sec. 2.2)
     "bunch-100mev-au-5mm": (dict(W.bunch(100.0, "Au")["run"]), 300, 5000),
+    # the same 1 GeV bunch with null-collision brems (majorant candidates, P/P_hat thinning)
+    "bunch-1gev-au-5mm-null": (dict(W.bunch(1000.0, "Au")["run"], brems_method=1), 300, 5000),
+    # null collisions in the dense fields-off target and under the 1D plane wave (paired kernel)
+    "beam-au-brems-null": (dict(a0=0.0, init_dist=2, beam_gamma=2000.0, ne_over_nc=2e4, slab_x0_m=-1e-3,
+                                slab_thick_m=2e-3, enable_ncs=0, seed=9, brems_method=1, **W.AU), 1000, 1000),
+    "1d-au-a270-dense-null": (dict(a0=270.0, init_dist=1, T_mev=1.0, seed=12, brems_method=1, slab_thick_m=20e-6,
+                                   **dict(W.AU, ne_over_nc=2e4)), 1000, 1500),
+    # reflected wave: the a0 = 270 pulse reflected by a mirror at the slab's rear face (eta ~ 1)
+    "1d-au-a270-refl-lp": (dict(a0=270.0, init_dist=1, T_mev=1.0, seed=2, reflect_r=1.0, mirror_x_m=3e-6,
+                                **W.AU), 1000, 1500),
+    "1d-au-a270-refl-cp": (dict(a0=270.0, polarisation=1, init_dist=1, T_mev=1.0, seed=3, reflect_r=0.8,
+                                mirror_x_m=3e-6, **W.AU), 700, 1500),
 }
 
 
@@ -157,12 +173,15 @@ def test_f64_parity(case):
     run = W.base_run(**runkw)
     Z = (13.0, 79.0)
     lt, ot = tables(_tp(48), Z)
-    st_o, ph_o, nph_o, hist_o, tal_o, ev_o = run_oracle(ot, run, Z, np.arange(n), steps)
+    wait_o = np.zeros(n, dtype=np.uint32) if run.get("brems_method") else None
+    st_o, ph_o, nph_o, hist_o, tal_o, ev_o = run_oracle(ot, run, Z, np.arange(n), steps, wait=wait_o)
     r, out = run_gpu(lt, run, n, steps, pe.PE_F64)
     st = r.state()
     ev = r.event_words()
     assert np.array_equal(ev, ev_o), f"{np.sum(ev != ev_o)} particles with different event lists"
     np.testing.assert_allclose(st, st_o, rtol=F64_RTOL, atol=1e-9)
+    if wait_o is not None:
+        np.testing.assert_array_equal(r.wait_words(), wait_o)
     tal = np.frombuffer(bytes(out.tally), dtype=np.uint64)
     for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED", "N_BR_BELOW", "N_PHOTONS", "N_ETA_ABOVE",
               "N_ETA_BELOW", "N_GAMMA_ABOVE", "N_CLAMP"):
