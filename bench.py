@@ -301,7 +301,9 @@ def main():
         res["e2e"] = e2e(pe, tables, cfg, stream)
         res["workloads"] = {"batch64_graph": batch64(pe, stream, flush),
                             "gauss2d_cp_a855_3e7x2000": gauss2d(pe, stream, flush),
-                            "serving_poisson50hz": serving(pe, stream)}
+                            "serving_poisson50hz": serving(pe, stream),
+                            "bunch_1gev_au_5mm_1e6": bunch_methods(pe, stream, flush),
+                            "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush)}
     if rank == 0 and not args.skip_cpu_baseline:
         threads = os.cpu_count() or 1
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
@@ -448,6 +450,73 @@ def gauss2d(pe, stream, flush):
     r.close()
     pe.pe_destroy_tables(tables)
     return res
+
+
+def _timed_jobs(pe, r, tables, steps, stream, flush, reps=3):
+    """Mean CUDA-event time of reps - 1 jobs (the first is warm-up) from the same initial state."""
+    import torch
+    snap = r.snapshot()
+    times = []
+    for k in range(reps):
+        with torch.cuda.stream(stream):
+            r.restore(snap)
+            flush.fill_(1.0)
+        r.rebind(tables)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.pe_step([r.handle], steps)
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            times.append(e0.elapsed_time(e1))
+    return float(np.mean(times))
+
+
+def bunch_methods(pe, stream, flush, n=1_000_000):
+    """The Sec. 2.2 bunch benchmark: 1 GeV electrons into 5 mm of fully ionised Au, fields off,
+    pusher + brems only, 5000 steps of one laser period; the direct test of Eq. 4 in every step
+    against null collisions, FP32, 1e6 electrons (ten of the paper's 1e5-electron bunches)."""
+    import torch
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.bunch(1000.0, "Au", n=n)
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    out = {}
+    for name, method in (("direct", pe.PE_BREMS_DIRECT), ("null", pe.PE_BREMS_NULL)):
+        with torch.cuda.stream(stream):
+            r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **dict(c["run"], brems_method=method)), n,
+                       capacity=1 << 24, stream=stream)
+        stream.synchronize()
+        ms = _timed_jobs(pe, r, tables, c["steps"], stream, flush)
+        t = r.tally_out()
+        st = r.state()
+        g = np.sqrt(1 + (st[:, 2:5] ** 2).sum(1))
+        g0 = 1000.0 / 0.51099895 + 1.0
+        out[name] = {"value": t.live_particle_steps / (ms * 1e-3), "ms_per_job": ms,
+                     "brems_stored": int(t.tally[pe.T["N_BR_STORED"]]),
+                     "mean_energy_fraction_left": float((g - 1).mean() / (g0 - 1))}
+        r.close()
+    pe.pe_destroy_tables(tables)
+    out.update({"unit": UNIT, "electrons": n, "steps": c["steps"], "speedup_null": out["null"]["value"] /
+                out["direct"]["value"], "kernel": "k_step_persistent (FP32, constant fields)"})
+    return out
+
+
+def reflected(pe, tables, cfg, stream, flush):
+    """The headline 1D Au a0 = 270 job with the pulse reflected by a mirror at the slab's rear face
+    (r = 1): electrons meet the counter-propagating wave and emit at eta ~ 1."""
+    import torch
+    run = dict(cfg["run"], run_id=11, reflect_r=1.0, mirror_x_m=cfg["run"]["slab_x0_m"] + cfg["run"]["slab_thick_m"])
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), cfg["n"], capacity=1 << 28, stream=stream)
+    stream.synchronize()
+    ms = _timed_jobs(pe, r, tables, cfg["steps"], stream, flush)
+    t = r.tally_out()
+    r.close()
+    return {"value": t.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": cfg["n"],
+            "steps": cfg["steps"], "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]),
+            "ncs_below_cut": int(t.tally[pe.T["N_NCS_BELOW"]]), "photons": int(t.tally[pe.T["N_PHOTONS"]]),
+            "kernel": "k_step_persistent (FP32, reflected-wave field kind)"}
 
 
 def serving(pe, stream, n_requests=60):

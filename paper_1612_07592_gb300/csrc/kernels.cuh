@@ -151,12 +151,28 @@ struct StepOut {
     Photon pn, pb;
 };
 
-// NCS emission at a crossing of the optical depth (Sec. 2.2): photon energy by
-// inverse CDF, recoil along u, tallies, new optical depth.  gamma is updated.
+// The emission branches are real calls (__noinline__): compiled once per
+// precision, so every kernel that steps a particle (single run or batch, any
+// launch shape) performs bit-identical emission arithmetic, and the rarely taken
+// code stays out of the step loop's instruction stream.  They take the particle
+// by value and return it (no address of the loop-carried state escapes, so it
+// stays in registers).
 template <typename R>
-__device__ __forceinline__ void ncs_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
-                                         Particle<R>& P, R& gamma, R eta, R xn, R yn, bool& stored, Photon& ph,
-                                         unsigned long long* hist, unsigned long long* tally) {
+struct Emission {
+    Particle<R> P;     // particle after the branch
+    R gamma;           // its Lorentz factor
+    bool stored;       // a photon above the cut was produced
+    Photon ph;
+};
+
+// NCS emission at a crossing of the optical depth (Sec. 2.2): photon energy by
+// inverse CDF, recoil along u, tallies, new optical depth.
+template <typename R>
+__device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                             Particle<R> P, R gamma, R eta, R xn, R yn, unsigned long long* hist,
+                                             unsigned long long* tally) {
+    Emission<R> out;
+    out.stored = false;
     const StepC<R>& c = r.c;
     const R photon_min = tabc<R>(t).photon_min;
     uint4 w = draw(r, id, n, PUR_NCS);
@@ -174,14 +190,16 @@ __device__ __forceinline__ void ncs_emit(const TablesDev& t, const RunDevT<R>& r
         atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
         fx_add_r(tally + PE_T_E_NCS_STORED, ew);
         hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
-        stored = true;
-        ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
+        out.stored = true;
+        out.ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
     } else {
         atomicAdd(tally + PE_T_N_NCS_BELOW, 1ull);
         fx_add_r(tally + PE_T_E_NCS_BELOW, ew);
     }
-    gamma = gn;
     tau_draw(P, w);
+    out.P = P;
+    out.gamma = gn;
+    return out;
 }
 
 // Probability of a brems collision in this step, Eq. (4): P = 1 - exp(-x_b) with
@@ -198,11 +216,13 @@ __device__ __forceinline__ R brems_prob(const TablesDev& t, const RunDevT<R>& r,
 }
 
 // Brems photon (text after Eq. 4): y from sigma(y, E) = sigma(E) R2, k^ = v^,
-// recoil, tallies.  gamma is updated.
+// recoil, tallies.
 template <typename R>
-__device__ __forceinline__ void brems_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
-                                           Particle<R>& P, R& gamma, R xn, R yn, uint4 w, bool& stored, Photon& ph,
-                                           unsigned long long* hist, unsigned long long* tally) {
+__device__ __noinline__ Emission<R> brems_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                               Particle<R> P, R gamma, R xn, R yn, uint4 w, unsigned long long* hist,
+                                               unsigned long long* tally) {
+    Emission<R> out;
+    out.stored = false;
     const R photon_min = tabc<R>(t).photon_min;
     R yy = sample_y(t, r.iz, gamma, w);
     R ew = yy * gamma;
@@ -215,13 +235,24 @@ __device__ __forceinline__ void brems_emit(const TablesDev& t, const RunDevT<R>&
         atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
         fx_add_r(tally + PE_T_E_BR_STORED, ew);
         hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.c.inv_log_emax);
-        stored = true;
-        ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
+        out.stored = true;
+        out.ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
     } else {
         atomicAdd(tally + PE_T_N_BR_BELOW, 1ull);
         fx_add_r(tally + PE_T_E_BR_BELOW, ew);
     }
-    gamma = gn;
+    out.P = P;
+    out.gamma = gn;
+    return out;
+}
+
+// copy an emission branch's result back into the caller's state
+template <typename R>
+__device__ __forceinline__ void take(const Emission<R>& e, Particle<R>& P, R& gamma, bool& stored, Photon& ph) {
+    P = e.P;
+    gamma = e.gamma;
+    stored = e.stored;
+    ph = e.ph;
 }
 
 // Bremsstrahlung direct MC collision (Eq. 4 and the text after it) for an
@@ -233,7 +264,7 @@ __device__ __forceinline__ void brems_collide(const TablesDev& t, const RunDevT<
                                               unsigned long long* tally) {
     R Pbr = brems_prob<R>(t, r, sig_tab, P, gamma, tally);
     uint4 w = draw(r, id, n, PUR_BREMS);
-    if (brems_event(Pbr, w)) brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, stored, ph, hist, tally);
+    if (brems_event(Pbr, w)) take(brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, hist, tally), P, gamma, stored, ph);
 }
 
 // steps to the next candidate of the majorant process, floor(-ln U / x_hat), in
@@ -248,17 +279,21 @@ __device__ __forceinline__ uint32_t wait_draw(double x_hat, uint32_t lo, uint32_
 // Null-collision candidate (majorant process, see pe.h): a collision with
 // probability P / P_hat (P of Eq. 4, 0 outside the slab), then the next wait.
 template <typename R>
-__device__ __forceinline__ void brems_candidate(const TablesDev& t, const RunDevT<R>& r, const R* sig_tab,
-                                                uint32_t id, uint32_t n, Particle<R>& P, R& gamma, bool in_slab,
-                                                R xn, R yn, bool& stored, Photon& ph, unsigned long long* hist,
-                                                unsigned long long* tally) {
+__device__ __noinline__ Emission<R> brems_candidate(const TablesDev& t, const RunDevT<R>& r, const R* sig_tab,
+                                                    uint32_t id, uint32_t n, Particle<R> P, R gamma, bool in_slab,
+                                                    R xn, R yn, unsigned long long* hist, unsigned long long* tally) {
+    Emission<R> out;
+    out.stored = false;
+    out.gamma = gamma;
     R p_acc = 0;
     if (in_slab && gamma > (R)1 + tabc<R>(t).photon_min)
         p_acc = brems_prob<R>(t, r, sig_tab, P, gamma, tally) / r.c.P_hat;
     uint4 w = draw(r, id, n, PUR_BREMS);
-    if (brems_event(p_acc, w)) brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, stored, ph, hist, tally);
+    if (brems_event(p_acc, w)) out = brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, hist, tally);
+    else out.P = P;
     uint4 v = draw(r, id, n + 1u, PUR_WAIT);
-    P.wait = wait_draw(r.x_hat, v.x, v.y);
+    out.P.wait = wait_draw(r.x_hat, v.x, v.y);
+    return out;
 }
 
 // absorbing boundary in x (Sec. 3): the electron is removed (x = NaN)
@@ -293,7 +328,8 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
         tau_sub(P, c.ncs_coef * (eta / gamma) * h);
-        if (tau_crossed(P)) ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, out.ncs, out.pn, hist, tally);
+        if (tau_crossed(P))
+            take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, out.ncs, out.pn);
     }
 
     if (r.enable_brems) {
@@ -301,7 +337,8 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if ((G == FK_GAUSS_LP || G == FK_GAUSS_CP) && fabs(yn) > c.yh) in_slab = false;
         if (r.brems_method == PE_BREMS_NULL) {
             if (P.wait == 0u)
-                brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, out.br, out.pb, hist, tally);
+                take(brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, hist, tally), P, gamma, out.br,
+                     out.pb);
             else if (P.wait != PE_WAIT_NEVER)
                 --P.wait;
         } else if (in_slab && gamma > (R)1 + photon_min) {

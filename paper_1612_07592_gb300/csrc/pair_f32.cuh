@@ -195,8 +195,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         for (int k = 0; k < 2; ++k) {
             if (Q.act[k] && comp(tsum, k) <= 0.0f) {
                 Particle<float> P = unpack(Q, k);
-                ncs_emit<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, st_ncs[k], pn[k], hist,
-                                tally);
+                take(ncs_emit<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, hist, tally), P,
+                     gam[k], st_ncs[k], pn[k]);
                 repack(Q, k, P);
             }
         }
@@ -210,8 +210,9 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 if (Q.wait[k] == 0u) {
                     const float x = comp(xn, k);
                     Particle<float> P = unpack(Q, k);
-                    brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], x >= c.x0 && x <= c.x1, x, 0.0f,
-                                           st_br[k], pb[k], hist, tally);
+                    take(brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], x >= c.x0 && x <= c.x1, x, 0.0f,
+                                                hist, tally),
+                         P, gam[k], st_br[k], pb[k]);
                     repack(Q, k, P);
                 } else if (Q.wait[k] != PE_WAIT_NEVER) {
                     --Q.wait[k];

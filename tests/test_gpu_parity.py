@@ -159,11 +159,14 @@ CASES = {
                                 slab_thick_m=2e-3, enable_ncs=0, seed=9, brems_method=1, **W.AU), 1000, 1000),
     "1d-au-a270-dense-null": (dict(a0=270.0, init_dist=1, T_mev=1.0, seed=12, brems_method=1, slab_thick_m=20e-6,
                                    **dict(W.AU, ne_over_nc=2e4)), 1000, 1500),
-    # reflected wave: the a0 = 270 pulse reflected by a mirror at the slab's rear face (eta ~ 1)
+    # reflected wave: the a0 = 270 pulse reflected by a mirror at the slab's rear face (eta ~ 1).  The
+    # standing wave is chaotic (the oracle pin: in LP a 2^-50 perturbation reaches O(1) by step ~900),
+    # so per-particle parity runs to the horizon where a 1e-15 perturbation stays below ~1e-11
+    # (LP 400 steps, CP r = 0.8 700 steps); the FP32 statistics run longer (test_gpu_variants)
     "1d-au-a270-refl-lp": (dict(a0=270.0, init_dist=1, T_mev=1.0, seed=2, reflect_r=1.0, mirror_x_m=3e-6,
-                                **W.AU), 1000, 1500),
+                                **W.AU), 1000, 400),
     "1d-au-a270-refl-cp": (dict(a0=270.0, polarisation=1, init_dist=1, T_mev=1.0, seed=3, reflect_r=0.8,
-                                mirror_x_m=3e-6, **W.AU), 700, 1500),
+                                mirror_x_m=3e-6, **W.AU), 700, 700),
 }
 
 
@@ -179,7 +182,11 @@ def test_f64_parity(case):
     st = r.state()
     ev = r.event_words()
     assert np.array_equal(ev, ev_o), f"{np.sum(ev != ev_o)} particles with different event lists"
-    np.testing.assert_allclose(st, st_o, rtol=F64_RTOL, atol=1e-9)
+    np.testing.assert_allclose(st[:, [0, 1, 5]], st_o[:, [0, 1, 5]], rtol=F64_RTOL, atol=1e-9)
+    # momenta relative to each electron's momentum scale (a small component of a large u carries
+    # the rounding of |u|)
+    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), 1.0)
+    assert (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u).max() < F64_RTOL
     if wait_o is not None:
         np.testing.assert_array_equal(r.wait_words(), wait_o)
     tal = np.frombuffer(bytes(out.tally), dtype=np.uint64)

@@ -25,7 +25,11 @@ def _f32_vs_oracle(case):
     r, out = run_gpu(lt, run, n, steps, pe.PE_F32)
     st, ev = r.state(), r.event_words()
     match = ev == ev_o
-    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), max(run["a0"], 1.0))
+    # FP32 momentum updates are good to the rounding of the largest momentum the electron had:
+    # the quiver amplitude a0, or the beam momentum of a fields-off bunch (a hard photon can
+    # take most of the energy, leaving |u| far below its initial value)
+    u_beam = math.sqrt(run["beam_gamma"] ** 2 - 1) if run["init_dist"] == pe.PE_BEAM else 0.0
+    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), max(run["a0"], u_beam, 1.0))
     err_u = (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u)[match]
     wait = r.wait_words() if wait_o is not None else None
     return run, r, out, st, st_o, ev, ev_o, match, err_u, tal_o, hist_o, wait, wait_o
@@ -44,30 +48,8 @@ def test_f32_null_collision_fields_off(case):
     r.close()
 
 
-@pytest.mark.parametrize("case", ["1d-au-a270-dense-null", "1d-au-a270-refl-lp", "1d-au-a270-refl-cp"])
-def test_f32_variant_parity(case):
-    """Under the a0 = 270 field the FP32 bound is distributional (see test_gpu_parity); with the
-    reflected wave the electrons emit ~100 photons each (eta ~ 1), so event lists flip more often
-    and yields and spectra are compared statistically."""
-    run, r, out, st, st_o, ev, ev_o, match, err_u, tal_o, hist_o, wait, wait_o = _f32_vs_oracle(case)
-    frac = match.mean()
-    print(f"{case}: event match {frac:.4f}, median err u {np.median(err_u) if len(err_u) else 0:.2e}, "
-          f"NCS {tal_o[O.T['N_NCS_STORED']]}, brems {tal_o[O.T['N_BR_STORED']]}")
-    if case.endswith("null"):
-        assert frac > 0.9
-        assert tal_o[O.T["N_BR_STORED"]] > 50
-        assert np.mean(wait[match] == wait_o[match]) > 0.99
-    else:
-        assert frac > 0.3
-    assert np.median(err_u) < F32_RTOL
-    assert np.quantile(err_u, 0.95) < 1e-3
-    for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED"):
-        a, b = int(out.tally[pe.T[k]]), int(tal_o[O.T[k]])
-        assert abs(a - b) <= 4 * math.sqrt(max(b, 1)) + 0.05 * b, (k, a, b)
-    # NCS photon spectra (chi-square over merged bins)
+def _chi2_p(h1, h2):
     from scipy.stats import chi2
-    h1 = np.frombuffer(bytes(out.hist), dtype=np.uint64)[:512].astype(float)
-    h2 = hist_o[:512].astype(float)
     m1, m2, a, b = [], [], 0.0, 0.0
     for x, y in zip(h1, h2):
         a += x; b += y
@@ -78,7 +60,48 @@ def test_f32_variant_parity(case):
     m1, m2 = np.array(m1), np.array(m2)
     k1, k2 = math.sqrt(m2.sum() / m1.sum()), math.sqrt(m1.sum() / m2.sum())
     stat = np.sum((k1 * m1 - k2 * m2) ** 2 / (m1 + m2))
-    assert chi2.sf(stat, len(m1) - 1) > 1e-3, stat
+    return chi2.sf(stat, len(m1) - 1)
+
+
+@pytest.mark.parametrize("case", ["1d-au-a270-dense-null", "1d-au-a270-refl-lp", "1d-au-a270-refl-cp"])
+def test_f32_variant_parity(case):
+    """Under the a0 = 270 field the FP32 bound is distributional (see test_gpu_parity).  With the
+    reflected wave the electrons emit tens of photons each (eta ~ 1) and the LP standing wave is
+    chaotic, so the per-particle comparison stops at the parity horizon of the FP64 case."""
+    run, r, out, st, st_o, ev, ev_o, match, err_u, tal_o, hist_o, wait, wait_o = _f32_vs_oracle(case)
+    frac = match.mean()
+    print(f"{case}: event match {frac:.4f}, median err u {np.median(err_u) if len(err_u) else 0:.2e}, "
+          f"p95 {np.quantile(err_u, 0.95):.2e}, NCS {tal_o[O.T['N_NCS_STORED']]}, brems {tal_o[O.T['N_BR_STORED']]}")
+    assert frac > 0.9
+    if case.endswith("null"):
+        assert tal_o[O.T["N_BR_STORED"]] > 50
+        assert np.mean(wait[match] == wait_o[match]) > 0.99
+    assert np.median(err_u) < F32_RTOL
+    assert np.quantile(err_u, 0.95) < 1e-3
+    for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED"):
+        a, b = int(out.tally[pe.T[k]]), int(tal_o[O.T[k]])
+        assert abs(a - b) <= 4 * math.sqrt(max(b, 1)) + 0.05 * b, (k, a, b)
+    h1 = np.frombuffer(bytes(out.hist), dtype=np.uint64)[:512].astype(float)
+    assert _chi2_p(h1, hist_o[:512].astype(float)) > 1e-3
+    r.close()
+
+
+def test_f32_reflected_wave_statistics():
+    """The full 1500-step reflected LP job, past the chaotic horizon: photon yields and the NCS
+    spectrum of the FP32 GPU run and the FP64 oracle on independent seeds agree statistically."""
+    runkw, n, _ = CASES["1d-au-a270-refl-lp"]
+    lt, ot = tables(_tp(48), Z)
+    _, _, _, hist_o, tal_o, _ = run_oracle(ot, W.base_run(**dict(runkw, seed=301)), Z, np.arange(4000), 1500)
+    r, out = run_gpu(lt, W.base_run(**dict(runkw, seed=302)), 4000, 1500, pe.PE_F32)
+    for k in ("N_NCS_STORED", "N_NCS_BELOW"):
+        a, b = int(out.tally[pe.T[k]]), int(tal_o[O.T[k]])
+        print(k, a, b)
+        assert abs(a / b - 1) < 0.1, (k, a, b)
+    h1 = np.frombuffer(bytes(out.hist), dtype=np.uint64)[:512].astype(float)
+    h2 = hist_o[:512].astype(float)
+    p = _chi2_p(h1, h2)
+    print("spectrum chi2 p", p)
+    assert p > 1e-3
     r.close()
 
 

@@ -229,3 +229,29 @@ def test_reflected_wave_eta_light_front():
         assert abs(O.eta(u, E, B, E_S) / want - 1) < 1e-9
         checked[int(ref)] += 1
     assert min(checked) > 20
+
+
+def test_reflected_wave_dynamics_are_chaotic():
+    """In the LP standing wave in front of a perfect mirror (a0 = 270, r = 1) nearby trajectories
+    separate exponentially: a 2^-50 relative perturbation of the initial momenta grows by more than
+    1e10 within 900 steps (it stays below 1e-11 in the plane wave alone).  Per-particle parity of two
+    implementations with different rounding therefore has a horizon of a few hundred steps after the
+    reflected pulse arrives; beyond it the comparison is statistical."""
+    from paper_1612_07592_gb300 import workloads as W
+    p = O.table_params(n_eta=48, n_y=48, n_E=48, n_s=48)
+    t = O.Tables(p, [13.0, 79.0])
+    worst = {}
+    for name, refl in (("refl", 1.0), ("plane", 0.0)):
+        run = W.base_run(a0=270.0, init_dist=1, T_mev=1.0, seed=2, reflect_r=refl, mirror_x_m=3e-6, **W.AU)
+        run["iz"] = 1
+        r = O.run_params(**run)
+        ids = np.arange(200)
+        a = O.init(t, r, ids)
+        b = a.copy()
+        b[:, 2:5] *= 1 + 2.0 ** -50
+        O.run(t, r, ids, a, 0, 900, capacity=16)
+        O.run(t, r, ids, b, 0, 900, capacity=16)
+        scale = np.maximum(np.abs(a[:, 2:5]).max(1), 270.0)
+        worst[name] = (np.abs(a[:, 2:5] - b[:, 2:5]).max(1) / scale).max()
+    assert worst["plane"] < 1e-11
+    assert worst["refl"] > 1e10 * 2.0 ** -50
