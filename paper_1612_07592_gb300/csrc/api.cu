@@ -20,6 +20,7 @@ struct pe_tables {
     HostTables host;
     TablesDev dev;
     void* dmem = nullptr;
+    void* dmemq = nullptr;    // pair-row tables and guides of the FP32 emission branch
     int device = 0;
 };
 
@@ -115,6 +116,74 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
         return cuda_fail(e, "pe_create_tables: cudaMemcpy");
     }
     TablesDev& D = t->dev;
+    {
+        // pair-row tables and guide tables (see internal.h)
+        const int ne = p->n_eta, ny = p->n_y, nE = p->n_E, ns = p->n_s, nZ = p->n_Z;
+        auto pow2 = [](int v) { int m = 1; while (m < v) m <<= 1; return m; };
+        const int My = pow2(ny), Ms = pow2(ns);
+        const size_t nq_n = (size_t)ne * ny, nq_b = (size_t)nZ * (nE - 1) * ns;
+        const size_t ng_n = (size_t)ne * My, ng_b = (size_t)nZ * (nE - 1) * Ms;
+        std::vector<float4> q((nq_n + nq_b));
+        std::vector<short4> g(ng_n + ng_b);
+        const float* c32 = all32.data() + n_h;
+        const float* c32lo = all32lo.data() + n_h;
+        const float* b32 = all32.data() + n_h + n_c + n_sg;
+        const float* b32lo = all32lo.data() + n_h + n_c + n_sg;
+        // out[m] = J(m / M) for m = 0..M, J(u) the largest j with hi[j] + lo[j] <= u (the
+        // float pair summed exactly in double), -1 if none: column k counts from the first
+        // m with m / M >= c_k (c_k M is exact, M a power of two), then a running maximum
+        auto guide = [](const float* hi, const float* lo, int n, int M, short* out) {
+            std::vector<int> mark(M + 1, -1);
+            for (int k = 0; k < n; ++k) {
+                double x = std::ceil(((double)hi[k] + (double)lo[k]) * M);
+                if (x > M) continue;
+                int m0 = x < 0 ? 0 : (int)x;
+                mark[m0] = std::max(mark[m0], k);
+            }
+            int run = -1;
+            for (int m = 0; m <= M; ++m) {
+                run = std::max(run, mark[m]);
+                out[m] = (short)run;
+            }
+        };
+        auto fill = [&](float4* qd, short4* gd, const float* ah, const float* al, const float* bh, const float* bl,
+                        int n, int M) {
+            for (int j = 0; j < n; ++j) qd[j] = make_float4(ah[j], al[j], bh[j], bl[j]);
+            std::vector<short> ja(M + 1), jb(M + 1);
+            guide(ah, al, n, M, ja.data());
+            guide(bh, bl, n, M, jb.data());
+            for (int m = 0; m < M; ++m) gd[m] = make_short4(ja[m], jb[m], ja[m + 1], jb[m + 1]);
+        };
+        for (int i = 0; i < ne; ++i) {
+            const size_t ra = (size_t)(i < ne - 1 ? i : ne) * ny, rb = (size_t)(i < ne - 1 ? i + 1 : ne) * ny;
+            fill(q.data() + (size_t)i * ny, g.data() + (size_t)i * My, c32 + ra, c32lo + ra, c32 + rb, c32lo + rb,
+                 ny, My);
+        }
+        for (int z = 0; z < nZ; ++z)
+            for (int i = 0; i < nE - 1; ++i) {
+                const size_t ra = ((size_t)z * nE + i) * ns, rb = ra + ns;
+                const size_t pr = (size_t)z * (nE - 1) + i;
+                fill(q.data() + nq_n + pr * ns, g.data() + ng_n + pr * Ms, b32 + ra, b32lo + ra, b32 + rb, b32lo + rb,
+                     ns, Ms);
+            }
+        const size_t qbytes = q.size() * sizeof(float4), gbytes = g.size() * sizeof(short4);
+        e = cudaMalloc(&t->dmemq, qbytes + gbytes);
+        if (e == cudaSuccess) e = cudaMemcpy(t->dmemq, q.data(), qbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(static_cast<char*>(t->dmemq) + qbytes, g.data(), gbytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(t->dmem);
+            if (t->dmemq) cudaFree(t->dmemq);
+            delete t;
+            return cuda_fail(e, "pe_create_tables: guide tables");
+        }
+        const float4* dq = static_cast<const float4*>(t->dmemq);
+        const short4* dg = reinterpret_cast<const short4*>(static_cast<const char*>(t->dmemq) + qbytes);
+        D.cdfq = dq; D.bcdfq = dq + nq_n;
+        D.gq = dg; D.bgq = dg + ng_n;
+        D.M_y = My; D.M_s = Ms;
+        D.fM_y = (float)My; D.fM_s = (float)Ms;
+    }
     D.h64 = d64; D.cdf64 = d64 + n_h; D.sig64 = D.cdf64 + n_c; D.bcdf64 = D.sig64 + n_sg;
     D.h32 = d32; D.cdf32 = d32 + n_h; D.sig32 = D.cdf32 + n_c; D.bcdf32 = D.sig32 + n_sg;
     D.cdf32lo = d32lo + n_h;
@@ -144,6 +213,7 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
 extern "C" pe_status pe_destroy_tables(pe_tables* t) {
     if (!t) return fail(PE_ERR_ARG, "pe_destroy_tables: null");
     if (t->dmem) cudaFree(t->dmem);
+    if (t->dmemq) cudaFree(t->dmemq);
     delete t;
     return PE_OK;
 }

@@ -43,6 +43,20 @@ struct TablesDev {
     const float* bcdf32; const double* bcdf64;  // [n_Z * n_E * n_s]
     const float* cdf32lo;                       // float-pair remainders: value = cdf32 + cdf32lo
     const float* bcdf32lo;
+    // FP32 emission tables by pairs of adjacent rows: entry (i, j) holds column j of
+    // rows i and i+1 as float pairs (hi_i, lo_i, hi_i+1, lo_i+1), so one 16-byte load
+    // gives both values the row interpolation needs.  NCS: pair-rows 0..n_eta-2 and
+    // pair-row n_eta-1 = (classical, classical); brems: n_E - 1 pair-rows per Z.
+    const float4* cdfq;                         // [n_eta * n_y]
+    const float4* bcdfq;                        // [n_Z * (n_E - 1) * n_s]
+    // Guide tables (Chen & Asau 1974) of the pair-rows: for m in [0, M), entry m holds
+    // (J_i(m/M), J_i+1(m/M), J_i((m+1)/M), J_i+1((m+1)/M)) with J_r(u) the largest
+    // column j with CDF_r[j] <= u (-1 if none).  The inverse of the interpolated row
+    // at u in [m/M, (m+1)/M) lies between the smallest and the largest of them.
+    const short4* gq;                           // [n_eta * M_y]
+    const short4* bgq;                          // [n_Z * (n_E - 1) * M_s]
+    int M_y, M_s;                               // guide sizes (powers of two >= n_y, n_s)
+    float fM_y, fM_s;
     int n_eta, n_y, n_E, n_s, n_Z;
     TabC<float> cf;
     TabC<double> cd;

@@ -50,38 +50,72 @@ __device__ __forceinline__ DF uni53_pair(uint32_t lo, uint32_t hi) {
     float f3 = __int_as_float(0x4B000000 | (int)p3) - 0x1.0p23f + 0.5f;
     return DF{f1 * 0x1.0p-23f, fmaf(f3, 0x1.0p-53f, f2 * 0x1.0p-46f)};
 }
-// row-interpolated CDF value (1 - w) A_k + w B_k with A, B float pairs
-__device__ __forceinline__ DF row_value(const float* ah, const float* al, const float* bh, const float* bl,
-                                        float w, int k) {
-    float Ah = ah[k], Al = al[k];
-    if (w == 0.0f) return DF{Ah, Al};
-    DF d = two_sum(bh[k], -Ah);                       // B_hi - A_hi exactly
-    float dl = d.lo + (bl[k] - Al);
+// row-interpolated CDF value (1 - w) A + w B of one pair-row entry e = (A_hi, A_lo, B_hi, B_lo)
+__device__ __forceinline__ DF pair_value(float4 e, float w) {
+    if (w == 0.0f) return DF{e.x, e.y};
+    DF d = two_sum(e.z, -e.x);                        // B_hi - A_hi exactly
+    float dl = d.lo + (e.w - e.y);
     float p = w * d.hi;
     float ep = fmaf(w, d.hi, -p);                     // exact error of the product
-    DF c = two_sum(Ah, p);
-    return DF{c.hi, c.lo + (Al + fmaf(w, dl, ep))};
+    DF c = two_sum(e.x, p);
+    return DF{c.hi, c.lo + (e.y + fmaf(w, dl, ep))};
 }
 // sign of a - b for float pairs
 __device__ __forceinline__ float df_diff(DF a, DF b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-// inverse of the row-interpolated CDF at the uniform R: largest j with c_j <= R
-// (j = -1 below the first node, n - 1 at or above the last) and the fraction
-// (R - c_j) / (c_{j+1} - c_j), or R / c_0 below the first node
-__device__ __forceinline__ float invert_rows_df(const float* ah, const float* al, const float* bh, const float* bl,
-                                                float w, int n, DF R, int& j_out) {
-    DF c0 = row_value(ah, al, bh, bl, w, 0);
+// Inverse of the row-interpolated CDF of pair-row q (n columns, guide g of M entries)
+// at the uniform R: the largest j with c_j <= R (j = -1 below the first node, n - 1 at or
+// above the last) and the fraction (R - c_j) / (c_{j+1} - c_j), or R / c_0 below the
+// first node.  The guide brackets j to a few columns, which are loaded together, so the
+// search costs two dependent rounds of loads instead of a binary search's log2(n).
+__device__ __forceinline__ float invert_pair_df(const float4* q, const short4* g, float w, int n, int M, float fM,
+                                                DF R, int& j_out) {
+    // m with m / M <= R < (m + 1) / M (R.hi M is exact, M a power of two)
+    float rm = R.hi * fM;
+    int m = (int)floor_small(rm);
+    if (R.lo < 0.0f && int_to_float_small(m) == rm) --m;
+    m = m < M - 1 ? m : M - 1;
+    const float4 e0 = __ldg(q), en = __ldg(q + n - 1);
+    const short4 gg = __ldg(g + m);
+    DF c0 = pair_value(e0, w);
     if (df_diff(R, c0) < 0.0f) { j_out = -1; return (R.hi + R.lo) / (c0.hi + c0.lo); }
-    DF cn = row_value(ah, al, bh, bl, w, n - 1);
+    DF cn = pair_value(en, w);
     if (df_diff(R, cn) >= 0.0f) { j_out = n - 1; return 0.0f; }
-    int lo = 0, hi = n - 1;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (df_diff(R, row_value(ah, al, bh, bl, w, mid)) >= 0.0f) lo = mid; else hi = mid;
+    // bracket from the two rows' inverses, widened by one column for rounding
+    int a = min((int)gg.x, (int)gg.y) - 1, b = max((int)gg.z, (int)gg.w) + 1;
+    a = a > 0 ? a : 0;
+    b = b < n - 2 ? b : n - 2;
+    DF cl, ch;
+    int j;
+    if (b - a <= 5) {
+        constexpr int kW = 7;
+        float4 v[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) v[k] = __ldg(q + min(a + k, n - 1));
+        DF c[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) c[k] = pair_value(v[k], w);
+        int k = 0;
+#pragma unroll
+        for (int kk = 1; kk < kW - 1; ++kk)
+            if (a + kk <= b && df_diff(R, c[kk]) >= 0.0f) k = kk;
+        j = a + k;
+        cl = c[0];
+        ch = c[1];
+#pragma unroll
+        for (int kk = 1; kk < kW - 1; ++kk)
+            if (k == kk) { cl = c[kk]; ch = c[kk + 1]; }
+    } else {
+        int lo = a, hi = b + 1;                       // c_lo <= R < c_hi
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (df_diff(R, pair_value(__ldg(q + mid), w)) >= 0.0f) lo = mid; else hi = mid;
+        }
+        j = lo;
+        cl = pair_value(__ldg(q + lo), w);
+        ch = pair_value(__ldg(q + hi), w);
     }
-    DF cl = row_value(ah, al, bh, bl, w, lo);
-    DF ch = row_value(ah, al, bh, bl, w, hi);
-    j_out = lo;
+    j_out = j;
     float num = df_diff(R, cl), den = df_diff(ch, cl);
     return den > 0.0f ? num / den : 0.0f;
 }
@@ -90,24 +124,20 @@ __device__ __forceinline__ float invert_rows_df(const float* ah, const float* al
 __device__ __forceinline__ float sample_ncs_delta_f32(const TablesDev& t, float eta, uint32_t wlo, uint32_t whi,
                                                       bool& below) {
     const TabC<float>& c = t.cf;
-    const float *ah, *al, *bh, *bl;
     float w;
+    int pr;
     below = false;
     if (!(eta >= c.eta_min)) {
-        size_t off = (size_t)t.n_eta * t.n_y;
-        ah = bh = t.cdf32 + off;
-        al = bl = t.cdf32lo + off;
+        pr = t.n_eta - 1;                              // (classical, classical)
         w = 0.0f;
         below = true;
     } else {
-        int i, fl;
-        row_pos<float>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, fl);
-        size_t off = (size_t)i * t.n_y;
-        ah = t.cdf32 + off; al = t.cdf32lo + off;
-        bh = ah + t.n_y; bl = al + t.n_y;
+        int fl;
+        row_pos<float>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, pr, w, fl);
     }
     int j;
-    float fr = invert_rows_df(ah, al, bh, bl, w, t.n_y, uni53_pair(wlo, whi), j);
+    float fr = invert_pair_df(t.cdfq + (size_t)pr * t.n_y, t.gq + (size_t)pr * t.M_y, w, t.n_y, t.M_y, t.fM_y,
+                              uni53_pair(wlo, whi), j);
     float y;
     if (j < 0) y = c.y_min * fr * fr * fr;           // CDF ~ y^(1/3) below the grid
     else if (j >= t.n_y - 1) y = c.y_max;
@@ -123,11 +153,10 @@ __device__ __forceinline__ float sample_brems_y_f32(const TablesDev& t, int iz, 
     int i, fl;
     float w;
     row_pos<float>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
-    size_t off = ((size_t)iz * t.n_E + i) * t.n_s;
-    const float* ah = t.bcdf32 + off;
-    const float* al = t.bcdf32lo + off;
+    const size_t pr = (size_t)iz * (t.n_E - 1) + i;
     int j;
-    float fr = invert_rows_df(ah, al, ah + t.n_s, al + t.n_s, w, t.n_s, uni53_pair(wlo, whi), j);
+    float fr = invert_pair_df(t.bcdfq + pr * t.n_s, t.bgq + pr * t.M_s, w, t.n_s, t.M_s, t.fM_s,
+                              uni53_pair(wlo, whi), j);
     float s;
     if (j < 0) s = 0.0f;
     else if (j >= t.n_s - 1) s = 1.0f;
