@@ -148,7 +148,7 @@ def cpu_baseline(cfg, n_sample, steps, threads):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--block", type=int, default=0)
@@ -385,7 +385,7 @@ def batch64(pe, stream, flush):
             runs.append(pe.Run(tables, pe.run_params(precision=pe.PE_F32, **rk), int(n),
                                capacity=int(min(2 * n, 1 << 23)), stream=stream))
     stream.synchronize()
-    cfg, trials = autotune.tune(tables, runs, 200, space=dict(block=(128, 256), ctas_per_sm=(2, 3, 4),
+    cfg, trials = autotune.tune(tables, runs, 200, space=dict(block=(128, 256), ctas_per_sm=(5, 10, 15),
                                                                  steps_per_launch=(200,)), use_cache=False)
     cfg = dict(cfg, steps_per_launch=500)
     snaps = [r.snapshot() for r in runs]

@@ -174,8 +174,9 @@ typedef struct {
  * ctas_per_sm: CTAs per SM
  * in the grid; steps_per_launch: steps done per launch with the state held in
  * registers (1 = state round-trips memory every step).  Zeros pick defaults:
- * 256 electrons per tile, twice the CTAs that fit on an SM, min(steps, 4096)
- * steps per launch.                                                            */
+ * 256 electrons per tile; three times the CTAs that fit on an SM for the FP32
+ * plane-wave kernel, twice for the other kernels; min(steps, 4096) steps per
+ * launch.                                                                      */
 typedef struct {
     int block, ctas_per_sm, steps_per_launch;
 } pe_launch_config;

@@ -14,7 +14,7 @@ import os
 from . import HERE, pe_step_ex
 
 CACHE = os.path.join(HERE, "_autotune_cache.json")
-DEFAULT_SPACE = dict(block=(128, 256), ctas_per_sm=(2, 3, 4), steps_per_launch=(256, 1024, 2048))
+DEFAULT_SPACE = dict(block=(128, 256), ctas_per_sm=(4, 8, 15), steps_per_launch=(256, 1024, 2048))
 
 
 def _key(device_name: str, runs) -> str:

@@ -398,12 +398,6 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
     int smem = persistent_smem_bytes(t->dev, prec);
     if (smem > 200 * 1024)
         return fail(PE_ERR_ARG, "pe_step: rate tables (n_eta + n_Z * n_E) too large for shared memory");
-    // default grid: twice the resident CTAs, so the block scheduler evens out the last
-    // partial wave of tiles (measured +4 % over one resident wave on 1e6 electrons)
-    int per_sm = (cfg && cfg->ctas_per_sm > 0)
-                     ? cfg->ctas_per_sm
-                     : 2 * (prec == PE_F32 ? persistent_occupancy_f32(block, smem) : persistent_occupancy_f64(block, smem));
-    if (per_sm < 1) per_sm = 1;
     for (int fk = 0; fk < kFieldKinds; ++fk) {
         std::vector<int> idx;
         for (int k = 0; k < n_runs; ++k)
@@ -415,6 +409,12 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
         for (int k = 0; k < m; ++k) tile_start[k + 1] = tile_start[k] + (runs[idx[k]]->dev.n + block - 1) / block;
         int64_t n_tiles = tile_start[m];
         if (n_tiles == 0) continue;
+        // default grid: three resident waves of the paired plane-wave kernel, twice the resident
+        // CTAs of the one-electron kernel, so the block scheduler evens out tiles of unequal cost
+        int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm
+                                                  : (prec == PE_F32 ? default_ctas_per_sm_f32(fk, block, smem)
+                                                                    : 2 * persistent_occupancy_f64(block, smem));
+        if (per_sm < 1) per_sm = 1;
         int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
         for (int64_t done = 0; done < n_steps; done += K) {
             PlanLaunch L;

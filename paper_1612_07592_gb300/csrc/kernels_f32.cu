@@ -53,6 +53,20 @@ const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem, int block
     return f;
 }
 
+// default CTAs per SM of the grid: three waves of the paired kernel (plane-wave kinds;
+// tiles differ in cost with their emission histories, and a CTA per one or two tiles lets
+// the block scheduler balance them: measured +6 % over one wave, +2.5 % over two, on
+// 1e6 electrons), twice the resident CTAs of the one-electron kernel otherwise
+int default_ctas_per_sm_f32(int fk, int block, int smem) {
+    if (fk == FK_PLANE_LP || fk == FK_PLANE_CP) {
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP>, block / 2,
+                                                                      smem);
+        return 3 * (e == cudaSuccess && occ > 0 ? occ : 1);
+    }
+    return 2 * persistent_occupancy_f32(block, smem);
+}
+
 int persistent_occupancy_f32(int block, int smem) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false, FK_PLANE_LP>, block, smem);
