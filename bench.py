@@ -303,6 +303,7 @@ def main():
                             "gauss2d_cp_a855_3e7x2000": gauss2d(pe, stream, flush),
                             "serving_poisson50hz": serving(pe, stream),
                             "bunch_1gev_au_5mm_1e6": bunch_methods(pe, stream, flush),
+                            "bunch_1gev_au_5mm_1e6_dt_T10": bunch_methods(pe, stream, flush, dt_over_T=0.1),
                             "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush)}
     if rank == 0 and not args.skip_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -473,13 +474,14 @@ def _timed_jobs(pe, r, tables, steps, stream, flush, reps=3):
     return float(np.mean(times))
 
 
-def bunch_methods(pe, stream, flush, n=1_000_000):
+def bunch_methods(pe, stream, flush, n=1_000_000, dt_over_T=1.0):
     """The Sec. 2.2 bunch benchmark: 1 GeV electrons into 5 mm of fully ionised Au, fields off,
-    pusher + brems only, 5000 steps of one laser period; the direct test of Eq. 4 in every step
-    against null collisions, FP32, 1e6 electrons (ten of the paper's 1e5-electron bunches)."""
+    pusher + brems only, steps of dt_over_T laser periods (5000 steps at one period); the direct
+    test of Eq. 4 in every step against null collisions, FP32, 1e6 electrons (ten of the paper's
+    1e5-electron bunches)."""
     import torch
     from paper_1612_07592_gb300 import workloads as W
-    c = W.bunch(1000.0, "Au", n=n)
+    c = W.bunch(1000.0, "Au", n=n, dt_over_T=dt_over_T)
     tables = pe.pe_create_tables(c["tables"], c["Z"])
     out = {}
     for name, method in (("direct", pe.PE_BREMS_DIRECT), ("null", pe.PE_BREMS_NULL)):

@@ -129,8 +129,8 @@ typedef struct {
      * kept per particle in pe_buffers.brems_wait; a candidate is a collision
      * with probability P / (1 - exp(-x_hat)), P the Eq. 4 probability of the
      * step, so collisions have the law of the direct method.  Philox purposes:
-     * 0 at the candidate step (acceptance, photon energy), 256 at step 0 (first
-     * wait) and at candidate step + 1 (next wait).                               */
+     * 256 at step 0 (first wait) and at candidate step + 1 (next wait, test
+     * word), 0 at the candidate step only for a collision (photon energy).      */
     int brems_method;
 } pe_run_params;
 

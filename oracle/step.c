@@ -447,12 +447,22 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
                     P = -expm1(-xb);
                 }
                 double p_acc = nullc ? P / c->P_hat : P;
-                uint32_t w[4];
-                draw(r, id, (uint32_t)n, PUR_BREMS, w);
-                uint64_t U = word64(w[0], w[1]);
+                /* direct: one draw of purpose 0 at step n (test word, photon-energy word);
+                 * null: one draw of purpose 256 at step n + 1 (next-wait word, test word),
+                 * and purpose 0 at step n only for a collision (photon-energy word)  */
+                uint32_t w[4], v[4];
+                uint64_t U;
+                if (nullc) {
+                    draw(r, id, (uint32_t)n + 1u, PUR_WAIT, v);
+                    U = word64(v[2], v[3]);
+                } else {
+                    draw(r, id, (uint32_t)n, PUR_BREMS, w);
+                    U = word64(w[0], w[1]);
+                }
                 uint64_t thr = (uint64_t)floor(p_acc * 18446744073709551616.0);
                 if (p_acc >= 1.0) thr = UINT64_MAX;
                 if (U < thr) {
+                    if (nullc) draw(r, id, (uint32_t)n, PUR_BREMS, w);
                     double yy = or_sample_brems_y(t, r->iz, gamma, u53(word64(w[2], w[3])));
                     double ew = yy * gamma;
                     double k[3];
@@ -471,10 +481,7 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
                     }
                     gamma = gn;
                 }
-                if (nullc) {
-                    draw(r, id, (uint32_t)n + 1u, PUR_WAIT, w);
-                    *wait = wait_draw(c->x_hat, word64(w[0], w[1]));
-                }
+                if (nullc) *wait = wait_draw(c->x_hat, word64(v[0], v[1]));
             }
         }
         x += c->dt * u[0] / gamma;

@@ -288,10 +288,13 @@ __device__ __noinline__ Emission<R> brems_candidate(const TablesDev& t, const Ru
     R p_acc = 0;
     if (in_slab && gamma > (R)1 + tabc<R>(t).photon_min)
         p_acc = brems_prob<R>(t, r, sig_tab, P, gamma, tally) / r.c.P_hat;
-    uint4 w = draw(r, id, n, PUR_BREMS);
-    if (brems_event(p_acc, w)) out = brems_emit<R>(t, r, id, n, P, gamma, xn, yn, w, hist, tally);
-    else out.P = P;
+    // one draw of purpose 256 at step n + 1: the next wait (x, y) and the test word (z, w);
+    // purpose 0 at step n only for a collision (the photon-energy word, as in the direct method)
     uint4 v = draw(r, id, n + 1u, PUR_WAIT);
+    if (brems_event(p_acc, make_uint4(v.z, v.w, 0u, 0u)))
+        out = brems_emit<R>(t, r, id, n, P, gamma, xn, yn, draw(r, id, n, PUR_BREMS), hist, tally);
+    else
+        out.P = P;
     out.P.wait = wait_draw(r.x_hat, v.x, v.y);
     return out;
 }
