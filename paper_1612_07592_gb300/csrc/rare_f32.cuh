@@ -66,8 +66,9 @@ __device__ __forceinline__ float df_diff(DF a, DF b) { return (a.hi - b.hi) + (a
 // Inverse of the row-interpolated CDF of pair-row q (n columns, guide g of M entries)
 // at the uniform R: the largest j with c_j <= R (j = -1 below the first node, n - 1 at or
 // above the last) and the fraction (R - c_j) / (c_{j+1} - c_j), or R / c_0 below the
-// first node.  The guide brackets j to a few columns, which are loaded together, so the
-// search costs two dependent rounds of loads instead of a binary search's log2(n).
+// first node.  The guide brackets j to a few columns, so the binary search that follows
+// takes one or two probes instead of log2(n) (a wider search window loaded at once
+// measured slower: its registers crowd the step loop).
 __device__ __forceinline__ float invert_pair_df(const float4* q, const short4* g, float w, int n, int M, float fM,
                                                 DF R, int& j_out) {
     // m with m / M <= R < (m + 1) / M (R.hi M is exact, M a power of two)
@@ -85,36 +86,13 @@ __device__ __forceinline__ float invert_pair_df(const float4* q, const short4* g
     int a = min((int)gg.x, (int)gg.y) - 1, b = max((int)gg.z, (int)gg.w) + 1;
     a = a > 0 ? a : 0;
     b = b < n - 2 ? b : n - 2;
-    DF cl, ch;
-    int j;
-    if (b - a <= 5) {
-        constexpr int kW = 7;
-        float4 v[kW];
-#pragma unroll
-        for (int k = 0; k < kW; ++k) v[k] = __ldg(q + min(a + k, n - 1));
-        DF c[kW];
-#pragma unroll
-        for (int k = 0; k < kW; ++k) c[k] = pair_value(v[k], w);
-        int k = 0;
-#pragma unroll
-        for (int kk = 1; kk < kW - 1; ++kk)
-            if (a + kk <= b && df_diff(R, c[kk]) >= 0.0f) k = kk;
-        j = a + k;
-        cl = c[0];
-        ch = c[1];
-#pragma unroll
-        for (int kk = 1; kk < kW - 1; ++kk)
-            if (k == kk) { cl = c[kk]; ch = c[kk + 1]; }
-    } else {
-        int lo = a, hi = b + 1;                       // c_lo <= R < c_hi
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (df_diff(R, pair_value(__ldg(q + mid), w)) >= 0.0f) lo = mid; else hi = mid;
-        }
-        j = lo;
-        cl = pair_value(__ldg(q + lo), w);
-        ch = pair_value(__ldg(q + hi), w);
+    int lo = a, hi = b + 1;                           // c_lo <= R < c_hi
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (df_diff(R, pair_value(__ldg(q + mid), w)) >= 0.0f) lo = mid; else hi = mid;
     }
+    const int j = lo;
+    const DF cl = pair_value(__ldg(q + lo), w), ch = pair_value(__ldg(q + hi), w);
     j_out = j;
     float num = df_diff(R, cl), den = df_diff(ch, cl);
     return den > 0.0f ? num / den : 0.0f;
