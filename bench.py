@@ -43,9 +43,9 @@ BYTES_PER_PSTEP_1D = 56
 BYTES_PER_PSTEP_2D = 72
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per electron and launch of the dominant kernel, from the ncu
-# capture in profiles/k_step_pair__1d-au-a270-mj-2e5x400__full.md (7.48 MB for 2e5 electrons:
-# the state once plus the cold emission tables); None once the kernel changes after that capture.
+# DRAM bytes (read + write) per electron and launch of the dominant kernel, from an ncu capture
+# of one 400-step launch on 2e5 electrons of the same physics (7.48 MB: the state once plus the
+# cold emission tables); None once the kernel changes after that capture.
 NCU_TRAFFIC_BYTES_PER_ELECTRON = 37.4
 
 
