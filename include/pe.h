@@ -48,7 +48,7 @@ typedef enum {
     PE_ERR_NOMEM = 3,        /* the library could not allocate its own device memory    */
     PE_ERR_BUFFER_FULL = 4,  /* photon buffer overflowed; counts stay exact             */
     PE_ERR_TABLE_RANGE = 5,  /* reserved: out-of-table values are counted, not fatal    */
-    PE_ERR_TIMEOUT = 6,      /* reserved for bounded device waits                       */
+    PE_ERR_TIMEOUT = 6,      /* a bounded device wait ran out (counted in the tally)     */
     PE_ERR_STATE = 7         /* call out of order (e.g. mixed precisions in one batch)  */
 } pe_status;
 
@@ -74,6 +74,7 @@ enum {
     PE_T_N_ETA_BELOW = 6,    /* NCS emissions sampled from the classical (eta->0) row      */
     PE_T_N_GAMMA_ABOVE = 7,  /* brems tests with gamma above the table (row clamped)       */
     PE_T_N_KILLED = 8, PE_T_KILLED_STEPS = 9, PE_T_N_CLAMP = 10, PE_T_N_HIST_OVER = 11,
+    PE_T_N_WAIT_TIMEOUT = 12, /* device waits that ran out (pe_tally then returns PE_ERR_TIMEOUT) */
     PE_T_E_NCS_STORED = 16, PE_T_E_NCS_BELOW = 18, PE_T_E_BR_STORED = 20, PE_T_E_BR_BELOW = 22,
     PE_T_E_RECOIL_NCS = 24, PE_T_E_RECOIL_BR = 26
 };

@@ -31,7 +31,7 @@ HIST_WORDS = 2 * HIST_E_BINS + 2 * HIST_T_BINS
 TALLY_WORDS = 32
 MAX_BATCH = 64
 T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4, N_ETA_ABOVE=5,
-         N_ETA_BELOW=6, N_GAMMA_ABOVE=7, N_KILLED=8, KILLED_STEPS=9, N_CLAMP=10, N_HIST_OVER=11,
+         N_ETA_BELOW=6, N_GAMMA_ABOVE=7, N_KILLED=8, KILLED_STEPS=9, N_CLAMP=10, N_HIST_OVER=11, N_WAIT_TIMEOUT=12,
          E_NCS_STORED=16, E_NCS_BELOW=18, E_BR_STORED=20, E_BR_BELOW=22, E_RECOIL_NCS=24, E_RECOIL_BR=26)
 PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
                          ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])

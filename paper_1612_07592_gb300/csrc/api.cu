@@ -412,7 +412,7 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
         // default grid: three resident waves of the paired plane-wave kernel, twice the resident
         // CTAs of the one-electron kernel, so the block scheduler evens out tiles of unequal cost
         int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm
-                                                  : (prec == PE_F32 ? default_ctas_per_sm_f32(fk, block, smem)
+                                                  : (prec == PE_F32 ? default_ctas_per_sm_f32(fk, block, smem, K)
                                                                     : 2 * persistent_occupancy_f64(block, smem));
         if (per_sm < 1) per_sm = 1;
         int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
@@ -530,6 +530,8 @@ extern "C" pe_status pe_tally(pe_run* r, pe_tally_out* out) {
     out->e_br_below = fx_value(out->tally, PE_T_E_BR_BELOW);
     out->e_recoil_ncs = fx_value(out->tally, PE_T_E_RECOIL_NCS);
     out->e_recoil_br = fx_value(out->tally, PE_T_E_RECOIL_BR);
+    if (out->tally[PE_T_N_WAIT_TIMEOUT])
+        return fail(PE_ERR_TIMEOUT, "pe_tally: a device wait for staged particle state ran out");
     if (np > (uint64_t)r->buf.photon_capacity)
         return fail(PE_ERR_BUFFER_FULL, "pe_tally: photon buffer overflowed (counts are exact)");
     return PE_OK;
@@ -586,11 +588,13 @@ extern "C" pe_status pe_graph_create(pe_run* const* runs, int n_runs, int64_t st
         cudaKernelNodeParams& p = g->params[k];
         std::memset(&p, 0, sizeof(p));
         int threads = L.block;
-        p.func = const_cast<void*>(L.prec == PE_F32 ? persistent_kernel_f32(*L.bf, L.smem, L.block, &threads)
+        int smem = L.smem;
+        p.func = const_cast<void*>(L.prec == PE_F32 ? persistent_kernel_f32(*L.bf, L.steps, L.smem, L.block, &threads,
+                                                                            &smem)
                                                     : persistent_kernel_f64(*L.bd, L.smem, L.block, &threads));
         p.gridDim = dim3(L.grid);
         p.blockDim = dim3(threads);
-        p.sharedMemBytes = L.smem;
+        p.sharedMemBytes = smem;
         p.kernelParams = g->args[k].data();
         e = cudaGraphAddKernelNode(&g->nodes[k], g->graph, k ? &g->nodes[k - 1] : nullptr, k ? 1 : 0, &p);
     }

@@ -4,12 +4,29 @@
 
 namespace pe {
 
-// The 1D plane-wave kinds use the paired kernel (two electrons per thread, block/2
-// threads per tile of `block` electrons); the others one electron per thread.
+// Launches of at most this many steps (the state round-trips memory) on a single run
+// of a plane-wave kind use the streaming form of the paired kernel.
+constexpr int kStreamMaxSteps = 4;
+
+static bool plane_kind(int fk) { return fk == FK_PLANE_LP || fk == FK_PLANE_CP; }
+static bool use_stream(const BatchDevT<float>& b, int steps, int block) {
+    return b.n_runs == 1 && plane_kind(b.runs[0].fk) && steps <= kStreamMaxSteps && block == kStreamTile;
+}
+// tables, then 128-byte alignment slack, two stage buffers and two mbarriers
+static int stream_smem_bytes(int base) { return base + 128 + 2 * kStageBytes + 16; }
+
+// The kernel of a launch, its threads per CTA and dynamic shared memory: the 1D
+// plane-wave kinds use the paired kernel (two electrons per thread, block/2 threads
+// per tile of `block` electrons) or its streaming form; the others one electron per thread.
 template <bool kSingle, int G>
-static const void* kernel_of(int block, int& threads) {
+static const void* kernel_of(const BatchDevT<float>& b, int steps, int block, int base_smem, int& threads, int& smem) {
+    smem = base_smem;
     if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
         threads = block / 2;
+        if (kSingle && use_stream(b, steps, block)) {
+            smem = stream_smem_bytes(base_smem);
+            return (const void*)k_step_pair_stream<G>;
+        }
         return (const void*)k_step_pair<kSingle, G>;
     } else {
         threads = block;
@@ -19,14 +36,18 @@ static const void* kernel_of(int block, int& threads) {
 
 template <bool kSingle, int G>
 static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block, cudaStream_t s,
-                       int smem) {
-    int threads;
-    const void* f = kernel_of<kSingle, G>(block, threads);
+                       int base_smem) {
+    int threads, smem;
+    const void* f = kernel_of<kSingle, G>(b, steps, block, base_smem, threads, smem);
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP)
-        k_step_pair<kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
-    else
+    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+        if (f == (const void*)k_step_pair_stream<G>)
+            k_step_pair_stream<G><<<grid, threads, smem, s>>>(t, b, steps);
+        else
+            k_step_pair<kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
+    } else {
         k_step_persistent<float, kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
+    }
 }
 
 void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
@@ -39,30 +60,37 @@ void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, i
     });
 }
 
-// the kernel a launch of these runs uses and its threads per CTA (for graph nodes);
-// sets the shared-memory attribute
-const void* persistent_kernel_f32(const BatchDevT<float>& b, int smem, int block, int* threads) {
+// the kernel a launch of these runs uses, its threads per CTA and dynamic shared memory
+// (for graph nodes); sets the shared-memory attribute
+const void* persistent_kernel_f32(const BatchDevT<float>& b, int steps, int base_smem, int block, int* threads,
+                                  int* smem_out) {
     const void* f = nullptr;
-    int th = block;
+    int th = block, smem = base_smem;
     with_field_kind(b.runs[0].fk, [&](auto g) {
-        f = b.n_runs == 1 ? kernel_of<true, decltype(g)::value>(block, th)
-                          : kernel_of<false, decltype(g)::value>(block, th);
+        f = b.n_runs == 1 ? kernel_of<true, decltype(g)::value>(b, steps, block, base_smem, th, smem)
+                          : kernel_of<false, decltype(g)::value>(b, steps, block, base_smem, th, smem);
     });
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     *threads = th;
+    *smem_out = smem;
     return f;
 }
 
-// default CTAs per SM of the grid: three waves of the paired kernel (plane-wave kinds;
-// tiles differ in cost with their emission histories, and a CTA per one or two tiles lets
-// the block scheduler balance them: measured +6 % over one wave, +2.5 % over two, on
-// 1e6 electrons), twice the resident CTAs of the one-electron kernel otherwise
-int default_ctas_per_sm_f32(int fk, int block, int smem) {
-    if (fk == FK_PLANE_LP || fk == FK_PLANE_CP) {
+// Default CTAs per SM of the grid.  Paired kernel (plane-wave kinds): three resident waves
+// (tiles differ in cost with their emission histories, and a CTA per one or two tiles lets
+// the block scheduler balance them: measured +6 % over one wave, +2.5 % over two, on 1e6
+// electrons); one wave for the streaming form (each CTA streams many tiles of equal cost).
+// One-electron kernel: twice its resident CTAs.
+int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch) {
+    if (plane_kind(fk)) {
+        const bool stream = steps_per_launch <= kStreamMaxSteps && block == kStreamTile;
         int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP>, block / 2,
-                                                                      smem);
-        return 3 * (e == cudaSuccess && occ > 0 ? occ : 1);
+        cudaError_t e = stream ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair_stream<FK_PLANE_LP>,
+                                                                             block / 2, stream_smem_bytes(smem))
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP>,
+                                                                             block / 2, smem);
+        occ = e == cudaSuccess && occ > 0 ? occ : 1;
+        return stream ? occ : 3 * occ;
     }
     return 2 * persistent_occupancy_f32(block, smem);
 }

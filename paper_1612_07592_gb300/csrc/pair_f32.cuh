@@ -256,19 +256,11 @@ __device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pai
     Q.act[k] = !isnan(P.x);
 }
 
-// K steps of the two electrons i0 = base + tid and i1 = base + tid + blockDim
+// K steps of the pair Q (electrons i0 and i1) with warp-aggregated photon appends
 template <int G>
-__device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
-                                                const float* sig_z, int64_t i0, int64_t i1, int steps,
-                                                unsigned long long* s_hist, unsigned long long* s_tally) {
-    Pair Q;
-    Q.x = Q.x_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
-    Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
-    Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
-    Q.act[0] = Q.act[1] = false;
-    if (i0 < r.n) load_one(r, i0, Q, 0);
-    if (i1 < r.n) load_one(r, i1, Q, 1);
-    const bool live0 = i0 < r.n, live1 = i1 < r.n;
+__device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
+                                          const float* sig_z, int64_t i0, int64_t i1, Pair& Q, int steps,
+                                          unsigned long long* s_hist, unsigned long long* s_tally) {
     const uint32_t id[2] = {(uint32_t)i0, (uint32_t)i1};
     const uint32_t n0 = (uint32_t)r.step0;
     float nf = (float)n0;
@@ -294,6 +286,26 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
             warp_append(r, st_br[1], pb[1]);
         }
     }
+}
+
+__device__ __forceinline__ void pair_clear(Pair& Q) {
+    Q.x = Q.x_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
+    Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
+    Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
+    Q.act[0] = Q.act[1] = false;
+}
+
+// K steps of the two electrons i0 = base + tid and i1 = base + tid + blockDim
+template <int G>
+__device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
+                                                const float* sig_z, int64_t i0, int64_t i1, int steps,
+                                                unsigned long long* s_hist, unsigned long long* s_tally) {
+    Pair Q;
+    pair_clear(Q);
+    if (i0 < r.n) load_one(r, i0, Q, 0);
+    if (i1 < r.n) load_one(r, i1, Q, 1);
+    const bool live0 = i0 < r.n, live1 = i1 < r.n;
+    pair_loop<G>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
     if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
     if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
 }
@@ -341,6 +353,162 @@ __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t
     } else if (cur >= 0) {
         flush_shared<float>(s_hist, s_tally, s_run);
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// Streaming form for launches of a few steps (the state round-trips HBM): each CTA
+// prefetches the state of its next tile into shared memory with bulk copies (TMA,
+// cp.async.bulk) that complete on an mbarrier while it steps the current tile, so the
+// loads of one tile overlap the arithmetic of the previous one.  Single run; tiles
+// of 256 electrons (x pairs 2 KB, u 3 x 1 KB, tau pairs 2 KB per tile); the ragged
+// last tile and the optional event / wait words use plain loads.
+// ---------------------------------------------------------------------------
+constexpr int kStreamTile = 256;
+constexpr int kStageBytes = kStreamTile * (8 + 4 + 4 + 4 + 8);
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity to complete; gives up after about 2 s (returns false)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
+// thread 0: bulk copies of the full tile `tile` into stage buffer `buf`
+__device__ __forceinline__ void stream_issue(const RunDevT<float>& r, int64_t tile, unsigned char* buf, uint32_t bar) {
+    const int64_t base = tile * kStreamTile;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of buf first
+    mbar_expect_tx(bar, kStageBytes);
+    const uint32_t d = smem_addr(buf);
+    bulk_g2s(d, (const float2*)r.x + base, kStreamTile * 8, bar);
+    bulk_g2s(d + kStreamTile * 8, (const float*)r.ux + base, kStreamTile * 4, bar);
+    bulk_g2s(d + kStreamTile * 12, (const float*)r.uy + base, kStreamTile * 4, bar);
+    bulk_g2s(d + kStreamTile * 16, (const float*)r.uz + base, kStreamTile * 4, bar);
+    bulk_g2s(d + kStreamTile * 20, (const float2*)r.tau + base, kStreamTile * 8, bar);
+}
+
+// electron j of a staged tile into pair slot k (the optional words from global memory)
+__device__ __forceinline__ void stream_take(const RunDevT<float>& r, const unsigned char* buf, int j, int64_t i,
+                                            Pair& Q, int k) {
+    const float2 x = reinterpret_cast<const float2*>(buf)[j];
+    const float* u = reinterpret_cast<const float*>(buf + kStreamTile * 8);
+    const float2 tau = reinterpret_cast<const float2*>(buf + kStreamTile * 20)[j];
+    set_comp(Q.x, k, x.x); set_comp(Q.x_lo, k, x.y);
+    set_comp(Q.u0, k, u[j]); set_comp(Q.u1, k, u[kStreamTile + j]); set_comp(Q.u2, k, u[2 * kStreamTile + j]);
+    set_comp(Q.tau, k, tau.x); set_comp(Q.tau_lo, k, tau.y);
+    Q.wait[k] = r.wait ? r.wait[i] : PE_WAIT_NEVER;
+    if (r.events) {
+        unsigned long long e = r.events[i];
+        Q.ev_cnt[k] = (uint32_t)e;
+        Q.ev_hash[k] = (uint32_t)(e >> 32);
+    }
+    Q.act[k] = !isnan(x.x);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair_stream(TablesDev t, BatchDevT<float> b, int steps) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
+    float* s_h = reinterpret_cast<float*>(s_tally + PE_TALLY_WORDS);
+    float* s_sig = s_h + t.n_eta;
+    // stage buffers on a 128-byte boundary of the shared window after the tables
+    const uint32_t s0 = smem_addr(smem);
+    const uint32_t table_end = s0 + 8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + 4 * (t.n_eta + t.n_Z * t.n_E);
+    unsigned char* stage_buf = smem + (((table_end + 127u) & ~127u) - s0);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage_buf + 2 * kStageBytes);
+    const RunDevT<float>& r = b.runs[0];
+
+    for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
+    for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = t.h32[k];
+    for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = t.sig32[k];
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int64_t n_tiles = b.tile_start[1];
+    const int64_t n_full = r.n / kStreamTile;          // tiles with all 256 electrons present
+    const float* sig_z = s_sig + (size_t)r.iz * t.n_E;
+    uint32_t parity[2] = {0u, 0u};
+    bool pending[2] = {false, false};                   // a copy into the stage awaits its wait
+    bool stuck[2] = {false, false};                     // its wait ran out: the stage is not reused
+    bool broken = false;                                // after a timeout: plain loads only
+    int stage = 0;
+    int64_t tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < n_full) stream_issue(r, tile, stage_buf, bar0);
+    pending[0] = tile < n_full;
+    for (; tile < n_tiles; tile += gridDim.x) {
+        const int64_t next = tile + gridDim.x;
+        if (!broken && next < n_full) {
+            if (threadIdx.x == 0) stream_issue(r, next, stage_buf + (stage ^ 1) * kStageBytes, stage ? bar0 : bar1);
+            pending[stage ^ 1] = true;
+        }
+        const int64_t i0 = tile * kStreamTile + threadIdx.x, i1 = i0 + blockDim.x;
+        Pair Q;
+        pair_clear(Q);
+        bool staged = false;
+        if (pending[stage]) {
+            staged = mbar_wait(stage ? bar1 : bar0, parity[stage]);
+            pending[stage] = false;
+            if (staged) {
+                parity[stage] ^= 1u;
+            } else {
+                stuck[stage] = true;
+                broken = true;
+                if (threadIdx.x == 0) atomicAdd(s_tally + PE_T_N_WAIT_TIMEOUT, 1ull);
+            }
+        }
+        if (staged) {
+            const unsigned char* buf = stage_buf + stage * kStageBytes;
+            stream_take(r, buf, threadIdx.x, i0, Q, 0);
+            stream_take(r, buf, threadIdx.x + blockDim.x, i1, Q, 1);
+        } else {                                        // ragged last tile (or a timed-out copy)
+            if (i0 < r.n) load_one(r, i0, Q, 0);
+            if (i1 < r.n) load_one(r, i1, Q, 1);
+        }
+        const bool live0 = i0 < r.n, live1 = i1 < r.n;
+        pair_loop<G>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
+        if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
+        if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
+        __syncthreads();                                // the stage is read before it is refilled
+        stage ^= 1;
+    }
+    // copies still in flight after a timeout must land before the CTA exits (bounded again)
+    for (int k = 0; k < 2; ++k)
+        if (pending[k] || stuck[k]) mbar_wait(k ? bar1 : bar0, parity[k]);
+    if (n_tiles > 0) flush_shared<float>(s_hist, s_tally, r);
 }
 
 }  // namespace pe
