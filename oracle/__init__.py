@@ -124,6 +124,14 @@ def lib():
             L.or_boris.argtypes = [dp, dp, dp, C.c_double]
             L.or_null_x_hat.argtypes = [C.c_void_p, C.POINTER(RunParams)]
             L.or_null_x_hat.restype = C.c_double
+            L.or_pic_init.argtypes = [C.POINTER(RunParams), C.c_int, C.c_double, dp, C.c_int64, dp]
+            L.or_pic_init.restype = C.c_int
+            L.or_pic_run.argtypes = [C.c_void_p, C.POINTER(RunParams), C.c_int, C.c_double, C.POINTER(C.c_int64),
+                                     C.c_int64, C.c_int64, C.c_int64, dp, u32p, dp, C.c_void_p, C.c_int64,
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                     C.POINTER(C.c_uint64), C.c_int]
+            L.or_pic_run.restype = C.c_int
+            L.or_pic_gather.argtypes = [C.c_int, C.c_double, dp, C.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -264,6 +272,63 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
 def fixed_to_float(tally: np.ndarray, idx: int) -> float:
     """Value of a 128-bit fixed-point tally pair (lo, hi) in m c^2."""
     return float(int(tally[idx + 1])) + float(int(tally[idx])) / 2.0 ** 64
+
+
+# ---------------------------------------------------------------- 1D PIC ----
+def pic_grid_words(n_cells: int) -> int:
+    return 6 * n_cells + 5
+
+
+def pic_weight(run: RunParams, n_total: int) -> float:
+    """Areal density of one macro-electron: n_e (n_c) x slab thickness (c/omega) / electrons."""
+    kl = 2 * np.pi / run.lambda_m
+    return run.ne_over_nc * run.slab_thick_m * kl / n_total
+
+
+def pic_init(run: RunParams, n_cells: int, weight: float, state: np.ndarray) -> np.ndarray:
+    grid = np.zeros(pic_grid_words(n_cells))
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    rc = lib().or_pic_init(C.byref(run), n_cells, weight, _dp(st), len(st), _dp(grid))
+    if rc != 0:
+        raise RuntimeError("or_pic_init failed")
+    return grid
+
+
+def pic_run(tables: "Tables", run: RunParams, n_cells: int, weight: float, ids, state, grid, step0: int,
+            n_steps: int, capacity: int = 1 << 20, threads: int | None = None, events=None, wait=None):
+    """Advance particles (n x 6, in place) and grid (in place) together; returns
+    (photons, true photon count, hist, tally)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    assert state.dtype == np.float64 and state.flags.c_contiguous and state.shape == (len(ids), 6)
+    assert grid.dtype == np.float64 and grid.shape == (pic_grid_words(n_cells),)
+    photons = np.zeros(capacity, dtype=PHOTON_DTYPE)
+    hist = np.zeros(HIST_WORDS, dtype=np.uint64)
+    tally = np.zeros(TALLY_WORDS, dtype=np.uint64)
+    n_ph = C.c_int64(0)
+    nt = threads if threads else (os.cpu_count() or 1)
+    rc = lib().or_pic_run(tables._h, C.byref(run), n_cells, weight, ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                          len(ids), step0, n_steps, _dp(state), _wait_ptr(run, wait, len(ids)), _dp(grid),
+                          photons.ctypes.data_as(C.c_void_p), capacity, C.byref(n_ph),
+                          hist.ctypes.data_as(C.POINTER(C.c_uint64)), tally.ctypes.data_as(C.POINTER(C.c_uint64)),
+                          events.ctypes.data_as(C.POINTER(C.c_uint64)) if events is not None else None, nt)
+    if rc != 0:
+        raise RuntimeError("or_pic_run failed")
+    return photons[:min(n_ph.value, capacity)], n_ph.value, hist, tally
+
+
+def pic_fields(grid, n_cells: int):
+    """(ex at half nodes, ey, ez, by, bz at nodes, rho_ion at nodes) from a grid array."""
+    n = n_cells
+    ex = grid[:n]
+    fp, fm, gp, gm, rho = (grid[n + k * (n + 1): n + (k + 1) * (n + 1)] for k in range(5))
+    return ex, 0.5 * (fp + fm), 0.5 * (gp + gm), 0.5 * (gm - gp), 0.5 * (fp - fm), rho
+
+
+def pic_gather(grid, n_cells: int, dx: float, x: float):
+    E = np.zeros(3)
+    B = np.zeros(3)
+    lib().or_pic_gather(n_cells, dx, _dp(grid), x, _dp(E), _dp(B))
+    return E, B
 
 
 def null_x_hat(tables: Tables, run: RunParams) -> float:

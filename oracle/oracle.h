@@ -79,7 +79,7 @@ double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* abov
 
 /* ---- run description ------------------------------------------------------- */
 enum { OR_LP_Y = 0, OR_CP = 1 };
-enum { OR_PLANE_1D = 0, OR_GAUSS_2D = 1, OR_CONST = 2 };
+enum { OR_PLANE_1D = 0, OR_GAUSS_2D = 1, OR_CONST = 2, OR_PIC_1D = 3 };
 enum { OR_REST = 0, OR_MAXWELL_JUTTNER = 1, OR_BEAM = 2 };
 
 typedef struct {
@@ -144,6 +144,32 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
 /* events (nullable): per particle, low 32 bits = NCS count | brems count << 16,
  * high 32 bits = sum over emissions of (step + 1) * (1 or 0x9E3779B1 for brems)
  * mod 2^32 -- a fingerprint of the particle's event list.                     */
+
+/* ---- 1D electromagnetic PIC around the step ------------------------------
+ * Geometry OR_PIC_1D: the fields at the particles come from a grid that the
+ * electrons' own currents and the injected laser drive (the paper's PIC host with
+ * the field solver and weighting on).  n_cells cells over [0, L], dx = c dt;
+ * grid layout (doubles, n = n_cells):
+ *   ex[n]     E_x at half nodes (i + 1/2) dx
+ *   fp[n+1]   E_y + B_z at nodes i dx (moves along +x)
+ *   fm[n+1]   E_y - B_z (moves along -x)
+ *   gp[n+1]   E_z - B_y (moves along +x)
+ *   gm[n+1]   E_z + B_y (moves along -x)
+ *   rho[n+1]  immobile ion charge density at the nodes (the electrons' initial
+ *             charge with the opposite sign)
+ * weight: areal density of one macro-electron (n_c c/omega units).           */
+#define OR_PIC_GRID_WORDS(n) (6 * (int64_t)(n) + 5)
+/* grid after or_init: zero fields, rho from the initial electrons (state) */
+int or_pic_init(const or_run_params* r, int n_cells, double weight, const double* state, int64_t n, double* grid);
+/* Advance particles and grid together (step-major); arguments as or_run.  The
+ * particle list must be the whole run (the currents of all electrons drive the
+ * fields).  Electrons leaving [0, L] are removed.                            */
+int or_pic_run(const or_tables* t, const or_run_params* r, int n_cells, double weight, const int64_t* ids,
+               int64_t n_ids, int64_t step0, int64_t n_steps, double* state, uint32_t* wait, double* grid,
+               or_photon* photons, int64_t cap, int64_t* n_photons, uint64_t* hist, uint64_t* tally,
+               uint64_t* events, int n_threads);
+/* fields at x from the grid (linear weights; zero beyond the grid) */
+void or_pic_gather(int n_cells, double dx, const double* grid, double x, double E[3], double B[3]);
 
 /* normalised helpers (exposed for unit pins) */
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */

@@ -383,6 +383,113 @@ static void note_event(uint64_t* ev, int64_t n, int mech) {
     *ev = ((uint64_t)hs << 32) | cnt;
 }
 
+/* One step n of one particle in the fields E, B at (x^n, t^n) (Sec. 2.2 order):
+ * push, NCS optical depth and emission, brems test (Eq. 4, direct or null
+ * collisions), position update, absorbing box.                               */
+static void particle_step(const or_tables* t, const or_run_params* r, const run_ctx* c, int64_t id, int64_t n,
+                          double* px, double* py, double u[3], double* ptau, uint32_t* wait, const double E[3],
+                          const double B[3], plist* pl, uint64_t* hist, uint64_t* tally, uint64_t* ev) {
+    double x = *px, y = *py, tau = *ptau;
+    or_boris(u, E, B, c->dt);
+    double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (r->enable_ncs) {
+        double eta = or_eta(u, E, B, c->E_S);
+        int fl;
+        double h = or_ncs_h_interp(t, eta, &fl);
+        if (fl == 1) tally[ORT_N_ETA_ABOVE]++;
+        tau -= c->C_ncs * (eta / gamma) * h * c->dt;
+        if (tau <= 0.0) {
+            uint32_t w[4];
+            draw(r, id, (uint32_t)n, PUR_NCS, w);
+            int below;
+            double delta = or_sample_ncs_delta(t, eta, u53(word64(w[0], w[1])), &below);
+            if (below) tally[ORT_N_ETA_BELOW]++;
+            double ew = delta * gamma;
+            if (ew > gamma - 1.0) { ew = gamma - 1.0; tally[ORT_N_CLAMP]++; }
+            double k[3];
+            recoil(u, gamma, ew, k);
+            note_event(ev, n, 0);
+            double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            fx_add(tally + ORT_E_RECOIL_NCS, gamma - gn);
+            if (ew >= c->photon_min) {
+                tally[ORT_N_NCS_STORED]++;
+                tally[ORT_N_PHOTONS]++;
+                fx_add(tally + ORT_E_NCS_STORED, ew);
+                record(c, x, y, ew, k, (uint32_t)n, id, 0, pl, hist, tally);
+            } else {
+                tally[ORT_N_NCS_BELOW]++;
+                fx_add(tally + ORT_E_NCS_BELOW, ew);
+            }
+            gamma = gn;
+            tau = -log(u53(word64(w[2], w[3])));
+        }
+    }
+    if (r->enable_brems) {
+        int in_slab = (x >= c->x0 && x <= c->x1);
+        if (r->geometry == OR_GAUSS_2D && fabs(y) > c->yh) in_slab = 0;
+        int nullc = (r->brems_method == OR_BREMS_NULL);
+        /* direct method: every step in the slab is a test (Eq. 4); null
+         * collisions: only the candidate steps of the majorant process  */
+        int test = nullc ? (*wait == 0) : (in_slab && gamma > 1.0 + c->photon_min);
+        if (nullc && !test && *wait != OR_WAIT_NEVER) --*wait;
+        if (test) {
+            double P = 0.0;                  /* Eq. 4 probability of this step */
+            if (in_slab && gamma > 1.0 + c->photon_min) {
+                int above;
+                double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
+                if (above) tally[ORT_N_GAMMA_ABOVE]++;
+                double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double xb = c->K_br * sig * (um / gamma);
+                P = -expm1(-xb);
+            }
+            double p_acc = nullc ? P / c->P_hat : P;
+            /* direct: one draw of purpose 0 at step n (test word, photon-energy word);
+             * null: one draw of purpose 256 at step n + 1 (next-wait word, test word),
+             * and purpose 0 at step n only for a collision (photon-energy word)  */
+            uint32_t w[4], v[4];
+            uint64_t U;
+            if (nullc) {
+                draw(r, id, (uint32_t)n + 1u, PUR_WAIT, v);
+                U = word64(v[2], v[3]);
+            } else {
+                draw(r, id, (uint32_t)n, PUR_BREMS, w);
+                U = word64(w[0], w[1]);
+            }
+            uint64_t thr = (uint64_t)floor(p_acc * 18446744073709551616.0);
+            if (p_acc >= 1.0) thr = UINT64_MAX;
+            if (U < thr) {
+                if (nullc) draw(r, id, (uint32_t)n, PUR_BREMS, w);
+                double yy = or_sample_brems_y(t, r->iz, gamma, u53(word64(w[2], w[3])));
+                double ew = yy * gamma;
+                double k[3];
+                recoil(u, gamma, ew, k);
+                note_event(ev, n, 1);
+                double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                fx_add(tally + ORT_E_RECOIL_BR, gamma - gn);
+                if (ew >= c->photon_min) {
+                    tally[ORT_N_BR_STORED]++;
+                    tally[ORT_N_PHOTONS]++;
+                    fx_add(tally + ORT_E_BR_STORED, ew);
+                    record(c, x, y, ew, k, (uint32_t)n, id, 1, pl, hist, tally);
+                } else {
+                    tally[ORT_N_BR_BELOW]++;
+                    fx_add(tally + ORT_E_BR_BELOW, ew);
+                }
+                gamma = gn;
+            }
+            if (nullc) *wait = wait_draw(c->x_hat, word64(v[0], v[1]));
+        }
+    }
+    x += c->dt * u[0] / gamma;
+    if (r->geometry == OR_GAUSS_2D) y += c->dt * u[1] / gamma;
+    if (r->box_enable && (x < c->box0 || x > c->box1)) {
+        x = NAN;
+        tally[ORT_N_KILLED]++;
+        tally[ORT_KILLED_STEPS] += (uint64_t)(n + 1);
+    }
+    *px = x; *py = y; *ptau = tau;
+}
+
 static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c, int64_t id,
                     int64_t step0, int64_t n_steps, double* s, uint32_t* wait, plist* pl, uint64_t* hist,
                     uint64_t* tally, uint64_t* ev) {
@@ -394,103 +501,7 @@ static void run_one(const or_tables* t, const or_run_params* r, const run_ctx* c
         double tn = (double)n * c->dt;
         double E[3], B[3];
         or_fields(r, x, y, tn, E, B);
-        or_boris(u, E, B, c->dt);
-        double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        if (r->enable_ncs) {
-            double eta = or_eta(u, E, B, c->E_S);
-            int fl;
-            double h = or_ncs_h_interp(t, eta, &fl);
-            if (fl == 1) tally[ORT_N_ETA_ABOVE]++;
-            tau -= c->C_ncs * (eta / gamma) * h * c->dt;
-            if (tau <= 0.0) {
-                uint32_t w[4];
-                draw(r, id, (uint32_t)n, PUR_NCS, w);
-                int below;
-                double delta = or_sample_ncs_delta(t, eta, u53(word64(w[0], w[1])), &below);
-                if (below) tally[ORT_N_ETA_BELOW]++;
-                double ew = delta * gamma;
-                if (ew > gamma - 1.0) { ew = gamma - 1.0; tally[ORT_N_CLAMP]++; }
-                double k[3];
-                recoil(u, gamma, ew, k);
-                note_event(ev, n, 0);
-                double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                fx_add(tally + ORT_E_RECOIL_NCS, gamma - gn);
-                if (ew >= c->photon_min) {
-                    tally[ORT_N_NCS_STORED]++;
-                    tally[ORT_N_PHOTONS]++;
-                    fx_add(tally + ORT_E_NCS_STORED, ew);
-                    record(c, x, y, ew, k, (uint32_t)n, id, 0, pl, hist, tally);
-                } else {
-                    tally[ORT_N_NCS_BELOW]++;
-                    fx_add(tally + ORT_E_NCS_BELOW, ew);
-                }
-                gamma = gn;
-                tau = -log(u53(word64(w[2], w[3])));
-            }
-        }
-        if (r->enable_brems) {
-            int in_slab = (x >= c->x0 && x <= c->x1);
-            if (r->geometry == OR_GAUSS_2D && fabs(y) > c->yh) in_slab = 0;
-            int nullc = (r->brems_method == OR_BREMS_NULL);
-            /* direct method: every step in the slab is a test (Eq. 4); null
-             * collisions: only the candidate steps of the majorant process  */
-            int test = nullc ? (*wait == 0) : (in_slab && gamma > 1.0 + c->photon_min);
-            if (nullc && !test && *wait != OR_WAIT_NEVER) --*wait;
-            if (test) {
-                double P = 0.0;                  /* Eq. 4 probability of this step */
-                if (in_slab && gamma > 1.0 + c->photon_min) {
-                    int above;
-                    double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
-                    if (above) tally[ORT_N_GAMMA_ABOVE]++;
-                    double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                    double xb = c->K_br * sig * (um / gamma);
-                    P = -expm1(-xb);
-                }
-                double p_acc = nullc ? P / c->P_hat : P;
-                /* direct: one draw of purpose 0 at step n (test word, photon-energy word);
-                 * null: one draw of purpose 256 at step n + 1 (next-wait word, test word),
-                 * and purpose 0 at step n only for a collision (photon-energy word)  */
-                uint32_t w[4], v[4];
-                uint64_t U;
-                if (nullc) {
-                    draw(r, id, (uint32_t)n + 1u, PUR_WAIT, v);
-                    U = word64(v[2], v[3]);
-                } else {
-                    draw(r, id, (uint32_t)n, PUR_BREMS, w);
-                    U = word64(w[0], w[1]);
-                }
-                uint64_t thr = (uint64_t)floor(p_acc * 18446744073709551616.0);
-                if (p_acc >= 1.0) thr = UINT64_MAX;
-                if (U < thr) {
-                    if (nullc) draw(r, id, (uint32_t)n, PUR_BREMS, w);
-                    double yy = or_sample_brems_y(t, r->iz, gamma, u53(word64(w[2], w[3])));
-                    double ew = yy * gamma;
-                    double k[3];
-                    recoil(u, gamma, ew, k);
-                    note_event(ev, n, 1);
-                    double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                    fx_add(tally + ORT_E_RECOIL_BR, gamma - gn);
-                    if (ew >= c->photon_min) {
-                        tally[ORT_N_BR_STORED]++;
-                        tally[ORT_N_PHOTONS]++;
-                        fx_add(tally + ORT_E_BR_STORED, ew);
-                        record(c, x, y, ew, k, (uint32_t)n, id, 1, pl, hist, tally);
-                    } else {
-                        tally[ORT_N_BR_BELOW]++;
-                        fx_add(tally + ORT_E_BR_BELOW, ew);
-                    }
-                    gamma = gn;
-                }
-                if (nullc) *wait = wait_draw(c->x_hat, word64(v[0], v[1]));
-            }
-        }
-        x += c->dt * u[0] / gamma;
-        if (r->geometry == OR_GAUSS_2D) y += c->dt * u[1] / gamma;
-        if (r->box_enable && (x < c->box0 || x > c->box1)) {
-            x = NAN;
-            tally[ORT_N_KILLED]++;
-            tally[ORT_KILLED_STEPS] += (uint64_t)(n + 1);
-        }
+        particle_step(t, r, c, id, n, &x, &y, u, &tau, wait, E, B, pl, hist, tally, ev);
     }
     s[0] = x; s[1] = y; s[2] = u[0]; s[3] = u[1]; s[4] = u[2]; s[5] = tau;
 }
@@ -539,5 +550,206 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
     }
     *n_photons = total;
     free(lists); free(th_hist); free(th_tally);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 1D electromagnetic PIC around the step.                                   */
+/* Normalised Maxwell equations (c = 1, E and B in m c omega / e, J in        */
+/* e n_c c, so that dE/dt = curl B - J).  In 1D the transverse fields split   */
+/* into waves along +x and -x: F+- = E_y +- B_z and G+- = E_z -+ B_y obey     */
+/* dF+-/dt +- dF+-/dx = -J_y and dG+-/dt +- dG+-/dx = -J_z.  With dx = dt      */
+/* each is carried one cell per step along its characteristic, the current   */
+/* taken at the midpoint of the path (half node, half step):                  */
+/*   F+_i^{n+1} = F+_{i-1}^n - dt J_y,i-1/2^{n+1/2},                          */
+/*   F-_i^{n+1} = F-_{i+1}^n - dt J_y,i+1/2^{n+1/2}  (same for G with J_z),   */
+/* which propagates vacuum waves exactly and, unlike the Yee scheme at        */
+/* dx = dt, stays stable with a plasma; E_x^{n+1} = E_x^n - dt J_x^{n+1/2} at */
+/* half nodes (Gauss's law is kept by the charge-conserving current).  The    */
+/* laser enters at x = 0 (F+_0 = 2 g_y, G+_0 = 2 g_z, g the incident field);   */
+/* nothing enters at x = L (F-_N = G-_N = 0); outgoing waves leave freely.    */
+/* One step: particles in E^n, B^n (gathered by linear weights) -> x^{n+1};   */
+/* currents J^{n+1/2} by linear weighting; fields to n + 1.  Currents are     */
+/* summed in 2^-36 fixed point per contribution (exact and order-free, the    */
+/* same rule the device code uses).                                          */
+/* ------------------------------------------------------------------------- */
+#define PIC_FX 68719476736.0                  /* 2^36 */
+
+/* weight of grid point k (node, or half node with off = 0.5) for a particle at s = x/dx */
+static double lin_w(double s, int64_t k, double off) {
+    double d = fabs(s - ((double)k + off));
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+void or_pic_gather(int n_cells, double dx, const double* grid, double x, double E[3], double B[3]) {
+    const int64_t n = n_cells;
+    const double* ex = grid;
+    const double* fp = ex + n;
+    const double* fm = fp + n + 1;
+    const double* gp = fm + n + 1;
+    const double* gm = gp + n + 1;
+    double s = x / dx;
+    int64_t i = (int64_t)floor(s);
+    double f = s - (double)i;
+    double v[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int k = 0; k < 2; ++k) {
+        int64_t m = i + k;
+        if (m >= 0 && m <= n) { v[0][k] = fp[m]; v[1][k] = fm[m]; v[2][k] = gp[m]; v[3][k] = gm[m]; }
+    }
+    double Fp = (1.0 - f) * v[0][0] + f * v[0][1], Fm = (1.0 - f) * v[1][0] + f * v[1][1];
+    double Gp = (1.0 - f) * v[2][0] + f * v[2][1], Gm = (1.0 - f) * v[3][0] + f * v[3][1];
+    E[1] = 0.5 * (Fp + Fm);
+    B[2] = 0.5 * (Fp - Fm);
+    E[2] = 0.5 * (Gp + Gm);
+    B[1] = 0.5 * (Gm - Gp);
+    B[0] = 0.0;
+    /* E_x at half nodes j + 1/2 */
+    double sh = s - 0.5;
+    int64_t j = (int64_t)floor(sh);
+    double fh = sh - (double)j;
+    double h0 = (j >= 0 && j < n) ? ex[j] : 0.0, h1 = (j + 1 >= 0 && j + 1 < n) ? ex[j + 1] : 0.0;
+    E[0] = (1.0 - fh) * h0 + fh * h1;
+}
+
+int or_pic_init(const or_run_params* r, int n_cells, double weight, const double* state, int64_t n, double* grid) {
+    if (n_cells < 4 || !grid) return -1;
+    memset(grid, 0, sizeof(double) * (size_t)OR_PIC_GRID_WORDS(n_cells));
+    double* rho = grid + n_cells + 4 * ((int64_t)n_cells + 1);
+    double dx = r->dt_over_T * 2.0 * M_PI;
+    for (int64_t p = 0; p < n; ++p) {
+        double x = state[6 * p];
+        if (isnan(x)) continue;
+        double s = x / dx;
+        int64_t i0 = (int64_t)floor(s);
+        for (int64_t k = i0; k <= i0 + 1; ++k)
+            if (k >= 0 && k <= n_cells) rho[k] += weight * lin_w(s, k, 0.0) / dx;   /* ions +, electrons - */
+    }
+    return 0;
+}
+
+/* Current of one electron moving from x_old to x_new (|x_new - x_old| < dx) with
+ * velocity (u/gamma): J_x at half nodes from the change of its node weights
+ * (cumulative, charge conserving), J_y, J_z at half nodes with the mean of its
+ * half-node weights at the two positions.  Accumulated as dimensionless
+ * fixed-point sums; the caller applies the weight and the charge sign.       */
+static void pic_deposit(double dx, int n_cells, double x_old, double x_new, const double u[3], double gamma,
+                        int64_t* ax, int64_t* ay, int64_t* az) {
+    double so = x_old / dx, sn = x_new / dx;
+    int64_t ia = (int64_t)floor(fmin(so, sn));
+    double cum = 0.0;
+    for (int64_t k = ia; k <= ia + 1; ++k) {          /* half nodes ia, ia+1 (node ia+2 closes the sum) */
+        cum += lin_w(sn, k, 0.0) - lin_w(so, k, 0.0);
+        if (k >= 0 && k < n_cells) ax[k] += (int64_t)nearbyint(cum * PIC_FX);
+    }
+    double vy = u[1] / gamma, vz = u[2] / gamma;
+    for (int64_t k = ia - 1; k <= ia + 1; ++k) {      /* half nodes touched by either position */
+        double sbar = 0.5 * (lin_w(so, k, 0.5) + lin_w(sn, k, 0.5));
+        if (sbar > 0.0 && k >= 0 && k < n_cells) {
+            ay[k] += (int64_t)nearbyint(vy * sbar * PIC_FX);
+            az[k] += (int64_t)nearbyint(vz * sbar * PIC_FX);
+        }
+    }
+}
+
+int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double weight, const int64_t* ids,
+               int64_t n_ids, int64_t step0, int64_t n_steps, double* state, uint32_t* wait, double* grid,
+               or_photon* photons, int64_t cap, int64_t* n_photons, uint64_t* hist, uint64_t* tally,
+               uint64_t* events, int n_threads) {
+    if (!t || !r0 || n_ids < 0 || n_steps < 0 || n_cells < 4 || !grid) return -1;
+    if (r0->brems_method == OR_BREMS_NULL && !wait && n_ids > 0) return -1;
+    or_run_params rr = *r0;
+    const double kl = 2.0 * M_PI / rr.lambda_m;
+    const double dt = rr.dt_over_T * 2.0 * M_PI, dx = dt;
+    const int64_t n = n_cells;
+    rr.box_enable = 1;                                   /* electrons leaving the grid are removed */
+    rr.box_x_m[0] = 0.0;
+    rr.box_x_m[1] = (double)n * dx / kl;
+    const or_run_params* r = &rr;
+    run_ctx c;
+    make_ctx(t, r, &c, or__photon_min(t));
+    int nt = n_threads > 0 ? n_threads : 1;
+    plist* lists = (plist*)calloc(n_ids > 0 ? n_ids : 1, sizeof(plist));
+    uint64_t* th_hist = (uint64_t*)calloc((size_t)nt * OR_HIST_WORDS, sizeof(uint64_t));
+    uint64_t* th_tally = (uint64_t*)calloc((size_t)nt * ORT_WORDS, sizeof(uint64_t));
+    int64_t* acc = (int64_t*)calloc((size_t)nt * 3 * n, sizeof(int64_t));
+    int64_t* jsum = (int64_t*)calloc((size_t)3 * n, sizeof(int64_t));
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    double* ex = grid;
+    double* fp = ex + n;
+    double* fm = fp + n + 1;
+    double* gp = fm + n + 1;
+    double* gm = gp + n + 1;
+    for (int64_t s_ = step0; s_ < step0 + n_steps; ++s_) {
+        memset(acc, 0, sizeof(int64_t) * (size_t)nt * 3 * n);
+        /* particles in E^n, B^n; currents J^{n+1/2} */
+#pragma omp parallel for num_threads(nt) schedule(static)
+        for (int64_t k = 0; k < n_ids; ++k) {
+            int me = 0;
+#ifdef _OPENMP
+            me = omp_get_thread_num();
+#endif
+            double* s = state + 6 * k;
+            if (isnan(s[0])) continue;
+            double x = s[0], y = s[1], u[3] = {s[2], s[3], s[4]}, tau = s[5];
+            double E[3], B[3];
+            or_pic_gather(n_cells, dx, grid, x, E, B);
+            double x_old = x;
+            particle_step(t, r, &c, ids[k], s_, &x, &y, u, &tau, wait ? wait + k : NULL, E, B, &lists[k],
+                          th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS,
+                          events ? events + k : NULL);
+            if (!isnan(x)) {
+                double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                int64_t* a = acc + (size_t)me * 3 * n;
+                pic_deposit(dx, n_cells, x_old, x, u, gamma, a, a + n, a + 2 * n);
+            }
+            s[0] = x; s[1] = y; s[2] = u[0]; s[3] = u[1]; s[4] = u[2]; s[5] = tau;
+        }
+        memset(jsum, 0, sizeof(int64_t) * 3 * (size_t)n);
+        for (int th = 0; th < nt; ++th)
+            for (int64_t k = 0; k < 3 * n; ++k) jsum[k] += acc[(size_t)th * 3 * n + k];
+        /* J_x = (w/dt) sum dS (the electron charge -1 included), J_y,z = -(w/dx) sum v S */
+        const double kx = weight / dt / PIC_FX, kyz = -weight / dx / PIC_FX;
+        const int64_t* jx = jsum;
+        const int64_t* jy = jsum + n;
+        const int64_t* jz = jsum + 2 * n;
+        for (int64_t j = 0; j < n; ++j) ex[j] -= dt * kx * (double)jx[j];
+        /* waves along +x: node i from node i - 1 through half node i - 1 */
+        double gy, gz;
+        plane_e(r, (double)(s_ + 1) * dt, &gy, &gz);      /* incident field at x = 0, t^{n+1} */
+        memcpy(tmp, fp, sizeof(double) * (size_t)(n + 1));
+        for (int64_t i = 1; i <= n; ++i) fp[i] = tmp[i - 1] - dt * kyz * (double)jy[i - 1];
+        fp[0] = 2.0 * gy;
+        memcpy(tmp, gp, sizeof(double) * (size_t)(n + 1));
+        for (int64_t i = 1; i <= n; ++i) gp[i] = tmp[i - 1] - dt * kyz * (double)jz[i - 1];
+        gp[0] = 2.0 * gz;
+        /* waves along -x: node i from node i + 1 through half node i */
+        memcpy(tmp, fm, sizeof(double) * (size_t)(n + 1));
+        for (int64_t i = 0; i < n; ++i) fm[i] = tmp[i + 1] - dt * kyz * (double)jy[i];
+        fm[n] = 0.0;
+        memcpy(tmp, gm, sizeof(double) * (size_t)(n + 1));
+        for (int64_t i = 0; i < n; ++i) gm[i] = tmp[i + 1] - dt * kyz * (double)jz[i];
+        gm[n] = 0.0;
+    }
+    for (int k = 0; k < nt; ++k) {
+        const uint64_t* th = th_tally + (size_t)k * ORT_WORDS;
+        for (int i = 0; i < OR_HIST_WORDS; ++i) hist[i] += th_hist[(size_t)k * OR_HIST_WORDS + i];
+        for (int i = 0; i < ORT_E_NCS_STORED; ++i) tally[i] += th[i];
+        for (int i = ORT_E_NCS_STORED; i <= ORT_E_RECOIL_BR; i += 2) {
+            uint64_t old = tally[i];
+            tally[i] = old + th[i];
+            if (tally[i] < old) tally[i + 1] += 1;
+            tally[i + 1] += th[i + 1];
+        }
+    }
+    int64_t total = 0;
+    for (int64_t k = 0; k < n_ids; ++k) {
+        for (int64_t j = 0; j < lists[k].n; ++j) {
+            if (total < cap) photons[total] = lists[k].v[j];
+            ++total;
+        }
+        free(lists[k].v);
+    }
+    *n_photons = total;
+    free(lists); free(th_hist); free(th_tally); free(acc); free(jsum); free(tmp);
     return 0;
 }

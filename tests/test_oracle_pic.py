@@ -1,0 +1,160 @@
+"""Pins of the oracle's 1D electromagnetic PIC around the emission step.
+
+The fields at the electrons come from a grid driven by their own currents and by
+the laser injected at x = 0 (the paper's PIC host with field solver and weighting
+on).  Pinned against: the exact vacuum solution (the incident wave) at dx = c dt,
+the cold-plasma frequency omega_p = sqrt(n_e / n_c) and its density scaling,
+Gauss's law kept by the charge-conserving current, reflection by an overdense and
+transmission through an underdense slab with the energy balance closed, the
+prescribed-field step for an electron too light to perturb the fields, and the
+photon-energy bookkeeping.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+DT = 0.01 * 2 * math.pi          # dt = T/100; dx = c dt
+KL = 2 * math.pi / 1e-6
+
+
+def _tables():
+    return O.Tables(O.table_params(n_eta=16, n_y=16, n_E=16, n_s=16), [13.0])
+
+
+def _plasma(t, nc, N, **kw):
+    d = dict(geometry=3, charge_state=1.0, Z=13.0, enable_ncs=0, enable_brems=0, init_dist=0, seed=4,
+             flat_s=10e-15, ramp_periods=2.0)
+    d.update(kw)
+    r = O.run_params(**d)
+    ids = np.arange(N)
+    st = O.init(t, r, ids)
+    w = O.pic_weight(r, N) if N else 0.0
+    grid = O.pic_init(r, nc, w, st)
+    return r, ids, st, w, grid
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_pic_vacuum_injection_is_exact(pol):
+    """No plasma: the laser injected at x = 0 is the incident plane wave everywhere on the grid
+    (E and B at the nodes) to rounding, at dx = c dt."""
+    t = _tables()
+    nc = 2500
+    r, ids, st, w, grid = _plasma(t, nc, 0, a0=3.0, polarisation=pol, ne_over_nc=0.0)
+    O.pic_run(t, r, nc, w, ids, st, grid, 0, 1800, capacity=16)
+    ex, ey, ez, by, bz, rho = O.pic_fields(grid, nc)
+    x = np.arange(nc + 1) * DT
+    F = np.array([np.concatenate(O.fields(r, xi, 0.0, 1800 * DT)) for xi in x])
+    assert np.abs(F[:, 1]).max() > 2.5
+    for got, want in ((ey, F[:, 1]), (ez, F[:, 2]), (by, F[:, 4]), (bz, F[:, 5])):
+        assert np.abs(got - want).max() < 1e-12 * 3.0
+    assert np.all(ex == 0.0)
+
+
+def _crossing_spacing(ne):
+    t = _tables()
+    nc = 1000
+    r, ids, st, w, grid = _plasma(t, nc, 20000, a0=0.0, ne_over_nc=ne, slab_x0_m=2e-6, slab_thick_m=4e-6, seed=3)
+    st[:, 2] = 0.01                                   # a small uniform drift starts the oscillation
+    um = []
+    for k in range(160):
+        O.pic_run(t, r, nc, w, ids, st, grid, 2 * k, 2, capacity=16)
+        um.append(st[:, 2].mean())
+    um = np.array(um)
+    s = np.sign(um)
+    zc = np.where(s[:-1] != s[1:])[0]
+    # linear interpolation of the crossing times (in steps)
+    tz = np.array([2 * (k + 1) + 2 * um[k] / (um[k] - um[k + 1]) for k in zc])
+    return np.diff(tz).mean()
+
+
+def test_pic_plasma_frequency():
+    """A cold slab given a uniform drift oscillates at omega_p = sqrt(n_e/n_c): the mean momentum
+    changes sign every pi/omega_p; quadrupling the density halves the period."""
+    half = _crossing_spacing(0.25)
+    expect = math.pi / math.sqrt(0.25) / DT
+    assert abs(half / expect - 1) < 0.03, (half, expect)
+    half4 = _crossing_spacing(1.0)
+    assert abs(half / half4 / 2.0 - 1) < 0.03, (half, half4)
+
+
+def test_pic_gauss_law():
+    """The charge-conserving current keeps div E_x = rho_ion + rho_e on every interior node while a
+    laser drives a warm slab (to the 2^-36 quantum of the current sums)."""
+    t = _tables()
+    nc = 1500
+    r, ids, st, w, grid = _plasma(t, nc, 5000, a0=5.0, ne_over_nc=5.0, slab_x0_m=5e-6, slab_thick_m=2e-6,
+                                  init_dist=1, T_mev=0.05)
+    O.pic_run(t, r, nc, w, ids, st, grid, 0, 900, capacity=16)
+    ex, ey, ez, by, bz, rho = O.pic_fields(grid, nc)
+    rho_e = np.zeros(nc + 1)
+    live = ~np.isnan(st[:, 0])
+    s = st[live, 0] / DT
+    i = np.floor(s).astype(int)
+    f = s - i
+    np.add.at(rho_e, i, -w * (1 - f) / DT)
+    np.add.at(rho_e, i + 1, -w * f / DT)
+    res = (ex[1:] - ex[:-1]) / DT - (rho[1:-1] + rho_e[1:-1])
+    assert np.abs(ex).max() > 0.1                     # a real charge separation
+    assert np.abs(res).max() < 1e-9 * np.abs(rho_e).max()
+
+
+def _slab_energy(ne, a0=1.0, steps=1800):
+    t = _tables()
+    nc = 3000
+    r, ids, st, w, grid = _plasma(t, nc, 20000, a0=a0, ne_over_nc=ne, slab_x0_m=10e-6, slab_thick_m=2e-6)
+    O.pic_run(t, r, nc, w, ids, st, grid, 0, steps, capacity=16)
+    ex, ey, ez, by, bz, rho = O.pic_fields(grid, nc)
+    x = np.arange(nc + 1) * DT
+    dens = 0.5 * (ey ** 2 + bz ** 2 + ez ** 2 + by ** 2) * DT
+    left, right = dens[x < 10e-6 * KL].sum(), dens[x > 12e-6 * KL].sum()
+    g = np.sqrt(1 + (st[:, 2:5] ** 2).sum(1))
+    kin = w * np.nansum(g - 1)
+    exe = 0.5 * (ex ** 2).sum() * DT
+    xs = np.arange(0, 300, DT)
+    inc = sum(O.fields(r, xi, 0, 150.0)[0][1] ** 2 for xi in xs) * DT
+    return left / inc, right / inc, (left + right + kin + exe) / inc
+
+
+def test_pic_reflection_and_transmission():
+    """A 10 n_c slab reflects the a0 = 1 pulse, a 0.1 n_c slab lets it through; the field,
+    kinetic and charge-separation energies add up to the incident pulse energy."""
+    refl, trans, tot = _slab_energy(10.0)
+    assert refl > 0.97 and trans < 0.005 and abs(tot - 1) < 0.01, (refl, trans, tot)
+    refl, trans, tot = _slab_energy(0.1)
+    assert trans > 0.95 and refl < 0.02, (refl, trans, tot)
+
+
+def test_pic_light_electron_follows_prescribed_fields():
+    """Electrons whose weight is negligible feel the injected wave only: their PIC trajectories
+    converge to the prescribed plane-wave step of the oracle at second order in dx = c dt (the
+    linear interpolation of the grid fields); the error falls by ~4 per halving of the step."""
+    t = _tables()
+    errs = []
+    for dto, steps, nc in ((0.01, 900, 1200), (0.005, 1800, 2400)):
+        kw = dict(a0=2.0, ne_over_nc=1e-12, slab_x0_m=2e-6, slab_thick_m=1e-6, init_dist=0, seed=8, dt_over_T=dto)
+        r, ids, st, w, grid = _plasma(t, nc, 64, **kw)
+        ref = st.copy()
+        O.pic_run(t, r, nc, w, ids, st, grid, 0, steps, capacity=16)
+        rp = O.run_params(**dict(kw, geometry=0, charge_state=1.0, Z=13.0, enable_ncs=0, enable_brems=0,
+                                 flat_s=10e-15, ramp_periods=2.0))
+        O.run(t, rp, ids, ref, 0, steps, capacity=16)
+        assert np.abs(ref[:, 3]).max() > 1.0
+        errs.append(np.abs(st[:, 2:5] - ref[:, 2:5]).max() / 2.0)
+    assert errs[0] < 0.02 and 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+def test_pic_emission_bookkeeping():
+    """With emission on, the electrons' recoil energy equals the photon energy emitted (1e-12)."""
+    t = O.Tables(O.table_params(n_eta=32, n_y=32, n_E=32, n_s=32), [79.0])
+    nc = 800
+    r, ids, st, w, grid = _plasma(t, nc, 400, a0=200.0, ne_over_nc=5.0, Z=79.0, charge_state=51.0,
+                                  slab_x0_m=2e-6, slab_thick_m=1e-6, enable_ncs=1, enable_brems=1, init_dist=1,
+                                  T_mev=1.0)
+    ph, n, hist, tally = O.pic_run(t, r, nc, w, ids, st, grid, 0, 600, capacity=1 << 18)
+    emitted = sum(O.fixed_to_float(tally, O.T[k]) for k in ("E_NCS_STORED", "E_NCS_BELOW", "E_BR_STORED", "E_BR_BELOW"))
+    recoil = O.fixed_to_float(tally, O.T["E_RECOIL_NCS"]) + O.fixed_to_float(tally, O.T["E_RECOIL_BR"])
+    assert tally[O.T["N_NCS_STORED"]] + tally[O.T["N_NCS_BELOW"]] > 50
+    assert abs(recoil / emitted - 1) < 1e-12
