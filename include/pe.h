@@ -53,11 +53,13 @@ typedef enum {
 } pe_status;
 
 enum { PE_LP_Y = 0, PE_CP = 1 };                          /* polarisation                */
-enum { PE_PLANE_1D = 0, PE_GAUSS_2D = 1, PE_CONST = 2 };  /* field geometry              */
+enum { PE_PLANE_1D = 0, PE_GAUSS_2D = 1, PE_CONST = 2, PE_PIC_1D = 3 };  /* field geometry */
 enum { PE_F64 = 0, PE_F32 = 1 };                          /* arithmetic of the step      */
 enum { PE_REST = 0, PE_MAXWELL_JUTTNER = 1, PE_BEAM = 2, PE_CALLER = 3 };  /* initial state */
 enum { PE_BREMS_DIRECT = 0, PE_BREMS_NULL = 1 };          /* bremsstrahlung MC method    */
 #define PE_WAIT_NEVER 0xFFFFFFFFu   /* brems_wait value: no further candidate in this run */
+#define PE_PIC_GRID_WORDS(n) (6 * (int64_t)(n) + 5)   /* grid words of a PE_PIC_1D run */
+#define PE_PIC_MAX_CELLS 4096
 
 #define PE_HIST_E_BINS 512    /* log bins of photon energy over [0.511 MeV, 10 GeV]      */
 #define PE_HIST_T_BINS 180    /* bins of theta = atan2(k_y, k_x) over [-pi, pi)          */
@@ -133,6 +135,18 @@ typedef struct {
      * 256 at step 0 (first wait) and at candidate step + 1 (next wait, test
      * word), 0 at the candidate step only for a collision (photon energy).      */
     int brems_method;
+    /* PE_PIC_1D: the 1D electromagnetic PIC around the step (the paper's host
+     * with the field solver and current weighting on, Sec. 2.2, Sec. 3): the
+     * fields at the electrons come from a grid of n_cells cells over [0, L],
+     * dx = c dt, driven by the electrons' currents and by the laser (a0,
+     * polarisation, envelope as for PE_PLANE_1D) entering at x = 0.  Ions are
+     * immobile at the electrons' initial positions (neutral start).  Each
+     * macro-electron carries the areal density ne_over_nc x slab thickness / n.
+     * Electrons leaving [0, L] are removed.  In 1D the transverse fields move as
+     * F+- = E_y +- B_z and G+- = E_z -+ B_y along +-x: one cell per step along
+     * the characteristics with the current at the midpoint (exact in vacuum);
+     * E_x follows -J_x of the charge-conserving linear weighting.             */
+    int n_cells;
 } pe_run_params;
 
 /* Caller-owned device buffers of one run.
@@ -154,6 +168,12 @@ typedef struct {
  *                      NCS emissions | brems emissions << 16, high 32 bits =
  *                      sum over emissions of (step + 1) * (1, or 0x9E3779B1 for
  *                      brems) mod 2^32.  Used to compare event lists.
+ *   grid             : PE_PIC_1D only (NULL otherwise): PE_PIC_GRID_WORDS(n_cells)
+ *                      words, double (PE_F64) or float (PE_F32): E_x at the n half
+ *                      nodes, then F+, F-, G+, G- and the ion charge density at
+ *                      the n + 1 nodes (n = n_cells); set by pe_init_particles
+ *                      (zero fields, ion charge from the initial electrons) and
+ *                      advanced by pe_step.
  *   brems_wait       : n uint32, steps to each particle's next candidate
  *                      collision (PE_WAIT_NEVER: none); written by
  *                      pe_init_particles, required for PE_BREMS_NULL, ignored
@@ -167,6 +187,7 @@ typedef struct {
     void* tally;
     void* events;
     void* brems_wait;
+    void* grid;
 } pe_buffers;
 
 /* Launch shape of the persistent FP32 kernel (the autotuner's knobs).

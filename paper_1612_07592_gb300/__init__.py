@@ -21,7 +21,7 @@ LIB_PATH = os.environ.get("PE_LIB_PATH") or os.path.join(HERE, "libpe.so")
 
 PE_OK, PE_ERR_ARG, PE_ERR_CUDA, PE_ERR_NOMEM, PE_ERR_BUFFER_FULL, PE_ERR_TABLE_RANGE, PE_ERR_TIMEOUT, PE_ERR_STATE = range(8)
 PE_LP_Y, PE_CP = 0, 1
-PE_PLANE_1D, PE_GAUSS_2D, PE_CONST = 0, 1, 2
+PE_PLANE_1D, PE_GAUSS_2D, PE_CONST, PE_PIC_1D = 0, 1, 2, 3
 PE_F64, PE_F32 = 0, 1
 PE_REST, PE_MAXWELL_JUTTNER, PE_BEAM, PE_CALLER = 0, 1, 2, 3
 PE_BREMS_DIRECT, PE_BREMS_NULL = 0, 1
@@ -63,14 +63,14 @@ class RunParams(C.Structure):
                 ("T_mev", C.c_double), ("beam_gamma", C.c_double), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("enable_ncs", C.c_int), ("enable_brems", C.c_int),
                 ("box_enable", C.c_int), ("box_x_m", C.c_double * 2), ("reflect_r", C.c_double),
-                ("mirror_x_m", C.c_double), ("brems_method", C.c_int)]
+                ("mirror_x_m", C.c_double), ("brems_method", C.c_int), ("n_cells", C.c_int)]
 
 
 class Buffers(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
                 ("uz", C.c_void_p), ("tau", C.c_void_p), ("photons", C.c_void_p),
                 ("photon_capacity", C.c_int64), ("hist", C.c_void_p), ("tally", C.c_void_p),
-                ("events", C.c_void_p), ("brems_wait", C.c_void_p)]
+                ("events", C.c_void_p), ("brems_wait", C.c_void_p), ("grid", C.c_void_p)]
 
 
 class LaunchConfig(C.Structure):
@@ -158,6 +158,11 @@ def pe_tables_export(h: int, which: int, iz: int = 0) -> np.ndarray:
     out = np.empty(max(n.value, 1), dtype=np.float64)
     _check(lib().pe_tables_export(h, which, iz, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
     return out[:n.value]
+
+
+def pic_grid_words(n_cells: int) -> int:
+    """Words of the field grid of a PE_PIC_1D run (PE_PIC_GRID_WORDS)."""
+    return 6 * int(n_cells) + 5
 
 
 def run_params(**kw) -> RunParams:
@@ -257,6 +262,9 @@ class Run:
         self.events = torch.zeros(m, dtype=torch.int64, device=dev) if events else None
         # null-collision brems: steps to each particle's next candidate (uint32 words)
         self.wait = torch.zeros(m, dtype=torch.int32, device=dev) if params.brems_method == PE_BREMS_NULL else None
+        # 1D PIC: the field grid (E_x at half nodes; F+, F-, G+, G-, ion charge at nodes)
+        self.grid = (torch.zeros(pic_grid_words(params.n_cells), dtype=dt, device=dev)
+                     if params.geometry == PE_PIC_1D else None)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self.params = params
         self.handle = pe_init_particles(tables, params, self.n, self._buffers(), self.stream.cuda_stream)
@@ -266,7 +274,8 @@ class Run:
                        self.uz.data_ptr(), self.tau.data_ptr(), self.photons.data_ptr(), self.capacity,
                        self.hist.data_ptr(), self.tally.data_ptr(),
                        self.events.data_ptr() if self.events is not None else None,
-                       self.wait.data_ptr() if self.wait is not None else None)
+                       self.wait.data_ptr() if self.wait is not None else None,
+                       self.grid.data_ptr() if self.grid is not None else None)
 
     def rebind(self, tables: int, precision_params: RunParams | None = None):
         """Replace the run handle by a fresh one on the same buffers (caller-provided state,
@@ -281,7 +290,7 @@ class Run:
 
     def _state_tensors(self):
         ts = [self.x, self.y, self.ux, self.uy, self.uz, self.tau]
-        return ts + ([self.wait] if self.wait is not None else [])
+        return ts + [t for t in (self.wait, self.grid) if t is not None]
 
     def snapshot(self):
         return [t.clone() for t in self._state_tensors()]
@@ -312,6 +321,14 @@ class Run:
 
     def event_words(self) -> np.ndarray:
         return self.events[:self.n].cpu().numpy().view(np.uint64)
+
+    def pic_fields(self):
+        """1D PIC grid as float64 arrays (ex at half nodes; ey, ez, by, bz, ion charge at nodes)."""
+        g = self.grid.double().cpu().numpy()
+        n = self.params.n_cells
+        ex = g[:n]
+        fp, fm, gp, gm, rho = (g[n + k * (n + 1): n + (k + 1) * (n + 1)] for k in range(5))
+        return ex, 0.5 * (fp + fm), 0.5 * (gp + gm), 0.5 * (gm - gp), 0.5 * (fp - fm), rho
 
     def wait_words(self) -> np.ndarray:
         """Null-collision waits (uint32, PE_WAIT_NEVER = no further candidate)."""

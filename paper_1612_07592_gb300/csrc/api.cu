@@ -31,6 +31,10 @@ struct pe_run {
     const pe_tables* tables = nullptr;
     cudaStream_t stream = nullptr;
     int64_t steps_done = 0;
+    void* jacc = nullptr;     // 1D PIC: the library's current sums of one step
+    ~pe_run() {
+        if (jacc) cudaFree(jacc);
+    }
 };
 
 namespace {
@@ -246,7 +250,15 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     *out = nullptr;
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_init_particles: n must be in [0, 2^31)");
     if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_init_particles: precision");
-    if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_CONST) return fail(PE_ERR_ARG, "pe_init_particles: geometry");
+    if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_PIC_1D) return fail(PE_ERR_ARG, "pe_init_particles: geometry");
+    if (rp->geometry == PE_PIC_1D) {
+        if (rp->n_cells < 4 || rp->n_cells > PE_PIC_MAX_CELLS)
+            return fail(PE_ERR_ARG, "pe_init_particles: n_cells must be in [4, PE_PIC_MAX_CELLS]");
+        if (n > 0 && (!b->grid || !aligned16(b->grid))) return fail(PE_ERR_ARG, "pe_init_particles: PIC grid buffer");
+        const double L_m = rp->n_cells * rp->dt_over_T * rp->lambda_m;       // n_cells dx, dx = c dt
+        if (!(rp->slab_x0_m > 0 && rp->slab_x0_m + rp->slab_thick_m < L_m))
+            return fail(PE_ERR_ARG, "pe_init_particles: the slab must lie inside the PIC grid (0, n_cells c dt)");
+    }
     if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP) return fail(PE_ERR_ARG, "pe_init_particles: polarisation");
     if (rp->init_dist < PE_REST || rp->init_dist > PE_CALLER) return fail(PE_ERR_ARG, "pe_init_particles: init_dist");
     if (!(rp->lambda_m > 0 && rp->dt_over_T > 0 && rp->charge_state > 0 && rp->ne_over_nc >= 0 &&
@@ -335,6 +347,17 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     d.enable_ncs = rp->enable_ncs;
     d.enable_brems = rp->enable_brems;
     d.box_enable = rp->box_enable;
+    if (rp->geometry == PE_PIC_1D) {
+        // electrons leaving the grid are removed; each carries the areal density n_e d / n
+        d.box_enable = 1;
+        c.box0 = 0.0;
+        c.box1 = rp->n_cells * c.dt;
+        const double w = n > 0 ? rp->ne_over_nc * rp->slab_thick_m * kl / (double)n : 0.0;
+        c.pic_kx = w / c.dt / 68719476736.0;
+        c.pic_kyz = -w / c.dt / 68719476736.0;
+        d.grid = b->grid;
+        d.n_cells = rp->n_cells;
+    }
     d.iz = iz;
     d.run_id = rp->run_id;
     d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
@@ -356,6 +379,28 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
         if (e != cudaSuccess) {
             delete r;
             return cuda_fail(e, "pe_init_particles: k_init");
+        }
+    }
+    if (rp->geometry == PE_PIC_1D && n > 0) {
+        // zero fields, the ion charge of the neutral start, cleared current sums
+        const size_t rs = rp->precision == PE_F32 ? 4 : 8;
+        e = cudaMalloc(&r->jacc, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells);
+        if (e != cudaSuccess) {
+            r->jacc = nullptr;
+            delete r;
+            return fail(PE_ERR_NOMEM, std::string("pe_init_particles: PIC current sums: ") + cudaGetErrorString(e));
+        }
+        d.jacc = static_cast<unsigned long long*>(r->jacc);
+        e = cudaMemsetAsync(r->jacc, 0, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells, r->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->grid, 0, rs * (size_t)PE_PIC_GRID_WORDS(rp->n_cells), r->stream);
+        if (e == cudaSuccess) {
+            launch_pic_rho(d, rp->precision, r->stream);
+            g_launches += 2;
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            delete r;
+            return cuda_fail(e, "pe_init_particles: PIC grid");
         }
     }
     *out = r;
@@ -460,6 +505,9 @@ static pe_status check_batch(pe_run* const* runs, int n_runs, int64_t n_steps) {
     for (int k = 0; k < n_runs; ++k)
         if (runs[k]->steps_done + n_steps >= (int64_t(1) << 32))
             return fail(PE_ERR_ARG, "pe_step: step index would exceed 2^32");
+    if (n_runs > 1)
+        for (int k = 0; k < n_runs; ++k)
+            if (runs[k]->dev.fk == FK_PIC) return fail(PE_ERR_STATE, "pe_step: a PE_PIC_1D run steps alone");
     return PE_OK;
 }
 
@@ -471,6 +519,25 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
     if (n_steps == 0) return PE_OK;
     cudaStream_t s = runs[0]->stream;
 
+    if (runs[0]->dev.fk == FK_PIC) {
+        // the grid changes every step: a particle launch and a field launch per step
+        pe_run* r = runs[0];
+        int dev, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        RunDev d = r->dev;
+        if (d.n > 0) {
+            for (int64_t k = 0; k < n_steps; ++k) {
+                d.step0 = r->steps_done + k;
+                launch_pic_step(t->dev, d, prec, sms, s);
+                g_launches += 2;
+            }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "pe_step: PIC step");
+        r->steps_done += n_steps;
+        return PE_OK;
+    }
     if (n_runs == 1 && prec == PE_F64 && !(cfg && cfg->steps_per_launch > 0)) {
         pe_run* r = runs[0];
         RunDev d = r->dev;
@@ -566,6 +633,8 @@ extern "C" pe_status pe_graph_create(pe_run* const* runs, int n_runs, int64_t st
     pe_status st = check_batch(runs, n_runs, steps_per_replay);
     if (st != PE_OK) return st;
     if (steps_per_replay < 1) return fail(PE_ERR_ARG, "pe_graph_create: steps_per_replay must be >= 1");
+    for (int k = 0; k < n_runs; ++k)
+        if (runs[k]->dev.fk == FK_PIC) return fail(PE_ERR_STATE, "pe_graph_create: PE_PIC_1D runs step through pe_step");
     pe_graph* g = new pe_graph();
     g->runs.assign(runs, runs + n_runs);
     g->steps = steps_per_replay;

@@ -76,6 +76,7 @@ struct StepC {
     R refl_r;                 // reflected wave amplitude coefficient
     R xm2_hi, xm2_lo;         // 2 x_m (mirror plane) as hi + lo: in float an exact pair
     R P_hat;                  // null collisions: candidate probability 1 - exp(-x_hat) per step
+    R pic_kx, pic_kyz;        // 1D PIC: J_x = pic_kx * sum, J_y,z = pic_kyz * sum (fixed-point sums)
 };
 
 // Device view of one run.  Optical depth: double for PE_F64, a float pair
@@ -101,6 +102,9 @@ struct RunDevT {
     int brems_method;             // PE_BREMS_DIRECT | PE_BREMS_NULL
     uint32_t* wait;               // null collisions: steps to the next candidate
     double x_hat;                 // null collisions: majorant optical depth per step (both precisions)
+    void* grid;                   // 1D PIC: field grid (the run's precision, layout in pe.h)
+    unsigned long long* jacc;     // 1D PIC: current sums of one step (3 n_cells, 2^-36 fixed point)
+    int n_cells;                  // 1D PIC: cells of the grid (0 otherwise)
 };
 using RunDev = RunDevT<double>;
 
@@ -125,8 +129,13 @@ inline RunDevT<float> to_float(const RunDevT<double>& d) {
     f.enable_ncs = d.enable_ncs; f.enable_brems = d.enable_brems; f.box_enable = d.box_enable;
     f.iz = d.iz; f.run_id = d.run_id; f.seed_lo = d.seed_lo; f.seed_hi = d.seed_hi;
     f.fk = d.fk; f.brems_method = d.brems_method; f.wait = d.wait; f.x_hat = d.x_hat;
+    f.grid = d.grid; f.jacc = d.jacc; f.n_cells = d.n_cells;
     return f;
 }
+
+// 1D PIC (kernels_pic.cu)
+void launch_pic_rho(const RunDev& r, int precision, cudaStream_t s);
+void launch_pic_step(const TablesDev& t, const RunDev& r, int precision, int sms, cudaStream_t s);
 
 // host-side table build (tables.cpp)
 struct HostTables {

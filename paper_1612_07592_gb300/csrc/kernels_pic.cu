@@ -1,0 +1,230 @@
+// kernels_pic.cu -- the 1D electromagnetic PIC around the emission step.
+//
+//  k_pic_particles  one thread per electron: fields gathered from the grid at
+//                   x^n (linear weights), the emission step of Sec. 2.2 (push,
+//                   NCS, brems, position), then the electron's current J^{n+1/2}
+//                   by charge-conserving linear weighting, summed per CTA in
+//                   shared memory and once per CTA into the run's accumulator.
+//  k_pic_fields     one CTA: E_x -= dt J_x at the half nodes; the wave variants
+//                   F+- = E_y +- B_z and G+- = E_z -+ B_y carried one cell along
+//                   +-x with the current at the path's midpoint; the laser enters
+//                   at x = 0; the accumulator is cleared for the next step.
+//  k_pic_rho        ion charge of the neutral start (the electrons' initial
+//                   charge with the opposite sign), a diagnostic of Gauss's law.
+//
+// Currents are summed as dimensionless 2^-36 fixed-point integers, one rounding
+// per contribution: exact and independent of the order of the atomic adds.
+#include "kernels.cuh"
+
+namespace pe {
+
+namespace {
+
+__device__ __forceinline__ long long fxq(double v) { return __double2ll_rn(v * 68719476736.0); }
+__device__ __forceinline__ long long fxq(float v) { return __float2ll_rn(v * 68719476736.0f); }
+
+// weight of grid point k (node, or half node with off = 1/2) for a particle at s = x/dx
+template <typename R>
+__device__ __forceinline__ R lin_w(R s, int k, R off) {
+    R d = fabs(s - ((R)k + off));
+    return d < (R)1 ? (R)1 - d : (R)0;
+}
+
+__device__ __forceinline__ void acc_add(unsigned long long* a, long long v) {
+    if (v) atomicAdd(a, (unsigned long long)v);
+}
+
+// current of one electron moving from x_old to x_new (|x_new - x_old| < dx) with
+// velocity (vy, vz): J_x at half nodes from the change of its node weights
+// (cumulative, charge conserving); J_y, J_z at half nodes with the mean of its
+// half-node weights at the two positions.  Dimensionless sums; the field kernel
+// applies the weight and the charge sign.
+template <typename R>
+__device__ __forceinline__ void pic_deposit(R dx, int n, R x_old, R x_new, R vy, R vz, unsigned long long* sj) {
+    const R so = x_old / dx, sn = x_new / dx;
+    const int ia = (int)floor(so < sn ? so : sn);
+    R cum = 0;
+#pragma unroll
+    for (int k = ia; k <= ia + 1; ++k) {
+        cum += lin_w<R>(sn, k, (R)0) - lin_w<R>(so, k, (R)0);
+        if (k >= 0 && k < n) acc_add(sj + k, fxq(cum));
+    }
+#pragma unroll
+    for (int k = ia - 1; k <= ia + 1; ++k) {
+        const R sbar = (R)0.5 * (lin_w<R>(so, k, (R)0.5) + lin_w<R>(sn, k, (R)0.5));
+        if (sbar > (R)0 && k >= 0 && k < n) {
+            acc_add(sj + n + k, fxq(vy * sbar));
+            acc_add(sj + 2 * n + k, fxq(vz * sbar));
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pic_particles(TablesDev t, RunDevT<R> r) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
+    unsigned long long* s_j = s_tally + PE_TALLY_WORDS;             // 3 n_cells current sums
+    R* s_h = reinterpret_cast<R*>(s_j + 3 * r.n_cells);
+    R* s_sig = s_h + t.n_eta;
+    const R* g_h = (sizeof(R) == 4) ? (const R*)t.h32 : (const R*)t.h64;
+    const R* g_sig = (sizeof(R) == 4) ? (const R*)t.sig32 : (const R*)t.sig64;
+    const int nj = 3 * r.n_cells;
+    for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS + nj; k += blockDim.x) s_hist[k] = 0;
+    for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = g_h[k];
+    for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = g_sig[k];
+    __syncthreads();
+
+    const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
+    const uint32_t step = (uint32_t)r.step0;
+    const R nf = (R)step;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < r.n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        bool active = i < r.n;
+        Particle<R> P;
+        StepOut<R> out;
+        out.ncs = out.br = false;
+        if (active) {
+            load_particle<R>(r, i, P);
+            active = !isnan(P.x);
+        }
+        if (active) {
+            const R x_old = P.x + P.x_lo;
+            step_one<R, FK_PIC>(t, r, s_h, sig_z, (uint32_t)i, step, nf, P, out, s_hist, s_tally);
+            if (!isnan(P.x)) {
+                const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+                pic_deposit<R>(r.c.dt, r.n_cells, x_old, P.x + P.x_lo, P.u[1] / gamma, P.u[2] / gamma, s_j);
+            }
+            store_particle<R>(r, i, P);
+        }
+        if (__any_sync(0xffffffffu, out.ncs || out.br)) {
+            warp_append(r, out.ncs, out.pn);
+            warp_append(r, out.br, out.pb);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nj; k += blockDim.x) {
+        const unsigned long long v = s_j[k];
+        if (v) atomicAdd(r.jacc + k, v);
+    }
+    flush_shared<R>(s_hist, s_tally, r);
+}
+
+constexpr int kFieldThreads = 1024;
+constexpr int kNodesPerThread = (PE_PIC_MAX_CELLS + 1 + kFieldThreads - 1) / kFieldThreads;
+
+template <typename R, bool kCP>
+__global__ void __launch_bounds__(kFieldThreads) k_pic_fields(RunDevT<R> r) {
+    const int n = r.n_cells;
+    const StepC<R>& c = r.c;
+    R* ex = static_cast<R*>(r.grid);
+    R* fp = ex + n;
+    R* fm = fp + n + 1;
+    R* gp = fm + n + 1;
+    R* gm = gp + n + 1;
+    unsigned long long* jx = r.jacc;
+    unsigned long long* jy = jx + n;
+    unsigned long long* jz = jy + n;
+    const R dt = c.dt;
+    // J_x = (w/dt) sum (the electron charge -1 included), J_y,z = -(w/dx) sum
+    const R kx = c.pic_kx, kyz = c.pic_kyz;
+    // read the carried values and the midpoint currents of this thread's nodes
+    R nfp[kNodesPerThread], nfm[kNodesPerThread], ngp[kNodesPerThread], ngm[kNodesPerThread];
+#pragma unroll
+    for (int q = 0; q < kNodesPerThread; ++q) {
+        const int i = threadIdx.x + q * kFieldThreads;
+        nfp[q] = nfm[q] = ngp[q] = ngm[q] = 0;
+        if (i > 0 && i <= n) {                       // along +x from node i - 1 through half node i - 1
+            nfp[q] = fp[i - 1] - dt * kyz * (R)(long long)jy[i - 1];
+            ngp[q] = gp[i - 1] - dt * kyz * (R)(long long)jz[i - 1];
+        }
+        if (i < n) {                                 // along -x from node i + 1 through half node i
+            nfm[q] = fm[i + 1] - dt * kyz * (R)(long long)jy[i];
+            ngm[q] = gm[i + 1] - dt * kyz * (R)(long long)jz[i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNodesPerThread; ++q) {
+        const int i = threadIdx.x + q * kFieldThreads;
+        if (i < n) {
+            ex[i] -= dt * kx * (R)(long long)jx[i];
+            jx[i] = jy[i] = jz[i] = 0;
+        }
+        if (i <= n) {
+            fp[i] = nfp[q];
+            fm[i] = nfm[q];
+            gp[i] = ngp[q];
+            gm[i] = ngm[q];
+        }
+    }
+    if (threadIdx.x == 0) {
+        // the laser enters at x = 0: F+ = 2 g_y, G+ = 2 g_z at t^{n+1}
+        R gy, gz;
+        const R nf1 = (R)(r.step0 + 1);
+        plane_e<R, kCP>(c, phase(c, nf1, (R)0, (R)0), gy, gz);
+        fp[0] = (R)2 * gy;
+        gp[0] = (R)2 * gz;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pic_rho_deposit(RunDevT<R> r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    Particle<R> P;
+    load_pos(r, i, P);
+    const R x = P.x + P.x_lo;
+    if (isnan(x)) return;
+    const R s = x / r.c.dt;
+    const int i0 = (int)floor(s);
+    for (int k = i0; k <= i0 + 1; ++k)
+        if (k >= 0 && k <= r.n_cells) acc_add(r.jacc + k, fxq(lin_w<R>(s, k, (R)0)));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads) k_pic_rho_store(RunDevT<R> r) {
+    const int n = r.n_cells;
+    R* rho = static_cast<R*>(r.grid) + n + 4 * (n + 1);
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+        rho[i] = -r.c.pic_kyz * (R)(long long)r.jacc[i];   // + (w/dx) sum of node weights
+        r.jacc[i] = 0;
+    }
+}
+
+}  // namespace
+
+static int pic_smem_bytes(const TablesDev& t, int n_cells, int precision) {
+    const size_t rs = precision == PE_F32 ? 4 : 8;
+    return (int)(8 * (PE_HIST_WORDS + PE_TALLY_WORDS + 3 * (size_t)n_cells) + rs * (t.n_eta + (size_t)t.n_Z * t.n_E));
+}
+
+template <typename R>
+static void pic_step(const TablesDev& t, const RunDevT<R>& r, int sms, cudaStream_t s) {
+    const int smem = pic_smem_bytes(t, r.n_cells, sizeof(R) == 4 ? PE_F32 : PE_F64);
+    cudaFuncSetAttribute(k_pic_particles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int64_t blocks = (r.n + 255) / 256;
+    const int grid = (int)(blocks < 2 * (int64_t)sms ? (blocks > 0 ? blocks : 1) : 2 * (int64_t)sms);
+    k_pic_particles<R><<<grid, 256, smem, s>>>(t, r);
+    if (r.polarisation == PE_CP) k_pic_fields<R, true><<<1, kFieldThreads, 0, s>>>(r);
+    else k_pic_fields<R, false><<<1, kFieldThreads, 0, s>>>(r);
+}
+
+void launch_pic_step(const TablesDev& t, const RunDev& r, int precision, int sms, cudaStream_t s) {
+    if (precision == PE_F32) pic_step<float>(t, to_float(r), sms, s);
+    else pic_step<double>(t, r, sms, s);
+}
+
+void launch_pic_rho(const RunDev& r, int precision, cudaStream_t s) {
+    const int grid = (int)((r.n + 255) / 256);
+    if (precision == PE_F32) {
+        const RunDevT<float> f = to_float(r);
+        if (grid > 0) k_pic_rho_deposit<float><<<grid, 256, 0, s>>>(f);
+        k_pic_rho_store<float><<<1, kFieldThreads, 0, s>>>(f);
+    } else {
+        if (grid > 0) k_pic_rho_deposit<double><<<grid, 256, 0, s>>>(r);
+        k_pic_rho_store<double><<<1, kFieldThreads, 0, s>>>(r);
+    }
+}
+
+}  // namespace pe

@@ -198,10 +198,11 @@ __device__ __forceinline__ float phase_refl(const StepC<float>& c, float nf, flo
 // Field kind of a run, a compile-time parameter of the step so that each geometry
 // and polarisation gets its own straight-line code.
 enum { FK_PLANE_LP = 0, FK_PLANE_CP = 1, FK_GAUSS_LP = 2, FK_GAUSS_CP = 3, FK_CONST = 4, FK_REFL_LP = 5,
-       FK_REFL_CP = 6 };
-constexpr int kFieldKinds = 7;
+       FK_REFL_CP = 6, FK_PIC = 7 };
+constexpr int kFieldKinds = 7;        // kinds of the prescribed-field kernels (FK_PIC has its own path)
 __host__ __device__ __forceinline__ int field_kind(int geometry, int polarisation, bool reflected) {
     if (geometry == PE_CONST) return FK_CONST;
+    if (geometry == PE_PIC_1D) return FK_PIC;
     int cp = polarisation == PE_CP ? 1 : 0;
     if (geometry == PE_PLANE_1D && reflected) return FK_REFL_LP + cp;
     return (geometry == PE_GAUSS_2D ? 2 : 0) + cp;
@@ -234,11 +235,55 @@ __device__ __forceinline__ void plane_e(const StepC<R>& c, R p, R& ey, R& ez) {
     ez = kCP ? c.a0 * (dg * ct - g * st) : (R)0;
 }
 
+// 1D PIC: fields at x from the grid, linear weights of the nodes (transverse fields
+// from the wave variants F+- = E_y +- B_z, G+- = E_z -+ B_y) and of the half nodes (E_x);
+// zero beyond the grid
+template <typename R>
+__device__ __forceinline__ void pic_gather(const RunDevT<R>& r, R x, R E[3], R B[3]) {
+    const int n = r.n_cells;
+    const R* ex = static_cast<const R*>(r.grid);
+    const R* fp = ex + n;
+    const R* fm = fp + n + 1;
+    const R* gp = fm + n + 1;
+    const R* gm = gp + n + 1;
+    const R s = x / r.c.dt;                          // dx = c dt
+    const R fl = floor(s);
+    const int i = (int)fl;
+    const R f = s - fl;
+    R v[4][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int m = i + k;
+        const bool in = m >= 0 && m <= n;
+        v[0][k] = in ? fp[m] : (R)0;
+        v[1][k] = in ? fm[m] : (R)0;
+        v[2][k] = in ? gp[m] : (R)0;
+        v[3][k] = in ? gm[m] : (R)0;
+    }
+    const R Fp = ((R)1 - f) * v[0][0] + f * v[0][1], Fm = ((R)1 - f) * v[1][0] + f * v[1][1];
+    const R Gp = ((R)1 - f) * v[2][0] + f * v[2][1], Gm = ((R)1 - f) * v[3][0] + f * v[3][1];
+    E[1] = (R)0.5 * (Fp + Fm);
+    B[2] = (R)0.5 * (Fp - Fm);
+    E[2] = (R)0.5 * (Gp + Gm);
+    B[1] = (R)0.5 * (Gm - Gp);
+    B[0] = 0;
+    const R sh = s - (R)0.5;
+    const R flh = floor(sh);
+    const int j = (int)flh;
+    const R fh = sh - flh;
+    const R h0 = (j >= 0 && j < n) ? ex[j] : (R)0, h1 = (j + 1 >= 0 && j + 1 < n) ? ex[j + 1] : (R)0;
+    E[0] = ((R)1 - fh) * h0 + fh * h1;
+}
+
 template <typename R, int G>
 __device__ __forceinline__ void fields(const RunDevT<R>& r, R x, R x_lo, R y, R nf, R E[3], R B[3]) {
     const StepC<R>& c = r.c;
     E[0] = E[1] = E[2] = 0;
     B[0] = B[1] = B[2] = 0;
+    if (G == FK_PIC) {
+        pic_gather<R>(r, x + x_lo, E, B);
+        return;
+    }
     if (G == FK_CONST) {
         for (int k = 0; k < 3; ++k) { E[k] = c.E_const[k]; B[k] = c.B_const[k]; }
         return;

@@ -1,0 +1,144 @@
+"""GPU parity of the 1D electromagnetic PIC around the emission step (PE_PIC_1D)
+with the oracle's PIC, and the field-solver properties on the device."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1612_07592_gb300 as pe
+from paper_1612_07592_gb300 import workloads as W
+from test_gpu_parity import F64_RTOL, _tp, tables
+
+pytestmark = pytest.mark.gpu
+Z = (13.0, 79.0)
+NC = 800
+
+
+def _run(**kw):
+    """1D Au 51+ slab (2-3 um, 50 n_c) in a grid of NC cells, a0 = 270 pulse, MJ 1 MeV electrons."""
+    d = dict(W.AU, ne_over_nc=50.0, a0=270.0, geometry=pe.PE_PIC_1D, n_cells=NC, init_dist=1, T_mev=1.0, seed=5)
+    d.update(kw)
+    return W.base_run(**d)
+
+
+def _oracle(ot, run, n, steps):
+    d = dict(run)
+    nc = d.pop("n_cells")
+    d.pop("precision", None)
+    d["iz"] = list(Z).index(d["Z"])
+    r = O.run_params(**d)
+    ids = np.arange(n)
+    st = O.init(ot, r, ids)
+    w = O.pic_weight(r, n)
+    grid = O.pic_init(r, nc, w, st)
+    ev = np.zeros(n, dtype=np.uint64)
+    ph, nph, hist, tally = O.pic_run(ot, r, nc, w, ids, st, grid, 0, steps, capacity=1 << 20, events=ev)
+    return st, grid, ev, ph, nph, hist, tally
+
+
+def _gpu(lt, run, n, steps, precision):
+    r = pe.Run(lt, pe.run_params(precision=precision, **run), n, capacity=1 << 20, events=True)
+    pe.pe_step([r.handle], steps)
+    return r, r.tally_out()
+
+
+def test_pic_f64_parity():
+    """FP64 device PIC against the oracle's PIC: identical event lists, state and grid to 1e-9 of
+    their scales, the same tallies, on a 1D Au slab (50 n_c) hit by the a0 = 270 pulse (the
+    interaction starts near step 200; within this horizon the two runs have not parted)."""
+    run = _run()
+    n, steps = 2000, 400
+    lt, ot = tables(_tp(48), Z)
+    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, steps)
+    r, out = _gpu(lt, run, n, steps, pe.PE_F64)
+    st, ev = r.state(), r.event_words()
+    assert tal_o[O.T["N_NCS_STORED"]] + tal_o[O.T["N_NCS_BELOW"]] > 1000
+    assert np.array_equal(ev, ev_o), f"{np.sum(ev != ev_o)} particles with different event lists"
+    np.testing.assert_allclose(st[:, [0, 5]], st_o[:, [0, 5]], rtol=F64_RTOL, atol=1e-9)
+    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), 1.0)
+    assert (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u).max() < F64_RTOL
+    fo, fg = O.pic_fields(grid_o, NC), r.pic_fields()
+    for a, b in zip(fg[:5], fo[:5]):
+        assert np.abs(a - b).max() <= F64_RTOL * max(np.abs(b).max(), 1.0)
+    np.testing.assert_allclose(fg[5], fo[5], rtol=1e-9, atol=1e-9 * np.abs(fo[5]).max())
+    for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED", "N_PHOTONS", "N_KILLED"):
+        assert int(out.tally[pe.T[k]]) == int(tal_o[O.T[k]]), k
+    r.close()
+
+
+def test_pic_f32_statistics():
+    """FP32 device PIC over the whole interaction (1000 steps): field energy, kinetic energy and
+    photon yields agree with the FP64 oracle within the statistics of the run."""
+    run = _run()
+    n, steps = 4000, 1000
+    lt, ot = tables(_tp(48), Z)
+    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, steps)
+    r, out = _gpu(lt, run, n, steps, pe.PE_F32)
+    st = r.state()
+    fo, fg = O.pic_fields(grid_o, NC), r.pic_fields()
+    dx = 0.01 * 2 * math.pi
+    energy = lambda f: 0.5 * sum((a ** 2).sum() for a in f[:5]) * dx
+    kin = lambda s: np.nansum(np.sqrt(1 + (s[:, 2:5] ** 2).sum(1)) - 1)
+    print("field energy", energy(fg), energy(fo), "kinetic", kin(st), kin(st_o))
+    assert abs(energy(fg) / energy(fo) - 1) < 0.03
+    assert abs(kin(st) / kin(st_o) - 1) < 0.05
+    for k in ("N_NCS_STORED", "N_NCS_BELOW"):
+        a, b = int(out.tally[pe.T[k]]), int(tal_o[O.T[k]])
+        print(k, a, b)
+        assert abs(a / b - 1) < 0.05, (k, a, b)
+    r.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(pe.PE_F64, 1e-11), (pe.PE_F32, 1e-4)])
+def test_pic_vacuum_injection_on_device(prec, tol):
+    """No plasma (an electron-free slab of negligible density): the device grid carries the incident
+    wave exactly (FP64 to rounding, FP32 to its rounding of the phase)."""
+    lt, ot = tables(_tp(33), Z)
+    run = _run(a0=3.0, polarisation=1, ne_over_nc=1e-12, n_cells=2000, flat_s=10e-15, ramp_periods=2.0,
+               Z=13.0, charge_state=11.0)
+    r, out = _gpu(lt, run, 8, 1500, prec)
+    ex, ey, ez, by, bz, rho = r.pic_fields()
+    rp = O.run_params(**{k: v for k, v in run.items() if k not in ("n_cells",)})
+    dt = 0.01 * 2 * math.pi
+    x = np.arange(2001) * dt
+    F = np.array([np.concatenate(O.fields(rp, xi, 0.0, 1500 * dt)) for xi in x])
+    for got, want in ((ey, F[:, 1]), (ez, F[:, 2]), (by, F[:, 4]), (bz, F[:, 5])):
+        assert np.abs(got - want).max() < tol * 3.0, np.abs(got - want).max()
+    r.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(pe.PE_F64, 1e-9), (pe.PE_F32, 1e-4)])
+def test_pic_gauss_law_on_device(prec, tol):
+    """The device's charge-conserving currents keep div E_x = rho_ion + rho_e."""
+    lt, ot = tables(_tp(33), Z)
+    run = _run(a0=20.0, n_cells=600)
+    n = 3000
+    r, out = _gpu(lt, run, n, 500, prec)
+    ex, ey, ez, by, bz, rho = r.pic_fields()
+    st = r.state()
+    dx = 0.01 * 2 * math.pi
+    w = 50.0 * 1e-6 * (2 * math.pi / 1e-6) / n
+    live = ~np.isnan(st[:, 0])
+    s = st[live, 0] / dx
+    i = np.floor(s).astype(int)
+    f = s - i
+    rho_e = np.zeros(601)
+    np.add.at(rho_e, i, -w * (1 - f) / dx)
+    np.add.at(rho_e, i + 1, -w * f / dx)
+    res = (ex[1:] - ex[:-1]) / dx - (rho[1:-1] + rho_e[1:-1])
+    assert np.abs(ex).max() > 1.0
+    assert np.abs(res).max() < tol * np.abs(rho_e).max(), np.abs(res).max() / np.abs(rho_e).max()
+    r.close()
+
+
+def test_pic_runs_step_alone():
+    lt, ot = tables(_tp(33), Z)
+    a = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=300)), 100)
+    b = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=300)), 100)
+    with pytest.raises(pe.PeError):
+        pe.pe_step([a.handle, b.handle], 5)
+    with pytest.raises(pe.PeError):
+        pe.pe_graph_create([a.handle], 5)
+    with pytest.raises(pe.PeError):                  # slab outside the grid
+        pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=100)), 10)
