@@ -163,7 +163,8 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
 int or_pic_init(const or_run_params* r, int n_cells, double weight, const double* state, int64_t n, double* grid);
 /* Advance particles and grid together (step-major); arguments as or_run.  The
  * particle list must be the whole run (the currents of all electrons drive the
- * fields).  Electrons leaving [0, L] are removed.                            */
+ * fields).  Electrons leaving [0, L] are removed after depositing their last
+ * move (their charge leaves through the boundary).                           */
 int or_pic_run(const or_tables* t, const or_run_params* r, int n_cells, double weight, const int64_t* ids,
                int64_t n_ids, int64_t step0, int64_t n_steps, double* state, uint32_t* wait, double* grid,
                or_photon* photons, int64_t cap, int64_t* n_photons, uint64_t* hist, uint64_t* tally,

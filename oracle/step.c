@@ -569,6 +569,9 @@ int or_run(const or_tables* t, const or_run_params* r, const int64_t* ids, int64
 /* laser enters at x = 0 (F+_0 = 2 g_y, G+_0 = 2 g_z, g the incident field);   */
 /* nothing enters at x = L (F-_N = G-_N = 0); outgoing waves leave freely.    */
 /* One step: particles in E^n, B^n (gathered by linear weights) -> x^{n+1};   */
+/* an electron that leaves [0, L] deposits its last move, so Gauss's law      */
+/* holds on the grid with its charge gone through the boundary, and is then  */
+/* removed;                                                                  */
 /* currents J^{n+1/2} by linear weighting; fields to n + 1.  Currents are     */
 /* summed in 2^-36 fixed point per contribution (exact and order-free, the    */
 /* same rule the device code uses).                                          */
@@ -661,9 +664,8 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
     const double kl = 2.0 * M_PI / rr.lambda_m;
     const double dt = rr.dt_over_T * 2.0 * M_PI, dx = dt;
     const int64_t n = n_cells;
-    rr.box_enable = 1;                                   /* electrons leaving the grid are removed */
-    rr.box_x_m[0] = 0.0;
-    rr.box_x_m[1] = (double)n * dx / kl;
+    rr.box_enable = 0;              /* electrons leaving the grid are removed below, after their current */
+    const double L = (double)n * dx;
     const or_run_params* r = &rr;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
@@ -697,10 +699,14 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
             particle_step(t, r, &c, ids[k], s_, &x, &y, u, &tau, wait ? wait + k : NULL, E, B, &lists[k],
                           th_hist + (size_t)me * OR_HIST_WORDS, th_tally + (size_t)me * ORT_WORDS,
                           events ? events + k : NULL);
-            if (!isnan(x)) {
-                double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                int64_t* a = acc + (size_t)me * 3 * n;
-                pic_deposit(dx, n_cells, x_old, x, u, gamma, a, a + n, a + 2 * n);
+            double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            int64_t* a = acc + (size_t)me * 3 * n;
+            pic_deposit(dx, n_cells, x_old, x, u, gamma, a, a + n, a + 2 * n);
+            if (x < 0.0 || x > L) {     /* it left through a boundary face, carrying its charge out */
+                x = NAN;
+                uint64_t* tl = th_tally + (size_t)me * ORT_WORDS;
+                tl[ORT_N_KILLED]++;
+                tl[ORT_KILLED_STEPS] += (uint64_t)(s_ + 1);
             }
             s[0] = x; s[1] = y; s[2] = u[0]; s[3] = u[1]; s[4] = u[2]; s[5] = tau;
         }

@@ -348,8 +348,9 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     d.enable_brems = rp->enable_brems;
     d.box_enable = rp->box_enable;
     if (rp->geometry == PE_PIC_1D) {
-        // electrons leaving the grid are removed; each carries the areal density n_e d / n
-        d.box_enable = 1;
+        // electrons leaving the grid are removed by the PIC kernel after depositing their
+        // last move; each carries the areal density n_e d / n
+        d.box_enable = 0;
         c.box0 = 0.0;
         c.box1 = rp->n_cells * c.dt;
         const double w = n > 0 ? rp->ne_over_nc * rp->slab_thick_m * kl / (double)n : 0.0;

