@@ -275,6 +275,35 @@ pe_status pe_destroy(pe_run* run);
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */
 double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);
 
+/* PIC steps that allocate nothing.  The paper has no counterpart: this is an
+ * interface choice of this library.  pe_init_particles allocates, for a
+ * PE_PIC_1D run, the device memory in which each step sums the electrons'
+ * currents.  Some callers cannot call cudaMalloc at all: programs whose device
+ * memory is handed out by a host framework or a fixed pool they must not
+ * bypass, or that run under a memory budget that forbids new allocations
+ * once the simulation is set up.  This entry point advances such a caller's
+ * PIC state by n_steps steps from step index step0 with the same kernels and
+ * results as pe_step on a run made by pe_init_particles with the same
+ * parameters and buffers, but it sums the currents in a fixed array compiled
+ * into the library (3 x PE_PIC_MAX_CELLS x 8 bytes = 96 KiB, held on every GPU
+ * that loads the library until the process exits).  It calls no cudaMalloc or
+ * cudaFree and no routine that allocates.
+ *   tables, params, n and buffers describe the run as for pe_init_particles
+ *   (params->geometry = PE_PIC_1D); the caller owns every buffer, which must
+ *   hold a PIC state (for instance one set up by pe_init_particles, or a grid
+ *   cleared to zero with the caller's own electrons).  hist and tally
+ *   accumulate as in pe_step.  Asynchronous on cuda_stream.
+ *   The first call on a device looks up the array's device address with that
+ *   device current (cudaGetSymbolAddress) and keeps it; make that first call
+ *   before any stream capture.  Every call shares the one array and clears it
+ *   before use, so calls whose work overlaps on the GPU (other streams, other
+ *   host threads) race and give wrong currents: serialise them.
+ * Errors: PE_ERR_ARG (null, wrong geometry, n_cells outside [4,
+ * PE_PIC_MAX_CELLS] -- the array's limit --, bad sizes or alignment, Z not in
+ * the tables), PE_ERR_CUDA.                                                    */
+pe_status pe_pic_step_noalloc(const pe_tables* tables, const pe_run_params* params, int64_t n,
+                              const pe_buffers* buffers, int64_t step0, int64_t n_steps, void* cuda_stream);
+
 /* Number of kernel launches the library has issued (all runs, this process). */
 int64_t pe_launch_count(void);
 

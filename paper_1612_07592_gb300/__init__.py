@@ -26,6 +26,7 @@ PE_F64, PE_F32 = 0, 1
 PE_REST, PE_MAXWELL_JUTTNER, PE_BEAM, PE_CALLER = 0, 1, 2, 3
 PE_BREMS_DIRECT, PE_BREMS_NULL = 0, 1
 PE_WAIT_NEVER = 0xFFFFFFFF
+PE_PIC_MAX_CELLS = 4096
 HIST_E_BINS, HIST_T_BINS = 512, 180
 HIST_WORDS = 2 * HIST_E_BINS + 2 * HIST_T_BINS
 TALLY_WORDS = 32
@@ -112,13 +113,15 @@ def lib():
             L.pe_graph_launch.argtypes = [vp]
             L.pe_graph_destroy.argtypes = [vp]
             L.pe_destroy.argtypes = [vp]
+            L.pe_pic_step_noalloc.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), C.c_int64,
+                                              C.c_int64, vp]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
             L.pe_last_error.restype = C.c_char_p
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
-                         "pe_graph_destroy"):
+                         "pe_graph_destroy", "pe_pic_step_noalloc"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -221,6 +224,14 @@ def pe_tally(run: int) -> TallyOut:
     st = _check(lib().pe_tally(run, C.byref(out)), allow=(PE_ERR_BUFFER_FULL,))
     out.status = st
     return out
+
+
+def pe_pic_step_noalloc(tables: int, params: RunParams, n: int, buffers: Buffers, step0: int, n_steps: int,
+                        stream) -> None:
+    """PIC steps on caller-owned buffers with the library's fixed scratch array (no device
+    allocation); see pe.h.  ``stream`` is a cudaStream_t value (e.g. torch's ``cuda_stream``)."""
+    _check(lib().pe_pic_step_noalloc(tables, C.byref(params), int(n), C.byref(buffers), int(step0), int(n_steps),
+                                     stream))
 
 
 def pe_destroy(run: int):

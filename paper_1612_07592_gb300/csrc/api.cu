@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <array>
 #include <memory>
+#include <mutex>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -701,5 +702,151 @@ extern "C" pe_status pe_graph_destroy(pe_graph* g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
+    return PE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PIC steps that allocate nothing (pe_pic_step_noalloc)
+// ---------------------------------------------------------------------------
+// The current sums of one PIC step live in this fixed array instead of memory
+// that pe_init_particles allocates: 3 x PE_PIC_MAX_CELLS x 8 bytes = 96 KiB, held
+// on every GPU that loads the library until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned long long g_pic_scratch[3 * PE_PIC_MAX_CELLS];
+
+namespace {
+
+constexpr int kMaxDevices = 128;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (with that device current) and cached.  In host code the array's name
+// only stands for it: kernels get this address.
+pe_status pic_scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_pic_step_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_pic_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "pe_pic_step_noalloc: cudaGetSymbolAddress of the scratch array");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return PE_OK;
+}
+
+// The device description of a PE_PIC_1D run from its parameters and buffers (the
+// same quantities pe_init_particles sets up), without creating a run.
+pe_status pic_describe(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, RunDev& d) {
+    int iz = -1;
+    for (int k = 0; k < t->host.p.n_Z; ++k)
+        if (std::fabs(t->host.Z[k] - rp->Z) < 1e-9) iz = k;
+    if (iz < 0) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: Z is not in the table set");
+    std::memset(&d, 0, sizeof(d));
+    d.x = b->x; d.y = b->y; d.ux = b->ux; d.uy = b->uy; d.uz = b->uz;
+    d.tau = b->tau;
+    d.photons = static_cast<uint8_t*>(b->photons);
+    d.hist = static_cast<unsigned long long*>(b->hist);
+    d.tally = static_cast<unsigned long long*>(b->tally);
+    d.events = static_cast<unsigned long long*>(b->events);
+    d.n = n;
+    d.capacity = b->photon_capacity;
+    StepC<double>& c = d.c;
+    const double kl = 2.0 * kPi / rp->lambda_m;
+    c.dt = rp->dt_over_T * 2.0 * kPi;
+    split_dt(c.dt, &c.dt_hi, &c.dt_lo);
+    const double E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
+    c.inv_ES = 1.0 / E_S;
+    c.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * E_S * c.dt;
+    const double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
+    const double n_i = rp->ne_over_nc * n_c / rp->charge_state;
+    c.K_br = n_i * kAlpha * kRe * kRe * (c.dt / kl);
+    c.x0 = rp->slab_x0_m * kl;
+    c.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
+    c.yh = rp->y_half_m * kl;
+    c.inv_log_emax = 1.0 / std::log(kHistEmaxMeV / kMec2MeV);
+    c.a0 = rp->a0;
+    c.phi_r = 2.0 * kPi * rp->ramp_periods;
+    c.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
+    c.k_env = 0.5 * kPi / c.phi_r;
+    double smax = 0;
+    for (int i = 0; i < t->host.p.n_E; ++i) smax = std::max(smax, t->host.sigma[(size_t)iz * t->host.p.n_E + i]);
+    d.x_hat = c.K_br * smax;
+    c.P_hat = -std::expm1(-d.x_hat);
+    d.brems_method = rp->brems_method;
+    d.wait = rp->brems_method == PE_BREMS_NULL ? static_cast<uint32_t*>(b->brems_wait) : nullptr;
+    d.fk = FK_PIC;
+    d.geometry = rp->geometry;
+    d.polarisation = rp->polarisation;
+    d.enable_ncs = rp->enable_ncs;
+    d.enable_brems = rp->enable_brems;
+    d.box_enable = 0;                       // the PIC kernel removes electrons leaving [0, L]
+    c.box0 = 0.0;
+    c.box1 = rp->n_cells * c.dt;
+    const double w = n > 0 ? rp->ne_over_nc * rp->slab_thick_m * kl / (double)n : 0.0;
+    c.pic_kx = w / c.dt / 68719476736.0;
+    c.pic_kyz = -w / c.dt / 68719476736.0;
+    d.grid = b->grid;
+    d.n_cells = rp->n_cells;
+    d.iz = iz;
+    d.run_id = rp->run_id;
+    d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
+    d.seed_hi = (uint32_t)(rp->seed >> 32);
+    return PE_OK;
+}
+
+}  // namespace
+
+extern "C" pe_status pe_pic_step_noalloc(const pe_tables* t, const pe_run_params* rp, int64_t n,
+                                         const pe_buffers* b, int64_t step0, int64_t n_steps, void* stream) {
+    if (!t || !rp || !b) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: null argument");
+    if (rp->geometry != PE_PIC_1D) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: geometry must be PE_PIC_1D");
+    if (rp->n_cells < 4 || rp->n_cells > PE_PIC_MAX_CELLS)
+        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: n_cells must be in [4, PE_PIC_MAX_CELLS = 4096]: the fixed "
+                                "scratch array holds the current sums of at most PE_PIC_MAX_CELLS cells");
+    if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: precision");
+    if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP)
+        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: polarisation");
+    if (rp->brems_method != PE_BREMS_DIRECT && rp->brems_method != PE_BREMS_NULL)
+        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: brems_method");
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: n must be in [0, 2^31)");
+    if (step0 < 0 || n_steps < 0 || step0 + n_steps >= (int64_t(1) << 32))
+        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: step range");
+    if (!(rp->lambda_m > 0 && rp->dt_over_T > 0 && rp->charge_state > 0 && rp->ramp_periods > 0))
+        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: lambda, dt, charge state, ramp must be positive");
+    if (n > 0) {
+        const void* ps[] = {b->x, b->y, b->ux, b->uy, b->uz, b->tau, b->hist, b->tally, b->grid};
+        for (const void* q : ps)
+            if (!q || !aligned16(q)) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: buffers must be non-null and 16-byte aligned");
+        if (rp->brems_method == PE_BREMS_NULL && (!b->brems_wait || !aligned16(b->brems_wait)))
+            return fail(PE_ERR_ARG, "pe_pic_step_noalloc: PE_BREMS_NULL needs brems_wait");
+        if (b->photon_capacity < 0 || (b->photon_capacity > 0 && (!b->photons || !aligned16(b->photons))))
+            return fail(PE_ERR_ARG, "pe_pic_step_noalloc: photon buffer");
+    }
+    if (n == 0 || n_steps == 0) return PE_OK;
+    RunDev d;
+    pe_status st = pic_describe(t, rp, n, b, d);
+    if (st != PE_OK) return st;
+    void* scratch = nullptr;
+    st = pic_scratch_address(&scratch);
+    if (st != PE_OK) return st;
+    d.jacc = static_cast<unsigned long long*>(scratch);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the array keeps what the last call left: the current sums must start at zero
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_pic_step_noalloc: clearing the scratch array");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int64_t k = 0; k < n_steps; ++k) {
+        d.step0 = step0 + k;
+        launch_pic_step(t->dev, d, rp->precision, sms, s);
+        g_launches += 2;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pe_pic_step_noalloc: PIC step");
     return PE_OK;
 }
