@@ -304,7 +304,8 @@ def main():
                             "serving_poisson50hz": serving(pe, stream),
                             "bunch_1gev_au_5mm_1e6": bunch_methods(pe, stream, flush),
                             "bunch_1gev_au_5mm_1e6_dt_T10": bunch_methods(pe, stream, flush, dt_over_T=0.1),
-                            "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush)}
+                            "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush),
+                            "pic_1d_au_a270_1e6x2000": pic_job(pe, tables, cfg, stream, flush)}
     if rank == 0 and not args.skip_cpu_baseline:
         threads = os.cpu_count() or 1
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
@@ -519,6 +520,26 @@ def reflected(pe, tables, cfg, stream, flush):
             "steps": cfg["steps"], "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]),
             "ncs_below_cut": int(t.tally[pe.T["N_NCS_BELOW"]]), "photons": int(t.tally[pe.T["N_PHOTONS"]]),
             "kernel": "k_step_persistent (FP32, reflected-wave field kind)"}
+
+
+def pic_job(pe, tables, cfg, stream, flush, n=1_000_000, n_cells=1000, steps=2000):
+    """The config-2 physics with self-consistent fields (1D PIC around the step): 1e6 electrons in
+    a 1 um Au 51+ slab at 50 n_c, the a0 = 270 pulse injected at x = 0 of a 10 um grid (1000 cells),
+    2000 steps; FP32.  Two launches per step (particles with current deposit, field solve)."""
+    import torch
+    run = dict(cfg["run"], run_id=13, geometry=pe.PE_PIC_1D, n_cells=n_cells)
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=1 << 26, stream=stream)
+    stream.synchronize()
+    ms = _timed_jobs(pe, r, tables, steps, stream, flush)
+    t = r.tally_out()
+    ex, ey, ez, by, bz, rho = r.pic_fields()
+    r.close()
+    return {"value": t.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": n,
+            "n_cells": n_cells, "steps": steps, "us_per_step": 1e3 * ms / steps,
+            "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]), "killed": int(t.tally[pe.T["N_KILLED"]]),
+            "max_Ex": float(np.abs(ex).max()),
+            "kernels": "k_pic_particles + k_pic_fields (FP32), one launch each per step"}
 
 
 def serving(pe, stream, n_requests=60):
