@@ -158,7 +158,12 @@ def main():
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
     ap.add_argument("--particles", type=int, default=0, help="override N (profiling runs only)")
     ap.add_argument("--job-steps", type=int, default=0, help="override steps per job (profiling runs only)")
+    ap.add_argument("--profile-pic", action="store_true",
+                    help="profiling run only: one PE_PIC_1D job (--particles, --job-steps) of the config-2 physics")
     args = ap.parse_args()
+    if args.profile_pic:
+        profile_pic(args.particles or 200_000, args.job_steps or 500)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -540,6 +545,24 @@ def pic_job(pe, tables, cfg, stream, flush, n=1_000_000, n_cells=1000, steps=200
             "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]), "killed": int(t.tally[pe.T["N_KILLED"]]),
             "max_Ex": float(np.abs(ex).max()),
             "kernels": "k_pic_particles + k_pic_fields (FP32), one launch each per step"}
+
+
+def profile_pic(n, steps):
+    """One untimed PE_PIC_1D job for profilers: the config-2 physics with self-consistent fields
+    (1000 cells), n electrons, `steps` steps in one pe_step call."""
+    import torch
+    import paper_1612_07592_gb300 as pe
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.config2()
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **dict(c["run"], geometry=pe.PE_PIC_1D, n_cells=1000)), n,
+               capacity=1 << 24)
+    pe.pe_step([r.handle], steps)
+    torch.cuda.synchronize()
+    t = r.tally_out()
+    print(json.dumps({"profile_pic": True, "electrons": n, "steps": steps,
+                      "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]), "killed": int(t.tally[pe.T["N_KILLED"]])}))
+    r.close()
 
 
 def serving(pe, stream, n_requests=60):
