@@ -271,6 +271,25 @@ pe_status pe_tally(pe_run* run, pe_tally_out* out);
 
 pe_status pe_destroy(pe_run* run);
 
+/* Kinetic-energy spectrum of the run's live electrons (the electron spectra of
+ * the paper's Fig. 5): counts (uint64, device memory of the caller, n_bins
+ * words, 16-byte aligned, cleared by the call) in n_bins log bins of (gamma - 1)
+ * m c^2 over [e_min_mev, e_max_mev); energies outside are not counted.
+ * Asynchronous on the run's stream.  Errors: PE_ERR_ARG (null, n_bins outside
+ * [1, 4096], bad range, misaligned), PE_ERR_CUDA.                             */
+pe_status pe_electron_spectrum(pe_run* run, int n_bins, double e_min_mev, double e_max_mev, void* counts);
+
+/* Map of the stored photons over emission position x and energy (the photon
+ * density maps of the paper's Fig. 4, reduced to 1D): counts (uint64, device
+ * memory of the caller, nx * ne words, x-major, cleared by the call) in nx
+ * linear bins of x over [x_min_m, x_max_m) and ne log bins of the photon
+ * energy over [e_min_mev, e_max_mev).  Reads the stored count on the device
+ * (min(appended, capacity)).  Asynchronous on the run's stream.  Errors:
+ * PE_ERR_ARG (null, nx * ne outside [1, 2^24], bad ranges, misaligned),
+ * PE_ERR_CUDA.                                                                */
+pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int ne, double e_min_mev,
+                        double e_max_mev, void* counts);
+
 /* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */
 double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);

@@ -115,13 +115,15 @@ def lib():
             L.pe_destroy.argtypes = [vp]
             L.pe_pic_step_noalloc.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), C.c_int64,
                                               C.c_int64, vp]
+            L.pe_electron_spectrum.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
+            L.pe_photon_map.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, vp]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
             L.pe_last_error.restype = C.c_char_p
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
-                         "pe_graph_destroy", "pe_pic_step_noalloc"):
+                         "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -234,6 +236,16 @@ def pe_pic_step_noalloc(tables: int, params: RunParams, n: int, buffers: Buffers
                                      stream))
 
 
+def pe_electron_spectrum(run: int, n_bins: int, e_min_mev: float, e_max_mev: float, counts_ptr: int) -> None:
+    _check(lib().pe_electron_spectrum(run, int(n_bins), float(e_min_mev), float(e_max_mev), counts_ptr))
+
+
+def pe_photon_map(run: int, nx: int, x_min_m: float, x_max_m: float, ne: int, e_min_mev: float, e_max_mev: float,
+                  counts_ptr: int) -> None:
+    _check(lib().pe_photon_map(run, int(nx), float(x_min_m), float(x_max_m), int(ne), float(e_min_mev),
+                               float(e_max_mev), counts_ptr))
+
+
 def pe_destroy(run: int):
     _check(lib().pe_destroy(run))
 
@@ -340,6 +352,19 @@ class Run:
         ex = g[:n]
         fp, fm, gp, gm, rho = (g[n + k * (n + 1): n + (k + 1) * (n + 1)] for k in range(5))
         return ex, 0.5 * (fp + fm), 0.5 * (gp + gm), 0.5 * (gm - gp), 0.5 * (fp - fm), rho
+
+    def electron_spectrum(self, n_bins: int = 200, e_min_mev: float = 0.01, e_max_mev: float = 1e4) -> np.ndarray:
+        """Counts of live electrons in log bins of kinetic energy (MeV), computed on the device."""
+        out = self.torch.zeros(n_bins, dtype=self.torch.int64, device=self.x.device)
+        pe_electron_spectrum(self.handle, n_bins, e_min_mev, e_max_mev, out.data_ptr())
+        return out.cpu().numpy().view(np.uint64)
+
+    def photon_map(self, nx: int, x_min_m: float, x_max_m: float, ne: int = 64, e_min_mev: float = 0.511,
+                   e_max_mev: float = 1e4) -> np.ndarray:
+        """Counts of stored photons over (emission x, log energy), computed on the device (nx x ne)."""
+        out = self.torch.zeros(nx * ne, dtype=self.torch.int64, device=self.x.device)
+        pe_photon_map(self.handle, nx, x_min_m, x_max_m, ne, e_min_mev, e_max_mev, out.data_ptr())
+        return out.cpu().numpy().view(np.uint64).reshape(nx, ne)
 
     def wait_words(self) -> np.ndarray:
         """Null-collision waits (uint32, PE_WAIT_NEVER = no further candidate)."""

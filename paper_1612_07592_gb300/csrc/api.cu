@@ -606,6 +606,38 @@ extern "C" pe_status pe_tally(pe_run* r, pe_tally_out* out) {
     return PE_OK;
 }
 
+extern "C" pe_status pe_electron_spectrum(pe_run* r, int n_bins, double e_min_mev, double e_max_mev, void* counts) {
+    if (!r || !counts) return fail(PE_ERR_ARG, "pe_electron_spectrum: null argument");
+    if (n_bins < 1 || n_bins > 4096) return fail(PE_ERR_ARG, "pe_electron_spectrum: n_bins must be in [1, 4096]");
+    if (!(e_min_mev > 0 && e_max_mev > e_min_mev)) return fail(PE_ERR_ARG, "pe_electron_spectrum: energy range");
+    if (!aligned16(counts)) return fail(PE_ERR_ARG, "pe_electron_spectrum: counts must be 16-byte aligned");
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (size_t)n_bins, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_electron_spectrum");
+    launch_electron_spectrum(r->dev, r->params.precision, e_min_mev, e_max_mev, n_bins,
+                             static_cast<unsigned long long*>(counts), r->stream);
+    g_launches++;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_electron_spectrum");
+}
+
+extern "C" pe_status pe_photon_map(pe_run* r, int nx, double x_min_m, double x_max_m, int ne, double e_min_mev,
+                                   double e_max_mev, void* counts) {
+    if (!r || !counts) return fail(PE_ERR_ARG, "pe_photon_map: null argument");
+    if (nx < 1 || ne < 1 || (int64_t)nx * ne > (int64_t(1) << 24))
+        return fail(PE_ERR_ARG, "pe_photon_map: nx, ne >= 1 and nx * ne <= 2^24");
+    if (!(x_max_m > x_min_m && e_min_mev > 0 && e_max_mev > e_min_mev))
+        return fail(PE_ERR_ARG, "pe_photon_map: ranges");
+    if (!aligned16(counts)) return fail(PE_ERR_ARG, "pe_photon_map: counts must be 16-byte aligned");
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (size_t)nx * ne, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_photon_map");
+    const double kl = 2.0 * kPi / r->params.lambda_m;
+    launch_photon_map(r->dev, x_min_m * kl, x_max_m * kl, nx, e_min_mev, e_max_mev, ne,
+                      static_cast<unsigned long long*>(counts), r->stream);
+    g_launches++;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_photon_map");
+}
+
 extern "C" pe_status pe_destroy(pe_run* r) {
     if (!r) return fail(PE_ERR_ARG, "pe_destroy: null");
     delete r;

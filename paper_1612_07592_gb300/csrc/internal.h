@@ -133,6 +133,12 @@ inline RunDevT<float> to_float(const RunDevT<double>& d) {
     return f;
 }
 
+// diagnostics (kernels.cu)
+void launch_electron_spectrum(const RunDev& r, int precision, double e_lo, double e_hi, int n_bins,
+                              unsigned long long* out, cudaStream_t s);
+void launch_photon_map(const RunDev& r, double x_lo, double x_hi, int nx, double e_lo, double e_hi, int ne,
+                       unsigned long long* out, cudaStream_t s);
+
 // 1D PIC (kernels_pic.cu)
 void launch_pic_rho(const RunDev& r, int precision, cudaStream_t s);
 void launch_pic_step(const TablesDev& t, const RunDev& r, int precision, int sms, cudaStream_t s);

@@ -1,5 +1,8 @@
 // kernels.cu -- launchers of the init and plain FP64 kernels and the precision-
 // specific persistent kernels (instantiated in kernels_f32.cu / kernels_f64.cu).
+#include <algorithm>
+#include <cmath>
+
 #include "kernels.cuh"
 
 namespace pe {
@@ -118,6 +121,74 @@ void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s) 
 int persistent_smem_bytes(const TablesDev& t, int precision) {
     size_t rs = precision == PE_F32 ? 4 : 8;
     return (int)(8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + rs * (t.n_eta + (size_t)t.n_Z * t.n_E));
+}
+
+}  // namespace pe
+
+namespace pe {
+
+// ---------------------------------------------------------------------------
+// diagnostics: electron energy spectrum (Fig. 5) and photon (x, energy) map (Fig. 4)
+// ---------------------------------------------------------------------------
+// bin of v in [lo, hi) on log bins: -1 below, n_bins at or above
+__device__ __forceinline__ int log_bin(double v, double ln_lo, double inv_dln, int n_bins) {
+    if (!(v > 0.0)) return -1;
+    const double b = (log(v) - ln_lo) * inv_dln;
+    if (b < 0.0) return -1;
+    return b >= (double)n_bins ? n_bins : (int)b;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_electron_spectrum(RunDevT<double> r, double ln_lo, double inv_dln, int n_bins,
+                                                           unsigned long long* out) {
+    extern __shared__ unsigned long long s_bins[];
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) s_bins[k] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = sizeof(R) == 4 ? (double)((const float2*)r.x)[i].x : ((const double*)r.x)[i];
+        if (isnan(x)) continue;
+        const double u0 = ((const R*)r.ux)[i], u1 = ((const R*)r.uy)[i], u2 = ((const R*)r.uz)[i];
+        const double ek = (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0) * kMec2MeV;   // kinetic energy, MeV
+        const int b = log_bin(ek, ln_lo, inv_dln, n_bins);
+        if (b >= 0 && b < n_bins) atomicAdd(&s_bins[b], 1ull);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x)
+        if (s_bins[k]) atomicAdd(out + k, s_bins[k]);
+}
+
+__global__ void __launch_bounds__(256) k_photon_map(const uint8_t* photons, const unsigned long long* tally,
+                                                    int64_t capacity, double x_lo, double inv_dx, int nx,
+                                                    double ln_lo, double inv_dln, int ne, unsigned long long* out) {
+    const unsigned long long appended = tally[PE_T_N_PHOTONS];
+    const int64_t count = appended < (unsigned long long)capacity ? (int64_t)appended : capacity;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4*>(photons + i * 32)[0];   // x, y, energy (m c^2), kx
+        const double xb = ((double)a.x - x_lo) * inv_dx;
+        if (!(xb >= 0.0) || xb >= (double)nx) continue;
+        const int eb = log_bin((double)a.z * kMec2MeV, ln_lo, inv_dln, ne);
+        if (eb < 0 || eb >= ne) continue;
+        atomicAdd(out + (size_t)((int)xb) * ne + eb, 1ull);
+    }
+}
+
+void launch_electron_spectrum(const RunDev& r, int precision, double e_lo, double e_hi, int n_bins,
+                              unsigned long long* out, cudaStream_t s) {
+    const double ln_lo = std::log(e_lo), inv_dln = n_bins / (std::log(e_hi) - std::log(e_lo));
+    const int grid = (int)std::min<int64_t>((r.n + 255) / 256, 1024);
+    if (grid <= 0) return;
+    const size_t smem = sizeof(unsigned long long) * (size_t)n_bins;
+    if (precision == PE_F32) k_electron_spectrum<float><<<grid, 256, smem, s>>>(r, ln_lo, inv_dln, n_bins, out);
+    else k_electron_spectrum<double><<<grid, 256, smem, s>>>(r, ln_lo, inv_dln, n_bins, out);
+}
+
+void launch_photon_map(const RunDev& r, double x_lo, double x_hi, int nx, double e_lo, double e_hi, int ne,
+                       unsigned long long* out, cudaStream_t s) {
+    if (r.capacity <= 0) return;
+    // the stored count is read on the device: a grid-stride launch sized for the capacity
+    const int grid = (int)std::min<int64_t>((r.capacity + 255) / 256, 2048);
+    k_photon_map<<<grid, 256, 0, s>>>(r.photons, r.tally, r.capacity, x_lo, nx / (x_hi - x_lo), nx, std::log(e_lo),
+                                      ne / (std::log(e_hi) - std::log(e_lo)), ne, out);
 }
 
 }  // namespace pe

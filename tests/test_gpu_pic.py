@@ -151,3 +151,44 @@ def test_pic_runs_step_alone():
         pe.pe_graph_create([a.handle], 5)
     with pytest.raises(pe.PeError):                  # slab outside the grid
         pe.Run(lt, pe.run_params(precision=pe.PE_F32, **_run(n_cells=100)), 10)
+
+
+def _log_hist(v, lo, hi, n):
+    ln_lo, inv = math.log(lo), n / (math.log(hi) - math.log(lo))
+    v = v[v > 0]
+    b = np.floor((np.log(v) - ln_lo) * inv)
+    b = b[(b >= 0) & (b < n)].astype(int)
+    return np.bincount(b, minlength=n)
+
+
+def test_pic_spectra_and_photon_map():
+    """The device's electron spectrum and photon (x, energy) map (the paper's Figs. 5 and 4, in 1D)
+    equal the histograms of the device state and photon records, and the spectrum equals the
+    oracle's within the FP64 parity horizon."""
+    run = _run()
+    n, steps = 2000, 100
+    lt, ot = tables(_tp(48), Z)
+    st_o, grid_o, ev_o, ph_o, nph_o, hist_o, tal_o = _oracle(ot, run, n, steps)
+    r, out = _gpu(lt, run, n, steps, pe.PE_F64)
+    spec = r.electron_spectrum(200, 0.01, 1e4)
+    st = r.state()
+    ek = (np.sqrt(1 + (st[:, 2:5] ** 2).sum(1)) - 1) * 0.51099895
+    ek_o = (np.sqrt(1 + (st_o[:, 2:5] ** 2).sum(1)) - 1) * 0.51099895
+    want = _log_hist(ek[~np.isnan(st[:, 0])], 0.01, 1e4, 200)
+    assert np.abs(spec.astype(np.int64) - want).sum() <= 2
+    assert np.abs(spec.astype(np.int64) - _log_hist(ek_o[~np.isnan(st_o[:, 0])], 0.01, 1e4, 200)).sum() <= 2
+    assert spec.sum() > 0.9 * n
+    r.close()
+    # photon map after the interaction
+    r, out = _gpu(lt, run, n, 500, pe.PE_F32)
+    kl = 2 * math.pi / 1e-6
+    m = r.photon_map(40, 0.0, NC * 0.01e-6, 32, 0.511, 1e4)
+    ph = r.photon_records()
+    xb = np.floor((ph["x"].astype(np.float64) - 0.0) * (40 / (NC * 0.01e-6 * kl)))
+    eb = np.floor((np.log(ph["energy"].astype(np.float64) * 0.51099895) - math.log(0.511)) * (32 / (math.log(1e4) - math.log(0.511))))
+    ok = (xb >= 0) & (xb < 40) & (eb >= 0) & (eb < 32)
+    want = np.zeros((40, 32), dtype=np.int64)
+    np.add.at(want, (xb[ok].astype(int), eb[ok].astype(int)), 1)
+    assert m.sum() > 100
+    assert np.abs(m.astype(np.int64) - want).sum() <= 4
+    r.close()
