@@ -24,6 +24,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f)); }
 // per-electron operations (no paired form)
 __device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 __device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
 __device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__logf(a.x), __logf(a.y)); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
@@ -147,7 +148,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float2 um1 = sub2(Q.u1, mul2(h, ey));
     float2 um2 = (G == FK_PLANE_CP) ? sub2(Q.u2, mul2(h, ez)) : Q.u2;
     float2 q = fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f))));
-    float2 ig = div2(P2(1.0f), sqrt2(q));
+    float2 ig = rsqrt2(q);
     float2 t1 = (G == FK_PLANE_CP) ? mul2(mul2(h, ez), ig) : P2(0.0f);   // -h B_y / gamma
     float2 t2 = mul2(neg2(mul2(h, ey)), ig);                           // -h B_z / gamma
     float2 f = div2(P2(2.0f), fma2(t2, t2, fma2(t1, t1, P2(1.0f))));
@@ -158,7 +159,11 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
     Q.u1 = sub2(sub2(um1, mul2(p0, s2)), mul2(h, ey));
     Q.u2 = (G == FK_PLANE_CP) ? sub2(add2(um2, mul2(p0, s1)), mul2(h, ez)) : um2;
-    float2 gamma = sqrt2(fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, fma2(Q.u0, Q.u0, P2(1.0f)))));
+    // gamma and 1/gamma from one reciprocal square root (1/gamma serves the rate and the
+    // position update; emitting lanes refresh it from their new gamma)
+    const float2 g2 = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, fma2(Q.u0, Q.u0, P2(1.0f))));
+    float2 inv_g = rsqrt2(g2);
+    float2 gamma = mul2(g2, inv_g);
     const float2 xn = Q.x;
     float gam[2] = {gamma.x, gamma.y};
 
@@ -185,7 +190,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         if (Q.act[0] && abx) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         if (Q.act[1] && aby) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // tau -= ncs_coef (eta / gamma) h(eta), compensated
-        float2 dtau = mul2(mul2(P2(c.ncs_coef), div2(eta, gamma)), hv);
+        float2 dtau = mul2(mul2(P2(c.ncs_coef), mul2(eta, inv_g)), hv);
         float2 s, e;
         two_sum2(Q.tau, neg2(dtau), s, e);
         Q.tau = s;
@@ -198,6 +203,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 take(ncs_emit<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, hist, tally), P,
                      gam[k], st_ncs[k], pn[k]);
                 repack(Q, k, P);
+                set_comp(inv_g, k, 1.0f / gam[k]);
             }
         }
     }
@@ -214,6 +220,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                                                 hist, tally),
                          P, gam[k], st_br[k], pb[k]);
                     repack(Q, k, P);
+                    set_comp(inv_g, k, 1.0f / gam[k]);
                 } else if (Q.wait[k] != PE_WAIT_NEVER) {
                     --Q.wait[k];
                 }
@@ -227,13 +234,14 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist,
                                          tally);
                     repack(Q, k, P);
+                    set_comp(inv_g, k, 1.0f / gam[k]);
                 }
             }
         }
     }
 
     // x^{n+1} = x^n + dt u_x / gamma, compensated
-    float2 d = div2(mul2(dt, Q.u0), make_float2(gam[0], gam[1]));
+    float2 d = mul2(mul2(dt, Q.u0), inv_g);
     float2 s, e;
     two_sum2(Q.x, d, s, e);
     Q.x = s;
