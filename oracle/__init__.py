@@ -35,6 +35,10 @@ T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4
 
 PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
                          ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
+PAIR_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("e_minus", "<f4"), ("e_plus", "<f4"), ("kx", "<f4"),
+                       ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("photon", "<u4"), ("id_mech", "<u4")])
+PAIR_TALLY_WORDS = 8
+PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, E_PAIRS=4, E_POSITRONS=6)
 
 
 def build(force: bool = False) -> str:
@@ -95,6 +99,17 @@ def lib():
             L.or_brems_dcs_raw.restype = C.c_double
             L.or_brems_sigma_direct.argtypes = [C.c_double, C.c_double, C.c_double]
             L.or_brems_sigma_direct.restype = C.c_double
+            L.or_bh_dcs_raw.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.or_bh_dcs_raw.restype = C.c_double
+            L.or_bh_sigma_direct.argtypes = [C.c_double, C.c_double]
+            L.or_bh_sigma_direct.restype = C.c_double
+            L.or_bh_sigma_interp.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int)]
+            L.or_bh_sigma_interp.restype = C.c_double
+            L.or_sample_bh_x.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.or_sample_bh_x.restype = C.c_double
+            L.or_pair_transport.argtypes = [C.c_void_p, C.POINTER(RunParams), C.c_void_p, C.c_int64, C.c_int64,
+                                            C.c_void_p, C.c_int64, C.POINTER(C.c_uint64)]
+            L.or_pair_transport.restype = C.c_int
             L.or_tables_build.argtypes = [C.POINTER(TableParams), C.c_int, dp]
             L.or_tables_build.restype = C.c_void_p
             L.or_tables_free.argtypes = [C.c_void_p]
@@ -191,14 +206,15 @@ class Tables:
 
     def export(self, which: int, iz: int = 0) -> np.ndarray:
         p = self.params
-        n = {0: p.n_eta, 1: p.n_eta * p.n_y, 2: p.n_y, 3: p.n_E, 4: p.n_E * p.n_s}[which]
+        n = {0: p.n_eta, 1: p.n_eta * p.n_y, 2: p.n_y, 3: p.n_E, 4: p.n_E * p.n_s, 5: p.n_E,
+             6: p.n_E * p.n_s}[which]
         out = np.empty(n, dtype=np.float64)
         got = lib().or_tables_export(self._h, which, iz, _dp(out), n)
         if got != n:
             raise RuntimeError("export failed")
         if which == 1:
             out = out.reshape(p.n_eta, p.n_y)
-        if which == 4:
+        if which in (4, 6):
             out = out.reshape(p.n_E, p.n_s)
         return out
 
@@ -222,6 +238,14 @@ class Tables:
         f = C.c_int(0)
         v = lib().or_brems_sigma_interp(self._h, iz, gamma, C.byref(f))
         return v, f.value
+
+    def bh_sigma_interp(self, iz: int, k: float):
+        f = C.c_int(0)
+        v = lib().or_bh_sigma_interp(self._h, iz, k, C.byref(f))
+        return v, f.value
+
+    def sample_bh_x(self, iz: int, k: float, R: float) -> float:
+        return lib().or_sample_bh_x(self._h, iz, k, R)
 
 
 def _wait_ptr(run: RunParams, wait, n: int):
@@ -267,6 +291,21 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
     if rc != 0:
         raise RuntimeError("or_run failed")
     return photons[:min(n_ph.value, capacity)], n_ph.value, hist, tally
+
+
+def pair_transport(tables: Tables, run: RunParams, photons, step_end: int, capacity: int = 1 << 20):
+    """Bethe-Heitler conversion of the photon records (PHOTON_DTYPE) in the target up to
+    step_end (see oracle.h); returns (pairs, true pair count, tally)."""
+    ph = np.ascontiguousarray(photons, dtype=PHOTON_DTYPE)
+    pairs = np.zeros(capacity, dtype=PAIR_DTYPE)
+    tally = np.zeros(PAIR_TALLY_WORDS, dtype=np.uint64)
+    rc = lib().or_pair_transport(tables._h, C.byref(run), ph.ctypes.data_as(C.c_void_p), len(ph), int(step_end),
+                                 pairs.ctypes.data_as(C.c_void_p), capacity,
+                                 tally.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc != 0:
+        raise RuntimeError("or_pair_transport failed")
+    n = int(tally[PT["N_PAIRS"]])
+    return pairs[:min(n, capacity)], n, tally
 
 
 def fixed_to_float(tally: np.ndarray, idx: int) -> float:
@@ -364,6 +403,7 @@ def __getattr__(name):
          "ncs_power_integral": "or_ncs_power_integral", "ncs_h_direct": "or_ncs_h_direct",
          "coulomb_f": "or_coulomb_f", "brems_dcs_raw": "or_brems_dcs_raw",
          "brems_sigma_direct": "or_brems_sigma_direct", "schwinger_field": "or_schwinger_field",
+         "bh_dcs_raw": "or_bh_dcs_raw", "bh_sigma_direct": "or_bh_sigma_direct",
          "critical_density": "or_critical_density"}
     if name in m:
         return getattr(lib(), m[name])

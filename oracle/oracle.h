@@ -51,6 +51,14 @@ double or_brems_dcs_raw(double Z, double gamma, double y, int complete);
  * ycut = photon_min/gamma, ymax = 1 - 1/gamma; units alpha r_e^2.            */
 double or_brems_sigma_direct(double Z, double gamma, double photon_min);
 
+/* ---- Bethe-Heitler pair production (Sec. 2.2: implemented like the brems) --
+ * d sigma / d x per atom in units of alpha r_e^2 for a photon of energy k (m c^2)
+ * giving a positron of energy x k and an electron of energy (1 - x) k; Tsai's
+ * DCS of the crossed process with the screening fits of Eq. (1).  Not clamped. */
+double or_bh_dcs_raw(double Z, double k, double x, int complete);
+/* sigma_BH(k) = int_{1/k}^{1-1/k} max(dsigma/dx, 0) dx (0 for k <= 2), alpha r_e^2 */
+double or_bh_sigma_direct(double Z, double k);
+
 /* ---- tables ---------------------------------------------------------------- */
 typedef struct {
     int n_eta, n_y;           /* NCS rows (log eta) x columns (log y)          */
@@ -65,7 +73,9 @@ typedef struct or_tables or_tables;
 or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z);
 void or_tables_free(or_tables* t);
 /* which: 0 = h(eta_i) [n_eta], 1 = NCS CDF [n_eta*n_y], 2 = classical CDF [n_y],
- *        3 = sigma_Z(gamma_i) [n_E] for Z index iz, 4 = brems CDF [n_E*n_s].
+ *        3 = sigma_Z(gamma_i) [n_E] for Z index iz, 4 = brems CDF [n_E*n_s],
+ *        5 = sigma_BH(k_i) [n_E] with k_i log spaced on [2, gamma_max],
+ *        6 = Bethe-Heitler CDF over s [n_E*n_s], x = 1/k + s (1 - 2/k).
  * Returns the number of doubles written, or -1.                               */
 int64_t or_tables_export(const or_tables* t, int which, int iz, double* out, int64_t cap);
 /* classical-limit total int_0^inf (int_y^inf K53) dy as integrated (5 pi/3)  */
@@ -76,6 +86,8 @@ double or_sample_ncs_delta(const or_tables* t, double eta, double R, int* below)
 double or_sample_brems_y(const or_tables* t, int iz, double gamma, double R);
 double or_ncs_h_interp(const or_tables* t, double eta, int* range_flag);
 double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* above);
+double or_bh_sigma_interp(const or_tables* t, int iz, double k, int* above);
+double or_sample_bh_x(const or_tables* t, int iz, double k, double R);
 
 /* ---- run description ------------------------------------------------------- */
 enum { OR_LP_Y = 0, OR_CP = 1 };
@@ -171,6 +183,31 @@ int or_pic_run(const or_tables* t, const or_run_params* r, int n_cells, double w
                uint64_t* events, int n_threads);
 /* fields at x from the grid (linear weights; zero beyond the grid) */
 void or_pic_gather(int n_cells, double dx, const double* grid, double x, double E[3], double B[3]);
+
+/* ---- Bethe-Heitler conversion of the emitted photons in the target ----------
+ * Each photon record (k = energy > 2 m c^2) moves at c along its direction from
+ * its emission point: at step m (emission step n_e < m < step_end) its position
+ * is p = x_e + k^ (m - n_e) c dt.  At every step with p inside the target (the
+ * slab, and |y| <= y_half in 2D) it takes the test of Eq. (4) with sigma_BH:
+ * P = 1 - exp(-n_i sigma_BH(k) c dt), one draw of counter (id_mech, run id, m,
+ * 0x40000000 + n_e): test word = words 0-1 against floor(P 2^64), fraction word
+ * = words 2-3.  On conversion x is drawn from the CDF (u53 of the fraction word),
+ * E+ = x k, E- = k - E+, both along k^; the photon is gone.  A photon that leaves
+ * the target, or is outside and moving away from it, is not followed further. */
+typedef struct {
+    float x, y;               /* conversion point (position at the start of `step`) */
+    float e_minus, e_plus;    /* total energies of the electron and the positron, m c^2 */
+    float kx, ky, kz;         /* direction of the converted photon                */
+    uint32_t step;            /* step of the conversion                           */
+    uint32_t photon;          /* index of the photon record                       */
+    uint32_t id_mech;         /* the photon's id_mech                             */
+} or_pair;
+enum { ORP_N_PAIRS = 0, ORP_N_ENTERED = 1, ORP_N_K_ABOVE = 2, ORP_E_PAIRS = 4, ORP_E_POSITRONS = 6, ORP_WORDS = 8 };
+/* pairs in photon order to pairs[0..cap); tally (ORP_WORDS, cleared here):
+ * pair count (true count), photons that entered the target, of them above the
+ * table's k range, and 128-bit fixed-point sums of k and E+ of the conversions. */
+int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
+                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally);
 
 /* normalised helpers (exposed for unit pins) */
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */

@@ -53,6 +53,8 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 
 /* purposes of the per-particle Philox streams */
 enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4, PUR_WAIT = 256 };
+/* photon streams: counter word 0 = the photon's id_mech, word 3 = PUR_BH + emission step */
+#define PUR_BH 0x40000000u
 
 static void draw(const or_run_params* r, int64_t id, uint32_t step, uint32_t purpose, uint32_t w[4]) {
     uint32_t ctr[4] = {(uint32_t)id, r->run_id, step, purpose};
@@ -757,5 +759,69 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
     }
     *n_photons = total;
     free(lists); free(th_hist); free(th_tally); free(acc); free(jsum); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bethe-Heitler conversion of the photons in the target (Sec. 2.2: "similar */
+/* to the bremsstrahlung"): the direct MC collision of Eq. (4) per step with */
+/* sigma_BH, photons moving at c along their direction.                      */
+/* ------------------------------------------------------------------------- */
+int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
+                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally) {
+    run_ctx c;
+    make_ctx(t, r, &c, or__photon_min(t));
+    for (int k = 0; k < ORP_WORDS; ++k) tally[k] = 0;
+    const int two_d = (r->geometry == OR_GAUSS_2D);
+    for (int64_t j = 0; j < n_photons; ++j) {
+        const or_photon* ph = photons + j;
+        double k = (double)ph->energy;
+        if (!(k > 2.0)) continue;
+        double kx = (double)ph->kx, ky = (double)ph->ky, kz = (double)ph->kz;
+        double xe = (double)ph->x, ye = (double)ph->y;
+        int64_t ne = (int64_t)ph->step;
+        int above;
+        double sig = or_bh_sigma_interp(t, r->iz, k, &above);
+        double P = -expm1(-c.K_br * sig);                  /* beta = 1 */
+        uint64_t thr = (uint64_t)floor(P * 18446744073709551616.0);
+        if (P >= 1.0) thr = UINT64_MAX;
+        int was_in = 0;
+        for (int64_t m = ne + 1; m < step_end; ++m) {
+            double tt = (double)(m - ne) * c.dt;
+            double px = fma(kx, tt, xe), py = fma(ky, tt, ye);
+            int in = (px >= c.x0 && px <= c.x1);
+            if (two_d && fabs(py) > c.yh) in = 0;
+            if (!in) {
+                if (was_in) break;                         /* left the target */
+                if ((px < c.x0 && kx <= 0.0) || (px > c.x1 && kx >= 0.0)) break;
+                if (two_d && fabs(py) > c.yh && py * ky >= 0.0) break;
+                continue;
+            }
+            if (!was_in) {
+                was_in = 1;
+                tally[ORP_N_ENTERED]++;
+                if (above) tally[ORP_N_K_ABOVE]++;
+            }
+            uint32_t ctr[4] = {ph->id_mech, r->run_id, (uint32_t)m, PUR_BH + (uint32_t)ne};
+            uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
+            uint32_t w[4];
+            or_philox4x32_10(ctr, key, w);
+            if (word64(w[0], w[1]) < thr) {
+                double x = or_sample_bh_x(t, r->iz, k, u53(word64(w[2], w[3])));
+                double ep = x * k;
+                int64_t q = (int64_t)tally[ORP_N_PAIRS]++;
+                fx_add(tally + ORP_E_PAIRS, k);
+                fx_add(tally + ORP_E_POSITRONS, ep);
+                if (q < cap) {
+                    or_pair* o = pairs + q;
+                    o->x = (float)px; o->y = (float)(two_d ? py : 0.0);
+                    o->e_minus = (float)(k - ep); o->e_plus = (float)ep;
+                    o->kx = ph->kx; o->ky = ph->ky; o->kz = ph->kz;
+                    o->step = (uint32_t)m; o->photon = (uint32_t)j; o->id_mech = ph->id_mech;
+                }
+                break;
+            }
+        }
+    }
     return 0;
 }

@@ -15,6 +15,10 @@
  *  - sigma(E) integrates Eq. (1) from y_cut (hard-photon cut, Sec. 3) to the
  *    kinematic end point; the photon energy is drawn from the partial integral
  *    sigma(y, E) = sigma(E) R2 (Sec. 2.2, text after Eq. 4).
+ *  - Bethe-Heitler pair production, which Sec. 2.2 says is implemented like the
+ *    bremsstrahlung: Tsai's DCS of the crossed process with the same screening
+ *    fits, integrated over the positron fraction x in [1/k, 1 - 1/k], and the
+ *    CDF of the partial integral tabulated linearly in x.
  */
 #include "oracle.h"
 #include <math.h>
@@ -224,6 +228,50 @@ double or_brems_sigma_direct(double Z, double gamma, double photon_min) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Bethe-Heitler pair production, which Sec. 2.2 says is implemented like the   */
+/* bremsstrahlung: Tsai's screened DCS of the crossed process (Rev. Mod. Phys.  */
+/* 46, 815, the reference of Eq. 1) with the same screening fits and Coulomb    */
+/* correction.  Photon energy k (m c^2), positron energy fraction x = E+/k,     */
+/* E- = (1 - x) k; screening variables 100 m k / (E+ E- Z^{1/3}) and            */
+/* 100 m k / (E+ E- Z^{2/3}).                                                   */
+/* ------------------------------------------------------------------------- */
+double or_bh_dcs_raw(double Z, double k, double x, int complete) {
+    double g = 0.0, e = 0.0;
+    if (!complete) {
+        g = 100.0 / (k * x * (1.0 - x) * cbrt(Z));
+        e = 100.0 / (k * x * (1.0 - x) * cbrt(Z * Z));
+    }
+    double phi1 = 20.863 - 2.0 * log(1.0 + (0.55846 * g) * (0.55846 * g))
+                  - 4.0 * (1.0 - 0.6 * exp(-0.9 * g) - 0.4 * exp(-1.5 * g));
+    double phi2 = phi1 - (2.0 / 3.0) / (1.0 + 6.5 * g + 6.0 * g * g);
+    double psi1 = 28.340 - 2.0 * log(1.0 + (3.621 * e) * (3.621 * e))
+                  - 4.0 * (1.0 - 0.7 * exp(-8.0 * e) - 0.3 * exp(-29.2 * e));
+    double psi2 = psi1 - (2.0 / 3.0) / (1.0 + 40.0 * e + 400.0 * e * e);
+    double lnZ = log(Z);
+    double f = or_coulomb_f(Z);
+    double xx = x * (1.0 - x);
+    double t1 = (1.0 - 4.0 / 3.0 * xx)
+              * (Z * Z * (phi1 - 4.0 / 3.0 * lnZ - 4.0 * f) + Z * (psi1 - 8.0 / 3.0 * lnZ));
+    double t2 = -(2.0 / 3.0) * xx * (Z * Z * (phi1 - phi2) + Z * (psi1 - psi2));
+    return t1 + t2;
+}
+
+typedef struct { double Z, k, xmin, span; } bh_ctx;
+/* integrand in s with x = xmin + s span: dsigma/dx * span, clamped at 0 */
+static double bh_integrand(double s, const void* vc) {
+    const bh_ctx* c = (const bh_ctx*)vc;
+    double d = or_bh_dcs_raw(c->Z, c->k, c->xmin + s * c->span, 0);
+    if (d < 0.0) d = 0.0;
+    return d * c->span;
+}
+
+double or_bh_sigma_direct(double Z, double k) {
+    if (!(k > 2.0)) return 0.0;
+    bh_ctx c = {Z, k, 1.0 / k, 1.0 - 2.0 / k};
+    return integrate(bh_integrand, &c, 0.0, 1.0, 1e-14, 1e-300);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Tables                                                                    */
 /* ------------------------------------------------------------------------- */
 struct or_tables {
@@ -236,6 +284,8 @@ struct or_tables {
     double cl_total;
     double* sigma;    /* [n_Z][n_E]       */
     double* bcdf;     /* [n_Z][n_E][n_s]  */
+    double* bh_sigma; /* [n_Z][n_E]  Bethe-Heitler, k on the log grid [2, gamma_max] */
+    double* bh_cdf;   /* [n_Z][n_E][n_s] */
 };
 
 static double grid_log(double lo, double hi, int i, int n) {
@@ -284,6 +334,29 @@ static void build_brems_row(const or_table_params* p, double Z, double gamma, do
     }
 }
 
+static void build_bh_row(const or_table_params* p, double Z, double k, double* row, double* sigma) {
+    int n = p->n_s;
+    if (!(k > 2.0)) {
+        for (int j = 0; j < n; ++j) row[j] = (double)j / (double)(n - 1);
+        *sigma = 0.0;
+        return;
+    }
+    bh_ctx c = {Z, k, 1.0 / k, 1.0 - 2.0 / k};
+    double cum = 0.0;
+    row[0] = 0.0;
+    for (int j = 1; j < n; ++j) {
+        cum += integrate(bh_integrand, &c, (double)(j - 1) / (n - 1), (double)j / (n - 1), 1e-14, 1e-300);
+        row[j] = cum;
+    }
+    *sigma = cum;
+    if (cum > 0.0) {
+        for (int j = 0; j < n; ++j) row[j] /= cum;
+        row[n - 1] = 1.0;
+    } else {
+        for (int j = 0; j < n; ++j) row[j] = (double)j / (double)(n - 1);
+    }
+}
+
 or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z) {
     if (!p || p->n_eta < 2 || p->n_y < 2 || p->n_E < 2 || p->n_s < 2 || n_Z < 0) return NULL;
     or_tables* t = (or_tables*)calloc(1, sizeof(or_tables));
@@ -296,6 +369,8 @@ or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z) {
     t->cdf_cl = (double*)malloc(sizeof(double) * p->n_y);
     t->sigma = (double*)malloc(sizeof(double) * (n_Z > 0 ? n_Z : 1) * p->n_E);
     t->bcdf = (double*)malloc(sizeof(double) * (n_Z > 0 ? n_Z : 1) * p->n_E * p->n_s);
+    t->bh_sigma = (double*)malloc(sizeof(double) * (n_Z > 0 ? n_Z : 1) * p->n_E);
+    t->bh_cdf = (double*)malloc(sizeof(double) * (n_Z > 0 ? n_Z : 1) * p->n_E * p->n_s);
 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < p->n_eta; ++i) {
@@ -311,12 +386,21 @@ or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z) {
             build_brems_row(p, Z[iz], g, t->bcdf + ((int64_t)iz * p->n_E + i) * p->n_s,
                             &t->sigma[iz * p->n_E + i]);
         }
+
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int iz = 0; iz < n_Z; ++iz)
+        for (int i = 0; i < p->n_E; ++i) {
+            double k = grid_log(2.0, p->gamma_max, i, p->n_E);
+            build_bh_row(p, Z[iz], k, t->bh_cdf + ((int64_t)iz * p->n_E + i) * p->n_s,
+                         &t->bh_sigma[iz * p->n_E + i]);
+        }
     return t;
 }
 
 void or_tables_free(or_tables* t) {
     if (!t) return;
     free(t->Z); free(t->h); free(t->cdf); free(t->cdf_cl); free(t->sigma); free(t->bcdf);
+    free(t->bh_sigma); free(t->bh_cdf);
     free(t);
 }
 
@@ -340,6 +424,9 @@ int64_t or_tables_export(const or_tables* t, int which, int iz, double* out, int
         case 2: src = t->cdf_cl; n = p->n_y; break;
         case 3: if (iz < 0 || iz >= t->n_Z) return -1; src = t->sigma + (int64_t)iz * p->n_E; n = p->n_E; break;
         case 4: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bcdf + (int64_t)iz * p->n_E * p->n_s;
+                n = (int64_t)p->n_E * p->n_s; break;
+        case 5: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bh_sigma + (int64_t)iz * p->n_E; n = p->n_E; break;
+        case 6: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bh_cdf + (int64_t)iz * p->n_E * p->n_s;
                 n = (int64_t)p->n_E * p->n_s; break;
         default: return -1;
     }
@@ -447,4 +534,32 @@ double or_sample_brems_y(const or_tables* t, int iz, double gamma, double R) {
     else s = ((double)j + fr) / (double)(p->n_s - 1);
     double ycut = p->photon_min / gamma, ymax = 1.0 - 1.0 / gamma;
     return ycut * exp(s * log(ymax / ycut));
+}
+
+/* Bethe-Heitler lookups on the pair grid k in [2, gamma_max] (log spaced) */
+double or_bh_sigma_interp(const or_tables* t, int iz, double k, int* above) {
+    const or_table_params* p = &t->p;
+    *above = 0;
+    if (!(k > 2.0)) return 0.0;
+    int i, fl; double w;
+    row_pos(k, 2.0, p->gamma_max, p->n_E, &i, &w, &fl);
+    *above = (fl == 1);
+    const double* s = t->bh_sigma + (int64_t)iz * p->n_E;
+    return (1.0 - w) * s[i] + w * s[i + 1];
+}
+
+double or_sample_bh_x(const or_tables* t, int iz, double k, double R) {
+    const or_table_params* p = &t->p;
+    int i, fl; double w;
+    row_pos(k, 2.0, p->gamma_max, p->n_E, &i, &w, &fl);
+    const double* base = t->bh_cdf + (int64_t)iz * p->n_E * p->n_s;
+    const double* ra = base + (int64_t)i * p->n_s;
+    const double* rb = base + (int64_t)(i + 1) * p->n_s;
+    double c0, fr; int j;
+    invert_row(ra, rb, w, p->n_s, R, &c0, &j, &fr);
+    double s;
+    if (j < 0) s = 0.0;
+    else if (j >= p->n_s - 1) s = 1.0;
+    else s = ((double)j + fr) / (double)(p->n_s - 1);
+    return 1.0 / k + s * (1.0 - 2.0 / k);
 }

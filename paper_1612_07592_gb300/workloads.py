@@ -119,3 +119,32 @@ def bunch(E0_mev: float, target: str, thickness_m: float = 5e-3, n: int = 100_00
                    dt_over_T=dt_over_T, enable_ncs=0, seed=77, **tgt)
     return dict(name=f"bunch-{E0_mev:g}MeV-{target}-{thickness_m * 1e3:g}mm", n=n, steps=steps,
                 tables=tables_small(), Z=(13.0, 79.0), run=run)
+
+
+PHOTON_RECORD = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"), ("ky", "<f4"),
+                          ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
+
+
+def synthetic_photons(n: int, seed: int, x_range, k_range, step_range, theta_max: float = 0.3,
+                      y_half: float = 0.0, mech_frac: float = 0.5) -> np.ndarray:
+    """Seeded photon records (the 32-byte layout of the photon buffer) for the pair-production
+    tests: emission points uniform in x_range (c/omega units) and, if y_half > 0, in |y| < y_half;
+    energies log-uniform over k_range (m c^2); directions uniform in a cone of half-angle
+    theta_max about +x (a fraction reversed to -x); emission steps uniform over step_range;
+    distinct parent ids and a mechanism bit."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(n, dtype=PHOTON_RECORD)
+    p["x"] = rng.uniform(x_range[0], x_range[1], n)
+    p["y"] = rng.uniform(-y_half, y_half, n) if y_half > 0 else 0.0
+    p["energy"] = np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1]), n))
+    ct = rng.uniform(np.cos(theta_max), 1.0, n)
+    st = np.sqrt(1.0 - ct * ct)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    back = rng.uniform(0.0, 1.0, n) < 0.1
+    p["kx"] = np.where(back, -ct, ct)
+    p["ky"] = st * np.cos(ph)
+    p["kz"] = st * np.sin(ph)
+    p["step"] = rng.integers(step_range[0], step_range[1], n)
+    mech = (rng.uniform(0.0, 1.0, n) < mech_frac).astype(np.uint32)
+    p["id_mech"] = rng.permutation(n).astype(np.uint32) | (mech << np.uint32(31))
+    return p
