@@ -285,7 +285,8 @@ struct or_tables {
     double* sigma;    /* [n_Z][n_E]       */
     double* bcdf;     /* [n_Z][n_E][n_s]  */
     double* bh_sigma; /* [n_Z][n_E]  Bethe-Heitler, k on the log grid [2, gamma_max] */
-    double* bh_cdf;   /* [n_Z][n_E][n_s] */
+    double* bh_cdf;   /* [n_Z][n_E][n_s]; both built on first use */
+    int bh_built;
 };
 
 static double grid_log(double lo, double hi, int i, int n) {
@@ -386,15 +387,31 @@ or_tables* or_tables_build(const or_table_params* p, int n_Z, const double* Z) {
             build_brems_row(p, Z[iz], g, t->bcdf + ((int64_t)iz * p->n_E + i) * p->n_s,
                             &t->sigma[iz * p->n_E + i]);
         }
-
-#pragma omp parallel for collapse(2) schedule(dynamic, 1)
-    for (int iz = 0; iz < n_Z; ++iz)
-        for (int i = 0; i < p->n_E; ++i) {
-            double k = grid_log(2.0, p->gamma_max, i, p->n_E);
-            build_bh_row(p, Z[iz], k, t->bh_cdf + ((int64_t)iz * p->n_E + i) * p->n_s,
-                         &t->bh_sigma[iz * p->n_E + i]);
-        }
     return t;
+}
+
+/* the Bethe-Heitler tables, built on the first call that needs them */
+static void ensure_bh(const or_tables* tc) {
+    or_tables* t = (or_tables*)tc;
+    int done;
+#pragma omp atomic read
+    done = t->bh_built;
+    if (done) return;
+#pragma omp critical(or_bh_build)
+    {
+        if (!t->bh_built) {
+            const or_table_params* p = &t->p;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+            for (int iz = 0; iz < t->n_Z; ++iz)
+                for (int i = 0; i < p->n_E; ++i) {
+                    double k = grid_log(2.0, p->gamma_max, i, p->n_E);
+                    build_bh_row(p, t->Z[iz], k, t->bh_cdf + ((int64_t)iz * p->n_E + i) * p->n_s,
+                                 &t->bh_sigma[iz * p->n_E + i]);
+                }
+#pragma omp atomic write
+            t->bh_built = 1;
+        }
+    }
 }
 
 void or_tables_free(or_tables* t) {
@@ -425,8 +442,8 @@ int64_t or_tables_export(const or_tables* t, int which, int iz, double* out, int
         case 3: if (iz < 0 || iz >= t->n_Z) return -1; src = t->sigma + (int64_t)iz * p->n_E; n = p->n_E; break;
         case 4: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bcdf + (int64_t)iz * p->n_E * p->n_s;
                 n = (int64_t)p->n_E * p->n_s; break;
-        case 5: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bh_sigma + (int64_t)iz * p->n_E; n = p->n_E; break;
-        case 6: if (iz < 0 || iz >= t->n_Z) return -1; src = t->bh_cdf + (int64_t)iz * p->n_E * p->n_s;
+        case 5: if (iz < 0 || iz >= t->n_Z) return -1; ensure_bh(t); src = t->bh_sigma + (int64_t)iz * p->n_E; n = p->n_E; break;
+        case 6: if (iz < 0 || iz >= t->n_Z) return -1; ensure_bh(t); src = t->bh_cdf + (int64_t)iz * p->n_E * p->n_s;
                 n = (int64_t)p->n_E * p->n_s; break;
         default: return -1;
     }
@@ -539,6 +556,7 @@ double or_sample_brems_y(const or_tables* t, int iz, double gamma, double R) {
 /* Bethe-Heitler lookups on the pair grid k in [2, gamma_max] (log spaced) */
 double or_bh_sigma_interp(const or_tables* t, int iz, double k, int* above) {
     const or_table_params* p = &t->p;
+    ensure_bh(t);
     *above = 0;
     if (!(k > 2.0)) return 0.0;
     int i, fl; double w;
@@ -550,6 +568,7 @@ double or_bh_sigma_interp(const or_tables* t, int iz, double k, int* above) {
 
 double or_sample_bh_x(const or_tables* t, int iz, double k, double R) {
     const or_table_params* p = &t->p;
+    ensure_bh(t);
     int i, fl; double w;
     row_pos(k, 2.0, p->gamma_max, p->n_E, &i, &w, &fl);
     const double* base = t->bh_cdf + (int64_t)iz * p->n_E * p->n_s;
