@@ -224,7 +224,11 @@ pe_status pe_destroy_tables(pe_tables* tables);
 
 /* Copy one table to host memory: which = 0 h(eta) [n_eta], 1 NCS CDF
  * [n_eta*n_y], 2 classical CDF [n_y], 3 sigma_Z [n_E] (iz), 4 brems CDF
- * [n_E*n_s] (iz).  *n_out receives the element count; cap too small -> ARG. */
+ * [n_E*n_s] (iz), 5 Bethe-Heitler sigma_BH [n_E] (iz; k log spaced on
+ * [2, gamma_max] m c^2, alpha r_e^2), 6 Bethe-Heitler CDF [n_E*n_s] (iz; over
+ * s with positron fraction x = 1/k + s (1 - 2/k)).  Kinds 5 and 6 build the
+ * pair tables on first use.  *n_out receives the element count; cap too small
+ * -> ARG.                                                                     */
 pe_status pe_tables_export(const pe_tables* tables, int which, int iz, double* host_out,
                            int64_t cap, int64_t* n_out);
 
@@ -289,6 +293,55 @@ pe_status pe_electron_spectrum(pe_run* run, int n_bins, double e_min_mev, double
  * PE_ERR_CUDA.                                                                */
 pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int ne, double e_min_mev,
                         double e_max_mev, void* counts);
+
+/* Bethe-Heitler pair production of emitted photons in the target.  Sec. 2.2
+ * says pair production by photons in the field of the nuclei is implemented
+ * like the bremsstrahlung: a direct MC collision of Eq. (4) with the pair
+ * cross section, here Tsai's DCS of the crossed process with the screening
+ * fits of Eq. (1), clamped at zero, over the positron energy fraction x in
+ * [1/k, 1 - 1/k] (k the photon energy in m c^2; no pairs for k <= 2).
+ *
+ * Each photon record (the 32-byte layout of the photon buffer) moves at c
+ * along its direction from its emission point: at step m (emission step n_e
+ * < m < step_end) it is at p = x_e + k^ (m - n_e) c dt.  At every step with p
+ * in the run's target (the slab; and |y| <= y_half in 2D) it takes the test
+ * P = 1 - exp(-n_i sigma_BH(k) c dt) with one Philox draw of counter
+ * (id_mech, run id, m, 0x40000000 + n_e) under the run's seed: words 0-1
+ * against floor(P 2^64), words 2-3 (53 bits) for x by the inverse CDF.  A
+ * conversion writes one pe_pair (E+ = x k, E- = k - E+, both along k^) and
+ * ends the photon; a photon that has left the target, or is outside it and
+ * moving away, is not followed further.  Photons do not feel the fields, so
+ * following each one after the fact equals stepping it with the electrons.
+ *   run       : the run whose target, step, seed, run id and Z apply
+ *   photons   : device array of n_photons records (for instance the run's own
+ *               photon buffer); 4-byte aligned; read only
+ *   step_end  : first step not taken (-1: the run's steps done so far)
+ *   pairs     : device array of capacity pe_pair records (may be null if
+ *               capacity is 0); written in no particular order
+ *   tally     : device array of PE_PAIR_TALLY_WORDS uint64, cleared by the
+ *               call: the true pair count (it may exceed capacity; the
+ *               excess is not written), photons that entered the target,
+ *               of them above the table's k range (last row used), and
+ *               128-bit fixed-point (lo, hi; 2^-64 m c^2) sums of k and E+
+ *               of the conversions
+ * Asynchronous on the run's stream.  The first call on a table set builds
+ * its pair tables on the host and uploads them (synchronous).
+ * Errors: PE_ERR_ARG (null, n_photons < 0 or >= 2^31, capacity < 0,
+ * misaligned, step_end beyond the run), PE_ERR_NOMEM, PE_ERR_CUDA.             */
+typedef struct {
+    float x, y;               /* conversion point: the photon's position at `step` (y = 0 in 1D) */
+    float e_minus, e_plus;    /* total energies of the electron and the positron, m c^2 */
+    float kx, ky, kz;         /* direction of the converted photon */
+    uint32_t step;            /* step of the conversion */
+    uint32_t photon;          /* index of the photon record */
+    uint32_t id_mech;         /* the photon's id_mech */
+} pe_pair;
+#define PE_PAIR_TALLY_WORDS 8
+enum {
+    PE_PT_N_PAIRS = 0, PE_PT_N_ENTERED = 1, PE_PT_N_K_ABOVE = 2, PE_PT_E_PAIRS = 4, PE_PT_E_POSITRONS = 6
+};
+pe_status pe_pair_transport(pe_run* run, const void* photons, int64_t n_photons, int64_t step_end, void* pairs,
+                            int64_t capacity, void* tally);
 
 /* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */

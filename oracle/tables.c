@@ -265,10 +265,31 @@ static double bh_integrand(double s, const void* vc) {
     return d * c->span;
 }
 
+static double bh_raw_s(const bh_ctx* c, double s) { return or_bh_dcs_raw(c->Z, c->k, c->xmin + s * c->span, 0); }
+
+/* integral of the clamped integrand over [a, b] in s.  The clamp puts a kink where the
+ * DCS changes sign; each side of it is integrated separately.  The DCS is symmetric about
+ * x = 1/2, so the cell is first split there, leaving at most one sign change per part. */
+static double bh_cell(const bh_ctx* c, double a, double b) {
+    double sm = (0.5 - c->xmin) / c->span;
+    if (a < sm && sm < b) return bh_cell(c, a, sm) + bh_cell(c, sm, b);
+    double fa = bh_raw_s(c, a), fb = bh_raw_s(c, b);
+    if ((fa < 0.0) != (fb < 0.0)) {
+        double u = a, v = b;
+        for (int it = 0; it < 200 && v - u > 1e-17 * (1.0 + fabs(u)); ++it) {
+            double m = 0.5 * (u + v);
+            if ((bh_raw_s(c, m) < 0.0) == (fa < 0.0)) u = m; else v = m;
+        }
+        double r = 0.5 * (u + v);
+        return integrate(bh_integrand, c, a, r, 1e-14, 1e-300) + integrate(bh_integrand, c, r, b, 1e-14, 1e-300);
+    }
+    return integrate(bh_integrand, c, a, b, 1e-14, 1e-300);
+}
+
 double or_bh_sigma_direct(double Z, double k) {
     if (!(k > 2.0)) return 0.0;
     bh_ctx c = {Z, k, 1.0 / k, 1.0 - 2.0 / k};
-    return integrate(bh_integrand, &c, 0.0, 1.0, 1e-14, 1e-300);
+    return bh_cell(&c, 0.0, 1.0);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -346,7 +367,7 @@ static void build_bh_row(const or_table_params* p, double Z, double k, double* r
     double cum = 0.0;
     row[0] = 0.0;
     for (int j = 1; j < n; ++j) {
-        cum += integrate(bh_integrand, &c, (double)(j - 1) / (n - 1), (double)j / (n - 1), 1e-14, 1e-300);
+        cum += bh_cell(&c, (double)(j - 1) / (n - 1), (double)j / (n - 1));
         row[j] = cum;
     }
     *sigma = cum;

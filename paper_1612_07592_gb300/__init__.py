@@ -36,9 +36,14 @@ T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4
          E_NCS_STORED=16, E_NCS_BELOW=18, E_BR_STORED=20, E_BR_BELOW=22, E_RECOIL_NCS=24, E_RECOIL_BR=26)
 PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
                          ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
+# Bethe-Heitler pair records (pe_pair) and the pair tally words
+PAIR_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("e_minus", "<f4"), ("e_plus", "<f4"), ("kx", "<f4"),
+                       ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("photon", "<u4"), ("id_mech", "<u4")])
+PAIR_TALLY_WORDS = 8
+PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, E_PAIRS=4, E_POSITRONS=6)
 EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
             "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch", "pe_graph_destroy",
-            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error"]
+            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport"]
 
 
 class PeError(RuntimeError):
@@ -117,13 +122,15 @@ def lib():
                                               C.c_int64, vp]
             L.pe_electron_spectrum.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
             L.pe_photon_map.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, vp]
+            L.pe_pair_transport.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
             L.pe_last_error.restype = C.c_char_p
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
-                         "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map"):
+                         "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map",
+                         "pe_pair_transport"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -246,6 +253,12 @@ def pe_photon_map(run: int, nx: int, x_min_m: float, x_max_m: float, ne: int, e_
                                float(e_max_mev), counts_ptr))
 
 
+def pe_pair_transport(run: int, photons_ptr: int, n_photons: int, step_end: int, pairs_ptr: int, capacity: int,
+                      tally_ptr: int) -> None:
+    _check(lib().pe_pair_transport(run, photons_ptr, int(n_photons), int(step_end), pairs_ptr, int(capacity),
+                                   tally_ptr))
+
+
 def pe_destroy(run: int):
     _check(lib().pe_destroy(run))
 
@@ -365,6 +378,34 @@ class Run:
         out = self.torch.zeros(nx * ne, dtype=self.torch.int64, device=self.x.device)
         pe_photon_map(self.handle, nx, x_min_m, x_max_m, ne, e_min_mev, e_max_mev, out.data_ptr())
         return out.cpu().numpy().view(np.uint64).reshape(nx, ne)
+
+    def pair_transport(self, photons=None, n_photons: int | None = None, step_end: int = -1,
+                       capacity: int | None = None):
+        """Bethe-Heitler conversion, computed on the device, of photon records in this run's target up
+        to step_end (-1: the steps done).  photons: a CUDA uint8/int32 tensor of records or a
+        PHOTON_DTYPE numpy array (copied to the device); default the run's own stored photons.
+        Returns (pairs as PAIR_DTYPE, true pair count, tally words)."""
+        torch = self.torch
+        if photons is None:
+            n = self.tally_out().photons_stored if n_photons is None else n_photons
+        else:
+            n = (len(photons) if isinstance(photons, np.ndarray) else 0) if n_photons is None else n_photons
+        cap = max(int(n), 1) if capacity is None else int(capacity)
+        with torch.cuda.stream(self.stream):
+            if photons is None:
+                dev_ph = self.photons
+            elif isinstance(photons, np.ndarray):
+                host = torch.from_numpy(np.ascontiguousarray(photons).view(np.int32).reshape(-1))
+                dev_ph = host.to(self.x.device)
+            else:
+                dev_ph = photons
+            pairs = torch.zeros(max(cap, 1) * 10, dtype=torch.int32, device=self.x.device)
+            tally = torch.zeros(PAIR_TALLY_WORDS, dtype=torch.int64, device=self.x.device)
+        pe_pair_transport(self.handle, dev_ph.data_ptr(), int(n), step_end, pairs.data_ptr(), cap, tally.data_ptr())
+        self.stream.synchronize()
+        t = tally.cpu().numpy().view(np.uint64)
+        k = int(min(t[PT["N_PAIRS"]], cap))
+        return pairs[: k * 10].cpu().numpy().view(PAIR_DTYPE), int(t[PT["N_PAIRS"]]), t
 
     def wait_words(self) -> np.ndarray:
         """Null-collision waits (uint32, PE_WAIT_NEVER = no further candidate)."""

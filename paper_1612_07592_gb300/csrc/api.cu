@@ -23,6 +23,10 @@ struct pe_tables {
     void* dmem = nullptr;
     void* dmemq = nullptr;    // pair-row tables and guides of the FP32 emission branch
     int device = 0;
+    // Bethe-Heitler tables, built and uploaded by the first call that needs them
+    mutable std::mutex bh_mu;
+    mutable std::vector<double> bh_sigma, bh_cdf;
+    mutable double* bh_dev = nullptr;     // sigma_BH then the CDF, FP64
 };
 
 struct pe_run {
@@ -208,6 +212,8 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
     C.eta_last = p->n_eta - 1;
     C.g_last = p->n_E - 1;
     C.s_step = 1.0 / (p->n_s - 1);
+    C.ln_k_min = std::log(2.0);
+    C.inv_dln_k = p->gamma_max > 2.0 ? (p->n_E - 1) / (std::log(p->gamma_max) - std::log(2.0)) : 0.0;
     const double* cs = &C.eta_min;
     float* cfp = &D.cf.eta_min;
     for (size_t k = 0; k < sizeof(TabC<double>) / sizeof(double); ++k) cfp[k] = (float)cs[k];
@@ -219,9 +225,36 @@ extern "C" pe_status pe_destroy_tables(pe_tables* t) {
     if (!t) return fail(PE_ERR_ARG, "pe_destroy_tables: null");
     if (t->dmem) cudaFree(t->dmem);
     if (t->dmemq) cudaFree(t->dmemq);
+    if (t->bh_dev) cudaFree(t->bh_dev);
     delete t;
     return PE_OK;
 }
+
+namespace {
+// the Bethe-Heitler tables of t on the host and, with upload, on t's device
+pe_status ensure_bh(const pe_tables* t, bool upload) {
+    std::lock_guard<std::mutex> lock(t->bh_mu);
+    if (!(t->host.p.gamma_max > 2.0)) return fail(PE_ERR_ARG, "pair tables: gamma_max must exceed 2");
+    if (t->bh_sigma.empty()) build_host_bh_tables(t->host, t->bh_sigma, t->bh_cdf);
+    if (upload && !t->bh_dev) {
+        const size_t n1 = t->bh_sigma.size(), n2 = t->bh_cdf.size();
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != t->device) cudaSetDevice(t->device);
+        double* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(double) * (n1 + n2));
+        if (e == cudaSuccess) e = cudaMemcpy(d, t->bh_sigma.data(), sizeof(double) * n1, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + n1, t->bh_cdf.data(), sizeof(double) * n2, cudaMemcpyHostToDevice);
+        if (cur != t->device) cudaSetDevice(cur);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            return cuda_fail(e, "pair tables: upload");
+        }
+        t->bh_dev = d;
+    }
+    return PE_OK;
+}
+}  // namespace
 
 extern "C" pe_status pe_tables_export(const pe_tables* t, int which, int iz, double* out, int64_t cap,
                                       int64_t* n_out) {
@@ -230,14 +263,20 @@ extern "C" pe_status pe_tables_export(const pe_tables* t, int which, int iz, dou
     const pe_table_params& p = H.p;
     const double* src = nullptr;
     int64_t n = 0;
-    if ((which == 3 || which == 4) && (iz < 0 || iz >= p.n_Z)) return fail(PE_ERR_ARG, "pe_tables_export: bad iz");
+    if ((which >= 3 && which <= 6) && (iz < 0 || iz >= p.n_Z)) return fail(PE_ERR_ARG, "pe_tables_export: bad iz");
+    if (which == 5 || which == 6) {
+        pe_status st = ensure_bh(t, false);
+        if (st != PE_OK) return st;
+    }
     switch (which) {
         case 0: src = H.h.data(); n = p.n_eta; break;
         case 1: src = H.cdf.data(); n = (int64_t)p.n_eta * p.n_y; break;
         case 2: src = H.cdf.data() + (size_t)p.n_eta * p.n_y; n = p.n_y; break;
         case 3: src = H.sigma.data() + (size_t)iz * p.n_E; n = p.n_E; break;
         case 4: src = H.bcdf.data() + (size_t)iz * p.n_E * p.n_s; n = (int64_t)p.n_E * p.n_s; break;
-        default: return fail(PE_ERR_ARG, "pe_tables_export: which must be 0..4");
+        case 5: src = t->bh_sigma.data() + (size_t)iz * p.n_E; n = p.n_E; break;
+        case 6: src = t->bh_cdf.data() + (size_t)iz * p.n_E * p.n_s; n = (int64_t)p.n_E * p.n_s; break;
+        default: return fail(PE_ERR_ARG, "pe_tables_export: which must be 0..6");
     }
     if (n_out) *n_out = n;
     if (cap < n) return fail(PE_ERR_ARG, "pe_tables_export: output too small");
@@ -636,6 +675,32 @@ extern "C" pe_status pe_photon_map(pe_run* r, int nx, double x_min_m, double x_m
     g_launches++;
     e = cudaGetLastError();
     return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_photon_map");
+}
+
+extern "C" pe_status pe_pair_transport(pe_run* r, const void* photons, int64_t n_photons, int64_t step_end,
+                                        void* pairs, int64_t capacity, void* tally) {
+    if (!r || !tally || (n_photons > 0 && !photons) || (capacity > 0 && !pairs))
+        return fail(PE_ERR_ARG, "pe_pair_transport: null argument");
+    if (n_photons < 0 || n_photons >= (int64_t(1) << 31) || capacity < 0)
+        return fail(PE_ERR_ARG, "pe_pair_transport: n_photons must be in [0, 2^31), capacity >= 0");
+    if ((reinterpret_cast<uintptr_t>(photons) & 3u) || (reinterpret_cast<uintptr_t>(pairs) & 3u) ||
+        (reinterpret_cast<uintptr_t>(tally) & 7u))
+        return fail(PE_ERR_ARG, "pe_pair_transport: misaligned buffer");
+    if (step_end < 0) step_end = r->steps_done;
+    if (step_end > r->steps_done) return fail(PE_ERR_ARG, "pe_pair_transport: step_end beyond the run's steps");
+    pe_status st = ensure_bh(r->tables, true);
+    if (st != PE_OK) return st;
+    cudaError_t e = cudaMemsetAsync(tally, 0, sizeof(unsigned long long) * PE_PAIR_TALLY_WORDS, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_pair_transport");
+    if (n_photons == 0) return PE_OK;
+    TablesDev D = r->tables->dev;
+    D.bhsig64 = r->tables->bh_dev;
+    D.bhcdf64 = r->tables->bh_dev + r->tables->bh_sigma.size();
+    launch_pair_transport(D, r->dev, photons, n_photons, step_end, pairs, capacity,
+                          static_cast<unsigned long long*>(tally), r->stream);
+    g_launches++;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_pair_transport");
 }
 
 extern "C" pe_status pe_destroy(pe_run* r) {

@@ -33,6 +33,7 @@ struct TabC {
     R h_classical;                        // 5 pi / 3
     R eta_last, g_last;                   // n_eta - 1 and n_E - 1 (last row position)
     R s_step;                             // 1 / (n_s - 1)
+    R ln_k_min, inv_dln_k;                // Bethe-Heitler rows: k log spaced on [2, gamma_max]
 };
 
 // Device view of one table set.  f32 and f64 copies of every table.
@@ -55,6 +56,10 @@ struct TablesDev {
     // at u in [m/M, (m+1)/M) lies between the smallest and the largest of them.
     const short4* gq;                           // [n_eta * M_y]
     const short4* bgq;                          // [n_Z * (n_E - 1) * M_s]
+    // Bethe-Heitler pair production (FP64 only; built on the first pair call): sigma_BH [n_Z * n_E]
+    // and the CDF over s [n_Z * n_E * n_s], x = 1/k + s (1 - 2/k), rows k log spaced on [2, gamma_max]
+    const double* bhsig64;
+    const double* bhcdf64;
     int M_y, M_s;                               // guide sizes (powers of two >= n_y, n_s)
     float fM_y, fM_s;
     int n_eta, n_y, n_E, n_s, n_Z;
@@ -154,6 +159,13 @@ struct HostTables {
     double classical_total = 0;
 };
 bool build_host_tables(const pe_table_params& p, HostTables& out, std::string* err);
+// Bethe-Heitler tables of the same parameters: sigma_BH [n_Z * n_E], CDF [n_Z * n_E * n_s]
+void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::vector<double>& cdf);
+
+// kernels_pair.cu: Bethe-Heitler conversion of photon records in the run's target
+void launch_pair_transport(const TablesDev& t, const RunDev& r, const void* photons, int64_t n_photons,
+                           int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally,
+                           cudaStream_t s);
 
 // kernels.cu
 void launch_init(const RunDev& r, int precision, int init_dist, double theta, double beam_u, cudaStream_t s);

@@ -14,12 +14,17 @@
 // photon_min / gamma to y_max = 1 - 1/gamma, and the CDF of sigma(y, E) is
 // tabulated over s with y = y_cut (y_max / y_cut)^s.
 //
+// Bethe-Heitler pair production (Sec. 2.2: implemented like the bremsstrahlung):
+// Tsai's DCS of the crossed process with the same fits, clamped at zero, integrated
+// over the positron fraction x in [1/k, 1 - 1/k]; the CDF is tabulated linearly in x.
+//
 // Numerics (chosen independently of the test oracle): the Bessel integrals
 // K_nu(x) = Int_0^inf exp(-x cosh t) cosh(nu t) dt and Int_x^inf K_{5/3} =
 // Int_0^inf exp(-x cosh t) cosh(5t/3) / cosh t dt are evaluated by the
 // trapezoidal rule, which converges geometrically for these even integrands
 // analytic in |Im t| < pi/2; table cells use composite 8-point Gauss-Legendre
 // on panels refined where the integrand varies fast.
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <thread>
@@ -187,6 +192,87 @@ void brems_row(const pe_table_params& p, const Tsai& ts, double gamma, double* r
     }
 }
 
+// ---- Bethe-Heitler pair production -------------------------------------------
+// Tsai's DCS of the crossed process with the same screening fits: photon k (m c^2),
+// positron fraction x, screening variables 100 / (k x (1-x) Z^{1/3}), 100 / (k x (1-x)
+// Z^{2/3}); d sigma / dx in alpha r_e^2 (unclamped).
+double bh_dcs(const Tsai& ts, double k, double x) {
+    double xx = x * (1.0 - x);
+    double q = 100.0 / (k * xx);
+    double g = q / ts.z13, e = q / ts.z23;
+    double phi1 = 20.863 - 2.0 * std::log(1.0 + 0.55846 * 0.55846 * g * g)
+                  - 4.0 * (1.0 - 0.6 * std::exp(-0.9 * g) - 0.4 * std::exp(-1.5 * g));
+    double dphi = (2.0 / 3.0) / (1.0 + g * (6.5 + 6.0 * g));
+    double psi1 = 28.340 - 2.0 * std::log(1.0 + 3.621 * 3.621 * e * e)
+                  - 4.0 * (1.0 - 0.7 * std::exp(-8.0 * e) - 0.3 * std::exp(-29.2 * e));
+    double dpsi = (2.0 / 3.0) / (1.0 + e * (40.0 + 400.0 * e));
+    return (1.0 - (4.0 / 3.0) * xx) * (ts.Z2 * (phi1 - (4.0 / 3.0) * ts.lnZ - 4.0 * ts.f) + ts.Z * (psi1 - (8.0 / 3.0) * ts.lnZ))
+           - (2.0 / 3.0) * xx * (ts.Z2 * dphi + ts.Z * dpsi);
+}
+
+// integral over s in [a, b] of max(dsigma/dx, 0) * span, x = xmin + s span: breakpoints
+// where x or 1 - x halves (the screening varies with ln x near the ends), and the clamp
+// kink bisected
+double bh_piece(const Tsai& ts, double k, double xmin, double span, double a, double b) {
+    std::vector<double> br{a};
+    for (int e = 1; e < 64; ++e) {
+        const double h = std::ldexp(1.0, -e);
+        for (double xv : {h, 1.0 - h}) {
+            double s = (xv - xmin) / span;
+            if (s > a && s < b) br.push_back(s);
+        }
+        if (h < xmin) break;
+    }
+    br.push_back(b);
+    std::sort(br.begin(), br.end());
+    auto raw = [&](double s) { return bh_dcs(ts, k, xmin + s * span); };
+    auto fn = [&](double s) {
+        double v = raw(s);
+        return v > 0.0 ? v * span : 0.0;
+    };
+    double tot = 0.0;
+    for (size_t q = 0; q + 1 < br.size(); ++q) {
+        double lo = br[q], hi = br[q + 1];
+        if (!(hi > lo)) continue;
+        double flo = raw(lo), fhi = raw(hi);
+        if ((flo < 0.0) != (fhi < 0.0)) {
+            double u = lo, v = hi;
+            for (int it = 0; it < 200 && v - u > 1e-16 * (1.0 + std::fabs(u)); ++it) {
+                double m = 0.5 * (u + v);
+                if ((raw(m) < 0.0) == (flo < 0.0)) u = m; else v = m;
+            }
+            double r = 0.5 * (u + v);
+            tot += gauss8_panels(fn, lo, r, 4) + gauss8_panels(fn, r, hi, 4);
+        } else {
+            tot += gauss8_panels(fn, lo, hi, 4);
+        }
+    }
+    return tot;
+}
+
+void bh_row(const pe_table_params& p, const Tsai& ts, double k, double* row, double* sigma) {
+    int n = p.n_s;
+    if (!(k > 2.0)) {
+        for (int j = 0; j < n; ++j) row[j] = (double)j / (n - 1);
+        *sigma = 0.0;
+        return;
+    }
+    double xmin = 1.0 / k, span = 1.0 - 2.0 / k;
+    double cum = 0.0;
+    row[0] = 0.0;
+    for (int j = 1; j < n; ++j) {
+        cum += bh_piece(ts, k, xmin, span, (double)(j - 1) / (n - 1), (double)j / (n - 1));
+        row[j] = cum;
+    }
+    *sigma = cum;
+    if (cum > 0.0) {
+        for (int j = 0; j < n; ++j) row[j] /= cum;
+        row[n - 1] = 1.0;
+    } else {
+        for (int j = 0; j < n; ++j) row[j] = (double)j / (n - 1);
+    }
+}
+
 template <class F>
 void parallel_for(int n, const F& f) {
     unsigned nt = std::thread::hardware_concurrency();
@@ -237,6 +323,24 @@ bool build_host_tables(const pe_table_params& p, HostTables& out, std::string* e
             return false;
         }
     return true;
+}
+
+}  // namespace pe
+
+namespace pe {
+
+void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::vector<double>& cdf) {
+    const pe_table_params& p = h.p;
+    const int nZ = (int)h.Z.size();
+    sigma.assign((size_t)nZ * p.n_E, 0.0);
+    cdf.assign((size_t)nZ * p.n_E * p.n_s, 0.0);
+    const double l0 = std::log(2.0), l1 = std::log(p.gamma_max);
+    parallel_for(nZ * p.n_E, [&](int b) {
+        int iz = b / p.n_E, i = b % p.n_E;
+        Tsai ts(h.Z[iz]);
+        double k = std::exp(l0 + (l1 - l0) * i / (p.n_E - 1));
+        bh_row(p, ts, k, &cdf[((size_t)iz * p.n_E + i) * p.n_s], &sigma[(size_t)iz * p.n_E + i]);
+    });
 }
 
 }  // namespace pe
