@@ -160,9 +160,14 @@ def main():
     ap.add_argument("--job-steps", type=int, default=0, help="override steps per job (profiling runs only)")
     ap.add_argument("--profile-pic", action="store_true",
                     help="profiling run only: one PE_PIC_1D job (--particles, --job-steps) of the config-2 physics")
+    ap.add_argument("--profile-pairs", action="store_true",
+                    help="profiling run only: the 1 GeV Au bunch (--particles electrons), then two pair transports")
     args = ap.parse_args()
     if args.profile_pic:
         profile_pic(args.particles or 200_000, args.job_steps or 500)
+        return
+    if args.profile_pairs:
+        profile_pairs(args.particles or 100_000)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -310,7 +315,8 @@ def main():
                             "bunch_1gev_au_5mm_1e6": bunch_methods(pe, stream, flush),
                             "bunch_1gev_au_5mm_1e6_dt_T10": bunch_methods(pe, stream, flush, dt_over_T=0.1),
                             "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush),
-                            "pic_1d_au_a270_1e6x2000": pic_job(pe, tables, cfg, stream, flush)}
+                            "pic_1d_au_a270_1e6x2000": pic_job(pe, tables, cfg, stream, flush),
+                            "pairs_bh_bunch_1gev_au_5mm_1e6": bunch_pairs(pe, stream, flush)}
     if rank == 0 and not args.skip_cpu_baseline:
         threads = os.cpu_count() or 1
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
@@ -508,6 +514,64 @@ def bunch_methods(pe, stream, flush, n=1_000_000, dt_over_T=1.0):
     out.update({"unit": UNIT, "electrons": n, "steps": c["steps"], "speedup_null": out["null"]["value"] /
                 out["direct"]["value"], "kernel": "k_step_persistent (FP32, constant fields)"})
     return out
+
+
+def bunch_pairs(pe, stream, flush, n=1_000_000, reps=3):
+    """Bethe-Heitler pair production of the bunch's photons (Sec. 2.2): the 1 GeV Au bunch of
+    1e6 electrons is run once (direct brems test, FP32), then its stored photons are stepped
+    through the rest of the 5 mm target (pe_pair_transport, the Eq. 4 test per step with the
+    pair cross section), timed by CUDA events on the run's stream with L2 flushed in between."""
+    import torch
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.bunch(1000.0, "Au", n=n)
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    with torch.cuda.stream(stream):
+        r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **c["run"]), n, capacity=1 << 25, stream=stream)
+    pe.pe_step([r.handle], c["steps"])
+    stream.synchronize()
+    n_ph = r.tally_out().photons_stored
+    with torch.cuda.stream(stream):
+        pairs = torch.zeros(n_ph * 10, dtype=torch.int32, device="cuda")
+        tally = torch.zeros(pe.PAIR_TALLY_WORDS, dtype=torch.int64, device="cuda")
+    ts = []
+    for k in range(reps + 1):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.pe_pair_transport(r.handle, r.photons.data_ptr(), n_ph, -1, pairs.data_ptr(), n_ph, tally.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ts.append(e0.elapsed_time(e1))
+    t = tally.cpu().numpy().view(np.uint64)
+    ms = float(np.median(ts))
+    r.close()
+    pe.pe_destroy_tables(tables)
+    tests = int(t[pe.PT["N_TESTS"]])
+    return {"value": tests / (ms * 1e-3), "unit": "Eq. 4 pair tests/s", "ms_per_transport": ms, "photons": n_ph,
+            "photons_per_s": n_ph / (ms * 1e-3), "tests": tests, "pairs": int(t[pe.PT["N_PAIRS"]]),
+            "entered": int(t[pe.PT["N_ENTERED"]]), "electrons": n, "steps": c["steps"],
+            "kernel": "k_pair_transport (FP64 positions, one photon per thread)"}
+
+
+def profile_pairs(n):
+    """Profiling run: the 1 GeV Au bunch with n electrons (untimed), then two pair transports of
+    its photons (the second is the one to capture)."""
+    import torch
+    import paper_1612_07592_gb300 as pe
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.bunch(1000.0, "Au", n=n)
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **c["run"]), n, capacity=1 << 24)
+    pe.pe_step([r.handle], c["steps"])
+    out = None
+    for _ in range(2):
+        out = r.pair_transport()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pairs": True, "electrons": n, "photons": int(r.tally_out().photons_stored),
+                      "pairs": out[1], "tests": int(out[2][pe.PT["N_TESTS"]])}))
+    r.close()
 
 
 def reflected(pe, tables, cfg, stream, flush):

@@ -321,9 +321,9 @@ pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int
  *   tally     : device array of PE_PAIR_TALLY_WORDS uint64, cleared by the
  *               call: the true pair count (it may exceed capacity; the
  *               excess is not written), photons that entered the target,
- *               of them above the table's k range (last row used), and
- *               128-bit fixed-point (lo, hi; 2^-64 m c^2) sums of k and E+
- *               of the conversions
+ *               of them above the table's k range (last row used), tests
+ *               taken (one draw each), and 128-bit fixed-point (lo, hi;
+ *               2^-64 m c^2) sums of k and E+ of the conversions
  * Asynchronous on the run's stream.  The first call on a table set builds
  * its pair tables on the host and uploads them (synchronous).
  * Errors: PE_ERR_ARG (null, n_photons < 0 or >= 2^31, capacity < 0,
@@ -338,7 +338,8 @@ typedef struct {
 } pe_pair;
 #define PE_PAIR_TALLY_WORDS 8
 enum {
-    PE_PT_N_PAIRS = 0, PE_PT_N_ENTERED = 1, PE_PT_N_K_ABOVE = 2, PE_PT_E_PAIRS = 4, PE_PT_E_POSITRONS = 6
+    PE_PT_N_PAIRS = 0, PE_PT_N_ENTERED = 1, PE_PT_N_K_ABOVE = 2, PE_PT_N_TESTS = 3, PE_PT_E_PAIRS = 4,
+    PE_PT_E_POSITRONS = 6
 };
 pe_status pe_pair_transport(pe_run* run, const void* photons, int64_t n_photons, int64_t step_end, void* pairs,
                             int64_t capacity, void* tally);

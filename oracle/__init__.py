@@ -38,7 +38,7 @@ PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "
 PAIR_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("e_minus", "<f4"), ("e_plus", "<f4"), ("kx", "<f4"),
                        ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("photon", "<u4"), ("id_mech", "<u4")])
 PAIR_TALLY_WORDS = 8
-PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, E_PAIRS=4, E_POSITRONS=6)
+PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, N_TESTS=3, E_PAIRS=4, E_POSITRONS=6)
 
 
 def build(force: bool = False) -> str:

@@ -202,10 +202,12 @@ typedef struct {
     uint32_t photon;          /* index of the photon record                       */
     uint32_t id_mech;         /* the photon's id_mech                             */
 } or_pair;
-enum { ORP_N_PAIRS = 0, ORP_N_ENTERED = 1, ORP_N_K_ABOVE = 2, ORP_E_PAIRS = 4, ORP_E_POSITRONS = 6, ORP_WORDS = 8 };
+enum { ORP_N_PAIRS = 0, ORP_N_ENTERED = 1, ORP_N_K_ABOVE = 2, ORP_N_TESTS = 3, ORP_E_PAIRS = 4, ORP_E_POSITRONS = 6,
+       ORP_WORDS = 8 };
 /* pairs in photon order to pairs[0..cap); tally (ORP_WORDS, cleared here):
  * pair count (true count), photons that entered the target, of them above the
- * table's k range, and 128-bit fixed-point sums of k and E+ of the conversions. */
+ * table's k range, tests taken (draws), and 128-bit fixed-point sums of k and E+
+ * of the conversions.                                                         */
 int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
                       int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally);
 

@@ -806,6 +806,7 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
             uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
+            tally[ORP_N_TESTS]++;
             if (word64(w[0], w[1]) < thr) {
                 double x = or_sample_bh_x(t, r->iz, k, u53(word64(w[2], w[3])));
                 double ep = x * k;

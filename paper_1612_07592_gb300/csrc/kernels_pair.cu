@@ -6,10 +6,14 @@
 // emission point; at every step inside the target it takes the test, and on a conversion
 // the positron fraction x is drawn from the tabulated CDF of Tsai's pair DCS.
 //
-// One thread per photon (FP64: the arithmetic per step is one position, two compares and
-// the Philox draw); the steps before the photon can reach the target are skipped, then
-// the steps are taken one by one exactly as the definition states them.  Conversions
-// are appended per warp (one atomic per warp and round of photons).
+// Rounds of 32 photons per warp.  Each lane first finds its photon's run of consecutive
+// steps inside the target by binary search on the FP64 position computed exactly as the
+// definition computes it at each step (GB300's FP64 pipe is narrow: the literal per-step
+// position kept it 84 % busy).  Then the warp takes the tests of the round's photons one
+// photon at a time, 32 steps at once (the draws are counter-based, so the first passing
+// step is found from a ballot): the per-step work is a Philox draw and a 64-bit integer
+// compare on every lane, whatever the spread of path lengths.  Conversions are appended
+// per warp (one atomic per warp and round).
 #include "kernels.cuh"
 
 namespace pe {
@@ -53,6 +57,13 @@ __device__ __forceinline__ double bh_sample_x(const TablesDev& t, const double* 
     return 1.0 / k + s * (1.0 - 2.0 / k);
 }
 
+// the photon's coordinate (direction component d, emission coordinate e) at step m, as the
+// definition computes it: e + d ((m - n_e) c dt), one rounding for the step product and one
+// for the fused multiply-add
+__device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, double e, int64_t ne, int64_t m) {
+    return __fma_rn(d, __dmul_rn((double)(m - ne), c.dt), e);
+}
+
 __global__ void __launch_bounds__(256) k_pair_transport(TablesDev t, RunDev r, const Photon* ph, int64_t n_ph,
                                                         int64_t step_end, PairRec* out, int64_t cap,
                                                         unsigned long long* tally) {
@@ -65,67 +76,125 @@ __global__ void __launch_bounds__(256) k_pair_transport(TablesDev t, RunDev r, c
     const bool two_d = r.geometry == PE_GAUSS_2D;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform rounds of photons, so that every lane reaches the append
+    // warp-uniform rounds of 32 photons, so that every lane reaches the shuffles and the append
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_ph; base += stride) {
         const int64_t j = base + lane;
         bool conv = false;
+        unsigned long long tests = 0;
         PairRec q;
+        // lane's photon: the run [a, b] of steps inside the target and the threshold of the test
+        Photon p{};
+        int64_t a = 1, b = 0;
+        uint64_t thr = 0;
+        double k = 0.0;
         if (j < n_ph) {
-            const Photon p = ph[j];
-            const double k = (double)p.e;
+            p = ph[j];
+            k = (double)p.e;
             if (k > 2.0) {
                 const double kx = p.kx, ky = p.ky, xe = p.x, ye = p.y;
                 const int64_t ne = p.step;
                 bool above;
                 const double P = -expm1(-c.K_br * bh_sigma_of(t, sig, k, above));
-                // skip the steps at which the photon is still at least two steps short of
-                // the target along x (no test is taken there)
-                int64_t m = ne + 1;
-                const double vdt = kx * c.dt;
-                const double margin = 1e-9 * (fabs(c.x0) + fabs(c.x1) + 1.0);
-                double q_skip = 0.0;
-                if (vdt > margin && xe < c.x0) q_skip = floor((c.x0 - xe) / vdt);
-                else if (vdt < -margin && xe > c.x1) q_skip = floor((c.x1 - xe) / vdt);
-                q_skip = fmin(q_skip, (double)(step_end - ne));
-                if (q_skip > 2.0) m = ne + (int64_t)q_skip - 1;
-                bool was_in = false;
-                for (; m < step_end; ++m) {
-                    const double tt = __dmul_rn((double)(m - ne), c.dt);
-                    const double px = __fma_rn(kx, tt, xe), py = __fma_rn(ky, tt, ye);
-                    bool in = px >= c.x0 && px <= c.x1;
-                    if (two_d && fabs(py) > c.yh) in = false;
-                    if (!in) {
-                        if (was_in) break;                        // left the target
-                        if ((px < c.x0 && kx <= 0.0) || (px > c.x1 && kx >= 0.0)) break;
-                        if (two_d && fabs(py) > c.yh && py * ky >= 0.0) break;
-                        continue;
+                thr = P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+                // The steps with the photon inside the target form one run [a, b] (its position
+                // is monotone in the step and the target convex): bound it with each face by
+                // binary search on the position exactly as the step computes it, so the tests
+                // run on integers only.
+                a = ne + 1;
+                b = step_end - 1;
+                auto clip = [&](double d, double e, double lo, double hi) {
+                    if (a > b) return;
+                    if (d == 0.0) {
+                        const double v = photon_pos(c, d, e, ne, a);
+                        if (!(v >= lo && v <= hi)) b = a - 1;
+                        return;
                     }
-                    if (!was_in) {
-                        was_in = true;
-                        atomicAdd(&s_t[PE_PT_N_ENTERED], 1ull);
-                        if (above) atomicAdd(&s_t[PE_PT_N_K_ABOVE], 1ull);
+                    // the entry face is reached (d > 0: pos >= lo; d < 0: pos <= hi) ...
+                    auto entered = [&](int64_t m) {
+                        const double v = photon_pos(c, d, e, ne, m);
+                        return d > 0.0 ? v >= lo : v <= hi;
+                    };
+                    // ... and the exit face not yet passed
+                    auto before_exit = [&](int64_t m) {
+                        const double v = photon_pos(c, d, e, ne, m);
+                        return d > 0.0 ? v <= hi : v >= lo;
+                    };
+                    if (!entered(b)) { b = a - 1; return; }
+                    if (!entered(a)) {
+                        int64_t u = a, v = b;              // entered(u) false, entered(v) true
+                        while (v - u > 1) {
+                            const int64_t mid = u + (v - u) / 2;
+                            if (entered(mid)) v = mid; else u = mid;
+                        }
+                        a = v;
                     }
-                    const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)m, kPurBH + (uint32_t)ne),
-                                                  r.seed_lo, r.seed_hi);
-                    if (below_threshold(P, w.x, w.y)) {
-                        const double x = bh_sample_x(t, cdf, k, uni53(w64(w.z, w.w)));
-                        const double ep = x * k;
-                        q.x = (float)px;
-                        q.y = (float)(two_d ? py : 0.0);
-                        q.e_minus = (float)(k - ep);
-                        q.e_plus = (float)ep;
-                        q.kx = p.kx; q.ky = p.ky; q.kz = p.kz;
-                        q.step = (uint32_t)m;
-                        q.photon = (uint32_t)j;
-                        q.id_mech = p.id_mech;
-                        fx_add(&s_t[PE_PT_E_PAIRS], k);
-                        fx_add(&s_t[PE_PT_E_POSITRONS], ep);
-                        conv = true;
-                        break;
+                    if (!before_exit(a)) { b = a - 1; return; }
+                    if (!before_exit(b)) {
+                        int64_t u = a, v = b;              // before_exit(u) true, before_exit(v) false
+                        while (v - u > 1) {
+                            const int64_t mid = u + (v - u) / 2;
+                            if (before_exit(mid)) u = mid; else v = mid;
+                        }
+                        b = u;
                     }
+                };
+                clip(kx, xe, c.x0, c.x1);
+                if (two_d) clip(ky, ye, -c.yh, c.yh);
+                if (a <= b) {
+                    atomicAdd(&s_t[PE_PT_N_ENTERED], 1ull);
+                    if (above) atomicAdd(&s_t[PE_PT_N_K_ABOVE], 1ull);
                 }
             }
         }
+        // The warp takes the tests of each photon of the round in turn, 32 steps at a time
+        // (lane l tests step m0 + l); the conversion is at the first step whose draw passes.
+        for (int src = 0; src < 32; ++src) {
+            const int64_t as = __shfl_sync(0xffffffffu, a, src), bs = __shfl_sync(0xffffffffu, b, src);
+            if (as > bs) continue;
+            const uint32_t idm = __shfl_sync(0xffffffffu, p.id_mech, src);
+            const uint32_t ne = __shfl_sync(0xffffffffu, p.step, src);
+            const uint64_t th = __shfl_sync(0xffffffffu, thr, src);
+            int64_t hit = -1;
+            uint32_t hz = 0, hw = 0;
+            for (int64_t m0 = as; m0 <= bs; m0 += 32) {
+                const int64_t m = m0 + lane;
+                bool ok = false;
+                uint4 w = make_uint4(0, 0, 0, 0);
+                if (m <= bs) {
+                    w = philox4x32_10(make_uint4(idm, r.run_id, (uint32_t)m, kPurBH + ne), r.seed_lo, r.seed_hi);
+                    ok = w64(w.x, w.y) < th;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (bal) {
+                    const int first = __ffs(bal) - 1;
+                    hit = m0 + first;
+                    hz = __shfl_sync(0xffffffffu, w.z, first);
+                    hw = __shfl_sync(0xffffffffu, w.w, first);
+                    break;
+                }
+            }
+            if (lane == src) {
+                tests += (unsigned long long)((hit >= 0 ? hit : bs) - as + 1);
+                if (hit >= 0) {
+                    const double x = bh_sample_x(t, cdf, k, uni53(w64(hz, hw)));
+                    const double ep = x * k;
+                    q.x = (float)photon_pos(c, p.kx, p.x, p.step, hit);
+                    q.y = (float)(two_d ? photon_pos(c, p.ky, p.y, p.step, hit) : 0.0);
+                    q.e_minus = (float)(k - ep);
+                    q.e_plus = (float)ep;
+                    q.kx = p.kx; q.ky = p.ky; q.kz = p.kz;
+                    q.step = (uint32_t)hit;
+                    q.photon = (uint32_t)j;
+                    q.id_mech = p.id_mech;
+                    fx_add(&s_t[PE_PT_E_PAIRS], k);
+                    fx_add(&s_t[PE_PT_E_POSITRONS], ep);
+                    conv = true;
+                }
+            }
+        }
+        // tests of the warp's round, one shared atomic per warp
+        for (int o = 16; o > 0; o >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, o);
+        if (lane == 0 && tests) atomicAdd(&s_t[PE_PT_N_TESTS], tests);
         const unsigned mask = __ballot_sync(0xffffffffu, conv);
         if (mask) {
             const int leader = __ffs(mask) - 1;
@@ -142,6 +211,7 @@ __global__ void __launch_bounds__(256) k_pair_transport(TablesDev t, RunDev r, c
     if (threadIdx.x == 0) {
         if (s_t[PE_PT_N_ENTERED]) atomicAdd(tally + PE_PT_N_ENTERED, s_t[PE_PT_N_ENTERED]);
         if (s_t[PE_PT_N_K_ABOVE]) atomicAdd(tally + PE_PT_N_K_ABOVE, s_t[PE_PT_N_K_ABOVE]);
+        if (s_t[PE_PT_N_TESTS]) atomicAdd(tally + PE_PT_N_TESTS, s_t[PE_PT_N_TESTS]);
         for (int k = PE_PT_E_PAIRS; k <= PE_PT_E_POSITRONS; k += 2) {
             unsigned long long lo = s_t[k], hi = s_t[k + 1];
             if (lo || hi) {

@@ -44,7 +44,7 @@ def _oracle_pairs(ot, d, photons, step_end):
 
 def _compare(dev, dev_n, dev_t, orc, orc_n, orc_t):
     assert dev_n == orc_n
-    for k in ("N_PAIRS", "N_ENTERED", "N_K_ABOVE"):
+    for k in ("N_PAIRS", "N_ENTERED", "N_K_ABOVE", "N_TESTS"):
         assert int(dev_t[pe.PT[k]]) == int(orc_t[O.PT[k]]), k
     for k in ("E_PAIRS", "E_POSITRONS"):
         a, b = pe.fixed_to_float(dev_t, pe.PT[k]), O.fixed_to_float(orc_t, O.PT[k])
