@@ -552,7 +552,7 @@ def bunch_pairs(pe, stream, flush, n=1_000_000, reps=3):
     return {"value": tests / (ms * 1e-3), "unit": "Eq. 4 pair tests/s", "ms_per_transport": ms, "photons": n_ph,
             "photons_per_s": n_ph / (ms * 1e-3), "tests": tests, "pairs": int(t[pe.PT["N_PAIRS"]]),
             "entered": int(t[pe.PT["N_ENTERED"]]), "electrons": n, "steps": c["steps"],
-            "kernel": "k_pair_transport (FP64 positions, one photon per thread)"}
+            "kernel": "k_pair_transport (warp-cooperative tests, integer Philox per step)"}
 
 
 def profile_pairs(n):

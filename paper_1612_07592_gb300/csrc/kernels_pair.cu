@@ -64,7 +64,11 @@ __device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, d
     return __fma_rn(d, __dmul_rn((double)(m - ne), c.dt), e);
 }
 
-__global__ void __launch_bounds__(256) k_pair_transport(TablesDev t, RunDev r, const Photon* ph, int64_t n_ph,
+#ifndef PE_PAIR_MIN_CTAS_SM
+#define PE_PAIR_MIN_CTAS_SM 3      // resident CTAs of 256 threads per SM the registers are sized for
+#endif
+
+__global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(TablesDev t, RunDev r, const Photon* ph, int64_t n_ph,
                                                         int64_t step_end, PairRec* out, int64_t cap,
                                                         unsigned long long* tally) {
     __shared__ unsigned long long s_t[PE_PAIR_TALLY_WORDS];
