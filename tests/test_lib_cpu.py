@@ -42,14 +42,16 @@ def test_header_symbols_exported(libpath):
 def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pe.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pe_table_params),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pe_table_params),'
                     ' sizeof(pe_run_params), sizeof(pe_buffers), sizeof(pe_launch_config), sizeof(pe_tally_out),'
-                    ' offsetof(pe_run_params, seed), offsetof(pe_tally_out, live_particle_steps));return 0;}\n')
+                    ' offsetof(pe_run_params, seed), offsetof(pe_tally_out, live_particle_steps), sizeof(pe_pair),'
+                    ' offsetof(pe_pair, step));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
     want = [C.sizeof(pe.TableParams), C.sizeof(pe.RunParams), C.sizeof(pe.Buffers), C.sizeof(pe.LaunchConfig),
-            C.sizeof(pe.TallyOut), pe.RunParams.seed.offset, pe.TallyOut.live_particle_steps.offset]
+            C.sizeof(pe.TallyOut), pe.RunParams.seed.offset, pe.TallyOut.live_particle_steps.offset,
+            pe.PAIR_DTYPE.itemsize, pe.PAIR_DTYPE.fields["step"][1]]
     assert got == want
 
 
