@@ -35,27 +35,53 @@ __device__ __forceinline__ void acc_add(unsigned long long* a, long long v) {
     if (v) atomicAdd(a, (unsigned long long)v);
 }
 
+// Shared-memory current sums as two 32-bit words per grid word (32-bit shared atomics
+// run about four times faster than 64-bit ones on GB300): a contribution v (|v| <= 2^36)
+// adds v >> 16 (|.| <= 2^20) to the high word and v & 0xffff to the low word, so
+// v = hi 2^16 + lo exactly.  Up to kFlushTiles tiles of 256 electrons (each adds at
+// most once per word per electron) the high sums stay below 2^31 in magnitude and the
+// low sums below 2^32; the CTA then moves them into the run's 64-bit sums.
+constexpr int kFlushTiles = 7;
+struct SplitSums {
+    unsigned int* hi;   // [3 n_cells], two's complement
+    unsigned int* lo;   // [3 n_cells]
+};
+__device__ __forceinline__ void acc_add(const SplitSums& a, int k, long long v) {
+    if (v) {
+        atomicAdd(a.hi + k, (unsigned int)(int)(v >> 16));
+        atomicAdd(a.lo + k, (unsigned int)(v & 0xffff));
+    }
+}
+__device__ __forceinline__ void flush_split(const SplitSums& a, int nj, unsigned long long* acc) {
+    for (int k = threadIdx.x; k < nj; k += blockDim.x) {
+        const long long v = (long long)(int)a.hi[k] * 65536 + (long long)a.lo[k];
+        if (v) atomicAdd(acc + k, (unsigned long long)v);
+        a.hi[k] = 0;
+        a.lo[k] = 0;
+    }
+}
+
 // current of one electron moving from x_old to x_new (|x_new - x_old| < dx) with
 // velocity (vy, vz): J_x at half nodes from the change of its node weights
 // (cumulative, charge conserving); J_y, J_z at half nodes with the mean of its
 // half-node weights at the two positions.  Dimensionless sums; the field kernel
 // applies the weight and the charge sign.
 template <typename R>
-__device__ __forceinline__ void pic_deposit(R dx, int n, R x_old, R x_new, R vy, R vz, unsigned long long* sj) {
+__device__ __forceinline__ void pic_deposit(R dx, int n, R x_old, R x_new, R vy, R vz, const SplitSums& sj) {
     const R so = x_old / dx, sn = x_new / dx;
     const int ia = (int)floor(so < sn ? so : sn);
     R cum = 0;
 #pragma unroll
     for (int k = ia; k <= ia + 1; ++k) {
         cum += lin_w<R>(sn, k, (R)0) - lin_w<R>(so, k, (R)0);
-        if (k >= 0 && k < n) acc_add(sj + k, fxq(cum));
+        if (k >= 0 && k < n) acc_add(sj, k, fxq(cum));
     }
 #pragma unroll
     for (int k = ia - 1; k <= ia + 1; ++k) {
         const R sbar = (R)0.5 * (lin_w<R>(so, k, (R)0.5) + lin_w<R>(sn, k, (R)0.5));
         if (sbar > (R)0 && k >= 0 && k < n) {
-            acc_add(sj + n + k, fxq(vy * sbar));
-            acc_add(sj + 2 * n + k, fxq(vz * sbar));
+            acc_add(sj, n + k, fxq(vy * sbar));
+            acc_add(sj, 2 * n + k, fxq(vz * sbar));
         }
     }
 }
@@ -65,7 +91,8 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
-    unsigned long long* s_j = s_tally + PE_TALLY_WORDS;             // 3 n_cells current sums
+    unsigned long long* s_j = s_tally + PE_TALLY_WORDS;             // 3 n_cells current sums (split)
+    const SplitSums sj{reinterpret_cast<unsigned int*>(s_j), reinterpret_cast<unsigned int*>(s_j) + 3 * r.n_cells};
     R* s_h = reinterpret_cast<R*>(s_j + 3 * r.n_cells);
     R* s_sig = s_h + t.n_eta;
     const R* g_h = (sizeof(R) == 4) ? (const R*)t.h32 : (const R*)t.h64;
@@ -79,7 +106,15 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
     const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
     const uint32_t step = (uint32_t)r.step0;
     const R nf = (R)step;
+    int tiles = 0;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < r.n; base += (int64_t)gridDim.x * blockDim.x) {
+        if (tiles == kFlushTiles) {                     // keep the split sums in range
+            __syncthreads();
+            flush_split(sj, nj, r.jacc);
+            __syncthreads();
+            tiles = 0;
+        }
+        ++tiles;
         const int64_t i = base + threadIdx.x;
         bool active = i < r.n;
         Particle<R> P;
@@ -94,7 +129,7 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
             step_one<R, FK_PIC>(t, r, s_h, sig_z, (uint32_t)i, step, nf, P, out, s_hist, s_tally);
             const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
             const R x_new = P.x + P.x_lo;
-            pic_deposit<R>(r.c.dt, r.n_cells, x_old, x_new, P.u[1] / gamma, P.u[2] / gamma, s_j);
+            pic_deposit<R>(r.c.dt, r.n_cells, x_old, x_new, P.u[1] / gamma, P.u[2] / gamma, sj);
             if (x_new < (R)0 || x_new > r.c.box1) {   // it left through a boundary face, carrying its charge out
                 P.x = (R)NAN;
                 atomicAdd(s_tally + PE_T_N_KILLED, 1ull);
@@ -108,10 +143,7 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nj; k += blockDim.x) {
-        const unsigned long long v = s_j[k];
-        if (v) atomicAdd(r.jacc + k, v);
-    }
+    flush_split(sj, nj, r.jacc);
     flush_shared<R>(s_hist, s_tally, r);
 }
 
