@@ -594,7 +594,7 @@ def reflected(pe, tables, cfg, stream, flush):
 def pic_job(pe, tables, cfg, stream, flush, n=1_000_000, n_cells=1000, steps=2000):
     """The config-2 physics with self-consistent fields (1D PIC around the step): 1e6 electrons in
     a 1 um Au 51+ slab at 50 n_c, the a0 = 270 pulse injected at x = 0 of a 10 um grid (1000 cells),
-    2000 steps; FP32.  Two launches per step (particles with current deposit, field solve)."""
+    2000 steps; FP32.  One launch per step (particles with current deposit; the last CTA advances the fields)."""
     import torch
     run = dict(cfg["run"], run_id=13, geometry=pe.PE_PIC_1D, n_cells=n_cells)
     with torch.cuda.stream(stream):
@@ -608,7 +608,7 @@ def pic_job(pe, tables, cfg, stream, flush, n=1_000_000, n_cells=1000, steps=200
             "n_cells": n_cells, "steps": steps, "us_per_step": 1e3 * ms / steps,
             "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]), "killed": int(t.tally[pe.T["N_KILLED"]]),
             "max_Ex": float(np.abs(ex).max()),
-            "kernels": "k_pic_particles + k_pic_fields (FP32), one launch each per step"}
+            "kernels": "k_pic_particles (FP32; deposit, then the field update by the last CTA), one launch per step"}
 
 
 def profile_pic(n, steps):

@@ -358,8 +358,9 @@ double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);
  * PIC state by n_steps steps from step index step0 with the same kernels and
  * results as pe_step on a run made by pe_init_particles with the same
  * parameters and buffers, but it sums the currents in a fixed array compiled
- * into the library (3 x PE_PIC_MAX_CELLS x 8 bytes = 96 KiB, held on every GPU
- * that loads the library until the process exits).  It calls no cudaMalloc or
+ * into the library ((3 x PE_PIC_MAX_CELLS + 1) x 8 bytes = 96 KiB + 8 bytes: the
+ * sums and the count of CTAs done with a step, held on every GPU that loads
+ * the library until the process exits).  It calls no cudaMalloc or
  * cudaFree and no routine that allocates.
  *   tables, params, n and buffers describe the run as for pe_init_particles
  *   (params->geometry = PE_PIC_1D); the caller owns every buffer, which must

@@ -425,14 +425,15 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     if (rp->geometry == PE_PIC_1D && n > 0) {
         // zero fields, the ion charge of the neutral start, cleared current sums
         const size_t rs = rp->precision == PE_F32 ? 4 : 8;
-        e = cudaMalloc(&r->jacc, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells);
+        // 3 n_cells current sums and one word that counts the CTAs done with a step
+        e = cudaMalloc(&r->jacc, sizeof(unsigned long long) * (3 * (size_t)rp->n_cells + 1));
         if (e != cudaSuccess) {
             r->jacc = nullptr;
             delete r;
             return fail(PE_ERR_NOMEM, std::string("pe_init_particles: PIC current sums: ") + cudaGetErrorString(e));
         }
         d.jacc = static_cast<unsigned long long*>(r->jacc);
-        e = cudaMemsetAsync(r->jacc, 0, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells, r->stream);
+        e = cudaMemsetAsync(r->jacc, 0, sizeof(unsigned long long) * (3 * (size_t)rp->n_cells + 1), r->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->grid, 0, rs * (size_t)PE_PIC_GRID_WORDS(rp->n_cells), r->stream);
         if (e == cudaSuccess) {
             launch_pic_rho(d, rp->precision, r->stream);
@@ -571,7 +572,7 @@ extern "C" pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps
             for (int64_t k = 0; k < n_steps; ++k) {
                 d.step0 = r->steps_done + k;
                 launch_pic_step(t->dev, d, prec, sms, s);
-                g_launches += 2;
+                g_launches += 1;
             }
         }
         cudaError_t e = cudaGetLastError();
@@ -805,10 +806,11 @@ extern "C" pe_status pe_graph_destroy(pe_graph* g) {
 // ---------------------------------------------------------------------------
 // PIC steps that allocate nothing (pe_pic_step_noalloc)
 // ---------------------------------------------------------------------------
-// The current sums of one PIC step live in this fixed array instead of memory
-// that pe_init_particles allocates: 3 x PE_PIC_MAX_CELLS x 8 bytes = 96 KiB, held
-// on every GPU that loads the library until the process exits.  All calls share it.
-static __device__ __align__(256) unsigned long long g_pic_scratch[3 * PE_PIC_MAX_CELLS];
+// The current sums of one PIC step and the count of CTAs done with it live in this
+// fixed array instead of memory that pe_init_particles allocates: (3 x
+// PE_PIC_MAX_CELLS + 1) x 8 bytes = 96 KiB + 8 bytes, held on every GPU that loads the
+// library until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned long long g_pic_scratch[3 * PE_PIC_MAX_CELLS + 1];
 
 namespace {
 
@@ -933,7 +935,7 @@ extern "C" pe_status pe_pic_step_noalloc(const pe_tables* t, const pe_run_params
     d.jacc = static_cast<unsigned long long*>(scratch);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the array keeps what the last call left: the current sums must start at zero
-    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * 3 * (size_t)rp->n_cells, s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (3 * (size_t)rp->n_cells + 1), s);
     if (e != cudaSuccess) return cuda_fail(e, "pe_pic_step_noalloc: clearing the scratch array");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -941,7 +943,7 @@ extern "C" pe_status pe_pic_step_noalloc(const pe_tables* t, const pe_run_params
     for (int64_t k = 0; k < n_steps; ++k) {
         d.step0 = step0 + k;
         launch_pic_step(t->dev, d, rp->precision, sms, s);
-        g_launches += 2;
+        g_launches += 1;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pe_pic_step_noalloc: PIC step");

@@ -6,10 +6,12 @@
 //                   by charge-conserving linear weighting, summed per CTA in
 //                   shared memory and once per CTA into the run's accumulator;
 //                   an electron that left [0, L] is removed after its deposit.
-//  k_pic_fields     one CTA: E_x -= dt J_x at the half nodes; the wave variants
+//                   The last CTA to finish (a count after the sums) then advances
+//                   the grid: E_x -= dt J_x at the half nodes; the wave variants
 //                   F+- = E_y +- B_z and G+- = E_z -+ B_y carried one cell along
 //                   +-x with the current at the path's midpoint; the laser enters
-//                   at x = 0; the accumulator is cleared for the next step.
+//                   at x = 0; the sums and the count are cleared for the next step.
+//                   One launch per step.
 //  k_pic_rho        ion charge of the neutral start (the electrons' initial
 //                   charge with the opposite sign), a diagnostic of Gauss's law.
 //
@@ -86,6 +88,62 @@ __device__ __forceinline__ void pic_deposit(R dx, int n, R x_old, R x_new, R vy,
     }
 }
 
+// The field update of one step by one CTA of any size: E_x -= dt J_x at the half nodes;
+// F+ and G+ carried one cell along +x, F- and G- along -x, each with the current at the
+// midpoint of its path; the laser enters at x = 0; the current sums are cleared.  Each
+// thread updates one contiguous run of nodes in place (descending for the +x variants,
+// ascending for the -x ones) after keeping the one value it needs from the neighbouring
+// run.  The sums are read at L2 (they were built there by atomics).
+template <typename R, bool kCP>
+__device__ void pic_fields_block(const RunDevT<R>& r) {
+    const int n = r.n_cells;
+    const StepC<R>& c = r.c;
+    R* ex = static_cast<R*>(r.grid);
+    R* fp = ex + n;
+    R* fm = fp + n + 1;
+    R* gp = fm + n + 1;
+    R* gm = gp + n + 1;
+    unsigned long long* jx = r.jacc;
+    unsigned long long* jy = jx + n;
+    unsigned long long* jz = jy + n;
+    const R dt = c.dt;
+    const R kx = c.pic_kx, kyz = c.pic_kyz;   // J_x = kx sum, J_y,z = kyz sum (charge sign included)
+    auto J = [](const unsigned long long* a, int i) { return (R)(long long)__ldcg(a + i); };
+    const int chunk = (n + 1 + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * chunk, i1 = min(i0 + chunk, n + 1) - 1;   // this thread's nodes [i0, i1]
+    R fp_in = 0, gp_in = 0, fm_in = 0, gm_in = 0;
+    if (i0 <= i1) {
+        if (i0 >= 1) { fp_in = fp[i0 - 1]; gp_in = gp[i0 - 1]; }
+        if (i1 < n) { fm_in = fm[i1 + 1]; gm_in = gm[i1 + 1]; }
+    }
+    __syncthreads();
+    if (i0 <= i1) {
+        for (int i = i1; i >= i0; --i) {            // along +x from node i - 1 through half node i - 1
+            const R f = i == i0 ? fp_in : fp[i - 1];
+            const R g = i == i0 ? gp_in : gp[i - 1];
+            fp[i] = i > 0 ? f - dt * kyz * J(jy, i - 1) : (R)0;
+            gp[i] = i > 0 ? g - dt * kyz * J(jz, i - 1) : (R)0;
+        }
+        for (int i = i0; i <= i1; ++i) {            // along -x from node i + 1 through half node i
+            const R f = i == i1 ? fm_in : fm[i + 1];
+            const R g = i == i1 ? gm_in : gm[i + 1];
+            fm[i] = i < n ? f - dt * kyz * J(jy, i) : (R)0;
+            gm[i] = i < n ? g - dt * kyz * J(jz, i) : (R)0;
+        }
+        for (int i = i0; i <= i1 && i < n; ++i) ex[i] -= dt * kx * J(jx, i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) jx[i] = 0;
+    if (threadIdx.x == 0) {
+        // the laser enters at x = 0: F+ = 2 g_y, G+ = 2 g_z at t^{n+1}
+        R gy, gz;
+        const R nf1 = (R)(r.step0 + 1);
+        plane_e<R, kCP>(c, phase(c, nf1, (R)0, (R)0), gy, gz);
+        fp[0] = (R)2 * gy;
+        gp[0] = (R)2 * gz;
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R> r) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -145,65 +203,23 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
     __syncthreads();
     flush_split(sj, nj, r.jacc);
     flush_shared<R>(s_hist, s_tally, r);
+    // the last CTA to finish (its sums and every other CTA's are in the run's sums) advances
+    // the fields; the count word after the sums goes back to zero for the next step
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    unsigned int* done = reinterpret_cast<unsigned int*>(r.jacc + 3 * r.n_cells);
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (r.polarisation == PE_CP) pic_fields_block<R, true>(r);
+        else pic_fields_block<R, false>(r);
+        if (threadIdx.x == 0) *done = 0;
+    }
 }
 
 constexpr int kFieldThreads = 1024;
-constexpr int kNodesPerThread = (PE_PIC_MAX_CELLS + 1 + kFieldThreads - 1) / kFieldThreads;
-
-template <typename R, bool kCP>
-__global__ void __launch_bounds__(kFieldThreads) k_pic_fields(RunDevT<R> r) {
-    const int n = r.n_cells;
-    const StepC<R>& c = r.c;
-    R* ex = static_cast<R*>(r.grid);
-    R* fp = ex + n;
-    R* fm = fp + n + 1;
-    R* gp = fm + n + 1;
-    R* gm = gp + n + 1;
-    unsigned long long* jx = r.jacc;
-    unsigned long long* jy = jx + n;
-    unsigned long long* jz = jy + n;
-    const R dt = c.dt;
-    // J_x = (w/dt) sum (the electron charge -1 included), J_y,z = -(w/dx) sum
-    const R kx = c.pic_kx, kyz = c.pic_kyz;
-    // read the carried values and the midpoint currents of this thread's nodes
-    R nfp[kNodesPerThread], nfm[kNodesPerThread], ngp[kNodesPerThread], ngm[kNodesPerThread];
-#pragma unroll
-    for (int q = 0; q < kNodesPerThread; ++q) {
-        const int i = threadIdx.x + q * kFieldThreads;
-        nfp[q] = nfm[q] = ngp[q] = ngm[q] = 0;
-        if (i > 0 && i <= n) {                       // along +x from node i - 1 through half node i - 1
-            nfp[q] = fp[i - 1] - dt * kyz * (R)(long long)jy[i - 1];
-            ngp[q] = gp[i - 1] - dt * kyz * (R)(long long)jz[i - 1];
-        }
-        if (i < n) {                                 // along -x from node i + 1 through half node i
-            nfm[q] = fm[i + 1] - dt * kyz * (R)(long long)jy[i];
-            ngm[q] = gm[i + 1] - dt * kyz * (R)(long long)jz[i];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kNodesPerThread; ++q) {
-        const int i = threadIdx.x + q * kFieldThreads;
-        if (i < n) {
-            ex[i] -= dt * kx * (R)(long long)jx[i];
-            jx[i] = jy[i] = jz[i] = 0;
-        }
-        if (i <= n) {
-            fp[i] = nfp[q];
-            fm[i] = nfm[q];
-            gp[i] = ngp[q];
-            gm[i] = ngm[q];
-        }
-    }
-    if (threadIdx.x == 0) {
-        // the laser enters at x = 0: F+ = 2 g_y, G+ = 2 g_z at t^{n+1}
-        R gy, gz;
-        const R nf1 = (R)(r.step0 + 1);
-        plane_e<R, kCP>(c, phase(c, nf1, (R)0, (R)0), gy, gz);
-        fp[0] = (R)2 * gy;
-        gp[0] = (R)2 * gz;
-    }
-}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_pic_rho_deposit(RunDevT<R> r) {
@@ -245,8 +261,6 @@ static void pic_step(const TablesDev& t, const RunDevT<R>& r, int sms, cudaStrea
     const int64_t blocks = (r.n + 255) / 256;
     const int grid = (int)(blocks < 4 * (int64_t)sms ? (blocks > 0 ? blocks : 1) : 4 * (int64_t)sms);
     k_pic_particles<R><<<grid, 256, smem, s>>>(t, r);
-    if (r.polarisation == PE_CP) k_pic_fields<R, true><<<1, kFieldThreads, 0, s>>>(r);
-    else k_pic_fields<R, false><<<1, kFieldThreads, 0, s>>>(r);
 }
 
 void launch_pic_step(const TablesDev& t, const RunDev& r, int precision, int sms, cudaStream_t s) {
