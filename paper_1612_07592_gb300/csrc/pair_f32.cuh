@@ -61,28 +61,17 @@ __device__ __forceinline__ void ramp_sincos2(float2 v, float2& s_out, float2& c_
     c_out = mul2(r, sub2(cd, sd));
 }
 
-// sine and cosine (Cody-Waite reduction by pi/2, Taylor series), paired
+// sine and cosine of the carrier phase, paired: Cody-Waite reduction (1980) by 2 pi with a
+// two-part constant to |r| <= pi, then the hardware sine and cosine (absolute error below
+// 2^-21.4 on [-pi, pi]; 20 instructions per pair fewer than the polynomial form)
 __device__ __forceinline__ void sincos2(float2 v, float2& s_out, float2& c_out) {
     const float kMagic = 0x1.8p23f;
-    float2 t = fma2(v, P2(0.636619772367581343f), P2(kMagic));
-    int qx = __float_as_int(t.x), qy = __float_as_int(t.y);
-    float2 k = sub2(t, P2(kMagic));
-    float2 r = fma2(neg2(k), P2(1.57079637050628662f), v);
-    r = fma2(neg2(k), P2(-4.37113900018624283e-8f), r);
-    float2 r2 = mul2(r, r);
-    float2 sp = fma2(r2, P2(2.75573192e-6f), P2(-1.98412698e-4f));
-    sp = fma2(r2, sp, P2(8.33333333e-3f));
-    sp = fma2(r2, sp, P2(-1.66666667e-1f));
-    float2 sn = fma2(mul2(r, r2), sp, r);
-    float2 cp = fma2(r2, P2(-2.75573192e-7f), P2(2.48015873e-5f));
-    cp = fma2(r2, cp, P2(-1.38888889e-3f));
-    cp = fma2(r2, cp, P2(4.16666667e-2f));
-    cp = fma2(r2, cp, P2(-0.5f));
-    float2 cs = fma2(r2, cp, P2(1.0f));
-    float2 a = sel2(qx & 1, qy & 1, cs, sn);
-    float2 b = sel2(qx & 1, qy & 1, sn, cs);
-    s_out = sel2(qx & 2, qy & 2, neg2(a), a);
-    c_out = sel2((qx + 1) & 2, (qy + 1) & 2, neg2(b), b);
+    const float2 t = fma2(v, P2(0.159154943091895336f), P2(kMagic));    // 2 pi k + ..., k = rint(v / 2 pi)
+    const float2 k = sub2(t, P2(kMagic));
+    float2 r = fma2(neg2(k), P2(6.28318548202514648f), v);              // 2 pi, nearest float
+    r = fma2(neg2(k), P2(-1.74845553e-7f), r);                          // 2 pi - its nearest float
+    s_out = make_float2(__sinf(r.x), __sinf(r.y));
+    c_out = make_float2(__cosf(r.x), __cosf(r.y));
 }
 
 // two electrons; per-electron activity, optical-depth pairs and event fingerprints
