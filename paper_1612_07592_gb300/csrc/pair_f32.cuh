@@ -43,22 +43,10 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
     e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
-// ramp sine/cosine of the envelope (Taylor series about pi/4), paired
+// ramp sine/cosine of the envelope (0 <= v <= pi/2), paired: the hardware units
 __device__ __forceinline__ void ramp_sincos2(float2 v, float2& s_out, float2& c_out) {
-    float2 d = sub2(v, P2(0.785398163397448310f));
-    float2 d2 = mul2(d, d);
-    float2 sp = fma2(d2, P2(2.75573192e-6f), P2(-1.98412698e-4f));
-    sp = fma2(d2, sp, P2(8.33333333e-3f));
-    sp = fma2(d2, sp, P2(-1.66666667e-1f));
-    float2 sd = fma2(mul2(d, d2), sp, d);
-    float2 cp = fma2(d2, P2(-2.75573192e-7f), P2(2.48015873e-5f));
-    cp = fma2(d2, cp, P2(-1.38888889e-3f));
-    cp = fma2(d2, cp, P2(4.16666667e-2f));
-    cp = fma2(d2, cp, P2(-0.5f));
-    float2 cd = fma2(d2, cp, P2(1.0f));
-    const float2 r = P2(0.707106781186547524f);
-    s_out = mul2(r, add2(cd, sd));
-    c_out = mul2(r, sub2(cd, sd));
+    s_out = make_float2(__sinf(v.x), __sinf(v.y));
+    c_out = make_float2(__cosf(v.x), __cosf(v.y));
 }
 
 // sine and cosine of the carrier phase, paired: Cody-Waite reduction (1980) by 2 pi with a

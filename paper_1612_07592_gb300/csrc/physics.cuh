@@ -25,53 +25,24 @@ __device__ __forceinline__ float m_expm1(float v) { return expm1f(v); }
 __device__ __forceinline__ double m_expm1(double v) { return expm1(v); }
 __device__ __forceinline__ float m_atan(float v) { return atanf(v); }
 __device__ __forceinline__ double m_atan(double v) { return atan(v); }
-// Single-precision sine and cosine without int/float conversion instructions:
-// Cody-Waite reduction by pi/2 (quadrant by magic-number rounding, two-part
-// constant with fused multiply-adds), then the Taylor series of sin and cos on
-// [-pi/4, pi/4] (truncation error below 2e-10, so the result is accurate to a
-// few float ulps).  Valid for |v| < 2^22.
+// Single-precision sine and cosine: Cody-Waite reduction (1980) by 2 pi with a
+// two-part constant to |r| <= pi (the multiple by magic-number rounding, no int/float
+// conversion), then the hardware sine and cosine (absolute error below 2^-21.4 on
+// [-pi, pi]).  Valid for |v| < 2^24.
 __device__ __forceinline__ void m_sincos(float v, float* s_out, float* c_out) {
     const float kMagic = 0x1.8p23f;                       // 1.5 * 2^23
-    float t = fmaf(v, 0.636619772367581343f, kMagic);     // v * 2/pi rounded to an integer
-    int q = __float_as_int(t);                            // quadrant in the low bits
-    float k = t - kMagic;
-    float r = fmaf(-k, 1.57079637050628662f, v);          // pi/2 = 1.5707963705... + (-4.37e-8)
-    r = fmaf(-k, -4.37113900018624283e-8f, r);
-    float r2 = r * r;
-    float sp = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);  //  1/9!, -1/7!
-    sp = fmaf(r2, sp, 8.33333333e-3f);                      //  1/5!
-    sp = fmaf(r2, sp, -1.66666667e-1f);                     // -1/3!
-    float sn = fmaf(r * r2, sp, r);
-    float cp = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);  // -1/10!, 1/8!
-    cp = fmaf(r2, cp, -1.38888889e-3f);                     // -1/6!
-    cp = fmaf(r2, cp, 4.16666667e-2f);                      //  1/4!
-    cp = fmaf(r2, cp, -0.5f);                               // -1/2!
-    float cs = fmaf(r2, cp, 1.0f);
-    // rotate by the quadrant: (sin, cos) of v = rotation of (sn, cs) by q * pi/2
-    float a = (q & 1) ? cs : sn;
-    float b = (q & 1) ? sn : cs;
-    *s_out = (q & 2) ? -a : a;
-    *c_out = ((q + 1) & 2) ? -b : b;
+    const float k = fmaf(v, 0.159154943091895336f, kMagic) - kMagic;   // rint(v / 2 pi)
+    float r = fmaf(-k, 6.28318548202514648f, v);          // 2 pi, nearest float
+    r = fmaf(-k, -1.74845553e-7f, r);                     // 2 pi - its nearest float
+    *s_out = __sinf(r);
+    *c_out = __cosf(r);
 }
 __device__ __forceinline__ void m_sincos(double v, double* s, double* c) { sincos(v, s, c); }
 
-// sin and cos of 0 <= v <= pi/2 (the envelope ramps) by their Taylor series about
-// pi/4 in the offset d = v - pi/4, |d| <= pi/4: no range reduction needed
+// sin and cos of 0 <= v <= pi/2 (the envelope ramps): the hardware units, no reduction
 __device__ __forceinline__ void ramp_sincos(float v, float* s_out, float* c_out) {
-    float d = v - 0.785398163397448310f;
-    float d2 = d * d;
-    float sp = fmaf(d2, 2.75573192e-6f, -1.98412698e-4f);
-    sp = fmaf(d2, sp, 8.33333333e-3f);
-    sp = fmaf(d2, sp, -1.66666667e-1f);
-    float sd = fmaf(d * d2, sp, d);                       // sin d
-    float cp = fmaf(d2, -2.75573192e-7f, 2.48015873e-5f);
-    cp = fmaf(d2, cp, -1.38888889e-3f);
-    cp = fmaf(d2, cp, 4.16666667e-2f);
-    cp = fmaf(d2, cp, -0.5f);
-    float cd = fmaf(d2, cp, 1.0f);                        // cos d
-    const float r = 0.707106781186547524f;                // sin(pi/4) = cos(pi/4)
-    *s_out = r * (cd + sd);
-    *c_out = r * (cd - sd);
+    *s_out = __sinf(v);
+    *c_out = __cosf(v);
 }
 __device__ __forceinline__ void ramp_sincos(double v, double* s, double* c) { sincos(v, s, c); }
 __device__ __forceinline__ float m_atan2(float a, float b) { return atan2f(a, b); }
