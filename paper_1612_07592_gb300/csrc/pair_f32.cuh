@@ -101,19 +101,18 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     const float2 nf2 = P2(nf);
     float2 phi = fma2(nf2, P2(c.dt_lo), sub2(mul2(nf2, P2(c.dt_hi)), Q.x));
     phi = sub2(phi, Q.x_lo);
-    const bool upx = phi.x < c.phi_r, upy = phi.y < c.phi_r;
-    float2 arg = sel2(upx, upy, mul2(P2(c.k_env), phi),
-                      sub2(P2(1.57079632679489662f), mul2(P2(c.k_env), sub2(sub2(phi, P2(c.phi_r)), P2(c.phi_f)))));
-    arg = clamp2(arg, 0.0f, 1.57079632679489662f);
+    // envelope g = sin^2(k psi), psi the phase distance to the nearer end of the pulse, k psi
+    // clamped to [0, pi/2] (0 outside the pulse, pi/2 on the flat top); dg/dphi = +-k sin(2 k psi),
+    // + before the middle of the pulse and - after it (it vanishes on the flat top and outside)
+    const float2 rem = sub2(P2(2.0f * c.phi_r + c.phi_f), phi);
+    const float2 psi = make_float2(fminf(phi.x, rem.x), fminf(phi.y, rem.y));
+    const float2 arg = clamp2(mul2(P2(c.k_env), psi), 0.0f, 1.57079632679489662f);
     float2 rs, rc;
     ramp_sincos2(arg, rs, rc);
-    const float2 two_sc = mul2(mul2(P2(2.0f), rs), rc);
-    const bool flx = !upx && phi.x <= c.phi_r + c.phi_f, fly = !upy && phi.y <= c.phi_r + c.phi_f;
-    const bool oux = !(phi.x > 0.0f) || phi.x >= 2.0f * c.phi_r + c.phi_f;
-    const bool ouy = !(phi.y > 0.0f) || phi.y >= 2.0f * c.phi_r + c.phi_f;
-    float2 g = sel2(oux, ouy, P2(0.0f), sel2(flx, fly, P2(1.0f), mul2(rs, rs)));
-    float2 kts = mul2(P2(c.k_env), two_sc);
-    float2 dg = sel2(oux || flx, ouy || fly, P2(0.0f), sel2(upx, upy, kts, neg2(kts)));
+    const float2 g = mul2(rs, rs);
+    const float2 kts = mul2(P2(2.0f * c.k_env), mul2(rs, rc));
+    const float2 side = sub2(rem, phi);
+    const float2 dg = make_float2(copysignf(kts.x, side.x), copysignf(kts.y, side.y));
     float2 st, ct;
     sincos2(phi, st, ct);
     const float2 ma0 = P2(-c.a0);
