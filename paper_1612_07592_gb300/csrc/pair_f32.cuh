@@ -26,7 +26,7 @@ __device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f
 __device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 __device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
-__device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__logf(a.x), __logf(a.y)); }
+__device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__log2f(a.x), __log2f(a.y)); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
     return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
 }
@@ -93,7 +93,7 @@ template <int G>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
                                           bool st_ncs[2], Photon pn[2], bool st_br[2], Photon pb[2],
-                                          unsigned long long* hist, unsigned long long* tally) {
+                                          unsigned long long* hist, unsigned long long* tally, uint32_t& n_above) {
     const StepC<float>& c = r.c;
     const TabC<float>& tc = t.cf;
     const float2 dt = P2(c.dt), h = P2(0.5f * c.dt);
@@ -149,22 +149,19 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, div2(up, add2(gamma, Q.u0)), sub2(gamma, Q.u0));
         float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
         float2 eta = mul2(mul2(gm, Emag), P2(c.inv_ES));
-        // h(eta): row interpolation in log eta, classical limit below the table
-        float2 tp = mul2(sub2(log2v(eta), P2(tc.ln_eta_min)), P2(tc.inv_dln_eta));
-        const bool abx = tp.x >= tc.eta_last, aby = tp.y >= tc.eta_last;
-        float2 tpc = clamp2(tp, 0.0f, tc.eta_last);
-        float2 tt = add2(sub2(tpc, P2(0.5f)), P2(0x1.8p23f));
-        int ix = __float_as_int(tt.x) - 0x4B400000, iy = __float_as_int(tt.y) - 0x4B400000;
-        float2 w = sub2(tpc, sub2(tt, P2(0x1.8p23f)));
-        const bool topx = ix > t.n_eta - 2, topy = iy > t.n_eta - 2;
-        ix = topx ? t.n_eta - 2 : ix;
-        iy = topy ? t.n_eta - 2 : iy;
-        w = sel2(topx, topy, P2(1.0f), w);
-        float2 h0 = make_float2(h_tab[ix], h_tab[iy]), h1 = make_float2(h_tab[ix + 1], h_tab[iy + 1]);
-        float2 hv = add2(mul2(sub2(P2(1.0f), w), h0), mul2(w, h1));
+        // h(eta): row interpolation in log eta (log2 scaled to the row position by one FMA), the
+        // classical limit below the table; above it the last row, counted (the position is clamped
+        // just below the top node, so the split needs no correction there)
+        const float2 tp = fma2(log2v(eta), P2(tc.inv_dln_eta * 0.693147180559945309f),
+                               P2(-tc.ln_eta_min * tc.inv_dln_eta));
+        n_above += (uint32_t)(Q.act[0] && tp.x >= tc.eta_last) + (uint32_t)(Q.act[1] && tp.y >= tc.eta_last);
+        const float2 tpc = clamp2(tp, 0.0f, tc.eta_last - 0x1.0p-10f);
+        const float2 tt = add2(sub2(tpc, P2(0.5f)), P2(0x1.8p23f));
+        const int ix = __float_as_int(tt.x) - 0x4B400000, iy = __float_as_int(tt.y) - 0x4B400000;
+        const float2 w = sub2(tpc, sub2(tt, P2(0x1.8p23f)));
+        const float2 h0 = make_float2(h_tab[ix], h_tab[iy]), h1 = make_float2(h_tab[ix + 1], h_tab[iy + 1]);
+        float2 hv = fma2(w, sub2(h1, h0), h0);
         hv = sel2(eta.x >= tc.eta_min, eta.y >= tc.eta_min, hv, P2(tc.h_classical));
-        if (Q.act[0] && abx) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
-        if (Q.act[1] && aby) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // tau -= ncs_coef (eta / gamma) h(eta), compensated
         float2 dtau = mul2(mul2(P2(c.ncs_coef), mul2(eta, inv_g)), hv);
         float2 s, e;
@@ -248,11 +245,13 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
     const uint32_t id[2] = {(uint32_t)i0, (uint32_t)i1};
     const uint32_t n0 = (uint32_t)r.step0;
     float nf = (float)n0;
+    uint32_t n_above = 0;                               // particle-steps with eta above the table
     for (int s = 0; s < steps; ++s, nf += 1.0f) {
         bool st_ncs[2] = {false, false}, st_br[2] = {false, false};
         Photon pn[2], pb[2];
         if (Q.act[0] || Q.act[1]) {
-            step_pair<G>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally);
+            step_pair<G>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally,
+                         n_above);
             if (r.box_enable) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -270,6 +269,7 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
             warp_append(r, st_br[1], pb[1]);
         }
     }
+    if (n_above) atomicAdd(s_tally + PE_T_N_ETA_ABOVE, (unsigned long long)n_above);
 }
 
 __device__ __forceinline__ void pair_clear(Pair& Q) {
