@@ -118,20 +118,17 @@ __device__ __forceinline__ void envelope(const StepC<R>& c, R phi, R& g, R& dg) 
 }
 
 // Float version without branches (lanes of a warp sit in different parts of the
-// pulse): one ramp sine/cosine serves both ramps, the falling ramp through
-// cos^2(k q) = sin^2(pi/2 - k q), and selects pick the region.
+// pulse): g = sin^2(k psi) with psi the phase distance to the nearer end of the pulse,
+// k psi clamped to [0, pi/2] (0 outside, pi/2 on the flat top; the falling ramp
+// through cos^2(k q) = sin^2(pi/2 - k q)); dg/dphi = +-k sin(2 k psi), + before the
+// middle of the pulse and - after it.
 __device__ __forceinline__ void envelope_sel(const StepC<float>& c, float phi, float& g, float& dg) {
-    const float pr = c.phi_r, pf = c.phi_f, k = c.k_env;
-    const bool up = phi < pr;
-    float arg = up ? k * phi : 1.57079632679489662f - k * (phi - pr - pf);
-    arg = fminf(fmaxf(arg, 0.0f), 1.57079632679489662f);
+    const float rem = (2.0f * c.phi_r + c.phi_f) - phi;
+    const float arg = fminf(fmaxf(c.k_env * fminf(phi, rem), 0.0f), 1.57079632679489662f);
     float s, cc;
     ramp_sincos(arg, &s, &cc);
-    const float two_s_c = 2.0f * s * cc;
-    const bool flat = !up && phi <= pr + pf;
-    const bool out = !(phi > 0.0f) || phi >= 2.0f * pr + pf;
-    g = out ? 0.0f : (flat ? 1.0f : s * s);
-    dg = (out || flat) ? 0.0f : (up ? k * two_s_c : -k * two_s_c);
+    g = s * s;
+    dg = copysignf(2.0f * c.k_env * s * cc, rem - phi);
 }
 
 // phase t^n - x with t^n = n dt.  In float, n * dt_hi is exact (dt_hi has 11
@@ -374,17 +371,16 @@ template <typename R>
 __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int& flag) {
     const TabC<R>& c = tabc<R>(t);
     if constexpr (sizeof(R) == 4) {
-        // clamps and selects instead of branches; flag = 1 above the table
-        float tp = (m_log(eta) - c.ln_eta_min) * c.inv_dln_eta;
+        // clamps and selects instead of branches; flag = 1 above the table.  The row position
+        // comes from log2 by one FMA and is clamped just below the top node, so the split
+        // needs no correction there (above the table: the last row).
+        const float tp = fmaf(__log2f(eta), c.inv_dln_eta * 0.693147180559945309f, -c.ln_eta_min * c.inv_dln_eta);
         flag = tp >= c.eta_last ? 1 : 0;
-        float tpc = fminf(fmaxf(tp, 0.0f), c.eta_last);
+        const float tpc = fminf(fmaxf(tp, 0.0f), c.eta_last - 0x1.0p-10f);
         int i;
         float w;
         split_pos(tpc, i, w);
-        const bool top = i > t.n_eta - 2;
-        i = top ? t.n_eta - 2 : i;
-        w = top ? 1.0f : w;
-        float v = (1.0f - w) * h[i] + w * h[i + 1];
+        const float v = fmaf(w, h[i + 1] - h[i], h[i]);
         return (eta >= c.eta_min) ? v : c.h_classical;
     } else {
         if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
