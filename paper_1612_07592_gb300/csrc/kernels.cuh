@@ -321,7 +321,23 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
     R E[3], B[3];
     fields<R, G>(r, P.x, P.x_lo, P.y, nf, E, B);
     boris<R>(P.u, E, B, dt);
-    R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    // gamma; in FP32 also 1/gamma from one reciprocal square root (v / gamma below becomes
+    // v * (1/gamma); an emission refreshes it)
+    R gamma, inv_g = 0;
+    if constexpr (sizeof(R) == 4) {
+        const float g2 = 1.0f + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2];
+        inv_g = rsqrtf(g2);
+        gamma = g2 * inv_g;
+    } else {
+        gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+    }
+    auto over_gamma = [&](R v) -> R {
+        if constexpr (sizeof(R) == 4) return v * inv_g;
+        else return v / gamma;
+    };
+    auto refresh = [&]() {
+        if constexpr (sizeof(R) == 4) inv_g = 1.0f / gamma;
+    };
     const R xn = P.x, yn = P.y;
 
     if (r.enable_ncs) {
@@ -330,27 +346,34 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         R h = h_of_eta<R>(t, h_tab, eta, fl);
         if (fl == 1) atomicAdd(tally + PE_T_N_ETA_ABOVE, 1ull);
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
-        tau_sub(P, c.ncs_coef * (eta / gamma) * h);
-        if (tau_crossed(P))
+        tau_sub(P, c.ncs_coef * over_gamma(eta) * h);
+        if (tau_crossed(P)) {
             take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, out.ncs, out.pn);
+            refresh();
+        }
     }
 
     if (r.enable_brems) {
         bool in_slab = (xn >= c.x0 && xn <= c.x1);
         if ((G == FK_GAUSS_LP || G == FK_GAUSS_CP) && fabs(yn) > c.yh) in_slab = false;
         if (r.brems_method == PE_BREMS_NULL) {
-            if (P.wait == 0u)
+            if (P.wait == 0u) {
+                const R g_before = gamma;
                 take(brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, hist, tally), P, gamma, out.br,
                      out.pb);
-            else if (P.wait != PE_WAIT_NEVER)
+                if (gamma != g_before) refresh();
+            } else if (P.wait != PE_WAIT_NEVER) {
                 --P.wait;
+            }
         } else if (in_slab && gamma > (R)1 + photon_min) {
+            const R g_before = gamma;
             brems_collide<R>(t, r, sig_tab, id, n, P, gamma, xn, yn, out.br, out.pb, hist, tally);
+            if (gamma != g_before) refresh();
         }
     }
 
-    advance(P.x, P.x_lo, dt * P.u[0] / gamma);
-    if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) advance(P.y, P.y_lo, dt * P.u[1] / gamma);
+    advance(P.x, P.x_lo, over_gamma(dt * P.u[0]));
+    if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) advance(P.y, P.y_lo, over_gamma(dt * P.u[1]));
     box_check<R>(r, P, n, tally);
 }
 

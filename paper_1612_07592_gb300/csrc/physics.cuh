@@ -309,7 +309,9 @@ template <typename R>
 __device__ __forceinline__ void boris(R u[3], const R E[3], const R B[3], R dt) {
     const R h = (R)0.5 * dt;
     R um0 = u[0] - h * E[0], um1 = u[1] - h * E[1], um2 = u[2] - h * E[2];
-    R ig = (R)1 / m_sqrt((R)1 + um0 * um0 + um1 * um1 + um2 * um2);
+    R ig;                                           // 1/gamma at the half step
+    if constexpr (sizeof(R) == 4) ig = rsqrtf(1.0f + um0 * um0 + um1 * um1 + um2 * um2);
+    else ig = (R)1 / m_sqrt((R)1 + um0 * um0 + um1 * um1 + um2 * um2);
     R t0 = -h * B[0] * ig, t1 = -h * B[1] * ig, t2 = -h * B[2] * ig;
     R f = (R)2 / ((R)1 + t0 * t0 + t1 * t1 + t2 * t2);
     R s0 = f * t0, s1 = f * t1, s2 = f * t2;
