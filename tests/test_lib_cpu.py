@@ -81,6 +81,9 @@ def test_argument_errors_are_reported(libpath):
     assert e.value.status == pe.PE_ERR_ARG
     assert pe.pe_a0_from_intensity(1e21) == pytest.approx(0.855 * 1000 ** 0.5)
     assert pe.pe_a0_from_intensity(1e24) == pytest.approx(855.0, rel=1e-3)
+    with pytest.raises(pe.PeError) as e:                 # pair transport without a run
+        pe.pe_pair_transport(0, 0, 1, -1, 0, 0, 0)
+    assert e.value.status == pe.PE_ERR_ARG
 
 
 def test_workloads():
@@ -93,3 +96,10 @@ def test_workloads():
     arr = [q["arrival_s"] for q in c5["requests"]]
     assert np.all(np.diff(arr) > 0)
     assert W.config2()["n"] == 1_000_000 and W.config3()["n"] == 30_000_000
+    ph = W.synthetic_photons(2000, 1, (0.0, 10.0), (1.0, 1e4), (0, 100), theta_max=0.3, y_half=2.0)
+    assert ph.dtype.itemsize == 32 and len(ph) == 2000
+    k = np.sqrt(ph["kx"].astype(np.float64) ** 2 + ph["ky"] ** 2 + ph["kz"] ** 2)
+    assert np.abs(k - 1).max() < 1e-6
+    assert 0.05 < np.mean(ph["kx"] < 0) < 0.15 and np.all(np.abs(ph["kx"]) >= np.cos(0.3) - 1e-6)
+    assert ph["energy"].min() >= 1.0 and ph["energy"].max() <= 1e4 and np.all(np.abs(ph["y"]) <= 2.0)
+    assert len(np.unique(ph["id_mech"] & 0x7FFFFFFF)) == 2000
