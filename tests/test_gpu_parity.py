@@ -444,7 +444,65 @@ def test_config2_full_size_sampled():
     r.close()
 
 
+def test_config3_full_size_sampled():
+    """Config 3 at full size (3e7 electrons, 2D Gaussian focus, CP a0 = 855, 2000 steps) in the
+    benchmark's launch shape; 128 sampled electrons advanced one by one by the oracle.  The 2D
+    case is well resolved at dt = T/100: every electron whose events match is within F32_RTOL."""
+    c = W.config3()
+    Z = c["Z"]
+    lt, ot = tables(c["tables"], Z)
+    r, out = run_gpu(lt, c["run"], c["n"], c["steps"], pe.PE_F32, capacity=1 << 22)
+    ids = np.random.default_rng(3).choice(c["n"], 128, replace=False)
+    st = r.state()[ids]
+    ev = r.event_words()[ids]
+    r.close()
+    st_o, _, _, _, _, ev_o = run_oracle(ot, c["run"], Z, ids, c["steps"])
+    match = ev == ev_o
+    scale = np.maximum(np.abs(st_o[:, 2:5]).max(1), c["run"]["a0"])
+    err = (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale)[match]
+    err_x = (np.abs(st[:, 0:2] - st_o[:, 0:2]).max(1) / np.maximum(np.abs(st_o[:, 0:2]).max(1), 1.0))[match]
+    print(f"config 3 full size: event match {match.mean():.4f}, max {err.max():.2e}, x {err_x.max():.2e}")
+    assert match.mean() > 0.95
+    assert err.max() < F32_RTOL and err_x.max() < F32_RTOL
+
+
+def test_config4_full_size_sampled():
+    """Config 4 at full size (64 runs, 2.05e7 electrons, 1000 steps) advanced by one CUDA graph of
+    batched launches; four sampled electrons per run advanced one by one by the oracle.  The
+    batch spans a0 = 27..855 in 1D at dt = T/100, so the FP32 bound is the distributional one."""
+    c = W.config4()
+    Z = c["Z"]
+    lt, ot = tables(c["tables"], Z)
+    runs = [pe.Run(lt, pe.run_params(precision=pe.PE_F32, **rk), int(n), capacity=int(min(2 * n, 1 << 23)),
+                   events=True) for rk, n in zip(c["runs"], c["n"])]
+    g = pe.pe_graph_create([r.handle for r in runs], c["steps"], block=256, ctas_per_sm=15, steps_per_launch=500)
+    pe.pe_graph_launch(g)
+    pe.pe_graph_destroy(g)
+    rng = np.random.default_rng(4)
+    errs, matches = [], []
+    for rk, n, r in zip(c["runs"], c["n"], runs):
+        ids = rng.choice(int(n), 4, replace=False)
+        st = r.state()[ids]
+        ev = r.event_words()[ids]
+        st_o, _, _, _, _, ev_o = run_oracle(ot, rk, Z, ids, c["steps"])
+        m = ev == ev_o
+        scale = np.maximum(np.abs(st_o[:, 2:5]).max(1), rk["a0"])
+        errs.append((np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale)[m])
+        matches.append(m)
+        r.close()
+    err = np.concatenate(errs)
+    match = np.concatenate(matches)
+    print(f"config 4 full size: event match {match.mean():.4f}, median {np.median(err):.2e}, "
+          f"within {F32_RTOL:g}: {np.mean(err < F32_RTOL):.3f}, p95 {np.quantile(err, 0.95):.2e}, max {err.max():.2e}")
+    assert match.mean() > 0.9
+    assert np.median(err) < F32_RTOL
+    assert np.mean(err < F32_RTOL) > F32_FRAC_WITHIN
+    assert np.quantile(err, 0.95) < F32_ILL_P95
+    assert err.max() < F32_ILL_MAX
+
+
 # ------------------------------------------------------- graph, autotune ----
+
 def test_graph_equals_direct_steps():
     Z = (13.0, 79.0)
     lt, _ = tables(_tp(48), Z)
