@@ -246,6 +246,19 @@ pe_status pe_tables_export(const pe_tables* tables, int which, int iz, double* h
 pe_status pe_init_particles(const pe_tables* tables, const pe_run_params* params, int64_t n,
                             const pe_buffers* buffers, void* cuda_stream, pe_run** out);
 
+/* Resume a run from a checkpoint: the caller's buffers (the same layout as for
+ * pe_init_particles) already hold the state a run reached after step0 steps --
+ * positions, momenta, optical depths, null-collision waits, event words,
+ * photons, histograms, tallies and, for PE_PIC_1D, the grid -- for instance
+ * copied to the host and back.  Nothing is drawn or cleared; the run's step
+ * index is step0, so the next pe_step continues exactly where the checkpointed
+ * run stopped (the draws are keyed on the step) and the results equal those of
+ * the uninterrupted run bit for bit.  params and n must be those of the run that
+ * was checkpointed.  A library extension for long jobs (the paper has no
+ * counterpart).  Errors: as pe_init_particles, and step0 outside [0, 2^32).    */
+pe_status pe_resume_particles(const pe_tables* tables, const pe_run_params* params, int64_t n,
+                              const pe_buffers* buffers, int64_t step0, void* cuda_stream, pe_run** out);
+
 /* Advance runs by n_steps.  n_runs == 1: PE_F64 runs use the plain kernel
  * (one launch per step); PE_F32 runs use the persistent kernel.  n_runs > 1
  * (<= PE_MAX_BATCH): all runs must be PE_F32 and share the first run's

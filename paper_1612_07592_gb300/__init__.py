@@ -43,7 +43,7 @@ PAIR_TALLY_WORDS = 8
 PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, N_TESTS=3, E_PAIRS=4, E_POSITRONS=6)
 EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
             "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch", "pe_graph_destroy",
-            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport"]
+            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport", "pe_resume_particles"]
 
 
 class PeError(RuntimeError):
@@ -123,6 +123,8 @@ def lib():
             L.pe_electron_spectrum.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
             L.pe_photon_map.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, vp]
             L.pe_pair_transport.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
+            L.pe_resume_particles.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), C.c_int64, vp,
+                                              C.POINTER(vp)]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
@@ -130,7 +132,7 @@ def lib():
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
                          "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map",
-                         "pe_pair_transport"):
+                         "pe_pair_transport", "pe_resume_particles"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -197,6 +199,12 @@ def run_params(**kw) -> RunParams:
 def pe_init_particles(tables: int, params: RunParams, n: int, buffers: Buffers, stream: int) -> int:
     h = C.c_void_p()
     _check(lib().pe_init_particles(tables, C.byref(params), n, C.byref(buffers), stream, C.byref(h)))
+    return h.value
+
+
+def pe_resume_particles(tables: int, params: RunParams, n: int, buffers: Buffers, step0: int, stream: int) -> int:
+    h = C.c_void_p()
+    _check(lib().pe_resume_particles(tables, C.byref(params), n, C.byref(buffers), int(step0), stream, C.byref(h)))
     return h.value
 
 
@@ -276,7 +284,7 @@ class Run:
     """One run with caller-owned buffers allocated as torch CUDA tensors."""
 
     def __init__(self, tables: int, params: RunParams, n: int, capacity: int = 1 << 20, stream=None,
-                 device="cuda", events: bool = False):
+                 device="cuda", events: bool = False, _resume_step: int | None = None, _arrays=None):
         import torch
         self.torch = torch
         dt = torch.float32 if params.precision == PE_F32 else torch.float64
@@ -303,7 +311,51 @@ class Run:
                      if params.geometry == PE_PIC_1D else None)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self.params = params
-        self.handle = pe_init_particles(tables, params, self.n, self._buffers(), self.stream.cuda_stream)
+        if _resume_step is None:
+            self.handle = pe_init_particles(tables, params, self.n, self._buffers(), self.stream.cuda_stream)
+        else:
+            with torch.cuda.stream(self.stream):
+                for name, arr in _arrays.items():
+                    dst = getattr(self, name)
+                    src = torch.from_numpy(np.ascontiguousarray(arr)).view(dst.dtype).reshape(-1)
+                    dst[: src.numel()].copy_(src.to(dev))
+            self.handle = pe_resume_particles(tables, params, self.n, self._buffers(), _resume_step,
+                                              self.stream.cuda_stream)
+
+    # ------------------------------------------------------------ checkpoint ----
+    def checkpoint(self) -> dict:
+        """Host copy of everything the run's next steps depend on: the state arrays, the stored
+        photons, histograms, tallies, event and wait words, the PIC grid, and the step index."""
+        out = self.tally_out()
+        arrays = {}
+        for name in ("x", "y", "ux", "uy", "uz", "tau", "hist", "tally", "events", "wait", "grid"):
+            t = getattr(self, name)
+            if t is not None:
+                arrays[name] = t.cpu().numpy().copy()
+        arrays["photons"] = self.photons[: out.photons_stored * 8].cpu().numpy().copy()
+        return {"step": int(out.steps_done), "n": self.n, "capacity": self.capacity,
+                "events": self.events is not None, "arrays": arrays}
+
+    @classmethod
+    def resume(cls, tables: int, params: RunParams, ckpt: dict, stream=None, device="cuda"):
+        """A run continuing from a checkpoint (pe_resume_particles): the next pe_step gives the
+        results the checkpointed run would have given."""
+        return cls(tables, params, ckpt["n"], capacity=ckpt["capacity"], stream=stream, device=device,
+                   events=ckpt["events"], _resume_step=ckpt["step"], _arrays=ckpt["arrays"])
+
+    def save(self, path: str):
+        """Write a checkpoint to an .npz file."""
+        c = self.checkpoint()
+        np.savez(path, _step=c["step"], _n=c["n"], _capacity=c["capacity"], _events=c["events"], **c["arrays"])
+
+    @classmethod
+    def load(cls, tables: int, params: RunParams, path: str, stream=None, device="cuda"):
+        """Resume from an .npz checkpoint written by save()."""
+        z = np.load(path)
+        arrays = {k: z[k] for k in z.files if not k.startswith("_")}
+        ckpt = {"step": int(z["_step"]), "n": int(z["_n"]), "capacity": int(z["_capacity"]),
+                "events": bool(z["_events"]), "arrays": arrays}
+        return cls.resume(tables, params, ckpt, stream=stream, device=device)
 
     def _buffers(self) -> Buffers:
         return Buffers(self.x.data_ptr(), self.y.data_ptr(), self.ux.data_ptr(), self.uy.data_ptr(),

@@ -284,10 +284,14 @@ extern "C" pe_status pe_tables_export(const pe_tables* t, int which, int iz, dou
     return PE_OK;
 }
 
-extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* rp, int64_t n,
-                                       const pe_buffers* b, void* stream, pe_run** out) {
+// A run on the caller's buffers.  resume = false: a new run (initial state drawn unless
+// PE_CALLER, histograms, tallies and events cleared, PIC grid set up).  resume = true: the
+// buffers already hold the state of step `step0` (a checkpoint) and are taken as they are.
+static pe_status make_run(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, void* stream,
+                          bool resume, int64_t step0, pe_run** out) {
     if (!t || !rp || !b || !out) return fail(PE_ERR_ARG, "pe_init_particles: null argument");
     *out = nullptr;
+    if (step0 < 0 || step0 >= (int64_t(1) << 32)) return fail(PE_ERR_ARG, "pe_resume_particles: step0 out of range");
     if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_init_particles: n must be in [0, 2^31)");
     if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_init_particles: precision");
     if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_PIC_1D) return fail(PE_ERR_ARG, "pe_init_particles: geometry");
@@ -404,16 +408,20 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
     d.seed_hi = (uint32_t)(rp->seed >> 32);
 
-    cudaError_t e = cudaMemsetAsync(b->hist, 0, sizeof(uint64_t) * PE_HIST_WORDS, r->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->tally, 0, sizeof(uint64_t) * PE_TALLY_WORDS, r->stream);
-    if (e == cudaSuccess && b->events && n > 0) e = cudaMemsetAsync(b->events, 0, sizeof(uint64_t) * n, r->stream);
+    r->steps_done = step0;
+    cudaError_t e = cudaSuccess;
+    if (!resume) {
+        e = cudaMemsetAsync(b->hist, 0, sizeof(uint64_t) * PE_HIST_WORDS, r->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->tally, 0, sizeof(uint64_t) * PE_TALLY_WORDS, r->stream);
+        if (e == cudaSuccess && b->events && n > 0) e = cudaMemsetAsync(b->events, 0, sizeof(uint64_t) * n, r->stream);
+    }
     if (e != cudaSuccess) {
         delete r;
         return cuda_fail(e, "pe_init_particles: cudaMemsetAsync");
     }
     double theta = rp->T_mev / kMec2MeV;
     double beam_u = rp->init_dist == PE_BEAM ? std::sqrt(rp->beam_gamma * rp->beam_gamma - 1.0) : 0.0;
-    if (n > 0) {
+    if (n > 0 && !resume) {
         launch_init(d, rp->precision, rp->init_dist, theta, beam_u, r->stream);
         g_launches++;
         e = cudaGetLastError();
@@ -434,8 +442,9 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
         }
         d.jacc = static_cast<unsigned long long*>(r->jacc);
         e = cudaMemsetAsync(r->jacc, 0, sizeof(unsigned long long) * (3 * (size_t)rp->n_cells + 1), r->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->grid, 0, rs * (size_t)PE_PIC_GRID_WORDS(rp->n_cells), r->stream);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && !resume)
+            e = cudaMemsetAsync(b->grid, 0, rs * (size_t)PE_PIC_GRID_WORDS(rp->n_cells), r->stream);
+        if (e == cudaSuccess && !resume) {
             launch_pic_rho(d, rp->precision, r->stream);
             g_launches += 2;
             e = cudaGetLastError();
@@ -447,6 +456,16 @@ extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* 
     }
     *out = r;
     return PE_OK;
+}
+
+extern "C" pe_status pe_init_particles(const pe_tables* t, const pe_run_params* rp, int64_t n,
+                                       const pe_buffers* b, void* stream, pe_run** out) {
+    return make_run(t, rp, n, b, stream, false, 0, out);
+}
+
+extern "C" pe_status pe_resume_particles(const pe_tables* t, const pe_run_params* rp, int64_t n,
+                                         const pe_buffers* b, int64_t step0, void* stream, pe_run** out) {
+    return make_run(t, rp, n, b, stream, true, step0, out);
 }
 
 // One persistent launch of a step call: the runs of one field kind, one chunk of
