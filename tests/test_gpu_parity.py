@@ -383,6 +383,20 @@ def test_edge_cases():
     assert bytes(os_.tally) == bytes(ob.tally)
     assert os_.photons_stored == 3
     assert np.all(small.photons[3 * 8:].cpu().numpy() == 0)
+    for cap in (0, 1):                                   # no room, or room for one record
+        tiny = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **run), 800, capacity=cap)
+        pe.pe_step([tiny.handle], 600)
+        ot_ = tiny.tally_out()
+        assert ot_.status == pe.PE_ERR_BUFFER_FULL and bytes(ot_.tally) == bytes(ob.tally)
+        assert ot_.photons_stored == cap
+        assert np.all(tiny.photons[cap * 8:].cpu().numpy() == 0)
+        tiny.close()
+    # a device wait that ran out (injected on the host as the tally word the kernel would set)
+    # makes pe_tally report PE_ERR_TIMEOUT
+    small.tally[pe.T["N_WAIT_TIMEOUT"]] = 1
+    with pytest.raises(pe.PeError) as e:
+        small.tally_out()
+    assert e.value.status == pe.PE_ERR_TIMEOUT
     # bad arguments
     with pytest.raises(pe.PeError) as e:
         pe.Run(lt, pe.run_params(precision=7, **run), 10)
