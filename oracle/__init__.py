@@ -108,7 +108,7 @@ def lib():
             L.or_sample_bh_x.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
             L.or_sample_bh_x.restype = C.c_double
             L.or_pair_transport.argtypes = [C.c_void_p, C.POINTER(RunParams), C.c_void_p, C.c_int64, C.c_int64,
-                                            C.c_void_p, C.c_int64, C.POINTER(C.c_uint64)]
+                                            C.c_void_p, C.c_int64, C.POINTER(C.c_uint64), C.c_int]
             L.or_pair_transport.restype = C.c_int
             L.or_tables_build.argtypes = [C.POINTER(TableParams), C.c_int, dp]
             L.or_tables_build.restype = C.c_void_p
@@ -293,7 +293,11 @@ def run(tables: Tables, run: RunParams, ids, state, step0: int, n_steps: int,
     return photons[:min(n_ph.value, capacity)], n_ph.value, hist, tally
 
 
-def pair_transport(tables: Tables, run: RunParams, photons, step_end: int, capacity: int = 1 << 20):
+PAIR_DIRECT, PAIR_FREE_PATH = 0, 1
+
+
+def pair_transport(tables: Tables, run: RunParams, photons, step_end: int, capacity: int = 1 << 20,
+                   method: int = PAIR_DIRECT):
     """Bethe-Heitler conversion of the photon records (PHOTON_DTYPE) in the target up to
     step_end (see oracle.h); returns (pairs, true pair count, tally)."""
     ph = np.ascontiguousarray(photons, dtype=PHOTON_DTYPE)
@@ -301,7 +305,7 @@ def pair_transport(tables: Tables, run: RunParams, photons, step_end: int, capac
     tally = np.zeros(PAIR_TALLY_WORDS, dtype=np.uint64)
     rc = lib().or_pair_transport(tables._h, C.byref(run), ph.ctypes.data_as(C.c_void_p), len(ph), int(step_end),
                                  pairs.ctypes.data_as(C.c_void_p), capacity,
-                                 tally.ctypes.data_as(C.POINTER(C.c_uint64)))
+                                 tally.ctypes.data_as(C.POINTER(C.c_uint64)), int(method))
     if rc != 0:
         raise RuntimeError("or_pair_transport failed")
     n = int(tally[PT["N_PAIRS"]])

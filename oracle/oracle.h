@@ -208,8 +208,15 @@ enum { ORP_N_PAIRS = 0, ORP_N_ENTERED = 1, ORP_N_K_ABOVE = 2, ORP_N_TESTS = 3, O
  * pair count (true count), photons that entered the target, of them above the
  * table's k range, tests taken (draws), and 128-bit fixed-point sums of k and E+
  * of the conversions.                                                         */
+enum { OR_PAIR_DIRECT = 0, OR_PAIR_FREE_PATH = 1 };
+/* method OR_PAIR_FREE_PATH: the same law by one draw per photon (the random free path):
+ * the trials of a crossing all have probability P, so the number of failures before the
+ * first success is geometric, j = floor(ln U / ln(1 - P)) with U the u53 of words 0-1 of
+ * the draw (id_mech, run id, first step inside, 0x50000000 + n_e); the photon converts at
+ * the first step inside + j if that is still inside, with the fraction word 2-3.  The
+ * tests tally then counts draws.  Returns -1 for an unknown method.                      */
 int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
-                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally);
+                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally, int method);
 
 /* normalised helpers (exposed for unit pins) */
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */

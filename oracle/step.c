@@ -55,6 +55,8 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 enum { PUR_BREMS = 0, PUR_NCS = 1, PUR_TAU0 = 2, PUR_POS = 3, PUR_MJ = 4, PUR_WAIT = 256 };
 /* photon streams: counter word 0 = the photon's id_mech, word 3 = PUR_BH + emission step */
 #define PUR_BH 0x40000000u
+/* free-path draws: word 3 = PUR_BH_FREE + emission step (emission steps below 2^28) */
+#define PUR_BH_FREE 0x50000000u
 
 static void draw(const or_run_params* r, int64_t id, uint32_t step, uint32_t purpose, uint32_t w[4]) {
     uint32_t ctr[4] = {(uint32_t)id, r->run_id, step, purpose};
@@ -767,8 +769,28 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
 /* to the bremsstrahlung"): the direct MC collision of Eq. (4) per step with */
 /* sigma_BH, photons moving at c along their direction.                      */
 /* ------------------------------------------------------------------------- */
+/* conversion of photon j at step m with the fraction word (w2, w3): record and tallies */
+static void pair_record(const or_tables* t, const or_run_params* r, const run_ctx* c, const or_photon* ph,
+                        int64_t j, int64_t m, double k, double px, double py, int two_d, uint32_t w2, uint32_t w3,
+                        or_pair* pairs, int64_t cap, uint64_t* tally) {
+    double x = or_sample_bh_x(t, r->iz, k, u53(word64(w2, w3)));
+    double ep = x * k;
+    int64_t q = (int64_t)tally[ORP_N_PAIRS]++;
+    fx_add(tally + ORP_E_PAIRS, k);
+    fx_add(tally + ORP_E_POSITRONS, ep);
+    (void)c;
+    if (q < cap) {
+        or_pair* o = pairs + q;
+        o->x = (float)px; o->y = (float)(two_d ? py : 0.0);
+        o->e_minus = (float)(k - ep); o->e_plus = (float)ep;
+        o->kx = ph->kx; o->ky = ph->ky; o->kz = ph->kz;
+        o->step = (uint32_t)m; o->photon = (uint32_t)j; o->id_mech = ph->id_mech;
+    }
+}
+
 int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
-                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally) {
+                      int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally, int method) {
+    if (method != OR_PAIR_DIRECT && method != OR_PAIR_FREE_PATH) return -1;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
     for (int k = 0; k < ORP_WORDS; ++k) tally[k] = 0;
@@ -785,7 +807,9 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
         double P = -expm1(-c.K_br * sig);                  /* beta = 1 */
         uint64_t thr = (uint64_t)floor(P * 18446744073709551616.0);
         if (P >= 1.0) thr = UINT64_MAX;
+        uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
         int was_in = 0;
+        int64_t first = -1, last = -1;                     /* the run of steps inside the target */
         for (int64_t m = ne + 1; m < step_end; ++m) {
             double tt = (double)(m - ne) * c.dt;
             double px = fma(kx, tt, xe), py = fma(ky, tt, ye);
@@ -799,28 +823,34 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
             }
             if (!was_in) {
                 was_in = 1;
+                first = m;
                 tally[ORP_N_ENTERED]++;
                 if (above) tally[ORP_N_K_ABOVE]++;
             }
+            last = m;
+            if (method == OR_PAIR_FREE_PATH) continue;     /* the run only; one draw below */
             uint32_t ctr[4] = {ph->id_mech, r->run_id, (uint32_t)m, PUR_BH + (uint32_t)ne};
-            uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
             tally[ORP_N_TESTS]++;
             if (word64(w[0], w[1]) < thr) {
-                double x = or_sample_bh_x(t, r->iz, k, u53(word64(w[2], w[3])));
-                double ep = x * k;
-                int64_t q = (int64_t)tally[ORP_N_PAIRS]++;
-                fx_add(tally + ORP_E_PAIRS, k);
-                fx_add(tally + ORP_E_POSITRONS, ep);
-                if (q < cap) {
-                    or_pair* o = pairs + q;
-                    o->x = (float)px; o->y = (float)(two_d ? py : 0.0);
-                    o->e_minus = (float)(k - ep); o->e_plus = (float)ep;
-                    o->kx = ph->kx; o->ky = ph->ky; o->kz = ph->kz;
-                    o->step = (uint32_t)m; o->photon = (uint32_t)j; o->id_mech = ph->id_mech;
-                }
+                pair_record(t, r, &c, ph, j, m, k, px, py, two_d, w[2], w[3], pairs, cap, tally);
                 break;
+            }
+        }
+        if (method == OR_PAIR_FREE_PATH && first >= 0 && P > 0.0) {
+            /* the per-step trials of one crossing, all with probability P, fail a geometric number
+             * of times before the first success: j = floor(ln U / ln(1 - P)) */
+            uint32_t ctr[4] = {ph->id_mech, r->run_id, (uint32_t)first, PUR_BH_FREE + (uint32_t)ne};
+            uint32_t w[4];
+            or_philox4x32_10(ctr, key, w);
+            tally[ORP_N_TESTS]++;
+            double q = (P >= 1.0) ? 0.0 : floor(log(u53(word64(w[0], w[1]))) / log1p(-P));
+            if (q <= (double)(last - first)) {
+                int64_t m = first + (int64_t)q;
+                double tt = (double)(m - ne) * c.dt;
+                pair_record(t, r, &c, ph, j, m, k, fma(kx, tt, xe), fma(ky, tt, ye), two_d, w[2], w[3], pairs, cap,
+                            tally);
             }
         }
     }

@@ -221,3 +221,52 @@ def test_pair_transport_edges():
     dt = 2 * math.pi
     last = int(np.floor(yh / (math.sin(0.01) * dt) + 1e-9))       # last step with |y| <= y_half
     assert n2 > 0 and p2["step"].max() <= last and np.all(np.abs(p2["y"]) <= yh * (1 + 1e-6))
+
+
+def test_pair_free_path_conversion_law():
+    """The free-path method (one geometric draw per crossing) gives the beam the same law: the
+    converted fraction 1 - (1 - P)^N and geometric depths, with one draw per photon."""
+    t = O.Tables(O.table_params(n_eta=16, n_y=16, n_E=65, n_s=65, gamma_max=1e6), [79.0])
+    r = _beam_run()
+    k, n = 1e4, 40000
+    ph = np.zeros(n, dtype=W.PHOTON_RECORD)
+    ph["x"] = -0.5
+    ph["energy"] = k
+    ph["kx"] = 1.0
+    ph["id_mech"] = np.arange(n, dtype=np.uint32)
+    pairs, npairs, tally = O.pair_transport(t, r, ph, step_end=1000, method=O.PAIR_FREE_PATH)
+    n_i = 4177.0 * math.pi / (R_E * 1e-12) / 79.0
+    P = -math.expm1(-n_i * ALPHA * R_E ** 2 * t.bh_sigma_interp(0, k)[0] * 1e-6)
+    n_in = 200
+    p_conv = 1.0 - (1.0 - P) ** n_in
+    assert tally[O.PT["N_TESTS"]] == n == tally[O.PT["N_ENTERED"]]
+    assert abs(npairs - n * p_conv) < 5 * math.sqrt(n * p_conv * (1 - p_conv))
+    m0 = 1                                              # first step inside: -0.5 + dt >= 0
+    j = pairs["step"].astype(np.int64) - m0
+    assert j.min() >= 0 and j.max() < n_in
+    jj = np.arange(n_in)
+    pj = (1 - P) ** jj * P / p_conv
+    mean = float((jj * pj).sum())
+    var = float(((jj - mean) ** 2 * pj).sum())
+    assert abs(j.mean() - mean) < 5 * math.sqrt(var / len(j))
+
+
+def test_pair_free_path_equals_direct_in_law():
+    """On synthetic photons through 2 mm of Au both methods convert the same number of photons,
+    at the same mean depth after entry and with the same positron-energy fractions, within the
+    statistics (the realisations differ: other draws)."""
+    t = O.Tables(O.table_params(n_eta=16, n_y=16, n_E=33, n_s=33, gamma_max=1e6), [79.0])
+    r = _beam_run(slab_thick_m=2e-3)
+    kl = 2 * math.pi / 1e-6
+    ph = W.synthetic_photons(40000, 6, (0.0, 2e-3 * kl), (3.0, 1e5), (0, 500))
+    res = {}
+    for m in (O.PAIR_DIRECT, O.PAIR_FREE_PATH):
+        pairs, n, tally = O.pair_transport(t, r, ph, step_end=3000, method=m)
+        depth = pairs["step"].astype(np.int64) - ph["step"][pairs["photon"]].astype(np.int64)
+        res[m] = (n, depth, pairs["e_plus"] / (pairs["e_plus"] + pairs["e_minus"]), tally)
+    (n1, d1, x1, t1), (n2, d2, x2, t2) = res[O.PAIR_DIRECT], res[O.PAIR_FREE_PATH]
+    assert n1 > 3000 and abs(n1 - n2) < 5 * math.sqrt(n1 + n2)
+    assert abs(d1.mean() - d2.mean()) < 5 * math.sqrt(d1.var() / len(d1) + d2.var() / len(d2))
+    assert abs(x1.mean() - x2.mean()) < 5 * math.sqrt(x1.var() / len(x1) + x2.var() / len(x2))
+    assert t1[O.PT["N_ENTERED"]] == t2[O.PT["N_ENTERED"]]
+    assert t2[O.PT["N_TESTS"]] <= t2[O.PT["N_ENTERED"]] < t1[O.PT["N_TESTS"]]
