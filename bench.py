@@ -520,7 +520,8 @@ def bunch_pairs(pe, stream, flush, n=1_000_000, reps=3):
     """Bethe-Heitler pair production of the bunch's photons (Sec. 2.2): the 1 GeV Au bunch of
     1e6 electrons is run once (direct brems test, FP32), then its stored photons are stepped
     through the rest of the 5 mm target (pe_pair_transport, the Eq. 4 test per step with the
-    pair cross section), timed by CUDA events on the run's stream with L2 flushed in between."""
+    pair cross section), timed by CUDA events on the run's stream with L2 flushed in between.
+    The free-path method (one geometric draw per photon, the same law) is timed beside it."""
     import torch
     from paper_1612_07592_gb300 import workloads as W
     c = W.bunch(1000.0, "Au", n=n)
@@ -533,26 +534,35 @@ def bunch_pairs(pe, stream, flush, n=1_000_000, reps=3):
     with torch.cuda.stream(stream):
         pairs = torch.zeros(n_ph * 10, dtype=torch.int32, device="cuda")
         tally = torch.zeros(pe.PAIR_TALLY_WORDS, dtype=torch.int64, device="cuda")
-    ts = []
-    for k in range(reps + 1):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pe.pe_pair_transport(r.handle, r.photons.data_ptr(), n_ph, -1, pairs.data_ptr(), n_ph, tally.data_ptr())
-        e1.record(stream)
-        e1.synchronize()
-        if k:
-            ts.append(e0.elapsed_time(e1))
-    t = tally.cpu().numpy().view(np.uint64)
-    ms = float(np.median(ts))
+
+    def timed(method):
+        ts = []
+        for k in range(reps + 1):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pe.pe_pair_transport(r.handle, r.photons.data_ptr(), n_ph, -1, pairs.data_ptr(), n_ph, tally.data_ptr(),
+                                 method)
+            e1.record(stream)
+            e1.synchronize()
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), tally.cpu().numpy().view(np.uint64).copy()
+
+    ms, t = timed(pe.PE_PAIR_DIRECT)
+    ms_f, tf = timed(pe.PE_PAIR_FREE_PATH)
     r.close()
     pe.pe_destroy_tables(tables)
     tests = int(t[pe.PT["N_TESTS"]])
     return {"value": tests / (ms * 1e-3), "unit": "Eq. 4 pair tests/s", "ms_per_transport": ms, "photons": n_ph,
             "photons_per_s": n_ph / (ms * 1e-3), "tests": tests, "pairs": int(t[pe.PT["N_PAIRS"]]),
             "entered": int(t[pe.PT["N_ENTERED"]]), "electrons": n, "steps": c["steps"],
-            "kernel": "k_pair_transport (warp-cooperative tests, integer Philox per step)"}
+            "kernel": "k_pair_transport (warp-cooperative tests, integer Philox per step)",
+            "free_path": {"ms_per_transport": ms_f, "photons_per_s": n_ph / (ms_f * 1e-3),
+                          "pairs": int(tf[pe.PT["N_PAIRS"]]), "draws": int(tf[pe.PT["N_TESTS"]]),
+                          "speedup_vs_direct": ms / ms_f,
+                          "kernel": "k_pair_transport (free path: one geometric draw per photon)"}}
 
 
 def profile_pairs(n):

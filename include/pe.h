@@ -325,6 +325,16 @@ pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int
  * ends the photon; a photon that has left the target, or is outside it and
  * moving away, is not followed further.  Photons do not feel the fields, so
  * following each one after the fact equals stepping it with the electrons.
+ *
+ * method PE_PAIR_FREE_PATH samples the same law with one draw per photon:
+ * the tests of one crossing all have the same P (sigma_BH(k) and n_i are
+ * constant along it), so the number of failures before the first success is
+ * geometric, j = floor(ln U / ln(1 - P)).  One Philox draw of counter
+ * (id_mech, run id, a, 0x50000000 + n_e), a the first step in the target:
+ * words 0-1 give U (53 bits), words 2-3 x; the photon converts at step a + j
+ * if that is within its run of steps in the target.  The conversions differ
+ * draw by draw from PE_PAIR_DIRECT's but follow the same distribution; the
+ * tests tally counts one per photon that had a draw.
  *   run       : the run whose target, step, seed, run id and Z apply
  *   photons   : device array of n_photons records (for instance the run's own
  *               photon buffer); 4-byte aligned; read only
@@ -337,10 +347,12 @@ pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int
  *               of them above the table's k range (last row used), tests
  *               taken (one draw each), and 128-bit fixed-point (lo, hi;
  *               2^-64 m c^2) sums of k and E+ of the conversions
+ *   method    : PE_PAIR_DIRECT (per-step tests) or PE_PAIR_FREE_PATH
  * Asynchronous on the run's stream.  The first call on a table set builds
  * its pair tables on the host and uploads them (synchronous).
  * Errors: PE_ERR_ARG (null, n_photons < 0 or >= 2^31, capacity < 0,
- * misaligned, step_end beyond the run), PE_ERR_NOMEM, PE_ERR_CUDA.             */
+ * misaligned, step_end beyond the run, unknown method), PE_ERR_NOMEM,
+ * PE_ERR_CUDA.                                                               */
 typedef struct {
     float x, y;               /* conversion point: the photon's position at `step` (y = 0 in 1D) */
     float e_minus, e_plus;    /* total energies of the electron and the positron, m c^2 */
@@ -354,8 +366,9 @@ enum {
     PE_PT_N_PAIRS = 0, PE_PT_N_ENTERED = 1, PE_PT_N_K_ABOVE = 2, PE_PT_N_TESTS = 3, PE_PT_E_PAIRS = 4,
     PE_PT_E_POSITRONS = 6
 };
+enum { PE_PAIR_DIRECT = 0, PE_PAIR_FREE_PATH = 1 };
 pe_status pe_pair_transport(pe_run* run, const void* photons, int64_t n_photons, int64_t step_end, void* pairs,
-                            int64_t capacity, void* tally);
+                            int64_t capacity, void* tally, int method);
 
 /* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */

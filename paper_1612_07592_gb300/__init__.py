@@ -41,6 +41,7 @@ PAIR_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("e_minus", "<f4"), ("e_plus"
                        ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("photon", "<u4"), ("id_mech", "<u4")])
 PAIR_TALLY_WORDS = 8
 PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, N_TESTS=3, E_PAIRS=4, E_POSITRONS=6)
+PE_PAIR_DIRECT, PE_PAIR_FREE_PATH = 0, 1
 EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
             "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch", "pe_graph_destroy",
             "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport", "pe_resume_particles"]
@@ -122,7 +123,7 @@ def lib():
                                               C.c_int64, vp]
             L.pe_electron_spectrum.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp]
             L.pe_photon_map.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, vp]
-            L.pe_pair_transport.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
+            L.pe_pair_transport.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp, C.c_int]
             L.pe_resume_particles.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), C.c_int64, vp,
                                               C.POINTER(vp)]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
@@ -262,9 +263,9 @@ def pe_photon_map(run: int, nx: int, x_min_m: float, x_max_m: float, ne: int, e_
 
 
 def pe_pair_transport(run: int, photons_ptr: int, n_photons: int, step_end: int, pairs_ptr: int, capacity: int,
-                      tally_ptr: int) -> None:
+                      tally_ptr: int, method: int = PE_PAIR_DIRECT) -> None:
     _check(lib().pe_pair_transport(run, photons_ptr, int(n_photons), int(step_end), pairs_ptr, int(capacity),
-                                   tally_ptr))
+                                   tally_ptr, int(method)))
 
 
 def pe_destroy(run: int):
@@ -432,10 +433,11 @@ class Run:
         return out.cpu().numpy().view(np.uint64).reshape(nx, ne)
 
     def pair_transport(self, photons=None, n_photons: int | None = None, step_end: int = -1,
-                       capacity: int | None = None):
+                       capacity: int | None = None, method: int = PE_PAIR_DIRECT):
         """Bethe-Heitler conversion, computed on the device, of photon records in this run's target up
         to step_end (-1: the steps done).  photons: a CUDA uint8/int32 tensor of records or a
         PHOTON_DTYPE numpy array (copied to the device); default the run's own stored photons.
+        method: PE_PAIR_DIRECT (per-step tests) or PE_PAIR_FREE_PATH (one geometric draw per photon).
         Returns (pairs as PAIR_DTYPE, true pair count, tally words)."""
         torch = self.torch
         if photons is None:
@@ -453,7 +455,8 @@ class Run:
                 dev_ph = photons
             pairs = torch.zeros(max(cap, 1) * 10, dtype=torch.int32, device=self.x.device)
             tally = torch.zeros(PAIR_TALLY_WORDS, dtype=torch.int64, device=self.x.device)
-        pe_pair_transport(self.handle, dev_ph.data_ptr(), int(n), step_end, pairs.data_ptr(), cap, tally.data_ptr())
+        pe_pair_transport(self.handle, dev_ph.data_ptr(), int(n), step_end, pairs.data_ptr(), cap, tally.data_ptr(),
+                          method)
         self.stream.synchronize()
         t = tally.cpu().numpy().view(np.uint64)
         k = int(min(t[PT["N_PAIRS"]], cap))

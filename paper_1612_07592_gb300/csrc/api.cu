@@ -698,9 +698,11 @@ extern "C" pe_status pe_photon_map(pe_run* r, int nx, double x_min_m, double x_m
 }
 
 extern "C" pe_status pe_pair_transport(pe_run* r, const void* photons, int64_t n_photons, int64_t step_end,
-                                        void* pairs, int64_t capacity, void* tally) {
+                                        void* pairs, int64_t capacity, void* tally, int method) {
     if (!r || !tally || (n_photons > 0 && !photons) || (capacity > 0 && !pairs))
         return fail(PE_ERR_ARG, "pe_pair_transport: null argument");
+    if (method != PE_PAIR_DIRECT && method != PE_PAIR_FREE_PATH)
+        return fail(PE_ERR_ARG, "pe_pair_transport: method must be PE_PAIR_DIRECT or PE_PAIR_FREE_PATH");
     if (n_photons < 0 || n_photons >= (int64_t(1) << 31) || capacity < 0)
         return fail(PE_ERR_ARG, "pe_pair_transport: n_photons must be in [0, 2^31), capacity >= 0");
     if ((reinterpret_cast<uintptr_t>(photons) & 3u) || (reinterpret_cast<uintptr_t>(pairs) & 3u) ||
@@ -717,7 +719,7 @@ extern "C" pe_status pe_pair_transport(pe_run* r, const void* photons, int64_t n
     D.bhsig64 = r->tables->bh_dev;
     D.bhcdf64 = r->tables->bh_dev + r->tables->bh_sigma.size();
     launch_pair_transport(D, r->dev, photons, n_photons, step_end, pairs, capacity,
-                          static_cast<unsigned long long*>(tally), r->stream);
+                          static_cast<unsigned long long*>(tally), method, r->stream);
     g_launches++;
     e = cudaGetLastError();
     return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_pair_transport");

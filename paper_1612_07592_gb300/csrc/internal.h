@@ -164,7 +164,7 @@ void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::
 
 // kernels_pair.cu: Bethe-Heitler conversion of photon records in the run's target
 void launch_pair_transport(const TablesDev& t, const RunDev& r, const void* photons, int64_t n_photons,
-                           int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally,
+                           int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally, int method,
                            cudaStream_t s);
 
 // kernels.cu

@@ -6,6 +6,10 @@
 // emission point; at every step inside the target it takes the test, and on a conversion
 // the positron fraction x is drawn from the tabulated CDF of Tsai's pair DCS.
 //
+// Two methods of the same law: the per-step tests of Eq. 4 (the paper's direct collision),
+// and the free path (the trials of one crossing share P, so the first success is geometric:
+// one draw per photon, the random-free-path sampling Sec. 2.2 mentions).
+//
 // Rounds of 32 photons per warp.  Each lane first finds its photon's run of consecutive
 // steps inside the target by binary search on the FP64 position computed exactly as the
 // definition computes it at each step (GB300's FP64 pipe is narrow: the literal per-step
@@ -19,7 +23,8 @@
 namespace pe {
 namespace {
 
-constexpr uint32_t kPurBH = 0x40000000u;   // counter word 3 = kPurBH + emission step
+constexpr uint32_t kPurBH = 0x40000000u;      // per-step tests: counter word 3 = kPurBH + emission step
+constexpr uint32_t kPurBHFree = 0x50000000u;  // free path: counter word 3 = kPurBHFree + emission step
 
 struct PairRec {
     float x, y, e_minus, e_plus, kx, ky, kz;
@@ -68,9 +73,12 @@ __device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, d
 #define PE_PAIR_MIN_CTAS_SM 3      // resident CTAs of 256 threads per SM the registers are sized for
 #endif
 
-__global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(TablesDev t, RunDev r, const Photon* ph, int64_t n_ph,
-                                                        int64_t step_end, PairRec* out, int64_t cap,
-                                                        unsigned long long* tally) {
+// kFree: the free-path method (one geometric draw per photon) instead of the per-step tests
+template <bool kFree>
+__global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(TablesDev t, RunDev r, const Photon* ph,
+                                                                           int64_t n_ph, int64_t step_end,
+                                                                           PairRec* out, int64_t cap,
+                                                                           unsigned long long* tally) {
     __shared__ unsigned long long s_t[PE_PAIR_TALLY_WORDS];
     if (threadIdx.x < PE_PAIR_TALLY_WORDS) s_t[threadIdx.x] = 0;
     __syncthreads();
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
         Photon p{};
         int64_t a = 1, b = 0;
         uint64_t thr = 0;
-        double k = 0.0;
+        double k = 0.0, P = 0.0;
         if (j < n_ph) {
             p = ph[j];
             k = (double)p.e;
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
                 const double kx = p.kx, ky = p.ky, xe = p.x, ye = p.y;
                 const int64_t ne = p.step;
                 bool above;
-                const double P = -expm1(-c.K_br * bh_sigma_of(t, sig, k, above));
+                P = -expm1(-c.K_br * bh_sigma_of(t, sig, k, above));
                 thr = P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
                 // The steps with the photon inside the target form one run [a, b] (its position
                 // is monotone in the step and the target convex): bound it with each face by
@@ -150,9 +158,36 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
                 }
             }
         }
+        // the lane's pair record for a conversion at step `hit` with the fraction word (wz, ww)
+        auto record = [&](int64_t hit, uint32_t wz, uint32_t ww) {
+            const double x = bh_sample_x(t, cdf, k, uni53(w64(wz, ww)));
+            const double ep = x * k;
+            q.x = (float)photon_pos(c, p.kx, p.x, p.step, hit);
+            q.y = (float)(two_d ? photon_pos(c, p.ky, p.y, p.step, hit) : 0.0);
+            q.e_minus = (float)(k - ep);
+            q.e_plus = (float)ep;
+            q.kx = p.kx; q.ky = p.ky; q.kz = p.kz;
+            q.step = (uint32_t)hit;
+            q.photon = (uint32_t)j;
+            q.id_mech = p.id_mech;
+            fx_add(&s_t[PE_PT_E_PAIRS], k);
+            fx_add(&s_t[PE_PT_E_POSITRONS], ep);
+            conv = true;
+        };
+        if constexpr (kFree) {
+            // the trials of the crossing all have probability P: the number of failures before
+            // the first success is geometric, floor(ln U / ln(1 - P)); one draw per photon
+            if (a <= b && P > 0.0) {
+                const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)a, kPurBHFree + p.step),
+                                              r.seed_lo, r.seed_hi);
+                tests = 1;
+                const double jf = P >= 1.0 ? 0.0 : floor(log(uni53(w64(w.x, w.y))) / log1p(-P));
+                if (jf <= (double)(b - a)) record(a + (int64_t)jf, w.z, w.w);
+            }
+        }
         // The warp takes the tests of each photon of the round in turn, 32 steps at a time
         // (lane l tests step m0 + l); the conversion is at the first step whose draw passes.
-        for (int src = 0; src < 32; ++src) {
+        for (int src = 0; src < 32 && !kFree; ++src) {
             const int64_t as = __shfl_sync(0xffffffffu, a, src), bs = __shfl_sync(0xffffffffu, b, src);
             if (as > bs) continue;
             const uint32_t idm = __shfl_sync(0xffffffffu, p.id_mech, src);
@@ -179,21 +214,7 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
             }
             if (lane == src) {
                 tests += (unsigned long long)((hit >= 0 ? hit : bs) - as + 1);
-                if (hit >= 0) {
-                    const double x = bh_sample_x(t, cdf, k, uni53(w64(hz, hw)));
-                    const double ep = x * k;
-                    q.x = (float)photon_pos(c, p.kx, p.x, p.step, hit);
-                    q.y = (float)(two_d ? photon_pos(c, p.ky, p.y, p.step, hit) : 0.0);
-                    q.e_minus = (float)(k - ep);
-                    q.e_plus = (float)ep;
-                    q.kx = p.kx; q.ky = p.ky; q.kz = p.kz;
-                    q.step = (uint32_t)hit;
-                    q.photon = (uint32_t)j;
-                    q.id_mech = p.id_mech;
-                    fx_add(&s_t[PE_PT_E_PAIRS], k);
-                    fx_add(&s_t[PE_PT_E_POSITRONS], ep);
-                    conv = true;
-                }
+                if (hit >= 0) record(hit, hz, hw);
             }
         }
         // tests of the warp's round, one shared atomic per warp
@@ -230,15 +251,19 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
 }  // namespace
 
 void launch_pair_transport(const TablesDev& t, const RunDev& r, const void* photons, int64_t n_photons,
-                           int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally,
+                           int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally, int method,
                            cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t blocks = (n_photons + 255) / 256;
     const int grid = (int)(blocks < (int64_t)sms * 8 ? (blocks > 0 ? blocks : 1) : (int64_t)sms * 8);
-    k_pair_transport<<<grid, 256, 0, s>>>(t, r, static_cast<const Photon*>(photons), n_photons, step_end,
-                                          static_cast<PairRec*>(pairs), capacity, tally);
+    if (method == PE_PAIR_FREE_PATH)
+        k_pair_transport<true><<<grid, 256, 0, s>>>(t, r, static_cast<const Photon*>(photons), n_photons, step_end,
+                                                    static_cast<PairRec*>(pairs), capacity, tally);
+    else
+        k_pair_transport<false><<<grid, 256, 0, s>>>(t, r, static_cast<const Photon*>(photons), n_photons, step_end,
+                                                     static_cast<PairRec*>(pairs), capacity, tally);
 }
 
 }  // namespace pe

@@ -35,11 +35,14 @@ def _run(lt, steps, precision=pe.PE_F64, **kw):
     return r, d
 
 
-def _oracle_pairs(ot, d, photons, step_end):
+def _oracle_pairs(ot, d, photons, step_end, method=O.PAIR_DIRECT):
     od = dict(W.base_run(**d))
     od.pop("precision", None)
     od["iz"] = list(Z).index(od["Z"])
-    return O.pair_transport(ot, O.run_params(**od), photons, step_end, capacity=len(photons) + 1)
+    return O.pair_transport(ot, O.run_params(**od), photons, step_end, capacity=len(photons) + 1, method=method)
+
+
+METHODS = [(pe.PE_PAIR_DIRECT, O.PAIR_DIRECT), (pe.PE_PAIR_FREE_PATH, O.PAIR_FREE_PATH)]
 
 
 def _compare(dev, dev_n, dev_t, orc, orc_n, orc_t):
@@ -57,23 +60,29 @@ def _compare(dev, dev_n, dev_t, orc, orc_n, orc_t):
         np.testing.assert_allclose(d[f], o[f], rtol=2e-7, err_msg=f)
 
 
+@pytest.mark.parametrize("method", METHODS, ids=["direct", "free_path"])
 @pytest.mark.parametrize("precision", [pe.PE_F64, pe.PE_F32])
-def test_pair_transport_parity_1d(precision):
+def test_pair_transport_parity_1d(precision, method):
     """Synthetic photons (emission points through and before a 2 mm solid-Au target, 1 mc^2 to
     1e5 mc^2, cones about +x with 10 % reversed, emission steps up to 2500): the device converts
-    the same photons at the same steps with the same positron energies as the oracle."""
+    the same photons at the same steps with the same positron energies as the oracle, by either
+    method."""
     lt, ot = tables(_tp(48), Z)
     steps = 3000
     r, d = _run(lt, steps, precision)
     ph = W.synthetic_photons(30000, 9, (-50.0, 2e-3 * KL), (1.0, 1e5), (0, 2500))
-    dev, dev_n, dev_t = r.pair_transport(ph)
-    orc, orc_n, orc_t = _oracle_pairs(ot, d, ph, steps)
+    dev, dev_n, dev_t = r.pair_transport(ph, method=method[0])
+    orc, orc_n, orc_t = _oracle_pairs(ot, d, ph, steps, method[1])
     assert orc_n > 2000 and orc_t[O.PT["N_K_ABOVE"]] == 0
+    if method[0] == pe.PE_PAIR_FREE_PATH:
+        # one draw per photon in the target with P > 0 (sigma_BH is clamped to 0 just above k = 2)
+        assert 0 < orc_t[O.PT["N_TESTS"]] <= orc_t[O.PT["N_ENTERED"]]
     _compare(dev, dev_n, dev_t, orc, orc_n, orc_t)
     r.close()
 
 
-def test_pair_transport_parity_2d_and_al():
+@pytest.mark.parametrize("method", METHODS, ids=["direct", "free_path"])
+def test_pair_transport_parity_2d_and_al(method):
     """2D target strip |y| <= 3 um (photons leave it sideways) on Al, and a transport window that
     ends before the run's last step."""
     lt, ot = tables(_tp(48), Z)
@@ -82,8 +91,8 @@ def test_pair_transport_parity_2d_and_al():
                 y_half_m=3e-6)
     ph = W.synthetic_photons(30000, 10, (0.0, 3e-3 * KL), (3.0, 2e6), (0, 3000), theta_max=0.003,
                              y_half=3e-6 * KL)
-    dev, dev_n, dev_t = r.pair_transport(ph, step_end=3500)
-    orc, orc_n, orc_t = _oracle_pairs(ot, d, ph, 3500)
+    dev, dev_n, dev_t = r.pair_transport(ph, step_end=3500, method=method[0])
+    orc, orc_n, orc_t = _oracle_pairs(ot, d, ph, 3500, method[1])
     assert orc_n > 100 and orc_t[O.PT["N_K_ABOVE"]] > 0
     _compare(dev, dev_n, dev_t, orc, orc_n, orc_t)
     r.close()
@@ -113,6 +122,12 @@ def test_pair_transport_edges_and_capacity():
     assert set(part["photon"].tolist()) <= set(full["photon"].tolist())
     with pytest.raises(pe.PeError):
         r.pair_transport(many, step_end=101)
+    with pytest.raises(pe.PeError):
+        r.pair_transport(many, method=2)
+    # the free path on the edge photons (entering at the last step, reversed, beyond the target)
+    dev, dev_n, dev_t = r.pair_transport(ph, method=pe.PE_PAIR_FREE_PATH)
+    orc, orc_n, orc_t = _oracle_pairs(ot, d, ph, 100, O.PAIR_FREE_PATH)
+    _compare(dev, dev_n, dev_t, orc, orc_n, orc_t)
     r.close()
 
 
@@ -128,6 +143,7 @@ def test_pair_conversion_of_the_bunch_photons():
     ph = run.photon_records()
     assert len(ph) > 100000
     pairs, n_pairs, t = run.pair_transport()
+    fpairs, n_free, tf = run.pair_transport(method=pe.PE_PAIR_FREE_PATH)
     steps = b["steps"]
     dt = 2 * math.pi
     x1 = 5e-3 * KL
@@ -149,6 +165,8 @@ def test_pair_conversion_of_the_bunch_photons():
     mean, var = pc.sum(), (pc * (1 - pc)).sum()
     assert n_pairs > 1000
     assert abs(n_pairs - mean) < 5 * math.sqrt(var), (n_pairs, mean)
-    np.testing.assert_allclose(pairs["e_minus"].astype(np.float64) + pairs["e_plus"], k[pairs["photon"]],
-                               rtol=1e-6)
+    assert abs(n_free - mean) < 5 * math.sqrt(var), (n_free, mean)
+    assert 0 < int(tf[pe.PT["N_TESTS"]]) <= int(tf[pe.PT["N_ENTERED"]]) == int(t[pe.PT["N_ENTERED"]])
+    for p in (pairs, fpairs):
+        np.testing.assert_allclose(p["e_minus"].astype(np.float64) + p["e_plus"], k[p["photon"]], rtol=1e-6)
     run.close()
