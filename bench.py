@@ -567,7 +567,8 @@ def bunch_pairs(pe, stream, flush, n=1_000_000, reps=3):
 
 def profile_pairs(n):
     """Profiling run: the 1 GeV Au bunch with n electrons (untimed), then two pair transports of
-    its photons (the second is the one to capture)."""
+    its photons by the per-step tests and two by the free path (the second of each is the one to
+    capture)."""
     import torch
     import paper_1612_07592_gb300 as pe
     from paper_1612_07592_gb300 import workloads as W
@@ -578,9 +579,11 @@ def profile_pairs(n):
     out = None
     for _ in range(2):
         out = r.pair_transport()
+    for _ in range(2):
+        free = r.pair_transport(method=pe.PE_PAIR_FREE_PATH)
     torch.cuda.synchronize()
     print(json.dumps({"profile_pairs": True, "electrons": n, "photons": int(r.tally_out().photons_stored),
-                      "pairs": out[1], "tests": int(out[2][pe.PT["N_TESTS"]])}))
+                      "pairs": out[1], "tests": int(out[2][pe.PT["N_TESTS"]]), "pairs_free_path": free[1]}))
     r.close()
 
 

@@ -329,7 +329,8 @@ pe_status pe_photon_map(pe_run* run, int nx, double x_min_m, double x_max_m, int
  * method PE_PAIR_FREE_PATH samples the same law with one draw per photon:
  * the tests of one crossing all have the same P (sigma_BH(k) and n_i are
  * constant along it), so the number of failures before the first success is
- * geometric, j = floor(ln U / ln(1 - P)).  One Philox draw of counter
+ * geometric, j = floor(ln U / ln(1 - P)) = floor(-ln U / lam), with lam =
+ * n_i sigma_BH(k) c dt the exponent of Eq. (4).  One Philox draw of counter
  * (id_mech, run id, a, 0x50000000 + n_e), a the first step in the target:
  * words 0-1 give U (53 bits), words 2-3 x; the photon converts at step a + j
  * if that is within its run of steps in the target.  The conversions differ

@@ -211,7 +211,8 @@ enum { ORP_N_PAIRS = 0, ORP_N_ENTERED = 1, ORP_N_K_ABOVE = 2, ORP_N_TESTS = 3, O
 enum { OR_PAIR_DIRECT = 0, OR_PAIR_FREE_PATH = 1 };
 /* method OR_PAIR_FREE_PATH: the same law by one draw per photon (the random free path):
  * the trials of a crossing all have probability P, so the number of failures before the
- * first success is geometric, j = floor(ln U / ln(1 - P)) with U the u53 of words 0-1 of
+ * first success is geometric, j = floor(ln U / ln(1 - P)) = floor(-ln U / lam) (Eq. 4:
+ * 1 - P = exp(-lam), lam = n_i sigma c dt, taken as computed) with U the u53 of words 0-1 of
  * the draw (id_mech, run id, first step inside, 0x50000000 + n_e); the photon converts at
  * the first step inside + j if that is still inside, with the fraction word 2-3.  The
  * tests tally then counts draws.  Returns -1 for an unknown method.                      */

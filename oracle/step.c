@@ -838,14 +838,15 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
                 break;
             }
         }
-        if (method == OR_PAIR_FREE_PATH && first >= 0 && P > 0.0) {
-            /* the per-step trials of one crossing, all with probability P, fail a geometric number
-             * of times before the first success: j = floor(ln U / ln(1 - P)) */
+        if (method == OR_PAIR_FREE_PATH && first >= 0 && c.K_br * sig > 0.0) {
+            /* the per-step trials of one crossing, all with probability P = 1 - exp(-lam) (Eq. 4,
+             * lam = n_i sigma c dt), fail a geometric number of times before the first success:
+             * j = floor(ln U / ln(1 - P)) = floor(-ln U / lam) */
             uint32_t ctr[4] = {ph->id_mech, r->run_id, (uint32_t)first, PUR_BH_FREE + (uint32_t)ne};
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
             tally[ORP_N_TESTS]++;
-            double q = (P >= 1.0) ? 0.0 : floor(log(u53(word64(w[0], w[1]))) / log1p(-P));
+            double q = floor(-log(u53(word64(w[0], w[1]))) / (c.K_br * sig));
             if (q <= (double)(last - first)) {
                 int64_t m = first + (int64_t)q;
                 double tt = (double)(m - ne) * c.dt;

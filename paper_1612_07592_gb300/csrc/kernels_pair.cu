@@ -33,24 +33,23 @@ struct PairRec {
 static_assert(sizeof(PairRec) == 40, "pe_pair layout");
 static_assert(sizeof(Photon) == 32, "photon record layout");
 
-// sigma_BH(k) by row interpolation in log k over [2, gamma_max] (0 for k <= 2)
-__device__ __forceinline__ double bh_sigma_of(const TablesDev& t, const double* sig, double k, bool& above) {
+// sigma_BH(k) by row interpolation in log k over [2, gamma_max] (0 for k <= 2); the row
+// position (i, w) is kept for the sampling of x
+__device__ __forceinline__ double bh_sigma_of(const TablesDev& t, const double* sig, double k, bool& above, int& i,
+                                              double& w) {
     const TabC<double>& c = t.cd;
     above = false;
     if (!(k > 2.0)) return 0.0;
-    int i, fl;
-    double w;
+    int fl;
     row_pos<double>(k, c.ln_k_min, c.inv_dln_k, c.g_last, t.n_E, i, w, fl);
     above = (fl == 1);
     return (1.0 - w) * sig[i] + w * sig[i + 1];
 }
 
-// positron fraction x in [1/k, 1 - 1/k] from the row-interpolated CDF at uniform Rv
-__device__ __forceinline__ double bh_sample_x(const TablesDev& t, const double* cdf_z, double k, double Rv) {
-    const TabC<double>& c = t.cd;
-    int i, fl;
-    double w;
-    row_pos<double>(k, c.ln_k_min, c.inv_dln_k, c.g_last, t.n_E, i, w, fl);
+// positron fraction x in [1/k, 1 - 1/k] from the CDF interpolated at row position (i, w) of k,
+// at uniform Rv (2/k is formed as 2 (1/k), the same double)
+__device__ __forceinline__ double bh_sample_x(const TablesDev& t, const double* cdf_z, double k, int i, double w,
+                                              double Rv) {
     const double* ra = cdf_z + (size_t)i * t.n_s;
     const double* rb = ra + t.n_s;
     int j;
@@ -59,7 +58,8 @@ __device__ __forceinline__ double bh_sample_x(const TablesDev& t, const double* 
     if (j < 0) s = 0.0;
     else if (j >= t.n_s - 1) s = 1.0;
     else s = ((double)j + fr) / (double)(t.n_s - 1);
-    return 1.0 / k + s * (1.0 - 2.0 / k);
+    const double ik = 1.0 / k;
+    return ik + s * (1.0 - 2.0 * ik);
 }
 
 // the photon's coordinate (direction component d, emission coordinate e) at step m, as the
@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
         Photon p{};
         int64_t a = 1, b = 0;
         uint64_t thr = 0;
-        double k = 0.0, P = 0.0;
+        double k = 0.0, lam = 0.0, wk = 0.0;       // lam = n_i sigma_BH c dt = -ln(1 - P)
+        int ik = 0;
         if (j < n_ph) {
             p = ph[j];
             k = (double)p.e;
@@ -106,8 +107,11 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
                 const double kx = p.kx, ky = p.ky, xe = p.x, ye = p.y;
                 const int64_t ne = p.step;
                 bool above;
-                P = -expm1(-c.K_br * bh_sigma_of(t, sig, k, above));
-                thr = P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+                lam = c.K_br * bh_sigma_of(t, sig, k, above, ik, wk);
+                if constexpr (!kFree) {
+                    const double P = -expm1(-lam);
+                    thr = P >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(P * 0x1.0p64);
+                }
                 // The steps with the photon inside the target form one run [a, b] (its position
                 // is monotone in the step and the target convex): bound it with each face by
                 // binary search on the position exactly as the step computes it, so the tests
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
         }
         // the lane's pair record for a conversion at step `hit` with the fraction word (wz, ww)
         auto record = [&](int64_t hit, uint32_t wz, uint32_t ww) {
-            const double x = bh_sample_x(t, cdf, k, uni53(w64(wz, ww)));
+            const double x = bh_sample_x(t, cdf, k, ik, wk, uni53(w64(wz, ww)));
             const double ep = x * k;
             q.x = (float)photon_pos(c, p.kx, p.x, p.step, hit);
             q.y = (float)(two_d ? photon_pos(c, p.ky, p.y, p.step, hit) : 0.0);
@@ -175,13 +179,13 @@ __global__ void __launch_bounds__(256, PE_PAIR_MIN_CTAS_SM) k_pair_transport(Tab
             conv = true;
         };
         if constexpr (kFree) {
-            // the trials of the crossing all have probability P: the number of failures before
-            // the first success is geometric, floor(ln U / ln(1 - P)); one draw per photon
-            if (a <= b && P > 0.0) {
+            // the trials of the crossing all have probability P = 1 - exp(-lam): the number of
+            // failures before the first success is geometric, floor(-ln U / lam); one draw per photon
+            if (a <= b && lam > 0.0) {
                 const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)a, kPurBHFree + p.step),
                                               r.seed_lo, r.seed_hi);
                 tests = 1;
-                const double jf = P >= 1.0 ? 0.0 : floor(log(uni53(w64(w.x, w.y))) / log1p(-P));
+                const double jf = floor(-log(uni53(w64(w.x, w.y))) / lam);
                 if (jf <= (double)(b - a)) record(a + (int64_t)jf, w.z, w.w);
             }
         }
