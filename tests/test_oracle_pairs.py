@@ -270,3 +270,31 @@ def test_pair_free_path_equals_direct_in_law():
     assert abs(x1.mean() - x2.mean()) < 5 * math.sqrt(x1.var() / len(x1) + x2.var() / len(x2))
     assert t1[O.PT["N_ENTERED"]] == t2[O.PT["N_ENTERED"]]
     assert t2[O.PT["N_TESTS"]] <= t2[O.PT["N_ENTERED"]] < t1[O.PT["N_TESTS"]]
+
+
+@pytest.mark.parametrize("method", [O.PAIR_DIRECT, O.PAIR_FREE_PATH])
+def test_pair_depth_histogram_is_geometric(method):
+    """With P ~ 0.1 per step (Au at 50x solid density, 10 um steps) the number of steps inside
+    before the conversion follows P (1 - P)^j for j < N_in and the rest pass through: a
+    chi-square over the N_in + 1 outcomes, by either method (a free path that rounded the
+    geometric count up or down by one step would fail it)."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    t = O.Tables(O.table_params(n_eta=16, n_y=16, n_E=65, n_s=65, gamma_max=1e6), [79.0])
+    r = _beam_run(ne_over_nc=4177.0 * 50, dt_over_T=10.0, seed=33)
+    k, n = 1e4, 40000
+    ph = np.zeros(n, dtype=W.PHOTON_RECORD)
+    ph["x"] = -0.5
+    ph["energy"] = k
+    ph["kx"] = 1.0
+    ph["id_mech"] = np.arange(n, dtype=np.uint32)
+    pairs, npairs, tally = O.pair_transport(t, r, ph, step_end=1000, method=method)
+    n_i = 50 * 4177.0 * math.pi / (R_E * 1e-12) / 79.0
+    P = -math.expm1(-n_i * ALPHA * R_E ** 2 * t.bh_sigma_interp(0, k)[0] * 10e-6)
+    assert 0.05 < P < 0.2
+    n_in = 20                                           # steps 1..20 at x = -0.5 + 10 * 2 pi m < 200 um
+    j = pairs["step"].astype(np.int64) - 1
+    assert j.min() >= 0 and j.max() < n_in
+    obs = np.append(np.bincount(j, minlength=n_in), n - npairs).astype(float)
+    exp = n * np.append(P * (1 - P) ** np.arange(n_in), (1 - P) ** n_in)
+    chi2 = float(((obs - exp) ** 2 / exp).sum())
+    assert scipy_stats.chi2.sf(chi2, n_in) > 1e-4, chi2
