@@ -25,7 +25,16 @@ __device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f
 // per-electron operations (no paired form)
 __device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-__device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
+// 1/d for d >= 1 (both uses below): the hardware reciprocal estimate refined by one Newton-Raphson
+// step, r' = r + r (1 - d r), which squares its relative error (about 1 ulp after it); it replaces
+// an IEEE division, whose special-case check and branch cost more than the estimate and two FMAs
+__device__ __forceinline__ float2 rcp2(float2 d) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
+    const float2 e = fma2(neg2(d), r, P2(1.0f));
+    return fma2(r, e, r);
+}
 __device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__log2f(a.x), __log2f(a.y)); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
     return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
@@ -127,7 +136,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float2 ig = rsqrt2(q);
     float2 t1 = (G == FK_PLANE_CP) ? mul2(mul2(h, ez), ig) : P2(0.0f);   // -h B_y / gamma
     float2 t2 = mul2(neg2(mul2(h, ey)), ig);                           // -h B_z / gamma
-    float2 f = div2(P2(2.0f), fma2(t2, t2, fma2(t1, t1, P2(1.0f))));
+    float2 f = mul2(P2(2.0f), rcp2(fma2(t2, t2, fma2(t1, t1, P2(1.0f)))));
     float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
     float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
     float2 p1 = sub2(um1, mul2(um0, t2));
@@ -146,7 +155,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     if (r.enable_ncs) {
         // eta = (gamma - u_x) |E| / E_S for the plane wave
         float2 up = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, P2(1.0f)));
-        float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, div2(up, add2(gamma, Q.u0)), sub2(gamma, Q.u0));
+        float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, mul2(up, rcp2(add2(gamma, Q.u0))), sub2(gamma, Q.u0));
         float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
         float2 eta = mul2(mul2(gm, Emag), P2(c.inv_ES));
         // h(eta): row interpolation in log eta (log2 scaled to the row position by one FMA), the
@@ -204,10 +213,12 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 const float x = comp(xn, k);
                 if (Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min) {
                     Particle<float> P = unpack(Q, k);
+                    const float g_before = gam[k];
                     brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist,
                                          tally);
                     repack(Q, k, P);
-                    set_comp(inv_g, k, 1.0f / gam[k]);
+                    // 1/gamma changes only with an emission (the test alone leaves the electron as it was)
+                    if (gam[k] != g_before) set_comp(inv_g, k, 1.0f / gam[k]);
                 }
             }
         }
