@@ -212,6 +212,12 @@ __device__ __forceinline__ R brems_prob(const TablesDev& t, const RunDevT<R>& r,
     if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
     R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
     R xb = r.c.K_br * sig * (um / gamma);
+    if constexpr (sizeof(R) == 4) {
+        // 1 - e^{-x} by its Taylor series x (1 - x/2 + x^2/6 - x^3/24) for x < 2^-5 (the
+        // truncation is below x^4/120 < 2^-26 relative): the per-step x_b of solid targets
+        // is 1e-6 to 1e-3
+        if (xb < 0x1.0p-5f) return xb * fmaf(xb, fmaf(xb, fmaf(xb, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f), 1.0f);
+    }
     return -m_expm1(-xb);
 }
 
