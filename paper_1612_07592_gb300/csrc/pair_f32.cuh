@@ -208,17 +208,48 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 }
             }
         } else {
+            // Eq. 4 for both electrons: x_b = K sigma_Z(gamma) beta on the paired instructions (row
+            // position in log gamma from log2 by one FMA, clamped below the top node as for h(eta);
+            // beta = |u| / gamma), then per electron in the target its draw and the integer test
+            bool in[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float x = comp(xn, k);
-                if (Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min) {
-                    Particle<float> P = unpack(Q, k);
-                    const float g_before = gam[k];
-                    brems_collide<float>(t, r, sig_tab, id[k], n, P, gam[k], x, 0.0f, st_br[k], pb[k], hist,
-                                         tally);
-                    repack(Q, k, P);
-                    // 1/gamma changes only with an emission (the test alone leaves the electron as it was)
-                    if (gam[k] != g_before) set_comp(inv_g, k, 1.0f / gam[k]);
+                in[k] = Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min;
+            }
+            if (in[0] || in[1]) {
+                const float2 gv = make_float2(gam[0], gam[1]);
+                const float2 tg = fma2(log2v(gv), P2(tc.inv_dln_g * 0.693147180559945309f),
+                                       P2(-tc.ln_g_min * tc.inv_dln_g));
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (in[k] && comp(tg, k) >= tc.g_last) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
+                const float2 tgc = clamp2(tg, 0.0f, tc.g_last - 0x1.0p-10f);
+                const float2 tt = add2(sub2(tgc, P2(0.5f)), P2(0x1.8p23f));
+                const int gx = __float_as_int(tt.x) - 0x4B400000, gy = __float_as_int(tt.y) - 0x4B400000;
+                const float2 w = sub2(tgc, sub2(tt, P2(0x1.8p23f)));
+                const float2 s0 = make_float2(sig_tab[gx], sig_tab[gy]);
+                const float2 s1 = make_float2(sig_tab[gx + 1], sig_tab[gy + 1]);
+                const float2 sig = fma2(w, sub2(s1, s0), s0);
+                const float2 um = sqrt2(fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, mul2(Q.u0, Q.u0))));
+                const float2 xb = mul2(mul2(P2(c.K_br), sig), mul2(um, inv_g));
+                // 1 - e^{-x_b} by its Taylor series x (1 - x/2 + x^2/6 - x^3/24) below 2^-5 (truncation
+                // under 2^-26 relative), the library expm1f above
+                const float2 ser = mul2(xb, fma2(xb, fma2(xb, fma2(xb, P2(-1.0f / 24.0f), P2(1.0f / 6.0f)),
+                                                           P2(-0.5f)), P2(1.0f)));
+                float pb_[2] = {ser.x, ser.y};
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (!in[k]) continue;
+                    if (!(comp(xb, k) < 0x1.0p-5f)) pb_[k] = -expm1f(-comp(xb, k));
+                    const uint4 wd = draw(r, id[k], n, PUR_BREMS);
+                    if (brems_event(pb_[k], wd)) {
+                        Particle<float> P = unpack(Q, k);
+                        take(brems_emit<float>(t, r, id[k], n, P, gam[k], comp(xn, k), 0.0f, wd, hist, tally), P,
+                             gam[k], st_br[k], pb[k]);
+                        repack(Q, k, P);
+                        set_comp(inv_g, k, 1.0f / gam[k]);
+                    }
                 }
             }
         }
