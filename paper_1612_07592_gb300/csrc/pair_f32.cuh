@@ -171,10 +171,12 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         const float2 h0 = make_float2(h_tab[ix], h_tab[iy]), h1 = make_float2(h_tab[ix + 1], h_tab[iy + 1]);
         float2 hv = fma2(w, sub2(h1, h0), h0);
         hv = sel2(eta.x >= tc.eta_min, eta.y >= tc.eta_min, hv, P2(tc.h_classical));
-        // tau -= ncs_coef (eta / gamma) h(eta), compensated
-        float2 dtau = mul2(mul2(P2(c.ncs_coef), mul2(eta, inv_g)), hv);
-        float2 s, e;
-        two_sum2(Q.tau, neg2(dtau), s, e);
+        // tau -= ncs_coef (eta / gamma) h(eta), compensated by Dekker's Fast2Sum (exact for
+        // |tau| >= |dtau|, which holds on every step but the one where tau crosses zero, and
+        // that step emits and resets tau)
+        const float2 ndtau = mul2(mul2(P2(-c.ncs_coef), mul2(eta, inv_g)), hv);
+        const float2 s = add2(Q.tau, ndtau);
+        const float2 e = sub2(ndtau, sub2(s, Q.tau));
         Q.tau = s;
         Q.tau_lo = add2(Q.tau_lo, e);
         float2 tsum = add2(Q.tau, Q.tau_lo);
