@@ -64,9 +64,9 @@ __device__ __forceinline__ void ramp_sincos2(float2 v, float2& s_out, float2& c_
 __device__ __forceinline__ void sincos2(float2 v, float2& s_out, float2& c_out) {
     const float kMagic = 0x1.8p23f;
     const float2 t = fma2(v, P2(0.159154943091895336f), P2(kMagic));    // 2 pi k + ..., k = rint(v / 2 pi)
-    const float2 k = sub2(t, P2(kMagic));
-    float2 r = fma2(neg2(k), P2(6.28318548202514648f), v);              // 2 pi, nearest float
-    r = fma2(neg2(k), P2(-1.74845553e-7f), r);                          // 2 pi - its nearest float
+    const float2 nk = sub2(P2(kMagic), t);                              // -k, exact
+    float2 r = fma2(nk, P2(6.28318548202514648f), v);                   // 2 pi, nearest float
+    r = fma2(nk, P2(-1.74845553e-7f), r);                               // 2 pi - its nearest float
     s_out = make_float2(__sinf(r.x), __sinf(r.y));
     c_out = make_float2(__cosf(r.x), __cosf(r.y));
 }
@@ -129,20 +129,21 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float2 ez = P2(0.0f);
     if (G == FK_PLANE_CP) ez = mul2(P2(c.a0), sub2(mul2(dg, ct), mul2(g, st)));   // a0 (g' cos - g sin)
     // Boris push with E = (0, ey, ez), B = (0, -ez, ey)
+    const float2 mhey = mul2(P2(-0.5f * c.dt), ey);                    // -h E_y (the sign is exact)
     float2 um0 = Q.u0;
-    float2 um1 = sub2(Q.u1, mul2(h, ey));
+    float2 um1 = add2(Q.u1, mhey);
     float2 um2 = (G == FK_PLANE_CP) ? sub2(Q.u2, mul2(h, ez)) : Q.u2;
     float2 q = fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f))));
     float2 ig = rsqrt2(q);
     float2 t1 = (G == FK_PLANE_CP) ? mul2(mul2(h, ez), ig) : P2(0.0f);   // -h B_y / gamma
-    float2 t2 = mul2(neg2(mul2(h, ey)), ig);                           // -h B_z / gamma
+    float2 t2 = mul2(mhey, ig);                                        // -h B_z / gamma
     float2 f = mul2(P2(2.0f), rcp2(fma2(t2, t2, fma2(t1, t1, P2(1.0f)))));
     float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
     float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
     float2 p1 = sub2(um1, mul2(um0, t2));
     float2 p2 = add2(um2, mul2(um0, t1));
     Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
-    Q.u1 = sub2(sub2(um1, mul2(p0, s2)), mul2(h, ey));
+    Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
     Q.u2 = (G == FK_PLANE_CP) ? sub2(add2(um2, mul2(p0, s1)), mul2(h, ez)) : um2;
     // gamma and 1/gamma from one reciprocal square root (1/gamma serves the rate and the
     // position update; emitting lanes refresh it from their new gamma)
