@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from an ncu capture
 # of one 400-step launch on 2e5 electrons of the same physics (7.45 MB: the state once plus the
 # cold emission tables); None once the kernel changes after that capture.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 37.4
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 37.3
 
 
 def peaks():
