@@ -1,11 +1,14 @@
 // pair_f32.cuh -- the FP32 step for the 1D plane-wave field kinds with two
 // electrons per thread.  Blackwell issues paired single-precision arithmetic
 // (FFMA2/FADD2/FMUL2: two FP32 results per instruction), so the common path of
-// the step -- fields, Boris push, eta, rate lookup, optical depth, position --
-// runs on float2 values holding the two electrons, with the operations of the
-// one-electron float step in the same order.  Emissions, the
-// bremsstrahlung test in the slab and the absorbing boundary leave the packed
-// path and run the one-electron code for the electron concerned.
+// the step -- fields, Boris push, eta, rate lookup, optical depth, the
+// bremsstrahlung probability of Eq. 4, position -- runs on float2 values holding
+// the two electrons, with the operations of the one-electron float step in the
+// same order (where a form differs -- a Newton-refined reciprocal for a
+// division, a series for 1 - e^{-x} at small x, Fast2Sum for the optical depth
+// -- the comment at the spot says why it holds).  The draws of the
+// bremsstrahlung test, emissions and the absorbing boundary leave the packed
+// path and run per electron.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
