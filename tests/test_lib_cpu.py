@@ -103,3 +103,30 @@ def test_workloads():
     assert 0.05 < np.mean(ph["kx"] < 0) < 0.15 and np.all(np.abs(ph["kx"]) >= np.cos(0.3) - 1e-6)
     assert ph["energy"].min() >= 1.0 and ph["energy"].max() <= 1e4 and np.all(np.abs(ph["y"]) <= 2.0)
     assert len(np.unique(ph["id_mech"] & 0x7FFFFFFF)) == 2000
+
+
+def test_constants_match_header(tmp_path):
+    """Every constant the binding passes across the boundary (status codes, enums, tally word
+    indices, sizes) equals the header's value, read by compiling the header."""
+    names = {"PE_OK": pe.PE_OK, "PE_ERR_ARG": pe.PE_ERR_ARG, "PE_ERR_CUDA": pe.PE_ERR_CUDA,
+             "PE_ERR_NOMEM": pe.PE_ERR_NOMEM, "PE_ERR_BUFFER_FULL": pe.PE_ERR_BUFFER_FULL,
+             "PE_ERR_TABLE_RANGE": pe.PE_ERR_TABLE_RANGE, "PE_ERR_TIMEOUT": pe.PE_ERR_TIMEOUT,
+             "PE_ERR_STATE": pe.PE_ERR_STATE, "PE_LP_Y": pe.PE_LP_Y, "PE_CP": pe.PE_CP,
+             "PE_PLANE_1D": pe.PE_PLANE_1D, "PE_GAUSS_2D": pe.PE_GAUSS_2D, "PE_CONST": pe.PE_CONST,
+             "PE_PIC_1D": pe.PE_PIC_1D, "PE_F64": pe.PE_F64, "PE_F32": pe.PE_F32, "PE_REST": pe.PE_REST,
+             "PE_MAXWELL_JUTTNER": pe.PE_MAXWELL_JUTTNER, "PE_BEAM": pe.PE_BEAM, "PE_CALLER": pe.PE_CALLER,
+             "PE_BREMS_DIRECT": pe.PE_BREMS_DIRECT, "PE_BREMS_NULL": pe.PE_BREMS_NULL,
+             "PE_WAIT_NEVER": pe.PE_WAIT_NEVER, "PE_PIC_MAX_CELLS": pe.PE_PIC_MAX_CELLS,
+             "PE_PAIR_DIRECT": pe.PE_PAIR_DIRECT, "PE_PAIR_FREE_PATH": pe.PE_PAIR_FREE_PATH,
+             "PE_PAIR_TALLY_WORDS": pe.PAIR_TALLY_WORDS}
+    names.update({"PE_T_" + k: v for k, v in pe.T.items()})
+    names.update({"PE_PT_" + k: v for k, v in pe.PT.items()})
+    prog = tmp_path / "consts.c"
+    body = "".join(f'printf("{n} %lld\\n", (long long)({n}));' for n in names)
+    prog.write_text('#include <stdio.h>\n#include "pe.h"\nint main(void){' + body + "return 0;}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    bad = {n: (int(got[n]), v) for n, v in names.items() if int(got[n]) != int(v)}
+    assert not bad, bad
