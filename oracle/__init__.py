@@ -90,9 +90,25 @@ def lib():
                 getattr(L, name).argtypes = [C.c_double, C.c_double]
                 getattr(L, name).restype = C.c_double
             for name in ("or_int_k53", "or_ncs_power_integral", "or_ncs_h_direct", "or_coulomb_f",
-                         "or_schwinger_field", "or_critical_density"):
+                         "or_schwinger_field", "or_critical_density", "or_int_k13", "or_bw_T_direct"):
                 getattr(L, name).argtypes = [C.c_double]
                 getattr(L, name).restype = C.c_double
+            L.or_bw_G.argtypes = [C.c_double, C.c_double]
+            L.or_bw_G.restype = C.c_double
+            L.or_chi_photon.argtypes = [dp, dp, dp, C.c_double]
+            L.or_chi_photon.restype = C.c_double
+            L.or_bw_tables_build.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
+            L.or_bw_tables_build.restype = C.c_void_p
+            L.or_bw_tables_free.argtypes = [C.c_void_p]
+            L.or_bw_tables_export.argtypes = [C.c_void_p, C.c_int, dp, C.c_int64]
+            L.or_bw_tables_export.restype = C.c_int64
+            L.or_bw_T_interp.argtypes = [C.c_void_p, C.c_double, C.POINTER(C.c_int)]
+            L.or_bw_T_interp.restype = C.c_double
+            L.or_bw_sample_x.argtypes = [C.c_void_p, C.c_double, C.c_double]
+            L.or_bw_sample_x.restype = C.c_double
+            L.or_bw_transport.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(RunParams), C.c_void_p, C.c_int64,
+                                          C.c_int64, C.c_void_p, C.c_int64, C.POINTER(C.c_uint64)]
+            L.or_bw_transport.restype = C.c_int
             L.or_ncs_F.argtypes = [C.c_double, C.c_double]
             L.or_ncs_F.restype = C.c_double
             L.or_brems_dcs_raw.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
@@ -312,6 +328,60 @@ def pair_transport(tables: Tables, run: RunParams, photons, step_end: int, capac
     return pairs[:min(n, capacity)], n, tally
 
 
+class BWTables:
+    """Breit-Wheeler tables (see oracle.h): T(chi) on n_chi log-spaced chi in [chi_min, chi_max]
+    and the CDF of the pair spectrum over the positron fraction x at n_x nodes."""
+
+    def __init__(self, n_chi: int = 64, chi_min: float = 1e-2, chi_max: float = 1e3, n_x: int = 128):
+        self.n_chi, self.n_x, self.chi_min, self.chi_max = n_chi, n_x, chi_min, chi_max
+        self._h = lib().or_bw_tables_build(n_chi, chi_min, chi_max, n_x)
+        if not self._h:
+            raise ValueError("bad Breit-Wheeler table parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_bw_tables_free(h)
+            self._h = None
+
+    def export(self, which: int) -> np.ndarray:
+        n = self.n_chi if which == 0 else self.n_chi * self.n_x
+        out = np.zeros(n)
+        if lib().or_bw_tables_export(self._h, which, _dp(out), n) != n:
+            raise ValueError(which)
+        return out if which == 0 else out.reshape(self.n_chi, self.n_x)
+
+    def T_interp(self, chi: float):
+        fl = C.c_int(0)
+        v = lib().or_bw_T_interp(self._h, chi, C.byref(fl))
+        return v, fl.value
+
+    def sample_x(self, chi: float, R: float) -> float:
+        return lib().or_bw_sample_x(self._h, chi, R)
+
+
+def bw_transport(bw: BWTables, tables: Tables, run: RunParams, photons, step_end: int, capacity: int = 1 << 20):
+    """Breit-Wheeler conversion of the photon records (PHOTON_DTYPE) in the run's prescribed fields up
+    to step_end (see oracle.h); returns (pairs, true pair count, tally)."""
+    ph = np.ascontiguousarray(photons, dtype=PHOTON_DTYPE)
+    pairs = np.zeros(capacity, dtype=PAIR_DTYPE)
+    tally = np.zeros(PAIR_TALLY_WORDS, dtype=np.uint64)
+    rc = lib().or_bw_transport(bw._h, tables._h, C.byref(run), ph.ctypes.data_as(C.c_void_p), len(ph),
+                               int(step_end), pairs.ctypes.data_as(C.c_void_p), capacity,
+                               tally.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc != 0:
+        raise RuntimeError("or_bw_transport failed")
+    n = int(tally[PT["N_PAIRS"]])
+    return pairs[:min(n, capacity)], n, tally
+
+
+def chi_photon(kvec, E, B, E_S: float) -> float:
+    kvec = np.ascontiguousarray(kvec, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    return lib().or_chi_photon(_dp(kvec), _dp(E), _dp(B), E_S)
+
+
 def fixed_to_float(tally: np.ndarray, idx: int) -> float:
     """Value of a 128-bit fixed-point tally pair (lo, hi) in m c^2."""
     return float(int(tally[idx + 1])) + float(int(tally[idx])) / 2.0 ** 64
@@ -408,7 +478,8 @@ def __getattr__(name):
          "coulomb_f": "or_coulomb_f", "brems_dcs_raw": "or_brems_dcs_raw",
          "brems_sigma_direct": "or_brems_sigma_direct", "schwinger_field": "or_schwinger_field",
          "bh_dcs_raw": "or_bh_dcs_raw", "bh_sigma_direct": "or_bh_sigma_direct",
-         "critical_density": "or_critical_density"}
+         "critical_density": "or_critical_density", "int_k13": "or_int_k13", "bw_G": "or_bw_G",
+         "bw_T_direct": "or_bw_T_direct"}
     if name in m:
         return getattr(lib(), m[name])
     raise AttributeError(name)

@@ -89,6 +89,32 @@ double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* abov
 double or_bh_sigma_interp(const or_tables* t, int iz, double k, int* above);
 double or_sample_bh_x(const or_tables* t, int iz, double k, double R);
 
+/* ---- Breit-Wheeler pair production in the laser field ----------------------
+ * Sec. 1 names the process; as for the NCS module the rate is that of a locally
+ * constant crossed field.  For a photon of energy k (m c^2) with quantum
+ * parameter chi (or_chi_photon) the pair rate per unit time (1/omega_L) is
+ *   W = alpha E_S T(chi) / k,   T(chi) = (1/(sqrt 3 pi)) int_0^1 G(chi, x) dx,
+ *   G(chi, x) = (x/(1-x) + (1-x)/x) K_{2/3}(xi) + int_xi^inf K_{1/3}(t) dt,
+ *   xi = 2 / (3 chi x (1 - x)),
+ * x the positron's share of k (E_S = m c^2 / (hbar omega_L) in these units).   */
+double or_int_k13(double x);                      /* int_x^inf K_{1/3}(t) dt     */
+double or_bw_G(double chi, double x);
+double or_bw_T_direct(double chi);                /* by quadrature (no table)    */
+/* chi = sqrt((k E + kvec x B)^2 - (kvec . E)^2) / E_S for the photon momentum kvec
+ * (|kvec| = k): the electron's eta with u -> kvec and gamma -> k                */
+double or_chi_photon(const double kvec[3], const double E[3], const double B[3], double E_S);
+/* tables: T(chi_i) on n_chi log-spaced chi in [chi_min, chi_max] and the CDF of G
+ * over x at n_x nodes x_j = (1 - cos(pi j/(n_x - 1)))/2 (clustered at both ends).
+ * which: 0 = T [n_chi], 1 = CDF [n_chi * n_x].                                  */
+typedef struct or_bw_tables or_bw_tables;
+or_bw_tables* or_bw_tables_build(int n_chi, double chi_min, double chi_max, int n_x);
+void or_bw_tables_free(or_bw_tables* t);
+int64_t or_bw_tables_export(const or_bw_tables* t, int which, double* out, int64_t cap);
+/* ln T linear in ln chi; 0 below the table (flag -1), the last node above (flag 1) */
+double or_bw_T_interp(const or_bw_tables* t, double chi, int* flag);
+/* x from the CDF rows interpolated at chi, inverted linearly in s = acos(1-2x)/pi */
+double or_bw_sample_x(const or_bw_tables* t, double chi, double R);
+
 /* ---- run description ------------------------------------------------------- */
 enum { OR_LP_Y = 0, OR_CP = 1 };
 enum { OR_PLANE_1D = 0, OR_GAUSS_2D = 1, OR_CONST = 2, OR_PIC_1D = 3 };
@@ -218,6 +244,21 @@ enum { OR_PAIR_DIRECT = 0, OR_PAIR_FREE_PATH = 1 };
  * tests tally then counts draws.  Returns -1 for an unknown method.                      */
 int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photon* photons, int64_t n_photons,
                       int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally, int method);
+
+/* ---- Breit-Wheeler conversion of the emitted photons in the laser field ----
+ * Each photon record (k > 2 m c^2) moves at c along its direction from its
+ * emission point; at step m (n_e < m < step_end) it is at x_e + k^ (m - n_e) c dt
+ * and the fields there at t = m dt give its chi (or_chi_photon, kvec = k k^).
+ * tau_0 = -ln U, U the u53 of words 0-1 of the draw (id_mech, run id, n_e,
+ * 0x60000000 + n_e), falls by alpha E_S T(chi) dt / k per step (T from the table,
+ * or_bw_T_interp); at the first step with tau <= 0 the photon converts: x from
+ * words 0-1 of the draw (id_mech, run id, m, 0x70000000 + n_e) by or_bw_sample_x,
+ * E+ = x k, E- = k - E+, both along k^, at the photon's position.  The tally
+ * words are those of the Bethe-Heitler transport with: [1] photons followed,
+ * [2] photon-steps with chi above the table, [3] photon-steps taken.  Not for
+ * OR_PIC_1D runs (returns -1).                                                */
+int or_bw_transport(const or_bw_tables* bt, const or_tables* t, const or_run_params* r, const or_photon* photons,
+                    int64_t n_photons, int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally);
 
 /* normalised helpers (exposed for unit pins) */
 double or_schwinger_field(double lambda_m);   /* E_S in m c omega / e          */

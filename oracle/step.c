@@ -857,3 +857,87 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Photon quantum parameter: the electron's eta with u -> kvec, gamma -> |k|, */
+/* in the same cancellation-safe arrangement (k - k_x = k_perp^2/(k + k_x)).  */
+/* ------------------------------------------------------------------------- */
+double or_chi_photon(const double kv[3], const double E[3], const double B[3], double E_S) {
+    double k = sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+    double gm = (kv[0] > 0.0) ? (kv[1] * kv[1] + kv[2] * kv[2]) / (k + kv[0]) : k - kv[0];
+    double dB[3] = {B[0], B[1] + E[2], B[2] - E[1]};
+    double V[3] = {gm * E[0] + (kv[1] * dB[2] - kv[2] * dB[1]),
+                   gm * E[1] + (kv[2] * dB[0] - kv[0] * dB[2]),
+                   gm * E[2] + (kv[0] * dB[1] - kv[1] * dB[0])};
+    double kE = kv[0] * E[0] + kv[1] * E[1] + kv[2] * E[2];
+    double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2] + 2.0 * V[0] * kE;
+    return q > 0.0 ? sqrt(q) / E_S : 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Breit-Wheeler pair production of the photons in the laser field.  Each     */
+/* photon moves at c along its direction from its emission point; at step m   */
+/* (n_e < m < step_end) it is at p_m = x_e + k^ (m - n_e) c dt, where the     */
+/* fields at (p_m, t_m = m dt) give its chi.  An optical depth tau_0 = -ln U  */
+/* falls by W(chi, k) dt per step and the photon converts at the first step   */
+/* where it is <= 0: the per-step optical-depth method of the NCS module.     */
+/* Photons do not feel the fields, so following each one after the run       */
+/* equals stepping it with the electrons (prescribed fields).                 */
+/* ------------------------------------------------------------------------- */
+#define PUR_BW_TAU 0x60000000u   /* tau_0: counter (id_mech, run id, n_e, PUR_BW_TAU + n_e) */
+#define PUR_BW_X 0x70000000u     /* x at the conversion step m: (id_mech, run id, m, PUR_BW_X + n_e) */
+
+int or_bw_transport(const or_bw_tables* bt, const or_tables* t, const or_run_params* r, const or_photon* photons,
+                    int64_t n_photons, int64_t step_end, or_pair* pairs, int64_t cap, uint64_t* tally) {
+    if (r->geometry == OR_PIC_1D) return -1;     /* self-consistent fields are not stored */
+    run_ctx c;
+    make_ctx(t, r, &c, or__photon_min(t));
+    for (int k = 0; k < ORP_WORDS; ++k) tally[k] = 0;
+    const int two_d = (r->geometry == OR_GAUSS_2D);
+    const double coef = C_ALPHA * c.E_S * c.dt;          /* W dt = coef T(chi) / k */
+    uint32_t key[2] = {(uint32_t)(r->seed & 0xffffffffu), (uint32_t)(r->seed >> 32)};
+    for (int64_t j = 0; j < n_photons; ++j) {
+        const or_photon* ph = photons + j;
+        double k = (double)ph->energy;
+        if (!(k > 2.0)) continue;
+        double kx = (double)ph->kx, ky = (double)ph->ky, kz = (double)ph->kz;
+        double kvec[3] = {k * kx, k * ky, k * kz};
+        double xe = (double)ph->x, ye = (double)ph->y;
+        int64_t ne = (int64_t)ph->step;
+        uint32_t ctr[4] = {ph->id_mech, r->run_id, (uint32_t)ne, PUR_BW_TAU + (uint32_t)ne};
+        uint32_t w[4];
+        or_philox4x32_10(ctr, key, w);
+        double tau = -log(u53(word64(w[0], w[1])));
+        tally[ORP_N_ENTERED]++;
+        for (int64_t m = ne + 1; m < step_end; ++m) {
+            double tt = (double)(m - ne) * c.dt;
+            double px = fma(kx, tt, xe), py = fma(ky, tt, ye);
+            double E[3], B[3];
+            or_fields(r, px, py, (double)m * c.dt, E, B);
+            double chi = or_chi_photon(kvec, E, B, c.E_S);
+            int fl;
+            double T = or_bw_T_interp(bt, chi, &fl);
+            tally[ORP_N_TESTS]++;
+            if (fl == 1) tally[ORP_N_K_ABOVE]++;
+            tau -= coef * T / k;
+            if (tau <= 0.0) {
+                uint32_t cx[4] = {ph->id_mech, r->run_id, (uint32_t)m, PUR_BW_X + (uint32_t)ne};
+                or_philox4x32_10(cx, key, w);
+                double x = or_bw_sample_x(bt, chi, u53(word64(w[0], w[1])));
+                double ep = x * k;
+                int64_t q = (int64_t)tally[ORP_N_PAIRS]++;
+                fx_add(tally + ORP_E_PAIRS, k);
+                fx_add(tally + ORP_E_POSITRONS, ep);
+                if (q < cap) {
+                    or_pair* o = pairs + q;
+                    o->x = (float)px; o->y = (float)(two_d ? py : 0.0);
+                    o->e_minus = (float)(k - ep); o->e_plus = (float)ep;
+                    o->kx = ph->kx; o->ky = ph->ky; o->kz = ph->kz;
+                    o->step = (uint32_t)m; o->photon = (uint32_t)j; o->id_mech = ph->id_mech;
+                }
+                break;
+            }
+        }
+    }
+    return 0;
+}

@@ -603,3 +603,122 @@ double or_sample_bh_x(const or_tables* t, int iz, double k, double R) {
     else s = ((double)j + fr) / (double)(p->n_s - 1);
     return 1.0 / k + s * (1.0 - 2.0 / k);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Breit-Wheeler pair production of a photon in a locally constant crossed    */
+/* field (Sec. 1 names the process; the rate is the one of the same LCFA      */
+/* model as the NCS module).  Per unit positron energy fraction x, with       */
+/* xi = 2 / (3 chi x (1 - x)):                                                */
+/*   G(chi, x) = (x/(1-x) + (1-x)/x) K_{2/3}(xi) + int_xi^inf K_{1/3}(t) dt   */
+/* and the rate W = alpha (m c^2/hbar) (m c^2 / (hbar omega)) T(chi),         */
+/*   T(chi) = (1 / (sqrt 3 pi)) int_0^1 G(chi, x) dx.                         */
+/* ------------------------------------------------------------------------- */
+double or_int_k13(double x) { return bessel_common(1.0 / 3.0, x, 1); }
+
+double or_bw_G(double chi, double x) {
+    if (!(chi > 0.0) || !(x > 0.0) || !(x < 1.0)) return 0.0;
+    double xi = 2.0 / (3.0 * chi * x * (1.0 - x));
+    if (xi > 700.0) return 0.0;                  /* below 1e-300 of the peak */
+    return (x / (1.0 - x) + (1.0 - x) / x) * or_bessel_k(2.0 / 3.0, xi) + or_int_k13(xi);
+}
+
+/* the x grid of the tables: x_j = (1 - cos(pi s_j)) / 2, s_j = j / (n - 1), which
+ * clusters the nodes at both ends where the spectrum of large chi peaks */
+static double bw_x_of_s(double s) { return 0.5 * (1.0 - cos(M_PI * s)); }
+
+typedef struct { double chi; } bw_ctx;
+static double bw_integrand_s(double s, const void* vc) {
+    const bw_ctx* c = (const bw_ctx*)vc;
+    return or_bw_G(c->chi, bw_x_of_s(s)) * 0.5 * M_PI * sin(M_PI * s);      /* dx = (pi/2) sin(pi s) ds */
+}
+
+/* int_0^1 G dx over the cells of an n-node s grid, each cell by a fixed 15-point
+ * Gauss-Kronrod rule on two halves (G is smooth in s within a cell; a fixed rule keeps
+ * the cost bounded where the nested Bessel quadratures carry rounding noise), cumulative
+ * values into row if given (row[0] = 0) */
+static double bw_cumulate(double chi, int n, double* row) {
+    bw_ctx c = {chi};
+    double cum = 0.0;
+    if (row) row[0] = 0.0;
+    for (int j = 1; j < n; ++j) {
+        double a = (double)(j - 1) / (double)(n - 1), b = (double)j / (double)(n - 1), m = 0.5 * (a + b);
+        double k1, g1, m1, k2, g2, m2;
+        gk15(bw_integrand_s, &c, a, m, &k1, &g1, &m1);
+        gk15(bw_integrand_s, &c, m, b, &k2, &g2, &m2);
+        cum += k1 + k2;
+        if (row) row[j] = cum;
+    }
+    return cum;
+}
+
+/* by the same rule on 256 cells (no table) */
+double or_bw_T_direct(double chi) {
+    if (!(chi > 0.0)) return 0.0;
+    return bw_cumulate(chi, 257, NULL) / (sqrt(3.0) * M_PI);
+}
+
+struct or_bw_tables {
+    int n_chi, n_x;
+    double chi_min, chi_max;
+    double* T;        /* [n_chi] T(chi_i), chi_i log spaced on [chi_min, chi_max] */
+    double* cdf;      /* [n_chi][n_x] normalised cumulative G over x_j            */
+};
+
+or_bw_tables* or_bw_tables_build(int n_chi, double chi_min, double chi_max, int n_x) {
+    if (n_chi < 2 || n_x < 2 || !(chi_min > 0.0) || !(chi_max > chi_min)) return NULL;
+    or_bw_tables* t = (or_bw_tables*)calloc(1, sizeof(or_bw_tables));
+    t->n_chi = n_chi; t->n_x = n_x; t->chi_min = chi_min; t->chi_max = chi_max;
+    t->T = (double*)calloc((size_t)n_chi, sizeof(double));
+    t->cdf = (double*)calloc((size_t)n_chi * n_x, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n_chi; ++i) {
+        double chi = grid_log(chi_min, chi_max, i, n_chi);
+        double* row = t->cdf + (int64_t)i * n_x;
+        double tot = bw_cumulate(chi, n_x, row);
+        t->T[i] = tot / (sqrt(3.0) * M_PI);
+        for (int j = 0; j < n_x; ++j) row[j] = tot > 0.0 ? row[j] / tot : (double)j / (double)(n_x - 1);
+    }
+    return t;
+}
+
+void or_bw_tables_free(or_bw_tables* t) {
+    if (!t) return;
+    free(t->T); free(t->cdf); free(t);
+}
+
+int64_t or_bw_tables_export(const or_bw_tables* t, int which, double* out, int64_t cap) {
+    int64_t n = which == 0 ? t->n_chi : which == 1 ? (int64_t)t->n_chi * t->n_x : -1;
+    if (n < 0 || n > cap) return -1;
+    memcpy(out, which == 0 ? t->T : t->cdf, (size_t)n * sizeof(double));
+    return n;
+}
+
+/* T(chi) between nodes: ln(T e^{8/(3 chi)}) linear in ln chi (the factor takes out the
+ * exponential of the small-chi limit, which no polynomial in ln chi follows); 0 below the
+ * table (flag -1), the last node above it (flag 1) */
+double or_bw_T_interp(const or_bw_tables* t, double chi, int* flag) {
+    if (!(chi >= t->chi_min)) { *flag = -1; return 0.0; }
+    int i; double w;
+    row_pos(chi, t->chi_min, t->chi_max, t->n_chi, &i, &w, flag);
+    if (*flag == 1) return t->T[t->n_chi - 1];
+    double ca = grid_log(t->chi_min, t->chi_max, i, t->n_chi), cb = grid_log(t->chi_min, t->chi_max, i + 1, t->n_chi);
+    double la = log(t->T[i]) + 8.0 / (3.0 * ca), lb = log(t->T[i + 1]) + 8.0 / (3.0 * cb);
+    return exp((1.0 - w) * la + w * lb - 8.0 / (3.0 * chi));
+}
+
+/* positron energy fraction x from the CDF rows interpolated at chi (weights linear
+ * in ln chi, clamped to the table), inverted linearly in s between nodes */
+double or_bw_sample_x(const or_bw_tables* t, double chi, double R) {
+    int i, fl; double w;
+    if (!(chi >= t->chi_min)) chi = t->chi_min;
+    row_pos(chi, t->chi_min, t->chi_max, t->n_chi, &i, &w, &fl);
+    const double* ra = t->cdf + (int64_t)i * t->n_x;
+    const double* rb = ra + t->n_x;
+    double c0, fr; int j;
+    invert_row(ra, rb, w, t->n_x, R, &c0, &j, &fr);
+    double s;
+    if (j < 0) s = 0.0;
+    else if (j >= t->n_x - 1) s = 1.0;
+    else s = ((double)j + fr) / (double)(t->n_x - 1);
+    return bw_x_of_s(s);
+}
