@@ -371,6 +371,21 @@ enum { PE_PAIR_DIRECT = 0, PE_PAIR_FREE_PATH = 1 };
 pe_status pe_pair_transport(pe_run* run, const void* photons, int64_t n_photons, int64_t step_end, void* pairs,
                             int64_t capacity, void* tally, int method);
 
+/* Breit-Wheeler pair production of a photon in the laser field (Sec. 1 names the
+ * process; its rate is the one of a locally constant crossed field, the model of
+ * the NCS module): a photon of energy k (m c^2) with quantum parameter
+ * chi = sqrt((k E + kvec x B)^2 - (kvec . E)^2) / E_S makes pairs at the rate
+ *   W = alpha (m c^2/hbar) T(chi) / k,   T(chi) = (1/(sqrt 3 pi)) int_0^1 G dx,
+ *   G(chi, x) = (x/(1-x) + (1-x)/x) K_{2/3}(xi) + int_xi^inf K_{1/3}(t) dt,
+ *   xi = 2 / (3 chi x (1 - x)), x the positron's share of k.
+ * Computed on the host (no device needed):
+ *   T   : n_chi doubles, T(chi_i) for chi_i log spaced on [chi_min, chi_max]
+ *   cdf : n_chi * n_x doubles (row i = chi_i), the normalised cumulative integral
+ *         of G over x at the nodes x_j = (1 - cos(pi j / (n_x - 1))) / 2
+ * Both arrays belong to the caller.  Errors: PE_ERR_ARG (null, n_chi or n_x
+ * outside [2, 4096], not 0 < chi_min < chi_max).                                */
+pe_status pe_bw_tables_host(int n_chi, double chi_min, double chi_max, int n_x, double* T, double* cdf);
+
 /* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */
 double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);

@@ -44,7 +44,8 @@ PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, N_TESTS=3, E_PAIRS=4, E_POSITRONS
 PE_PAIR_DIRECT, PE_PAIR_FREE_PATH = 0, 1
 EXPORTED = ["pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles", "pe_step",
             "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch", "pe_graph_destroy",
-            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport", "pe_resume_particles"]
+            "pe_a0_from_intensity", "pe_launch_count", "pe_last_error", "pe_pair_transport", "pe_resume_particles",
+            "pe_bw_tables_host"]
 
 
 class PeError(RuntimeError):
@@ -126,6 +127,8 @@ def lib():
             L.pe_pair_transport.argtypes = [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp, C.c_int]
             L.pe_resume_particles.argtypes = [vp, C.POINTER(RunParams), C.c_int64, C.POINTER(Buffers), C.c_int64, vp,
                                               C.POINTER(vp)]
+            L.pe_bw_tables_host.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
@@ -133,7 +136,7 @@ def lib():
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
                          "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map",
-                         "pe_pair_transport", "pe_resume_particles"):
+                         "pe_pair_transport", "pe_resume_particles", "pe_bw_tables_host"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -266,6 +269,15 @@ def pe_pair_transport(run: int, photons_ptr: int, n_photons: int, step_end: int,
                       tally_ptr: int, method: int = PE_PAIR_DIRECT) -> None:
     _check(lib().pe_pair_transport(run, photons_ptr, int(n_photons), int(step_end), pairs_ptr, int(capacity),
                                    tally_ptr, int(method)))
+
+
+def pe_bw_tables_host(n_chi: int, chi_min: float, chi_max: float, n_x: int):
+    """Breit-Wheeler tables built on the host: (T [n_chi], CDF [n_chi, n_x]); see pe.h."""
+    T = np.zeros(n_chi)
+    cdf = np.zeros(n_chi * n_x)
+    _check(lib().pe_bw_tables_host(int(n_chi), float(chi_min), float(chi_max), int(n_x),
+                                   T.ctypes.data_as(C.POINTER(C.c_double)), cdf.ctypes.data_as(C.POINTER(C.c_double))))
+    return T, cdf.reshape(n_chi, n_x)
 
 
 def pe_destroy(run: int):

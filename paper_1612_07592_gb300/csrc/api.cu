@@ -75,6 +75,16 @@ extern "C" double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polar
     return polarisation == PE_CP ? a / std::sqrt(2.0) : a;
 }
 
+extern "C" pe_status pe_bw_tables_host(int n_chi, double chi_min, double chi_max, int n_x, double* T,
+                                        double* cdf) {
+    if (!T || !cdf) return fail(PE_ERR_ARG, "pe_bw_tables_host: null argument");
+    if (n_chi < 2 || n_x < 2 || n_chi > 4096 || n_x > 4096 || !(chi_min > 0.0) || !(chi_max > chi_min) ||
+        !std::isfinite(chi_max))
+        return fail(PE_ERR_ARG, "pe_bw_tables_host: need 2 <= n_chi, n_x <= 4096 and 0 < chi_min < chi_max");
+    build_host_bw_tables(n_chi, chi_min, chi_max, n_x, T, cdf);
+    return PE_OK;
+}
+
 extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out) {
     if (!p || !out) return fail(PE_ERR_ARG, "pe_create_tables: null argument");
     *out = nullptr;

@@ -161,6 +161,8 @@ struct HostTables {
 bool build_host_tables(const pe_table_params& p, HostTables& out, std::string* err);
 // Bethe-Heitler tables of the same parameters: sigma_BH [n_Z * n_E], CDF [n_Z * n_E * n_s]
 void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::vector<double>& cdf);
+// Breit-Wheeler tables on the host: T(chi_i) [n_chi] and the CDF over x_j [n_chi * n_x]
+void build_host_bw_tables(int n_chi, double chi_min, double chi_max, int n_x, double* T, double* cdf);
 
 // kernels_pair.cu: Bethe-Heitler conversion of photon records in the run's target
 void launch_pair_transport(const TablesDev& t, const RunDev& r, const void* photons, int64_t n_photons,

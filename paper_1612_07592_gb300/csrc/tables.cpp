@@ -344,3 +344,63 @@ void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::
 }
 
 }  // namespace pe
+
+// ---- Breit-Wheeler tables ---------------------------------------------------------
+// Pair production of a photon in a locally constant crossed field: per unit positron
+// energy fraction x, G(chi, x) = (x/(1-x) + (1-x)/x) K_{2/3}(xi) + int_xi^inf K_{1/3},
+// xi = 2 / (3 chi x (1 - x)); the rate is alpha (m c^2/hbar)(m c^2/(hbar omega)) T(chi),
+// T = (1/(sqrt 3 pi)) int_0^1 G dx.
+namespace pe {
+namespace {
+
+// trapezoid over t of exp(-x cosh t) g(t) with a step small against the width 1/sqrt(x) of
+// the integrand at large x (the error falls as exp(-2 pi^2 / (x h^2)))
+template <class G>
+double trap_bessel_fine(double x, double nu, const G& g) {
+    const double h = std::min(0.2, 0.5 / std::sqrt(x));
+    double T = h;
+    while (x * (std::cosh(T) - 1.0) - nu * T < 50.0) T += h;
+    double s = 0.5 * std::exp(-x) * g(0.0);
+    for (int k = 1; k * h <= T; ++k) {
+        const double t = k * h;
+        s += std::exp(-x * std::cosh(t)) * g(t);
+    }
+    return s * h;
+}
+
+double bw_G(double chi, double x) {
+    if (!(x > 0.0) || !(x < 1.0)) return 0.0;
+    const double xi = 2.0 / (3.0 * chi * x * (1.0 - x));
+    if (xi > 700.0) return 0.0;
+    const double k23 = trap_bessel_fine(xi, 2.0 / 3.0, [](double t) { return std::cosh(2.0 * t / 3.0); });
+    const double ik13 = trap_bessel_fine(xi, 1.0 / 3.0, [](double t) { return std::cosh(t / 3.0) / std::cosh(t); });
+    return (x / (1.0 - x) + (1.0 - x) / x) * k23 + ik13;
+}
+
+// cumulative int G dx over the cells of the node grid x_j = (1 - cos(pi s_j))/2, s_j = j/(n-1),
+// integrated in s (dx = (pi/2) sin(pi s) ds), two 8-point Gauss panels per cell
+void bw_row(double chi, int n, double* row, double* T) {
+    const auto f = [chi](double s) {
+        return bw_G(chi, 0.5 * (1.0 - std::cos(M_PI * s))) * 0.5 * M_PI * std::sin(M_PI * s);
+    };
+    double cum = 0.0;
+    row[0] = 0.0;
+    for (int j = 1; j < n; ++j) {
+        cum += gauss8_panels(f, (double)(j - 1) / (n - 1), (double)j / (n - 1), 2);
+        row[j] = cum;
+    }
+    *T = cum / (std::sqrt(3.0) * M_PI);
+    for (int j = 0; j < n; ++j) row[j] = cum > 0.0 ? row[j] / cum : (double)j / (n - 1);
+}
+
+}  // namespace
+
+void build_host_bw_tables(int n_chi, double chi_min, double chi_max, int n_x, double* T, double* cdf) {
+    const double l0 = std::log(chi_min), l1 = std::log(chi_max);
+    parallel_for(n_chi, [&](int i) {
+        const double chi = std::exp(l0 + (l1 - l0) * i / (n_chi - 1));
+        bw_row(chi, n_x, cdf + (size_t)i * n_x, T + i);
+    });
+}
+
+}  // namespace pe

@@ -130,3 +130,17 @@ def test_constants_match_header(tmp_path):
                                                         check=True).stdout.splitlines())
     bad = {n: (int(got[n]), v) for n, v in names.items() if int(got[n]) != int(v)}
     assert not bad, bad
+
+
+def test_bw_tables_host_match_oracle(libpath):
+    """The library's Breit-Wheeler tables (its own Bessel trapezoid and Gauss panels, built on the
+    host) equal the oracle's (adaptive Gauss-Kronrod Bessel functions): T to 1e-8, the CDF to 1e-9."""
+    import oracle as O
+    T, cdf = pe.pe_bw_tables_host(24, 1e-2, 1e3, 64)
+    bw = O.BWTables(24, 1e-2, 1e3, 64)
+    np.testing.assert_allclose(T, bw.export(0), rtol=1e-8)
+    np.testing.assert_allclose(cdf, bw.export(1), rtol=0, atol=1e-9)
+    for bad in ((1, 1e-2, 1e3, 64), (24, 0.0, 1e3, 64), (24, 1e-2, 1e-3, 64), (24, 1e-2, 1e3, 5000)):
+        with pytest.raises(pe.PeError) as e:
+            pe.pe_bw_tables_host(*bad)
+        assert e.value.status == pe.PE_ERR_ARG
