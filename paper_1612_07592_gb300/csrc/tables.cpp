@@ -380,8 +380,9 @@ double bw_G(double chi, double x) {
 // cumulative int G dx over the cells of the node grid x_j = (1 - cos(pi s_j))/2, s_j = j/(n-1),
 // integrated in s (dx = (pi/2) sin(pi s) ds), two 8-point Gauss panels per cell
 void bw_row(double chi, int n, double* row, double* T) {
+    constexpr double kPi = 3.14159265358979323846;
     const auto f = [chi](double s) {
-        return bw_G(chi, 0.5 * (1.0 - std::cos(M_PI * s))) * 0.5 * M_PI * std::sin(M_PI * s);
+        return bw_G(chi, 0.5 * (1.0 - std::cos(kPi * s))) * 0.5 * kPi * std::sin(kPi * s);
     };
     double cum = 0.0;
     row[0] = 0.0;
@@ -389,7 +390,7 @@ void bw_row(double chi, int n, double* row, double* T) {
         cum += gauss8_panels(f, (double)(j - 1) / (n - 1), (double)j / (n - 1), 2);
         row[j] = cum;
     }
-    *T = cum / (std::sqrt(3.0) * M_PI);
+    *T = cum / (std::sqrt(3.0) * kPi);
     for (int j = 0; j < n; ++j) row[j] = cum > 0.0 ? row[j] / cum : (double)j / (n - 1);
 }
 
