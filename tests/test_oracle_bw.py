@@ -9,14 +9,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1612_07592_gb300 import workloads as W
 
 ALPHA = 7.2973525693e-3
-
-
-def _kv(nu, x):
-    sp = pytest.importorskip("scipy.special")
-    return sp.kv(nu, x)
 
 
 def _int_kv(nu, x):
