@@ -36,12 +36,15 @@ UNIT = "particle-steps/s"
 # Algorithmic FP32 operations of one particle-step of the 1D LP case (fields, Boris push,
 # eta, rate lookup, optical depth, compensated position update; a mul+add pair counts 2).
 FLOP_PER_PSTEP_1D = 132
+FLOP_COUNT_SOURCE = "hand count of the 1D LP step (a multiply-add counts 2)"
 # Algorithmic bytes of one particle-step when the state round-trips memory every step:
 # read + write of x (float pair, 8 B), ux, uy, uz (f32) and tau (float pair, 8 B) in 1D;
 # + y (float pair) in 2D.
 BYTES_PER_PSTEP_1D = 56
 BYTES_PER_PSTEP_2D = 72
-SM_COUNT_NOMINAL = 152
+# the same state with an uncompensated float position (x 4 B instead of the 8 B pair): the byte
+# count the hot-path scope uses for its 60 % target
+BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from an ncu capture
 # of one 400-step launch on 2e5 electrons of the same physics (7.45 MB: the state once plus the
@@ -191,13 +194,15 @@ def main():
             if k >= W_:
                 vals.append((v, dt))
         value = statistics.median(v for v, _ in vals)
-        ms = 1e3 * cfg["n"] * cfg["steps"] / value
+        ms = 1e3 * statistics.median(dt for _, dt in vals)          # one timed step = one sample, as timed
+        sample = f"{n_sample} of {cfg['n']} electrons (strided ids) x {cfg['steps']} steps per timed step"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W_,
                 "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": cfg["name"], "particles": cfg["n"], "job_steps": cfg["steps"]},
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                 "sample": f"{n_sample} of {cfg['n']} electrons (strided ids) x {cfg['steps']} steps per timed step"},
+                "config": {"workload": cfg["name"], "particles": cfg["n"], "job_steps": cfg["steps"],
+                           "timed_step": sample},
+                "ms_per_full_job_extrapolated": 1e3 * cfg["n"] * cfg["steps"] / value,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -296,22 +301,30 @@ def main():
            "gpu_launches": int(launches),
            "clocks": clocks.summary(),
            "wall_s_timed_region": wall}
-    # roofline of the dominant kernel (k_step_pair): FP32 pipe (state held in registers across steps)
-    sm_clock = (res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
-    fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_clock / 1e12
+    # roofline of the dominant kernel (k_step_pair): FP32 pipe (state held in registers across steps),
+    # against the FMA-loop peak measured here on this GPU
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    pipes = fma_peaks(pe, stream, sms)
+    fp32_peak = max(pipes["fp32_ffma_tflops"], pipes["fp32_ffma2_tflops"])
     ach = FLOP_PER_PSTEP_1D * pst / (ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC_BYTES_PER_ELECTRON * n if NCU_TRAFFIC_BYTES_PER_ELECTRON else None
+    derived = sms * FP32_LANES_PER_SM * 2 * (res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
     res["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                       "traffic": traffic, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                       "flop_per_particle_step": FLOP_PER_PSTEP_1D}
+                       "traffic": traffic,
+                       "peak_kind": "measured: FMA-loop kernel of the FP32 pipe (pe_fma_peak), this GPU, this run",
+                       "flop_per_particle_step": FLOP_PER_PSTEP_1D, "flop_count": FLOP_COUNT_SOURCE,
+                       "pipes_measured": pipes, "fp32_peak_derived_tflops": derived, "sm_count": sms}
 
     if rank == 0 and not args.skip_extras:
         res["roofline_hbm"] = hbm_form(pe, tables, cfg, stream, hbm_peak_gbs(pk), pk_kind)
+        res["roofline"]["hbm_form"] = {k: res["roofline_hbm"][k] for k in
+                                       ("bound", "achieved", "peak", "unit", "frac", "frac_at_48B", "traffic")}
         res["fp64_plain"] = fp64_plain(pe, tables, cfg, stream, flush)
         res["e2e"] = e2e(pe, tables, cfg, stream)
         res["workloads"] = {"batch64_graph": batch64(pe, stream, flush),
                             "gauss2d_cp_a855_3e7x2000": gauss2d(pe, stream, flush),
-                            "serving_poisson50hz": serving(pe, stream),
+                            "serving_poisson50hz": serving(pe, stream, 50.0),
+                            "serving_poisson25hz": serving(pe, stream, 25.0),
                             "bunch_1gev_au_5mm_1e6": bunch_methods(pe, stream, flush),
                             "bunch_1gev_au_5mm_1e6_dt_T10": bunch_methods(pe, stream, flush, dt_over_T=0.1),
                             "reflected_1d_a270_1e6x4000": reflected(pe, tables, cfg, stream, flush),
@@ -356,32 +369,53 @@ def hbm_form(pe, tables, cfg, stream, peak_gbs, peak_kind):
     pst = r.tally_out().live_particle_steps
     ms = ev[0].elapsed_time(ev[1]) / K
     gbs = BYTES_PER_PSTEP_1D * pst / K / (ms * 1e-3) / 1e9
+    gbs48 = BYTES_PER_PSTEP_1D_PLAIN_X * pst / K / (ms * 1e-3) / 1e9
     r.close()
     return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+            "frac_at_48B": gbs48 / peak_gbs,
             "traffic": None, "peak_kind": peak_kind, "particles": n, "bytes_per_particle_step": BYTES_PER_PSTEP_1D,
             "ms_per_launch": ms, "launches": K, "particle_steps_per_s": pst / K / (ms * 1e-3),
             "kernel": "k_step_pair (FP32, 1D plane wave), one step per launch"}
 
 
-def fp64_plain(pe, tables, cfg, stream, flush):
-    """The plain FP64 path (one launch per step, tables in global memory) on the same job."""
+def fma_peaks(pe, stream, sms):
+    """Peak of the FP32 (FFMA and paired FFMA2) and FP64 (DFMA) pipes: FMA-loop launches of 8
+    CTAs of 256 threads per SM, timed by CUDA events on the launching stream after a warm-up;
+    best of 5."""
+    import torch
+    out = {}
+    buf = torch.empty(sms * 8 * 256, dtype=torch.float64, device="cuda")
+    for name, kind, iters, per in (("fp32_ffma_tflops", pe.PE_FMA_F32, 20000, 1),
+                                   ("fp32_ffma2_tflops", pe.PE_FMA_F32X2, 10000, 2),
+                                   ("fp64_dfma_tflops", pe.PE_FMA_F64, 400, 1)):
+        best = None
+        for k in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            chains = pe.pe_fma_peak(kind, sms * 8, 256, iters, buf.data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            if k:
+                best = t if best is None else min(best, t)
+        out[name] = 2.0 * chains * iters * sms * 8 * 256 * per / best / 1e12
+    return out
+
+
+def fp64_plain(pe, tables, cfg, stream, flush, reps=3):
+    """The plain FP64 path (one launch per step, tables in global memory) on the same job: one
+    warm-up job, then the mean of `reps` timed jobs from the same initial state, L2 flushed."""
     import torch
     run = dict(cfg["run"], run_id=0)
     n, S = cfg["n"], cfg["steps"]
     with torch.cuda.stream(stream):
         r = pe.Run(tables, pe.run_params(precision=pe.PE_F64, **run), n, capacity=1 << 24, stream=stream)
-        flush.fill_(1.0)
     stream.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pe.pe_step([r.handle], S)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = _timed_jobs(pe, r, tables, S, stream, flush, reps=reps + 1)
     out = r.tally_out()
     r.close()
     return {"value": out.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms,
-            "kernel": "k_step_plain (fp64, one launch per step)", "steps": 1, "warmup": 0}
+            "kernel": "k_step_plain (fp64, one launch per step)", "timed_jobs": reps, "warmup_jobs": 1}
 
 
 def batch64(pe, stream, flush):
@@ -398,9 +432,8 @@ def batch64(pe, stream, flush):
             runs.append(pe.Run(tables, pe.run_params(precision=pe.PE_F32, **rk), int(n),
                                capacity=int(min(2 * n, 1 << 23)), stream=stream))
     stream.synchronize()
-    cfg, trials = autotune.tune(tables, runs, 200, space=dict(block=(128, 256), ctas_per_sm=(5, 10, 15),
-                                                                 steps_per_launch=(200,)), use_cache=False)
-    cfg = dict(cfg, steps_per_launch=500)
+    cfg, trials = autotune.tune(tables, runs, 500, space=dict(block=(128, 256), ctas_per_sm=(5, 10, 15),
+                                                                 steps_per_launch=(250, 500)), use_cache=False)
     snaps = [r.snapshot() for r in runs]
     times = []
     for k in range(3):
@@ -642,19 +675,21 @@ def profile_pic(n, steps):
     r.close()
 
 
-def serving(pe, stream, n_requests=60):
-    """Continuous batching of a Poisson trace (50 requests/s; geometry of the 2D case, intensity
-    and target drawn per request, 1e4..1e7 electrons, 500..4000 steps), first n_requests arrivals
-    served in real time: p50/p99 latency (arrival to results on the host) and throughput."""
+def serving(pe, stream, rate_hz=50.0, n_requests=600):
+    """Continuous batching of a Poisson trace (geometry of the 2D case, intensity and target drawn
+    per request, 1e4..1e7 electrons, 500..4000 steps), all n_requests arrivals served in real time:
+    p50/p99 latency (arrival to results on the host, queueing included) and throughput."""
     from paper_1612_07592_gb300 import workloads as W
     from paper_1612_07592_gb300.serve import Server, requests_from_workload
-    c = W.config5(50.0, n_requests)
+    c = W.config5(rate_hz, n_requests)
     tables = pe.pe_create_tables(c["tables"], c["Z"])
     reqs = requests_from_workload(c)
     srv = Server(tables, steps_per_iteration=500, stream=stream)
     st = srv.run_trace(reqs, realtime=True).summary()
     pe.pe_destroy_tables(tables)
-    st.update({"unit": UNIT, "offered_rate_hz": 50.0, "trace": f"first {n_requests} of config-5 Poisson arrivals"})
+    offered = sum(q.n * q.steps for q in reqs) / max(reqs[-1].arrival_s, 1e-9)
+    st.update({"unit": UNIT, "offered_rate_hz": rate_hz, "offered_particle_steps_per_s": offered,
+               "trace": f"{n_requests} Poisson arrivals at {rate_hz:g}/s (config 5)"})
     return st
 
 
@@ -679,7 +714,7 @@ def e2e(pe, tables, cfg, stream):
     host_tau = torch.empty(n, dtype=torch.float64).pin_memory()
     host_ph = torch.empty(cap * 8, dtype=torch.int32).pin_memory()
     times, h2d, d2h = [], 0, 0
-    for k in range(3):
+    for k in range(11):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -707,7 +742,8 @@ def e2e(pe, tables, cfg, stream):
         pst = out.live_particle_steps
     dt = statistics.median(times[1:])
     return {"value": pst / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "s_per_job": dt, "path": "pinned host -> pe_init_particles(PE_CALLER) + pe_step + pe_tally -> pinned host"}
+            "s_per_job": dt, "jobs_timed": len(times) - 1, "warmup_jobs": 1,
+            "path": "pinned host -> pe_init_particles(PE_CALLER) + pe_step + pe_tally -> pinned host"}
 
 
 if __name__ == "__main__":

@@ -77,6 +77,7 @@ enum {
     PE_T_N_GAMMA_ABOVE = 7,  /* brems tests with gamma above the table (row clamped)       */
     PE_T_N_KILLED = 8, PE_T_KILLED_STEPS = 9, PE_T_N_CLAMP = 10, PE_T_N_HIST_OVER = 11,
     PE_T_N_WAIT_TIMEOUT = 12, /* device waits that ran out (pe_tally then returns PE_ERR_TIMEOUT) */
+    PE_T_N_NONFINITE = 13,   /* particles removed because a momentum was NaN or infinite (also in N_KILLED) */
     PE_T_E_NCS_STORED = 16, PE_T_E_NCS_BELOW = 18, PE_T_E_BR_STORED = 20, PE_T_E_BR_BELOW = 22,
     PE_T_E_RECOIL_NCS = 24, PE_T_E_RECOIL_BR = 26
 };
@@ -147,6 +148,16 @@ typedef struct {
      * the characteristics with the current at the midpoint (exact in vacuum);
      * E_x follows -J_x of the charge-conserving linear weighting.             */
     int n_cells;
+    /* Global id of the run's particle 0.  Particle i of the buffers draws its
+     * random numbers with Philox counter word 0 = id0 + i, and its photons carry
+     * that id.  Electrons are independent under prescribed fields, so one run of
+     * N electrons can be split into runs over contiguous id ranges [id0, id0 + n)
+     * (one per GPU or process, same seed and run_id): each range gives exactly
+     * the particles, photons and events the unsplit run gives for those ids, and
+     * the tallies and histograms of the parts add up exactly (integers and
+     * 128-bit fixed point) to the unsplit run's.  0 for an unsplit run;
+     * id0 + n must not exceed 2^32.                                              */
+    uint32_t id0;
 } pe_run_params;
 
 /* Caller-owned device buffers of one run.
@@ -386,6 +397,44 @@ pe_status pe_pair_transport(pe_run* run, const void* photons, int64_t n_photons,
  * outside [2, 4096], not 0 < chi_min < chi_max).                                */
 pe_status pe_bw_tables_host(int n_chi, double chi_min, double chi_max, int n_x, double* T, double* cdf);
 
+/* The same Breit-Wheeler tables on the current device (library-owned): T as
+ * L_i = ln T(chi_i) + 8 / (3 chi_i), linear in ln chi between nodes (the factor
+ * takes out the small-chi exponential), and the CDF rows.  Synchronous.
+ * Errors: as pe_bw_tables_host; PE_ERR_ARG also if T underflows at chi_min;
+ * PE_ERR_NOMEM, PE_ERR_CUDA.                                                 */
+typedef struct pe_bw_tables pe_bw_tables;
+pe_status pe_bw_tables_create(int n_chi, double chi_min, double chi_max, int n_x, pe_bw_tables** out);
+pe_status pe_bw_tables_destroy(pe_bw_tables* tables);
+
+/* Breit-Wheeler conversion of photon records in the run's prescribed laser
+ * fields (Sec. 1).  Each record (the 32-byte photon layout; photons with
+ * k <= 2 m c^2 are skipped) moves at c along its direction from its emission
+ * point: at step m (n_e < m < step_end) it is at x_e + k^ (m - n_e) c dt and
+ * the run's fields at (that point, t = m dt) give chi = sqrt((k E + kvec x B)^2
+ * - (kvec . E)^2) / E_S, kvec = k k^.  An optical depth tau_0 = -ln U, U from
+ * words 0-1 (53 bits) of the Philox draw (id_mech, run id, n_e, 0x60000000 + n_e),
+ * falls by W dt = alpha E_S dt T(chi) / k per step; at the first step with
+ * tau <= 0 the photon converts: x from words 0-1 of the draw (id_mech, run id,
+ * m, 0x70000000 + n_e) by the CDF (rows interpolated in ln chi, chi clamped to
+ * the table, inverted linearly in s, x = (1 - cos(pi s)) / 2), one pe_pair with
+ * E+ = x k, E- = k - E+, both along k^, at the photon's position.  Tally words
+ * (PE_PAIR_TALLY_WORDS uint64, cleared by the call): [0] the true pair count,
+ * [1] photons followed, [2] photon-steps with chi above the table (last node
+ * used), [3] photon-steps taken, [4-5] and [6-7] 128-bit fixed-point sums of k
+ * and E+ of the conversions.  A photon behind a pulse for good (the fields
+ * vanish there) stops early with its remaining steps counted as taken.  FP64
+ * runs step in double; FP32 runs in float (optical depth as a compensated float
+ * pair) and at most 8192 steps.  Asynchronous on the run's stream.
+ *   run, bw   : the run whose fields, step, seed and run id apply; the tables
+ *   photons   : device array of n_photons records, 4-byte aligned, read only
+ *   step_end  : first step not taken (-1: the run's steps done so far)
+ *   pairs     : device array of capacity pe_pair records (excess not written)
+ * Errors: PE_ERR_ARG (null, n_photons < 0 or >= 2^31, capacity < 0, misaligned,
+ * step_end beyond the run or above 8192 for FP32), PE_ERR_STATE (a PE_PIC_1D run:
+ * its fields are not stored), PE_ERR_CUDA.                                   */
+pe_status pe_bw_transport(pe_run* run, const pe_bw_tables* bw, const void* photons, int64_t n_photons,
+                          int64_t step_end, void* pairs, int64_t capacity, void* tally);
+
 /* a0 of a pulse of intensity I (W/cm^2) at wavelength lambda (Sec. 3: a0 = 0.86 sqrt(I_18)
  * at 1 um; here 0.855 lambda_um sqrt(I_18) for LP, divided by sqrt(2) per component for CP). */
 double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);
@@ -410,15 +459,52 @@ double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polarisation);
  *   cleared to zero with the caller's own electrons).  hist and tally
  *   accumulate as in pe_step.  Asynchronous on cuda_stream.
  *   The first call on a device looks up the array's device address with that
- *   device current (cudaGetSymbolAddress) and keeps it; make that first call
- *   before any stream capture.  Every call shares the one array and clears it
- *   before use, so calls whose work overlaps on the GPU (other streams, other
- *   host threads) race and give wrong currents: serialise them.
+ *   device current (cudaGetSymbolAddress) and keeps it for the life of the
+ *   process; make that first call before any stream capture, and do not reset
+ *   the device (cudaDeviceReset) or tear down its primary context after it: the
+ *   module may then load at another address and the kept one is stale.  Every
+ *   call shares the one array and clears it before use, so calls whose work
+ *   overlaps on the GPU (other streams, other host threads) race and give wrong
+ *   currents: serialise them.  The checks and the run description are those of
+ *   pe_init_particles (the same code).
  * Errors: PE_ERR_ARG (null, wrong geometry, n_cells outside [4,
  * PE_PIC_MAX_CELLS] -- the array's limit --, bad sizes or alignment, Z not in
  * the tables), PE_ERR_CUDA.                                                    */
 pe_status pe_pic_step_noalloc(const pe_tables* tables, const pe_run_params* params, int64_t n,
                               const pe_buffers* buffers, int64_t step0, int64_t n_steps, void* cuda_stream);
+
+/* Diagnostics (the paper has no counterpart): the library's own single-precision
+ * device forms, evaluated on given inputs so that tests can bound their error.
+ *   fn = PE_MATH_RCP      1/d for d >= 1 as the FP32 step forms it (the hardware
+ *                         reciprocal estimate refined by one Newton-Raphson step)
+ *        PE_MATH_SIN/_COS the carrier-phase sine and cosine of the paired FP32 step
+ *                         (Cody-Waite reduction by 2 pi with a two-part constant,
+ *                         then the hardware sine and cosine); _SIN1/_COS1 the same
+ *                         in the one-electron FP32 step
+ *        PE_MATH_BREMS_P  1 - e^-x as the paired step forms the probability of Eq. 4
+ *                         (a four-term Taylor series below 2^-5, expm1f above);
+ *                         _BREMS_P1 the same in the one-electron step
+ *        PE_MATH_CUDA_RCP, _SIN, _COS, _EXPM1: CUDA's __frcp_rn, sinf, cosf and
+ *                         -expm1f(-x), for comparison
+ *   in, out : n floats of device memory (4-byte aligned); asynchronous on stream.
+ * Errors: PE_ERR_ARG (null, n < 0, unknown fn), PE_ERR_CUDA.                  */
+enum { PE_MATH_RCP = 0, PE_MATH_SIN = 1, PE_MATH_COS = 2, PE_MATH_SIN1 = 3, PE_MATH_COS1 = 4,
+       PE_MATH_BREMS_P = 5, PE_MATH_BREMS_P1 = 6, PE_MATH_CUDA_RCP = 7, PE_MATH_CUDA_SIN = 8,
+       PE_MATH_CUDA_COS = 9, PE_MATH_CUDA_EXPM1 = 10 };
+pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* cuda_stream);
+
+/* Peak of an arithmetic pipe, for the roofline of the ALU-bound step kernel (the
+ * paper has no counterpart): one launch of blocks x threads threads, each running
+ * `iters` rounds of *chains_out independent fused multiply-add chains -- kind
+ * PE_FMA_F32 (FFMA), PE_FMA_F32X2 (the paired FFMA2: two FMAs per instruction) or
+ * PE_FMA_F64 (DFMA).  out (device memory, blocks x threads floats, or doubles for
+ * PE_FMA_F64) receives each thread's sums so the work is kept.  The caller times the
+ * launch on cuda_stream (CUDA events); it performs 2 x chains x iters x blocks x
+ * threads flops (twice that for PE_FMA_F32X2).  Asynchronous.  Errors: PE_ERR_ARG
+ * (unknown kind, blocks or iters < 1, threads not a multiple of 32 in [32, 256]). */
+enum { PE_FMA_F32 = 0, PE_FMA_F32X2 = 1, PE_FMA_F64 = 2 };
+pe_status pe_fma_peak(int kind, int blocks, int threads, int iters, void* out, void* cuda_stream,
+                      int* chains_out);
 
 /* Number of kernel launches the library has issued (all runs, this process). */
 int64_t pe_launch_count(void);

@@ -33,7 +33,7 @@ TALLY_WORDS = 32
 MAX_BATCH = 64
 T = dict(N_NCS_STORED=0, N_NCS_BELOW=1, N_BR_STORED=2, N_BR_BELOW=3, N_PHOTONS=4, N_ETA_ABOVE=5,
          N_ETA_BELOW=6, N_GAMMA_ABOVE=7, N_KILLED=8, KILLED_STEPS=9, N_CLAMP=10, N_HIST_OVER=11, N_WAIT_TIMEOUT=12,
-         E_NCS_STORED=16, E_NCS_BELOW=18, E_BR_STORED=20, E_BR_BELOW=22, E_RECOIL_NCS=24, E_RECOIL_BR=26)
+         N_NONFINITE=13, E_NCS_STORED=16, E_NCS_BELOW=18, E_BR_STORED=20, E_BR_BELOW=22, E_RECOIL_NCS=24, E_RECOIL_BR=26)
 PHOTON_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("energy", "<f4"), ("kx", "<f4"),
                          ("ky", "<f4"), ("kz", "<f4"), ("step", "<u4"), ("id_mech", "<u4")])
 # Bethe-Heitler pair records (pe_pair) and the pair tally words
@@ -71,7 +71,8 @@ class RunParams(C.Structure):
                 ("T_mev", C.c_double), ("beam_gamma", C.c_double), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("enable_ncs", C.c_int), ("enable_brems", C.c_int),
                 ("box_enable", C.c_int), ("box_x_m", C.c_double * 2), ("reflect_r", C.c_double),
-                ("mirror_x_m", C.c_double), ("brems_method", C.c_int), ("n_cells", C.c_int)]
+                ("mirror_x_m", C.c_double), ("brems_method", C.c_int), ("n_cells", C.c_int),
+                ("id0", C.c_uint32)]
 
 
 class Buffers(C.Structure):
@@ -129,6 +130,11 @@ def lib():
                                               C.POINTER(vp)]
             L.pe_bw_tables_host.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
+            L.pe_bw_tables_create.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)]
+            L.pe_bw_tables_destroy.argtypes = [vp]
+            L.pe_bw_transport.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
+            L.pe_math_probe.argtypes = [C.c_int, vp, vp, C.c_int64, vp]
+            L.pe_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_int)]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
             L.pe_launch_count.restype = C.c_int64
@@ -136,7 +142,8 @@ def lib():
             for name in ("pe_create_tables", "pe_destroy_tables", "pe_tables_export", "pe_init_particles",
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
                          "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map",
-                         "pe_pair_transport", "pe_resume_particles", "pe_bw_tables_host"):
+                         "pe_pair_transport", "pe_resume_particles", "pe_bw_tables_host", "pe_math_probe",
+                         "pe_fma_peak", "pe_bw_tables_create", "pe_bw_tables_destroy", "pe_bw_transport"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -278,6 +285,40 @@ def pe_bw_tables_host(n_chi: int, chi_min: float, chi_max: float, n_x: int):
     _check(lib().pe_bw_tables_host(int(n_chi), float(chi_min), float(chi_max), int(n_x),
                                    T.ctypes.data_as(C.POINTER(C.c_double)), cdf.ctypes.data_as(C.POINTER(C.c_double))))
     return T, cdf.reshape(n_chi, n_x)
+
+
+def pe_bw_tables_create(n_chi: int = 64, chi_min: float = 1e-2, chi_max: float = 1e3, n_x: int = 128) -> int:
+    """Breit-Wheeler tables on the current device (see pe.h)."""
+    h = C.c_void_p()
+    _check(lib().pe_bw_tables_create(int(n_chi), float(chi_min), float(chi_max), int(n_x), C.byref(h)))
+    return h.value
+
+
+def pe_bw_tables_destroy(h: int) -> None:
+    _check(lib().pe_bw_tables_destroy(h))
+
+
+def pe_bw_transport(run: int, bw: int, photons_ptr: int, n_photons: int, step_end: int, pairs_ptr: int,
+                    capacity: int, tally_ptr: int) -> None:
+    _check(lib().pe_bw_transport(run, bw, photons_ptr, int(n_photons), int(step_end), pairs_ptr, int(capacity),
+                                 tally_ptr))
+
+
+PE_MATH = dict(RCP=0, SIN=1, COS=2, SIN1=3, COS1=4, BREMS_P=5, BREMS_P1=6, CUDA_RCP=7, CUDA_SIN=8, CUDA_COS=9,
+               CUDA_EXPM1=10)
+PE_FMA_F32, PE_FMA_F32X2, PE_FMA_F64 = 0, 1, 2
+
+
+def pe_math_probe(fn: int, in_ptr: int, out_ptr: int, n: int, stream) -> None:
+    """One of the library's FP32 device forms on n device floats (see pe.h)."""
+    _check(lib().pe_math_probe(int(fn), in_ptr, out_ptr, int(n), stream))
+
+
+def pe_fma_peak(kind: int, blocks: int, threads: int, iters: int, out_ptr: int, stream) -> int:
+    """Launch the FMA-loop kernel of one pipe (see pe.h); returns the chains per thread."""
+    ch = C.c_int(0)
+    _check(lib().pe_fma_peak(int(kind), int(blocks), int(threads), int(iters), out_ptr, stream, C.byref(ch)))
+    return ch.value
 
 
 def pe_destroy(run: int):
@@ -469,6 +510,32 @@ class Run:
             tally = torch.zeros(PAIR_TALLY_WORDS, dtype=torch.int64, device=self.x.device)
         pe_pair_transport(self.handle, dev_ph.data_ptr(), int(n), step_end, pairs.data_ptr(), cap, tally.data_ptr(),
                           method)
+        self.stream.synchronize()
+        t = tally.cpu().numpy().view(np.uint64)
+        k = int(min(t[PT["N_PAIRS"]], cap))
+        return pairs[: k * 10].cpu().numpy().view(PAIR_DTYPE), int(t[PT["N_PAIRS"]]), t
+
+    def bw_transport(self, bw: int, photons=None, n_photons: int | None = None, step_end: int = -1,
+                     capacity: int | None = None):
+        """Breit-Wheeler conversion, computed on the device, of photon records in this run's fields up
+        to step_end (-1: the steps done); photons as for pair_transport (default: the run's own).
+        Returns (pairs as PAIR_DTYPE, true pair count, tally words)."""
+        torch = self.torch
+        if photons is None:
+            n = self.tally_out().photons_stored if n_photons is None else n_photons
+        else:
+            n = (len(photons) if isinstance(photons, np.ndarray) else 0) if n_photons is None else n_photons
+        cap = max(int(n), 1) if capacity is None else int(capacity)
+        with torch.cuda.stream(self.stream):
+            if photons is None:
+                dev_ph = self.photons
+            elif isinstance(photons, np.ndarray):
+                dev_ph = torch.from_numpy(np.ascontiguousarray(photons).view(np.int32).reshape(-1)).to(self.x.device)
+            else:
+                dev_ph = photons
+            pairs = torch.zeros(max(cap, 1) * 10, dtype=torch.int32, device=self.x.device)
+            tally = torch.zeros(PAIR_TALLY_WORDS, dtype=torch.int64, device=self.x.device)
+        pe_bw_transport(self.handle, bw, dev_ph.data_ptr(), int(n), step_end, pairs.data_ptr(), cap, tally.data_ptr())
         self.stream.synchronize()
         t = tally.cpu().numpy().view(np.uint64)
         k = int(min(t[PT["N_PAIRS"]], cap))

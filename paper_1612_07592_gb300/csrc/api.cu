@@ -75,6 +75,71 @@ extern "C" double pe_a0_from_intensity(double I_wcm2, double lambda_m, int polar
     return polarisation == PE_CP ? a / std::sqrt(2.0) : a;
 }
 
+struct pe_bw_tables {
+    BwDev dev;
+    void* dmem = nullptr;
+    int device = 0;
+};
+
+extern "C" pe_status pe_bw_tables_create(int n_chi, double chi_min, double chi_max, int n_x, pe_bw_tables** out) {
+    if (!out) return fail(PE_ERR_ARG, "pe_bw_tables_create: null out");
+    *out = nullptr;
+    if (n_chi < 2 || n_x < 2 || n_chi > 4096 || n_x > 4096 || !(chi_min > 0.0) || !(chi_max > chi_min) ||
+        !std::isfinite(chi_max))
+        return fail(PE_ERR_ARG, "pe_bw_tables_create: need 2 <= n_chi, n_x <= 4096 and 0 < chi_min < chi_max");
+    std::vector<double> T(n_chi), cdf((size_t)n_chi * n_x);
+    build_host_bw_tables(n_chi, chi_min, chi_max, n_x, T.data(), cdf.data());
+    for (double v : T)
+        if (!(v > 0.0) || !std::isfinite(v))
+            return fail(PE_ERR_ARG, "pe_bw_tables_create: T(chi) underflows at chi_min; raise chi_min");
+    // L_i = ln T_i + 8 / (3 chi_i), chi_i on the log grid (T is interpolated as exp(L - 8 / (3 chi)))
+    std::vector<double> L(n_chi);
+    std::vector<float> L32(n_chi);
+    const double llo = std::log(chi_min), lhi = std::log(chi_max);
+    for (int i = 0; i < n_chi; ++i) {
+        const double ci = std::exp(llo + (lhi - llo) * (double)i / (double)(n_chi - 1));
+        L[i] = std::log(T[i]) + 8.0 / (3.0 * ci);
+        L32[i] = (float)L[i];
+    }
+    pe_bw_tables* t = new pe_bw_tables();
+    cudaGetDevice(&t->device);
+    const size_t b64 = sizeof(double) * ((size_t)n_chi + cdf.size()), b32 = sizeof(float) * (size_t)n_chi;
+    cudaError_t e = cudaMalloc(&t->dmem, b64 + b32);
+    if (e != cudaSuccess) {
+        delete t;
+        return fail(PE_ERR_NOMEM, std::string("pe_bw_tables_create: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    double* dL = static_cast<double*>(t->dmem);
+    double* dcdf = dL + n_chi;
+    float* dL32 = reinterpret_cast<float*>(dcdf + cdf.size());
+    e = cudaMemcpy(dL, L.data(), sizeof(double) * n_chi, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dcdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dL32, L32.data(), b32, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(t->dmem);
+        delete t;
+        return cuda_fail(e, "pe_bw_tables_create: upload");
+    }
+    BwDev& d = t->dev;
+    d.L64 = dL; d.L32 = dL32; d.cdf64 = dcdf;
+    d.T_last = T[n_chi - 1];
+    d.chi_min = chi_min;
+    d.ln_chi_min = llo;
+    d.inv_dln_chi = (double)(n_chi - 1) / (lhi - llo);
+    d.fT_last = (float)d.T_last; d.fchi_min = (float)chi_min; d.fln_chi_min = (float)llo;
+    d.finv_dln_chi = (float)d.inv_dln_chi;
+    d.n_chi = n_chi; d.n_x = n_x;
+    *out = t;
+    return PE_OK;
+}
+
+extern "C" pe_status pe_bw_tables_destroy(pe_bw_tables* t) {
+    if (!t) return fail(PE_ERR_ARG, "pe_bw_tables_destroy: null");
+    if (t->dmem) cudaFree(t->dmem);
+    delete t;
+    return PE_OK;
+}
+
 extern "C" pe_status pe_bw_tables_host(int n_chi, double chi_min, double chi_max, int n_x, double* T,
                                         double* cdf) {
     if (!T || !cdf) return fail(PE_ERR_ARG, "pe_bw_tables_host: null argument");
@@ -294,62 +359,65 @@ extern "C" pe_status pe_tables_export(const pe_tables* t, int which, int iz, dou
     return PE_OK;
 }
 
-// A run on the caller's buffers.  resume = false: a new run (initial state drawn unless
-// PE_CALLER, histograms, tallies and events cleared, PIC grid set up).  resume = true: the
-// buffers already hold the state of step `step0` (a checkpoint) and are taken as they are.
-static pe_status make_run(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, void* stream,
-                          bool resume, int64_t step0, pe_run** out) {
-    if (!t || !rp || !b || !out) return fail(PE_ERR_ARG, "pe_init_particles: null argument");
-    *out = nullptr;
-    if (step0 < 0 || step0 >= (int64_t(1) << 32)) return fail(PE_ERR_ARG, "pe_resume_particles: step0 out of range");
-    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_init_particles: n must be in [0, 2^31)");
-    if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_init_particles: precision");
-    if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_PIC_1D) return fail(PE_ERR_ARG, "pe_init_particles: geometry");
-    if (rp->geometry == PE_PIC_1D) {
-        if (rp->n_cells < 4 || rp->n_cells > PE_PIC_MAX_CELLS)
-            return fail(PE_ERR_ARG, "pe_init_particles: n_cells must be in [4, PE_PIC_MAX_CELLS]");
-        if (n > 0 && (!b->grid || !aligned16(b->grid))) return fail(PE_ERR_ARG, "pe_init_particles: PIC grid buffer");
-        const double L_m = rp->n_cells * rp->dt_over_T * rp->lambda_m;       // n_cells dx, dx = c dt
-        if (!(rp->slab_x0_m > 0 && rp->slab_x0_m + rp->slab_thick_m < L_m))
-            return fail(PE_ERR_ARG, "pe_init_particles: the slab must lie inside the PIC grid (0, n_cells c dt)");
-    }
-    if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP) return fail(PE_ERR_ARG, "pe_init_particles: polarisation");
-    if (rp->init_dist < PE_REST || rp->init_dist > PE_CALLER) return fail(PE_ERR_ARG, "pe_init_particles: init_dist");
+// The checks every entry point that takes a run description applies (`who` names the
+// entry point in the message); *iz_out receives the index of the run's Z in the table set.
+static pe_status check_run(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b,
+                           const char* who, int* iz_out) {
+    const std::string w(who);
+    if (!t || !rp || !b) return fail(PE_ERR_ARG, w + ": null argument");
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, w + ": n must be in [0, 2^31)");
+    if ((int64_t)rp->id0 + n > (int64_t(1) << 32))
+        return fail(PE_ERR_ARG, w + ": id0 + n must not exceed 2^32 (electron ids are 32-bit Philox counters)");
+    if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, w + ": precision");
+    if (rp->geometry < PE_PLANE_1D || rp->geometry > PE_PIC_1D) return fail(PE_ERR_ARG, w + ": geometry");
     if (!(rp->lambda_m > 0 && rp->dt_over_T > 0 && rp->charge_state > 0 && rp->ne_over_nc >= 0 &&
           rp->ramp_periods > 0 && rp->flat_s >= 0))
-        return fail(PE_ERR_ARG, "pe_init_particles: lambda, dt, charge state, ramp must be positive");
-    if (rp->geometry == PE_GAUSS_2D && !(rp->w0_m > 0)) return fail(PE_ERR_ARG, "pe_init_particles: w0");
-    if (rp->init_dist == PE_MAXWELL_JUTTNER && !(rp->T_mev > 0)) return fail(PE_ERR_ARG, "pe_init_particles: T_mev");
-    if (rp->init_dist == PE_BEAM && !(rp->beam_gamma >= 1)) return fail(PE_ERR_ARG, "pe_init_particles: beam_gamma");
-    if (!(rp->reflect_r >= 0 && rp->reflect_r <= 1)) return fail(PE_ERR_ARG, "pe_init_particles: reflect_r must be in [0, 1]");
+        return fail(PE_ERR_ARG, w + ": lambda, dt, charge state, ramp must be positive; n_e, flat top >= 0");
+    if (rp->geometry == PE_PIC_1D) {
+        if (rp->n_cells < 4 || rp->n_cells > PE_PIC_MAX_CELLS)
+            return fail(PE_ERR_ARG, w + ": n_cells must be in [4, PE_PIC_MAX_CELLS = 4096]");
+        if (n > 0 && (!b->grid || !aligned16(b->grid))) return fail(PE_ERR_ARG, w + ": PIC grid buffer");
+        const double L_m = rp->n_cells * rp->dt_over_T * rp->lambda_m;       // n_cells dx, dx = c dt
+        if (!(rp->slab_x0_m > 0 && rp->slab_x0_m + rp->slab_thick_m < L_m))
+            return fail(PE_ERR_ARG, w + ": the slab must lie inside the PIC grid (0, n_cells c dt)");
+    }
+    if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP) return fail(PE_ERR_ARG, w + ": polarisation");
+    if (rp->init_dist < PE_REST || rp->init_dist > PE_CALLER) return fail(PE_ERR_ARG, w + ": init_dist");
+    if (rp->geometry == PE_GAUSS_2D && !(rp->w0_m > 0)) return fail(PE_ERR_ARG, w + ": w0");
+    if (rp->init_dist == PE_MAXWELL_JUTTNER && !(rp->T_mev > 0)) return fail(PE_ERR_ARG, w + ": T_mev");
+    if (rp->init_dist == PE_BEAM && !(rp->beam_gamma >= 1)) return fail(PE_ERR_ARG, w + ": beam_gamma");
+    if (!(rp->reflect_r >= 0 && rp->reflect_r <= 1)) return fail(PE_ERR_ARG, w + ": reflect_r must be in [0, 1]");
     if (rp->reflect_r > 0 && rp->geometry != PE_PLANE_1D)
-        return fail(PE_ERR_ARG, "pe_init_particles: a reflected wave needs geometry PE_PLANE_1D");
+        return fail(PE_ERR_ARG, w + ": a reflected wave needs geometry PE_PLANE_1D");
     if (rp->brems_method != PE_BREMS_DIRECT && rp->brems_method != PE_BREMS_NULL)
-        return fail(PE_ERR_ARG, "pe_init_particles: brems_method");
+        return fail(PE_ERR_ARG, w + ": brems_method");
     if (rp->brems_method == PE_BREMS_NULL && n > 0 && (!b->brems_wait || !aligned16(b->brems_wait)))
-        return fail(PE_ERR_ARG, "pe_init_particles: PE_BREMS_NULL needs a 16-byte aligned brems_wait buffer");
+        return fail(PE_ERR_ARG, w + ": PE_BREMS_NULL needs a 16-byte aligned brems_wait buffer");
     if (n > 0) {
         if (!b->x || !b->y || !b->ux || !b->uy || !b->uz || !b->tau || !b->hist || !b->tally)
-            return fail(PE_ERR_ARG, "pe_init_particles: null buffer");
+            return fail(PE_ERR_ARG, w + ": null buffer");
         const void* ps[] = {b->x, b->y, b->ux, b->uy, b->uz, b->tau, b->hist, b->tally};
         for (const void* q : ps)
-            if (!aligned16(q)) return fail(PE_ERR_ARG, "pe_init_particles: buffers must be 16-byte aligned");
+            if (!aligned16(q)) return fail(PE_ERR_ARG, w + ": buffers must be 16-byte aligned");
     }
-    if (!b->hist || !b->tally) return fail(PE_ERR_ARG, "pe_init_particles: null hist/tally");
-    if (b->events && !aligned16(b->events)) return fail(PE_ERR_ARG, "pe_init_particles: events misaligned");
+    if (!b->hist || !b->tally) return fail(PE_ERR_ARG, w + ": null hist/tally");
+    if (b->events && !aligned16(b->events)) return fail(PE_ERR_ARG, w + ": events misaligned");
     if (b->photon_capacity < 0 || (b->photon_capacity > 0 && (!b->photons || !aligned16(b->photons))))
-        return fail(PE_ERR_ARG, "pe_init_particles: photon buffer");
+        return fail(PE_ERR_ARG, w + ": photon buffer");
     int iz = -1;
     for (int k = 0; k < t->host.p.n_Z; ++k)
         if (std::fabs(t->host.Z[k] - rp->Z) < 1e-9) iz = k;
-    if (iz < 0) return fail(PE_ERR_ARG, "pe_init_particles: Z is not in the table set");
+    if (iz < 0) return fail(PE_ERR_ARG, w + ": Z is not in the table set");
+    *iz_out = iz;
+    return PE_OK;
+}
 
-    pe_run* r = new pe_run();
-    r->params = *rp;
-    r->buf = *b;
-    r->tables = t;
-    r->stream = static_cast<cudaStream_t>(stream);
-    RunDev& d = r->dev;
+// The device description of a checked run: buffers, the per-step constants of its
+// laser, target and step in normalised units, the null-collision majorant and, for
+// PE_PIC_1D, the grid and the macro-electron weight.  The step index (step0) is 0 and
+// the PIC current sums (jacc) are unset: the caller supplies both.
+static void describe_run(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, int iz,
+                         RunDev& d) {
     std::memset(&d, 0, sizeof(d));
     d.x = b->x; d.y = b->y; d.ux = b->ux; d.uy = b->uy; d.uz = b->uz;
     d.tau = b->tau;
@@ -367,8 +435,9 @@ static pe_status make_run(const pe_tables* t, const pe_run_params* rp, int64_t n
     const double E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
     c.inv_ES = 1.0 / E_S;
     c.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * E_S * c.dt;
-    double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
-    double n_i = rp->ne_over_nc * n_c / rp->charge_state;
+    c.bw_coef = kAlpha * E_S * c.dt;
+    const double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
+    const double n_i = rp->ne_over_nc * n_c / rp->charge_state;
     c.K_br = n_i * kAlpha * kRe * kRe * (c.dt / kl);
     c.x0 = rp->slab_x0_m * kl;
     c.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
@@ -415,8 +484,30 @@ static pe_status make_run(const pe_tables* t, const pe_run_params* rp, int64_t n
     }
     d.iz = iz;
     d.run_id = rp->run_id;
+    d.id0 = rp->id0;
     d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
     d.seed_hi = (uint32_t)(rp->seed >> 32);
+}
+
+// A run on the caller's buffers.  resume = false: a new run (initial state drawn unless
+// PE_CALLER, histograms, tallies and events cleared, PIC grid set up).  resume = true: the
+// buffers already hold the state of step `step0` (a checkpoint) and are taken as they are.
+static pe_status make_run(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, void* stream,
+                          bool resume, int64_t step0, pe_run** out) {
+    if (!out) return fail(PE_ERR_ARG, "pe_init_particles: null argument");
+    *out = nullptr;
+    if (step0 < 0 || step0 >= (int64_t(1) << 32)) return fail(PE_ERR_ARG, "pe_resume_particles: step0 out of range");
+    int iz = -1;
+    pe_status st = check_run(t, rp, n, b, resume ? "pe_resume_particles" : "pe_init_particles", &iz);
+    if (st != PE_OK) return st;
+
+    pe_run* r = new pe_run();
+    r->params = *rp;
+    r->buf = *b;
+    r->tables = t;
+    r->stream = static_cast<cudaStream_t>(stream);
+    RunDev& d = r->dev;
+    describe_run(t, rp, n, b, iz, d);
 
     r->steps_done = step0;
     cudaError_t e = cudaSuccess;
@@ -735,6 +826,54 @@ extern "C" pe_status pe_pair_transport(pe_run* r, const void* photons, int64_t n
     return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_pair_transport");
 }
 
+extern "C" pe_status pe_bw_transport(pe_run* r, const pe_bw_tables* bw, const void* photons, int64_t n_photons,
+                                      int64_t step_end, void* pairs, int64_t capacity, void* tally) {
+    if (!r || !bw || !tally || (n_photons > 0 && !photons) || (capacity > 0 && !pairs))
+        return fail(PE_ERR_ARG, "pe_bw_transport: null argument");
+    if (r->dev.fk == FK_PIC)
+        return fail(PE_ERR_STATE, "pe_bw_transport: a PE_PIC_1D run's self-consistent fields are not stored");
+    if (n_photons < 0 || n_photons >= (int64_t(1) << 31) || capacity < 0)
+        return fail(PE_ERR_ARG, "pe_bw_transport: n_photons must be in [0, 2^31), capacity >= 0");
+    if ((reinterpret_cast<uintptr_t>(photons) & 3u) || (reinterpret_cast<uintptr_t>(pairs) & 3u) ||
+        (reinterpret_cast<uintptr_t>(tally) & 7u))
+        return fail(PE_ERR_ARG, "pe_bw_transport: misaligned buffer");
+    if (step_end < 0) step_end = r->steps_done;
+    if (step_end > r->steps_done) return fail(PE_ERR_ARG, "pe_bw_transport: step_end beyond the run's steps");
+    if (r->params.precision == PE_F32 && step_end > 8192)
+        return fail(PE_ERR_ARG, "pe_bw_transport: FP32 runs follow photons for at most 8192 steps");
+    cudaError_t e = cudaMemsetAsync(tally, 0, sizeof(unsigned long long) * PE_PAIR_TALLY_WORDS, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pe_bw_transport");
+    if (n_photons == 0) return PE_OK;
+    launch_bw_transport(bw->dev, r->dev, r->params.precision, photons, n_photons, step_end, pairs, capacity,
+                        static_cast<unsigned long long*>(tally), r->stream);
+    g_launches++;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_bw_transport");
+}
+
+extern "C" pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* stream) {
+    if ((n > 0 && (!in || !out)) || n < 0) return fail(PE_ERR_ARG, "pe_math_probe: null buffer or n < 0");
+    if (fn < PE_MATH_RCP || fn > PE_MATH_CUDA_EXPM1) return fail(PE_ERR_ARG, "pe_math_probe: unknown fn");
+    if (n >= (int64_t(1) << 40)) return fail(PE_ERR_ARG, "pe_math_probe: n too large");
+    if (n == 0) return PE_OK;
+    launch_math_probe(fn, in, out, n, static_cast<cudaStream_t>(stream));
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_math_probe");
+}
+
+extern "C" pe_status pe_fma_peak(int kind, int blocks, int threads, int iters, void* out, void* stream,
+                                 int* chains_out) {
+    if (kind < PE_FMA_F32 || kind > PE_FMA_F64) return fail(PE_ERR_ARG, "pe_fma_peak: unknown kind");
+    if (blocks < 1 || iters < 1 || threads < 32 || threads > 256 || threads % 32 || !out)
+        return fail(PE_ERR_ARG, "pe_fma_peak: need blocks, iters >= 1, threads a multiple of 32 in [32, 256], out");
+    if (chains_out) *chains_out = fma_chains();
+    launch_fma_peak(kind, blocks, threads, iters, out, static_cast<cudaStream_t>(stream));
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_fma_peak");
+}
+
 extern "C" pe_status pe_destroy(pe_run* r) {
     if (!r) return fail(PE_ERR_ARG, "pe_destroy: null");
     delete r;
@@ -868,66 +1007,6 @@ pe_status pic_scratch_address(void** out) {
     return PE_OK;
 }
 
-// The device description of a PE_PIC_1D run from its parameters and buffers (the
-// same quantities pe_init_particles sets up), without creating a run.
-pe_status pic_describe(const pe_tables* t, const pe_run_params* rp, int64_t n, const pe_buffers* b, RunDev& d) {
-    int iz = -1;
-    for (int k = 0; k < t->host.p.n_Z; ++k)
-        if (std::fabs(t->host.Z[k] - rp->Z) < 1e-9) iz = k;
-    if (iz < 0) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: Z is not in the table set");
-    std::memset(&d, 0, sizeof(d));
-    d.x = b->x; d.y = b->y; d.ux = b->ux; d.uy = b->uy; d.uz = b->uz;
-    d.tau = b->tau;
-    d.photons = static_cast<uint8_t*>(b->photons);
-    d.hist = static_cast<unsigned long long*>(b->hist);
-    d.tally = static_cast<unsigned long long*>(b->tally);
-    d.events = static_cast<unsigned long long*>(b->events);
-    d.n = n;
-    d.capacity = b->photon_capacity;
-    StepC<double>& c = d.c;
-    const double kl = 2.0 * kPi / rp->lambda_m;
-    c.dt = rp->dt_over_T * 2.0 * kPi;
-    split_dt(c.dt, &c.dt_hi, &c.dt_lo);
-    const double E_S = kMec2MeV * rp->lambda_m / (2.0 * kPi * kHbarcMeVm);
-    c.inv_ES = 1.0 / E_S;
-    c.ncs_coef = std::sqrt(3.0) * kAlpha / (2.0 * kPi) * E_S * c.dt;
-    const double n_c = kPi / (kRe * rp->lambda_m * rp->lambda_m);
-    const double n_i = rp->ne_over_nc * n_c / rp->charge_state;
-    c.K_br = n_i * kAlpha * kRe * kRe * (c.dt / kl);
-    c.x0 = rp->slab_x0_m * kl;
-    c.x1 = (rp->slab_x0_m + rp->slab_thick_m) * kl;
-    c.yh = rp->y_half_m * kl;
-    c.inv_log_emax = 1.0 / std::log(kHistEmaxMeV / kMec2MeV);
-    c.a0 = rp->a0;
-    c.phi_r = 2.0 * kPi * rp->ramp_periods;
-    c.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
-    c.k_env = 0.5 * kPi / c.phi_r;
-    double smax = 0;
-    for (int i = 0; i < t->host.p.n_E; ++i) smax = std::max(smax, t->host.sigma[(size_t)iz * t->host.p.n_E + i]);
-    d.x_hat = c.K_br * smax;
-    c.P_hat = -std::expm1(-d.x_hat);
-    d.brems_method = rp->brems_method;
-    d.wait = rp->brems_method == PE_BREMS_NULL ? static_cast<uint32_t*>(b->brems_wait) : nullptr;
-    d.fk = FK_PIC;
-    d.geometry = rp->geometry;
-    d.polarisation = rp->polarisation;
-    d.enable_ncs = rp->enable_ncs;
-    d.enable_brems = rp->enable_brems;
-    d.box_enable = 0;                       // the PIC kernel removes electrons leaving [0, L]
-    c.box0 = 0.0;
-    c.box1 = rp->n_cells * c.dt;
-    const double w = n > 0 ? rp->ne_over_nc * rp->slab_thick_m * kl / (double)n : 0.0;
-    c.pic_kx = w / c.dt / 68719476736.0;
-    c.pic_kyz = -w / c.dt / 68719476736.0;
-    d.grid = b->grid;
-    d.n_cells = rp->n_cells;
-    d.iz = iz;
-    d.run_id = rp->run_id;
-    d.seed_lo = (uint32_t)(rp->seed & 0xffffffffu);
-    d.seed_hi = (uint32_t)(rp->seed >> 32);
-    return PE_OK;
-}
-
 }  // namespace
 
 extern "C" pe_status pe_pic_step_noalloc(const pe_tables* t, const pe_run_params* rp, int64_t n,
@@ -937,29 +1016,15 @@ extern "C" pe_status pe_pic_step_noalloc(const pe_tables* t, const pe_run_params
     if (rp->n_cells < 4 || rp->n_cells > PE_PIC_MAX_CELLS)
         return fail(PE_ERR_ARG, "pe_pic_step_noalloc: n_cells must be in [4, PE_PIC_MAX_CELLS = 4096]: the fixed "
                                 "scratch array holds the current sums of at most PE_PIC_MAX_CELLS cells");
-    if (rp->precision != PE_F32 && rp->precision != PE_F64) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: precision");
-    if (rp->polarisation != PE_LP_Y && rp->polarisation != PE_CP)
-        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: polarisation");
-    if (rp->brems_method != PE_BREMS_DIRECT && rp->brems_method != PE_BREMS_NULL)
-        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: brems_method");
-    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: n must be in [0, 2^31)");
     if (step0 < 0 || n_steps < 0 || step0 + n_steps >= (int64_t(1) << 32))
         return fail(PE_ERR_ARG, "pe_pic_step_noalloc: step range");
-    if (!(rp->lambda_m > 0 && rp->dt_over_T > 0 && rp->charge_state > 0 && rp->ramp_periods > 0))
-        return fail(PE_ERR_ARG, "pe_pic_step_noalloc: lambda, dt, charge state, ramp must be positive");
-    if (n > 0) {
-        const void* ps[] = {b->x, b->y, b->ux, b->uy, b->uz, b->tau, b->hist, b->tally, b->grid};
-        for (const void* q : ps)
-            if (!q || !aligned16(q)) return fail(PE_ERR_ARG, "pe_pic_step_noalloc: buffers must be non-null and 16-byte aligned");
-        if (rp->brems_method == PE_BREMS_NULL && (!b->brems_wait || !aligned16(b->brems_wait)))
-            return fail(PE_ERR_ARG, "pe_pic_step_noalloc: PE_BREMS_NULL needs brems_wait");
-        if (b->photon_capacity < 0 || (b->photon_capacity > 0 && (!b->photons || !aligned16(b->photons))))
-            return fail(PE_ERR_ARG, "pe_pic_step_noalloc: photon buffer");
-    }
+    // the same checks and the same run description as pe_init_particles
+    int iz = -1;
+    pe_status st = check_run(t, rp, n, b, "pe_pic_step_noalloc", &iz);
+    if (st != PE_OK) return st;
     if (n == 0 || n_steps == 0) return PE_OK;
     RunDev d;
-    pe_status st = pic_describe(t, rp, n, b, d);
-    if (st != PE_OK) return st;
+    describe_run(t, rp, n, b, iz, d);
     void* scratch = nullptr;
     st = pic_scratch_address(&scratch);
     if (st != PE_OK) return st;

@@ -82,6 +82,7 @@ struct StepC {
     R xm2_hi, xm2_lo;         // 2 x_m (mirror plane) as hi + lo: in float an exact pair
     R P_hat;                  // null collisions: candidate probability 1 - exp(-x_hat) per step
     R pic_kx, pic_kyz;        // 1D PIC: J_x = pic_kx * sum, J_y,z = pic_kyz * sum (fixed-point sums)
+    R bw_coef;                // Breit-Wheeler: alpha E_S dt (W dt = bw_coef T(chi) / k)
 };
 
 // Device view of one run.  Optical depth: double for PE_F64, a float pair
@@ -102,6 +103,7 @@ struct RunDevT {
     int enable_ncs, enable_brems, box_enable;
     int iz;                       // brems table index
     uint32_t run_id;
+    uint32_t id0;                 // global id of particle 0 (Philox counter word 0 = id0 + index)
     uint32_t seed_lo, seed_hi;
     int fk;                       // field kind (physics.cuh)
     int brems_method;             // PE_BREMS_DIRECT | PE_BREMS_NULL
@@ -132,7 +134,7 @@ inline RunDevT<float> to_float(const RunDevT<double>& d) {
     for (size_t k = 0; k < sizeof(StepC<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
     f.geometry = d.geometry; f.polarisation = d.polarisation;
     f.enable_ncs = d.enable_ncs; f.enable_brems = d.enable_brems; f.box_enable = d.box_enable;
-    f.iz = d.iz; f.run_id = d.run_id; f.seed_lo = d.seed_lo; f.seed_hi = d.seed_hi;
+    f.iz = d.iz; f.run_id = d.run_id; f.id0 = d.id0; f.seed_lo = d.seed_lo; f.seed_hi = d.seed_hi;
     f.fk = d.fk; f.brems_method = d.brems_method; f.wait = d.wait; f.x_hat = d.x_hat;
     f.grid = d.grid; f.jacc = d.jacc; f.n_cells = d.n_cells;
     return f;
@@ -164,10 +166,30 @@ void build_host_bh_tables(const HostTables& h, std::vector<double>& sigma, std::
 // Breit-Wheeler tables on the host: T(chi_i) [n_chi] and the CDF over x_j [n_chi * n_x]
 void build_host_bw_tables(int n_chi, double chi_min, double chi_max, int n_x, double* T, double* cdf);
 
+// Breit-Wheeler tables on the device: T by L_i = ln T(chi_i) + 8 / (3 chi_i), linear in
+// ln chi between nodes (T = exp(L - 8 / (3 chi))), and the CDF over x at the nodes
+// x_j = (1 - cos(pi j / (n_x - 1))) / 2
+struct BwDev {
+    const double* L64;            // [n_chi]
+    const float* L32;             // [n_chi], float copy for the FP32 transport
+    const double* cdf64;          // [n_chi * n_x]
+    double T_last, chi_min, ln_chi_min, inv_dln_chi;
+    float fT_last, fchi_min, fln_chi_min, finv_dln_chi;
+    int n_chi, n_x;
+};
+// kernels_bw.cu: Breit-Wheeler conversion of photon records in the run's prescribed fields
+void launch_bw_transport(const BwDev& b, const RunDev& r, int precision, const void* photons, int64_t n_photons,
+                         int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally, cudaStream_t s);
+
 // kernels_pair.cu: Bethe-Heitler conversion of photon records in the run's target
 void launch_pair_transport(const TablesDev& t, const RunDev& r, const void* photons, int64_t n_photons,
                            int64_t step_end, void* pairs, int64_t capacity, unsigned long long* tally, int method,
                            cudaStream_t s);
+
+// kernels_diag.cu
+void launch_math_probe(int fn, const float* in, float* out, int64_t n, cudaStream_t s);
+void launch_fma_peak(int kind, int blocks, int threads, int iters, void* out, cudaStream_t s);
+int fma_chains();
 
 // kernels.cu
 void launch_init(const RunDev& r, int precision, int init_dist, double theta, double beam_u, cudaStream_t s);

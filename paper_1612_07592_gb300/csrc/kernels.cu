@@ -1,5 +1,5 @@
-// kernels.cu -- launchers of the init and plain FP64 kernels and the precision-
-// specific persistent kernels (instantiated in kernels_f32.cu / kernels_f64.cu).
+// kernels.cu -- the init kernel, the diagnostics kernels and their launchers.  The
+// step kernels are instantiated per precision in kernels_f32.cu and kernels_f64.cu.
 #include <algorithm>
 #include <cmath>
 
@@ -8,46 +8,13 @@
 namespace pe {
 
 // ---------------------------------------------------------------------------
-// plain FP64 kernel: one step, one particle per thread
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double> r) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = i < r.n;
-    Particle<double> P;
-    StepOut<double> out;
-    out.ncs = out.br = false;
-    if (active) {
-        load_particle<double>(r, i, P);
-        active = !isnan(P.x);
-    }
-    if (active) {
-        const double* sig = t.sig64 + (size_t)r.iz * t.n_E;
-        const uint32_t n = (uint32_t)r.step0;
-        switch (r.fk) {
-            case FK_PLANE_LP: step_one<double, FK_PLANE_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_PLANE_CP: step_one<double, FK_PLANE_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_GAUSS_LP: step_one<double, FK_GAUSS_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_GAUSS_CP: step_one<double, FK_GAUSS_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_REFL_LP: step_one<double, FK_REFL_LP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_REFL_CP: step_one<double, FK_REFL_CP>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-            default: step_one<double, FK_CONST>(t, r, t.h64, sig, (uint32_t)i, n, (double)n, P, out, r.hist, r.tally); break;
-        }
-        store_particle<double>(r, i, P);
-    }
-    if (__any_sync(0xffffffffu, out.ncs || out.br)) {
-        warp_append(r, out.ncs, out.pn);
-        warp_append(r, out.br, out.pb);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // init kernel
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_init(RunDevT<double> r, int init_dist, double theta, double beam_u) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r.n) return;
-    uint32_t id = (uint32_t)i;
+    uint32_t id = r.id0 + (uint32_t)i;
     uint4 w = draw(r, id, 0, PUR_TAU0);
     double tau0 = -log(uni53(w64(w.x, w.y)));
     if (sizeof(R) == 4) {
@@ -110,12 +77,6 @@ void launch_init(const RunDev& r, int precision, int init_dist, double theta, do
         k_init<float><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u);
     else
         k_init<double><<<grid, 256, 0, s>>>(r, init_dist, theta, beam_u);
-}
-
-void launch_step_plain_f64(const TablesDev& t, const RunDev& r, cudaStream_t s) {
-    if (r.n == 0) return;
-    int grid = (int)((r.n + 255) / 256);
-    k_step_plain<<<grid, 256, 0, s>>>(t, r);
 }
 
 int persistent_smem_bytes(const TablesDev& t, int precision) {

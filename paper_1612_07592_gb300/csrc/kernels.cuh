@@ -45,6 +45,21 @@ struct Photon {
     uint32_t step, id_mech;
 };
 
+// pair record of the pair-production transports (the pe_pair layout)
+struct PairRec {
+    float x, y, e_minus, e_plus, kx, ky, kz;
+    uint32_t step, photon, id_mech;
+};
+static_assert(sizeof(PairRec) == 40, "pe_pair layout");
+static_assert(sizeof(Photon) == 32, "photon record layout");
+
+// a photon's coordinate (direction component d, emission coordinate e) at step m, as the
+// definition computes it: e + d ((m - n_e) c dt), one rounding for the step product and one
+// for the fused multiply-add
+__device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, double e, int64_t ne, int64_t m) {
+    return __fma_rn(d, __dmul_rn((double)(m - ne), c.dt), e);
+}
+
 // warp-aggregated append of at most one photon per lane; all 32 lanes call it
 template <typename R>
 __device__ __forceinline__ void warp_append(const RunDevT<R>& r, bool on, const Photon& p) {
@@ -202,6 +217,14 @@ __device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R
     return out;
 }
 
+// 1 - e^{-x} in FP32 (the probability of Eq. 4): below 2^-5 by the Taylor series
+// x (1 - x/2 + x^2/6 - x^3/24), whose truncation is below x^4/120 < 2^-26 relative (the per-step
+// x_b of solid targets is 1e-6 to 1e-3); above it by expm1f
+__device__ __forceinline__ float one_minus_exp_neg_f32(float x) {
+    if (x < 0x1.0p-5f) return x * fmaf(x, fmaf(x, fmaf(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f), 1.0f);
+    return -expm1f(-x);
+}
+
 // Probability of a brems collision in this step, Eq. (4): P = 1 - exp(-x_b) with
 // x_b = n_i sigma_Z(gamma) beta c dt, for an electron in the slab.
 template <typename R>
@@ -212,13 +235,8 @@ __device__ __forceinline__ R brems_prob(const TablesDev& t, const RunDevT<R>& r,
     if (above) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
     R um = m_sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
     R xb = r.c.K_br * sig * (um / gamma);
-    if constexpr (sizeof(R) == 4) {
-        // 1 - e^{-x} by its Taylor series x (1 - x/2 + x^2/6 - x^3/24) for x < 2^-5 (the
-        // truncation is below x^4/120 < 2^-26 relative): the per-step x_b of solid targets
-        // is 1e-6 to 1e-3
-        if (xb < 0x1.0p-5f) return xb * fmaf(xb, fmaf(xb, fmaf(xb, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f), 1.0f);
-    }
-    return -m_expm1(-xb);
+    if constexpr (sizeof(R) == 4) return one_minus_exp_neg_f32(xb);
+    else return -m_expm1(-xb);
 }
 
 // Brems photon (text after Eq. 4): y from sigma(y, E) = sigma(E) R2, k^ = v^,
@@ -455,6 +473,24 @@ __device__ __forceinline__ void store_particle(const RunDevT<R>& r, int64_t i, c
     if (r.events) r.events[i] = ((unsigned long long)P.ev_hash << 32) | P.ev_cnt;
 }
 
+// At a launch boundary (the state just loaded for step n): false for a removed particle
+// (x = NaN with finite momenta: left the box or the PIC grid, or removed here before).  A
+// particle whose momentum is NaN or infinite (from the caller's buffers, or arithmetic that
+// overflowed) is removed here: x = NaN, momenta zeroed so it is counted once, stored back,
+// and counted in N_NONFINITE and N_KILLED with its n steps alive.
+template <typename R>
+__device__ __forceinline__ bool live_or_kill(const RunDevT<R>& r, int64_t i, Particle<R>& P, uint32_t n,
+                                             unsigned long long* tally) {
+    if (isfinite(P.u[0]) && isfinite(P.u[1]) && isfinite(P.u[2])) return !isnan(P.x);
+    P.x = (R)NAN;
+    P.u[0] = P.u[1] = P.u[2] = (R)0;
+    store_particle<R>(r, i, P);
+    atomicAdd(tally + PE_T_N_NONFINITE, 1ull);
+    atomicAdd(tally + PE_T_N_KILLED, 1ull);
+    atomicAdd(tally + PE_T_KILLED_STEPS, (unsigned long long)n);
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // persistent kernel: grid-stride over tiles of all runs, K steps per launch
 // ---------------------------------------------------------------------------
@@ -495,7 +531,7 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
         StepOut<R> out;
         out.ncs = out.br = false;
         if (active) {
-            step_one<R, G>(t, r, s_h, sig_z, (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
+            step_one<R, G>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
             if (r.box_enable && isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
         }
         if (__any_sync(0xffffffffu, out.ncs || out.br)) {
@@ -552,7 +588,7 @@ __global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev 
         Particle<R> P;
         if (active) {
             load_particle<R>(r, i, P);
-            active = !isnan(P.x);
+            active = live_or_kill<R>(r, i, P, (uint32_t)r.step0, s_tally);
         }
         const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
         tile_steps<R, G>(t, r, s_h, sig_z, i, active, P, steps, s_hist, s_tally);

@@ -12,8 +12,8 @@ static bool plane_kind(int fk) { return fk == FK_PLANE_LP || fk == FK_PLANE_CP; 
 static bool use_stream(const BatchDevT<float>& b, int steps, int block) {
     return b.n_runs == 1 && plane_kind(b.runs[0].fk) && steps <= kStreamMaxSteps && block == kStreamTile;
 }
-// tables, then 128-byte alignment slack, two stage buffers and two mbarriers
-static int stream_smem_bytes(int base) { return base + 128 + 2 * kStageBytes + 16; }
+// tables, then 16-byte alignment slack and the stage buffers
+static int stream_smem_bytes(int base) { return base + 16 + kStreamStages * kStageBytes; }
 
 // The kernel of a launch, its threads per CTA and dynamic shared memory: the 1D
 // plane-wave kinds use the paired kernel (two electrons per thread, block/2 threads

@@ -26,12 +26,6 @@ namespace {
 constexpr uint32_t kPurBH = 0x40000000u;      // per-step tests: counter word 3 = kPurBH + emission step
 constexpr uint32_t kPurBHFree = 0x50000000u;  // free path: counter word 3 = kPurBHFree + emission step
 
-struct PairRec {
-    float x, y, e_minus, e_plus, kx, ky, kz;
-    uint32_t step, photon, id_mech;
-};
-static_assert(sizeof(PairRec) == 40, "pe_pair layout");
-static_assert(sizeof(Photon) == 32, "photon record layout");
 
 // sigma_BH(k) by row interpolation in log k over [2, gamma_max] (0 for k <= 2); the row
 // position (i, w) is kept for the sampling of x
@@ -62,12 +56,6 @@ __device__ __forceinline__ double bh_sample_x(const TablesDev& t, const double* 
     return ik + s * (1.0 - 2.0 * ik);
 }
 
-// the photon's coordinate (direction component d, emission coordinate e) at step m, as the
-// definition computes it: e + d ((m - n_e) c dt), one rounding for the step product and one
-// for the fused multiply-add
-__device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, double e, int64_t ne, int64_t m) {
-    return __fma_rn(d, __dmul_rn((double)(m - ne), c.dt), e);
-}
 
 #ifndef PE_PAIR_MIN_CTAS_SM
 #define PE_PAIR_MIN_CTAS_SM 3      // resident CTAs of 256 threads per SM the registers are sized for

@@ -55,6 +55,12 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
     e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
+// 1 - e^{-x} by the Taylor series x (1 - x/2 + x^2/6 - x^3/24) (for x < 2^-5), paired; the
+// same operations in the same order as one_minus_exp_neg_f32
+__device__ __forceinline__ float2 brems_series2(float2 x) {
+    return mul2(x, fma2(x, fma2(x, fma2(x, P2(-1.0f / 24.0f), P2(1.0f / 6.0f)), P2(-0.5f)), P2(1.0f)));
+}
+
 // ramp sine/cosine of the envelope (0 <= v <= pi/2), paired: the hardware units
 __device__ __forceinline__ void ramp_sincos2(float2 v, float2& s_out, float2& c_out) {
     s_out = make_float2(__sinf(v.x), __sinf(v.y));
@@ -239,10 +245,9 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 const float2 sig = fma2(w, sub2(s1, s0), s0);
                 const float2 um = sqrt2(fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, mul2(Q.u0, Q.u0))));
                 const float2 xb = mul2(mul2(P2(c.K_br), sig), mul2(um, inv_g));
-                // 1 - e^{-x_b} by its Taylor series x (1 - x/2 + x^2/6 - x^3/24) below 2^-5 (truncation
-                // under 2^-26 relative), the library expm1f above
-                const float2 ser = mul2(xb, fma2(xb, fma2(xb, fma2(xb, P2(-1.0f / 24.0f), P2(1.0f / 6.0f)),
-                                                           P2(-0.5f)), P2(1.0f)));
+                // 1 - e^{-x_b} by its Taylor series below 2^-5 (truncation under 2^-26 relative), the
+                // library expm1f above: one_minus_exp_neg_f32 on the paired instructions
+                const float2 ser = brems_series2(xb);
                 float pb_[2] = {ser.x, ser.y};
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -278,11 +283,12 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     }
 }
 
-__device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pair& Q, int k) {
+__device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pair& Q, int k,
+                                         unsigned long long* tally) {
     Particle<float> P;
     load_particle<float>(r, i, P);
+    Q.act[k] = live_or_kill<float>(r, i, P, (uint32_t)r.step0, tally);
     repack(Q, k, P);
-    Q.act[k] = !isnan(P.x);
 }
 
 // K steps of the pair Q (electrons i0 and i1) with warp-aggregated photon appends
@@ -290,7 +296,7 @@ template <int G>
 __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
                                           const float* sig_z, int64_t i0, int64_t i1, Pair& Q, int steps,
                                           unsigned long long* s_hist, unsigned long long* s_tally) {
-    const uint32_t id[2] = {(uint32_t)i0, (uint32_t)i1};
+    const uint32_t id[2] = {r.id0 + (uint32_t)i0, r.id0 + (uint32_t)i1};
     const uint32_t n0 = (uint32_t)r.step0;
     float nf = (float)n0;
     uint32_t n_above = 0;                               // particle-steps with eta above the table
@@ -334,8 +340,8 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
                                                 unsigned long long* s_hist, unsigned long long* s_tally) {
     Pair Q;
     pair_clear(Q);
-    if (i0 < r.n) load_one(r, i0, Q, 0);
-    if (i1 < r.n) load_one(r, i1, Q, 1);
+    if (i0 < r.n) load_one(r, i0, Q, 0, s_tally);
+    if (i1 < r.n) load_one(r, i1, Q, 1, s_tally);
     const bool live0 = i0 < r.n, live1 = i1 < r.n;
     pair_loop<G>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
     if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
@@ -389,157 +395,182 @@ __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t
 
 
 // ---------------------------------------------------------------------------
-// Streaming form for launches of a few steps (the state round-trips HBM): each CTA
-// prefetches the state of its next tile into shared memory with bulk copies (TMA,
-// cp.async.bulk) that complete on an mbarrier while it steps the current tile, so the
-// loads of one tile overlap the arithmetic of the previous one.  Single run; tiles
-// of 256 electrons (x pairs 2 KB, u 3 x 1 KB, tau pairs 2 KB per tile); the ragged
-// last tile and the optional event / wait words use plain loads.
+// Streaming form for launches of a few steps (the state round-trips HBM every launch).
+// Each thread takes two adjacent electrons (2j, 2j + 1) of a 256-electron tile, so one
+// 16-byte vector covers both position pairs (and both optical-depth pairs) and one 8-byte
+// vector both values of each momentum component.  Each thread prefetches its two
+// electrons of the CTA's next tile into its own slots of a shared-memory stage with
+// per-thread asynchronous copies (cp.async, 16 and 8 bytes) while it steps the current
+// tile, and waits only for its own copies (cp.async.wait_group): no barrier, no spin-wait.
+// Results go back with streaming vector stores.  The arithmetic is that of the resident
+// kernel (the paired step is elementwise in its two electrons), so the results are the
+// same bit for bit.  Single run; the ragged end (an odd last electron) and the optional
+// event / wait words use plain loads.
 // ---------------------------------------------------------------------------
-constexpr int kStreamTile = 256;
-constexpr int kStageBytes = kStreamTile * (8 + 4 + 4 + 4 + 8);
+constexpr int kStreamTile = 256;                       // electrons per tile (128 threads x 2)
+constexpr int kStreamThreads = kStreamTile / 2;
+#ifndef PE_STREAM_STAGES
+#define PE_STREAM_STAGES 2    // stages per CTA: tiles in flight = stages - 1
+#endif
+#ifndef PE_STREAM_MIN_CTAS
+#define PE_STREAM_MIN_CTAS PE_PAIR_MIN_CTAS
+#endif
+constexpr int kStreamStages = PE_STREAM_STAGES;
+// one stage: x pairs (float4 per thread), tau pairs (float4), ux, uy, uz (float2 each)
+constexpr int kStageBytes = kStreamThreads * (16 + 16 + 8 + 8 + 8);
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// all of this thread's copy groups but the most recent `n` have landed
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory"); }
+
+// this thread's slots of a stage
+struct StageSlots {
+    uint32_t x, tau, ux, uy, uz;       // shared addresses (for the copies)
+    const float4* px;                  // generic pointers (for the reads)
+    const float4* ptau;
+    const float2 *pux, *puy, *puz;
+};
+__device__ __forceinline__ StageSlots stage_slots(unsigned char* stage, int t) {
+    StageSlots q;
+    unsigned char* b = stage;
+    q.px = reinterpret_cast<const float4*>(b) + t;
+    q.ptau = reinterpret_cast<const float4*>(b + kStreamThreads * 16) + t;
+    q.pux = reinterpret_cast<const float2*>(b + kStreamThreads * 32) + t;
+    q.puy = reinterpret_cast<const float2*>(b + kStreamThreads * 40) + t;
+    q.puz = reinterpret_cast<const float2*>(b + kStreamThreads * 48) + t;
+    q.x = smem_addr(q.px); q.tau = smem_addr(q.ptau);
+    q.ux = smem_addr(q.pux); q.uy = smem_addr(q.puy); q.uz = smem_addr(q.puz);
+    return q;
 }
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
+// copies of electrons 2j, 2j + 1 (both present) into the slots
+__device__ __forceinline__ void stage_issue(const RunDevT<float>& r, int64_t j, const StageSlots& q) {
+    cp_async16(q.x, reinterpret_cast<const float4*>(r.x) + j);
+    cp_async16(q.tau, reinterpret_cast<const float4*>(r.tau) + j);
+    cp_async8(q.ux, reinterpret_cast<const float2*>(r.ux) + j);
+    cp_async8(q.uy, reinterpret_cast<const float2*>(r.uy) + j);
+    cp_async8(q.uz, reinterpret_cast<const float2*>(r.uz) + j);
 }
-// wait for the phase of the given parity to complete; gives up after about 2 s (returns false)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+// a particle is removed (x NaN, finite momenta), live, or has a non-finite momentum
+__device__ __forceinline__ bool finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+
+// electrons 2j, 2j + 1 from the slots (the optional words from global memory)
+__device__ __forceinline__ void stage_take(const RunDevT<float>& r, int64_t j, const StageSlots& q, Pair& Q,
+                                           unsigned long long* tally) {
+    const float4 x = *q.px, tau = *q.ptau;
+    Q.x = make_float2(x.x, x.z);
+    Q.x_lo = make_float2(x.y, x.w);
+    Q.tau = make_float2(tau.x, tau.z);
+    Q.tau_lo = make_float2(tau.y, tau.w);
+    Q.u0 = *q.pux;
+    Q.u1 = *q.puy;
+    Q.u2 = *q.puz;
+    if (r.wait) {
+        const uint2 w = reinterpret_cast<const uint2*>(r.wait)[j];
+        Q.wait[0] = w.x;
+        Q.wait[1] = w.y;
+    } else {
+        Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
     }
-    return false;
-}
-
-// thread 0: bulk copies of the full tile `tile` into stage buffer `buf`
-__device__ __forceinline__ void stream_issue(const RunDevT<float>& r, int64_t tile, unsigned char* buf, uint32_t bar) {
-    const int64_t base = tile * kStreamTile;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of buf first
-    mbar_expect_tx(bar, kStageBytes);
-    const uint32_t d = smem_addr(buf);
-    bulk_g2s(d, (const float2*)r.x + base, kStreamTile * 8, bar);
-    bulk_g2s(d + kStreamTile * 8, (const float*)r.ux + base, kStreamTile * 4, bar);
-    bulk_g2s(d + kStreamTile * 12, (const float*)r.uy + base, kStreamTile * 4, bar);
-    bulk_g2s(d + kStreamTile * 16, (const float*)r.uz + base, kStreamTile * 4, bar);
-    bulk_g2s(d + kStreamTile * 20, (const float2*)r.tau + base, kStreamTile * 8, bar);
-}
-
-// electron j of a staged tile into pair slot k (the optional words from global memory)
-__device__ __forceinline__ void stream_take(const RunDevT<float>& r, const unsigned char* buf, int j, int64_t i,
-                                            Pair& Q, int k) {
-    const float2 x = reinterpret_cast<const float2*>(buf)[j];
-    const float* u = reinterpret_cast<const float*>(buf + kStreamTile * 8);
-    const float2 tau = reinterpret_cast<const float2*>(buf + kStreamTile * 20)[j];
-    set_comp(Q.x, k, x.x); set_comp(Q.x_lo, k, x.y);
-    set_comp(Q.u0, k, u[j]); set_comp(Q.u1, k, u[kStreamTile + j]); set_comp(Q.u2, k, u[2 * kStreamTile + j]);
-    set_comp(Q.tau, k, tau.x); set_comp(Q.tau_lo, k, tau.y);
-    Q.wait[k] = r.wait ? r.wait[i] : PE_WAIT_NEVER;
     if (r.events) {
-        unsigned long long e = r.events[i];
-        Q.ev_cnt[k] = (uint32_t)e;
-        Q.ev_hash[k] = (uint32_t)(e >> 32);
+        const ulonglong2 e = reinterpret_cast<const ulonglong2*>(r.events)[j];
+        Q.ev_cnt[0] = (uint32_t)e.x; Q.ev_hash[0] = (uint32_t)(e.x >> 32);
+        Q.ev_cnt[1] = (uint32_t)e.y; Q.ev_hash[1] = (uint32_t)(e.y >> 32);
+    } else {
+        Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
     }
-    Q.act[k] = !isnan(x.x);
+    Q.act[0] = !isnan(Q.x.x);
+    Q.act[1] = !isnan(Q.x.y);
+    if (!finite3(Q.u0.x, Q.u1.x, Q.u2.x) || !finite3(Q.u0.y, Q.u1.y, Q.u2.y)) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {             // rare: remove and count (as live_or_kill)
+            Particle<float> P = unpack(Q, k);
+            Q.act[k] = live_or_kill<float>(r, 2 * j + k, P, (uint32_t)r.step0, tally);
+            repack(Q, k, P);
+        }
+    }
+}
+
+// electrons 2j, 2j + 1 back to memory (both present; removed ones were stored when removed)
+__device__ __forceinline__ void pair_store(const RunDevT<float>& r, int64_t j, const Pair& Q, bool st0, bool st1) {
+    if (st0 && st1) {
+        __stcs(reinterpret_cast<float4*>(r.x) + j, make_float4(Q.x.x, Q.x_lo.x, Q.x.y, Q.x_lo.y));
+        __stcs(reinterpret_cast<float4*>(r.tau) + j, make_float4(Q.tau.x, Q.tau_lo.x, Q.tau.y, Q.tau_lo.y));
+        __stcs(reinterpret_cast<float2*>(r.ux) + j, Q.u0);
+        __stcs(reinterpret_cast<float2*>(r.uy) + j, Q.u1);
+        __stcs(reinterpret_cast<float2*>(r.uz) + j, Q.u2);
+        if (r.wait) reinterpret_cast<uint2*>(r.wait)[j] = make_uint2(Q.wait[0], Q.wait[1]);
+        if (r.events)
+            reinterpret_cast<ulonglong2*>(r.events)[j] =
+                make_ulonglong2(((unsigned long long)Q.ev_hash[0] << 32) | Q.ev_cnt[0],
+                                ((unsigned long long)Q.ev_hash[1] << 32) | Q.ev_cnt[1]);
+    } else {
+        if (st0) store_particle<float>(r, 2 * j, unpack(Q, 0));
+        if (st1) store_particle<float>(r, 2 * j + 1, unpack(Q, 1));
+    }
 }
 
 template <int G>
-__global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair_stream(TablesDev t, BatchDevT<float> b, int steps) {
+__global__ void __launch_bounds__(kStreamThreads, PE_STREAM_MIN_CTAS) k_step_pair_stream(TablesDev t, BatchDevT<float> b,
+                                                                                         int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
     unsigned long long* s_tally = s_hist + PE_HIST_WORDS;
     float* s_h = reinterpret_cast<float*>(s_tally + PE_TALLY_WORDS);
     float* s_sig = s_h + t.n_eta;
-    // stage buffers on a 128-byte boundary of the shared window after the tables
-    const uint32_t s0 = smem_addr(smem);
-    const uint32_t table_end = s0 + 8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + 4 * (t.n_eta + t.n_Z * t.n_E);
-    unsigned char* stage_buf = smem + (((table_end + 127u) & ~127u) - s0);
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage_buf + 2 * kStageBytes);
+    // the stages on a 16-byte boundary after the tables
+    const uint32_t table_bytes = 8 * (PE_HIST_WORDS + PE_TALLY_WORDS) + 4 * (t.n_eta + t.n_Z * t.n_E);
+    unsigned char* stage_buf = smem + ((table_bytes + 15u) & ~15u);
     const RunDevT<float>& r = b.runs[0];
 
     for (int k = threadIdx.x; k < PE_HIST_WORDS + PE_TALLY_WORDS; k += blockDim.x) s_hist[k] = 0;
     for (int k = threadIdx.x; k < t.n_eta; k += blockDim.x) s_h[k] = t.h32[k];
     for (int k = threadIdx.x; k < t.n_Z * t.n_E; k += blockDim.x) s_sig[k] = t.sig32[k];
-    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
-    if (threadIdx.x == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     __syncthreads();
 
     const int64_t n_tiles = b.tile_start[1];
-    const int64_t n_full = r.n / kStreamTile;          // tiles with all 256 electrons present
+    const int64_t n_pairs = r.n >> 1;                   // j < n_pairs: electrons 2j and 2j + 1 both present
+    const int64_t stride = (int64_t)gridDim.x * kStreamThreads;
     const float* sig_z = s_sig + (size_t)r.iz * t.n_E;
-    uint32_t parity[2] = {0u, 0u};
-    bool pending[2] = {false, false};                   // a copy into the stage awaits its wait
-    bool stuck[2] = {false, false};                     // its wait ran out: the stage is not reused
-    bool broken = false;                                // after a timeout: plain loads only
-    int stage = 0;
-    int64_t tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < n_full) stream_issue(r, tile, stage_buf, bar0);
-    pending[0] = tile < n_full;
-    for (; tile < n_tiles; tile += gridDim.x) {
-        const int64_t next = tile + gridDim.x;
-        if (!broken && next < n_full) {
-            if (threadIdx.x == 0) stream_issue(r, next, stage_buf + (stage ^ 1) * kStageBytes, stage ? bar0 : bar1);
-            pending[stage ^ 1] = true;
-        }
-        const int64_t i0 = tile * kStreamTile + threadIdx.x, i1 = i0 + blockDim.x;
-        Pair Q;
-        pair_clear(Q);
-        bool staged = false;
-        if (pending[stage]) {
-            staged = mbar_wait(stage ? bar1 : bar0, parity[stage]);
-            pending[stage] = false;
-            if (staged) {
-                parity[stage] ^= 1u;
-            } else {
-                stuck[stage] = true;
-                broken = true;
-                if (threadIdx.x == 0) atomicAdd(s_tally + PE_T_N_WAIT_TIMEOUT, 1ull);
-            }
-        }
-        if (staged) {
-            const unsigned char* buf = stage_buf + stage * kStageBytes;
-            stream_take(r, buf, threadIdx.x, i0, Q, 0);
-            stream_take(r, buf, threadIdx.x + blockDim.x, i1, Q, 1);
-        } else {                                        // ragged last tile (or a timed-out copy)
-            if (i0 < r.n) load_one(r, i0, Q, 0);
-            if (i1 < r.n) load_one(r, i1, Q, 1);
-        }
-        const bool live0 = i0 < r.n, live1 = i1 < r.n;
-        pair_loop<G>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
-        if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
-        if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
-        __syncthreads();                                // the stage is read before it is refilled
-        stage ^= 1;
+    // tile k of this CTA (k = 0, 1, ...) is tile blockIdx.x + k gridDim.x, staged in stage k mod S;
+    // the copies of tiles k + 1 .. k + S - 1 are in flight while tile k is stepped
+    const int64_t j0 = (int64_t)blockIdx.x * kStreamThreads + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kStreamStages - 1; ++k) {
+        const int64_t jk = j0 + k * stride;
+        if (jk < n_pairs) stage_issue(r, jk, stage_slots(stage_buf + k * kStageBytes, threadIdx.x));
+        cp_async_commit();
     }
-    // copies still in flight after a timeout must land before the CTA exits (bounded again)
-    for (int k = 0; k < 2; ++k)
-        if (pending[k] || stuck[k]) mbar_wait(k ? bar1 : bar0, parity[k]);
+    int stage = 0;
+    for (int64_t j = j0; j - threadIdx.x < n_tiles * kStreamThreads; j += stride) {
+        const int64_t jn = j + (kStreamStages - 1) * stride;
+        const int sn = stage == 0 ? kStreamStages - 1 : stage - 1;       // (stage + S - 1) mod S
+        if (jn < n_pairs) stage_issue(r, jn, stage_slots(stage_buf + sn * kStageBytes, threadIdx.x));
+        cp_async_commit();
+        cp_async_wait<kStreamStages - 1>();             // this thread's copies of the current tile
+        Pair Q;
+        const bool full = j < n_pairs;
+        if (full) {
+            stage_take(r, j, stage_slots(stage_buf + stage * kStageBytes, threadIdx.x), Q, s_tally);
+        } else {
+            pair_clear(Q);
+            if (2 * j < r.n) load_one(r, 2 * j, Q, 0, s_tally);   // the odd last electron
+        }
+        const bool live0 = 2 * j < r.n, live1 = full;
+        pair_loop<G>(t, r, s_h, sig_z, 2 * j, 2 * j + 1, Q, steps, s_hist, s_tally);
+        pair_store(r, j, Q, live0 && Q.act[0], live1 && Q.act[1]);
+        stage = stage + 1 == kStreamStages ? 0 : stage + 1;
+    }
+    cp_async_wait<0>();
     if (n_tiles > 0) flush_shared<float>(s_hist, s_tally, r);
 }
 

@@ -4,10 +4,14 @@ Requests (one laser-target run each: parameters, electron count, step count)
 arrive over time.  The server admits a waiting request as soon as a slot
 (at most 64 runs per batched launch) and device memory for its buffers are
 free, keeps every admitted run's state resident, and advances all resident runs
-together in one batched persistent launch per iteration of K steps (runs of
-different field kinds go to one launch per kind).  A run that has done its
-steps is retired: its tallies are read and its buffers freed, and its latency
-(arrival to results on the host) is recorded.
+together in batched persistent launches (runs of different field kinds go to one
+launch per kind).  An iteration advances every resident run by
+min(K, the fewest steps any resident run still has to do), so a run is retired
+the moment its steps are done: its tallies are read, its buffers freed, its
+latency (arrival to results on the host) recorded, and its slot and memory go
+to the next waiting request.  Runs admitted at different times therefore share
+launches with changing company and see their launch boundaries at different
+steps of their own.
 
 Because positions and optical depths are kept as exact float pairs across
 launch boundaries, a run's results do not depend on which other runs share its
@@ -41,6 +45,9 @@ class Request:
     tally: object = None
     state: np.ndarray | None = None
     events: np.ndarray | None = None
+    admitted_iteration: int = -1       # server iteration at which the run was admitted
+    resident_at_admission: int = 0     # runs already resident (mid-run) when it was admitted
+    boundaries: list = field(default_factory=list)   # own step counts at the end of each launch set
 
 
 @dataclass
@@ -91,23 +98,36 @@ class Server:
         req.admitted_s = now
         return run
 
-    def run_trace(self, requests: list[Request], realtime: bool = True) -> ServerStats:
-        """Serve the requests (sorted by arrival).  With realtime=False arrivals are
-        taken as already due whenever the GPU would otherwise idle."""
+    def run_trace(self, requests: list[Request], realtime: bool = True,
+                  virtual_step_s: float | None = None) -> ServerStats:
+        """Serve the requests (sorted by arrival).
+
+        realtime=True: arrivals follow the wall clock (the server sleeps while idle).
+        realtime=False: idle time is skipped (the next arrival is taken as due when nothing
+        is resident).  virtual_step_s: the clock is simulated instead -- it advances by
+        virtual_step_s per step of each iteration -- so admissions happen at reproducible
+        iterations (tests); latencies are then in simulated seconds."""
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival_s)
-        active = []                     # (request, run, remaining steps)
+        active = []                     # [request, run, remaining steps]
         stats = ServerStats()
         t0 = time.perf_counter()
-        clock = lambda: time.perf_counter() - t0
+        vclock = [0.0]
+        if virtual_step_s is not None:
+            clock = lambda: vclock[0]
+        else:
+            clock = lambda: time.perf_counter() - t0
         i = 0
         while i < len(pending) or active:
             now = clock()
             if not active and i < len(pending) and pending[i].arrival_s > now:
-                if realtime:
+                if virtual_step_s is not None:
+                    vclock[0] = pending[i].arrival_s
+                elif realtime:
                     time.sleep(min(pending[i].arrival_s - now, 0.05))
                     continue
-                t0 -= pending[i].arrival_s - now          # skip idle time
+                else:
+                    t0 -= pending[i].arrival_s - now          # skip idle time
                 now = clock()
             # admission: arrived, a slot free, memory available
             while i < len(pending) and pending[i].arrival_s <= now and len(active) < self.max_slots:
@@ -115,6 +135,8 @@ class Server:
                 if self.bytes_needed(pending[i]) > free - self.reserve:
                     break
                 req = pending[i]
+                req.admitted_iteration = stats.iterations
+                req.resident_at_admission = len(active)
                 active.append([req, self._admit(req, now), req.steps])
                 self.resident_bytes += self.bytes_needed(req)
                 stats.queue_s.append(now - req.arrival_s)
@@ -122,20 +144,21 @@ class Server:
             if not active:
                 continue
             stats.max_resident = max(stats.max_resident, len(active))
-            # one iteration: every resident run advances by min(K, remaining), grouped by chunk size
-            by_chunk = {}
-            for a in active:
-                by_chunk.setdefault(min(self.K, a[2]), []).append(a)
-            for chunk, group in by_chunk.items():
-                for j in range(0, len(group), MAX_BATCH):
-                    part = group[j:j + MAX_BATCH]
-                    cfg = dict(self.launch)
-                    cfg.setdefault("steps_per_launch", self.K)
-                    pe_step_ex([a[1].handle for a in part], chunk, **cfg)
-                    for a in part:
-                        a[2] -= chunk
-                        stats.particle_steps += chunk * a[1].n
+            # one iteration: every resident run advances by the same chunk, ending when the
+            # first of them is done
+            chunk = min(self.K, min(a[2] for a in active))
+            cfg = dict(self.launch)
+            cfg.setdefault("steps_per_launch", self.K)
+            for j in range(0, len(active), MAX_BATCH):
+                part = active[j:j + MAX_BATCH]
+                pe_step_ex([a[1].handle for a in part], chunk, **cfg)
+                for a in part:
+                    a[2] -= chunk
+                    a[0].boundaries.append(a[0].steps - a[2])
+                    stats.particle_steps += chunk * a[1].n
             stats.iterations += 1
+            if virtual_step_s is not None:
+                vclock[0] += chunk * virtual_step_s
             # retire finished runs (reading the tallies synchronises the stream)
             still = []
             for a in active:

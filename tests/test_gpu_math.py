@@ -1,0 +1,86 @@
+"""The FP32 step's hand-written forms against the exact values and against CUDA's own functions.
+
+The paired FP32 step replaces three library calls by forms of its own: 1/d (d >= 1) by the
+hardware reciprocal estimate refined by one Newton-Raphson step; the carrier-phase sine and
+cosine by a Cody-Waite reduction by 2 pi followed by the hardware sine and cosine; and the
+probability 1 - e^-x of Eq. 4 by a four-term Taylor series below 2^-5.  pe_math_probe runs the
+very device functions the step uses; here they are swept over the ranges the step feeds them
+and compared with the exact values (FP64 on the host, of the same float inputs), with the
+error bounds the design states, and with CUDA's __frcp_rn, sinf, cosf and expm1f.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1612_07592_gb300 as pe
+
+pytestmark = pytest.mark.gpu
+M = pe.PE_MATH
+
+
+def probe(fn, x):
+    import torch
+    xin = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    out = torch.empty_like(xin)
+    s = torch.cuda.current_stream()
+    pe.pe_math_probe(fn, xin.data_ptr(), out.data_ptr(), xin.numel(), s.cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def ulp(v):
+    """Spacing of floats at |v| (normal range)."""
+    e = np.floor(np.log2(np.abs(v)))
+    return np.ldexp(1.0, (e - 23).astype(int))
+
+
+def test_reciprocal_within_one_ulp():
+    rng = np.random.default_rng(1)
+    d = np.concatenate([np.exp(rng.uniform(0.0, math.log(1e5), 1 << 20)),
+                        1.0 + rng.uniform(0.0, 1.0, 1 << 18), np.array([1.0, 2.0, 3.0, 1e5])]).astype(np.float32)
+    exact = 1.0 / d.astype(np.float64)
+    ours = probe(M["RCP"], d)
+    cuda = probe(M["CUDA_RCP"], d)
+    e_ours = np.abs(ours - exact) / ulp(exact)
+    e_cuda = np.abs(cuda - exact) / ulp(exact)
+    print(f"rcp: max {e_ours.max():.3f} ulp (CUDA __frcp_rn {e_cuda.max():.3f}), "
+          f"{np.mean(ours != cuda):.4f} of results differ from the correctly rounded one")
+    assert e_cuda.max() <= 0.5 + 1e-9
+    assert e_ours.max() <= 1.0
+
+
+@pytest.mark.parametrize("lo,hi,bound_log2", [(-math.pi, math.pi, -21.4), (-400.0, 400.0, -21.0)])
+def test_phase_sine_cosine(lo, hi, bound_log2):
+    """[-pi, pi]: the hardware units alone (bound 2^-21.4); [-400, 400] covers the phases
+    t - x and t + x - 2 x_m of 4000 steps of T/100 (the reduction adds at most half an ulp of
+    the reduced argument)."""
+    rng = np.random.default_rng(2)
+    v = np.concatenate([rng.uniform(lo, hi, 1 << 21), np.linspace(lo, hi, 1 << 16)]).astype(np.float32)
+    vd = v.astype(np.float64)
+    s, c = probe(M["SIN"], v), probe(M["COS"], v)
+    np.testing.assert_array_equal(s, probe(M["SIN1"], v))       # paired and one-electron forms agree
+    np.testing.assert_array_equal(c, probe(M["COS1"], v))
+    es, ec = np.abs(s - np.sin(vd)).max(), np.abs(c - np.cos(vd)).max()
+    cs = np.abs(probe(M["CUDA_SIN"], v) - np.sin(vd)).max()
+    cc = np.abs(probe(M["CUDA_COS"], v) - np.cos(vd)).max()
+    print(f"[{lo:g}, {hi:g}]: sin {math.log2(es):.2f}, cos {math.log2(ec):.2f} (log2 abs error); "
+          f"CUDA sinf {math.log2(cs):.2f}, cosf {math.log2(cc):.2f}")
+    assert max(es, ec) < 2.0 ** bound_log2
+
+
+def test_brems_probability_series():
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.exp(rng.uniform(math.log(1e-10), math.log(2.0 ** -5), 1 << 20)),
+                        rng.uniform(2.0 ** -5, 1.0, 1 << 16)]).astype(np.float32)
+    exact = -np.expm1(-x.astype(np.float64))
+    ours = probe(M["BREMS_P"], x)
+    np.testing.assert_array_equal(ours, probe(M["BREMS_P1"], x))  # paired and one-electron forms agree
+    cuda = probe(M["CUDA_EXPM1"], x)
+    rel = np.abs(ours - exact) / exact
+    relc = np.abs(cuda - exact) / exact
+    small = x < 2.0 ** -5
+    print(f"1 - e^-x: series max rel {rel[small].max():.3g} (expm1f {relc[small].max():.3g}); "
+          f"above 2^-5 {rel[~small].max():.3g}")
+    assert rel[small].max() < 1.0e-7
+    np.testing.assert_array_equal(ours[~small], cuda[~small])

@@ -8,6 +8,7 @@ fingerprint matches the oracle's, a bounded fraction of legitimate event flips,
 and the photon spectrum statistically equal (chi-square).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -27,14 +28,76 @@ F32_RTOL = 1e-5
 # On the 1D Au a0 = 270 workload the time step T/100 does not resolve the passages
 # through the nodes of the vector potential at gamma ~ 5, where one step changes u by
 # ~8: the discrete map is ill-conditioned there (the FP64 oracle itself breaks the
-# plane-wave invariant gamma - u_x by ~10 % in such a step and responds to a 2^-24
-# perturbation of the initial momenta by up to ~1e-4; see the oracle pins).  For that
-# workload the bound is distributional: most particles within F32_RTOL, all within
-# F32_ILL_MAX.
-F32_FRAC_WITHIN = 0.6
-F32_ILL_P95 = 1e-3
-F32_ILL_MAX = 1e-2
+# plane-wave invariant gamma - u_x by ~10 % in such a step; see the oracle pins).  For that
+# workload the bound is the oracle's own response to FP32-sized rounding:
+# tests/golden/fp32_error_model.txt holds, for the FP64 oracle whose momenta are perturbed by up
+# to one FP32 ulp after every step, the event-match fraction and the fraction of matched
+# electrons below each error threshold (momentum, position, optical depth).  The FP32 path
+# must do no worse at any threshold, within 3 sigma of the two binomial estimates.
 WELL_RESOLVED = {"1d-al-a27-rest", "2d-au-a855-cp"}
+MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fp32_error_model.txt")
+THRESHOLDS = (1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2)
+
+
+def fp32_model(case):
+    rows = {}
+    for ln in open(MODEL_PATH):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        p = ln.split()
+        if p[0] == case:
+            rows[p[1]] = dict(n=int(p[2]), match=float(p[3]), frac=np.array([float(v) for v in p[4:]]))
+    return rows
+
+
+def _sig(f, n):
+    # binomial variance at (k + 1/2) / (n + 1), so that a fraction of 0 or 1 still carries sampling noise
+    q = (f * n + 0.5) / (n + 1.0)
+    return q * (1.0 - q) / max(n, 1)
+
+
+def assert_no_worse_than_model(case, match, errs, n_total):
+    """FP32 event-match fraction and error CDFs (u, x, tau over matched electrons) against the
+    oracle's per-step one-ulp model of the same electrons, threshold by threshold."""
+    model = fp32_model(case)
+    n_model_total = round(model["u"]["n"] / model["u"]["match"])
+    m = match.mean()
+    sig = math.sqrt(_sig(model["u"]["match"], n_model_total) + _sig(m, n_total))
+    assert m >= model["u"]["match"] - 3 * sig, ("event match", m, model["u"]["match"])
+    for q, e in errs.items():
+        for t, fm in zip(THRESHOLDS, model[q]["frac"]):
+            fg = float(np.mean(e < t))
+            sig = math.sqrt(_sig(fm, model[q]["n"]) + _sig(fg, len(e)))
+            assert fg >= fm - 3 * sig, (q, t, fg, fm)
+
+
+def state_errors(st, st_o, a0):
+    """Relative FP32 errors per electron: momentum (scale max(|u|, a0)), position (max(|x|, 1)),
+    optical depth (max(|tau|, 1)); the definitions of the model file."""
+    eu = np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / np.maximum(np.abs(st_o[:, 2:5]).max(1), a0)
+    ex = np.abs(st[:, 0:2] - st_o[:, 0:2]).max(1) / np.maximum(np.abs(st_o[:, 0:2]).max(1), 1.0)
+    et = np.abs(st[:, 5] - st_o[:, 5]) / np.maximum(np.abs(st_o[:, 5]), 1.0)
+    return eu, ex, et
+
+
+def assert_yields_within_flips(tal, tal_o, ev, ev_o):
+    """Photon counts against the oracle's on the same electrons and draws: an electron whose event
+    word matches emitted the same numbers of NCS and brems photons, so each total differs exactly
+    by the emissions of the electrons whose words differ; the stored/below-cut split can further
+    differ only for photons within FP32 rounding of the 1 m c^2 cut (at most 2 here)."""
+    ev, ev_o = ev.astype(np.uint64), ev_o.astype(np.uint64)
+    mis = ev != ev_o
+    for mech, (st_k, bl_k) in enumerate((("N_NCS_STORED", "N_NCS_BELOW"), ("N_BR_STORED", "N_BR_BELOW"))):
+        sh = np.uint64(16 * mech)
+        cg = ((ev >> sh) & np.uint64(0xFFFF)).astype(np.int64)
+        co = ((ev_o >> sh) & np.uint64(0xFFFF)).astype(np.int64)
+        tot_g = int(tal[pe.T[st_k]]) + int(tal[pe.T[bl_k]])
+        tot_o = int(tal_o[O.T[st_k]]) + int(tal_o[O.T[bl_k]])
+        assert tot_g == int(cg.sum()) and tot_o == int(co.sum()), (st_k, "totals against event words")
+        assert tot_g - tot_o == int((cg - co)[mis].sum()), st_k
+        flips = int((cg + co)[mis].sum())
+        assert abs(int(tal[pe.T[st_k]]) - int(tal_o[O.T[st_k]])) <= flips + 2, (st_k, flips)
+
 
 _TAB = {}
 
@@ -59,6 +122,7 @@ def tables(tp, Z):
 def orun(run: dict, Z):
     d = dict(run)
     d.pop("precision", None)
+    d.pop("id0", None)                  # the oracle takes the global ids themselves
     d["iz"] = list(Z).index(d["Z"])
     return O.run_params(**d)
 
@@ -213,18 +277,26 @@ def test_f64_parity(case):
     r.close()
 
 
-def test_f64_persistent_equals_plain():
-    run = W.base_run(a0=270.0, init_dist=1, seed=5, **W.AU)
+@pytest.mark.parametrize("case", ["1d-au-a270-mj", "2d-au-a855-cp", "1d-au-a270-refl-cp", "beam-au-brems-null"])
+def test_f64_persistent_equals_plain(case):
+    """The FP64 plain kernel (one step per launch, global atomics) and the FP64 persistent kernel
+    (K steps per launch in registers, shared-memory accumulators) round every operation alike
+    (their translation unit contracts no multiply-add), so they agree bit for bit: state, event
+    words, every tally word, histograms and photon records."""
+    runkw, n, steps = CASES[case]
+    run = W.base_run(**runkw)
     lt, _ = tables(_tp(48), (13.0, 79.0))
-    a = pe.Run(lt, pe.run_params(precision=pe.PE_F64, **run), 700, events=True)
-    b = pe.Run(lt, pe.run_params(precision=pe.PE_F64, **run), 700, events=True)
-    pe.pe_step([a.handle], 500)
-    pe.pe_step_ex([b.handle], 500, block=128, steps_per_launch=37)
-    # same arithmetic; the two kernels may contract a*b+c into FMAs differently (~1e-15)
-    np.testing.assert_allclose(a.state(), b.state(), rtol=1e-10, atol=1e-12)
+    a = pe.Run(lt, pe.run_params(precision=pe.PE_F64, **run), n, events=True)
+    b = pe.Run(lt, pe.run_params(precision=pe.PE_F64, **run), n, events=True)
+    pe.pe_step([a.handle], steps)
+    pe.pe_step_ex([b.handle], steps, block=128, steps_per_launch=37)
+    np.testing.assert_array_equal(a.state(), b.state())
     np.testing.assert_array_equal(a.event_words(), b.event_words())
+    if a.wait is not None:
+        np.testing.assert_array_equal(a.wait_words(), b.wait_words())
     ta, tb = a.tally_out(), b.tally_out()
-    assert list(ta.tally)[:16] == list(tb.tally)[:16] and bytes(ta.hist) == bytes(tb.hist)
+    assert bytes(ta.tally) == bytes(tb.tally) and bytes(ta.hist) == bytes(tb.hist)
+    np.testing.assert_array_equal(sort_photons(a.photon_records()), sort_photons(b.photon_records()))
 
 
 # ------------------------------------------------------------- FP32 parity ----
@@ -240,27 +312,17 @@ def test_f32_parity(case):
     ev = r.event_words()
     match = ev == ev_o
     frac = match.mean()
-    g = np.sqrt(1 + (st[:, 2:5] ** 2).sum(1))
-    go = np.sqrt(1 + (st_o[:, 2:5] ** 2).sum(1))
-    scale_u = np.maximum(np.abs(st_o[:, 2:5]).max(1), max(run["a0"], 1.0))
-    err_u = (np.abs(st[:, 2:5] - st_o[:, 2:5]).max(1) / scale_u)[match]
-    err_x = (np.abs(st[:, 0:2] - st_o[:, 0:2]).max(1) / np.maximum(np.abs(st_o[:, 0:2]).max(1), 1.0))[match]
-    print(f"{case}: event match {frac:.4f}, max rel err u {err_u.max():.2e} x {err_x.max():.2e}, "
-          f"gamma {np.abs(g / go - 1)[match].max():.2e}")
-    assert frac > 0.9
+    eu, ex, et = state_errors(st, st_o, max(run["a0"], 1.0))
+    err_u, err_x, err_t = eu[match], ex[match], et[match]
+    print(f"{case}: event match {frac:.4f}, max rel err u {err_u.max():.2e} x {err_x.max():.2e} tau {err_t.max():.2e}, "
+          f"within {F32_RTOL:g}: u {np.mean(err_u < F32_RTOL):.3f} x {np.mean(err_x < F32_RTOL):.3f} "
+          f"tau {np.mean(err_t < F32_RTOL):.3f}, median u {np.median(err_u):.2e}")
     if case in WELL_RESOLVED:
+        assert frac > 0.9
         assert err_u.max() < F32_RTOL and err_x.max() < F32_RTOL
     else:
-        print(f"   within {F32_RTOL:g}: {np.mean(err_u < F32_RTOL):.3f}, median {np.median(err_u):.2e}, "
-              f"p95 {np.quantile(err_u, 0.95):.2e}")
-        assert np.median(err_u) < F32_RTOL
-        assert np.mean(err_u < F32_RTOL) > F32_FRAC_WITHIN
-        assert np.quantile(err_u, 0.95) < F32_ILL_P95
-        assert err_u.max() < F32_ILL_MAX
-    # photon yields agree within Poisson noise (plus flips)
-    for k in ("N_NCS_STORED", "N_NCS_BELOW", "N_BR_STORED"):
-        a, b = int(out.tally[pe.T[k]]), int(tal_o[O.T[k]])
-        assert abs(a - b) <= 4 * math.sqrt(max(b, 1)) + 0.05 * b, (k, a, b)
+        assert_no_worse_than_model("small", match, dict(u=err_u, x=err_x, tau=err_t), n)
+    assert_yields_within_flips(np.frombuffer(bytes(out.tally), dtype=np.uint64), tal_o, ev, ev_o)
     r.close()
 
 
@@ -430,12 +492,14 @@ def test_absorbing_box_accounting():
 
 # ------------------------------------------------------ full-size sampled ----
 def test_config2_full_size_sampled():
-    """Config 2 at full size (1e6 electrons, 256x256 tables) in the benchmark's launch
-    shape; 256 sampled particles advanced one by one by the oracle."""
+    """Config 2 at full size (1e6 electrons, 256x256 tables, the whole 4000-step job) in the
+    benchmark's launch shape; 256 sampled electrons advanced one by one by the oracle; momenta,
+    positions and optical depths against the oracle's per-step one-ulp model of the same
+    electrons."""
     c = W.config2()
     Z = c["Z"]
     lt, ot = tables(c["tables"], Z)
-    steps = 1000
+    steps = c["steps"]
     r, out = run_gpu(lt, c["run"], c["n"], steps, pe.PE_F32, capacity=1 << 24)
     st = r.state()
     ev = r.event_words()
@@ -446,15 +510,11 @@ def test_config2_full_size_sampled():
     ids = np.random.default_rng(0).choice(c["n"], 256, replace=False)
     st_o, _, _, _, _, ev_o = run_oracle(ot, c["run"], Z, ids, steps)
     match = ev[ids] == ev_o
-    assert match.mean() > 0.9
-    scale = np.maximum(np.abs(st_o[:, 2:5]).max(1), c["run"]["a0"])
-    err = (np.abs(st[ids, 2:5] - st_o[:, 2:5]).max(1) / scale)[match]
-    print(f"config 2 full size: event match {match.mean():.4f}, median {np.median(err):.2e}, "
-          f"within {F32_RTOL:g}: {np.mean(err < F32_RTOL):.3f}, max {err.max():.2e}")
-    assert np.median(err) < F32_RTOL
-    assert np.mean(err < F32_RTOL) > F32_FRAC_WITHIN
-    assert np.quantile(err, 0.95) < F32_ILL_P95
-    assert err.max() < F32_ILL_MAX
+    eu, ex, et = state_errors(st[ids], st_o, c["run"]["a0"])
+    print(f"config 2 full size: event match {match.mean():.4f}, u median {np.median(eu[match]):.2e} "
+          f"within {F32_RTOL:g}: u {np.mean(eu[match] < F32_RTOL):.3f} x {np.mean(ex[match] < F32_RTOL):.3f} "
+          f"tau {np.mean(et[match] < F32_RTOL):.3f}")
+    assert_no_worse_than_model("full", match, dict(u=eu[match], x=ex[match], tau=et[match]), len(ids))
     r.close()
 
 
@@ -508,11 +568,12 @@ def test_config4_full_size_sampled():
     match = np.concatenate(matches)
     print(f"config 4 full size: event match {match.mean():.4f}, median {np.median(err):.2e}, "
           f"within {F32_RTOL:g}: {np.mean(err < F32_RTOL):.3f}, p95 {np.quantile(err, 0.95):.2e}, max {err.max():.2e}")
-    assert match.mean() > 0.9
-    assert np.median(err) < F32_RTOL
-    assert np.mean(err < F32_RTOL) > F32_FRAC_WITHIN
-    assert np.quantile(err, 0.95) < F32_ILL_P95
-    assert err.max() < F32_ILL_MAX
+    # the batch's runs take 1000 steps: bounded by the model of the 1500-step a0 = 270 Au case
+    model = fp32_model("small")["u"]
+    assert match.mean() >= model["match"] - 3 * math.sqrt(_sig(model["match"], 1000) + _sig(match.mean(), len(match)))
+    for t, fm in zip(THRESHOLDS, model["frac"]):
+        fg = float(np.mean(err < t))
+        assert fg >= fm - 3 * math.sqrt(_sig(fm, model["n"]) + _sig(fg, len(err))), (t, fg, fm)
 
 
 # ------------------------------------------------------- graph, autotune ----
@@ -556,27 +617,38 @@ def test_autotune_picks_a_shape():
 
 # ----------------------------------------------------------------- serving ----
 def test_serving_alone_equals_mix():
+    """Continuous batching: requests arrive while others are on the GPU and are admitted mid-run
+    (a simulated clock of 1 ms per step makes the admission points reproducible); every iteration
+    ends when the first resident run is done, so the runs share launches with changing company and
+    their launch boundaries fall at different steps of their own.  Each result equals the same run
+    stepped alone, bit for bit."""
     from paper_1612_07592_gb300.serve import Request, Server
     Z = (13.0, 79.0)
     lt, _ = tables(_tp(48), Z)
     kinds = [W.base_run(a0=270.0, init_dist=1, seed=11, run_id=0, **W.AU),
              W.base_run(a0=100.0, seed=12, run_id=1),
              W.base_run(a0=855.0, polarisation=1, geometry=1, slab_thick_m=2e-6, seed=13, run_id=2, **W.AU),
-             W.base_run(a0=60.0, seed=14, run_id=3, **W.AU)]
-    sizes, steps = [900, 300, 500, 257], [700, 450, 333, 600]
+             W.base_run(a0=60.0, seed=14, run_id=3, **W.AU),
+             W.base_run(a0=270.0, polarisation=1, init_dist=1, seed=15, run_id=4, **W.AU)]
+    sizes, steps = [900, 300, 500, 257, 611], [700, 450, 333, 600, 3]
+    arrivals = [0.0, 0.3, 0.55, 0.9, 1.0]
     alone = []
-    for rk, n, s in zip(kinds, sizes, steps):
+    for rk, n, st in zip(kinds, sizes, steps):
         r = pe.Run(lt, pe.run_params(precision=pe.PE_F32, **rk), n, capacity=1 << 16, events=True)
-        pe.pe_step([r.handle], s)
+        pe.pe_step([r.handle], st)
         alone.append((r.state(), r.event_words(), bytes(r.tally_out().tally), bytes(r.tally_out().hist)))
         r.close()
-    # all four arrive together: they share every launch until the shorter ones retire
-    reqs = [Request(arrival_s=0.0, n=n, steps=s, run=rk, capacity=1 << 16)
-            for k, (rk, n, s) in enumerate(zip(kinds, sizes, steps))]
+    reqs = [Request(arrival_s=t, n=n, steps=st, run=rk, capacity=1 << 16)
+            for t, rk, n, st in zip(arrivals, kinds, sizes, steps)]
     srv = Server(lt, steps_per_iteration=128, keep_results=True)
-    stats = srv.run_trace(reqs, realtime=False)
-    assert stats.summary()["requests"] == 4 and stats.max_resident == 4
+    stats = srv.run_trace(reqs, realtime=False, virtual_step_s=1e-3)
+    assert stats.summary()["requests"] == len(reqs) and stats.max_resident >= 3
+    mid = [q for q in reqs if q.resident_at_admission > 0 and q.admitted_iteration > 0]
+    assert len(mid) >= 3, [(q.admitted_iteration, q.resident_at_admission) for q in reqs]
+    offsets = {tuple(b % 128 for b in q.boundaries) for q in reqs}
+    assert len(offsets) >= 3, [q.boundaries for q in reqs]
     for q, (st, ev, tal, hist) in zip(reqs, alone):
+        assert q.boundaries[-1] == q.steps
         np.testing.assert_array_equal(q.state, st)
         np.testing.assert_array_equal(q.events, ev)
         assert bytes(q.tally.tally) == tal and bytes(q.tally.hist) == hist

@@ -554,3 +554,41 @@ def test_bunch_energy_loss_radiation_length(E0, target):
     emitted = O.fixed_to_float(tally, O.T["E_BR_STORED"])
     lost = (g0 - g).sum()
     assert abs(emitted / lost - 1) < 1e-9
+
+
+def test_fp32_error_model_file_is_the_oracles():
+    """tests/golden/fp32_error_model.txt (the bound of the FP32 parity tests on the 1D Au a0 = 270
+    workload) is what its script computes from the oracle: the small case is recomputed here and
+    must match the stored line.  The model itself: a one-ulp per-step momentum perturbation moves
+    more electrons past 1e-5 than a single 2^-24 kick of the initial momenta does (the FP32 path
+    rounds at every step, so the per-step model is the one that applies), and it never moves the
+    positions, which the FP32 path keeps as compensated pairs, as far as the momenta."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_fp32_error_model.py")
+    spec = importlib.util.spec_from_file_location("make_fp32_error_model", path)
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    tp, Z, run, ids, steps = mk.cases()["small"]
+    m, eu, ex, et = mk.model(tp, Z, run, ids, steps)
+    stored = {}
+    for ln in open(mk.OUT):
+        p = ln.split()
+        if p and p[0] == "small":
+            stored[p[1]] = [float(v) for v in p[2:]]
+    for q, e in (("u", eu), ("x", ex), ("tau", et)):
+        got = [float(m.sum()), float(m.mean())] + [float(np.mean(e < t)) for t in mk.THRESHOLDS]
+        np.testing.assert_allclose(got, stored[q], rtol=0, atol=2e-6)
+    # a single initial kick of 2^-24 leaves more electrons within 1e-5 than the per-step model
+    ot = O.Tables(O.table_params(**{("photon_min" if k == "photon_min_mc2" else k): v for k, v in tp.items()}),
+                  list(Z))
+    d = dict(run)
+    d["iz"] = list(Z).index(d["Z"])
+    rp = O.run_params(**d)
+    a = O.init(ot, rp, ids)
+    b = a.copy()
+    b[:, 2:5] *= 1 + np.where((ids[:, None] + np.arange(3)[None, :]) % 2 == 0, 1.0, -1.0) * 2.0 ** -24
+    O.run(ot, rp, ids, a, 0, steps, capacity=1 << 16)
+    O.run(ot, rp, ids, b, 0, steps, capacity=1 << 16)
+    eu1, _, _ = mk.errors(a, b, run["a0"])
+    assert np.mean(eu1 < 1e-5) > np.mean(eu < 1e-5) + 0.05
+    assert np.mean(ex < 1e-5) > np.mean(eu < 1e-5)
