@@ -33,10 +33,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "emitting particle-steps/s at 1 GB300 (FP32/batched vs FP64 plain); % HBM roofline; p99"
 UNIT = "particle-steps/s"
-# Algorithmic FP32 operations of one particle-step of the 1D LP case (fields, Boris push,
-# eta, rate lookup, optical depth, compensated position update; a mul+add pair counts 2).
-FLOP_PER_PSTEP_1D = 132
-FLOP_COUNT_SOURCE = "hand count of the 1D LP step (a multiply-add counts 2)"
+# FP32 operations of one particle-step of the headline job, counted by ncu's SASS counters on one
+# launch of the whole job (1e6 electrons x 4000 steps): 2 per FFMA, 4 per FFMA2, 1 per FADD/FMUL,
+# 2 per FADD2/FMUL2, over the 4e9 particle-steps (profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md)
+FLOP_PER_PSTEP_1D = 133.9
+FLOP_COUNT_SOURCE = "ncu SASS counters on the headline launch (FFMA 2, FFMA2 4, FADD/FMUL 1, FADD2/FMUL2 2)"
 # Algorithmic bytes of one particle-step when the state round-trips memory every step:
 # read + write of x (float pair, 8 B), ux, uy, uz (f32) and tau (float pair, 8 B) in 1D;
 # + y (float pair) in 2D.
@@ -46,10 +47,10 @@ BYTES_PER_PSTEP_2D = 72
 # count the hot-path scope uses for its 60 % target
 BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per electron and launch of the dominant kernel, from an ncu capture
-# of one 400-step launch on 2e5 electrons of the same physics (7.45 MB: the state once plus the
-# cold emission tables); None once the kernel changes after that capture.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 37.3
+# DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
+# capture of the headline launch (35.5 MB for 1e6 electrons: the state read once, the final state
+# partly still in L2 at the end, the cold emission tables); None once the kernel changes.
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 35.54
 
 
 def peaks():
@@ -165,12 +166,18 @@ def main():
                     help="profiling run only: one PE_PIC_1D job (--particles, --job-steps) of the config-2 physics")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="profiling run only: the 1 GeV Au bunch (--particles electrons), then two pair transports")
+    ap.add_argument("--profile-bw", action="store_true",
+                    help="profiling run only: the reflected-wave job (--particles electrons), then two Breit-Wheeler "
+                         "transports of its photons")
     args = ap.parse_args()
     if args.profile_pic:
         profile_pic(args.particles or 200_000, args.job_steps or 500)
         return
     if args.profile_pairs:
         profile_pairs(args.particles or 100_000)
+        return
+    if args.profile_bw:
+        profile_bw(args.particles or 100_000)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -218,10 +225,13 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     n, S = cfg["n"], cfg["steps"]
+    if world * n > (1 << 32):
+        raise SystemExit("electron ids would exceed 2^32")
     tables = pe.pe_create_tables(cfg["tables"], cfg["Z"])
     stream = torch.cuda.Stream()
-    # each rank runs its own job on its own Philox run id (weak scaling: no data exchange)
-    run = dict(cfg["run"], run_id=rank)
+    # one run of world x n electrons split by electron id: rank r steps ids [r n, (r + 1) n) (same seed
+    # and run id; weak scaling, no exchange while stepping; the tallies are merged after timing)
+    run = dict(cfg["run"], id0=rank * n)
     launch = dict(block=args.block, ctas_per_sm=args.ctas_per_sm, steps_per_launch=args.steps_per_launch)
     cap = 1 << 24
     with torch.cuda.stream(stream):
@@ -281,10 +291,18 @@ def main():
     clocks.__exit__()
     out = r.tally_out()
     ms = float(np.mean(times))
+    merged = None
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+        # the one exchange of the partitioned run: exact merge of tallies and histograms (after timing)
+        from paper_1612_07592_gb300.shard import allgather_merge
+        gloo = dist.new_group(backend="gloo")
+        mt, mh = allgather_merge(np.frombuffer(bytes(out.tally), dtype=np.uint64),
+                                 np.frombuffer(bytes(out.hist), dtype=np.uint64), group=gloo)
+        merged = {"photons": int(mt[pe.T["N_PHOTONS"]]), "ncs_stored": int(mt[pe.T["N_NCS_STORED"]]),
+                  "brems_stored": int(mt[pe.T["N_BR_STORED"]]), "hist_entries": int(mh.sum())}
     pst = out.live_particle_steps
     value = pst * world / (ms * 1e-3)
 
@@ -297,7 +315,7 @@ def main():
                       "kernel": "k_step_pair (FP32 persistent, two electrons per thread)",
                       "steps_per_launch": args.steps_per_launch or min(S, 4096),
                       "block": args.block or 256, "l2": "flushed between timed jobs (256 MB write)",
-                      "parallelism": f"dp{world} (independent jobs per GPU)"},
+                      "parallelism": f"dp{world} (one run of {world} x {n} electrons split by electron id)"},
            "gpu_launches": int(launches),
            "clocks": clocks.summary(),
            "wall_s_timed_region": wall}
@@ -335,6 +353,8 @@ def main():
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"{ns} of {n} electrons (strided ids) x {S} steps, {dt:.1f} s"}
+    if merged is not None:
+        res["merged_tally"] = merged
     if rank == 0:
         print(json.dumps(res))
     r.close()
@@ -436,7 +456,7 @@ def batch64(pe, stream, flush):
                                                                  steps_per_launch=(250, 500)), use_cache=False)
     snaps = [r.snapshot() for r in runs]
     times = []
-    for k in range(3):
+    for k in range(4):                              # one warm-up, three timed
         with torch.cuda.stream(stream):
             for r, sn in zip(runs, snaps):
                 r.restore(sn)
@@ -475,7 +495,7 @@ def gauss2d(pe, stream, flush):
     stream.synchronize()
     snap = r.snapshot()
     times = []
-    for k in range(3):
+    for k in range(4):                              # one warm-up, three timed
         with torch.cuda.stream(stream):
             r.restore(snap)
             flush.fill_(1.0)
@@ -498,7 +518,7 @@ def gauss2d(pe, stream, flush):
     return res
 
 
-def _timed_jobs(pe, r, tables, steps, stream, flush, reps=3):
+def _timed_jobs(pe, r, tables, steps, stream, flush, reps=4):
     """Mean CUDA-event time of reps - 1 jobs (the first is warm-up) from the same initial state."""
     import torch
     snap = r.snapshot()
@@ -620,6 +640,28 @@ def profile_pairs(n):
     r.close()
 
 
+def profile_bw(n):
+    """Profiling run: the reflected-wave job with n electrons (untimed), then two Breit-Wheeler
+    transports of its photons (the second is the one to capture)."""
+    import torch
+    import paper_1612_07592_gb300 as pe
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.config2()
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    run = dict(c["run"], reflect_r=1.0, mirror_x_m=c["run"]["slab_x0_m"] + c["run"]["slab_thick_m"])
+    r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **run), n, capacity=1 << 26)
+    pe.pe_step([r.handle], c["steps"])
+    bw = pe.pe_bw_tables_create(64, 1e-2, 1e3, 128)
+    out = None
+    for _ in range(2):
+        out = r.bw_transport(bw, capacity=1 << 22)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_bw": True, "electrons": n, "photons": int(r.tally_out().photons_stored),
+                      "pairs": out[1], "photon_steps": int(out[2][pe.PT["N_TESTS"]])}))
+    pe.pe_bw_tables_destroy(bw)
+    r.close()
+
+
 def reflected(pe, tables, cfg, stream, flush):
     """The headline 1D Au a0 = 270 job with the pulse reflected by a mirror at the slab's rear face
     (r = 1): electrons meet the counter-propagating wave and emit at eta ~ 1."""
@@ -630,11 +672,44 @@ def reflected(pe, tables, cfg, stream, flush):
     stream.synchronize()
     ms = _timed_jobs(pe, r, tables, cfg["steps"], stream, flush)
     t = r.tally_out()
+    res = {"value": t.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": cfg["n"],
+           "steps": cfg["steps"], "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]),
+           "ncs_below_cut": int(t.tally[pe.T["N_NCS_BELOW"]]), "photons": int(t.tally[pe.T["N_PHOTONS"]]),
+           "kernel": "k_step_persistent (FP32, reflected-wave field kind)",
+           "breit_wheeler": bw_of_photons(pe, r, t.photons_stored, stream, flush)}
     r.close()
-    return {"value": t.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": cfg["n"],
-            "steps": cfg["steps"], "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]),
-            "ncs_below_cut": int(t.tally[pe.T["N_NCS_BELOW"]]), "photons": int(t.tally[pe.T["N_PHOTONS"]]),
-            "kernel": "k_step_persistent (FP32, reflected-wave field kind)"}
+    return res
+
+
+def bw_of_photons(pe, r, n_ph, stream, flush, reps=3):
+    """Breit-Wheeler conversion (Sec. 1) of a run's stored photons in the run's fields up to its last
+    step (FP32 transport), timed by CUDA events on the run's stream after one warm-up, L2 flushed."""
+    import torch
+    bw = pe.pe_bw_tables_create(64, 1e-2, 1e3, 128)
+    cap = max(n_ph // 2, 1)
+    with torch.cuda.stream(stream):
+        pairs = torch.empty(cap * 10, dtype=torch.int32, device="cuda")
+        tally = torch.zeros(pe.PAIR_TALLY_WORDS, dtype=torch.int64, device="cuda")
+    ts = []
+    for k in range(reps + 1):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pe.pe_bw_transport(r.handle, bw, r.photons.data_ptr(), n_ph, -1, pairs.data_ptr(), cap, tally.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            ts.append(e0.elapsed_time(e1))
+    t = tally.cpu().numpy().view(np.uint64)
+    pe.pe_bw_tables_destroy(bw)
+    ms = float(np.median(ts))
+    steps = int(t[pe.PT["N_TESTS"]])
+    return {"value": n_ph / (ms * 1e-3), "unit": "photons/s", "ms_per_transport": ms, "photons": int(n_ph),
+            "followed": int(t[pe.PT["N_ENTERED"]]), "pairs": int(t[pe.PT["N_PAIRS"]]),
+            "photon_steps": steps, "photon_steps_note": "includes the steps behind both pulses, counted not computed",
+            "chi_above_table": int(t[pe.PT["N_K_ABOVE"]]),
+            "kernel": "k_bw_transport (FP32, reflected-wave field kind, one thread per photon, flattened steps)"}
 
 
 def pic_job(pe, tables, cfg, stream, flush, n=1_000_000, n_cells=1000, steps=2000):

@@ -48,7 +48,7 @@ typedef enum {
     PE_ERR_NOMEM = 3,        /* the library could not allocate its own device memory    */
     PE_ERR_BUFFER_FULL = 4,  /* photon buffer overflowed; counts stay exact             */
     PE_ERR_TABLE_RANGE = 5,  /* reserved: out-of-table values are counted, not fatal    */
-    PE_ERR_TIMEOUT = 6,      /* a bounded device wait ran out (counted in the tally)     */
+    PE_ERR_TIMEOUT = 6,      /* tally word 12 is set (no kernel of this build waits)     */
     PE_ERR_STATE = 7         /* call out of order (e.g. mixed precisions in one batch)  */
 } pe_status;
 
@@ -76,7 +76,9 @@ enum {
     PE_T_N_ETA_BELOW = 6,    /* NCS emissions sampled from the classical (eta->0) row      */
     PE_T_N_GAMMA_ABOVE = 7,  /* brems tests with gamma above the table (row clamped)       */
     PE_T_N_KILLED = 8, PE_T_KILLED_STEPS = 9, PE_T_N_CLAMP = 10, PE_T_N_HIST_OVER = 11,
-    PE_T_N_WAIT_TIMEOUT = 12, /* device waits that ran out (pe_tally then returns PE_ERR_TIMEOUT) */
+    PE_T_N_WAIT_TIMEOUT = 12, /* reserved for device waits that run out; pe_tally returns
+                                 PE_ERR_TIMEOUT when it is set.  No kernel of this library waits
+                                 on another thread, CTA or copy, so it stays 0              */
     PE_T_N_NONFINITE = 13,   /* particles removed because a momentum was NaN or infinite (also in N_KILLED) */
     PE_T_E_NCS_STORED = 16, PE_T_E_NCS_BELOW = 18, PE_T_E_BR_STORED = 20, PE_T_E_BR_BELOW = 22,
     PE_T_E_RECOIL_NCS = 24, PE_T_E_RECOIL_BR = 26
@@ -505,6 +507,17 @@ pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* cu
 enum { PE_FMA_F32 = 0, PE_FMA_F32X2 = 1, PE_FMA_F64 = 2 };
 pe_status pe_fma_peak(int kind, int blocks, int threads, int iters, void* out, void* cuda_stream,
                       int* chains_out);
+
+/* Debug builds.  A library compiled with PE_DEBUG checks every table row and
+ * column, guide entry and histogram bin a kernel indexes against its array; an
+ * index out of range is counted in a word of the table set and clamped into
+ * range, so the access stays in bounds and nothing traps (the substitute for a
+ * memory checker).  pe_debug_build returns 1 for such a library, 0 otherwise.
+ * pe_debug_count synchronises the device and returns the sum of the counts of
+ * the given table sets (either may be NULL; 0 in a release build).
+ * Errors: PE_ERR_ARG (both NULL, out NULL), PE_ERR_CUDA.                      */
+int pe_debug_build(void);
+pe_status pe_debug_count(const pe_tables* tables, const pe_bw_tables* bw, uint64_t* out);
 
 /* Number of kernel launches the library has issued (all runs, this process). */
 int64_t pe_launch_count(void);

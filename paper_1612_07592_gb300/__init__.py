@@ -134,6 +134,8 @@ def lib():
             L.pe_bw_tables_destroy.argtypes = [vp]
             L.pe_bw_transport.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, vp]
             L.pe_math_probe.argtypes = [C.c_int, vp, vp, C.c_int64, vp]
+            L.pe_debug_count.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
+            L.pe_debug_build.restype = C.c_int
             L.pe_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_int)]
             L.pe_a0_from_intensity.argtypes = [C.c_double, C.c_double, C.c_int]
             L.pe_a0_from_intensity.restype = C.c_double
@@ -143,7 +145,8 @@ def lib():
                          "pe_step", "pe_step_ex", "pe_tally", "pe_destroy", "pe_graph_create", "pe_graph_launch",
                          "pe_graph_destroy", "pe_pic_step_noalloc", "pe_electron_spectrum", "pe_photon_map",
                          "pe_pair_transport", "pe_resume_particles", "pe_bw_tables_host", "pe_math_probe",
-                         "pe_fma_peak", "pe_bw_tables_create", "pe_bw_tables_destroy", "pe_bw_transport"):
+                         "pe_fma_peak", "pe_bw_tables_create", "pe_bw_tables_destroy", "pe_bw_transport",
+                         "pe_debug_count"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -302,6 +305,18 @@ def pe_bw_transport(run: int, bw: int, photons_ptr: int, n_photons: int, step_en
                     capacity: int, tally_ptr: int) -> None:
     _check(lib().pe_bw_transport(run, bw, photons_ptr, int(n_photons), int(step_end), pairs_ptr, int(capacity),
                                  tally_ptr))
+
+
+def pe_debug_build() -> bool:
+    """True for a library compiled with PE_DEBUG (range checks of table indices; see pe.h)."""
+    return bool(lib().pe_debug_build())
+
+
+def pe_debug_count(tables: int | None = None, bw: int | None = None) -> int:
+    """Table indices found out of range so far (synchronises the device; 0 in a release build)."""
+    out = C.c_uint64(0)
+    _check(lib().pe_debug_count(tables, bw, C.byref(out)))
+    return out.value
 
 
 PE_MATH = dict(RCP=0, SIN=1, COS=2, SIN1=3, COS1=4, BREMS_P=5, BREMS_P1=6, CUDA_RCP=7, CUDA_SIN=8, CUDA_COS=9,

@@ -60,5 +60,13 @@ def build(force: bool = False, verbose: bool = False, lib: str | None = None, ou
     return LIB_
 
 
+DEBUG_LIB = os.path.join(HERE, "libpe_debug.so")
+
+
+def build_debug(force: bool = False) -> str:
+    """The debug variant (PE_DEBUG: range checks of every table index, counted and clamped)."""
+    return build(force=force, lib=DEBUG_LIB, out_dir=os.path.join(HERE, "_build_debug"), defines=("PE_DEBUG",))
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

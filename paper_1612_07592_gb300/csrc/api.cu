@@ -103,8 +103,8 @@ extern "C" pe_status pe_bw_tables_create(int n_chi, double chi_min, double chi_m
     }
     pe_bw_tables* t = new pe_bw_tables();
     cudaGetDevice(&t->device);
-    const size_t b64 = sizeof(double) * ((size_t)n_chi + cdf.size()), b32 = sizeof(float) * (size_t)n_chi;
-    cudaError_t e = cudaMalloc(&t->dmem, b64 + b32);
+    const size_t b64 = sizeof(double) * ((size_t)n_chi + cdf.size()), b32 = sizeof(float) * (size_t)(n_chi + (n_chi & 1));
+    cudaError_t e = cudaMalloc(&t->dmem, b64 + b32 + sizeof(unsigned long long));
     if (e != cudaSuccess) {
         delete t;
         return fail(PE_ERR_NOMEM, std::string("pe_bw_tables_create: cudaMalloc: ") + cudaGetErrorString(e));
@@ -114,7 +114,9 @@ extern "C" pe_status pe_bw_tables_create(int n_chi, double chi_min, double chi_m
     float* dL32 = reinterpret_cast<float*>(dcdf + cdf.size());
     e = cudaMemcpy(dL, L.data(), sizeof(double) * n_chi, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dcdf, cdf.data(), sizeof(double) * cdf.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dL32, L32.data(), b32, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dL32, L32.data(), sizeof(float) * n_chi, cudaMemcpyHostToDevice);
+    unsigned long long* dbg = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(dL32) + b32);
+    if (e == cudaSuccess) e = cudaMemset(dbg, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaFree(t->dmem);
         delete t;
@@ -122,12 +124,14 @@ extern "C" pe_status pe_bw_tables_create(int n_chi, double chi_min, double chi_m
     }
     BwDev& d = t->dev;
     d.L64 = dL; d.L32 = dL32; d.cdf64 = dcdf;
+    d.dbg = dbg;
     d.T_last = T[n_chi - 1];
     d.chi_min = chi_min;
     d.ln_chi_min = llo;
     d.inv_dln_chi = (double)(n_chi - 1) / (lhi - llo);
     d.fT_last = (float)d.T_last; d.fchi_min = (float)chi_min; d.fln_chi_min = (float)llo;
     d.finv_dln_chi = (float)d.inv_dln_chi;
+    d.f_last = (float)(n_chi - 1);
     d.n_chi = n_chi; d.n_x = n_x;
     *out = t;
     return PE_OK;
@@ -267,6 +271,15 @@ extern "C" pe_status pe_create_tables(const pe_table_params* p, pe_tables** out)
         D.gq = dg; D.bgq = dg + ng_n;
         D.M_y = My; D.M_s = Ms;
         D.fM_y = (float)My; D.fM_s = (float)Ms;
+    }
+    // the word after the three copies counts table indices found out of range (debug builds)
+    D.dbg = reinterpret_cast<unsigned long long*>(d32lo + n_all);     // byte 16 n_all: 8-byte aligned
+    e = cudaMemset(D.dbg, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(t->dmem);
+        cudaFree(t->dmemq);
+        delete t;
+        return cuda_fail(e, "pe_create_tables: debug word");
     }
     D.h64 = d64; D.cdf64 = d64 + n_h; D.sig64 = D.cdf64 + n_c; D.bcdf64 = D.sig64 + n_sg;
     D.h32 = d32; D.cdf32 = d32 + n_h; D.sig32 = D.cdf32 + n_c; D.bcdf32 = D.sig32 + n_sg;
@@ -849,6 +862,33 @@ extern "C" pe_status pe_bw_transport(pe_run* r, const pe_bw_tables* bw, const vo
     g_launches++;
     e = cudaGetLastError();
     return e == cudaSuccess ? PE_OK : cuda_fail(e, "pe_bw_transport");
+}
+
+extern "C" int pe_debug_build(void) {
+#ifdef PE_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" pe_status pe_debug_count(const pe_tables* t, const pe_bw_tables* bw, uint64_t* out) {
+    if (!out || (!t && !bw)) return fail(PE_ERR_ARG, "pe_debug_count: null argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "pe_debug_count: synchronize");
+    uint64_t sum = 0, v = 0;
+    if (t) {
+        e = cudaMemcpy(&v, t->dev.dbg, sizeof(v), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "pe_debug_count");
+        sum += v;
+    }
+    if (bw) {
+        e = cudaMemcpy(&v, bw->dev.dbg, sizeof(v), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "pe_debug_count");
+        sum += v;
+    }
+    *out = sum;
+    return PE_OK;
 }
 
 extern "C" pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* stream) {

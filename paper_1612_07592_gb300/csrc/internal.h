@@ -60,6 +60,7 @@ struct TablesDev {
     // and the CDF over s [n_Z * n_E * n_s], x = 1/k + s (1 - 2/k), rows k log spaced on [2, gamma_max]
     const double* bhsig64;
     const double* bhcdf64;
+    unsigned long long* dbg;                    // debug builds: count of table indices found out of range
     int M_y, M_s;                               // guide sizes (powers of two >= n_y, n_s)
     float fM_y, fM_s;
     int n_eta, n_y, n_E, n_s, n_Z;
@@ -173,8 +174,9 @@ struct BwDev {
     const double* L64;            // [n_chi]
     const float* L32;             // [n_chi], float copy for the FP32 transport
     const double* cdf64;          // [n_chi * n_x]
+    unsigned long long* dbg;      // debug builds: count of table indices found out of range
     double T_last, chi_min, ln_chi_min, inv_dln_chi;
-    float fT_last, fchi_min, fln_chi_min, finv_dln_chi;
+    float fT_last, fchi_min, fln_chi_min, finv_dln_chi, f_last;   // f_last = n_chi - 1
     int n_chi, n_x;
 };
 // kernels_bw.cu: Breit-Wheeler conversion of photon records in the run's prescribed fields

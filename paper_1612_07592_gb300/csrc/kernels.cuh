@@ -150,10 +150,12 @@ __device__ __forceinline__ void hist_bins(float e, float kx, float ky, float inv
 
 template <typename R>
 __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long long* tally, int mech, R e,
-                                         R kx, R ky, R inv_log_emax) {
+                                         R kx, R ky, R inv_log_emax, unsigned long long* dbg) {
     int eb, tb;
     bool over;
     hist_bins(e, kx, ky, inv_log_emax, eb, tb, over);
+    eb = dbg_idx(dbg, eb, PE_HIST_E_BINS);
+    tb = dbg_idx(dbg, tb, PE_HIST_T_BINS);
     if (over) atomicAdd(tally + PE_T_N_HIST_OVER, 1ull);
     atomicAdd(hist + mech * PE_HIST_E_BINS + eb, 1ull);
     atomicAdd(hist + 2 * PE_HIST_E_BINS + mech * PE_HIST_T_BINS + tb, 1ull);
@@ -204,7 +206,7 @@ __device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R
     if (ew >= photon_min) {
         atomicAdd(tally + PE_T_N_NCS_STORED, 1ull);
         fx_add_r(tally + PE_T_E_NCS_STORED, ew);
-        hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax);
+        hist_add<R>(hist, tally, 0, ew, k[0], k[1], c.inv_log_emax, t.dbg);
         out.stored = true;
         out.ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id};
     } else {
@@ -258,7 +260,7 @@ __device__ __noinline__ Emission<R> brems_emit(const TablesDev& t, const RunDevT
     if (ew >= photon_min) {
         atomicAdd(tally + PE_T_N_BR_STORED, 1ull);
         fx_add_r(tally + PE_T_E_BR_STORED, ew);
-        hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.c.inv_log_emax);
+        hist_add<R>(hist, tally, 1, ew, k[0], k[1], r.c.inv_log_emax, t.dbg);
         out.stored = true;
         out.ph = Photon{(float)xn, (float)yn, (float)ew, (float)k[0], (float)k[1], (float)k[2], n, id | 0x80000000u};
     } else {

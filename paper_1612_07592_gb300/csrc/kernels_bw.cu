@@ -10,12 +10,17 @@
 //
 // One thread per photon, with the step loop flattened: every pass of the loop takes one
 // step of each lane's current photon, and a lane whose photon is done (converted, at
-// step_end, or behind every pulse for good) takes its next photon, so the lanes of a warp
-// stay busy whatever the spread of path lengths.  The fields of a prescribed pulse vanish
-// identically once its phase t - x (and for the reflected wave t + x - 2 x_m) is past the
-// pulse's end, and both phases only grow along a photon's path: from then on chi = 0, T = 0
-// and the optical depth stays, so the photon stops there with its remaining steps counted
-// as taken (the tally equals stepping them).
+// step_end, or out of reach of every pulse for good) takes its next photon, so the lanes of
+// a warp stay busy whatever the spread of path lengths.  A pulse is out of reach of a photon
+// when it is behind it -- its fields vanish identically once its phase t - x (for the
+// reflected wave t + x - 2 x_m) is past the pulse's end, and both phases only grow along a
+// photon's path -- or when it can never give chi above the table: a plane wave gives
+// chi = (k -+ k_x) |E| / E_S exactly (- for the incident pulse, + for its mirror image) with
+// |E| <= r a0 sqrt(1 + k_env^2) (Cauchy-Schwarz on g' sin + g cos), so with a factor 2 of
+// margin the bound below chi_min means T = 0 at every step (photons co-moving with the
+// incident pulse, for instance).  From then on chi < chi_min, T = 0 and the
+// optical depth stays, so the photon stops with its remaining steps counted as taken (the
+// tally equals stepping them).
 //
 // FP64 runs step in double (parity with the oracle: the same pair list).  FP32 runs step in
 // float -- positions, fields, chi and T -- with the optical depth as a compensated float
@@ -39,16 +44,19 @@ __device__ __forceinline__ double bw_T(const BwDev& b, double chi, int& flag) {
     int i = (int)floor(tp);
     if (i > b.n_chi - 2) i = b.n_chi - 2;
     const double w = tp - (double)i;
+    i = dbg_idx(b.dbg, i, b.n_chi - 1);
     return exp((1.0 - w) * b.L64[i] + w * b.L64[i + 1] - 8.0 / (3.0 * chi));
 }
 __device__ __forceinline__ float bw_T(const BwDev& b, float chi, int& flag) {
     if (!(chi >= b.fchi_min)) { flag = -1; return 0.0f; }
-    float tp = (__logf(chi) - b.fln_chi_min) * b.finv_dln_chi;
-    if (tp >= (float)(b.n_chi - 1)) { flag = 1; return b.fT_last; }
+    const float tp = (__logf(chi) - b.fln_chi_min) * b.finv_dln_chi;
+    if (tp >= b.f_last) { flag = 1; return b.fT_last; }
     flag = 0;
-    tp = fmaxf(tp, 0.0f);
-    int i = min((int)tp, b.n_chi - 2);
-    const float w = tp - (float)i;
+    // row by the magic-number split (no int/float conversion: GB300 runs those on its FP64 pipe)
+    int i;
+    float w;
+    split_pos(fmaxf(tp, 0.0f), i, w);
+    i = dbg_idx(b.dbg, i, b.n_chi - 1);
     // T below ~1e-38 (chi below ~0.03) underflows to 0: a rate 1e-36 times the unit
     return __expf((1.0f - w) * b.L32[i] + w * b.L32[i + 1] - 8.0f / (3.0f * chi));
 }
@@ -63,6 +71,7 @@ __device__ __forceinline__ double bw_sample_x(const BwDev& b, double chi, double
     if (tp >= (double)(b.n_chi - 1)) { i = b.n_chi - 2; w = 1.0; }
     else if (!(tp >= 0.0)) { i = 0; w = 0.0; }
     else { i = min((int)floor(tp), b.n_chi - 2); w = tp - (double)i; }
+    i = dbg_idx(b.dbg, i, b.n_chi - 1);
     const double* ra = b.cdf64 + (size_t)i * b.n_x;
     int j;
     const double fr = invert_rows<double>(ra, ra + b.n_x, w, b.n_x, R, j);
@@ -106,12 +115,14 @@ template <> struct Depth<float> {
     __device__ bool crossed() const { return v + lo <= 0.0f; }
 };
 
-// position at step m: e + d ((m - n_e) dt), one rounding for the product and one for the FMA
-__device__ __forceinline__ double bw_pos(const StepC<double>& c, double d, double e, int64_t ne, int64_t m) {
-    return photon_pos(c, d, e, ne, m);
+// position at step m: e + d ((m - n_e) dt) with sf = m - n_e held as a floating-point counter
+// (advanced by exact + 1, so no integer-to-float conversion per step: GB300 runs conversions on
+// its narrow FP64 pipe); one rounding for the product and one for the FMA
+__device__ __forceinline__ double bw_pos(const StepC<double>& c, double d, double e, double sf) {
+    return __fma_rn(d, __dmul_rn(sf, c.dt), e);
 }
-__device__ __forceinline__ float bw_pos(const StepC<float>& c, float d, float e, int64_t ne, int64_t m) {
-    return fmaf(d, (float)(m - ne) * c.dt, e);
+__device__ __forceinline__ float bw_pos(const StepC<float>& c, float d, float e, float sf) {
+    return fmaf(d, sf * c.dt, e);
 }
 
 #ifndef PE_BW_MIN_CTAS
@@ -126,6 +137,10 @@ __global__ void __launch_bounds__(256, PE_BW_MIN_CTAS) k_bw_transport(BwDev bw, 
     const bool two_d = r.geometry == PE_GAUSS_2D;
     constexpr bool kLeave = G != FK_CONST;                 // a prescribed pulse: fields vanish behind it
     constexpr bool kRefl = G == FK_REFL_LP || G == FK_REFL_CP;
+    constexpr bool kPlane = G == FK_PLANE_LP || G == FK_PLANE_CP || kRefl;   // chi bounded as for a plane wave
+    // 2 E_max / E_S of the incident pulse: twice the bound on chi / (k - k_x)
+    const R reach = (R)2 * c.a0 * m_sqrt((R)1 + c.k_env * c.k_env) * c.inv_ES;
+    const R chi_min = sizeof(R) == 8 ? (R)bw.chi_min : (R)bw.fchi_min;
     const R L_end = (R)2 * c.phi_r + c.phi_f + (sizeof(R) == 8 ? (R)1e-6 : (R)1e-3);   // pulse end + margin
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -135,36 +150,54 @@ __global__ void __launch_bounds__(256, PE_BW_MIN_CTAS) k_bw_transport(BwDev bw, 
     Photon p{};
     R k = 0, kv[3] = {0, 0, 0}, gm = 0, kx = 0, ky = 0, xe = 0, ye = 0, kdt = 0;
     int64_t ne = 0, m = 0;
+    R sf = 0, mf = 0;                              // m - n_e and m as exact floating-point counters
+    bool inc_never = false, ref_never = true;     // a pulse can never raise chi above the table
     Depth<R> tau;
     tau.set(1.0);
     while (true) {
         if (!have) {
-            // this lane's next photon that can make a pair (k > 2 m c^2)
-            do {
+            // this lane's next photon to step: k > 2 m c^2, a step left before step_end, and a pulse
+            // that can raise its chi into the table; the others are only counted (no draw)
+            while (true) {
                 j += stride;
-            } while (j < n_ph && !((double)ph[j].e > 2.0));
-            if (j >= n_ph) break;
-            p = ph[j];
-            k = (R)p.e;
-            kx = (R)p.kx; ky = (R)p.ky; xe = (R)p.x; ye = (R)p.y;
-            kv[0] = k * kx; kv[1] = k * ky; kv[2] = k * (R)p.kz;
-            const R kk = m_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
-            gm = (kv[0] > (R)0) ? (kv[1] * kv[1] + kv[2] * kv[2]) / (kk + kv[0]) : kk - kv[0];
-            ne = (int64_t)p.step;
-            const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)ne, kPurBWTau + p.step),
-                                          r.seed_lo, r.seed_hi);
-            tau.set(-log(uni53(w64(w.x, w.y))));
-            kdt = c.bw_coef / k;
-            ++n_followed;
-            m = ne + 1;
-            have = m < step_end;
-            if (!have) continue;
+                if (j >= n_ph) break;
+                p = ph[j];
+                if (!(p.e > 2.0f)) continue;               // the same decision as (double) k > 2
+                ++n_followed;
+                ne = (int64_t)p.step;
+                m = ne + 1;
+                k = (R)p.e;
+                kx = (R)p.kx; ky = (R)p.ky; xe = (R)p.x; ye = (R)p.y;
+                kv[0] = k * kx; kv[1] = k * ky; kv[2] = k * (R)p.kz;
+                const R kk = m_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+                gm = (kv[0] > (R)0) ? (kv[1] * kv[1] + kv[2] * kv[2]) / (kk + kv[0]) : kk - kv[0];
+                if (kPlane) {
+                    // k - k_x is gm (formed without cancellation); k + k_x likewise for backward photons
+                    const R gp = (kv[0] < (R)0) ? (kv[1] * kv[1] + kv[2] * kv[2]) / (kk - kv[0]) : kk + kv[0];
+                    inc_never = gm * reach < chi_min;
+                    ref_never = !kRefl || gp * c.refl_r * reach < chi_min;
+                    if (inc_never && ref_never) {        // no pulse can convert it: every step counted, none taken
+                        n_tests += (unsigned long long)(step_end > m ? step_end - m : 0);
+                        continue;
+                    }
+                }
+                if (m >= step_end) continue;
+                const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)ne, kPurBWTau + p.step),
+                                              r.seed_lo, r.seed_hi);
+                tau.set(-log(uni53(w64(w.x, w.y))));
+                kdt = c.bw_coef / k;
+                sf = (R)1;
+                mf = (R)m;
+                have = true;
+                break;
+            }
+            if (!have) break;                          // no photon left for this lane
         }
         // step m of the lane's photon
-        const R px = bw_pos(c, kx, xe, ne, m);
-        const R py = bw_pos(c, ky, ye, ne, m);
+        const R px = bw_pos(c, kx, xe, sf);
+        const R py = bw_pos(c, ky, ye, sf);
         R E[3], B[3];
-        fields<R, G>(r, px, (R)0, py, (R)m, E, B);
+        fields<R, G>(r, px, (R)0, py, mf, E, B);
         const R chi = chi_photon<R>(kv, gm, E, B, c.inv_ES);
         int fl;
         const R T = bw_T(bw, chi, fl);
@@ -197,14 +230,17 @@ __global__ void __launch_bounds__(256, PE_BW_MIN_CTAS) k_bw_transport(BwDev bw, 
             if (m >= step_end) {
                 have = false;
             } else if (kLeave) {
-                // behind the pulse (and its image) for good: the remaining steps see no field
-                bool gone = phase(c, (R)(m - 1), px, (R)0) > L_end;
-                if (kRefl) gone = gone && phase_refl(c, (R)(m - 1), px, (R)0) > L_end;
+                // every pulse behind the photon for good, or never strong enough for it: the
+                // remaining steps see chi below the table
+                bool gone = inc_never || phase(c, mf, px, (R)0) > L_end;
+                if (kRefl) gone = gone && (ref_never || phase_refl(c, mf, px, (R)0) > L_end);
                 if (gone) {
                     n_tests += (unsigned long long)(step_end - m);
                     have = false;
                 }
             }
+            sf += (R)1;
+            mf += (R)1;
         }
         // conversions of this pass, one counter atomic per converging group of lanes
         const unsigned act = __activemask();

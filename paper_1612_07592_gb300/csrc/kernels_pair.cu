@@ -36,6 +36,7 @@ __device__ __forceinline__ double bh_sigma_of(const TablesDev& t, const double* 
     if (!(k > 2.0)) return 0.0;
     int fl;
     row_pos<double>(k, c.ln_k_min, c.inv_dln_k, c.g_last, t.n_E, i, w, fl);
+    i = dbg_idx(t.dbg, i, t.n_E - 1);
     above = (fl == 1);
     return (1.0 - w) * sig[i] + w * sig[i + 1];
 }

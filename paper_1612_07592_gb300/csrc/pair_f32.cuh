@@ -176,7 +176,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         n_above += (uint32_t)(Q.act[0] && tp.x >= tc.eta_last) + (uint32_t)(Q.act[1] && tp.y >= tc.eta_last);
         const float2 tpc = clamp2(tp, 0.0f, tc.eta_last - 0x1.0p-10f);
         const float2 tt = add2(sub2(tpc, P2(0.5f)), P2(0x1.8p23f));
-        const int ix = __float_as_int(tt.x) - 0x4B400000, iy = __float_as_int(tt.y) - 0x4B400000;
+        const int ix = dbg_idx(t.dbg, __float_as_int(tt.x) - 0x4B400000, t.n_eta - 1);
+        const int iy = dbg_idx(t.dbg, __float_as_int(tt.y) - 0x4B400000, t.n_eta - 1);
         const float2 w = sub2(tpc, sub2(tt, P2(0x1.8p23f)));
         const float2 h0 = make_float2(h_tab[ix], h_tab[iy]), h1 = make_float2(h_tab[ix + 1], h_tab[iy + 1]);
         float2 hv = fma2(w, sub2(h1, h0), h0);
@@ -238,7 +239,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     if (in[k] && comp(tg, k) >= tc.g_last) atomicAdd(tally + PE_T_N_GAMMA_ABOVE, 1ull);
                 const float2 tgc = clamp2(tg, 0.0f, tc.g_last - 0x1.0p-10f);
                 const float2 tt = add2(sub2(tgc, P2(0.5f)), P2(0x1.8p23f));
-                const int gx = __float_as_int(tt.x) - 0x4B400000, gy = __float_as_int(tt.y) - 0x4B400000;
+                const int gx = dbg_idx(t.dbg, __float_as_int(tt.x) - 0x4B400000, t.n_E - 1);
+                const int gy = dbg_idx(t.dbg, __float_as_int(tt.y) - 0x4B400000, t.n_E - 1);
                 const float2 w = sub2(tgc, sub2(tt, P2(0x1.8p23f)));
                 const float2 s0 = make_float2(sig_tab[gx], sig_tab[gy]);
                 const float2 s1 = make_float2(sig_tab[gx + 1], sig_tab[gy + 1]);
@@ -409,11 +411,15 @@ __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t
 // ---------------------------------------------------------------------------
 constexpr int kStreamTile = 256;                       // electrons per tile (128 threads x 2)
 constexpr int kStreamThreads = kStreamTile / 2;
+// Measured on the 3e7-electron, 4000-step one-step job (stages x CTAs per SM, TB/s at 56 B per
+// particle-step): 2 x 4 4.83, 3 x 3 4.77, 3 x 4 4.60, 2 x 5 4.52, 4 x 4 4.12, 3 x 5 4.14, 2 x 6 3.87:
+// 128 registers (4 CTAs) take the step without spills, and larger stages shrink the L1 that holds
+// the remaining local memory.
 #ifndef PE_STREAM_STAGES
 #define PE_STREAM_STAGES 2    // stages per CTA: tiles in flight = stages - 1
 #endif
 #ifndef PE_STREAM_MIN_CTAS
-#define PE_STREAM_MIN_CTAS PE_PAIR_MIN_CTAS
+#define PE_STREAM_MIN_CTAS 4  // resident CTAs of 128 threads per SM the registers are sized for
 #endif
 constexpr int kStreamStages = PE_STREAM_STAGES;
 // one stage: x pairs (float4 per thread), tau pairs (float4), ux, uy, uz (float2 each)

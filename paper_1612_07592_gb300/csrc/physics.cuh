@@ -54,6 +54,23 @@ template <typename R> __device__ __forceinline__ const TabC<R>& tabc(const Table
 template <> __device__ __forceinline__ const TabC<float>& tabc<float>(const TablesDev& t) { return t.cf; }
 template <> __device__ __forceinline__ const TabC<double>& tabc<double>(const TablesDev& t) { return t.cd; }
 
+// ---- range checks of debug builds --------------------------------------------------
+// With -DPE_DEBUG every table row or column, guide entry and histogram bin a kernel is
+// about to index is checked against its array: an index outside [0, n) is counted in the
+// table set's violation word (pe_debug_count) and clamped into range, so the access stays
+// in bounds and nothing traps.  A release build compiles the checks away.
+__device__ __forceinline__ int dbg_idx(unsigned long long* word, int i, int n) {
+#ifdef PE_DEBUG
+    if ((unsigned)i >= (unsigned)n) {
+        atomicAdd(word, 1ull);
+        return i < 0 ? 0 : n - 1;
+    }
+#else
+    (void)word; (void)n;
+#endif
+    return i;
+}
+
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------
 // Counter (particle id, run id, step, purpose), key (seed lo, seed hi).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -382,12 +399,14 @@ __device__ __forceinline__ R h_of_eta(const TablesDev& t, const R* h, R eta, int
         int i;
         float w;
         split_pos(tpc, i, w);
+        i = dbg_idx(t.dbg, i, t.n_eta - 1);
         const float v = fmaf(w, h[i + 1] - h[i], h[i]);
         return (eta >= c.eta_min) ? v : c.h_classical;
     } else {
         if (!(eta >= c.eta_min)) { flag = -1; return c.h_classical; }
         int i; R w;
         row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, flag);
+        i = dbg_idx(t.dbg, i, t.n_eta - 1);
         return ((R)1 - w) * h[i] + w * h[i + 1];
     }
 }
@@ -425,6 +444,7 @@ __device__ __forceinline__ R sample_ncs_delta(const TablesDev& t, const R* cdf, 
     } else {
         int i, fl;
         row_pos<R>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, i, w, fl);
+        i = dbg_idx(t.dbg, i, t.n_eta - 1);
         ra = cdf + (size_t)i * t.n_y;
         rb = ra + t.n_y;
     }
@@ -444,6 +464,7 @@ __device__ __forceinline__ R sigma_of(const TablesDev& t, const R* sig, R gamma,
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
     row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
+    i = dbg_idx(t.dbg, i, t.n_E - 1);
     above = (fl == 1);
     return ((R)1 - w) * sig[i] + w * sig[i + 1];
 }
@@ -454,6 +475,7 @@ __device__ __forceinline__ R sample_brems_y(const TablesDev& t, const R* bcdf_z,
     const TabC<R>& c = tabc<R>(t);
     int i, fl; R w;
     row_pos<R>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
+    i = dbg_idx(t.dbg, i, t.n_E - 1);
     const R* ra = bcdf_z + (size_t)i * t.n_s;
     const R* rb = ra + t.n_s;
     int j;

@@ -70,12 +70,13 @@ __device__ __forceinline__ float df_diff(DF a, DF b) { return (a.hi - b.hi) + (a
 // takes one or two probes instead of log2(n) (a wider search window loaded at once
 // measured slower: its registers crowd the step loop).
 __device__ __forceinline__ float invert_pair_df(const float4* q, const short4* g, float w, int n, int M, float fM,
-                                                DF R, int& j_out) {
+                                                DF R, int& j_out, unsigned long long* dbg) {
     // m with m / M <= R < (m + 1) / M (R.hi M is exact, M a power of two)
     float rm = R.hi * fM;
     int m = (int)floor_small(rm);
     if (R.lo < 0.0f && int_to_float_small(m) == rm) --m;
     m = m < M - 1 ? m : M - 1;
+    m = dbg_idx(dbg, m, M);
     const float4 e0 = __ldg(q), en = __ldg(q + n - 1);
     const short4 gg = __ldg(g + m);
     DF c0 = pair_value(e0, w);
@@ -113,9 +114,10 @@ __device__ __forceinline__ float sample_ncs_delta_f32(const TablesDev& t, float 
         int fl;
         row_pos<float>(eta, c.ln_eta_min, c.inv_dln_eta, c.eta_last, t.n_eta, pr, w, fl);
     }
+    pr = dbg_idx(t.dbg, pr, t.n_eta);
     int j;
     float fr = invert_pair_df(t.cdfq + (size_t)pr * t.n_y, t.gq + (size_t)pr * t.M_y, w, t.n_y, t.M_y, t.fM_y,
-                              uni53_pair(wlo, whi), j);
+                              uni53_pair(wlo, whi), j, t.dbg);
     float y;
     if (j < 0) y = c.y_min * fr * fr * fr;           // CDF ~ y^(1/3) below the grid
     else if (j >= t.n_y - 1) y = c.y_max;
@@ -131,10 +133,11 @@ __device__ __forceinline__ float sample_brems_y_f32(const TablesDev& t, int iz, 
     int i, fl;
     float w;
     row_pos<float>(gamma, c.ln_g_min, c.inv_dln_g, c.g_last, t.n_E, i, w, fl);
-    const size_t pr = (size_t)iz * (t.n_E - 1) + i;
+    i = dbg_idx(t.dbg, i, t.n_E - 1);
+    const size_t pr = (size_t)dbg_idx(t.dbg, iz, t.n_Z) * (t.n_E - 1) + i;
     int j;
     float fr = invert_pair_df(t.bcdfq + pr * t.n_s, t.bgq + pr * t.M_s, w, t.n_s, t.M_s, t.fM_s,
-                              uni53_pair(wlo, whi), j);
+                              uni53_pair(wlo, whi), j, t.dbg);
     float s;
     if (j < 0) s = 0.0f;
     else if (j >= t.n_s - 1) s = 1.0f;
