@@ -51,6 +51,11 @@ FP32_LANES_PER_SM = 128
 # capture of the headline launch (35.5 MB for 1e6 electrons: the state read once, the final state
 # partly still in L2 at the end, the cold emission tables); None once the kernel changes.
 NCU_TRAFFIC_BYTES_PER_ELECTRON = 35.54
+# DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
+# one launch on 8e6 electrons (391.3 MB: 28 B read, 20.9 B written -- the rest of the 28 B still
+# dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
+# (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md); None once the kernel changes.
+NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.91
 
 
 def peaks():
@@ -353,6 +358,9 @@ def main():
         v, ns, dt = cpu_baseline(cfg, 250_000 if not args.particles else max(1000, n // 4), S, threads)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"{ns} of {n} electrons (strided ids) x {S} steps, {dt:.1f} s"}
+        v1, ns1, dt1 = cpu_baseline(cfg, 10_000 if not args.particles else max(500, n // 100), S, 1)
+        res["cpu_baseline_1core"] = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                     "sample": f"{ns1} of {n} electrons (strided ids) x {S} steps, {dt1:.1f} s"}
     if merged is not None:
         res["merged_tally"] = merged
     if rank == 0:
@@ -393,7 +401,8 @@ def hbm_form(pe, tables, cfg, stream, peak_gbs, peak_kind):
     r.close()
     return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
             "frac_at_48B": gbs48 / peak_gbs,
-            "traffic": None, "peak_kind": peak_kind, "particles": n, "bytes_per_particle_step": BYTES_PER_PSTEP_1D,
+            "traffic": NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON * n if NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON else None,
+            "peak_kind": peak_kind, "particles": n, "bytes_per_particle_step": BYTES_PER_PSTEP_1D,
             "ms_per_launch": ms, "launches": K, "particle_steps_per_s": pst / K / (ms * 1e-3),
             "kernel": "k_step_pair (FP32, 1D plane wave), one step per launch"}
 

@@ -24,7 +24,7 @@
 //
 // FP64 runs step in double (parity with the oracle: the same pair list).  FP32 runs step in
 // float -- positions, fields, chi and T -- with the optical depth as a compensated float
-// pair; the once-per-photon draw of tau_0 and the once-per-conversion sampling of x run in
+// pair, tau_0 drawn in float-pair arithmetic; the once-per-conversion sampling of x runs in
 // double in both.
 #include "kernels.cuh"
 
@@ -107,6 +107,7 @@ template <> struct Depth<double> {
 template <> struct Depth<float> {
     float v, lo;
     __device__ void set(double t) { v = (float)t; lo = (float)(t - (double)v); }
+    __device__ void set(float t) { v = t; lo = 0.0f; }
     __device__ void sub(float d) {       // TwoSum: v + lo stays exact to ~2^-48
         const float s = v - d, bb = s - v;
         lo += (v - (s - bb)) + (-d - bb);
@@ -184,10 +185,17 @@ __global__ void __launch_bounds__(256, PE_BW_MIN_CTAS) k_bw_transport(BwDev bw, 
                 if (m >= step_end) continue;
                 const uint4 w = philox4x32_10(make_uint4(p.id_mech, r.run_id, (uint32_t)ne, kPurBWTau + p.step),
                                               r.seed_lo, r.seed_hi);
-                tau.set(-log(uni53(w64(w.x, w.y))));
                 kdt = c.bw_coef / k;
                 sf = (R)1;
-                mf = (R)m;
+                if constexpr (sizeof(R) == 8) {
+                    tau.set(-log(uni53(w64(w.x, w.y))));
+                    mf = (R)m;
+                } else {
+                    // -ln U from the same 53 bits in float-pair arithmetic, and the step as a float
+                    // without a conversion instruction (m < 8192): no FP64-pipe work per photon
+                    tau.set(tau_draw_f32(w.x, w.y));
+                    mf = int_to_float_small((int)m);
+                }
                 have = true;
                 break;
             }
