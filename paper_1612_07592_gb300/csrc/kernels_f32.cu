@@ -9,6 +9,15 @@ namespace pe {
 constexpr int kStreamMaxSteps = 4;
 
 static bool plane_kind(int fk) { return fk == FK_PLANE_LP || fk == FK_PLANE_CP; }
+// every run of the launch has the paper's setup: NCS on, direct brems, no absorbing box (the paired
+// kernels then take these flags as compile-time constants)
+static bool common_flags(const BatchDevT<float>& b) {
+    for (int k = 0; k < b.n_runs; ++k) {
+        const RunDevT<float>& r = b.runs[k];
+        if (!r.enable_ncs || !r.enable_brems || r.brems_method != PE_BREMS_DIRECT || r.box_enable) return false;
+    }
+    return true;
+}
 static bool use_stream(const BatchDevT<float>& b, int steps, int block) {
     return b.n_runs == 1 && plane_kind(b.runs[0].fk) && steps <= kStreamMaxSteps && block == kStreamTile;
 }
@@ -23,11 +32,12 @@ static const void* kernel_of(const BatchDevT<float>& b, int steps, int block, in
     smem = base_smem;
     if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
         threads = block / 2;
+        const bool common = common_flags(b);
         if (kSingle && use_stream(b, steps, block)) {
             smem = stream_smem_bytes(base_smem);
-            return (const void*)k_step_pair_stream<G>;
+            return common ? (const void*)k_step_pair_stream<G, true> : (const void*)k_step_pair_stream<G, false>;
         }
-        return (const void*)k_step_pair<kSingle, G>;
+        return common ? (const void*)k_step_pair<kSingle, G, true> : (const void*)k_step_pair<kSingle, G, false>;
     } else {
         threads = block;
         return (const void*)k_step_persistent<float, kSingle, G>;
@@ -41,10 +51,14 @@ static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps,
     const void* f = kernel_of<kSingle, G>(b, steps, block, base_smem, threads, smem);
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
-        if (f == (const void*)k_step_pair_stream<G>)
-            k_step_pair_stream<G><<<grid, threads, smem, s>>>(t, b, steps);
+        if (f == (const void*)k_step_pair_stream<G, true>)
+            k_step_pair_stream<G, true><<<grid, threads, smem, s>>>(t, b, steps);
+        else if (f == (const void*)k_step_pair_stream<G, false>)
+            k_step_pair_stream<G, false><<<grid, threads, smem, s>>>(t, b, steps);
+        else if (f == (const void*)k_step_pair<kSingle, G, true>)
+            k_step_pair<kSingle, G, true><<<grid, threads, smem, s>>>(t, b, steps);
         else
-            k_step_pair<kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
+            k_step_pair<kSingle, G, false><<<grid, threads, smem, s>>>(t, b, steps);
     } else {
         k_step_persistent<float, kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
     }
@@ -85,9 +99,9 @@ int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch) {
     if (plane_kind(fk)) {
         const bool stream = steps_per_launch <= kStreamMaxSteps && block == kStreamTile;
         int occ = 0;
-        cudaError_t e = stream ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair_stream<FK_PLANE_LP>,
+        cudaError_t e = stream ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair_stream<FK_PLANE_LP, true>,
                                                                              block / 2, stream_smem_bytes(smem))
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP>,
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP, true>,
                                                                              block / 2, smem);
         occ = e == cudaSuccess && occ > 0 ? occ : 1;
         return stream ? occ : 3 * occ;

@@ -106,8 +106,10 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
     Q.wait[k] = P.wait;
 }
 
-// one step of two electrons (plane wave, G = FK_PLANE_LP or FK_PLANE_CP)
-template <int G>
+// one step of two electrons (plane wave, G = FK_PLANE_LP or FK_PLANE_CP).  kCommon: the run
+// has NCS on, direct brems and no absorbing box (the paper's setup), known at compile time, so
+// the step carries no test of the run's flags; otherwise they are read from the run.
+template <int G, bool kCommon>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
                                           bool st_ncs[2], Photon pn[2], bool st_br[2], Photon pb[2],
@@ -162,7 +164,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     const float2 xn = Q.x;
     float gam[2] = {gamma.x, gamma.y};
 
-    if (r.enable_ncs) {
+    if (kCommon || r.enable_ncs) {
         // eta = (gamma - u_x) |E| / E_S for the plane wave
         float2 up = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, P2(1.0f)));
         float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, mul2(up, rcp2(add2(gamma, Q.u0))), sub2(gamma, Q.u0));
@@ -203,8 +205,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         }
     }
 
-    if (r.enable_brems) {
-        if (r.brems_method == PE_BREMS_NULL) {
+    if (kCommon || r.enable_brems) {
+        if (!kCommon && r.brems_method == PE_BREMS_NULL) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (!Q.act[k]) continue;
@@ -274,7 +276,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     two_sum2(Q.x, d, s, e);
     Q.x = s;
     Q.x_lo = add2(Q.x_lo, e);
-    if (r.box_enable) {
+    if (!kCommon && r.box_enable) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (!Q.act[k]) continue;
@@ -294,7 +296,7 @@ __device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pai
 }
 
 // K steps of the pair Q (electrons i0 and i1) with warp-aggregated photon appends
-template <int G>
+template <int G, bool kCommon>
 __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
                                           const float* sig_z, int64_t i0, int64_t i1, Pair& Q, int steps,
                                           unsigned long long* s_hist, unsigned long long* s_tally) {
@@ -306,9 +308,9 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
         bool st_ncs[2] = {false, false}, st_br[2] = {false, false};
         Photon pn[2], pb[2];
         if (Q.act[0] || Q.act[1]) {
-            step_pair<G>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally,
+            step_pair<G, kCommon>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally,
                          n_above);
-            if (r.box_enable) {
+            if (!kCommon && r.box_enable) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (Q.act[k] && isnan(comp(Q.x, k))) {
@@ -336,7 +338,7 @@ __device__ __forceinline__ void pair_clear(Pair& Q) {
 }
 
 // K steps of the two electrons i0 = base + tid and i1 = base + tid + blockDim
-template <int G>
+template <int G, bool kCommon>
 __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
                                                 const float* sig_z, int64_t i0, int64_t i1, int steps,
                                                 unsigned long long* s_hist, unsigned long long* s_tally) {
@@ -345,7 +347,7 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     if (i0 < r.n) load_one(r, i0, Q, 0, s_tally);
     if (i1 < r.n) load_one(r, i1, Q, 1, s_tally);
     const bool live0 = i0 < r.n, live1 = i1 < r.n;
-    pair_loop<G>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
+    pair_loop<G, kCommon>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
     if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
     if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
 }
@@ -354,7 +356,7 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 #define PE_PAIR_MIN_CTAS 5   // resident CTAs of 128 threads per SM the register budget is sized for (96 registers)
 #endif
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
-template <bool kSingle, int G>
+template <bool kSingle, int G, bool kCommon>
 __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<float> s_run;
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t
         const RunDevT<float>& r = kSingle ? b.runs[0] : s_run;
         const int64_t base = (tile - b.tile_start[run_idx]) * b.tile;
         const int64_t i0 = base + threadIdx.x, i1 = base + threadIdx.x + blockDim.x;
-        tile_steps_pair<G>(t, r, s_h, s_sig + (size_t)r.iz * t.n_E, i0, i1, steps, s_hist, s_tally);
+        tile_steps_pair<G, kCommon>(t, r, s_h, s_sig + (size_t)r.iz * t.n_E, i0, i1, steps, s_hist, s_tally);
     }
     if (kSingle) {
         if (n_tiles > 0) flush_shared<float>(s_hist, s_tally, b.runs[0]);
@@ -525,7 +527,7 @@ __device__ __forceinline__ void pair_store(const RunDevT<float>& r, int64_t j, c
     }
 }
 
-template <int G>
+template <int G, bool kCommon>
 __global__ void __launch_bounds__(kStreamThreads, PE_STREAM_MIN_CTAS) k_step_pair_stream(TablesDev t, BatchDevT<float> b,
                                                                                          int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(kStreamThreads, PE_STREAM_MIN_CTAS) k_step_pai
             if (2 * j < r.n) load_one(r, 2 * j, Q, 0, s_tally);   // the odd last electron
         }
         const bool live0 = 2 * j < r.n, live1 = full;
-        pair_loop<G>(t, r, s_h, sig_z, 2 * j, 2 * j + 1, Q, steps, s_hist, s_tally);
+        pair_loop<G, kCommon>(t, r, s_h, sig_z, 2 * j, 2 * j + 1, Q, steps, s_hist, s_tally);
         pair_store(r, j, Q, live0 && Q.act[0], live1 && Q.act[1]);
         stage = stage + 1 == kStreamStages ? 0 : stage + 1;
     }
