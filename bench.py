@@ -48,14 +48,14 @@ BYTES_PER_PSTEP_2D = 72
 BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
-# capture of the headline launch (35.5 MB for 1e6 electrons: the state read once, the final state
+# capture of the headline launch (32.9 MB for 1e6 electrons: the state read once, the final state
 # partly still in L2 at the end, the cold emission tables); None once the kernel changes.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 35.54
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 32.86
 # DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
-# one launch on 8e6 electrons (391.3 MB: 28 B read, 20.9 B written -- the rest of the 28 B still
+# one launch on 8e6 electrons (386.8 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
 # dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
 # (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md); None once the kernel changes.
-NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.91
+NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.36
 
 
 def peaks():

@@ -335,7 +335,9 @@ __device__ __forceinline__ void box_check(const RunDevT<R>& r, Particle<R>& P, u
     }
 }
 
-template <typename R, int G>
+// kCommon: the run has NCS on, direct brems and no absorbing box (the paper's setup), known at
+// compile time, so the step carries no test of the run's flags; otherwise they are read from the run.
+template <typename R, int G, bool kCommon = false>
 __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
                                          uint32_t id, uint32_t n, R nf,
                                          Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
@@ -366,7 +368,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
     };
     const R xn = P.x, yn = P.y;
 
-    if (r.enable_ncs) {
+    if (kCommon || r.enable_ncs) {
         R eta = eta_of<R, G>(P.u, gamma, E, B, c.inv_ES);
         int fl;
         R h = h_of_eta<R>(t, h_tab, eta, fl);
@@ -379,10 +381,10 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         }
     }
 
-    if (r.enable_brems) {
+    if (kCommon || r.enable_brems) {
         bool in_slab = (xn >= c.x0 && xn <= c.x1);
         if ((G == FK_GAUSS_LP || G == FK_GAUSS_CP) && fabs(yn) > c.yh) in_slab = false;
-        if (r.brems_method == PE_BREMS_NULL) {
+        if (!kCommon && r.brems_method == PE_BREMS_NULL) {
             if (P.wait == 0u) {
                 const R g_before = gamma;
                 take(brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, hist, tally), P, gamma, out.br,
@@ -400,7 +402,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
 
     advance(P.x, P.x_lo, over_gamma(dt * P.u[0]));
     if (G == FK_GAUSS_LP || G == FK_GAUSS_CP) advance(P.y, P.y_lo, over_gamma(dt * P.u[1]));
-    box_check<R>(r, P, n, tally);
+    if (!kCommon) box_check<R>(r, P, n, tally);
 }
 
 __device__ __forceinline__ void load_tau(const RunDevT<double>& r, int64_t i, Particle<double>& P) {
@@ -523,7 +525,7 @@ __device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_t
 
 // K steps of one particle with its state in registers (all lanes of the warp take
 // part in the photon appends)
-template <typename R, int G>
+template <typename R, int G, bool kCommon>
 __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>& r, const R* s_h, const R* sig_z,
                                            int64_t i, bool active, Particle<R>& P, int steps,
                                            unsigned long long* s_hist, unsigned long long* s_tally) {
@@ -533,8 +535,9 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
         StepOut<R> out;
         out.ncs = out.br = false;
         if (active) {
-            step_one<R, G>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist, s_tally);
-            if (r.box_enable && isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
+            step_one<R, G, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist,
+                                    s_tally);
+            if (!kCommon && r.box_enable && isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
         }
         if (__any_sync(0xffffffffu, out.ncs || out.br)) {
             warp_append(r, out.ncs, out.pn);
@@ -551,7 +554,7 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 #ifndef PE_MIN_CTAS
 #define PE_MIN_CTAS 4   // resident CTAs of 256 threads per SM the register budget is sized for
 #endif
-template <typename R, bool kSingle, int G>
+template <typename R, bool kSingle, int G, bool kCommon = false>
 __global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<R> s_run;
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev 
             active = live_or_kill<R>(r, i, P, (uint32_t)r.step0, s_tally);
         }
         const R* sig_z = s_sig + (size_t)r.iz * t.n_E;
-        tile_steps<R, G>(t, r, s_h, sig_z, i, active, P, steps, s_hist, s_tally);
+        tile_steps<R, G, kCommon>(t, r, s_h, sig_z, i, active, P, steps, s_hist, s_tally);
         cur = kSingle ? 0 : cur;
     }
     if (kSingle) {

@@ -40,7 +40,8 @@ static const void* kernel_of(const BatchDevT<float>& b, int steps, int block, in
         return common ? (const void*)k_step_pair<kSingle, G, true> : (const void*)k_step_pair<kSingle, G, false>;
     } else {
         threads = block;
-        return (const void*)k_step_persistent<float, kSingle, G>;
+        return common_flags(b) ? (const void*)k_step_persistent<float, kSingle, G, true>
+                               : (const void*)k_step_persistent<float, kSingle, G, false>;
     }
 }
 
@@ -60,7 +61,10 @@ static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps,
         else
             k_step_pair<kSingle, G, false><<<grid, threads, smem, s>>>(t, b, steps);
     } else {
-        k_step_persistent<float, kSingle, G><<<grid, threads, smem, s>>>(t, b, steps);
+        if (f == (const void*)k_step_persistent<float, kSingle, G, true>)
+            k_step_persistent<float, kSingle, G, true><<<grid, threads, smem, s>>>(t, b, steps);
+        else
+            k_step_persistent<float, kSingle, G, false><<<grid, threads, smem, s>>>(t, b, steps);
     }
 }
 

@@ -144,7 +144,8 @@ __device__ void pic_fields_block(const RunDevT<R>& r) {
     }
 }
 
-template <typename R>
+// kCommon: NCS on and direct brems (a PIC run has no absorbing box), known at compile time
+template <typename R, bool kCommon>
 __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R> r) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
         }
         if (active) {
             const R x_old = P.x + P.x_lo;
-            step_one<R, FK_PIC>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, step, nf, P, out, s_hist, s_tally);
+            step_one<R, FK_PIC, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, step, nf, P, out, s_hist, s_tally);
             const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
             const R x_new = P.x + P.x_lo;
             pic_deposit<R>(r.c.dt, r.n_cells, x_old, x_new, P.u[1] / gamma, P.u[2] / gamma, sj);
@@ -255,12 +256,15 @@ static int pic_smem_bytes(const TablesDev& t, int n_cells, int precision) {
 template <typename R>
 static void pic_step(const TablesDev& t, const RunDevT<R>& r, int sms, cudaStream_t s) {
     const int smem = pic_smem_bytes(t, r.n_cells, sizeof(R) == 4 ? PE_F32 : PE_F64);
-    cudaFuncSetAttribute(k_pic_particles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const bool common = r.enable_ncs && r.enable_brems && r.brems_method == PE_BREMS_DIRECT;
+    const void* f = common ? (const void*)k_pic_particles<R, true> : (const void*)k_pic_particles<R, false>;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     // four resident CTAs of 256 threads per SM (64 registers): measured 90 us per step on 1e6
     // electrons against 112 us at two (each CTA adds one flush of its current sums)
     const int64_t blocks = (r.n + 255) / 256;
     const int grid = (int)(blocks < 4 * (int64_t)sms ? (blocks > 0 ? blocks : 1) : 4 * (int64_t)sms);
-    k_pic_particles<R><<<grid, 256, smem, s>>>(t, r);
+    if (common) k_pic_particles<R, true><<<grid, 256, smem, s>>>(t, r);
+    else k_pic_particles<R, false><<<grid, 256, smem, s>>>(t, r);
 }
 
 void launch_pic_step(const TablesDev& t, const RunDev& r, int precision, int sms, cudaStream_t s) {
