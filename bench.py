@@ -48,9 +48,10 @@ BYTES_PER_PSTEP_2D = 72
 BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
-# capture of the headline launch (32.9 MB for 1e6 electrons: the state read once, the final state
-# partly still in L2 at the end, the cold emission tables); None once the kernel changes.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 32.86
+# capture of the headline launch (45.3 MB for 1e6 electrons: the state read once, the final state
+# partly still in L2 at the end, the cold emission tables, register spill lines evicted from L2;
+# profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md); None once the kernel changes.
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 45.34
 # DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
 # one launch on 8e6 electrons (386.8 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
 # dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
@@ -461,7 +462,7 @@ def batch64(pe, stream, flush):
             runs.append(pe.Run(tables, pe.run_params(precision=pe.PE_F32, **rk), int(n),
                                capacity=int(min(2 * n, 1 << 23)), stream=stream))
     stream.synchronize()
-    cfg, trials = autotune.tune(tables, runs, 500, space=dict(block=(128, 256), ctas_per_sm=(5, 10, 15),
+    cfg, trials = autotune.tune(tables, runs, 500, space=dict(block=(128, 256), ctas_per_sm=(7, 14, 21),
                                                                  steps_per_launch=(250, 500)), use_cache=False)
     snaps = [r.snapshot() for r in runs]
     times = []

@@ -201,7 +201,6 @@ void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, i
 void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, int steps, int grid, int block,
                                 cudaStream_t s);
 int persistent_smem_bytes(const TablesDev& t, int precision);
-int persistent_occupancy_f32(int block, int smem);
 int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch);
 const void* persistent_kernel_f32(const BatchDevT<float>& b, int steps, int smem, int block, int* threads,
                                   int* smem_out);

@@ -551,11 +551,22 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 // straight from the kernel parameters (constant-bank operands); otherwise the
 // current run's descriptor is copied to shared memory once per tile, so no step
 // reads an indexed kernel parameter.
+// Resident CTAs of 256 threads per SM the register budget is sized for.  FP32, measured (particle-steps/s):
+// the 2D focus 9.64e10 at 4 CTAs (64 registers), 9.57e10 at 5, 9.37e10 at 6, 9.40e10 at 8; the reflected
+// wave 4.17e10 at 4, 4.30e10 at 5, 4.09e10 at 6, 4.44e10 at 8 (32 registers).
 #ifndef PE_MIN_CTAS
-#define PE_MIN_CTAS 4   // resident CTAs of 256 threads per SM the register budget is sized for
+#define PE_MIN_CTAS 4
 #endif
+#ifndef PE_MIN_CTAS_REFL
+#define PE_MIN_CTAS_REFL 8
+#endif
+template <typename R, int G>
+constexpr int persistent_min_ctas() {
+    return (sizeof(R) == 4 && (G == FK_REFL_LP || G == FK_REFL_CP)) ? PE_MIN_CTAS_REFL : PE_MIN_CTAS;
+}
 template <typename R, bool kSingle, int G, bool kCommon = false>
-__global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
+__global__ void __launch_bounds__(256, persistent_min_ctas<R, G>()) k_step_persistent(TablesDev t, BatchDevT<R> b,
+                                                                                     int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<R> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);

@@ -110,13 +110,15 @@ int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch) {
         occ = e == cudaSuccess && occ > 0 ? occ : 1;
         return stream ? occ : 3 * occ;
     }
-    return 2 * persistent_occupancy_f32(block, smem);
-}
-
-int persistent_occupancy_f32(int block, int smem) {
+    // twice the resident CTAs of this field kind's one-electron kernel
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false, FK_PLANE_LP>, block, smem);
-    return e == cudaSuccess ? occ : 1;
+    with_field_kind(fk, [&](auto g) {
+        constexpr int G = decltype(g)::value;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_persistent<float, false, G, true>, block, smem) !=
+            cudaSuccess)
+            occ = 0;
+    });
+    return 2 * (occ > 0 ? occ : 1);
 }
 
 }  // namespace pe

@@ -352,8 +352,12 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     if (live1 && Q.act[1]) store_particle<float>(r, i1, unpack(Q, 1));
 }
 
+// Resident CTAs of 128 threads per SM the register budget is sized for.  Measured on the headline job
+// with the run's flags as compile-time constants (particle-steps/s): 4 CTAs (128 registers) 1.59e11,
+// 5 (96) 1.74e11, 6 (80) 1.78e11, 7 (72) 1.79e11, 8 (64) 1.77e11; the grid of three resident waves
+// (21 CTAs per SM) stays the best at 7 (7: 1.63e11, 14: 1.77e11, 21: 1.79e11, 28 and 35: 1.79e11).
 #ifndef PE_PAIR_MIN_CTAS
-#define PE_PAIR_MIN_CTAS 5   // resident CTAs of 128 threads per SM the register budget is sized for (96 registers)
+#define PE_PAIR_MIN_CTAS 7
 #endif
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
 template <bool kSingle, int G, bool kCommon>

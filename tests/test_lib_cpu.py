@@ -24,12 +24,12 @@ def libpath():
 
 def _declared():
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:[a-z_]+\s+\*?\s*|const char\*\s+)(pe_[a-z0-9_]+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:[a-z_0-9]+\s+\*?\s*|const char\*\s+)(pe_[a-z0-9_]+)\s*\(", src, re.M)))
 
 
 def test_header_symbols_exported(libpath):
     names = _declared()
-    assert "pe_step" in names and "pe_init_particles" in names and len(names) >= 10
+    assert "pe_step" in names and "pe_init_particles" in names and "pe_launch_count" in names and len(names) >= 27
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r"\bT (pe_[a-z0-9_]+)", out))
     missing = [n for n in names if n not in exported]
