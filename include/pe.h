@@ -478,7 +478,8 @@ pe_status pe_pic_step_noalloc(const pe_tables* tables, const pe_run_params* para
 /* Diagnostics (the paper has no counterpart): the library's own single-precision
  * device forms, evaluated on given inputs so that tests can bound their error.
  *   fn = PE_MATH_RCP      1/d for d >= 1 as the FP32 step forms it (the hardware
- *                         reciprocal estimate refined by one Newton-Raphson step)
+ *                         reciprocal estimate of -d refined by one Newton-Raphson
+ *                         step; the probe returns minus that result, an exact negation)
  *        PE_MATH_SIN/_COS the carrier-phase sine and cosine of the paired FP32 step
  *                         (Cody-Waite reduction by 2 pi with a two-part constant,
  *                         then the hardware sine and cosine); _SIN1/_COS1 the same

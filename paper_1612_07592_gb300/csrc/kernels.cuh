@@ -60,23 +60,22 @@ __device__ __forceinline__ double photon_pos(const StepC<double>& c, double d, d
     return __fma_rn(d, __dmul_rn((double)(m - ne), c.dt), e);
 }
 
-// warp-aggregated append of at most one photon per lane; all 32 lanes call it
+// Appends a photon from inside an emission branch: the lanes that are in the branch together
+// (__activemask) take consecutive slots with one atomic of their leader, so no photon is held
+// across the rest of the step (and the step loop has no per-step vote for appends).
 template <typename R>
-__device__ __forceinline__ void warp_append(const RunDevT<R>& r, bool on, const Photon& p) {
-    unsigned mask = __ballot_sync(0xffffffffu, on);
-    if (mask == 0) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
+__device__ __forceinline__ void append_now(const RunDevT<R>& r, const Photon& p) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(r.tally + PE_T_N_PHOTONS, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (on) {
-        unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-        if (slot < (unsigned long long)r.capacity) {
-            float4* dst = reinterpret_cast<float4*>(r.photons + slot * 32);
-            dst[0] = make_float4(p.x, p.y, p.e, p.kx);
-            dst[1] = make_float4(p.ky, p.kz, __uint_as_float(p.step), __uint_as_float(p.id_mech));
-        }
+    base = __shfl_sync(mask, base, leader);
+    const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+    if (slot < (unsigned long long)r.capacity) {
+        float4* dst = reinterpret_cast<float4*>(r.photons + slot * 32);
+        dst[0] = make_float4(p.x, p.y, p.e, p.kx);
+        dst[1] = make_float4(p.ky, p.kz, __uint_as_float(p.step), __uint_as_float(p.id_mech));
     }
 }
 
@@ -162,18 +161,15 @@ __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long
 }
 
 
-template <typename R>
-struct StepOut {
-    bool ncs, br;      // a stored photon of this mechanism
-    Photon pn, pb;
-};
-
 // The emission branches are real calls (__noinline__): compiled once per
 // precision, so every kernel that steps a particle (single run or batch, any
 // launch shape) performs bit-identical emission arithmetic, and the rarely taken
 // code stays out of the step loop's instruction stream.  They take the particle
 // by value and return it (no address of the loop-carried state escapes, so it
-// stays in registers).
+// stays in registers).  The paired FP32 kernels inline the NCS branch instead
+// (ncs_emit_body): with 72 registers a thread, the call's register convention cost
+// spills on the common path (measured 7 % of the headline job); both paired
+// kernels inline the same body, so they still agree bit for bit.
 template <typename R>
 struct Emission {
     Particle<R> P;     // particle after the branch
@@ -185,9 +181,9 @@ struct Emission {
 // NCS emission at a crossing of the optical depth (Sec. 2.2): photon energy by
 // inverse CDF, recoil along u, tallies, new optical depth.
 template <typename R>
-__device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
-                                             Particle<R> P, R gamma, R eta, R xn, R yn, unsigned long long* hist,
-                                             unsigned long long* tally) {
+__device__ __forceinline__ Emission<R> ncs_emit_body(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                                     Particle<R> P, R gamma, R eta, R xn, R yn,
+                                                     unsigned long long* hist, unsigned long long* tally) {
     Emission<R> out;
     out.stored = false;
     const StepC<R>& c = r.c;
@@ -217,6 +213,12 @@ __device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R
     out.P = P;
     out.gamma = gn;
     return out;
+}
+template <typename R>
+__device__ __noinline__ Emission<R> ncs_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                             Particle<R> P, R gamma, R eta, R xn, R yn, unsigned long long* hist,
+                                             unsigned long long* tally) {
+    return ncs_emit_body<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally);
 }
 
 // 1 - e^{-x} in FP32 (the probability of Eq. 4): below 2^-5 by the Taylor series
@@ -335,14 +337,18 @@ __device__ __forceinline__ void box_check(const RunDevT<R>& r, Particle<R>& P, u
     }
 }
 
+// FP32 one-electron kernels: inline the NCS emission branch (1) or call it (0)
+#ifndef PE_ONE_INLINE_NCS
+#define PE_ONE_INLINE_NCS 0
+#endif
 // kCommon: the run has NCS on, direct brems and no absorbing box (the paper's setup), known at
 // compile time, so the step carries no test of the run's flags; otherwise they are read from the run.
 template <typename R, int G, bool kCommon = false>
 __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r, const R* h_tab, const R* sig_tab,
-                                         uint32_t id, uint32_t n, R nf,
-                                         Particle<R>& P, StepOut<R>& out, unsigned long long* hist,
-                                         unsigned long long* tally) {
-    out.ncs = out.br = false;
+                                         uint32_t id, uint32_t n, R nf, Particle<R>& P,
+                                         unsigned long long* hist, unsigned long long* tally) {
+    bool st;           // an emission branch stored a photon, appended at once (append_now)
+    Photon ph;
     const StepC<R>& c = r.c;
     const R photon_min = tabc<R>(t).photon_min;
     const R dt = c.dt;
@@ -376,7 +382,13 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
         tau_sub(P, c.ncs_coef * over_gamma(eta) * h);
         if (tau_crossed(P)) {
-            take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, out.ncs, out.pn);
+#if PE_ONE_INLINE_NCS
+            if constexpr (sizeof(R) == 4)
+                take(ncs_emit_body<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
+            else
+#endif
+                take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
+            if (st) append_now(r, ph);
             refresh();
         }
     }
@@ -387,15 +399,17 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if (!kCommon && r.brems_method == PE_BREMS_NULL) {
             if (P.wait == 0u) {
                 const R g_before = gamma;
-                take(brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, hist, tally), P, gamma, out.br,
-                     out.pb);
+                take(brems_candidate<R>(t, r, sig_tab, id, n, P, gamma, in_slab, xn, yn, hist, tally), P, gamma, st, ph);
+                if (st) append_now(r, ph);
                 if (gamma != g_before) refresh();
             } else if (P.wait != PE_WAIT_NEVER) {
                 --P.wait;
             }
         } else if (in_slab && gamma > (R)1 + photon_min) {
             const R g_before = gamma;
-            brems_collide<R>(t, r, sig_tab, id, n, P, gamma, xn, yn, out.br, out.pb, hist, tally);
+            st = false;
+            brems_collide<R>(t, r, sig_tab, id, n, P, gamma, xn, yn, st, ph, hist, tally);
+            if (st) append_now(r, ph);
             if (gamma != g_before) refresh();
         }
     }
@@ -523,8 +537,7 @@ __device__ void flush_shared(unsigned long long* s_hist, unsigned long long* s_t
     __syncthreads();
 }
 
-// K steps of one particle with its state in registers (all lanes of the warp take
-// part in the photon appends)
+// K steps of one particle with its state in registers
 template <typename R, int G, bool kCommon>
 __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>& r, const R* s_h, const R* sig_z,
                                            int64_t i, bool active, Particle<R>& P, int steps,
@@ -532,16 +545,9 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
     const uint32_t n0 = (uint32_t)r.step0;
     R nf = (R)n0;                      // step index as a float, advanced by exact +1
     for (int s = 0; s < steps; ++s, nf += (R)1) {
-        StepOut<R> out;
-        out.ncs = out.br = false;
         if (active) {
-            step_one<R, G, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, n0 + (uint32_t)s, nf, P, out, s_hist,
-                                    s_tally);
+            step_one<R, G, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, n0 + (uint32_t)s, nf, P, s_hist, s_tally);
             if (!kCommon && r.box_enable && isnan(P.x)) { active = false; store_particle<R>(r, i, P); }
-        }
-        if (__any_sync(0xffffffffu, out.ncs || out.br)) {
-            warp_append(r, out.ncs, out.pn);
-            warp_append(r, out.br, out.pb);
         }
     }
     if (active) store_particle<R>(r, i, P);

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(256) k_math_probe(int fn, const float* in, flo
     const float v = in[i];
     float r = 0.0f;
     switch (fn) {
-        case PE_MATH_RCP: r = rcp2(P2(v)).x; break;
+        case PE_MATH_RCP: r = -nrcp2(P2(v)).x; break;
         case PE_MATH_SIN: { float2 s, c; sincos2(P2(v), s, c); r = s.x; } break;
         case PE_MATH_COS: { float2 s, c; sincos2(P2(v), s, c); r = c.x; } break;
         case PE_MATH_SIN1: { float s, c; m_sincos(v, &s, &c); r = s; } break;

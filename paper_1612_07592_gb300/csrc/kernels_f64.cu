@@ -19,8 +19,6 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < r.n;
     Particle<double> P;
-    StepOut<double> out;
-    out.ncs = out.br = false;
     if (active) {
         load_particle<double>(r, i, P);
         active = live_or_kill<double>(r, i, P, (uint32_t)r.step0, r.tally);
@@ -30,19 +28,15 @@ __global__ void __launch_bounds__(256) k_step_plain(TablesDev t, RunDevT<double>
         const uint32_t n = (uint32_t)r.step0;
         const uint32_t id = r.id0 + (uint32_t)i;
         switch (r.fk) {
-            case FK_PLANE_LP: step_one<double, FK_PLANE_LP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_PLANE_CP: step_one<double, FK_PLANE_CP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_GAUSS_LP: step_one<double, FK_GAUSS_LP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_GAUSS_CP: step_one<double, FK_GAUSS_CP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_REFL_LP: step_one<double, FK_REFL_LP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            case FK_REFL_CP: step_one<double, FK_REFL_CP>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
-            default: step_one<double, FK_CONST>(t, r, t.h64, sig, id, n, (double)n, P, out, r.hist, r.tally); break;
+            case FK_PLANE_LP: step_one<double, FK_PLANE_LP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            case FK_PLANE_CP: step_one<double, FK_PLANE_CP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            case FK_GAUSS_LP: step_one<double, FK_GAUSS_LP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            case FK_GAUSS_CP: step_one<double, FK_GAUSS_CP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            case FK_REFL_LP: step_one<double, FK_REFL_LP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            case FK_REFL_CP: step_one<double, FK_REFL_CP>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
+            default: step_one<double, FK_CONST>(t, r, t.h64, sig, id, n, (double)n, P, r.hist, r.tally); break;
         }
         store_particle<double>(r, i, P);
-    }
-    if (__any_sync(0xffffffffu, out.ncs || out.br)) {
-        warp_append(r, out.ncs, out.pn);
-        warp_append(r, out.br, out.pb);
     }
 }
 

@@ -177,15 +177,13 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
         const int64_t i = base + threadIdx.x;
         bool active = i < r.n;
         Particle<R> P;
-        StepOut<R> out;
-        out.ncs = out.br = false;
         if (active) {
             load_particle<R>(r, i, P);
             active = live_or_kill<R>(r, i, P, step, s_tally);
         }
         if (active) {
             const R x_old = P.x + P.x_lo;
-            step_one<R, FK_PIC, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, step, nf, P, out, s_hist, s_tally);
+            step_one<R, FK_PIC, kCommon>(t, r, s_h, sig_z, r.id0 + (uint32_t)i, step, nf, P, s_hist, s_tally);
             const R gamma = m_sqrt((R)1 + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
             const R x_new = P.x + P.x_lo;
             pic_deposit<R>(r.c.dt, r.n_cells, x_old, x_new, P.u[1] / gamma, P.u[2] / gamma, sj);
@@ -195,10 +193,6 @@ __global__ void __launch_bounds__(256, 4) k_pic_particles(TablesDev t, RunDevT<R
                 atomicAdd(s_tally + PE_T_KILLED_STEPS, (unsigned long long)step + 1ull);
             }
             store_particle<R>(r, i, P);
-        }
-        if (__any_sync(0xffffffffu, out.ncs || out.br)) {
-            warp_append(r, out.ncs, out.pn);
-            warp_append(r, out.br, out.pb);
         }
     }
     __syncthreads();

@@ -28,14 +28,17 @@ __device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f
 // per-electron operations (no paired form)
 __device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
-// 1/d for d >= 1 (both uses below): the hardware reciprocal estimate refined by one Newton-Raphson
-// step, r' = r + r (1 - d r), which squares its relative error (about 1 ulp after it); it replaces
-// an IEEE division, whose special-case check and branch cost more than the estimate and two FMAs
-__device__ __forceinline__ float2 rcp2(float2 d) {
+// -1/d for d >= 1 (both uses below): the hardware reciprocal estimate of -d refined by one
+// Newton-Raphson step, r' = r + r (1 + d r), which squares its relative error (about 1 ulp after
+// it); it replaces an IEEE division, whose special-case check and branch cost more than the
+// estimate and two FMAs.  The sign is taken by the estimate's operand (free) rather than by a
+// paired multiply by -1 (a whole instruction: paired arithmetic has no negated operands), and the
+// callers absorb it into a constant factor.
+__device__ __forceinline__ float2 nrcp2(float2 d) {
     float2 r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
-    const float2 e = fma2(neg2(d), r, P2(1.0f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(-d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(-d.y));
+    const float2 e = fma2(d, r, P2(1.0f));
     return fma2(r, e, r);
 }
 __device__ __forceinline__ float2 log2v(float2 a) { return make_float2(__log2f(a.x), __log2f(a.y)); }
@@ -112,7 +115,6 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
 template <int G, bool kCommon>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
-                                          bool st_ncs[2], Photon pn[2], bool st_br[2], Photon pb[2],
                                           unsigned long long* hist, unsigned long long* tally, uint32_t& n_above) {
     const StepC<float>& c = r.c;
     const TabC<float>& tc = t.cf;
@@ -146,16 +148,27 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float2 um2 = (G == FK_PLANE_CP) ? sub2(Q.u2, mul2(h, ez)) : Q.u2;
     float2 q = fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f))));
     float2 ig = rsqrt2(q);
-    float2 t1 = (G == FK_PLANE_CP) ? mul2(mul2(h, ez), ig) : P2(0.0f);   // -h B_y / gamma
     float2 t2 = mul2(mhey, ig);                                        // -h B_z / gamma
-    float2 f = mul2(P2(2.0f), rcp2(fma2(t2, t2, fma2(t1, t1, P2(1.0f)))));
-    float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
-    float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
-    float2 p1 = sub2(um1, mul2(um0, t2));
-    float2 p2 = add2(um2, mul2(um0, t1));
-    Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
-    Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
-    Q.u2 = (G == FK_PLANE_CP) ? sub2(add2(um2, mul2(p0, s1)), mul2(h, ez)) : um2;
+    if constexpr (G == FK_PLANE_CP) {
+        float2 t1 = mul2(mul2(h, ez), ig);                             // -h B_y / gamma
+        float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, fma2(t1, t1, P2(1.0f)))));
+        float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
+        float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
+        float2 p1 = sub2(um1, mul2(um0, t2));
+        float2 p2 = add2(um2, mul2(um0, t1));
+        Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
+        Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
+        Q.u2 = sub2(add2(um2, mul2(p0, s1)), mul2(h, ez));
+    } else {
+        // LP: B = (0, 0, E_y), so t and s lie along z and the rotation leaves u_z alone; the
+        // terms with t_y (exact zeros) are left out, which changes no rounding
+        float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, P2(1.0f))));
+        float2 s2 = mul2(f, t2);
+        float2 p0 = add2(um0, mul2(um1, t2));
+        float2 p1 = sub2(um1, mul2(um0, t2));
+        Q.u0 = add2(um0, mul2(p1, s2));
+        Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
+    }
     // gamma and 1/gamma from one reciprocal square root (1/gamma serves the rate and the
     // position update; emitting lanes refresh it from their new gamma)
     const float2 g2 = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, fma2(Q.u0, Q.u0, P2(1.0f))));
@@ -165,11 +178,12 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float gam[2] = {gamma.x, gamma.y};
 
     if (kCommon || r.enable_ncs) {
-        // eta = (gamma - u_x) |E| / E_S for the plane wave
+        // eta = (gamma - u_x) |E| / E_S for the plane wave; ngm = u_x - gamma, for u_x > 0 as
+        // -(1 + u_y^2 + u_z^2) / (gamma + u_x) (no cancellation), its sign taken by the last factor
         float2 up = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, P2(1.0f)));
-        float2 gm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, mul2(up, rcp2(add2(gamma, Q.u0))), sub2(gamma, Q.u0));
+        float2 ngm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, mul2(up, nrcp2(add2(gamma, Q.u0))), sub2(Q.u0, gamma));
         float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
-        float2 eta = mul2(mul2(gm, Emag), P2(c.inv_ES));
+        float2 eta = mul2(mul2(ngm, Emag), P2(-c.inv_ES));
         // h(eta): row interpolation in log eta (log2 scaled to the row position by one FMA), the
         // classical limit below the table; above it the last row, counted (the position is clamped
         // just below the top node, so the split needs no correction there)
@@ -193,14 +207,22 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         Q.tau = s;
         Q.tau_lo = add2(Q.tau_lo, e);
         float2 tsum = add2(Q.tau, Q.tau_lo);
+        if (tsum.x <= 0.0f || tsum.y <= 0.0f) {         // one test of the pair on the common path
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (Q.act[k] && comp(tsum, k) <= 0.0f) {
-                Particle<float> P = unpack(Q, k);
-                take(ncs_emit<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, hist, tally), P,
-                     gam[k], st_ncs[k], pn[k]);
-                repack(Q, k, P);
-                set_comp(inv_g, k, 1.0f / gam[k]);
+            for (int k = 0; k < 2; ++k) {
+                if (Q.act[k] && comp(tsum, k) <= 0.0f) {
+                    Particle<float> P = unpack(Q, k);
+                    bool st;
+                    Photon ph;
+                    take(ncs_emit_body<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, hist, tally),
+                         P, gam[k], st, ph);
+                    if (st) append_now(r, ph);
+                    repack(Q, k, P);
+                    // 1/gamma by the correctly rounded reciprocal: with the branch inlined, a plain
+                    // division of its sqrt result is open to per-kernel rewriting (1/sqrt as rsqrt),
+                    // and every paired kernel must round it alike
+                    set_comp(inv_g, k, __frcp_rn(gam[k]));
+                }
             }
         }
     }
@@ -213,11 +235,14 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                 if (Q.wait[k] == 0u) {
                     const float x = comp(xn, k);
                     Particle<float> P = unpack(Q, k);
+                    bool st;
+                    Photon ph;
                     take(brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], x >= c.x0 && x <= c.x1, x, 0.0f,
                                                 hist, tally),
-                         P, gam[k], st_br[k], pb[k]);
+                         P, gam[k], st, ph);
+                    if (st) append_now(r, ph);
                     repack(Q, k, P);
-                    set_comp(inv_g, k, 1.0f / gam[k]);
+                    set_comp(inv_g, k, __frcp_rn(gam[k]));
                 } else if (Q.wait[k] != PE_WAIT_NEVER) {
                     --Q.wait[k];
                 }
@@ -260,10 +285,13 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     const uint4 wd = draw(r, id[k], n, PUR_BREMS);
                     if (brems_event(pb_[k], wd)) {
                         Particle<float> P = unpack(Q, k);
+                        bool st;
+                        Photon ph;
                         take(brems_emit<float>(t, r, id[k], n, P, gam[k], comp(xn, k), 0.0f, wd, hist, tally), P,
-                             gam[k], st_br[k], pb[k]);
+                             gam[k], st, ph);
+                        if (st) append_now(r, ph);
                         repack(Q, k, P);
-                        set_comp(inv_g, k, 1.0f / gam[k]);
+                        set_comp(inv_g, k, __frcp_rn(gam[k]));
                     }
                 }
             }
@@ -295,7 +323,8 @@ __device__ __forceinline__ void load_one(const RunDevT<float>& r, int64_t i, Pai
     repack(Q, k, P);
 }
 
-// K steps of the pair Q (electrons i0 and i1) with warp-aggregated photon appends
+// K steps of the pair Q (electrons i0 and i1); photons are appended inside the emission branches
+// (append_now), so none is held across the step
 template <int G, bool kCommon>
 __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<float>& r, const float* s_h,
                                           const float* sig_z, int64_t i0, int64_t i1, Pair& Q, int steps,
@@ -305,11 +334,8 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
     float nf = (float)n0;
     uint32_t n_above = 0;                               // particle-steps with eta above the table
     for (int s = 0; s < steps; ++s, nf += 1.0f) {
-        bool st_ncs[2] = {false, false}, st_br[2] = {false, false};
-        Photon pn[2], pb[2];
         if (Q.act[0] || Q.act[1]) {
-            step_pair<G, kCommon>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, st_ncs, pn, st_br, pb, s_hist, s_tally,
-                         n_above);
+            step_pair<G, kCommon>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, s_hist, s_tally, n_above);
             if (!kCommon && r.box_enable) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -319,12 +345,6 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
                     }
                 }
             }
-        }
-        if (__any_sync(0xffffffffu, st_ncs[0] || st_br[0] || st_ncs[1] || st_br[1])) {
-            warp_append(r, st_ncs[0], pn[0]);
-            warp_append(r, st_br[0], pb[0]);
-            warp_append(r, st_ncs[1], pn[1]);
-            warp_append(r, st_br[1], pb[1]);
         }
     }
     if (n_above) atomicAdd(s_tally + PE_T_N_ETA_ABOVE, (unsigned long long)n_above);
