@@ -166,10 +166,14 @@ __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long
 // launch shape) performs bit-identical emission arithmetic, and the rarely taken
 // code stays out of the step loop's instruction stream.  They take the particle
 // by value and return it (no address of the loop-carried state escapes, so it
-// stays in registers).  The paired FP32 kernels inline the NCS branch instead
-// (ncs_emit_body): with 72 registers a thread, the call's register convention cost
-// spills on the common path (measured 7 % of the headline job); both paired
-// kernels inline the same body, so they still agree bit for bit.
+// stays in registers).  The paired FP32 kernels inline both branches instead
+// (ncs_emit_body, brems_emit_body), and so do the FP32 one-electron kernels of the
+// reflected wave for the NCS branch: with 72 (32) registers a thread, a call's
+// register convention cost spills on the common path (measured 9 % of the headline
+// job, 5 % of the reflected-wave job).  The kernels that inline a body refresh
+// 1/gamma after it by the correctly rounded reciprocal, so every instance rounds
+// alike (single run or batch, resident or streaming: compared bit for bit in the
+// tests).
 template <typename R>
 struct Emission {
     Particle<R> P;     // particle after the branch
@@ -246,9 +250,9 @@ __device__ __forceinline__ R brems_prob(const TablesDev& t, const RunDevT<R>& r,
 // Brems photon (text after Eq. 4): y from sigma(y, E) = sigma(E) R2, k^ = v^,
 // recoil, tallies.
 template <typename R>
-__device__ __noinline__ Emission<R> brems_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
-                                               Particle<R> P, R gamma, R xn, R yn, uint4 w, unsigned long long* hist,
-                                               unsigned long long* tally) {
+__device__ __forceinline__ Emission<R> brems_emit_body(const TablesDev& t, const RunDevT<R>& r, uint32_t id,
+                                                       uint32_t n, Particle<R> P, R gamma, R xn, R yn, uint4 w,
+                                                       unsigned long long* hist, unsigned long long* tally) {
     Emission<R> out;
     out.stored = false;
     const R photon_min = tabc<R>(t).photon_min;
@@ -272,6 +276,12 @@ __device__ __noinline__ Emission<R> brems_emit(const TablesDev& t, const RunDevT
     out.P = P;
     out.gamma = gn;
     return out;
+}
+template <typename R>
+__device__ __noinline__ Emission<R> brems_emit(const TablesDev& t, const RunDevT<R>& r, uint32_t id, uint32_t n,
+                                               Particle<R> P, R gamma, R xn, R yn, uint4 w, unsigned long long* hist,
+                                               unsigned long long* tally) {
+    return brems_emit_body<R>(t, r, id, n, P, gamma, xn, yn, w, hist, tally);
 }
 
 // copy an emission branch's result back into the caller's state
@@ -337,10 +347,6 @@ __device__ __forceinline__ void box_check(const RunDevT<R>& r, Particle<R>& P, u
     }
 }
 
-// FP32 one-electron kernels: inline the NCS emission branch (1) or call it (0)
-#ifndef PE_ONE_INLINE_NCS
-#define PE_ONE_INLINE_NCS 0
-#endif
 // kCommon: the run has NCS on, direct brems and no absorbing box (the paper's setup), known at
 // compile time, so the step carries no test of the run's flags; otherwise they are read from the run.
 template <typename R, int G, bool kCommon = false>
@@ -369,8 +375,11 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if constexpr (sizeof(R) == 4) return v * inv_g;
         else return v / gamma;
     };
+    // the reflected-wave FP32 kernels inline the NCS branch (see the emission branches above)
+    constexpr bool kInlineNcs = sizeof(R) == 4 && (G == FK_REFL_LP || G == FK_REFL_CP);
     auto refresh = [&]() {
-        if constexpr (sizeof(R) == 4) inv_g = 1.0f / gamma;
+        if constexpr (kInlineNcs) inv_g = __frcp_rn(gamma);
+        else if constexpr (sizeof(R) == 4) inv_g = 1.0f / gamma;
     };
     const R xn = P.x, yn = P.y;
 
@@ -382,11 +391,9 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
         tau_sub(P, c.ncs_coef * over_gamma(eta) * h);
         if (tau_crossed(P)) {
-#if PE_ONE_INLINE_NCS
-            if constexpr (sizeof(R) == 4)
+            if constexpr (kInlineNcs)
                 take(ncs_emit_body<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
             else
-#endif
                 take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
             if (st) append_now(r, ph);
             refresh();

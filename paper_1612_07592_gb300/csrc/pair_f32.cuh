@@ -287,7 +287,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                         Particle<float> P = unpack(Q, k);
                         bool st;
                         Photon ph;
-                        take(brems_emit<float>(t, r, id[k], n, P, gam[k], comp(xn, k), 0.0f, wd, hist, tally), P,
+                        take(brems_emit_body<float>(t, r, id[k], n, P, gam[k], comp(xn, k), 0.0f, wd, hist, tally), P,
                              gam[k], st, ph);
                         if (st) append_now(r, ph);
                         repack(Q, k, P);
@@ -376,6 +376,8 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 // with the run's flags as compile-time constants (particle-steps/s): 4 CTAs (128 registers) 1.59e11,
 // 5 (96) 1.74e11, 6 (80) 1.78e11, 7 (72) 1.79e11, 8 (64) 1.77e11; the grid of three resident waves
 // (21 CTAs per SM) stays the best at 7 (7: 1.63e11, 14: 1.77e11, 21: 1.79e11, 28 and 35: 1.79e11).
+// With the emission branches inlined (no call in the loop, no spill at 72 registers): 6 CTAs
+// 2.005e11, 7 2.058e11, 8 2.066e11 (at 64 registers the batch instance spills).
 #ifndef PE_PAIR_MIN_CTAS
 #define PE_PAIR_MIN_CTAS 7
 #endif
@@ -438,14 +440,15 @@ __global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t
 constexpr int kStreamTile = 256;                       // electrons per tile (128 threads x 2)
 constexpr int kStreamThreads = kStreamTile / 2;
 // Measured on the 3e7-electron, 4000-step one-step job (stages x CTAs per SM, TB/s at 56 B per
-// particle-step): 2 x 4 4.83, 3 x 3 4.77, 3 x 4 4.60, 2 x 5 4.52, 4 x 4 4.12, 3 x 5 4.14, 2 x 6 3.87:
-// 128 registers (4 CTAs) take the step without spills, and larger stages shrink the L1 that holds
-// the remaining local memory.
+// particle-step), with the emission calls of the step: 2 x 4 4.83, 3 x 3 4.77, 3 x 4 4.60, 2 x 5
+// 4.52, 4 x 4 4.12, 3 x 5 4.14, 2 x 6 3.87 (128 registers took the step without spills, and larger
+// stages shrink the L1 that holds the remaining local memory).  With the emission branches inlined
+// and photons appended in place the step needs 104 registers: 2 x 4 5.48, 2 x 5 5.80, 2 x 6 4.71.
 #ifndef PE_STREAM_STAGES
 #define PE_STREAM_STAGES 2    // stages per CTA: tiles in flight = stages - 1
 #endif
 #ifndef PE_STREAM_MIN_CTAS
-#define PE_STREAM_MIN_CTAS 4  // resident CTAs of 128 threads per SM the registers are sized for
+#define PE_STREAM_MIN_CTAS 5  // resident CTAs of 128 threads per SM the registers are sized for
 #endif
 constexpr int kStreamStages = PE_STREAM_STAGES;
 // one stage: x pairs (float4 per thread), tau pairs (float4), ux, uy, uz (float2 each)
