@@ -461,6 +461,8 @@ static void describe_run(const pe_tables* t, const pe_run_params* rp, int64_t n,
     c.a0 = rp->a0;
     c.w0 = rp->w0_m * kl;
     c.zr = 0.5 * c.w0 * c.w0;
+    c.inv_zr = c.zr > 0 ? 1.0 / c.zr : 0.0;
+    c.inv_w0sq = c.w0 > 0 ? 1.0 / (c.w0 * c.w0) : 0.0;
     c.xf = rp->focus_x_m * kl;
     c.phi_r = 2.0 * kPi * rp->ramp_periods;
     c.phi_f = 2.0 * kPi * rp->flat_s * kC / rp->lambda_m;
@@ -629,8 +631,8 @@ static pe_status build_plan(pe_run* const* runs, int n_runs, int64_t n_steps, co
         for (int k = 0; k < m; ++k) tile_start[k + 1] = tile_start[k] + (runs[idx[k]]->dev.n + block - 1) / block;
         int64_t n_tiles = tile_start[m];
         if (n_tiles == 0) continue;
-        // default grid: three resident waves of the paired plane-wave kernel, twice the resident
-        // CTAs of the one-electron kernel, so the block scheduler evens out tiles of unequal cost
+        // default grid: three resident waves of the paired kernel (plane wave, 2D focus), twice the
+        // resident CTAs of the one-electron kernel, so the block scheduler evens out tiles of unequal cost
         int per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm
                                                   : (prec == PE_F32 ? default_ctas_per_sm_f32(fk, block, smem, K)
                                                                     : 2 * persistent_occupancy_f64(block, smem));
@@ -893,7 +895,7 @@ extern "C" pe_status pe_debug_count(const pe_tables* t, const pe_bw_tables* bw, 
 
 extern "C" pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* stream) {
     if ((n > 0 && (!in || !out)) || n < 0) return fail(PE_ERR_ARG, "pe_math_probe: null buffer or n < 0");
-    if (fn < PE_MATH_RCP || fn > PE_MATH_CUDA_EXPM1) return fail(PE_ERR_ARG, "pe_math_probe: unknown fn");
+    if (fn < PE_MATH_RCP || fn > PE_MATH_EXP_NEG) return fail(PE_ERR_ARG, "pe_math_probe: unknown fn");
     if (n >= (int64_t(1) << 40)) return fail(PE_ERR_ARG, "pe_math_probe: n too large");
     if (n == 0) return PE_OK;
     launch_math_probe(fn, in, out, n, static_cast<cudaStream_t>(stream));

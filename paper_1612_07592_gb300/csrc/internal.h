@@ -78,6 +78,7 @@ struct StepC {
     R box0, box1;
     R inv_log_emax;           // 1 / ln(E_hist_max / m c^2)
     R a0, w0, zr, xf, phi_r, phi_f, k_env;   // fields; k_env = pi / (2 phi_r)
+    R inv_zr, inv_w0sq;       // 1 / z_R, 1 / w0^2 (2D focus)
     R E_const[3], B_const[3];
     R refl_r;                 // reflected wave amplitude coefficient
     R xm2_hi, xm2_lo;         // 2 x_m (mirror plane) as hi + lo: in float an exact pair

@@ -9,6 +9,10 @@ namespace pe {
 constexpr int kStreamMaxSteps = 4;
 
 static bool plane_kind(int fk) { return fk == FK_PLANE_LP || fk == FK_PLANE_CP; }
+// kinds stepped by the paired kernel (two electrons per thread): the 1D plane wave and the 2D focus
+static bool paired_kind(int fk) { return plane_kind(fk) || fk == FK_GAUSS_LP || fk == FK_GAUSS_CP; }
+template <int G>
+constexpr bool kPairedKind = G == FK_PLANE_LP || G == FK_PLANE_CP || G == FK_GAUSS_LP || G == FK_GAUSS_CP;
 // every run of the launch has the paper's setup: NCS on, direct brems, no absorbing box (the paired
 // kernels then take these flags as compile-time constants)
 static bool common_flags(const BatchDevT<float>& b) {
@@ -25,17 +29,20 @@ static bool use_stream(const BatchDevT<float>& b, int steps, int block) {
 static int stream_smem_bytes(int base) { return base + 16 + kStreamStages * kStageBytes; }
 
 // The kernel of a launch, its threads per CTA and dynamic shared memory: the 1D
-// plane-wave kinds use the paired kernel (two electrons per thread, block/2 threads
-// per tile of `block` electrons) or its streaming form; the others one electron per thread.
+// plane-wave and 2D focus kinds use the paired kernel (two electrons per thread, block/2
+// threads per tile of `block` electrons), the plane wave also its streaming form; the others
+// one electron per thread.
 template <bool kSingle, int G>
 static const void* kernel_of(const BatchDevT<float>& b, int steps, int block, int base_smem, int& threads, int& smem) {
     smem = base_smem;
-    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+    if constexpr (kPairedKind<G>) {
         threads = block / 2;
         const bool common = common_flags(b);
-        if (kSingle && use_stream(b, steps, block)) {
-            smem = stream_smem_bytes(base_smem);
-            return common ? (const void*)k_step_pair_stream<G, true> : (const void*)k_step_pair_stream<G, false>;
+        if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+            if (kSingle && use_stream(b, steps, block)) {
+                smem = stream_smem_bytes(base_smem);
+                return common ? (const void*)k_step_pair_stream<G, true> : (const void*)k_step_pair_stream<G, false>;
+            }
         }
         return common ? (const void*)k_step_pair<kSingle, G, true> : (const void*)k_step_pair<kSingle, G, false>;
     } else {
@@ -51,12 +58,18 @@ static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps,
     int threads, smem;
     const void* f = kernel_of<kSingle, G>(b, steps, block, base_smem, threads, smem);
     if (smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
-        if (f == (const void*)k_step_pair_stream<G, true>)
-            k_step_pair_stream<G, true><<<grid, threads, smem, s>>>(t, b, steps);
-        else if (f == (const void*)k_step_pair_stream<G, false>)
-            k_step_pair_stream<G, false><<<grid, threads, smem, s>>>(t, b, steps);
-        else if (f == (const void*)k_step_pair<kSingle, G, true>)
+    if constexpr (kPairedKind<G>) {
+        if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) {
+            if (f == (const void*)k_step_pair_stream<G, true>) {
+                k_step_pair_stream<G, true><<<grid, threads, smem, s>>>(t, b, steps);
+                return;
+            }
+            if (f == (const void*)k_step_pair_stream<G, false>) {
+                k_step_pair_stream<G, false><<<grid, threads, smem, s>>>(t, b, steps);
+                return;
+            }
+        }
+        if (f == (const void*)k_step_pair<kSingle, G, true>)
             k_step_pair<kSingle, G, true><<<grid, threads, smem, s>>>(t, b, steps);
         else
             k_step_pair<kSingle, G, false><<<grid, threads, smem, s>>>(t, b, steps);
@@ -94,21 +107,27 @@ const void* persistent_kernel_f32(const BatchDevT<float>& b, int steps, int base
     return f;
 }
 
-// Default CTAs per SM of the grid.  Paired kernel (plane-wave kinds): three resident waves
+// Default CTAs per SM of the grid.  Paired kernel (plane-wave and 2D focus kinds): three resident waves
 // (tiles differ in cost with their emission histories, and a CTA per one or two tiles lets
 // the block scheduler balance them: measured +6 % over one wave, +2.5 % over two, on 1e6
 // electrons); one wave for the streaming form (each CTA streams many tiles of equal cost).
 // One-electron kernel: twice its resident CTAs.
 int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch) {
-    if (plane_kind(fk)) {
-        const bool stream = steps_per_launch <= kStreamMaxSteps && block == kStreamTile;
+    if (plane_kind(fk) && steps_per_launch <= kStreamMaxSteps && block == kStreamTile) {
         int occ = 0;
-        cudaError_t e = stream ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair_stream<FK_PLANE_LP, true>,
-                                                                             block / 2, stream_smem_bytes(smem))
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP, true>,
-                                                                             block / 2, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair_stream<FK_PLANE_LP, true>,
+                                                                      block / 2, stream_smem_bytes(smem));
+        return e == cudaSuccess && occ > 0 ? occ : 1;
+    }
+    if (paired_kind(fk)) {
+        int occ = 0;
+        cudaError_t e = fk == FK_GAUSS_LP || fk == FK_GAUSS_CP
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_GAUSS_CP, true>,
+                                                                            block / 2, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_pair<true, FK_PLANE_LP, true>,
+                                                                            block / 2, smem);
         occ = e == cudaSuccess && occ > 0 ? occ : 1;
-        return stream ? occ : 3 * occ;
+        return 3 * occ;
     }
     // twice the resident CTAs of this field kind's one-electron kernel
     int occ = 0;

@@ -83,9 +83,35 @@ __device__ __forceinline__ void sincos2(float2 v, float2& s_out, float2& c_out) 
     c_out = make_float2(__cosf(r.x), __cosf(r.y));
 }
 
+// e^{-v} for v >= 0, paired: the hardware base-2 exponential of -v log2(e) (relative error a few
+// ulp; underflows to 0)
+__device__ __forceinline__ float2 exp_neg2(float2 v) {
+    const float2 a = mul2(v, P2(-1.44269504088896341f));
+    float2 r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(a.y));
+    return r;
+}
+
+// Amplitude and Gouy phase of the 2D paraxial focus at a = (x - x_f) / z_R, without an
+// arctangent: sqrt(w0 / w) e^{i atan(a) / 2} = (1 + i a)^{1/2} / |1 + i a|, and with
+// n = |1 + i a| = sqrt(1 + a^2) the square root of 1 + i a is R + i I, R = sqrt((n + 1) / 2),
+// I = a / (2 R) (the half-angle formulas; I written without the cancelling n - 1).  Returns
+// Rn = R / n and In = I / n, and 1 / n^2 = w0^2 / w^2.
+__device__ __forceinline__ void gouy2(float2 a, float2& Rn, float2& In, float2& inv_n2) {
+    const float2 q1 = fma2(a, a, P2(1.0f));                    // n^2
+    const float2 inv_n = rsqrt2(q1);
+    inv_n2 = mul2(inv_n, inv_n);
+    const float2 hh = fma2(mul2(q1, inv_n), P2(0.5f), P2(0.5f));   // (n + 1) / 2
+    const float2 inv_r = rsqrt2(hh);
+    Rn = mul2(mul2(hh, inv_r), inv_n);
+    In = mul2(mul2(P2(0.5f), a), mul2(inv_r, inv_n));
+}
+
 // two electrons; per-electron activity, optical-depth pairs and event fingerprints
 struct Pair {
     float2 x, x_lo, u0, u1, u2, tau, tau_lo;
+    float2 y, y_lo;                     // 2D focus only (zero and unused in 1D)
     uint32_t ev_cnt[2], ev_hash[2];
     uint32_t wait[2];
     bool act[2];
@@ -94,7 +120,7 @@ struct Pair {
 __device__ __forceinline__ Particle<float> unpack(const Pair& Q, int k) {
     Particle<float> P;
     P.x = comp(Q.x, k); P.x_lo = comp(Q.x_lo, k);
-    P.y = 0.0f; P.y_lo = 0.0f;
+    P.y = comp(Q.y, k); P.y_lo = comp(Q.y_lo, k);
     P.u[0] = comp(Q.u0, k); P.u[1] = comp(Q.u1, k); P.u[2] = comp(Q.u2, k);
     P.tau = comp(Q.tau, k); P.tau_lo = comp(Q.tau_lo, k);
     P.ev_cnt = Q.ev_cnt[k]; P.ev_hash = Q.ev_hash[k];
@@ -103,15 +129,17 @@ __device__ __forceinline__ Particle<float> unpack(const Pair& Q, int k) {
 }
 __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P) {
     set_comp(Q.x, k, P.x); set_comp(Q.x_lo, k, P.x_lo);
+    set_comp(Q.y, k, P.y); set_comp(Q.y_lo, k, P.y_lo);
     set_comp(Q.u0, k, P.u[0]); set_comp(Q.u1, k, P.u[1]); set_comp(Q.u2, k, P.u[2]);
     set_comp(Q.tau, k, P.tau); set_comp(Q.tau_lo, k, P.tau_lo);
     Q.ev_cnt[k] = P.ev_cnt; Q.ev_hash[k] = P.ev_hash;
     Q.wait[k] = P.wait;
 }
 
-// one step of two electrons (plane wave, G = FK_PLANE_LP or FK_PLANE_CP).  kCommon: the run
-// has NCS on, direct brems and no absorbing box (the paper's setup), known at compile time, so
-// the step carries no test of the run's flags; otherwise they are read from the run.
+// one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_GAUSS_LP,
+// FK_GAUSS_CP: the 2D paraxial focus).  kCommon: the run has NCS on, direct brems and no absorbing
+// box (the paper's setup), known at compile time, so the step carries no test of the run's flags;
+// otherwise they are read from the run.
 template <int G, bool kCommon>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
@@ -135,11 +163,14 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     const float2 kts = mul2(P2(2.0f * c.k_env), mul2(rs, rc));
     const float2 side = sub2(rem, phi);
     const float2 dg = make_float2(copysignf(kts.x, side.x), copysignf(kts.y, side.y));
+    constexpr bool kPlane = G == FK_PLANE_LP || G == FK_PLANE_CP;
+    constexpr bool kCP = G == FK_PLANE_CP || G == FK_GAUSS_CP;
+    const float2 ma0 = P2(-c.a0);
+    float2 ey, ez = P2(0.0f), ex = P2(0.0f), bx = P2(0.0f);
+    if constexpr (kPlane) {
     float2 st, ct;
     sincos2(phi, st, ct);
-    const float2 ma0 = P2(-c.a0);
-    float2 ey = mul2(ma0, fma2(dg, st, mul2(g, ct)));          // -a0 (g' sin + g cos)
-    float2 ez = P2(0.0f);
+    ey = mul2(ma0, fma2(dg, st, mul2(g, ct)));                 // -a0 (g' sin + g cos)
     if (G == FK_PLANE_CP) ez = mul2(P2(c.a0), sub2(mul2(dg, ct), mul2(g, st)));   // a0 (g' cos - g sin)
     // Boris push with E = (0, ey, ez), B = (0, -ez, ey)
     const float2 mhey = mul2(P2(-0.5f * c.dt), ey);                    // -h E_y (the sign is exact)
@@ -169,12 +200,65 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         Q.u0 = add2(um0, mul2(p1, s2));
         Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
     }
+    } else {
+        // 2D paraxial focus (fields() in physics.cuh), amplitude and Gouy phase by gouy2: with
+        // S = sqrt(w0 / w) e^{-y^2 / w^2} and theta = phi - y^2 / (2 R_c) + atan(a) / 2,
+        // E_y = -a0 S (g' sin + g cos), E_x = a0 g S (y / R_c cos + 2 y / w^2 sin), for CP
+        // E_z = a0 S (g' cos - g sin) and B_x = a0 g S (2 y / w^2 cos - y / R_c sin); B = (B_x, -E_z, E_y)
+        const float2 a = mul2(sub2(Q.x, P2(c.xf)), P2(c.inv_zr));
+        float2 Rn, In, inv_n2;
+        gouy2(a, Rn, In, inv_n2);
+        const float2 yy = mul2(Q.y, Q.y);
+        const float2 inv_w2 = mul2(inv_n2, P2(c.inv_w0sq));
+        const float2 inv_R = mul2(mul2(a, inv_n2), P2(c.inv_zr));
+        const float2 G_ = exp_neg2(mul2(yy, inv_w2));
+        float2 s0, c0;
+        sincos2(fma2(mul2(yy, inv_R), P2(-0.5f), phi), s0, c0);
+        const float2 Sc = mul2(G_, sub2(mul2(Rn, c0), mul2(In, s0)));    // S cos(theta)
+        const float2 Ss = mul2(G_, fma2(Rn, s0, mul2(In, c0)));          // S sin(theta)
+        ey = mul2(ma0, fma2(dg, Ss, mul2(g, Sc)));
+        const float2 yR = mul2(Q.y, inv_R), y2w = mul2(mul2(P2(2.0f), Q.y), inv_w2);
+        const float2 a0g = mul2(P2(c.a0), g);
+        ex = mul2(a0g, fma2(yR, Sc, mul2(y2w, Ss)));
+        if constexpr (kCP) {
+            ez = mul2(P2(c.a0), sub2(mul2(dg, Sc), mul2(g, Ss)));
+            bx = mul2(a0g, sub2(mul2(y2w, Sc), mul2(yR, Ss)));
+        }
+        // Boris push, u^- = u - h E, rotation by t = -h B / gamma^-, u^+ = u^- + (u^- + u^- x t) x s
+        // - h E (terms of the exact zeros left out: B_y = B_x = E_z = 0 for LP)
+        const float2 mh = P2(-0.5f * c.dt);
+        const float2 um0 = fma2(mh, ex, Q.u0);
+        const float2 um1 = fma2(mh, ey, Q.u1);
+        const float2 um2 = kCP ? fma2(mh, ez, Q.u2) : Q.u2;
+        const float2 ig = rsqrt2(fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f)))));
+        const float2 mhig = mul2(mh, ig);
+        const float2 t2 = mul2(ey, mhig);                              // -h B_z / gamma
+        if constexpr (kCP) {
+            const float2 t0 = mul2(bx, mhig);                          // -h B_x / gamma
+            const float2 t1 = mul2(ez, mul2(P2(0.5f * c.dt), ig));     // -h B_y / gamma, B_y = -E_z
+            const float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, fma2(t1, t1, fma2(t0, t0, P2(1.0f))))));
+            const float2 s0_ = mul2(f, t0), s1 = mul2(f, t1), s2 = mul2(f, t2);
+            const float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
+            const float2 p1 = add2(um1, sub2(mul2(um2, t0), mul2(um0, t2)));
+            const float2 p2 = add2(um2, sub2(mul2(um0, t1), mul2(um1, t0)));
+            Q.u0 = fma2(mh, ex, add2(um0, sub2(mul2(p1, s2), mul2(p2, s1))));
+            Q.u1 = fma2(mh, ey, add2(um1, sub2(mul2(p2, s0_), mul2(p0, s2))));
+            Q.u2 = fma2(mh, ez, add2(um2, sub2(mul2(p0, s1), mul2(p1, s0_))));
+        } else {
+            const float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, P2(1.0f))));
+            const float2 s2 = mul2(f, t2);
+            const float2 p0 = fma2(um1, t2, um0);
+            const float2 p1 = sub2(um1, mul2(um0, t2));
+            Q.u0 = fma2(mh, ex, fma2(p1, s2, um0));
+            Q.u1 = fma2(mh, ey, sub2(um1, mul2(p0, s2)));
+        }
+    }
     // gamma and 1/gamma from one reciprocal square root (1/gamma serves the rate and the
     // position update; emitting lanes refresh it from their new gamma)
     const float2 g2 = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, fma2(Q.u0, Q.u0, P2(1.0f))));
     float2 inv_g = rsqrt2(g2);
     float2 gamma = mul2(g2, inv_g);
-    const float2 xn = Q.x;
+    const float2 xn = Q.x, yn = Q.y;
     float gam[2] = {gamma.x, gamma.y};
 
     if (kCommon || r.enable_ncs) {
@@ -182,8 +266,24 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         // -(1 + u_y^2 + u_z^2) / (gamma + u_x) (no cancellation), its sign taken by the last factor
         float2 up = fma2(Q.u2, Q.u2, fma2(Q.u1, Q.u1, P2(1.0f)));
         float2 ngm = sel2(Q.u0.x > 0.0f, Q.u0.y > 0.0f, mul2(up, nrcp2(add2(gamma, Q.u0))), sub2(Q.u0, gamma));
-        float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
-        float2 eta = mul2(mul2(ngm, Emag), P2(-c.inv_ES));
+        float2 eta;
+        if constexpr (kPlane) {
+            float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
+            eta = mul2(mul2(ngm, Emag), P2(-c.inv_ES));
+        } else {
+            // eta = |V^2 + 2 V_x (u.E)|^{1/2} / E_S with V = (gamma - u_x) E + u x (B - x^ x E): here
+            // B_y + E_z = B_z - E_y = 0, so u x (...) = (0, u_z B_x, -u_y B_x); nV = -V except in y
+            const float2 nV0 = mul2(ngm, ex);
+            const float2 uE = fma2(Q.u1, ey, fma2(Q.u0, ex, kCP ? mul2(Q.u2, ez) : P2(0.0f)));
+            float2 V1 = mul2(ngm, ey), V2 = P2(0.0f);
+            if constexpr (kCP) {
+                V1 = sub2(mul2(Q.u2, bx), V1);                         // u_z B_x + (gamma - u_x) E_y
+                V2 = fma2(Q.u1, bx, mul2(ngm, ez));                    // -(V_z)
+            }
+            const float2 qv = sub2(fma2(V2, V2, fma2(V1, V1, mul2(nV0, nV0))), mul2(mul2(P2(2.0f), nV0), uE));
+            const float2 rq = sqrt2(make_float2(fmaxf(qv.x, 0.0f), fmaxf(qv.y, 0.0f)));
+            eta = mul2(rq, P2(c.inv_ES));
+        }
         // h(eta): row interpolation in log eta (log2 scaled to the row position by one FMA), the
         // classical limit below the table; above it the last row, counted (the position is clamped
         // just below the top node, so the split needs no correction there)
@@ -214,7 +314,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     Particle<float> P = unpack(Q, k);
                     bool st;
                     Photon ph;
-                    take(ncs_emit_body<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), 0.0f, hist, tally),
+                    take(ncs_emit_body<float>(t, r, id[k], n, P, gam[k], comp(eta, k), comp(xn, k), comp(yn, k), hist,
+                                              tally),
                          P, gam[k], st, ph);
                     if (st) append_now(r, ph);
                     repack(Q, k, P);
@@ -237,8 +338,9 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     Particle<float> P = unpack(Q, k);
                     bool st;
                     Photon ph;
-                    take(brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], x >= c.x0 && x <= c.x1, x, 0.0f,
-                                                hist, tally),
+                    const bool in_slab = x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh);
+                    take(brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], in_slab, x, comp(yn, k), hist,
+                                                tally),
                          P, gam[k], st, ph);
                     if (st) append_now(r, ph);
                     repack(Q, k, P);
@@ -255,7 +357,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float x = comp(xn, k);
-                in[k] = Q.act[k] && x >= c.x0 && x <= c.x1 && gam[k] > 1.0f + tc.photon_min;
+                in[k] = Q.act[k] && x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh) &&
+                        gam[k] > 1.0f + tc.photon_min;
             }
             if (in[0] || in[1]) {
                 const float2 gv = make_float2(gam[0], gam[1]);
@@ -287,7 +390,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                         Particle<float> P = unpack(Q, k);
                         bool st;
                         Photon ph;
-                        take(brems_emit_body<float>(t, r, id[k], n, P, gam[k], comp(xn, k), 0.0f, wd, hist, tally), P,
+                        take(brems_emit_body<float>(t, r, id[k], n, P, gam[k], comp(xn, k), comp(yn, k), wd, hist, tally), P,
                              gam[k], st, ph);
                         if (st) append_now(r, ph);
                         repack(Q, k, P);
@@ -304,6 +407,11 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     two_sum2(Q.x, d, s, e);
     Q.x = s;
     Q.x_lo = add2(Q.x_lo, e);
+    if constexpr (!kPlane) {                            // y^{n+1} = y^n + dt u_y / gamma, compensated
+        two_sum2(Q.y, mul2(mul2(dt, Q.u1), inv_g), s, e);
+        Q.y = s;
+        Q.y_lo = add2(Q.y_lo, e);
+    }
     if (!kCommon && r.box_enable) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -351,7 +459,7 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
 }
 
 __device__ __forceinline__ void pair_clear(Pair& Q) {
-    Q.x = Q.x_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
+    Q.x = Q.x_lo = Q.y = Q.y_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
     Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
     Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
     Q.act[0] = Q.act[1] = false;
@@ -366,6 +474,7 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     pair_clear(Q);
     if (i0 < r.n) load_one(r, i0, Q, 0, s_tally);
     if (i1 < r.n) load_one(r, i1, Q, 1, s_tally);
+    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) Q.y = Q.y_lo = P2(0.0f);   // 1D: y is not state
     const bool live0 = i0 < r.n, live1 = i1 < r.n;
     pair_loop<G, kCommon>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
     if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
@@ -381,9 +490,14 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 #ifndef PE_PAIR_MIN_CTAS
 #define PE_PAIR_MIN_CTAS 7
 #endif
+#ifndef PE_PAIR_MIN_CTAS_2D
+#define PE_PAIR_MIN_CTAS_2D 5
+#endif
+template <int G>
+constexpr int pair_min_ctas() { return (G == FK_GAUSS_LP || G == FK_GAUSS_CP) ? PE_PAIR_MIN_CTAS_2D : PE_PAIR_MIN_CTAS; }
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
 template <bool kSingle, int G, bool kCommon>
-__global__ void __launch_bounds__(128, PE_PAIR_MIN_CTAS) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
+__global__ void __launch_bounds__(128, pair_min_ctas<G>()) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<float> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);

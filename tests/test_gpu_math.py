@@ -1,9 +1,11 @@
 """The FP32 step's hand-written forms against the exact values and against CUDA's own functions.
 
-The paired FP32 step replaces three library calls by forms of its own: 1/d (d >= 1) by the
+The paired FP32 step replaces library calls by forms of its own: 1/d (d >= 1) by the
 hardware reciprocal estimate refined by one Newton-Raphson step; the carrier-phase sine and
-cosine by a Cody-Waite reduction by 2 pi followed by the hardware sine and cosine; and the
-probability 1 - e^-x of Eq. 4 by a four-term Taylor series below 2^-5.  pe_math_probe runs the
+cosine by a Cody-Waite reduction by 2 pi followed by the hardware sine and cosine; the
+probability 1 - e^-x of Eq. 4 by a four-term Taylor series below 2^-5; and, for the 2D focus,
+the amplitude and Gouy phase (1 + a^2)^(-1/4) e^{i atan(a)/2} by the half-angle square root of
+1 + i a, and the transverse profile e^{-y^2/w^2} by the hardware base-2 exponential.  pe_math_probe runs the
 very device functions the step uses; here they are swept over the ranges the step feeds them
 and compared with the exact values (FP64 on the host, of the same float inputs), with the
 error bounds the design states, and with CUDA's __frcp_rn, sinf, cosf and expm1f.
@@ -87,3 +89,33 @@ def test_brems_probability_series():
           f"above 2^-5 {rel[~small].max():.3g}")
     assert rel[small].max() < 1.0e-7
     np.testing.assert_array_equal(ours[~small], cuda[~small])
+
+
+def test_gouy_factors():
+    """(1 + a^2)^(-1/4) cos(atan(a)/2) and ... sin(...) against FP64: a over the distances from
+    the focus a run reaches (|a| < 1 in the 2D workloads) and beyond; the forms use two hardware
+    reciprocal square roots and a few roundings: measured on GB300 2^-21.8 (cos part) and 2^-23.7
+    (sin part) absolute, bound 2^-21 (the values are below 1)."""
+    rng = np.random.default_rng(4)
+    a = np.concatenate([rng.uniform(-1.0, 1.0, 1 << 20), rng.uniform(-50.0, 50.0, 1 << 16),
+                        np.array([0.0, 1e-6, -1e-6, 1.0, -1.0])]).astype(np.float32)
+    ad = a.astype(np.float64)
+    amp = (1.0 + ad * ad) ** -0.25
+    ec = np.abs(probe(M["GOUY_C"], a) - amp * np.cos(0.5 * np.arctan(ad))).max()
+    es = np.abs(probe(M["GOUY_S"], a) - amp * np.sin(0.5 * np.arctan(ad))).max()
+    print(f"Gouy factors: cos part {math.log2(ec):.2f}, sin part {math.log2(es):.2f} (log2 abs error)")
+    assert max(ec, es) < 2.0 ** -21
+
+
+def test_transverse_profile_exponential():
+    """e^-v for 0 <= v <= 30 against FP64: the hardware base-2 exponential of -v log2(e); the
+    product v log2(e) is rounded once, which adds about v 2^-24 relative: measured on GB300 1.6e-7
+    relative for v <= 1 and 1.7e-6 up to v = 30, bound 2^-21 (1 + v)."""
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.uniform(0.0, 1.0, 1 << 20), rng.uniform(0.0, 30.0, 1 << 18),
+                        np.array([0.0, 1e-30, 1.0])]).astype(np.float32)
+    vd = v.astype(np.float64)
+    exact = np.exp(-vd)
+    rel = np.abs(probe(M["EXP_NEG"], v) - exact) / exact
+    print(f"e^-v: max rel {rel.max():.3g}, over v <= 1 {rel[vd <= 1.0].max():.3g}")
+    assert np.all(rel < 2.0 ** -21 * (1.0 + vd))
