@@ -36,7 +36,7 @@ UNIT = "particle-steps/s"
 # FP32 operations of one particle-step of the headline job, counted by ncu's SASS counters on one
 # launch of the whole job (1e6 electrons x 4000 steps): 2 per FFMA, 4 per FFMA2, 1 per FADD/FMUL,
 # 2 per FADD2/FMUL2, over the 4e9 particle-steps (profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md)
-FLOP_PER_PSTEP_1D = 133.9
+FLOP_PER_PSTEP_1D = 122.9
 FLOP_COUNT_SOURCE = "ncu SASS counters on the headline launch (FFMA 2, FFMA2 4, FADD/FMUL 1, FADD2/FMUL2 2)"
 # Algorithmic bytes of one particle-step when the state round-trips memory every step:
 # read + write of x (float pair, 8 B), ux, uy, uz (f32) and tau (float pair, 8 B) in 1D;
@@ -48,15 +48,15 @@ BYTES_PER_PSTEP_2D = 72
 BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
-# capture of the headline launch (45.3 MB for 1e6 electrons: the state read once, the final state
-# partly still in L2 at the end, the cold emission tables, register spill lines evicted from L2;
-# profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md); None once the kernel changes.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 45.34
+# capture of the headline launch (29.1 MB for 1e6 electrons: the state read once, the final state
+# still in L2 at the end, the cold emission tables; profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md);
+# None once the kernel changes.
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.08
 # DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
-# one launch on 8e6 electrons (386.8 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
+# one launch on 8e6 electrons (386.7 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
 # dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
 # (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md); None once the kernel changes.
-NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.36
+NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.33
 
 
 def peaks():
@@ -172,6 +172,9 @@ def main():
                     help="profiling run only: one PE_PIC_1D job (--particles, --job-steps) of the config-2 physics")
     ap.add_argument("--profile-pairs", action="store_true",
                     help="profiling run only: the 1 GeV Au bunch (--particles electrons), then two pair transports")
+    ap.add_argument("--profile-2d", action="store_true",
+                    help="profiling run only: two launches of the 2D focus job (config 3 physics) on --particles "
+                         "electrons, --job-steps steps each (the second is the one to capture)")
     ap.add_argument("--profile-bw", action="store_true",
                     help="profiling run only: the reflected-wave job (--particles electrons), then two Breit-Wheeler "
                          "transports of its photons")
@@ -184,6 +187,9 @@ def main():
         return
     if args.profile_bw:
         profile_bw(args.particles or 100_000)
+        return
+    if args.profile_2d:
+        profile_2d(args.particles or 4_000_000, args.job_steps or 200)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -648,6 +654,25 @@ def profile_pairs(n):
     print(json.dumps({"profile_pairs": True, "electrons": n, "photons": int(r.tally_out().photons_stored),
                       "pairs": out[1], "tests": int(out[2][pe.PT["N_TESTS"]]), "pairs_free_path": free[1]}))
     r.close()
+
+
+def profile_2d(n, steps):
+    """Profiling run: the 2D focus job (config 3 physics) with n electrons, two launches of `steps`
+    steps (the second is the one to capture)."""
+    import torch
+    import paper_1612_07592_gb300 as pe
+    from paper_1612_07592_gb300 import workloads as W
+    c = W.config3()
+    tables = pe.pe_create_tables(c["tables"], c["Z"])
+    r = pe.Run(tables, pe.run_params(precision=pe.PE_F32, **c["run"]), n, capacity=1 << 24)
+    for _ in range(2):
+        pe.pe_step([r.handle], steps)
+    torch.cuda.synchronize()
+    out = r.tally_out()
+    print(json.dumps({"profile_2d": True, "electrons": n, "steps": 2 * steps,
+                      "photons": int(out.tally[pe.T["N_PHOTONS"]])}))
+    r.close()
+    pe.pe_destroy_tables(tables)
 
 
 def profile_bw(n):

@@ -108,6 +108,22 @@ __device__ __forceinline__ void gouy2(float2 a, float2& Rn, float2& In, float2& 
     In = mul2(mul2(P2(0.5f), a), mul2(inv_r, inv_n));
 }
 
+// envelope g = sin^2(k psi) of a pulse at phase phi, psi the phase distance to the nearer end of
+// the pulse, k psi clamped to [0, pi/2] (0 outside the pulse, pi/2 on the flat top); dg/dphi =
+// +-k sin(2 k psi), + before the middle of the pulse and - after it (it vanishes on the flat top
+// and outside)
+__device__ __forceinline__ void envelope2(const StepC<float>& c, float2 phi, float2& g, float2& dg) {
+    const float2 rem = sub2(P2(2.0f * c.phi_r + c.phi_f), phi);
+    const float2 psi = make_float2(fminf(phi.x, rem.x), fminf(phi.y, rem.y));
+    const float2 arg = clamp2(mul2(P2(c.k_env), psi), 0.0f, 1.57079632679489662f);
+    float2 rs, rc;
+    ramp_sincos2(arg, rs, rc);
+    g = mul2(rs, rs);
+    const float2 kts = mul2(P2(2.0f * c.k_env), mul2(rs, rc));
+    const float2 side = sub2(rem, phi);
+    dg = make_float2(copysignf(kts.x, side.x), copysignf(kts.y, side.y));
+}
+
 // two electrons; per-electron activity, optical-depth pairs and event fingerprints
 struct Pair {
     float2 x, x_lo, u0, u1, u2, tau, tau_lo;
@@ -151,18 +167,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     const float2 nf2 = P2(nf);
     float2 phi = fma2(nf2, P2(c.dt_lo), sub2(mul2(nf2, P2(c.dt_hi)), Q.x));
     phi = sub2(phi, Q.x_lo);
-    // envelope g = sin^2(k psi), psi the phase distance to the nearer end of the pulse, k psi
-    // clamped to [0, pi/2] (0 outside the pulse, pi/2 on the flat top); dg/dphi = +-k sin(2 k psi),
-    // + before the middle of the pulse and - after it (it vanishes on the flat top and outside)
-    const float2 rem = sub2(P2(2.0f * c.phi_r + c.phi_f), phi);
-    const float2 psi = make_float2(fminf(phi.x, rem.x), fminf(phi.y, rem.y));
-    const float2 arg = clamp2(mul2(P2(c.k_env), psi), 0.0f, 1.57079632679489662f);
-    float2 rs, rc;
-    ramp_sincos2(arg, rs, rc);
-    const float2 g = mul2(rs, rs);
-    const float2 kts = mul2(P2(2.0f * c.k_env), mul2(rs, rc));
-    const float2 side = sub2(rem, phi);
-    const float2 dg = make_float2(copysignf(kts.x, side.x), copysignf(kts.y, side.y));
+    float2 g, dg;
+    envelope2(c, phi, g, dg);
     constexpr bool kPlane = G == FK_PLANE_LP || G == FK_PLANE_CP;
     constexpr bool kCP = G == FK_PLANE_CP || G == FK_GAUSS_CP;
     const float2 ma0 = P2(-c.a0);
@@ -490,6 +496,8 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 #ifndef PE_PAIR_MIN_CTAS
 #define PE_PAIR_MIN_CTAS 7
 #endif
+// The 2D focus (config 3, one run, particle-steps/s): 4 CTAs (128 registers) 1.25e11, 5 (96)
+// 1.30e11, 6 (80) 1.31e11; at 80 registers the batch instance (served requests) spills, at 96 none.
 #ifndef PE_PAIR_MIN_CTAS_2D
 #define PE_PAIR_MIN_CTAS_2D 5
 #endif
