@@ -10,16 +10,20 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe.so")
-SOURCES = ["api.cu", "kernels.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels_pic.cu", "kernels_pair.cu",
-           "kernels_bw.cu", "kernels_diag.cu", "tables.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "kernels_f32.cu", "kernels_paired.cu", "kernels_f64.cu", "kernels_pic.cu",
+           "kernels_pair.cu", "kernels_bw.cu", "kernels_diag.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # single-precision division and square root at 2-ulp accuracy in the kernels (the FP64
 # arithmetic is unaffected); the stated FP32 error budget includes this
 KERNEL_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
-# the FP64 step kernels: no multiply-add contraction, so the plain and the persistent FP64
-# kernels round every operation alike (bit-identical results; the oracle builds the same way)
-FILE_FLAGS = {"kernels_f64.cu": ["-fmad=false"]}
+# Every rounding as written where kernels must agree bit for bit: the FP64 step kernels (no
+# multiply-add contraction: the plain and the persistent FP64 kernels round every operation
+# alike, and the oracle builds the same way), and the paired FP32 kernels, whose single-run, batch
+# and streaming instances inline the same emission branches (no contraction, IEEE division and
+# square root: approximate forms lowered per instance made them differ in the last bit).
+FILE_FLAGS = {"kernels_f64.cu": KERNEL_FLAGS + ["-fmad=false"],
+              "kernels_paired.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"]}
 
 
 def _nvcc() -> str:
@@ -42,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, lib: str | None = None, ou
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT, src + ".o")
-        extra = (KERNEL_FLAGS if src.startswith("kernels") else []) + FILE_FLAGS.get(src, []) + \
+        extra = FILE_FLAGS.get(src, KERNEL_FLAGS if src.startswith("kernels") else []) + \
             ["-D" + d for d in defines]
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):

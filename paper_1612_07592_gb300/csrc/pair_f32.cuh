@@ -26,7 +26,14 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, P2(-1.0f), a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, P2(-1.0f)); }
 // per-electron operations (no paired form)
-__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+// the hardware's approximate square root, written out (the translation unit that instantiates the
+// paired kernels rounds its own divisions and square roots as IEEE operations)
+__device__ __forceinline__ float2 sqrt2(float2 a) {
+    float2 r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r.y) : "f"(a.y));
+    return r;
+}
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 // -1/d for d >= 1 (both uses below): the hardware reciprocal estimate of -d refined by one
 // Newton-Raphson step, r' = r + r (1 + d r), which squares its relative error (about 1 ulp after
@@ -153,9 +160,12 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
 }
 
 // one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_GAUSS_LP,
-// FK_GAUSS_CP: the 2D paraxial focus).  kCommon: the run has NCS on, direct brems and no absorbing
-// box (the paper's setup), known at compile time, so the step carries no test of the run's flags;
-// otherwise they are read from the run.
+// FK_GAUSS_CP: the 2D paraxial focus).  An inactive half of the pair (a removed electron, or an
+// empty slot past the end of the run) has x = NaN, so its fields, momenta, eta and optical depth
+// are NaN from its first step on, and the optical depth's crossing and the target test are false
+// for it without reading the activity flags.  kCommon: the run has NCS on, direct brems and no
+// absorbing box (the paper's setup), known at compile time, so the step carries no test of the
+// run's flags; otherwise they are read from the run.
 template <int G, bool kCommon>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
@@ -316,7 +326,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         if (tsum.x <= 0.0f || tsum.y <= 0.0f) {         // one test of the pair on the common path
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (Q.act[k] && comp(tsum, k) <= 0.0f) {
+                if (comp(tsum, k) <= 0.0f) {
                     Particle<float> P = unpack(Q, k);
                     bool st;
                     Photon ph;
@@ -363,7 +373,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float x = comp(xn, k);
-                in[k] = Q.act[k] && x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh) &&
+                in[k] = x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh) &&
                         gam[k] > 1.0f + tc.photon_min;
             }
             if (in[0] || in[1]) {
@@ -465,7 +475,8 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
 }
 
 __device__ __forceinline__ void pair_clear(Pair& Q) {
-    Q.x = Q.x_lo = Q.y = Q.y_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau = Q.tau_lo = P2(0.0f);
+    Q.x_lo = Q.y = Q.y_lo = Q.u0 = Q.u1 = Q.u2 = Q.tau_lo = P2(0.0f);
+    Q.x = Q.tau = P2(__int_as_float(0x7fc00000));       // an empty slot is NaN, as a removed electron
     Q.ev_cnt[0] = Q.ev_cnt[1] = Q.ev_hash[0] = Q.ev_hash[1] = 0;
     Q.wait[0] = Q.wait[1] = PE_WAIT_NEVER;
     Q.act[0] = Q.act[1] = false;
