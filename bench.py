@@ -36,7 +36,7 @@ UNIT = "particle-steps/s"
 # FP32 operations of one particle-step of the headline job, counted by ncu's SASS counters on one
 # launch of the whole job (1e6 electrons x 4000 steps): 2 per FFMA, 4 per FFMA2, 1 per FADD/FMUL,
 # 2 per FADD2/FMUL2, over the 4e9 particle-steps (profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md)
-FLOP_PER_PSTEP_1D = 122.9
+FLOP_PER_PSTEP_1D = 123.9
 FLOP_COUNT_SOURCE = "ncu SASS counters on the headline launch (FFMA 2, FFMA2 4, FADD/FMUL 1, FADD2/FMUL2 2)"
 # Algorithmic bytes of one particle-step when the state round-trips memory every step:
 # read + write of x (float pair, 8 B), ux, uy, uz (f32) and tau (float pair, 8 B) in 1D;
@@ -47,16 +47,21 @@ BYTES_PER_PSTEP_2D = 72
 # count the hot-path scope uses for its 60 % target
 BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
+# warp instructions per 64 electron-steps of the dominant kernel (one warp steps 64 electrons), from
+# the same ncu capture of the headline launch; the kernel is bound by instruction issue (one warp
+# instruction per scheduler per clock), which the roofline's `issue` entry reports beside the FP32 pipe
+NCU_WARP_INST_PER_64_ESTEPS = 279.1
+SCHEDULERS_PER_SM = 4
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
 # capture of the headline launch (29.1 MB for 1e6 electrons: the state read once, the final state
 # still in L2 at the end, the cold emission tables; profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md);
 # None once the kernel changes.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.08
+NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.13
 # DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
 # one launch on 8e6 electrons (386.7 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
 # dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
 # (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md); None once the kernel changes.
-NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.33
+NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.34
 
 
 def peaks():
@@ -344,6 +349,13 @@ def main():
                        "peak_kind": "measured: FMA-loop kernel of the FP32 pipe (pe_fma_peak), this GPU, this run",
                        "flop_per_particle_step": FLOP_PER_PSTEP_1D, "flop_count": FLOP_COUNT_SOURCE,
                        "pipes_measured": pipes, "fp32_peak_derived_tflops": derived, "sm_count": sms}
+    clk = (res["clocks"].get("sm_mhz") or res["clocks"].get("sm_max_mhz") or 2070.0) * 1e6
+    issue_ceiling = sms * SCHEDULERS_PER_SM * clk
+    issued = NCU_WARP_INST_PER_64_ESTEPS / 64.0 * pst / (ms * 1e-3)
+    res["roofline"]["issue"] = {"achieved": issued, "peak": issue_ceiling, "unit": "warp instructions/s",
+                                "frac": issued / issue_ceiling,
+                                "warp_inst_per_64_electron_steps": NCU_WARP_INST_PER_64_ESTEPS,
+                                "peak_kind": "one warp instruction per scheduler per clock at the median SM clock"}
 
     if rank == 0 and not args.skip_extras:
         res["roofline_hbm"] = hbm_form(pe, tables, cfg, stream, hbm_peak_gbs(pk), pk_kind)

@@ -162,14 +162,14 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
 // one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_GAUSS_LP,
 // FK_GAUSS_CP: the 2D paraxial focus).  An inactive half of the pair (a removed electron, or an
 // empty slot past the end of the run) has x = NaN, so its fields, momenta, eta and optical depth
-// are NaN from its first step on, and the optical depth's crossing and the target test are false
-// for it without reading the activity flags.  kCommon: the run has NCS on, direct brems and no
+// are NaN from its first step on, and the eta count, the optical depth's crossing and the target
+// test are false for it without reading the activity flags.  kCommon: the run has NCS on, direct brems and no
 // absorbing box (the paper's setup), known at compile time, so the step carries no test of the
 // run's flags; otherwise they are read from the run.
 template <int G, bool kCommon>
 __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<float>& r, const float* h_tab,
                                           const float* sig_tab, const uint32_t id[2], uint32_t n, float nf, Pair& Q,
-                                          unsigned long long* hist, unsigned long long* tally, uint32_t& n_above) {
+                                          unsigned long long* hist, unsigned long long* tally, float2& n_above) {
     const StepC<float>& c = r.c;
     const TabC<float>& tc = t.cf;
     const float2 dt = P2(c.dt), h = P2(0.5f * c.dt);
@@ -305,7 +305,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         // just below the top node, so the split needs no correction there)
         const float2 tp = fma2(log2v(eta), P2(tc.inv_dln_eta * 0.693147180559945309f),
                                P2(-tc.ln_eta_min * tc.inv_dln_eta));
-        n_above += (uint32_t)(Q.act[0] && tp.x >= tc.eta_last) + (uint32_t)(Q.act[1] && tp.y >= tc.eta_last);
+        n_above = add2(n_above, make_float2(tp.x >= tc.eta_last ? 1.0f : 0.0f, tp.y >= tc.eta_last ? 1.0f : 0.0f));
         const float2 tpc = clamp2(tp, 0.0f, tc.eta_last - 0x1.0p-10f);
         const float2 tt = add2(sub2(tpc, P2(0.5f)), P2(0x1.8p23f));
         const int ix = dbg_idx(t.dbg, __float_as_int(tt.x) - 0x4B400000, t.n_eta - 1);
@@ -456,7 +456,7 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
     const uint32_t id[2] = {r.id0 + (uint32_t)i0, r.id0 + (uint32_t)i1};
     const uint32_t n0 = (uint32_t)r.step0;
     float nf = (float)n0;
-    uint32_t n_above = 0;                               // particle-steps with eta above the table
+    float2 n_above = P2(0.0f);                          // particle-steps with eta above the table (exact to 2^24)
     for (int s = 0; s < steps; ++s, nf += 1.0f) {
         if (Q.act[0] || Q.act[1]) {
             step_pair<G, kCommon>(t, r, s_h, sig_z, id, n0 + (uint32_t)s, nf, Q, s_hist, s_tally, n_above);
@@ -471,7 +471,8 @@ __device__ __forceinline__ void pair_loop(const TablesDev& t, const RunDevT<floa
             }
         }
     }
-    if (n_above) atomicAdd(s_tally + PE_T_N_ETA_ABOVE, (unsigned long long)n_above);
+    const unsigned int na = __float2uint_rz(n_above.x) + __float2uint_rz(n_above.y);
+    if (na) atomicAdd(s_tally + PE_T_N_ETA_ABOVE, (unsigned long long)na);
 }
 
 __device__ __forceinline__ void pair_clear(Pair& Q) {
