@@ -8,9 +8,12 @@
 //  k_step_persistent grid-stride over tiles of one or many runs, K steps per
 //                    launch with the particle state in registers, the rate
 //                    tables (h(eta), sigma_Z(gamma)) staged in shared memory,
-//                    photon append by warp-aggregated atomics, histograms and
-//                    tallies accumulated in shared memory and flushed once per
-//                    run per CTA.  Instantiated for float (fast path) and double.
+//                    photons appended inside the emission branch (one atomic per
+//                    group of lanes there together), histograms and tallies
+//                    accumulated in shared memory and flushed once per run per
+//                    CTA.  Instantiated for double, and for float where the
+//                    paired kernels (pair_f32.cuh) do not apply: the reflected
+//                    wave and constant fields.
 //
 // Step order per particle (Sec. 2.2): fields at (x^n, t^n) -> Boris push ->
 // eta -> NCS optical depth (emission at tau <= 0) -> brems test (Eq. 4) ->
@@ -565,8 +568,9 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 // current run's descriptor is copied to shared memory once per tile, so no step
 // reads an indexed kernel parameter.
 // Resident CTAs of 256 threads per SM the register budget is sized for.  FP32, measured (particle-steps/s):
-// the 2D focus 9.64e10 at 4 CTAs (64 registers), 9.57e10 at 5, 9.37e10 at 6, 9.40e10 at 8; the reflected
-// wave 4.17e10 at 4, 4.30e10 at 5, 4.09e10 at 6, 4.44e10 at 8 (32 registers).
+// the 2D focus (before it moved to the paired kernel) 9.64e10 at 4 CTAs (64 registers), 9.57e10 at 5,
+// 9.37e10 at 6, 9.40e10 at 8; the reflected wave 4.17e10 at 4, 4.30e10 at 5, 4.09e10 at 6, 4.44e10 at 8
+// (32 registers; 4.78e10 with its NCS branch inlined).
 #ifndef PE_MIN_CTAS
 #define PE_MIN_CTAS 4
 #endif
