@@ -539,6 +539,7 @@ def gauss2d(pe, stream, flush):
     out = r.tally_out()
     ms = float(np.mean(times))
     res = {"value": out.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": c["n"],
+           "kernel": "k_step_pair (FP32, 2D focus, two electrons per thread)",
            "steps": c["steps"], "photons": int(out.tally[pe.T["N_PHOTONS"]]),
            "ncs_stored": int(out.tally[pe.T["N_NCS_STORED"]]), "brems_stored": int(out.tally[pe.T["N_BR_STORED"]])}
     r.close()
@@ -722,7 +723,7 @@ def reflected(pe, tables, cfg, stream, flush):
     res = {"value": t.live_particle_steps / (ms * 1e-3), "unit": UNIT, "ms_per_job": ms, "electrons": cfg["n"],
            "steps": cfg["steps"], "ncs_stored": int(t.tally[pe.T["N_NCS_STORED"]]),
            "ncs_below_cut": int(t.tally[pe.T["N_NCS_BELOW"]]), "photons": int(t.tally[pe.T["N_PHOTONS"]]),
-           "kernel": "k_step_persistent (FP32, reflected-wave field kind)",
+           "kernel": "k_step_pair (FP32, reflected-wave field kind, two electrons per thread)",
            "breit_wheeler": bw_of_photons(pe, r, t.photons_stored, stream, flush)}
     r.close()
     return res

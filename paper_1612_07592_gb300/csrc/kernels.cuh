@@ -12,8 +12,7 @@
 //                    group of lanes there together), histograms and tallies
 //                    accumulated in shared memory and flushed once per run per
 //                    CTA.  Instantiated for double, and for float where the
-//                    paired kernels (pair_f32.cuh) do not apply: the reflected
-//                    wave and constant fields.
+//                    paired kernels (pair_f32.cuh) do not apply: constant fields.
 //
 // Step order per particle (Sec. 2.2): fields at (x^n, t^n) -> Boris push ->
 // eta -> NCS optical depth (emission at tau <= 0) -> brems test (Eq. 4) ->
@@ -170,13 +169,11 @@ __device__ __forceinline__ void hist_add(unsigned long long* hist, unsigned long
 // code stays out of the step loop's instruction stream.  They take the particle
 // by value and return it (no address of the loop-carried state escapes, so it
 // stays in registers).  The paired FP32 kernels inline both branches instead
-// (ncs_emit_body, brems_emit_body), and so do the FP32 one-electron kernels of the
-// reflected wave for the NCS branch: with 72 (32) registers a thread, a call's
-// register convention cost spills on the common path (measured 9 % of the headline
-// job, 5 % of the reflected-wave job).  The kernels that inline a body refresh
-// 1/gamma after it by the correctly rounded reciprocal, so every instance rounds
-// alike (single run or batch, resident or streaming: compared bit for bit in the
-// tests).
+// (ncs_emit_body, brems_emit_body): with 72 registers a thread, a call's register
+// convention cost spills on the common path (measured 9 % of the headline job).  Their
+// translation unit rounds every operation as written, so all of their instances
+// (single run or batch, resident or streaming: compared bit for bit in the tests)
+// round the inlined branches alike.
 template <typename R>
 struct Emission {
     Particle<R> P;     // particle after the branch
@@ -378,11 +375,8 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         if constexpr (sizeof(R) == 4) return v * inv_g;
         else return v / gamma;
     };
-    // the reflected-wave FP32 kernels inline the NCS branch (see the emission branches above)
-    constexpr bool kInlineNcs = sizeof(R) == 4 && (G == FK_REFL_LP || G == FK_REFL_CP);
     auto refresh = [&]() {
-        if constexpr (kInlineNcs) inv_g = __frcp_rn(gamma);
-        else if constexpr (sizeof(R) == 4) inv_g = 1.0f / gamma;
+        if constexpr (sizeof(R) == 4) inv_g = 1.0f / gamma;
     };
     const R xn = P.x, yn = P.y;
 
@@ -394,10 +388,7 @@ __device__ __forceinline__ void step_one(const TablesDev& t, const RunDevT<R>& r
         // dN/dt dt = sqrt(3) alpha/(2 pi) (m c^2/hbar) (eta/gamma) h(eta) dt
         tau_sub(P, c.ncs_coef * over_gamma(eta) * h);
         if (tau_crossed(P)) {
-            if constexpr (kInlineNcs)
-                take(ncs_emit_body<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
-            else
-                take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
+            take(ncs_emit<R>(t, r, id, n, P, gamma, eta, xn, yn, hist, tally), P, gamma, st, ph);
             if (st) append_now(r, ph);
             refresh();
         }
@@ -567,23 +558,13 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 // straight from the kernel parameters (constant-bank operands); otherwise the
 // current run's descriptor is copied to shared memory once per tile, so no step
 // reads an indexed kernel parameter.
-// Resident CTAs of 256 threads per SM the register budget is sized for.  FP32, measured (particle-steps/s):
-// the 2D focus (before it moved to the paired kernel) 9.64e10 at 4 CTAs (64 registers), 9.57e10 at 5,
-// 9.37e10 at 6, 9.40e10 at 8; the reflected wave 4.17e10 at 4, 4.30e10 at 5, 4.09e10 at 6, 4.44e10 at 8
-// (32 registers; 4.78e10 with its NCS branch inlined).
+// Resident CTAs of 256 threads per SM the register budget is sized for (64 registers): the FP64
+// kernels, and the FP32 runs of constant fields (the prescribed-field kinds take the paired kernel)
 #ifndef PE_MIN_CTAS
 #define PE_MIN_CTAS 4
 #endif
-#ifndef PE_MIN_CTAS_REFL
-#define PE_MIN_CTAS_REFL 8
-#endif
-template <typename R, int G>
-constexpr int persistent_min_ctas() {
-    return (sizeof(R) == 4 && (G == FK_REFL_LP || G == FK_REFL_CP)) ? PE_MIN_CTAS_REFL : PE_MIN_CTAS;
-}
 template <typename R, bool kSingle, int G, bool kCommon = false>
-__global__ void __launch_bounds__(256, persistent_min_ctas<R, G>()) k_step_persistent(TablesDev t, BatchDevT<R> b,
-                                                                                     int steps) {
+__global__ void __launch_bounds__(256, PE_MIN_CTAS) k_step_persistent(TablesDev t, BatchDevT<R> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<R> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);

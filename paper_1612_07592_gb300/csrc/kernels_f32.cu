@@ -1,6 +1,6 @@
-// kernels_f32.cu -- the FP32 launches: the paired kinds (1D plane wave, 2D focus) go to the
-// paired kernels (kernels_paired.cu); the others (reflected wave, constant fields) to the
-// one-electron persistent kernel instantiated here for float.
+// kernels_f32.cu -- the FP32 launches: the prescribed-field kinds (1D plane wave, its reflection,
+// 2D focus) go to the paired kernels (kernels_paired.cu); constant fields to the one-electron
+// persistent kernel instantiated here for float.
 #include "kernels.cuh"
 
 namespace pe {
@@ -25,13 +25,10 @@ static void launch_one(const TablesDev& t, const BatchDevT<float>& b, int steps,
         k_step_persistent<float, kSingle, G, false><<<grid, threads, smem, s>>>(t, b, steps);
 }
 
+// the kinds of the one-electron FP32 kernel: constant fields
 template <typename F>
-static void with_one_electron_kind(int fk, F&& f) {
-    switch (fk) {
-        case FK_REFL_LP: f(std::integral_constant<int, FK_REFL_LP>{}); break;
-        case FK_REFL_CP: f(std::integral_constant<int, FK_REFL_CP>{}); break;
-        default: f(std::integral_constant<int, FK_CONST>{}); break;
-    }
+static void with_one_electron_kind(int, F&& f) {
+    f(std::integral_constant<int, FK_CONST>{});
 }
 
 void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,

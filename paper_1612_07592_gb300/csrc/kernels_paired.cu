@@ -1,5 +1,6 @@
 // kernels_paired.cu -- instantiations and dispatch of the paired FP32 kernels (two electrons
-// per thread: the 1D plane wave and the 2D focus, and the plane wave's one-step streaming form).
+// per thread: the 1D plane wave, its reflection, the 2D focus, and the plane wave's one-step
+// streaming form).
 // This translation unit is built without multiply-add contraction and with IEEE division and
 // square root: its kernels (single run, batch, streaming) inline the same emission branches, and
 // with every rounding written in the source they agree bit for bit (the approximate forms the
@@ -64,7 +65,9 @@ static void with_paired_kind(int fk, F&& f) {
         case FK_PLANE_LP: f(std::integral_constant<int, FK_PLANE_LP>{}); break;
         case FK_PLANE_CP: f(std::integral_constant<int, FK_PLANE_CP>{}); break;
         case FK_GAUSS_LP: f(std::integral_constant<int, FK_GAUSS_LP>{}); break;
-        default: f(std::integral_constant<int, FK_GAUSS_CP>{}); break;
+        case FK_GAUSS_CP: f(std::integral_constant<int, FK_GAUSS_CP>{}); break;
+        case FK_REFL_LP: f(std::integral_constant<int, FK_REFL_LP>{}); break;
+        default: f(std::integral_constant<int, FK_REFL_CP>{}); break;
     }
 }
 

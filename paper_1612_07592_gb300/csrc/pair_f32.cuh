@@ -159,8 +159,8 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
     Q.wait[k] = P.wait;
 }
 
-// one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_GAUSS_LP,
-// FK_GAUSS_CP: the 2D paraxial focus).  An inactive half of the pair (a removed electron, or an
+// one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_REFL_LP,
+// FK_REFL_CP: the plane wave and its mirror image; FK_GAUSS_LP, FK_GAUSS_CP: the 2D paraxial focus).  An inactive half of the pair (a removed electron, or an
 // empty slot past the end of the run) has x = NaN, so its fields, momenta, eta and optical depth
 // are NaN from its first step on, and the eta count, the optical depth's crossing and the target
 // test are false for it without reading the activity flags.  kCommon: the run has NCS on, direct brems and no
@@ -180,7 +180,10 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     float2 g, dg;
     envelope2(c, phi, g, dg);
     constexpr bool kPlane = G == FK_PLANE_LP || G == FK_PLANE_CP;
-    constexpr bool kCP = G == FK_PLANE_CP || G == FK_GAUSS_CP;
+    constexpr bool kRefl = G == FK_REFL_LP || G == FK_REFL_CP;
+    constexpr bool kOneD = kPlane || kRefl;             // no transverse position
+    constexpr bool kCP = G == FK_PLANE_CP || G == FK_GAUSS_CP || G == FK_REFL_CP;
+    float2 by = P2(0.0f), bz = P2(0.0f);                // B_y, B_z of the reflected kinds
     const float2 ma0 = P2(-c.a0);
     float2 ey, ez = P2(0.0f), ex = P2(0.0f), bx = P2(0.0f);
     if constexpr (kPlane) {
@@ -216,6 +219,53 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         Q.u0 = add2(um0, mul2(p1, s2));
         Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
     }
+    } else if constexpr (kRefl) {
+        // incident pulse (B = x^ x E) plus the mirror image -r e(psi) at the reflected phase
+        // t + x - 2 x_m, moving along -x (B = -x^ x E): E = (0, e_y + r_y, e_z + r_z),
+        // B = (0, r_z - e_z, e_y - r_y)
+        float2 st, ct;
+        sincos2(phi, st, ct);
+        const float2 eiy = mul2(ma0, fma2(dg, st, mul2(g, ct)));
+        const float2 eiz = kCP ? mul2(P2(c.a0), sub2(mul2(dg, ct), mul2(g, st))) : P2(0.0f);
+        const float2 pr = add2(add2(fma2(nf2, P2(c.dt_hi), P2(-c.xm2_hi)), Q.x),
+                               fma2(nf2, P2(c.dt_lo), sub2(Q.x_lo, P2(c.xm2_lo))));
+        float2 gr, dgr, sr, cr;
+        envelope2(c, pr, gr, dgr);
+        sincos2(pr, sr, cr);
+        const float2 ry = mul2(P2(c.refl_r * c.a0), fma2(dgr, sr, mul2(gr, cr)));    // -r (-a0 (...))
+        ey = add2(eiy, ry);
+        bz = sub2(eiy, ry);
+        if constexpr (kCP) {
+            const float2 rz = mul2(P2(-c.refl_r * c.a0), sub2(mul2(dgr, cr), mul2(gr, sr)));
+            ez = add2(eiz, rz);
+            by = sub2(rz, eiz);
+        }
+        // Boris push with E = (0, E_y, E_z), B = (0, B_y, B_z)
+        const float2 mh = P2(-0.5f * c.dt);
+        const float2 um0 = Q.u0;
+        const float2 um1 = fma2(mh, ey, Q.u1);
+        const float2 um2 = kCP ? fma2(mh, ez, Q.u2) : Q.u2;
+        const float2 ig = rsqrt2(fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f)))));
+        const float2 mhig = mul2(mh, ig);
+        const float2 t2 = mul2(bz, mhig);                              // -h B_z / gamma
+        if constexpr (kCP) {
+            const float2 t1 = mul2(by, mhig);                          // -h B_y / gamma
+            const float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, fma2(t1, t1, P2(1.0f)))));
+            const float2 s1 = mul2(f, t1), s2 = mul2(f, t2);
+            const float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
+            const float2 p1 = sub2(um1, mul2(um0, t2));
+            const float2 p2 = fma2(um0, t1, um2);
+            Q.u0 = add2(um0, sub2(mul2(p1, s2), mul2(p2, s1)));
+            Q.u1 = fma2(mh, ey, sub2(um1, mul2(p0, s2)));
+            Q.u2 = fma2(mh, ez, fma2(p0, s1, um2));
+        } else {
+            const float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, P2(1.0f))));
+            const float2 s2 = mul2(f, t2);
+            const float2 p0 = fma2(um1, t2, um0);
+            const float2 p1 = sub2(um1, mul2(um0, t2));
+            Q.u0 = fma2(p1, s2, um0);
+            Q.u1 = fma2(mh, ey, sub2(um1, mul2(p0, s2)));
+        }
     } else {
         // 2D paraxial focus (fields() in physics.cuh), amplitude and Gouy phase by gouy2: with
         // S = sqrt(w0 / w) e^{-y^2 / w^2} and theta = phi - y^2 / (2 R_c) + atan(a) / 2,
@@ -286,6 +336,18 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         if constexpr (kPlane) {
             float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
             eta = mul2(mul2(ngm, Emag), P2(-c.inv_ES));
+        } else if constexpr (kRefl) {
+            // eta = |V^2 + 2 V_x (u.E)|^{1/2} / E_S with V = (gamma - u_x) E + u x d, d = B - x^ x E =
+            // (0, B_y + E_z, B_z - E_y); nV1, nV2 = -V_y, -V_z
+            const float2 d2 = sub2(bz, ey);
+            const float2 d1 = kCP ? add2(by, ez) : P2(0.0f);
+            const float2 V0 = kCP ? sub2(mul2(Q.u1, d2), mul2(Q.u2, d1)) : mul2(Q.u1, d2);
+            const float2 nV1 = fma2(ngm, ey, mul2(Q.u0, d2));
+            const float2 nV2 = kCP ? sub2(mul2(ngm, ez), mul2(Q.u0, d1)) : P2(0.0f);
+            const float2 uE = kCP ? fma2(Q.u2, ez, mul2(Q.u1, ey)) : mul2(Q.u1, ey);
+            const float2 qv = fma2(mul2(P2(2.0f), V0), uE, fma2(nV2, nV2, fma2(nV1, nV1, mul2(V0, V0))));
+            const float2 rq = sqrt2(make_float2(fmaxf(qv.x, 0.0f), fmaxf(qv.y, 0.0f)));
+            eta = mul2(rq, P2(c.inv_ES));
         } else {
             // eta = |V^2 + 2 V_x (u.E)|^{1/2} / E_S with V = (gamma - u_x) E + u x (B - x^ x E): here
             // B_y + E_z = B_z - E_y = 0, so u x (...) = (0, u_z B_x, -u_y B_x); nV = -V except in y
@@ -323,7 +385,27 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         Q.tau = s;
         Q.tau_lo = add2(Q.tau_lo, e);
         float2 tsum = add2(Q.tau, Q.tau_lo);
-        if (tsum.x <= 0.0f || tsum.y <= 0.0f) {         // one test of the pair on the common path
+        if (kRefl && (tsum.x <= 0.0f || tsum.y <= 0.0f)) {
+            // frequent emissions (about 4 % of the particle-steps in the reflected pulse): the crossings
+            // of a lane go one at a time through one inlined branch, so lanes whose crossing is in
+            // different halves of their pairs take it together
+            unsigned m = (unsigned)(tsum.x <= 0.0f) | ((unsigned)(tsum.y <= 0.0f) << 1);
+            while (m) {
+                const int k = (m & 1u) ? 0 : 1;
+                m &= m - 1u;
+                Particle<float> P = unpack(Q, k);
+                float gk = k ? gam[1] : gam[0];
+                bool st;
+                Photon ph;
+                take(ncs_emit_body<float>(t, r, k ? id[1] : id[0], n, P, gk, comp(eta, k), comp(xn, k), 0.0f, hist,
+                                          tally),
+                     P, gk, st, ph);
+                if (st) append_now(r, ph);
+                repack(Q, k, P);
+                set_comp(inv_g, k, __frcp_rn(gk));
+                if (k) gam[1] = gk; else gam[0] = gk;
+            }
+        } else if (tsum.x <= 0.0f || tsum.y <= 0.0f) {  // one test of the pair on the common path
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (comp(tsum, k) <= 0.0f) {
@@ -354,7 +436,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
                     Particle<float> P = unpack(Q, k);
                     bool st;
                     Photon ph;
-                    const bool in_slab = x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh);
+                    const bool in_slab = x >= c.x0 && x <= c.x1 && (kOneD || fabsf(comp(yn, k)) <= c.yh);
                     take(brems_candidate<float>(t, r, sig_tab, id[k], n, P, gam[k], in_slab, x, comp(yn, k), hist,
                                                 tally),
                          P, gam[k], st, ph);
@@ -373,7 +455,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float x = comp(xn, k);
-                in[k] = x >= c.x0 && x <= c.x1 && (kPlane || fabsf(comp(yn, k)) <= c.yh) &&
+                in[k] = x >= c.x0 && x <= c.x1 && (kOneD || fabsf(comp(yn, k)) <= c.yh) &&
                         gam[k] > 1.0f + tc.photon_min;
             }
             if (in[0] || in[1]) {
@@ -423,7 +505,7 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     two_sum2(Q.x, d, s, e);
     Q.x = s;
     Q.x_lo = add2(Q.x_lo, e);
-    if constexpr (!kPlane) {                            // y^{n+1} = y^n + dt u_y / gamma, compensated
+    if constexpr (!kOneD) {                             // y^{n+1} = y^n + dt u_y / gamma, compensated
         two_sum2(Q.y, mul2(mul2(dt, Q.u1), inv_g), s, e);
         Q.y = s;
         Q.y_lo = add2(Q.y_lo, e);
@@ -492,7 +574,7 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
     pair_clear(Q);
     if (i0 < r.n) load_one(r, i0, Q, 0, s_tally);
     if (i1 < r.n) load_one(r, i1, Q, 1, s_tally);
-    if constexpr (G == FK_PLANE_LP || G == FK_PLANE_CP) Q.y = Q.y_lo = P2(0.0f);   // 1D: y is not state
+    if constexpr (G != FK_GAUSS_LP && G != FK_GAUSS_CP) Q.y = Q.y_lo = P2(0.0f);   // 1D: y is not state
     const bool live0 = i0 < r.n, live1 = i1 < r.n;
     pair_loop<G, kCommon>(t, r, s_h, sig_z, i0, i1, Q, steps, s_hist, s_tally);
     if (live0 && Q.act[0]) store_particle<float>(r, i0, unpack(Q, 0));
@@ -513,8 +595,17 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 #ifndef PE_PAIR_MIN_CTAS_2D
 #define PE_PAIR_MIN_CTAS_2D 5
 #endif
+// The reflected wave (1e6 electrons x 4000 steps of the a0 = 270 job with the mirror at the slab
+// rear): 6 CTAs 4.97e10, 7 5.02e10, 8 4.63e10 (one electron per thread at 8 CTAs of 256 threads:
+// 4.78e10).
+#ifndef PE_PAIR_MIN_CTAS_REFL
+#define PE_PAIR_MIN_CTAS_REFL 7
+#endif
 template <int G>
-constexpr int pair_min_ctas() { return (G == FK_GAUSS_LP || G == FK_GAUSS_CP) ? PE_PAIR_MIN_CTAS_2D : PE_PAIR_MIN_CTAS; }
+constexpr int pair_min_ctas() {
+    return (G == FK_GAUSS_LP || G == FK_GAUSS_CP) ? PE_PAIR_MIN_CTAS_2D
+           : (G == FK_REFL_LP || G == FK_REFL_CP) ? PE_PAIR_MIN_CTAS_REFL : PE_PAIR_MIN_CTAS;
+}
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
 template <bool kSingle, int G, bool kCommon>
 __global__ void __launch_bounds__(128, pair_min_ctas<G>()) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
