@@ -594,7 +594,7 @@ def bunch_methods(pe, stream, flush, n=1_000_000, dt_over_T=1.0):
         r.close()
     pe.pe_destroy_tables(tables)
     out.update({"unit": UNIT, "electrons": n, "steps": c["steps"], "speedup_null": out["null"]["value"] /
-                out["direct"]["value"], "kernel": "k_step_persistent (FP32, constant fields)"})
+                out["direct"]["value"], "kernel": "k_step_pair (FP32, constant fields, two electrons per thread)"})
     return out
 
 

@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe.so")
-SOURCES = ["api.cu", "kernels.cu", "kernels_f32.cu", "kernels_paired.cu", "kernels_f64.cu", "kernels_pic.cu",
-           "kernels_pair.cu", "kernels_bw.cu", "kernels_diag.cu", "tables.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "kernels_paired.cu", "kernels_f64.cu", "kernels_pic.cu", "kernels_pair.cu",
+           "kernels_bw.cu", "kernels_diag.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # single-precision division and square root at 2-ulp accuracy in the kernels (the FP64

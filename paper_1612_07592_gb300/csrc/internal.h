@@ -203,13 +203,6 @@ void launch_step_persistent_f64(const TablesDev& t, const BatchDevT<double>& b, 
                                 cudaStream_t s);
 int persistent_smem_bytes(const TablesDev& t, int precision);
 int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch);
-// the paired FP32 kernels (kernels_paired.cu): the 1D plane-wave, reflected-wave and 2D focus kinds
-inline bool paired_kind_f32(int fk) { return fk <= 3 || fk == 5 || fk == 6; }   // FK_PLANE_*, FK_GAUSS_*, FK_REFL_*
-void launch_step_paired_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
-                            cudaStream_t s);
-const void* paired_kernel_f32(const BatchDevT<float>& b, int steps, int base_smem, int block, int* threads,
-                              int* smem_out);
-int default_ctas_per_sm_paired_f32(int fk, int block, int smem, int steps_per_launch);
 // every run of the launch has the paper's setup: NCS on, direct brems, no absorbing box (the FP32
 // kernels then take these flags as compile-time constants)
 inline bool common_flags_f32(const BatchDevT<float>& b) {

@@ -1,5 +1,5 @@
 // kernels.cu -- the init kernel, the diagnostics kernels and their launchers.  The
-// step kernels are instantiated per precision in kernels_f32.cu and kernels_f64.cu.
+// step kernels are instantiated per precision in kernels_paired.cu (FP32) and kernels_f64.cu.
 #include <algorithm>
 #include <cmath>
 

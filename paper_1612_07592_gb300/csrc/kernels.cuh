@@ -11,8 +11,9 @@
 //                    photons appended inside the emission branch (one atomic per
 //                    group of lanes there together), histograms and tallies
 //                    accumulated in shared memory and flushed once per run per
-//                    CTA.  Instantiated for double, and for float where the
-//                    paired kernels (pair_f32.cuh) do not apply: constant fields.
+//                    CTA.  Instantiated for double; the FP32 step runs on the
+//                    paired kernels (pair_f32.cuh), and the FP32 PIC kernel
+//                    uses step_one below.
 //
 // Step order per particle (Sec. 2.2): fields at (x^n, t^n) -> Boris push ->
 // eta -> NCS optical depth (emission at tau <= 0) -> brems test (Eq. 4) ->
@@ -558,8 +559,8 @@ __device__ __forceinline__ void tile_steps(const TablesDev& t, const RunDevT<R>&
 // straight from the kernel parameters (constant-bank operands); otherwise the
 // current run's descriptor is copied to shared memory once per tile, so no step
 // reads an indexed kernel parameter.
-// Resident CTAs of 256 threads per SM the register budget is sized for (64 registers): the FP64
-// kernels, and the FP32 runs of constant fields (the prescribed-field kinds take the paired kernel)
+// Resident CTAs of 256 threads per SM the register budget is sized for (64 registers; the FP64
+// persistent kernels)
 #ifndef PE_MIN_CTAS
 #define PE_MIN_CTAS 4
 #endif

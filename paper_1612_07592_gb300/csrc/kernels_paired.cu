@@ -1,6 +1,6 @@
-// kernels_paired.cu -- instantiations and dispatch of the paired FP32 kernels (two electrons
-// per thread: the 1D plane wave, its reflection, the 2D focus, and the plane wave's one-step
-// streaming form).
+// kernels_paired.cu -- the FP32 step: instantiations and dispatch of the paired kernels (two
+// electrons per thread) for every prescribed-field kind (the 1D plane wave, its reflection, the 2D
+// focus, constant fields), and the plane wave's one-step streaming form.
 // This translation unit is built without multiply-add contraction and with IEEE division and
 // square root: its kernels (single run, batch, streaming) inline the same emission branches, and
 // with every rounding written in the source they agree bit for bit (the approximate forms the
@@ -67,12 +67,13 @@ static void with_paired_kind(int fk, F&& f) {
         case FK_GAUSS_LP: f(std::integral_constant<int, FK_GAUSS_LP>{}); break;
         case FK_GAUSS_CP: f(std::integral_constant<int, FK_GAUSS_CP>{}); break;
         case FK_REFL_LP: f(std::integral_constant<int, FK_REFL_LP>{}); break;
-        default: f(std::integral_constant<int, FK_REFL_CP>{}); break;
+        case FK_REFL_CP: f(std::integral_constant<int, FK_REFL_CP>{}); break;
+        default: f(std::integral_constant<int, FK_CONST>{}); break;
     }
 }
 
-void launch_step_paired_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
-                            cudaStream_t s) {
+void launch_step_persistent_f32(const TablesDev& t, const BatchDevT<float>& b, int steps, int grid, int block,
+                                cudaStream_t s) {
     const int smem = persistent_smem_bytes(t, PE_F32);
     with_paired_kind(b.runs[0].fk, [&](auto g) {
         if (b.n_runs == 1) launch_one<true, decltype(g)::value>(t, b, steps, grid, block, s, smem);
@@ -80,8 +81,10 @@ void launch_step_paired_f32(const TablesDev& t, const BatchDevT<float>& b, int s
     });
 }
 
-const void* paired_kernel_f32(const BatchDevT<float>& b, int steps, int base_smem, int block, int* threads,
-                              int* smem_out) {
+// the kernel a launch of these runs uses, its threads per CTA and dynamic shared memory
+// (for graph nodes); sets the shared-memory attribute
+const void* persistent_kernel_f32(const BatchDevT<float>& b, int steps, int base_smem, int block, int* threads,
+                                  int* smem_out) {
     const void* f = nullptr;
     int th = block, smem = base_smem;
     with_paired_kind(b.runs[0].fk, [&](auto g) {
@@ -98,7 +101,7 @@ const void* paired_kernel_f32(const BatchDevT<float>& b, int steps, int base_sme
 // cost with their emission histories, and a CTA per one or two tiles lets the block scheduler balance
 // them: measured +6 % over one wave, +2.5 % over two, on 1e6 electrons); one wave for the streaming
 // form (each CTA streams many tiles of equal cost).
-int default_ctas_per_sm_paired_f32(int fk, int block, int smem, int steps_per_launch) {
+int default_ctas_per_sm_f32(int fk, int block, int smem, int steps_per_launch) {
     int occ = 0;
     cudaError_t e;
     if (plane_kind(fk) && steps_per_launch <= kStreamMaxSteps && block == kStreamTile) {

@@ -160,7 +160,8 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
 }
 
 // one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_REFL_LP,
-// FK_REFL_CP: the plane wave and its mirror image; FK_GAUSS_LP, FK_GAUSS_CP: the 2D paraxial focus).  An inactive half of the pair (a removed electron, or an
+// FK_REFL_CP: the plane wave and its mirror image; FK_GAUSS_LP, FK_GAUSS_CP: the 2D paraxial focus;
+// FK_CONST: constant fields).  An inactive half of the pair (a removed electron, or an
 // empty slot past the end of the run) has x = NaN, so its fields, momenta, eta and optical depth
 // are NaN from its first step on, and the eta count, the optical depth's crossing and the target
 // test are false for it without reading the activity flags.  kCommon: the run has NCS on, direct brems and no
@@ -181,7 +182,8 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
     envelope2(c, phi, g, dg);
     constexpr bool kPlane = G == FK_PLANE_LP || G == FK_PLANE_CP;
     constexpr bool kRefl = G == FK_REFL_LP || G == FK_REFL_CP;
-    constexpr bool kOneD = kPlane || kRefl;             // no transverse position
+    constexpr bool kConst = G == FK_CONST;
+    constexpr bool kOneD = kPlane || kRefl || kConst;   // no transverse position
     constexpr bool kCP = G == FK_PLANE_CP || G == FK_GAUSS_CP || G == FK_REFL_CP;
     float2 by = P2(0.0f), bz = P2(0.0f);                // B_y, B_z of the reflected kinds
     const float2 ma0 = P2(-c.a0);
@@ -219,6 +221,27 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         Q.u0 = add2(um0, mul2(p1, s2));
         Q.u1 = add2(sub2(um1, mul2(p0, s2)), mhey);
     }
+    } else if constexpr (kConst) {
+        // constant fields (the Sec. 2.2 bunch: fields off), the general Boris push
+        ex = P2(c.E_const[0]);
+        ey = P2(c.E_const[1]);
+        ez = P2(c.E_const[2]);
+        bx = P2(c.B_const[0]);
+        by = P2(c.B_const[1]);
+        bz = P2(c.B_const[2]);
+        const float2 mh = P2(-0.5f * c.dt);
+        const float2 um0 = fma2(mh, ex, Q.u0), um1 = fma2(mh, ey, Q.u1), um2 = fma2(mh, ez, Q.u2);
+        const float2 ig = rsqrt2(fma2(um2, um2, fma2(um1, um1, fma2(um0, um0, P2(1.0f)))));
+        const float2 mhig = mul2(mh, ig);
+        const float2 t0 = mul2(bx, mhig), t1 = mul2(by, mhig), t2 = mul2(bz, mhig);   // -h B / gamma
+        const float2 f = mul2(P2(-2.0f), nrcp2(fma2(t2, t2, fma2(t1, t1, fma2(t0, t0, P2(1.0f))))));
+        const float2 s0_ = mul2(f, t0), s1 = mul2(f, t1), s2 = mul2(f, t2);
+        const float2 p0 = add2(um0, sub2(mul2(um1, t2), mul2(um2, t1)));
+        const float2 p1 = add2(um1, sub2(mul2(um2, t0), mul2(um0, t2)));
+        const float2 p2 = add2(um2, sub2(mul2(um0, t1), mul2(um1, t0)));
+        Q.u0 = fma2(mh, ex, add2(um0, sub2(mul2(p1, s2), mul2(p2, s1))));
+        Q.u1 = fma2(mh, ey, add2(um1, sub2(mul2(p2, s0_), mul2(p0, s2))));
+        Q.u2 = fma2(mh, ez, add2(um2, sub2(mul2(p0, s1), mul2(p1, s0_))));
     } else if constexpr (kRefl) {
         // incident pulse (B = x^ x E) plus the mirror image -r e(psi) at the reflected phase
         // t + x - 2 x_m, moving along -x (B = -x^ x E): E = (0, e_y + r_y, e_z + r_z),
@@ -336,6 +359,17 @@ __device__ __forceinline__ void step_pair(const TablesDev& t, const RunDevT<floa
         if constexpr (kPlane) {
             float2 Emag = (G == FK_PLANE_CP) ? sqrt2(fma2(ez, ez, mul2(ey, ey))) : make_float2(fabsf(ey.x), fabsf(ey.y));
             eta = mul2(mul2(ngm, Emag), P2(-c.inv_ES));
+        } else if constexpr (kConst) {
+            // eta = |V^2 + 2 V_x (u.E)|^{1/2} / E_S with V = (gamma - u_x) E + u x d, d = B - x^ x E =
+            // (B_x, B_y + E_z, B_z - E_y); nV = -V
+            const float2 d1 = add2(by, ez), d2 = sub2(bz, ey);
+            const float2 nV0 = sub2(mul2(ngm, ex), sub2(mul2(Q.u1, d2), mul2(Q.u2, d1)));
+            const float2 nV1 = sub2(mul2(ngm, ey), sub2(mul2(Q.u2, bx), mul2(Q.u0, d2)));
+            const float2 nV2 = sub2(mul2(ngm, ez), sub2(mul2(Q.u0, d1), mul2(Q.u1, bx)));
+            const float2 uE = fma2(Q.u2, ez, fma2(Q.u1, ey, mul2(Q.u0, ex)));
+            const float2 qv = sub2(fma2(nV2, nV2, fma2(nV1, nV1, mul2(nV0, nV0))), mul2(mul2(P2(2.0f), nV0), uE));
+            const float2 rq = sqrt2(make_float2(fmaxf(qv.x, 0.0f), fmaxf(qv.y, 0.0f)));
+            eta = mul2(rq, P2(c.inv_ES));
         } else if constexpr (kRefl) {
             // eta = |V^2 + 2 V_x (u.E)|^{1/2} / E_S with V = (gamma - u_x) E + u x d, d = B - x^ x E =
             // (0, B_y + E_z, B_z - E_y); nV1, nV2 = -V_y, -V_z
