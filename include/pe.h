@@ -203,15 +203,15 @@ typedef struct {
     void* grid;
 } pe_buffers;
 
-/* Launch shape of the persistent FP32 kernel (the autotuner's knobs).
- * block: electrons per tile and threads per CTA (64, 128, 192 or 256; the FP32
- * plane-wave kernel covers a tile with block/2 threads, two electrons each);
- * ctas_per_sm: CTAs per SM
- * in the grid; steps_per_launch: steps done per launch with the state held in
- * registers (1 = state round-trips memory every step).  Zeros pick defaults:
- * 256 electrons per tile; three times the CTAs that fit on an SM for the FP32
- * plane-wave kernel, twice for the other kernels; min(steps, 4096) steps per
- * launch.                                                                      */
+/* Launch shape of the persistent kernels (the autotuner's knobs).
+ * block: electrons per tile (64, 128, 192 or 256); the FP32 kernel covers a
+ * tile with block/2 threads, two electrons each, the FP64 kernel with block
+ * threads; ctas_per_sm: CTAs per SM in the grid; steps_per_launch: steps done
+ * per launch with the state held in registers (1 = state round-trips memory
+ * every step).  Zeros pick defaults: 256 electrons per tile; three times the
+ * CTAs that fit on an SM for the FP32 kernel (once for the one-step form of a
+ * single plane-wave run, launches of at most 4 steps), twice for the FP64
+ * kernel; min(steps, 4096) steps per launch.                                   */
 typedef struct {
     int block, ctas_per_sm, steps_per_launch;
 } pe_launch_config;
@@ -275,8 +275,8 @@ pe_status pe_resume_particles(const pe_tables* tables, const pe_run_params* para
 /* Advance runs by n_steps.  n_runs == 1: PE_F64 runs use the plain kernel
  * (one launch per step); PE_F32 runs use the persistent kernel.  n_runs > 1
  * (<= PE_MAX_BATCH): all runs must be PE_F32 and share the first run's
- * stream; they advance together in one persistent launch per
- * steps_per_launch steps.  Asynchronous.  cfg may be NULL.                  */
+ * stream; they advance together, one persistent launch per field kind present
+ * per steps_per_launch steps.  Asynchronous.  cfg may be NULL.             */
 pe_status pe_step(pe_run* const* runs, int n_runs, int64_t n_steps);
 pe_status pe_step_ex(pe_run* const* runs, int n_runs, int64_t n_steps, const pe_launch_config* cfg);
 
@@ -483,10 +483,10 @@ pe_status pe_pic_step_noalloc(const pe_tables* tables, const pe_run_params* para
  *        PE_MATH_SIN/_COS the carrier-phase sine and cosine of the paired FP32 step
  *                         (Cody-Waite reduction by 2 pi with a two-part constant,
  *                         then the hardware sine and cosine); _SIN1/_COS1 the same
- *                         in the one-electron FP32 step
+ *                         in the one-electron FP32 step (the 1D PIC)
  *        PE_MATH_BREMS_P  1 - e^-x as the paired step forms the probability of Eq. 4
  *                         (a four-term Taylor series below 2^-5, expm1f above);
- *                         _BREMS_P1 the same in the one-electron step
+ *                         _BREMS_P1 the same in the one-electron step (the 1D PIC)
  *        PE_MATH_CUDA_RCP, _SIN, _COS, _EXPM1: CUDA's __frcp_rn, sinf, cosf and
  *                         -expm1f(-x), for comparison
  *        PE_MATH_GOUY_C/_S  at a = (x - x_f) / z_R, the factors (1 + a^2)^(-1/4) cos(atan(a)/2)
