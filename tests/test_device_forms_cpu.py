@@ -1,0 +1,152 @@
+"""The FP32 step's exact integer and float forms, emulated in NumPy float32 and checked against
+exact integer and rational arithmetic (CPU only; the GPU runs the same forms, and tests/test_gpu_*
+compare their results with the FP64 oracle).
+
+- the row split of a table position by the mantissa of 1.5 * 2^23 (split_pos, floor_small):
+  position = row + weight exactly;
+- the Eq. 4 test of the FP32 path (below_threshold_f32): the 32-bit comparisons equal the
+  64-bit comparison u64 < floor(P 2^64) for the float P, exactly;
+- the 128-bit fixed-point tally of a float (fx_add_f32): hi 2^64 + lo = floor(v 2^64), exactly;
+- the half-angle form of the 2D focus's amplitude and Gouy phase (gouy2), in FP64.
+"""
+from fractions import Fraction
+import math
+
+import numpy as np
+
+F = np.float32
+M = F(1.5 * 2 ** 23)                       # 0x4B400000 as a float
+
+
+def bits(x):
+    return int(np.array([x], dtype=np.float32).view(np.int32)[0])
+
+
+def from_bits(i):
+    return np.array([i], dtype=np.int32).view(np.float32)[0]
+
+
+def split_pos(tp):
+    """i, w with tp = i + w: the nearest integer to tp - 1/2 from the mantissa of 1.5 * 2^23."""
+    t = F(F(tp - F(0.5)) + M)
+    i = bits(t) - 0x4B400000
+    w = F(tp - F(t - M))
+    return i, w
+
+
+def int_to_float_small(i):
+    return F(from_bits(0x4B400000 + i) - M)
+
+
+def floor_small(v):
+    t = F(F(v - F(0.5)) + M)
+    i = bits(t) - 0x4B400000
+    if int_to_float_small(i + 1) <= v:
+        i += 1
+    return i
+
+
+def below_threshold_float(P, lo, hi):
+    """The float-P version for P 2^32 >= 2^22 (physics.cuh)."""
+    p32 = F(P * F(2.0 ** 32))
+    fth = F(math.floor(p32))
+    th = int(fth)
+    if hi != th:
+        return hi < th
+    tl = int(math.floor(F(F(p32 - fth) * F(2.0 ** 32))))
+    return lo < tl
+
+
+def below_threshold_f32(P, lo, hi):
+    if not P > 0:
+        return False
+    if P >= 1:
+        return True
+    p32 = F(P * F(2.0 ** 32))
+    if p32 >= F(2.0 ** 22):
+        return below_threshold_float(P, lo, hi)
+    th = floor_small(p32)
+    if hi != th:
+        return hi < th
+    frac = F(F(p32 - int_to_float_small(th)) * F(2.0 ** 32))
+    tl = int(frac)                          # truncation of a non-negative float
+    return lo < tl
+
+
+def fx_f32(v):
+    """(lo, hi) of the 128-bit fixed-point word that fx_add_f32 adds for v >= 0."""
+    b = bits(v) & 0xFFFFFFFF
+    e = b >> 23
+    m = (b & 0x7FFFFF) | (0x800000 if e else 0)
+    if e == 0:
+        e = 1
+    s = e - 86
+    if s >= 64:
+        lo, hi = 0, (m << (s - 64)) & (2 ** 64 - 1)
+    elif s > 0:
+        lo = (m << s) & (2 ** 64 - 1)
+        hi = (m >> (64 - s)) if s > 40 else 0
+    else:
+        lo, hi = (m >> (-s)) if s > -64 else 0, 0
+    return lo, hi
+
+
+def test_split_pos_is_exact():
+    rng = np.random.default_rng(11)
+    tps = np.concatenate([rng.uniform(0.0, 300.0, 20000), np.arange(0.0, 300.0, 0.25),
+                          rng.uniform(0.0, 2.0 ** 21, 2000)]).astype(np.float32)
+    for tp in tps:
+        i, w = split_pos(tp)
+        assert Fraction(float(i)) + Fraction(float(w)) == Fraction(float(tp))
+        assert 0.0 <= w <= 1.0
+        assert i == math.floor(tp) or (w == 1.0 and i == math.floor(tp) - 1)
+
+
+def test_floor_small_is_exact():
+    rng = np.random.default_rng(12)
+    vs = np.concatenate([rng.uniform(0.0, 2.0 ** 22 - 1, 20000), np.arange(0.0, 64.0, 0.5),
+                         np.nextafter(np.arange(1.0, 64.0, dtype=np.float32), np.float32(0))]).astype(np.float32)
+    for v in vs:
+        assert floor_small(v) == math.floor(v)
+
+
+def test_brems_threshold_equals_64_bit_comparison():
+    rng = np.random.default_rng(13)
+    Ps = np.concatenate([np.exp(rng.uniform(math.log(1e-12), math.log(0.999), 3000)),
+                         np.array([2.0 ** -30, 2.0 ** -10, 0.5, 0.75])]).astype(np.float32)
+    n_eq = 0
+    for P in Ps:
+        T = int(Fraction(float(P)) * 2 ** 64)            # floor(P 2^64), exact
+        th, tl = T >> 32, T & 0xFFFFFFFF
+        cases = [(int(x) & 0xFFFFFFFF, int(y) & 0xFFFFFFFF) for x, y in rng.integers(0, 2 ** 32, (4, 2))]
+        cases += [(tl, th), (max(tl - 1, 0), th), ((tl + 1) & 0xFFFFFFFF, th), (0, th), (0xFFFFFFFF, th),
+                  (tl, max(th - 1, 0)), (tl, th + 1)]
+        for lo, hi in cases:
+            assert below_threshold_f32(P, lo, hi) == ((hi << 32 | lo) < T), (P, lo, hi)
+            n_eq += hi == th
+    assert n_eq > 3 * len(Ps)                          # the low-word branch is exercised
+
+
+def test_fixed_point_tally_is_exact():
+    rng = np.random.default_rng(14)
+    vs = np.concatenate([np.exp(rng.uniform(math.log(1e-30), math.log(1e9), 20000)),
+                         np.array([1e-45, 1e-38, 1.0, 0.5, 3.0, 2.0 ** 40, 2.0 ** 62])]).astype(np.float32)
+    for v in vs:
+        if not v > 0:
+            continue
+        lo, hi = fx_f32(v)
+        assert hi * 2 ** 64 + lo == math.floor(Fraction(float(v)) * 2 ** 64), v
+
+
+def test_gouy_half_angle_form():
+    """(1 + i a)^{1/2} / |1 + i a| = (1 + a^2)^{-1/4} e^{i atan(a)/2}: with n = sqrt(1 + a^2),
+    R = sqrt((n + 1)/2) and I = a / (2R) (the half-angle formulas) satisfy (R + iI)^2 = 1 + i a, and
+    R/n, I/n are the cosine and sine parts of the direct form (FP64)."""
+    for a in (0.0, 1e-6, 0.1, -3.0 / 7.0, 1.0, 5.0, -40.0, 1e3):
+        n = math.sqrt(1.0 + a * a)
+        R = math.sqrt((n + 1.0) / 2.0)
+        I = a / (2.0 * R)
+        assert abs(R * R - I * I - 1.0) < 1e-12 * n and abs(2.0 * R * I - a) < 1e-12 * n
+        amp = (1.0 + a * a) ** -0.25
+        assert abs(R / n - amp * math.cos(0.5 * math.atan(a))) < 1e-14
+        assert abs(I / n - amp * math.sin(0.5 * math.atan(a))) < 1e-14
