@@ -146,8 +146,10 @@ __device__ __forceinline__ Particle<float> unpack(const Pair& Q, int k) {
     P.y = comp(Q.y, k); P.y_lo = comp(Q.y_lo, k);
     P.u[0] = comp(Q.u0, k); P.u[1] = comp(Q.u1, k); P.u[2] = comp(Q.u2, k);
     P.tau = comp(Q.tau, k); P.tau_lo = comp(Q.tau_lo, k);
-    P.ev_cnt = Q.ev_cnt[k]; P.ev_hash = Q.ev_hash[k];
-    P.wait = Q.wait[k];
+    // selects, not Q.ev_cnt[k]: an index unknown at compile time (the reflected wave's emission
+    // loop) would move the arrays to local memory
+    P.ev_cnt = k ? Q.ev_cnt[1] : Q.ev_cnt[0]; P.ev_hash = k ? Q.ev_hash[1] : Q.ev_hash[0];
+    P.wait = k ? Q.wait[1] : Q.wait[0];
     return P;
 }
 __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P) {
@@ -155,8 +157,8 @@ __device__ __forceinline__ void repack(Pair& Q, int k, const Particle<float>& P)
     set_comp(Q.y, k, P.y); set_comp(Q.y_lo, k, P.y_lo);
     set_comp(Q.u0, k, P.u[0]); set_comp(Q.u1, k, P.u[1]); set_comp(Q.u2, k, P.u[2]);
     set_comp(Q.tau, k, P.tau); set_comp(Q.tau_lo, k, P.tau_lo);
-    Q.ev_cnt[k] = P.ev_cnt; Q.ev_hash[k] = P.ev_hash;
-    Q.wait[k] = P.wait;
+    if (k) { Q.ev_cnt[1] = P.ev_cnt; Q.ev_hash[1] = P.ev_hash; Q.wait[1] = P.wait; }
+    else { Q.ev_cnt[0] = P.ev_cnt; Q.ev_hash[0] = P.ev_hash; Q.wait[0] = P.wait; }
 }
 
 // one step of two electrons (G = FK_PLANE_LP, FK_PLANE_CP: the 1D plane wave; FK_REFL_LP,
@@ -631,18 +633,28 @@ __device__ __forceinline__ void tile_steps_pair(const TablesDev& t, const RunDev
 #endif
 // The reflected wave (1e6 electrons x 4000 steps of the a0 = 270 job with the mirror at the slab
 // rear): 6 CTAs 4.97e10, 7 5.02e10, 8 4.63e10 (one electron per thread at 8 CTAs of 256 threads:
-// 4.78e10).
+// 4.78e10); 7 CTAs 5.50e10 once the emission loop's pair-half selects kept the per-electron words
+// out of local memory.
 #ifndef PE_PAIR_MIN_CTAS_REFL
 #define PE_PAIR_MIN_CTAS_REFL 7
 #endif
-template <int G>
+// The general instances (flags read at run time: the null-collision method, a process switched
+// off, the box boundary) carry more live state than the common ones, but more registers for them
+// measured slower on the 1 GeV Au bunch (1e6 electrons, fields off, dt = T; direct / null-collision
+// particle-steps/s): 7 CTAs (72 registers) 9.88e10 / 7.09e10, 6 (80) 9.55e10 / 6.70e10, 5 (96)
+// 9.34e10 / 7.01e10.
+#ifndef PE_PAIR_MIN_CTAS_GENERAL
+#define PE_PAIR_MIN_CTAS_GENERAL 7
+#endif
+template <int G, bool kCommon>
 constexpr int pair_min_ctas() {
-    return (G == FK_GAUSS_LP || G == FK_GAUSS_CP) ? PE_PAIR_MIN_CTAS_2D
-           : (G == FK_REFL_LP || G == FK_REFL_CP) ? PE_PAIR_MIN_CTAS_REFL : PE_PAIR_MIN_CTAS;
+    constexpr int kind = (G == FK_GAUSS_LP || G == FK_GAUSS_CP) ? PE_PAIR_MIN_CTAS_2D
+                         : (G == FK_REFL_LP || G == FK_REFL_CP) ? PE_PAIR_MIN_CTAS_REFL : PE_PAIR_MIN_CTAS;
+    return kCommon || kind < PE_PAIR_MIN_CTAS_GENERAL ? kind : PE_PAIR_MIN_CTAS_GENERAL;
 }
 // Persistent kernel of the paired form: 128 threads cover a tile of 256 electrons.
 template <bool kSingle, int G, bool kCommon>
-__global__ void __launch_bounds__(128, pair_min_ctas<G>()) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
+__global__ void __launch_bounds__(128, (pair_min_ctas<G, kCommon>())) k_step_pair(TablesDev t, BatchDevT<float> b, int steps) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ RunDevT<float> s_run;
     unsigned long long* s_hist = reinterpret_cast<unsigned long long*>(smem);
