@@ -494,12 +494,17 @@ pe_status pe_pic_step_noalloc(const pe_tables* tables, const pe_run_params* para
  *                         (amplitude sqrt(w0/w) and Gouy phase, formed without an arctangent)
  *        PE_MATH_EXP_NEG  e^(-x) for x >= 0 as the paired 2D focus forms its transverse
  *                         profile (the hardware base-2 exponential)
- *   in, out : n floats of device memory (4-byte aligned); asynchronous on stream.
+ *        PE_MATH_TAU      the optical depth -ln U every FP32 kernel draws after an
+ *                         emission (Sec. 2.2), U the 53-bit uniform of a 64-bit random
+ *                         word: `in` then holds 2n floats, read as the bit patterns of n
+ *                         word pairs (w_lo at in[2i], w_hi at in[2i + 1])
+ *   in, out : n floats of device memory (2n for PE_MATH_TAU; 4-byte aligned);
+ *             asynchronous on stream.
  * Errors: PE_ERR_ARG (null, n < 0, unknown fn), PE_ERR_CUDA.                  */
 enum { PE_MATH_RCP = 0, PE_MATH_SIN = 1, PE_MATH_COS = 2, PE_MATH_SIN1 = 3, PE_MATH_COS1 = 4,
        PE_MATH_BREMS_P = 5, PE_MATH_BREMS_P1 = 6, PE_MATH_CUDA_RCP = 7, PE_MATH_CUDA_SIN = 8,
        PE_MATH_CUDA_COS = 9, PE_MATH_CUDA_EXPM1 = 10, PE_MATH_GOUY_C = 11, PE_MATH_GOUY_S = 12,
-       PE_MATH_EXP_NEG = 13 };
+       PE_MATH_EXP_NEG = 13, PE_MATH_TAU = 14 };
 pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* cuda_stream);
 
 /* Peak of an arithmetic pipe, for the roofline of the ALU-bound step kernel (the

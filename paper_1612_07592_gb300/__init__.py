@@ -320,7 +320,7 @@ def pe_debug_count(tables: int | None = None, bw: int | None = None) -> int:
 
 
 PE_MATH = dict(RCP=0, SIN=1, COS=2, SIN1=3, COS1=4, BREMS_P=5, BREMS_P1=6, CUDA_RCP=7, CUDA_SIN=8, CUDA_COS=9,
-               CUDA_EXPM1=10, GOUY_C=11, GOUY_S=12, EXP_NEG=13)
+               CUDA_EXPM1=10, GOUY_C=11, GOUY_S=12, EXP_NEG=13, TAU=14)
 PE_FMA_F32, PE_FMA_F32X2, PE_FMA_F64 = 0, 1, 2
 
 

@@ -895,7 +895,7 @@ extern "C" pe_status pe_debug_count(const pe_tables* t, const pe_bw_tables* bw, 
 
 extern "C" pe_status pe_math_probe(int fn, const float* in, float* out, int64_t n, void* stream) {
     if ((n > 0 && (!in || !out)) || n < 0) return fail(PE_ERR_ARG, "pe_math_probe: null buffer or n < 0");
-    if (fn < PE_MATH_RCP || fn > PE_MATH_EXP_NEG) return fail(PE_ERR_ARG, "pe_math_probe: unknown fn");
+    if (fn < PE_MATH_RCP || fn > PE_MATH_TAU) return fail(PE_ERR_ARG, "pe_math_probe: unknown fn");
     if (n >= (int64_t(1) << 40)) return fail(PE_ERR_ARG, "pe_math_probe: n too large");
     if (n == 0) return PE_OK;
     launch_math_probe(fn, in, out, n, static_cast<cudaStream_t>(stream));

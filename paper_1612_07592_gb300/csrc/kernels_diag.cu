@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_math_probe(int fn, const float* in, flo
         case PE_MATH_GOUY_C: { float2 c, sn, q; gouy2(P2(v), c, sn, q); r = c.x; } break;
         case PE_MATH_GOUY_S: { float2 c, sn, q; gouy2(P2(v), c, sn, q); r = sn.x; } break;
         case PE_MATH_EXP_NEG: r = exp_neg2(P2(v)).x; break;
+        case PE_MATH_TAU: r = tau_draw_f32(__float_as_uint(in[2 * i]), __float_as_uint(in[2 * i + 1])); break;
         default: r = 0.0f; break;
     }
     out[i] = r;

@@ -146,14 +146,19 @@ __device__ __forceinline__ float sample_brems_y_f32(const TablesDev& t, int iz, 
     return ycut * __expf(s * __logf(ymax / ycut));
 }
 
-// new optical depth -ln U from the 53-bit uniform: for U >= 1/2 through
-// log1p of the complement (built exactly from the complemented bits)
+// new optical depth -ln U from the 53-bit uniform, to first order in the low part of the
+// pair: for U >= 1/2 through log1p of the complement (built exactly from the complemented
+// bits; the correction lo / (1 - hi) is below 2^-22), else -ln hi - lo / hi.  hi carries
+// the top 23 bits of U as a fixed-point number, so below 2^-10 it holds few of U's leading
+// bits (none below 2^-23, where it is 0): there the pair is first renormalised (exactly,
+// TwoSum), which bounds lo / hi by 2^-24.  Relative error about one ulp of the result.
 __device__ __forceinline__ float tau_draw_f32(uint32_t wlo, uint32_t whi) {
     if (whi & 0x80000000u) {
         DF q = uni53_pair(~wlo, ~whi);                  // 1 - U
         return -log1pf(-q.hi) + q.lo / (1.0f - q.hi);
     }
     DF u = uni53_pair(wlo, whi);
+    if (u.hi < 0x1.0p-10f) u = two_sum(u.hi, u.lo);
     return -logf(u.hi) - u.lo / u.hi;
 }
 
