@@ -9,7 +9,10 @@ compare their results with the FP64 oracle).
 - the 128-bit fixed-point tally of a float (fx_add_f32): hi 2^64 + lo = floor(v 2^64), exactly;
 - the half-angle form of the 2D focus's amplitude and Gouy phase (gouy2), in FP64;
 - the FP32 optical-depth draw -ln U (uni53_pair, tau_draw_f32) against 40-digit logarithms of
-  the same 53-bit U; its plausible mistakes fail the same bound.
+  the same 53-bit U; its plausible mistakes fail the same bound;
+- the samplers' double-float inverse CDF (pair_value, the guide bracket, invert_pair_df): the
+  column equals a linear scan in the same arithmetic and the exact column in rational
+  arithmetic away from ties.
 """
 from fractions import Fraction
 import math
@@ -251,3 +254,187 @@ def test_tau_draw_form_within_bound():
 @pytest.mark.parametrize("mistake", ["no renormalisation", "correction dropped", "correction sign", "no complement"])
 def test_tau_draw_bound_catches_mistakes(mistake):
     assert tau_worst(mistake) > 2.0 ** -21.5
+
+
+# ---- the double-float inverse CDF of the samplers ---------------------------------------
+
+def round_f32(x):
+    """A rational rounded to the nearest float32 (ties to even), as one hardware rounding."""
+    x = Fraction(x)
+    if x == 0:
+        return F(0.0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    scale = Fraction(2) ** (23 - e)
+    y = a * scale
+    q = y.numerator // y.denominator
+    rem = y - q
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and q % 2 == 1):
+        q += 1
+    return F(sign * float(q / scale))
+
+
+def fma32(a, b, c):
+    return round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
+
+
+def pair_value(e, w):
+    """(1 - w) A + w B of one pair-row entry e = (A_hi, A_lo, B_hi, B_lo) as a float pair."""
+    ah, al, bh, bl = e
+    if w == F(0.0):
+        return ah, al
+    dh, dlo = two_sum(bh, -ah)                       # B_hi - A_hi exactly
+    dl = F(dlo + F(bl - al))
+    p = F(w * dh)
+    ep = fma32(w, dh, -p)                            # the product's rounding error
+    ch, cl = two_sum(ah, p)
+    return ch, F(cl + F(al + fma32(w, dl, ep)))
+
+
+def df_diff(a, b):
+    return F(F(a[0] - b[0]) + F(a[1] - b[1]))
+
+
+def invert_pair_df(q, g, w, n, M, R, mistake=None):
+    """The device's inverse of a row-interpolated CDF: (j, fraction)."""
+    rm = F(R[0] * F(M))
+    m = floor_small(rm)
+    if R[1] < 0 and int_to_float_small(m) == rm:
+        m -= 1
+    m = min(m, M - 1)
+    c0 = pair_value(q[0], w)
+    if df_diff(R, c0) < 0:
+        return -1, F(F(R[0] + R[1]) / F(c0[0] + c0[1]))
+    cn = pair_value(q[n - 1], w)
+    if df_diff(R, cn) >= 0:
+        return n - 1, F(0.0)
+    gx, gy, gz, gw = g[m]
+    a = max(min(gx, gy) - 1, 0)                      # the two rows' brackets, widened by one
+    b = min(max(gz, gw) + 1, n - 2)
+    lo, hi = a, b + 1
+    while hi - lo > 1:
+        mid = (lo + hi) >> 1
+        d = df_diff(R, pair_value(q[mid], w))
+        if (d > 0) if mistake == "tie to the right" else (d >= 0):
+            lo = mid
+        else:
+            hi = mid
+    cl, ch = pair_value(q[lo], w), pair_value(q[hi], w)
+    num, den = df_diff(R, cl), df_diff(ch, cl)
+    return lo, (F(num / den) if den > 0 else F(0.0))
+
+
+def guide(hi, lo, n, M):
+    """The host's guide column: out[m] = the largest j with hi[j] + lo[j] <= m / M, -1 if none."""
+    mark = [-1] * (M + 1)
+    for k in range(n):
+        x = math.ceil((float(hi[k]) + float(lo[k])) * M)
+        if x > M:
+            continue
+        m0 = max(x, 0)
+        mark[m0] = max(mark[m0], k)
+    out, run = [], -1
+    for m in range(M + 1):
+        run = max(run, mark[m])
+        out.append(run)
+    return out
+
+
+def pair_rows(A, B, M):
+    """Float-pair rows of two CDFs (float64 arrays) and their guide cells, as the host builds them."""
+    n = len(A)
+    ah = A.astype(np.float32)
+    al = (A - ah.astype(np.float64)).astype(np.float32)
+    bh = B.astype(np.float32)
+    bl = (B - bh.astype(np.float64)).astype(np.float32)
+    q = [(ah[j], al[j], bh[j], bl[j]) for j in range(n)]
+    ja, jb = guide(ah, al, n, M), guide(bh, bl, n, M)
+    g = [(ja[m], jb[m], ja[m + 1], jb[m + 1]) for m in range(M)]
+    return q, g
+
+
+def sampler_cases():
+    """CDF row pairs: smooth, with flat runs (zero weights), identical rows, a last node below 1,
+    and rows whose nodes crowd into one guide cell."""
+    rng = np.random.default_rng(3)
+    n, M = 40, 64
+    cases = []
+    for kind in ("smooth", "flat", "same", "short", "crowded"):
+        wa, wb = rng.exponential(1.0, n), rng.exponential(1.0, n)
+        if kind == "flat":
+            wa[5:15] = 0.0
+            wb[20:30] = 0.0
+        if kind == "crowded":
+            wa[1:30] *= 1e-4
+            wb[1:35] *= 1e-4
+        A, B = np.cumsum(wa), np.cumsum(wb)
+        A, B = A / A[-1], B / B[-1]
+        if kind == "same":
+            B = A.copy()
+        if kind == "short":
+            A, B = A * 0.97, B * 0.99
+        cases.append((kind, n, M, A, B))
+    return cases
+
+
+def exact_inverse(q, w, R):
+    W = Fraction(float(w))
+    C = [(1 - W) * (Fraction(float(e[0])) + Fraction(float(e[1]))) + W * (Fraction(float(e[2])) + Fraction(float(e[3])))
+         for e in q]
+    r = Fraction(float(R[0])) + Fraction(float(R[1]))
+    j = max([k for k in range(len(C)) if C[k] <= r], default=-1)
+    return j, C, r
+
+
+def sampler_mismatches(mistake=None):
+    """(cases checked, cases whose column differs from a linear scan in the same float-pair
+    arithmetic, or from the exact one away from a tie)."""
+    rng = np.random.default_rng(9)
+    checked = bad = 0
+    tie = Fraction(1, 2 ** 40)
+    for kind, n, M, A, B in sampler_cases():
+        q, g = pair_rows(A, B, M)
+        for w in (F(0.0), F(0.25), F(0.7), F(1.0) - F(2.0 ** -24)):
+            Rs = [uni53_pair(int(a), int(b)) for a, b in rng.integers(0, 1 << 32, size=(60, 2))]
+            Rs += [pair_value(e, w) for e in q]                           # R on the nodes
+            Rs += [(e[0], F(0.0)) for e in q[::7]]                        # R on a node's high part
+            nodes = [pair_value(e, w) for e in q]
+            for R in Rs:
+                j, fr = invert_pair_df(q, g, w, n, M, R, mistake)
+                jx, C, r = exact_inverse(q, w, R)
+                checked += 1
+                # brute force in the device's own arithmetic: the largest j with c_j <= R
+                jb = max([k for k in range(n) if df_diff(R, nodes[k]) >= 0], default=-1)
+                if j != jb:
+                    bad += 1
+                    continue
+                near = min(abs(r - c) for c in C) < tie
+                if j != jx and not near:
+                    bad += 1
+                elif j != jx:
+                    # a tie within rounding: the column chosen must still bracket R to the tie width
+                    ok = (j < 0 or C[j] <= r + tie) and (j + 1 >= n or C[j + 1] > r - tie)
+                    bad += 0 if ok else 1
+                if mistake is None and 0 <= j < n - 1 and C[j + 1] - C[j] > Fraction(1, 2 ** 20):
+                    fx = (r - C[j]) / (C[j + 1] - C[j])
+                    assert abs(Fraction(float(fr)) - fx) < Fraction(1, 2 ** 18), (kind, w, j)
+    return checked, bad
+
+
+def test_inverse_cdf_picks_the_exact_column():
+    """Over smooth rows, flat runs, identical rows, a last node below 1 and crowded guide cells,
+    at four interpolation weights, for random 53-bit R and R on the nodes: the guided bisection
+    returns what a linear scan in the same float-pair arithmetic returns (the largest j with
+    c_j <= R), which is the exact column in rational arithmetic or within 2^-40 of a tie, and
+    the fraction within the column is exact to 2^-18."""
+    checked, bad = sampler_mismatches()
+    assert checked > 1000 and bad == 0
+
+
+@pytest.mark.parametrize("mistake", ["tie to the right"])
+def test_inverse_cdf_bound_catches_mistakes(mistake):
+    """A tie sent to the column on the right (R equal to a node must select that node) fails."""
+    assert sampler_mismatches(mistake)[1] > 0
