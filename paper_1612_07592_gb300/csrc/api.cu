@@ -470,8 +470,17 @@ static void describe_run(const pe_tables* t, const pe_run_params* rp, int64_t n,
     for (int k = 0; k < 3; ++k) { c.E_const[k] = rp->E_const[k]; c.B_const[k] = rp->B_const[k]; }
     c.refl_r = rp->reflect_r;
     const double xm2 = 2.0 * rp->mirror_x_m * kl;
-    c.xm2_hi = (double)(float)xm2;                 // an exact float, remainder below
-    c.xm2_lo = xm2 - c.xm2_hi;
+    // 2 x_m = hi + lo with hi on dt_hi's grid (multiples of its last bit), so that the FP32 phase
+    // of the reflected pulse forms n dt_hi - hi exactly (both on that grid, fewer than 2^24
+    // steps of it); a mirror beyond that range takes the nearest float.  hi + lo is 2 x_m exactly.
+    {
+        int e;
+        std::frexp(c.dt, &e);
+        const double q = std::ldexp(1.0, e - 11);
+        c.xm2_hi = std::nearbyint(xm2 / q) * q;
+        if (!(std::fabs(c.xm2_hi) < std::ldexp(q, 23))) c.xm2_hi = (double)(float)xm2;
+        c.xm2_lo = xm2 - c.xm2_hi;
+    }
     // null collisions: majorant from the largest tabulated sigma_Z (beta <= 1)
     double smax = 0;
     for (int i = 0; i < t->host.p.n_E; ++i) smax = std::max(smax, t->host.sigma[(size_t)iz * t->host.p.n_E + i]);

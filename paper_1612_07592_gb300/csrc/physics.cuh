@@ -171,7 +171,8 @@ __device__ __forceinline__ void advance(float& x, float& x_lo, float d) {
 __device__ __forceinline__ void advance(double& x, double&, double d) { x += d; }
 
 // phase of the reflected wave t^n + x - 2 x_m, with the same care as phase():
-// n * dt_hi - 2 x_m,hi rounds once, then x, then the small remainders.
+// n * dt_hi - 2 x_m,hi is exact in float (2 x_m,hi lies on dt_hi's grid), then x,
+// then the small remainders.
 __device__ __forceinline__ double phase_refl(const StepC<double>& c, double nf, double x, double) {
     return nf * c.dt + x - (c.xm2_hi + c.xm2_lo);
 }

@@ -14,7 +14,9 @@ compare their results with the FP64 oracle).
   column equals a linear scan in the same arithmetic and the exact column in rational
   arithmetic away from ties;
 - the branch-free pulse envelope of the paired step (envelope2) against the piecewise sin^2
-  ramps and flat top of the pulse definition, in every region and at its boundaries.
+  ramps and flat top of the pulse definition, in every region and at its boundaries;
+- the FP32 laser phases t - x and t + x - 2 x_m (t = n dt_hi + n dt_lo, the position a float
+  pair) against exact rational arithmetic, inside and beyond the exact range of n dt_hi.
 """
 from fractions import Fraction
 import math
@@ -502,3 +504,87 @@ def test_envelope_form_matches_definition():
 def test_envelope_form_catches_mistakes(mistake):
     wg, wd = envelope_worst(mistake)
     assert wg > 1e-3 or wd > 1e-3
+
+
+# ---- the FP32 laser phase ----------------------------------------------------------------
+
+def split_dt(dt):
+    """The host's split: dt_hi the largest value <= dt with 11 significant bits, dt_lo the rest."""
+    m, e = math.frexp(dt)
+    hi = math.ldexp(math.floor(math.ldexp(m, 11)), e - 11)
+    return hi, dt - hi
+
+
+def split_mirror(xm2, dt):
+    """The host's split of 2 x_m: hi on dt_hi's grid (multiples of its last bit), lo the rest."""
+    q = math.ldexp(1.0, math.frexp(dt)[1] - 11)
+    hi = round(xm2 / q) * q
+    if not abs(hi) < math.ldexp(q, 23):
+        hi = float(F(xm2))
+    return hi, xm2 - hi
+
+
+def phase_f32(nf, x, xl, dth, dtl, mistake=None):
+    """t^n - x as the paired step forms it: (n dt_hi - x) + n dt_lo in one fused multiply-add,
+    then minus the position's low part."""
+    p = fma32(nf, F(0.0) if mistake == "dt_lo dropped" else dtl, F(F(nf * dth) - x))
+    return p if mistake == "x_lo dropped" else F(p - xl)
+
+
+def phase_refl_f32(nf, x, xl, dth, dtl, mh, ml, mistake=None):
+    """t^n + x - 2 x_m: (n dt_hi - 2 x_m,hi) + x, plus n dt_lo + (x_lo - 2 x_m,lo)."""
+    a = F(fma32(nf, dth, -mh) + x)
+    d = F(xl + ml) if mistake == "mirror low part sign" else F(xl - ml)
+    return F(a + fma32(nf, dtl, d))
+
+
+def phase_errors(n_values, mistake=None):
+    """Largest |error| over positions in and around the pulse, in units of the result's ulp,
+    beside the documented extra term 2^-24 t."""
+    rng = np.random.default_rng(17)
+    dt = 0.01 * 2.0 * math.pi                       # dt = T / 100 in laser phase
+    dth, dtl = split_dt(dt)
+    dth32, dtl32 = F(dth), F(dtl)
+    assert float(dth32) == dth                      # 11 bits: exact in float
+    xm2 = 2.0 * 3e-6 * 2.0 * math.pi / 1e-6         # mirror 3 um from the origin, lambda 1 um
+    xh, xlo = split_mirror(xm2, dt)
+    mh, ml = F(xh), F(xlo)
+    assert float(mh) == xh and Fraction(xh) + Fraction(xlo) == Fraction(xm2)
+    worst = 0.0
+    for n in n_values:
+        nf = F(n)
+        t = Fraction(n) * Fraction(dt)
+        for target in rng.uniform(-10.0, 80.0, 4):
+            for refl in (False, True):
+                xe = (Fraction(xm2) - t + Fraction(float(target))) if refl else (t - Fraction(float(target)))
+                x = F(float(xe))
+                xl = F(float(xe - Fraction(float(x))))
+                xx = Fraction(float(x)) + Fraction(float(xl))
+                if refl:
+                    got = phase_refl_f32(nf, x, xl, dth32, dtl32, mh, ml, mistake)
+                    exact = t + xx - Fraction(xm2)
+                else:
+                    got = phase_f32(nf, x, xl, dth32, dtl32, mistake)
+                    exact = t - xx
+                err = abs(Fraction(float(got)) - exact)
+                allowed = 2 * half_ulp(abs(float(exact)) or 1e-30) * 2 + Fraction(2e-8) + t * Fraction(1, 2 ** 24) * (n >= 8192)
+                worst = max(worst, float(err / allowed))
+    return worst
+
+
+def test_phase_exact_within_8192_steps():
+    """Below step 2^13 the phases t - x and t + x - 2 x_m are exact to two ulps of the result plus
+    the rounding of the float dt_lo (n |dt_lo - float(dt_lo)| < 2e-8 rad): n dt_hi is exact, and
+    so is n dt_hi - 2 x_m,hi with 2 x_m,hi on dt_hi's grid.  (With 2 x_m,hi the nearest float, that
+    difference rounded at the magnitude of t: up to 110 times this bound by step 8191.)"""
+    assert phase_errors([0, 1, 2, 3, 100, 1234, 4000, 4095, 4096, 8000, 8191]) <= 1.0
+
+
+def test_phase_beyond_8192_steps_within_stated_rounding():
+    """From step 2^13 on, n dt_hi rounds: the error stays within the stated extra 2^-24 t."""
+    assert phase_errors([8192, 8193, 12345, 30000, 50000, 65535]) <= 1.0
+
+
+@pytest.mark.parametrize("mistake", ["x_lo dropped", "dt_lo dropped", "mirror low part sign"])
+def test_phase_bound_catches_mistakes(mistake):
+    assert phase_errors([1, 1234, 4000, 8191], mistake) > 1.0
