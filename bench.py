@@ -49,19 +49,24 @@ BYTES_PER_PSTEP_1D_PLAIN_X = 48
 FP32_LANES_PER_SM = 128
 # warp instructions per 64 electron-steps of the dominant kernel (one warp steps 64 electrons), from
 # the same ncu capture of the headline launch; the kernel is bound by instruction issue (one warp
-# instruction per scheduler per clock), which the roofline's `issue` entry reports beside the FP32 pipe
+# instruction per scheduler per clock), which the roofline's `issue` entry reports beside the FP32 pipe.
+# Counted before the optical-depth draw's renormalisation below U = 2^-10 entered the emission
+# branch: a compare per emission (2.9e6 per job) and the rare renormalisation, about 2e-3
+# instructions per particle-step, within the count's last digit.
 NCU_WARP_INST_PER_64_ESTEPS = 279.1
 SCHEDULERS_PER_SM = 4
 # DRAM bytes (read + write) per electron and launch of the dominant kernel, from the same ncu
 # capture of the headline launch (29.1 MB for 1e6 electrons: the state read once, the final state
-# still in L2 at the end, the cold emission tables; profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md);
-# None once the kernel changes.
-NCU_TRAFFIC_BYTES_PER_ELECTRON = 29.13
+# still in L2 at the end, the cold emission tables; profiles/k_step_pair__1d-au-a270-mj-1e6x4000__flops.md:
+# 29.13 B); None once the kernel changes, as it has since (the optical-depth draw of the inlined
+# emission branch), until the next capture.
+NCU_TRAFFIC_BYTES_PER_ELECTRON = None
 # DRAM bytes (read + write) per electron of one launch of the one-step form, from an ncu capture of
 # one launch on 8e6 electrons (386.7 MB: 28 B read, 20.3 B written -- the rest of the 28 B still
 # dirty in L2 when the kernel ends), scaled by the electron count of the measured workload
-# (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md); None once the kernel changes.
-NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = 48.34
+# (profiles/k_step_pair_stream__1d-au-a270-mj-8e6-K1__full.md: 48.34 B); None once the kernel
+# changes, as it has since (the same emission branch), until the next capture.
+NCU_STREAM_TRAFFIC_BYTES_PER_ELECTRON = None
 
 
 def peaks():
