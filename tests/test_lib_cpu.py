@@ -84,6 +84,12 @@ def test_argument_errors_are_reported(libpath):
     with pytest.raises(pe.PeError) as e:                 # pair transport without a run
         pe.pe_pair_transport(0, 0, 1, -1, 0, 0, 0)
     assert e.value.status == pe.PE_ERR_ARG
+    last = max(pe.PE_MATH.values())                       # the probe checks fn and n before any launch
+    for fn, n in ((last + 1, 0), (-1, 0), (pe.PE_MATH["TAU"], -1)):
+        with pytest.raises(pe.PeError) as e:
+            pe.pe_math_probe(fn, 0, 0, n, None)
+        assert e.value.status == pe.PE_ERR_ARG
+    pe.pe_math_probe(pe.PE_MATH["TAU"], 0, 0, 0, None)    # nothing to do: no launch, PE_OK
 
 
 def test_workloads():
@@ -121,6 +127,7 @@ def test_constants_match_header(tmp_path):
              "PE_PAIR_TALLY_WORDS": pe.PAIR_TALLY_WORDS}
     names.update({"PE_T_" + k: v for k, v in pe.T.items()})
     names.update({"PE_PT_" + k: v for k, v in pe.PT.items()})
+    names.update({"PE_MATH_" + k: v for k, v in pe.PE_MATH.items()})
     prog = tmp_path / "consts.c"
     body = "".join(f'printf("{n} %lld\\n", (long long)({n}));' for n in names)
     prog.write_text('#include <stdio.h>\n#include "pe.h"\nint main(void){' + body + "return 0;}\n")
