@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import scipy.integrate as si
 import scipy.special as sp
+import scipy.stats as st_
 from scipy.optimize import brentq
 
 import oracle as O
@@ -443,6 +444,57 @@ def test_brems_first_event_is_geometric():
     k = waits[waits < 400]
     mean_trunc = sum(kk * (1 - P) ** kk * P for kk in range(400)) / (1 - (1 - P) ** 400)
     assert abs(k.mean() / mean_trunc - 1) < 0.05
+
+
+def test_ncs_first_emission_follows_the_rate():
+    """The step's NCS optical depth falls at the paper's rate (Sec. 2.2): in a constant magnetic
+    field across the electron's velocity, gamma and eta stay fixed until it emits, so tau drops
+    by the same dtau = (sqrt3 alpha / 2 pi) (m c^2 / hbar omega) (eta / gamma) h(eta) omega dt each
+    step and the first emission comes at step ceil(tau_0 / dtau) - 1, P(n_1 >= k) = e^{-k dtau}.
+    m c^2 / hbar omega is lambda / (2 pi lambdabar_C) from CODATA, not the oracle's own E_S; h is
+    the table, pinned to brute-force quadrature above.  A rate without the 1/gamma, with another
+    prefactor or a decrement off by a step fails the chi^2."""
+    t = O.Tables(O.table_params(n_eta=64, n_y=32, n_E=2, n_s=2), [13.0])
+    lam, lbar_c = 1e-6, 3.8615926796e-13                     # m; CODATA reduced Compton wavelength
+    E_S = lam / (2 * math.pi * lbar_c)                       # m c^2 / (hbar omega) = E_S / (m c omega / e)
+    gamma, eta = 100.0, 0.05
+    u = math.sqrt(gamma * gamma - 1.0)
+    Bz = eta * E_S / u                                       # |u x B| / E_S = eta for u along x, B along z
+    r = O.run_params(geometry=2, B_const=(0.0, 0.0, Bz), init_dist=2, beam_gamma=gamma, enable_brems=0, seed=13)
+    dt = 2 * math.pi * 0.01
+    h, _ = t.h_interp(eta)
+    dtau = math.sqrt(3) * ALPHA / (2 * math.pi) * E_S * (eta / gamma) * h * dt
+    n, S = 20000, 60
+    ids = np.arange(n)
+    st = O.init(t, r, ids)
+    ev = np.zeros(n, dtype=np.uint64)
+    first = np.full(n, S)
+    for k in range(S):
+        O.run(t, r, ids, st, k, 1, capacity=1 << 16, events=ev)
+        emitted = (ev & np.uint64(0xFFFF)) > 0
+        first[(first == S) & emitted] = k
+    assert 0.05 < dtau < 0.2
+    edges = list(range(0, S, 4)) + [S]
+    obs = np.array([np.sum((first >= a) & (first < b)) for a, b in zip(edges[:-1], edges[1:])] + [np.sum(first == S)])
+
+    def expected(d, lag=0):
+        # P(n_1 >= k) = e^{-(k + lag) d}; lag = 1: the crossing tested before the step's decrement
+        def surv(k):
+            return math.exp(-max(k + lag, 0) * d)
+        return np.array([n * (surv(a) - surv(b)) for a, b in zip(edges[:-1], edges[1:])] + [n * surv(S)])
+
+    keep = expected(dtau) > 5                               # the bins of the stated rate, for every model
+
+    def chi2(d, lag=0):
+        e = np.maximum(expected(d, lag)[keep], 1e-3)
+        return float(((obs[keep] - e) ** 2 / e).sum())
+
+    dof = int(keep.sum()) - 1
+    c = chi2(dtau)
+    assert st_.chi2.sf(c, dof) > 1e-3, c
+    # the statistic separates the rate from its plausible misreadings
+    for wrong, lag in ((dtau * 1.05, 0), (dtau / 1.05, 0), (dtau * 2 * math.pi, 0), (dtau * gamma, 0), (dtau, 1)):
+        assert st_.chi2.sf(chi2(wrong, lag), dof) < 1e-5, (wrong, lag)
 
 
 def test_energy_bookkeeping():
