@@ -446,6 +446,39 @@ def test_brems_first_event_is_geometric():
     assert abs(k.mean() / mean_trunc - 1) < 0.05
 
 
+def test_brems_probability_carries_beta():
+    """Eq. 4's x_b = n_i sigma_Z(gamma) beta c dt: at gamma = 2.5 (beta = 0.917) the first-event
+    law of the direct test separates beta from its omission.  One event takes gamma below
+    1 + photon_min, so each electron's first event is its only one; fields off, thick slab."""
+    t = O.Tables(O.table_params(n_eta=2, n_y=4, n_E=64, n_s=32), [79.0])
+    g = 2.5
+    r = O.run_params(geometry=2, Z=79.0, charge_state=51.0, ne_over_nc=1e8, slab_x0_m=-1.0, slab_thick_m=2.0,
+                     init_dist=2, beam_gamma=g, enable_ncs=0, seed=19)
+    n, S = 20000, 300
+    ids = np.arange(n)
+    st = O.init(t, r, ids)
+    ph, _, _, _ = O.run(t, r, ids, st, 0, S, capacity=1 << 16)
+    first = np.full(n, S)
+    pid = ph["id_mech"].astype(np.int64) & 0x7FFFFFFF
+    np.minimum.at(first, pid, ph["step"].astype(np.int64))
+    sig, _ = t.sigma_interp(0, g)
+    n_i = 1e8 * O.critical_density(1e-6) / 51.0
+    dt = 2 * math.pi * 0.01
+    beta = math.sqrt(1 - 1 / g ** 2)
+    xb = n_i * ALPHA * RE * RE * dt * 1e-6 / (2 * math.pi) * sig * beta
+    edges = list(range(0, S, 20)) + [S]
+    obs = np.array([np.sum((first >= a) & (first < b)) for a, b in zip(edges[:-1], edges[1:])] + [np.sum(first == S)])
+
+    def chi2(x):
+        q = math.exp(-x)                                     # 1 - P per step
+        e = np.array([n * (q ** a - q ** b) for a, b in zip(edges[:-1], edges[1:])] + [n * q ** S])
+        return float(((obs - e) ** 2 / e).sum())
+
+    dof = len(obs) - 1
+    assert st_.chi2.sf(chi2(xb), dof) > 1e-3, chi2(xb)
+    assert st_.chi2.sf(chi2(xb / beta), dof) < 1e-5            # beta left out
+
+
 def test_ncs_first_emission_follows_the_rate():
     """The step's NCS optical depth falls at the paper's rate (Sec. 2.2): in a constant magnetic
     field across the electron's velocity, gamma and eta stay fixed until it emits, so tau drops
@@ -453,7 +486,8 @@ def test_ncs_first_emission_follows_the_rate():
     step and the first emission comes at step ceil(tau_0 / dtau) - 1, P(n_1 >= k) = e^{-k dtau}.
     m c^2 / hbar omega is lambda / (2 pi lambdabar_C) from CODATA, not the oracle's own E_S; h is
     the table, pinned to brute-force quadrature above.  A rate without the 1/gamma, with another
-    prefactor or a decrement off by a step fails the chi^2."""
+    prefactor or a decrement off by a step fails the chi^2.  The first photons point along the
+    analytically rotated velocity, which fixes the emission direction and the push's sense."""
     t = O.Tables(O.table_params(n_eta=64, n_y=32, n_E=2, n_s=2), [13.0])
     lam, lbar_c = 1e-6, 3.8615926796e-13                     # m; CODATA reduced Compton wavelength
     E_S = lam / (2 * math.pi * lbar_c)                       # m c^2 / (hbar omega) = E_S / (m c omega / e)
@@ -469,11 +503,24 @@ def test_ncs_first_emission_follows_the_rate():
     st = O.init(t, r, ids)
     ev = np.zeros(n, dtype=np.uint64)
     first = np.full(n, S)
+    photons = []
     for k in range(S):
-        O.run(t, r, ids, st, k, 1, capacity=1 << 16, events=ev)
+        ph, _, _, _ = O.run(t, r, ids, st, k, 1, capacity=1 << 16, events=ev)
         emitted = (ev & np.uint64(0xFFFF)) > 0
         first[(first == S) & emitted] = k
+        photons.append(ph)
     assert 0.05 < dtau < 0.2
+    # each electron's first photon leaves along its velocity (collinear emission, Sec. 2.2): after
+    # n + 1 pushes of a pure rotation by 2 atan(B dt / 2 gamma), toward +y for an electron from +x
+    ph = np.concatenate(photons)
+    pid = ph["id_mech"].astype(np.int64) & 0x7FFFFFFF
+    at_first = (ph["id_mech"] >> 31 == 0) & (ph["step"].astype(np.int64) == first[pid])
+    assert at_first.sum() > n // 4
+    theta = 2.0 * math.atan(0.5 * dt * Bz / gamma)
+    phi = (ph["step"][at_first].astype(np.float64) + 1.0) * theta
+    assert np.abs(ph["kx"][at_first] - np.cos(phi)).max() < 1e-6
+    assert np.abs(ph["ky"][at_first] - np.sin(phi)).max() < 1e-6
+    assert np.abs(ph["kz"][at_first]).max() < 1e-6
     edges = list(range(0, S, 4)) + [S]
     obs = np.array([np.sum((first >= a) & (first < b)) for a, b in zip(edges[:-1], edges[1:])] + [np.sum(first == S)])
 
