@@ -7,6 +7,10 @@ code with the CUDA library in ``paper_1612_07592_gb300``.
 
 What it computes, step by step, is stated in ``oracle/step.c`` and
 ``oracle/tables.c`` with the paper section or equation each part follows.
+
+The environment variable ``ORACLE_MUTANT`` (set only by tests/test_oracle_mutants.py,
+in a child process) builds and loads the oracle with one planted mistake from
+``MUTANTS`` instead, so that a test can show that the pins catch it.
 """
 from __future__ import annotations
 
@@ -21,6 +25,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = ["tables.c", "step.c"]
+# the planted mistakes step.c knows (OR_MUTANT_<name>)
+MUTANTS = ("PHILOX_MULT", "BORIS_SIGN", "ETA_UE", "PHOTON_BACKWARD", "NCS_NO_GAMMA", "NCS_LAG",
+           "RECOIL_TALLY", "BREMS_NO_BETA")
+
+
+def _mutant() -> str:
+    m = os.environ.get("ORACLE_MUTANT", "")
+    if m and m not in MUTANTS:
+        raise ValueError(f"unknown ORACLE_MUTANT {m!r}")
+    return m
 _lock = threading.Lock()
 _lib = None
 
@@ -42,20 +56,23 @@ PT = dict(N_PAIRS=0, N_ENTERED=1, N_K_ABOVE=2, N_TESTS=3, E_PAIRS=4, E_POSITRONS
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into ``oracle/_build/liboracle.so``."""
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so`` (with ORACLE_MUTANT
+    set, the mutant into ``liboracle_<mutant>.so``)."""
     os.makedirs(_BUILD, exist_ok=True)
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     hdr = os.path.join(_HERE, "oracle.h")
-    if not force and os.path.exists(_LIB_PATH):
+    m = _mutant()
+    path = os.path.join(_BUILD, f"liboracle_{m.lower()}.so") if m else _LIB_PATH
+    if not force and os.path.exists(path):
         newest = max(os.path.getmtime(p) for p in srcs + [hdr])
-        if os.path.getmtime(_LIB_PATH) >= newest:
-            return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        if os.path.getmtime(path) >= newest:
+            return path
+    tmp = path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c99", "-D_DEFAULT_SOURCE",
-           "-ffp-contract=off", "-o", tmp] + srcs + ["-lm"]
+           "-ffp-contract=off", "-o", tmp] + ([f"-DOR_MUTANT_{m}"] if m else []) + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class TableParams(C.Structure):

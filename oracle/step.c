@@ -27,6 +27,10 @@
 #define C_LIGHT 299792458.0
 #define HIST_EMAX_MEV 10000.0          /* top of the energy histogram   */
 
+/* OR_MUTANT_* (never defined in a normal build): each plants one plausible mistake
+ * (a dropped term, a wrong sign, a missing factor, a lag, a wrong constant) so that the
+ * tests can show that a pin fails for it (tests/test_oracle_mutants.py).               */
+
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10, from its published definition (Salmon et al., SC'11):      */
 /* 10 rounds of two 32x32->64 multiplies (M0 = 0xD2511F53, M1 = 0xCD9E8D57), */
@@ -36,7 +40,11 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
     uint32_t k0 = key[0], k1 = key[1];
     for (int r = 0; r < 10; ++r) {
+#ifdef OR_MUTANT_PHILOX_MULT
+        uint64_t p0 = (uint64_t)0xD2511F55u * (uint64_t)c0;
+#else
         uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+#endif
         uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
         uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
@@ -188,7 +196,11 @@ void or_boris(double u[3], const double E[3], const double B[3], double dt) {
     double h = 0.5 * dt;
     double um[3] = {u[0] - h * E[0], u[1] - h * E[1], u[2] - h * E[2]};
     double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#ifdef OR_MUTANT_BORIS_SIGN
+    double tv[3] = {h * B[0] / gm, h * B[1] / gm, h * B[2] / gm};
+#else
     double tv[3] = {-h * B[0] / gm, -h * B[1] / gm, -h * B[2] / gm};
+#endif
     double t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
     double sv[3] = {2.0 * tv[0] / (1.0 + t2), 2.0 * tv[1] / (1.0 + t2), 2.0 * tv[2] / (1.0 + t2)};
     double up[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]),
@@ -219,7 +231,12 @@ double or_eta(const double u[3], const double E[3], const double B[3], double E_
                    gm * E[1] + (u[2] * dB[0] - u[0] * dB[2]),
                    gm * E[2] + (u[0] * dB[1] - u[1] * dB[0])};
     double uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+#ifdef OR_MUTANT_ETA_UE
+    double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    (void)uE;
+#else
     double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2] + 2.0 * V[0] * uE;
+#endif
     return q > 0.0 ? sqrt(q) / E_S : 0.0;
 }
 
@@ -372,7 +389,11 @@ static void record(const run_ctx* c, double x, double y, double ew, const double
 /* energy-conserving recoil along u: gamma' = gamma - w, u' = u^ sqrt(gamma'^2 - 1) */
 static void recoil(double u[3], double gamma, double w, double khat[3]) {
     double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#ifdef OR_MUTANT_PHOTON_BACKWARD
+    if (um > 0.0) { khat[0] = -u[0] / um; khat[1] = -u[1] / um; khat[2] = -u[2] / um; }
+#else
     if (um > 0.0) { khat[0] = u[0] / um; khat[1] = u[1] / um; khat[2] = u[2] / um; }
+#endif
     else { khat[0] = 1.0; khat[1] = 0.0; khat[2] = 0.0; }
     double g2 = gamma - w;
     double un = (g2 > 1.0) ? sqrt(g2 * g2 - 1.0) : 0.0;
@@ -401,8 +422,17 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
         int fl;
         double h = or_ncs_h_interp(t, eta, &fl);
         if (fl == 1) tally[ORT_N_ETA_ABOVE]++;
+#if defined(OR_MUTANT_NCS_NO_GAMMA)
+        tau -= c->C_ncs * eta * h * c->dt;
+        if (tau <= 0.0) {
+#elif defined(OR_MUTANT_NCS_LAG)
+        const double tau_before = tau;
+        tau -= c->C_ncs * (eta / gamma) * h * c->dt;
+        if (tau_before <= 0.0) {
+#else
         tau -= c->C_ncs * (eta / gamma) * h * c->dt;
         if (tau <= 0.0) {
+#endif
             uint32_t w[4];
             draw(r, id, (uint32_t)n, PUR_NCS, w);
             int below;
@@ -414,7 +444,11 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
             recoil(u, gamma, ew, k);
             note_event(ev, n, 0);
             double gn = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#ifdef OR_MUTANT_RECOIL_TALLY
+            fx_add(tally + ORT_E_RECOIL_NCS, gn - gamma);
+#else
             fx_add(tally + ORT_E_RECOIL_NCS, gamma - gn);
+#endif
             if (ew >= c->photon_min) {
                 tally[ORT_N_NCS_STORED]++;
                 tally[ORT_N_PHOTONS]++;
@@ -443,7 +477,12 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
                 double sig = or_brems_sigma_interp(t, r->iz, gamma, &above);
                 if (above) tally[ORT_N_GAMMA_ABOVE]++;
                 double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#ifdef OR_MUTANT_BREMS_NO_BETA
+                double xb = c->K_br * sig;
+                (void)um;
+#else
                 double xb = c->K_br * sig * (um / gamma);
+#endif
                 P = -expm1(-xb);
             }
             double p_acc = nullc ? P / c->P_hat : P;

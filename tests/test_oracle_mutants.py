@@ -1,0 +1,40 @@
+"""Planted mistakes in the oracle, each caught by a pin (CPU only).
+
+Each mutant in ``oracle.MUTANTS`` is step.c compiled with ``OR_MUTANT_<name>``: one plausible
+mistake -- a dropped term, a wrong sign, a missing factor, a one-step lag, a wrong constant.
+The pin named beside it runs in a child process against that build and must fail with a test
+failure (pytest exit status 1, not a crash or a collection error); the same pins pass on the
+oracle itself in the normal suite.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = "tests/test_oracle_pins.py::"
+CAUGHT_BY = {
+    "PHILOX_MULT": PINS + "test_philox_known_answers",               # a wrong round multiplier
+    "BORIS_SIGN": PINS + "test_ncs_first_emission_follows_the_rate",  # rotation the wrong way
+    "ETA_UE": PINS + "test_eta_identity_exact",                       # the 2 V_x (u.E) term dropped
+    "PHOTON_BACKWARD": PINS + "test_ncs_first_emission_follows_the_rate",   # photon against the velocity
+    "NCS_NO_GAMMA": PINS + "test_ncs_first_emission_follows_the_rate",      # rate without 1/gamma
+    "NCS_LAG": PINS + "test_ncs_first_emission_follows_the_rate",     # crossing tested before the decrement
+    "RECOIL_TALLY": PINS + "test_energy_bookkeeping",                 # recoil energy tallied with its sign flipped
+    "BREMS_NO_BETA": PINS + "test_brems_probability_carries_beta",    # Eq. 4 without beta
+}
+
+
+def test_every_mutant_has_a_pin():
+    assert set(CAUGHT_BY) == set(O.MUTANTS)
+
+
+@pytest.mark.parametrize("mutant", sorted(CAUGHT_BY))
+def test_pin_catches_mutant(mutant):
+    env = dict(os.environ, ORACLE_MUTANT=mutant)
+    p = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", CAUGHT_BY[mutant]],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert p.returncode == 1, (p.returncode, p.stdout[-3000:], p.stderr[-2000:])
