@@ -25,9 +25,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = ["tables.c", "step.c"]
-# the planted mistakes step.c knows (OR_MUTANT_<name>)
+# the planted mistakes step.c and tables.c know (OR_MUTANT_<name>)
 MUTANTS = ("PHILOX_MULT", "BORIS_SIGN", "ETA_UE", "PHOTON_BACKWARD", "NCS_NO_GAMMA", "NCS_LAG",
-           "RECOIL_TALLY", "BREMS_NO_BETA")
+           "RECOIL_TALLY", "BREMS_NO_BETA", "NCS_F_QUANTUM", "NCS_H_JACOBIAN", "BREMS_COULOMB", "BW_NORM",
+           "MIRROR_SIGN", "INCIDENT_SIGN", "POSITION_NO_GAMMA", "PIC_CURRENT_SIGN")
 
 
 def _mutant() -> str:

@@ -27,9 +27,9 @@
 #define C_LIGHT 299792458.0
 #define HIST_EMAX_MEV 10000.0          /* top of the energy histogram   */
 
-/* OR_MUTANT_* (never defined in a normal build): each plants one plausible mistake
- * (a dropped term, a wrong sign, a missing factor, a lag, a wrong constant) so that the
- * tests can show that a pin fails for it (tests/test_oracle_mutants.py).               */
+/* OR_MUTANT_* (never defined in a normal build, here and in tables.c): each plants one
+ * plausible mistake (a dropped term, a wrong sign, a missing factor, a lag, a wrong
+ * constant) so that the tests can show that a pin fails for it (tests/test_oracle_mutants.py). */
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10, from its published definition (Salmon et al., SC'11):      */
@@ -143,7 +143,11 @@ static void incident_fields(const or_run_params* r, double x, double y, double t
     }
     double st = sin(theta), ct = cos(theta);
     /* y-polarised component: E_y = B_z = -a0 S (g' sin + g cos) */
+#ifdef OR_MUTANT_INCIDENT_SIGN
+    double ey = a0 * S * (dg * st + g * ct);
+#else
     double ey = -a0 * S * (dg * st + g * ct);
+#endif
     E[1] = ey;
     B[2] = ey;
     if (r->geometry == OR_GAUSS_2D)
@@ -169,7 +173,11 @@ static void plane_e(const or_run_params* r, double p, double* ey, double* ez) {
     double g, dg;
     envelope(r, p, &g, &dg);
     double st = sin(p), ct = cos(p);
+#ifdef OR_MUTANT_MIRROR_SIGN
+    *ey = r->a0 * (dg * st + g * ct);
+#else
     *ey = -r->a0 * (dg * st + g * ct);
+#endif
     *ez = (r->polarisation == OR_CP) ? r->a0 * (dg * ct - g * st) : 0.0;
 }
 
@@ -523,7 +531,11 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
             if (nullc) *wait = wait_draw(c->x_hat, word64(v[0], v[1]));
         }
     }
+#ifdef OR_MUTANT_POSITION_NO_GAMMA
+    x += c->dt * u[0];
+#else
     x += c->dt * u[0] / gamma;
+#endif
     if (r->geometry == OR_GAUSS_2D) y += c->dt * u[1] / gamma;
     if (r->box_enable && (x < c->box0 || x > c->box1)) {
         x = NAN;
@@ -685,7 +697,11 @@ static void pic_deposit(double dx, int n_cells, double x_old, double x_new, cons
     double cum = 0.0;
     for (int64_t k = ia; k <= ia + 1; ++k) {          /* half nodes ia, ia+1 (node ia+2 closes the sum) */
         cum += lin_w(sn, k, 0.0) - lin_w(so, k, 0.0);
+#ifdef OR_MUTANT_PIC_CURRENT_SIGN
+        if (k >= 0 && k < n_cells) ax[k] -= (int64_t)nearbyint(cum * PIC_FX);
+#else
         if (k >= 0 && k < n_cells) ax[k] += (int64_t)nearbyint(cum * PIC_FX);
+#endif
     }
     double vy = u[1] / gamma, vz = u[2] / gamma;
     for (int64_t k = ia - 1; k <= ia + 1; ++k) {      /* half nodes touched by either position */

@@ -125,7 +125,11 @@ double or_int_k53(double x) { return bessel_common(5.0 / 3.0, x, 1); }
 /* ------------------------------------------------------------------------- */
 static double F_of_y(double eta, double y) {
     double d = 3.0 * eta * y / (2.0 + 3.0 * eta * y);
+#ifdef OR_MUTANT_NCS_F_QUANTUM
+    return (1.0 - d) * y * or_int_k53(y);
+#else
     return d * d * y * or_bessel_k(2.0 / 3.0, y) + (1.0 - d) * y * or_int_k53(y);
+#endif
 }
 
 double or_ncs_F(double eta, double chi) {
@@ -140,7 +144,11 @@ static double ncs_cdf_integrand(double lny, const void* vc) {
     const ncs_ctx* c = (const ncs_ctx*)vc;
     double y = exp(lny);
     if (c->classical) return y * or_int_k53(y);          /* eta -> 0 limit    */
+#ifdef OR_MUTANT_NCS_H_JACOBIAN
+    return F_of_y(c->eta, y);
+#else
     return F_of_y(c->eta, y) * 2.0 / (2.0 + 3.0 * c->eta * y);
+#endif
 }
 /* integrand in ln y for int F dchi: dchi = 3 eta^2 y /(2+3 eta y)^2 d ln y  */
 static double ncs_pow_integrand(double lny, const void* vc) {
@@ -203,7 +211,11 @@ double or_brems_dcs_raw(double Z, double gamma, double y, int complete) {
                   - 4.0 * (1.0 - 0.7 * exp(-8.0 * e) - 0.3 * exp(-29.2 * e));
     double psi2 = psi1 - (2.0 / 3.0) / (1.0 + 40.0 * e + 400.0 * e * e);
     double lnZ = log(Z);
+#ifdef OR_MUTANT_BREMS_COULOMB
+    double f = 0.0;
+#else
     double f = or_coulomb_f(Z);
+#endif
     double t1 = (4.0 / 3.0 - 4.0 / 3.0 * y + y * y)
               * (Z * Z * (phi1 - 4.0 / 3.0 * lnZ - 4.0 * f) + Z * (psi1 - 8.0 / 3.0 * lnZ));
     double t2 = (2.0 / 3.0) * (1.0 - y) * (Z * Z * (phi1 - phi2) + Z * (psi1 - psi2));
@@ -651,10 +663,16 @@ static double bw_cumulate(double chi, int n, double* row) {
     return cum;
 }
 
+/* T = int G dx / (sqrt3 pi) */
+#ifdef OR_MUTANT_BW_NORM
+#define BW_NORM (sqrt(3.0) * 2.0 * M_PI)
+#else
+#define BW_NORM (sqrt(3.0) * M_PI)
+#endif
 /* by the same rule on 256 cells (no table) */
 double or_bw_T_direct(double chi) {
     if (!(chi > 0.0)) return 0.0;
-    return bw_cumulate(chi, 257, NULL) / (sqrt(3.0) * M_PI);
+    return bw_cumulate(chi, 257, NULL) / BW_NORM;
 }
 
 struct or_bw_tables {
@@ -675,7 +693,7 @@ or_bw_tables* or_bw_tables_build(int n_chi, double chi_min, double chi_max, int 
         double chi = grid_log(chi_min, chi_max, i, n_chi);
         double* row = t->cdf + (int64_t)i * n_x;
         double tot = bw_cumulate(chi, n_x, row);
-        t->T[i] = tot / (sqrt(3.0) * M_PI);
+        t->T[i] = tot / BW_NORM;
         for (int j = 0; j < n_x; ++j) row[j] = tot > 0.0 ? row[j] / tot : (double)j / (double)(n_x - 1);
     }
     return t;

@@ -25,6 +25,14 @@ CAUGHT_BY = {
     "NCS_LAG": PINS + "test_ncs_first_emission_follows_the_rate",     # crossing tested before the decrement
     "RECOIL_TALLY": PINS + "test_energy_bookkeeping",                 # recoil energy tallied with its sign flipped
     "BREMS_NO_BETA": PINS + "test_brems_probability_carries_beta",    # Eq. 4 without beta
+    "NCS_F_QUANTUM": PINS + "test_ncs_F_vs_scipy_pointwise",          # the emissivity's delta^2 y K_2/3 term dropped
+    "NCS_H_JACOBIAN": PINS + "test_ncs_table_vs_brute_force",         # h integrated without dchi/chi's Jacobian
+    "BREMS_COULOMB": PINS + "test_brems_complete_screening_closed_form",     # Eq. 1 without f(Z)
+    "INCIDENT_SIGN": PINS + "test_plane_wave_orbit_from_rest",        # the laser's E_y with the wrong sign
+    "POSITION_NO_GAMMA": PINS + "test_plane_wave_orbit_from_rest",    # x advanced by u dt instead of v dt
+    "MIRROR_SIGN": "tests/test_oracle_pins_variants.py::test_reflected_wave_mirror_node",   # mirror image not inverted
+    "BW_NORM": "tests/test_oracle_bw.py::test_small_chi_limit",       # T(chi) with a stray factor 2
+    "PIC_CURRENT_SIGN": "tests/test_oracle_pic.py::test_pic_gauss_law",     # J_x deposited with the wrong sign
 }
 
 
