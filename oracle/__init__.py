@@ -28,7 +28,8 @@ _SOURCES = ["tables.c", "step.c"]
 # the planted mistakes step.c and tables.c know (OR_MUTANT_<name>)
 MUTANTS = ("PHILOX_MULT", "BORIS_SIGN", "ETA_UE", "PHOTON_BACKWARD", "NCS_NO_GAMMA", "NCS_LAG",
            "RECOIL_TALLY", "BREMS_NO_BETA", "NCS_F_QUANTUM", "NCS_H_JACOBIAN", "BREMS_COULOMB", "BW_NORM",
-           "MIRROR_SIGN", "INCIDENT_SIGN", "POSITION_NO_GAMMA", "PIC_CURRENT_SIGN")
+           "MIRROR_SIGN", "INCIDENT_SIGN", "POSITION_NO_GAMMA", "PIC_CURRENT_SIGN", "NCS_SAMPLE_FLIP",
+           "BREMS_SAMPLE_FLIP", "NULL_THINNING", "ENVELOPE_FALL", "GOUY_SIGN", "MJ_TEMPERATURE")
 
 
 def _mutant() -> str:

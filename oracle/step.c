@@ -114,7 +114,11 @@ static void envelope(const or_run_params* r, double phi, double* g, double* dg) 
     double q = phi - pr - pf;
     double c = cos(0.5 * M_PI * q / pr);
     *g = c * c;
+#ifdef OR_MUTANT_ENVELOPE_FALL
+    *dg = (0.5 * M_PI / pr) * sin(M_PI * q / pr);
+#else
     *dg = -(0.5 * M_PI / pr) * sin(M_PI * q / pr);
+#endif
 }
 
 static void incident_fields(const or_run_params* r, double x, double y, double t, double E[3], double B[3]) {
@@ -139,7 +143,11 @@ static void incident_fields(const or_run_params* r, double x, double y, double t
         inv_w2 = 1.0 / w2;
         inv_R = xi / (xi * xi + zr * zr);
         S = sqrt(w0 / sqrt(w2)) * exp(-y * y * inv_w2);
+#ifdef OR_MUTANT_GOUY_SIGN
+        theta = phi - 0.5 * y * y * inv_R - 0.5 * atan(xi / zr);
+#else
         theta = phi - 0.5 * y * y * inv_R + 0.5 * atan(xi / zr);
+#endif
     }
     double st = sin(theta), ct = cos(theta);
     /* y-polarised component: E_y = B_z = -a0 S (g' sin + g cos) */
@@ -326,7 +334,11 @@ int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int6
     if (r->brems_method == OR_BREMS_NULL && !wait && n_ids > 0) return -1;
     run_ctx c;
     make_ctx(t, r, &c, or__photon_min(t));
+#ifdef OR_MUTANT_MJ_TEMPERATURE
+    double theta = 0.5 * r->T_mev / C_MEC2_MEV;
+#else
     double theta = r->T_mev / C_MEC2_MEV;
+#endif
     for (int64_t k = 0; k < n_ids; ++k) {
         int64_t id = ids[k];
         uint32_t w[4];
@@ -493,7 +505,11 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
 #endif
                 P = -expm1(-xb);
             }
+#ifdef OR_MUTANT_NULL_THINNING
+            double p_acc = P;
+#else
             double p_acc = nullc ? P / c->P_hat : P;
+#endif
             /* direct: one draw of purpose 0 at step n (test word, photon-energy word);
              * null: one draw of purpose 256 at step n + 1 (next-wait word, test word),
              * and purpose 0 at step n only for a collision (photon-energy word)  */

@@ -532,6 +532,9 @@ static double invert_row(const double* ra, const double* rb, double w, int n, do
 }
 
 double or_sample_ncs_delta(const or_tables* t, double eta, double R, int* below) {
+#ifdef OR_MUTANT_NCS_SAMPLE_FLIP
+    R = 1.0 - R;
+#endif
     const or_table_params* p = &t->p;
     const double *ra, *rb;
     double w;
@@ -570,6 +573,9 @@ double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* abov
 }
 
 double or_sample_brems_y(const or_tables* t, int iz, double gamma, double R) {
+#ifdef OR_MUTANT_BREMS_SAMPLE_FLIP
+    R = 1.0 - R;
+#endif
     const or_table_params* p = &t->p;
     int i, fl; double w;
     row_pos(gamma, p->gamma_min, p->gamma_max, p->n_E, &i, &w, &fl);

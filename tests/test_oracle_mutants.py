@@ -33,7 +33,27 @@ CAUGHT_BY = {
     "MIRROR_SIGN": "tests/test_oracle_pins_variants.py::test_reflected_wave_mirror_node",   # mirror image not inverted
     "BW_NORM": "tests/test_oracle_bw.py::test_small_chi_limit",       # T(chi) with a stray factor 2
     "PIC_CURRENT_SIGN": "tests/test_oracle_pic.py::test_pic_gauss_law",     # J_x deposited with the wrong sign
+    "NCS_SAMPLE_FLIP": PINS + "test_ncs_sampler_inverts_table",       # the NCS CDF inverted at 1 - R
+    "BREMS_SAMPLE_FLIP": PINS + "test_brems_sampler_range_and_inversion",   # the brems CDF inverted at 1 - R
+    "NULL_THINNING": "tests/test_oracle_pins_variants.py::test_null_collision_first_event_has_direct_probability",
+    "ENVELOPE_FALL": PINS + "test_plane_wave_fields_from_the_vector_potential",  # g' of the falling ramp signed wrong
+    "GOUY_SIGN": PINS + "test_gaussian_focus_satisfies_the_paraxial_equation",  # Gouy phase against the curvature
+    "MJ_TEMPERATURE": PINS + "test_maxwell_juttner_mean_energy",      # theta = T / 2 m c^2
 }
+
+
+def _run_pin(mutant):
+    env = dict(os.environ, ORACLE_MUTANT=mutant, OMP_NUM_THREADS="2")
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", CAUGHT_BY[mutant]],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+@pytest.fixture(scope="module")
+def pin_runs():
+    """Every mutant's pin, run in child processes side by side."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
+        return dict(zip(sorted(CAUGHT_BY), ex.map(_run_pin, sorted(CAUGHT_BY))))
 
 
 def test_every_mutant_has_a_pin():
@@ -41,8 +61,6 @@ def test_every_mutant_has_a_pin():
 
 
 @pytest.mark.parametrize("mutant", sorted(CAUGHT_BY))
-def test_pin_catches_mutant(mutant):
-    env = dict(os.environ, ORACLE_MUTANT=mutant)
-    p = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", CAUGHT_BY[mutant]],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+def test_pin_catches_mutant(mutant, pin_runs):
+    p = pin_runs[mutant]
     assert p.returncode == 1, (p.returncode, p.stdout[-3000:], p.stderr[-2000:])

@@ -562,6 +562,69 @@ def test_energy_bookkeeping():
 
 
 # ---------------------------------------------------------- field model ----
+def _envelope_definition(phi, pr, pf):
+    """Sec. 3's pulse envelope: sin^2 rise over pr, flat top pf, cos^2 fall."""
+    if phi <= 0.0 or phi >= 2.0 * pr + pf:
+        return 0.0
+    if phi < pr:
+        return math.sin(0.5 * math.pi * phi / pr) ** 2
+    if phi <= pr + pf:
+        return 1.0
+    return math.cos(0.5 * math.pi * (phi - pr - pf) / pr) ** 2
+
+
+def test_plane_wave_fields_from_the_vector_potential():
+    """The 1D pulse is defined through its vector potential, A_y = a0 g(phi) sin phi (and for CP
+    A_z = -a0 g(phi) cos phi), phi = t - x: E = -dA/dt and B = x^ x E at 997 phases across the
+    five parts of the pulse, by central differences of the test's own A (measured 2.3e-8 at
+    a0 = 10).  Maxwell's equations cannot catch a wrong envelope derivative -- any f(t - x) is a
+    vacuum wave -- so the fields are checked against the definition."""
+    worst = 0.0
+    for pol in (0, 1):
+        r = O.run_params(a0=10.0, polarisation=pol, geometry=0)
+        pr = 2 * math.pi * r.ramp_periods
+        pf = 2 * math.pi * r.flat_s * 299792458.0 / r.lambda_m
+
+        def A(p):
+            g = _envelope_definition(p, pr, pf)
+            return 10.0 * g * math.sin(p), (-10.0 * g * math.cos(p) if pol else 0.0)
+
+        h = 1e-4
+        for p in np.linspace(-3.0, 2 * pr + pf + 3.0, 997):
+            E, B = O.fields(r, 0.0, 0.0, p)
+            ap, am = A(p + h), A(p - h)
+            ey, ez = -(ap[0] - am[0]) / (2 * h), -(ap[1] - am[1]) / (2 * h)
+            worst = max(worst, abs(E[1] - ey), abs(E[2] - ez), abs(B[2] - E[1]), abs(B[1] + E[2]))
+    assert worst < 1e-6
+
+
+def test_gaussian_focus_satisfies_the_paraxial_equation():
+    """The 2D focus on the flat top is Re[u e^{i(t - x)}] with u the exact Gaussian-beam solution of
+    the paraxial equation 2i du/dx = d^2u/dy^2 (the wave equation without d^2u/dx^2): u is read off
+    two samples of E_y a quarter period apart and the equation checked by finite differences from
+    -150 to +170 about the focus, on and off axis (residual measured 4.2e-5 of |u|/z_R + |u_yy|).
+    A Gouy phase of the wrong sign against the wavefront curvature leaves a residual of order 1."""
+    r = O.run_params(a0=1.0, polarisation=0, geometry=1, w0_m=3e-6, focus_x_m=2e-6)
+    k = 2 * math.pi / 1e-6
+    xf, w0 = 2e-6 * k, 3e-6 * k
+    zr = 0.5 * w0 * w0
+
+    def u(x, y, t):
+        c = -O.fields(r, x, y, t)[0][1]
+        d = -O.fields(r, x, y, t + 0.5 * math.pi)[0][1]
+        return (c - 1j * d) * np.exp(-1j * (t - x))
+
+    hx, hy, worst = 0.5, 0.2, 0.0
+    for xi in (-150.0, -40.0, 0.0, 60.0, 170.0):
+        for y in (0.0, 5.0, 12.0, 20.0):
+            x = xf + xi
+            t = x + 30.0                                   # phase 30: on the flat top
+            ux = (u(x + hx, y, t) - u(x - hx, y, t)) / (2 * hx)
+            uyy = (u(x, y + hy, t) - 2 * u(x, y, t) + u(x, y - hy, t)) / (hy * hy)
+            worst = max(worst, abs(2j * ux - uyy) / (abs(u(x, y, t)) / zr + abs(uyy)))
+    assert worst < 1e-3
+
+
 def test_fields_gaussian_reduces_to_plane_wave():
     for pol in (0, 1):
         r1 = O.run_params(a0=10.0, polarisation=pol, geometry=0)
