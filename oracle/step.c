@@ -292,7 +292,11 @@ double or_null_x_hat(const or_tables* t, const or_run_params* r) {
 /* steps to the next candidate: floor(-ln U / x_hat), OR_WAIT_NEVER when that
  * does not fit in 32 bits (or x_hat = 0)                                    */
 static uint32_t wait_draw(double x_hat, uint64_t v) {
+#ifdef OR_MUTANT_WAIT_SCALE
+    double q = -log(u53(v)) / (2.0 * x_hat);
+#else
     double q = -log(u53(v)) / x_hat;
+#endif
     if (!(q < 4294967295.0)) return OR_WAIT_NEVER;
     return (uint32_t)floor(q);
 }
@@ -345,7 +349,11 @@ int or_init(const or_tables* t, const or_run_params* r, const int64_t* ids, int6
         double* s = st + 6 * k;
         draw(r, id, 0, PUR_POS, w);
         /* a beam enters at the front face of the slab (Sec. 2.2 bunch benchmark) */
+#ifdef OR_MUTANT_INIT_SPREAD
+        s[0] = (r->init_dist == OR_BEAM) ? c.x0 : c.x0 + 2.0 * (c.x1 - c.x0) * u32(w[0]);
+#else
         s[0] = (r->init_dist == OR_BEAM) ? c.x0 : c.x0 + (c.x1 - c.x0) * u32(w[0]);
+#endif
         s[1] = (r->geometry == OR_GAUSS_2D) ? -c.yh + 2.0 * c.yh * u32(w[1]) : 0.0;
         s[2] = s[3] = s[4] = 0.0;
         if (r->init_dist == OR_MAXWELL_JUTTNER) {
@@ -395,7 +403,11 @@ static void record(const run_ctx* c, double x, double y, double ew, const double
     p.step = step;
     p.id_mech = (uint32_t)id | ((uint32_t)mech << 31);
     plist_push(pl, &p);
+#ifdef OR_MUTANT_HIST_SHIFT
+    int eb = (int)floor((double)OR_HIST_E_BINS * log(ew) / c->log_emax) + 1;
+#else
     int eb = (int)floor((double)OR_HIST_E_BINS * log(ew) / c->log_emax);
+#endif
     if (eb >= OR_HIST_E_BINS) { eb = OR_HIST_E_BINS - 1; tally[ORT_N_HIST_OVER]++; }
     if (eb < 0) eb = 0;
     double th = atan2(k[1], k[0]);
@@ -799,7 +811,11 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
         plane_e(r, (double)(s_ + 1) * dt, &gy, &gz);      /* incident field at x = 0, t^{n+1} */
         memcpy(tmp, fp, sizeof(double) * (size_t)(n + 1));
         for (int64_t i = 1; i <= n; ++i) fp[i] = tmp[i - 1] - dt * kyz * (double)jy[i - 1];
+#ifdef OR_MUTANT_PIC_INJECT_HALF
+        fp[0] = gy;
+#else
         fp[0] = 2.0 * gy;
+#endif
         memcpy(tmp, gp, sizeof(double) * (size_t)(n + 1));
         for (int64_t i = 1; i <= n; ++i) gp[i] = tmp[i - 1] - dt * kyz * (double)jz[i - 1];
         gp[0] = 2.0 * gz;

@@ -264,7 +264,12 @@ double or_bh_dcs_raw(double Z, double k, double x, int complete) {
     double xx = x * (1.0 - x);
     double t1 = (1.0 - 4.0 / 3.0 * xx)
               * (Z * Z * (phi1 - 4.0 / 3.0 * lnZ - 4.0 * f) + Z * (psi1 - 8.0 / 3.0 * lnZ));
+#ifdef OR_MUTANT_BH_SECOND_TERM
+    double t2 = 0.0;
+    (void)phi2; (void)psi2;
+#else
     double t2 = -(2.0 / 3.0) * xx * (Z * Z * (phi1 - phi2) + Z * (psi1 - psi2));
+#endif
     return t1 + t2;
 }
 
@@ -560,7 +565,11 @@ double or_sample_ncs_delta(const or_tables* t, double eta, double R, int* below)
     } else {
         y = exp(log(p->y_min) + ((double)j + fr) * dly);
     }
+#ifdef OR_MUTANT_DELTA_MAP
+    return 3.0 * eta * y / (1.0 + 3.0 * eta * y);
+#else
     return 3.0 * eta * y / (2.0 + 3.0 * eta * y);
+#endif
 }
 
 double or_brems_sigma_interp(const or_tables* t, int iz, double gamma, int* above) {

@@ -544,6 +544,47 @@ def test_ncs_first_emission_follows_the_rate():
         assert st_.chi2.sf(chi2(wrong, lag), dof) < 1e-5, (wrong, lag)
 
 
+def test_histograms_bin_the_photon_records():
+    """The energy and angle histograms are the photon records binned by the stated rule: 512 bins
+    of ln(E / m c^2) up to 10 GeV and 180 bins of atan2(k_y, k_x) over [-pi, pi), NCS and brems
+    apart.  Only a record within 1e-5 of a bin edge may land one bin over (the record holds the
+    energy and direction in float)."""
+    p = O.table_params(n_eta=32, n_y=32, n_E=32, n_s=32)
+    t = O.Tables(p, [79.0])
+    r = O.run_params(a0=270.0, Z=79.0, charge_state=51.0, ne_over_nc=2e5, init_dist=1, T_mev=1.0, seed=4)
+    ids = np.arange(2000)
+    st = O.init(t, r, ids)
+    ph, n, hist, tally = O.run(t, r, ids, st, 0, 1500, capacity=1 << 18)
+    assert n == len(ph) and len(ph) > 500
+    mech = (ph["id_mech"] >> 31).astype(np.int64)
+    assert 0 < mech.sum() < len(ph)                           # both mechanisms present
+    fe = 512 * np.log(ph["energy"].astype(np.float64)) / math.log(10000.0 / 0.51099895)
+    ft = (np.arctan2(ph["ky"].astype(np.float64), ph["kx"].astype(np.float64)) + math.pi) / (2 * math.pi) * 180
+    near = (np.abs(fe - np.round(fe)) < 1e-5) | (np.abs(ft - np.round(ft)) < 1e-5)
+    eb = np.clip(np.floor(fe).astype(np.int64), 0, 511)
+    tb = np.clip(np.floor(ft).astype(np.int64), 0, 179)
+    want = np.zeros_like(hist)
+    np.add.at(want, mech * 512 + eb, 1)
+    np.add.at(want, 1024 + mech * 180 + tb, 1)
+    assert int(np.abs(hist.astype(np.int64) - want.astype(np.int64)).sum()) <= 2 * int(near.sum())
+
+
+def test_initial_positions_uniform_in_the_slab():
+    """Electrons start uniform over the slab (x in [x0, x1], and in 2D y in [-y_h, y_h]; KS), a
+    beam at its front face."""
+    from scipy.stats import kstest
+    t = O.Tables(O.table_params(n_eta=2, n_y=4, n_E=2, n_s=2), [13.0])
+    k = 2 * math.pi / 1e-6
+    r = O.run_params(geometry=1, slab_x0_m=2e-6, slab_thick_m=1e-6, y_half_m=3e-6, seed=23)
+    st = O.init(t, r, np.arange(20000))
+    x0, x1, yh = 2e-6 * k, 3e-6 * k, 3e-6 * k
+    assert st[:, 0].min() >= x0 and st[:, 0].max() <= x1 and np.abs(st[:, 1]).max() <= yh
+    assert kstest((st[:, 0] - x0) / (x1 - x0), "uniform").pvalue > 1e-3
+    assert kstest((st[:, 1] + yh) / (2 * yh), "uniform").pvalue > 1e-3
+    rb = O.run_params(slab_x0_m=2e-6, init_dist=2, beam_gamma=10.0, seed=23)
+    assert np.all(O.init(t, rb, np.arange(100))[:, 0] == x0)
+
+
 def test_energy_bookkeeping():
     p = O.table_params(n_eta=32, n_y=32, n_E=32, n_s=32)
     t = O.Tables(p, [79.0])
