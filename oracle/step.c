@@ -142,9 +142,15 @@ static void incident_fields(const or_run_params* r, double x, double y, double t
         double w2 = w0 * w0 * (1.0 + xi * xi / (zr * zr));
         inv_w2 = 1.0 / w2;
         inv_R = xi / (xi * xi + zr * zr);
+#ifdef OR_MUTANT_AMPLITUDE
+        S = (w0 / sqrt(w2)) * exp(-y * y * inv_w2);
+#else
         S = sqrt(w0 / sqrt(w2)) * exp(-y * y * inv_w2);
-#ifdef OR_MUTANT_GOUY_SIGN
+#endif
+#if defined(OR_MUTANT_GOUY_SIGN)
         theta = phi - 0.5 * y * y * inv_R - 0.5 * atan(xi / zr);
+#elif defined(OR_MUTANT_CURVATURE_SIGN)
+        theta = phi + 0.5 * y * y * inv_R + 0.5 * atan(xi / zr);
 #else
         theta = phi - 0.5 * y * y * inv_R + 0.5 * atan(xi / zr);
 #endif
@@ -564,8 +570,16 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
 #else
     x += c->dt * u[0] / gamma;
 #endif
+#ifdef OR_MUTANT_Y_UPDATE
+    if (r->geometry == OR_GAUSS_2D) y += c->dt * u[2] / gamma;
+#else
     if (r->geometry == OR_GAUSS_2D) y += c->dt * u[1] / gamma;
+#endif
+#ifdef OR_MUTANT_BOX_ONE_SIDED
+    if (r->box_enable && x > c->box1) {
+#else
     if (r->box_enable && (x < c->box0 || x > c->box1)) {
+#endif
         x = NAN;
         tally[ORT_N_KILLED]++;
         tally[ORT_KILLED_STEPS] += (uint64_t)(n + 1);
@@ -957,7 +971,12 @@ double or_chi_photon(const double kv[3], const double E[3], const double B[3], d
                    gm * E[1] + (kv[2] * dB[0] - kv[0] * dB[2]),
                    gm * E[2] + (kv[0] * dB[1] - kv[1] * dB[0])};
     double kE = kv[0] * E[0] + kv[1] * E[1] + kv[2] * E[2];
+#ifdef OR_MUTANT_CHI_KE
+    double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    (void)kE;
+#else
     double q = V[0] * V[0] + V[1] * V[1] + V[2] * V[2] + 2.0 * V[0] * kE;
+#endif
     return q > 0.0 ? sqrt(q) / E_S : 0.0;
 }
 
@@ -998,7 +1017,12 @@ int or_bw_transport(const or_bw_tables* bt, const or_tables* t, const or_run_par
         tally[ORP_N_ENTERED]++;
         for (int64_t m = ne + 1; m < step_end; ++m) {
             double tt = (double)(m - ne) * c.dt;
+#ifdef OR_MUTANT_BW_PHOTON_STILL
+            double px = xe, py = ye;
+            (void)tt;
+#else
             double px = fma(kx, tt, xe), py = fma(ky, tt, ye);
+#endif
             double E[3], B[3];
             or_fields(r, px, py, (double)m * c.dt, E, B);
             double chi = or_chi_photon(kvec, E, B, c.E_S);

@@ -585,6 +585,36 @@ def test_initial_positions_uniform_in_the_slab():
     assert np.all(O.init(t, rb, np.arange(100))[:, 0] == x0)
 
 
+def test_free_streaming_and_the_absorbing_box():
+    """Fields and emissions off, 2D geometry: each electron streams, x^n = x^0 + n dt u_x / gamma
+    and y^n = y^0 + n dt u_y / gamma, and the absorbing box removes it at the first step whose
+    position lies outside [box0, box1] through either face; the kill tallies count those steps."""
+    t = O.Tables(O.table_params(n_eta=2, n_y=4, n_E=2, n_s=2), [13.0])
+    k = 2 * math.pi / 1e-6
+    r = O.run_params(a0=0.0, geometry=1, init_dist=1, T_mev=1.0, enable_ncs=0, enable_brems=0, box_enable=1,
+                     box_x_m=(2.2e-6, 2.8e-6), slab_x0_m=2e-6, slab_thick_m=1e-6, y_half_m=3e-6, seed=29)
+    n, S = 5000, 50
+    ids = np.arange(n)
+    st = O.init(t, r, ids)
+    x0, y0, u = st[:, 0].copy(), st[:, 1].copy(), st[:, 2:5].copy()
+    _, _, _, tally = O.run(t, r, ids, st, 0, S, capacity=1 << 10)
+    dt = 2 * math.pi * 0.01
+    v = u / np.sqrt(1 + (u ** 2).sum(1))[:, None]
+    steps = np.arange(1, S + 1)[None, :]
+    xs = x0[:, None] + steps * dt * v[:, :1]
+    out = (xs < 2.2e-6 * k) | (xs > 2.8e-6 * k)
+    killed = out.any(1)
+    first = np.where(killed, out.argmax(1) + 1, 0)
+    assert 0.2 < killed.mean() < 0.9 and np.any(v[killed, 0] < 0) and np.any(v[killed, 0] > 0)
+    assert np.array_equal(np.isnan(st[:, 0]), killed)
+    assert int(tally[O.T["N_KILLED"]]) == int(killed.sum())
+    assert int(tally[O.T["KILLED_STEPS"]]) == int(first.sum())
+    live = ~killed
+    assert np.allclose(st[live, 0], x0[live] + S * dt * v[live, 0], rtol=0, atol=1e-11)
+    assert np.allclose(st[live, 1], y0[live] + S * dt * v[live, 1], rtol=0, atol=1e-11)
+    assert np.array_equal(st[:, 2:5], u)                     # no field, no emission: momenta unchanged
+
+
 def test_energy_bookkeeping():
     p = O.table_params(n_eta=32, n_y=32, n_E=32, n_s=32)
     t = O.Tables(p, [79.0])
