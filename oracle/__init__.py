@@ -31,7 +31,8 @@ MUTANTS = ("PHILOX_MULT", "BORIS_SIGN", "ETA_UE", "PHOTON_BACKWARD", "NCS_NO_GAM
            "MIRROR_SIGN", "INCIDENT_SIGN", "POSITION_NO_GAMMA", "PIC_CURRENT_SIGN", "NCS_SAMPLE_FLIP",
            "BREMS_SAMPLE_FLIP", "NULL_THINNING", "ENVELOPE_FALL", "GOUY_SIGN", "MJ_TEMPERATURE", "BH_SECOND_TERM",
            "DELTA_MAP", "WAIT_SCALE", "HIST_SHIFT", "INIT_SPREAD", "PIC_INJECT_HALF", "BW_PHOTON_STILL",
-           "CHI_KE", "Y_UPDATE", "BOX_ONE_SIDED", "CURVATURE_SIGN", "AMPLITUDE")
+           "CHI_KE", "Y_UPDATE", "BOX_ONE_SIDED", "CURVATURE_SIGN", "AMPLITUDE", "TAU_NO_RESET", "CLAMP_GAMMA",
+           "TARGET_Y", "ETA_GM", "BH_FREE_PATH")
 
 
 def _mutant() -> str:

@@ -247,7 +247,11 @@ void or_boris(double u[3], const double E[3], const double B[3], double dt) {
 /* ------------------------------------------------------------------------- */
 double or_eta(const double u[3], const double E[3], const double B[3], double E_S) {
     double gamma = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#ifdef OR_MUTANT_ETA_GM
+    double gm = (u[0] > 0.0) ? (u[1] * u[1] + u[2] * u[2]) / (gamma + u[0]) : gamma - u[0];
+#else
     double gm = (u[0] > 0.0) ? (1.0 + u[1] * u[1] + u[2] * u[2]) / (gamma + u[0]) : gamma - u[0];
+#endif
     double dB[3] = {B[0], B[1] + E[2], B[2] - E[1]};
     double V[3] = {gm * E[0] + (u[1] * dB[2] - u[2] * dB[1]),
                    gm * E[1] + (u[2] * dB[0] - u[0] * dB[2]),
@@ -477,7 +481,11 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
             double delta = or_sample_ncs_delta(t, eta, u53(word64(w[0], w[1])), &below);
             if (below) tally[ORT_N_ETA_BELOW]++;
             double ew = delta * gamma;
+#ifdef OR_MUTANT_CLAMP_GAMMA
+            if (ew > gamma) { ew = gamma; tally[ORT_N_CLAMP]++; }
+#else
             if (ew > gamma - 1.0) { ew = gamma - 1.0; tally[ORT_N_CLAMP]++; }
+#endif
             double k[3];
             recoil(u, gamma, ew, k);
             note_event(ev, n, 0);
@@ -497,12 +505,16 @@ static void particle_step(const or_tables* t, const or_run_params* r, const run_
                 fx_add(tally + ORT_E_NCS_BELOW, ew);
             }
             gamma = gn;
+#ifndef OR_MUTANT_TAU_NO_RESET
             tau = -log(u53(word64(w[2], w[3])));
+#endif
         }
     }
     if (r->enable_brems) {
         int in_slab = (x >= c->x0 && x <= c->x1);
+#ifndef OR_MUTANT_TARGET_Y
         if (r->geometry == OR_GAUSS_2D && fabs(y) > c->yh) in_slab = 0;
+#endif
         int nullc = (r->brems_method == OR_BREMS_NULL);
         /* direct method: every step in the slab is a test (Eq. 4); null
          * collisions: only the candidate steps of the majorant process  */
@@ -947,7 +959,11 @@ int or_pair_transport(const or_tables* t, const or_run_params* r, const or_photo
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
             tally[ORP_N_TESTS]++;
+#ifdef OR_MUTANT_BH_FREE_PATH
+            double q = floor(-log(u53(word64(w[0], w[1]))) / (2.0 * c.K_br * sig));
+#else
             double q = floor(-log(u53(word64(w[0], w[1]))) / (c.K_br * sig));
+#endif
             if (q <= (double)(last - first)) {
                 int64_t m = first + (int64_t)q;
                 double tt = (double)(m - ne) * c.dt;

@@ -51,6 +51,11 @@ CAUGHT_BY = {
     "BOX_ONE_SIDED": PINS + "test_free_streaming_and_the_absorbing_box",    # the box's rear face only
     "CURVATURE_SIGN": PINS + "test_gaussian_focus_satisfies_the_paraxial_equation",  # wavefront curvature sign
     "AMPLITUDE": PINS + "test_gaussian_focus_satisfies_the_paraxial_equation",       # w0 / w for sqrt(w0 / w)
+    "TAU_NO_RESET": PINS + "test_ncs_optical_depth_resets_after_emission",  # no fresh tau after an emission
+    "CLAMP_GAMMA": PINS + "test_photon_energy_clamp_conserves_energy",      # the photon clamped to gamma
+    "TARGET_Y": PINS + "test_brems_only_inside_the_target",           # the 2D target unbounded in y
+    "ETA_GM": PINS + "test_eta_identity_exact",                       # gamma - u_x without its 1
+    "BH_FREE_PATH": "tests/test_oracle_pairs.py::test_pair_free_path_conversion_law",  # free path at twice the rate
 }
 
 

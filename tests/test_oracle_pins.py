@@ -615,6 +615,62 @@ def test_free_streaming_and_the_absorbing_box():
     assert np.array_equal(st[:, 2:5], u)                     # no field, no emission: momenta unchanged
 
 
+def _constant_B_run(gamma, eta, n, seed):
+    """Electrons along +x at gamma in a constant B_z with |u x B| / E_S = eta, NCS only."""
+    t = O.Tables(O.table_params(n_eta=64, n_y=32, n_E=2, n_s=2), [13.0])
+    E_S = 1e-6 / (2 * math.pi * 3.8615926796e-13)
+    Bz = eta * E_S / math.sqrt(gamma * gamma - 1.0)
+    r = O.run_params(geometry=2, B_const=(0.0, 0.0, Bz), init_dist=2, beam_gamma=gamma, enable_brems=0, seed=seed)
+    ids = np.arange(n)
+    return t, r, ids, O.init(t, r, ids)
+
+
+def test_ncs_optical_depth_resets_after_emission():
+    """After the step of an NCS emission the optical depth is a fresh -ln U (Sec. 2.2): over the
+    electrons that emitted in a step, tau is exponential with unit mean (KS)."""
+    from scipy.stats import kstest
+    t, r, ids, st = _constant_B_run(100.0, 0.05, 20000, 31)
+    ev = np.zeros(len(ids), dtype=np.uint64)
+    taus = []
+    for k in range(30):
+        before = ev & np.uint64(0xFFFF)
+        O.run(t, r, ids, st, k, 1, capacity=1 << 16, events=ev)
+        taus.append(st[(ev & np.uint64(0xFFFF)) > before, 5])
+    taus = np.concatenate(taus)
+    assert len(taus) > 5000 and taus.min() > 0.0
+    assert kstest(taus, "expon").pvalue > 1e-3
+
+
+def test_photon_energy_clamp_conserves_energy():
+    """At gamma = 3 and eta = 5 the sampled fraction often exceeds 1 - 1/gamma; the photon then takes
+    gamma - 1 (counted) and leaves the electron at rest, and recoil still equals the emitted energy."""
+    t, r, ids, st = _constant_B_run(3.0, 5.0, 4000, 37)
+    ev = np.zeros(len(ids), dtype=np.uint64)
+    ph, n, hist, tally = O.run(t, r, ids, st, 0, 40, capacity=1 << 18, events=ev)
+    assert int(tally[O.T["N_CLAMP"]]) > 100
+    emitted = sum(O.fixed_to_float(tally, O.T[k]) for k in ("E_NCS_STORED", "E_NCS_BELOW"))
+    assert abs(O.fixed_to_float(tally, O.T["E_RECOIL_NCS"]) / emitted - 1) < 1e-12
+    # a clamped emission leaves the electron at rest for good (u = 0: eta = 0 in a pure B field)
+    assert int(np.all(st[:, 2:5] == 0.0, axis=1).sum()) == int(tally[O.T["N_CLAMP"]])
+
+
+def test_brems_only_inside_the_target():
+    """Eq. 4 acts in the target only: with fields off in 2D, electrons drifting out of the slab in x
+    and in y, every brems photon starts inside [x0, x1] x [-y_h, y_h]."""
+    t = O.Tables(O.table_params(n_eta=2, n_y=4, n_E=32, n_s=16), [79.0])
+    k = 2 * math.pi / 1e-6
+    r = O.run_params(a0=0.0, geometry=1, Z=79.0, charge_state=51.0, ne_over_nc=2e7, init_dist=1, T_mev=1.0,
+                     enable_ncs=0, slab_x0_m=2e-6, slab_thick_m=0.3e-6, y_half_m=0.3e-6, seed=41)
+    ids = np.arange(5000)
+    st = O.init(t, r, ids)
+    ph, n, _, _ = O.run(t, r, ids, st, 0, 60, capacity=1 << 18)
+    assert n > 500
+    x0, x1, yh = 2e-6 * k, 2.3e-6 * k, 0.3e-6 * k
+    assert np.mean((st[:, 0] < x0) | (st[:, 0] > x1) | (np.abs(st[:, 1]) > yh)) > 0.5   # most drifted out
+    tol = 1e-5
+    assert np.all((ph["x"] >= x0 - tol) & (ph["x"] <= x1 + tol) & (np.abs(ph["y"]) <= yh + tol))
+
+
 def test_energy_bookkeeping():
     p = O.table_params(n_eta=32, n_y=32, n_E=32, n_s=32)
     t = O.Tables(p, [79.0])
