@@ -204,7 +204,11 @@ static void add_reflected(const or_run_params* r, double x, double t, double E[3
     double psi = t + x - 2.0 * r->mirror_x_m * kl;
     double ey, ez;
     plane_e(r, psi, &ey, &ez);
+#ifdef OR_MUTANT_REFL_SQUARED
+    double ery = -r->reflect_r * r->reflect_r * ey, erz = -r->reflect_r * r->reflect_r * ez;
+#else
     double ery = -r->reflect_r * ey, erz = -r->reflect_r * ez;
+#endif
     E[1] += ery;
     E[2] += erz;
     B[1] += erz;

@@ -504,7 +504,11 @@ static void row_pos(double v, double lo, double hi, int n, int* i, double* w, in
     int k = (int)floor(tpos);
     if (k > n - 2) k = n - 2;
     *i = k;
+#ifdef OR_MUTANT_ROW_WEIGHT
+    *w = 1.0 - (tpos - (double)k);
+#else
     *w = tpos - (double)k;
+#endif
 }
 
 double or_ncs_h_interp(const or_tables* t, double eta, int* range_flag) {
@@ -651,7 +655,11 @@ double or_bw_G(double chi, double x) {
 
 /* the x grid of the tables: x_j = (1 - cos(pi s_j)) / 2, s_j = j / (n - 1), which
  * clusters the nodes at both ends where the spectrum of large chi peaks */
+#ifdef OR_MUTANT_BW_X_NODES
+static double bw_x_of_s(double s) { return s; }
+#else
 static double bw_x_of_s(double s) { return 0.5 * (1.0 - cos(M_PI * s)); }
+#endif
 
 typedef struct { double chi; } bw_ctx;
 static double bw_integrand_s(double s, const void* vc) {

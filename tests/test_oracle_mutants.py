@@ -56,6 +56,9 @@ CAUGHT_BY = {
     "TARGET_Y": PINS + "test_brems_only_inside_the_target",           # the 2D target unbounded in y
     "ETA_GM": PINS + "test_eta_identity_exact",                       # gamma - u_x without its 1
     "BH_FREE_PATH": "tests/test_oracle_pairs.py::test_pair_free_path_conversion_law",  # free path at twice the rate
+    "ROW_WEIGHT": PINS + "test_ncs_sampler_inverts_table",            # interpolation weight on the wrong row
+    "BW_X_NODES": "tests/test_oracle_bw.py::test_sampler_follows_the_spectrum",   # uniform x nodes for (1 - cos)/2
+    "REFL_SQUARED": "tests/test_oracle_pins_variants.py::test_reflected_wave_is_the_mirror_image_superposed",  # r^2 for r
 }
 
 

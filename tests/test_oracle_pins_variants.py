@@ -197,6 +197,30 @@ def test_reflected_wave_satisfies_maxwell(pol):
         assert abs(dtB[1] - dxE[2]) < tol          # (curl E)_y = -d_x E_z = -d_t B_y
 
 
+@pytest.mark.parametrize("pol", [0, 1])
+def test_reflected_wave_is_the_mirror_image_superposed(pol):
+    """The reflected run's field is the incident pulse plus its mirror image -r e(t + x - 2 x_m)
+    moving along -x: E = e(t - x) - r e(psi), B = x^ x e(t - x) + r x^ x e(psi) (B = -x^ x E_r),
+    with e the r = 0 pulse, at r = 0.7 over random (t, x) on both sides of the mirror.  Maxwell's
+    equations hold for any amplitude, so the amplitude is checked against this definition."""
+    rr = 0.7
+    k = 2 * math.pi / 1e-6
+    r0 = O.run_params(a0=20.0, polarisation=pol, geometry=0)
+    r1 = O.run_params(a0=20.0, polarisation=pol, geometry=0, reflect_r=rr, mirror_x_m=3e-6)
+    xm = 3e-6 * k
+    rng = np.random.default_rng(43)
+    hit = 0
+    for t, x in zip(rng.uniform(0.0, 150.0, 400), rng.uniform(-20.0, 60.0, 400)):
+        ei = O.fields(r0, 0.0, 0.0, t - x)[0]                # e at the incident phase
+        er = O.fields(r0, 0.0, 0.0, t + x - 2 * xm)[0]       # e at the reflected phase
+        E, B = O.fields(r1, x, 0.0, t)
+        want_E = (0.0, ei[1] - rr * er[1], ei[2] - rr * er[2])
+        want_B = (0.0, -ei[2] - rr * er[2], ei[1] + rr * er[1])
+        assert np.allclose(E, want_E, rtol=0, atol=1e-12) and np.allclose(B, want_B, rtol=0, atol=1e-12)
+        hit += abs(er[1]) > 1.0
+    assert hit > 50                                          # the mirror image is present at many points
+
+
 def test_reflected_wave_zero_r_is_plane_wave():
     run, run0 = _refl(1, r=0.0), O.run_params(a0=3.0, polarisation=1, flat_s=10e-15, ramp_periods=2.0)
     for (x, t) in ((5.0, 30.0), (15.0, 50.0), (20.0, 90.0)):
