@@ -720,7 +720,11 @@ void or_pic_gather(int n_cells, double dx, const double* grid, double x, double 
     B[1] = 0.5 * (Gm - Gp);
     B[0] = 0.0;
     /* E_x at half nodes j + 1/2 */
+#ifdef OR_MUTANT_PIC_GATHER_NODE
+    double sh = s;
+#else
     double sh = s - 0.5;
+#endif
     int64_t j = (int64_t)floor(sh);
     double fh = sh - (double)j;
     double h0 = (j >= 0 && j < n) ? ex[j] : 0.0, h1 = (j + 1 >= 0 && j + 1 < n) ? ex[j + 1] : 0.0;
@@ -763,7 +767,11 @@ static void pic_deposit(double dx, int n_cells, double x_old, double x_new, cons
     }
     double vy = u[1] / gamma, vz = u[2] / gamma;
     for (int64_t k = ia - 1; k <= ia + 1; ++k) {      /* half nodes touched by either position */
+#ifdef OR_MUTANT_PIC_JY_WEIGHT
+        double sbar = lin_w(sn, k, 0.5);
+#else
         double sbar = 0.5 * (lin_w(so, k, 0.5) + lin_w(sn, k, 0.5));
+#endif
         if (sbar > 0.0 && k >= 0 && k < n_cells) {
             ay[k] += (int64_t)nearbyint(vy * sbar * PIC_FX);
             az[k] += (int64_t)nearbyint(vz * sbar * PIC_FX);
@@ -835,7 +843,11 @@ int or_pic_run(const or_tables* t, const or_run_params* r0, int n_cells, double 
         const int64_t* jx = jsum;
         const int64_t* jy = jsum + n;
         const int64_t* jz = jsum + 2 * n;
+#ifdef OR_MUTANT_PIC_EX_SIGN
+        for (int64_t j = 0; j < n; ++j) ex[j] += dt * kx * (double)jx[j];
+#else
         for (int64_t j = 0; j < n; ++j) ex[j] -= dt * kx * (double)jx[j];
+#endif
         /* waves along +x: node i from node i - 1 through half node i - 1 */
         double gy, gz;
         plane_e(r, (double)(s_ + 1) * dt, &gy, &gz);      /* incident field at x = 0, t^{n+1} */

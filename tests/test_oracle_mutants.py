@@ -59,6 +59,9 @@ CAUGHT_BY = {
     "ROW_WEIGHT": PINS + "test_ncs_sampler_inverts_table",            # interpolation weight on the wrong row
     "BW_X_NODES": "tests/test_oracle_bw.py::test_sampler_follows_the_spectrum",   # uniform x nodes for (1 - cos)/2
     "REFL_SQUARED": "tests/test_oracle_pins_variants.py::test_reflected_wave_is_the_mirror_image_superposed",  # r^2 for r
+    "PIC_EX_SIGN": "tests/test_oracle_pic.py::test_pic_gauss_law",    # E_x driven up by J_x
+    "PIC_JY_WEIGHT": "tests/test_oracle_pic.py::test_pic_transverse_current_is_time_centred",  # J_y at x^{n+1} only
+    "PIC_GATHER_NODE": "tests/test_oracle_pic.py::test_pic_plasma_frequency",    # E_x gathered as if at nodes
 }
 
 

@@ -80,6 +80,29 @@ def test_pic_plasma_frequency():
     assert abs(half / half4 / 2.0 - 1) < 0.03, (half, half4)
 
 
+def test_pic_transverse_current_is_time_centred():
+    """J_y^{n+1/2} of one electron moving across a cell is deposited with the mean of its half-node
+    weights at x^n and x^{n+1}, so its centroid is the mid-position (x^n + x^{n+1}) / 2 (and its
+    sum the electron's v_y): read from the F- wave after one step from zero fields, where
+    F-_i = -dt k_yz J_y,i.  Gauss's law and the energy balance cannot see this time-centring."""
+    t = _tables()
+    nc = 400                                          # the grid reaches past the slab (x up to 25)
+    r, ids, st, w, grid = _plasma(t, nc, 1, a0=0.0, ne_over_nc=1.0, slab_x0_m=2e-6, slab_thick_m=1e-6)
+    ux, uy = 1.2, 0.8
+    st[0, 2:5] = (ux, uy, 0.0)
+    x_old = st[0, 0]
+    O.pic_run(t, r, nc, w, ids, st, grid, 0, 1, capacity=16)
+    gamma = math.sqrt(1 + ux * ux + uy * uy)
+    x_new = x_old + DT * ux / gamma
+    assert abs(st[0, 0] - x_new) < 1e-12
+    n = nc
+    fp, fm = grid[n: 2 * n + 1], grid[2 * n + 1: 3 * n + 2]
+    jy = -fm[:n]                                      # proportional to J_y at half nodes i + 1/2
+    centroid = float(((np.arange(n) + 0.5) * jy).sum() / jy.sum()) * DT
+    assert abs(centroid - 0.5 * (x_old + x_new)) < 1e-6 * DT
+    assert abs(x_new - x_old) > 0.3 * DT              # the time-centring is visible: a third of a cell
+
+
 def test_pic_gauss_law():
     """The charge-conserving current keeps div E_x = rho_ion + rho_e on every interior node while a
     laser drives a warm slab (to the 2^-36 quantum of the current sums)."""
