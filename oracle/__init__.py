@@ -33,7 +33,7 @@ MUTANTS = ("PHILOX_MULT", "BORIS_SIGN", "ETA_UE", "PHOTON_BACKWARD", "NCS_NO_GAM
            "DELTA_MAP", "WAIT_SCALE", "HIST_SHIFT", "INIT_SPREAD", "PIC_INJECT_HALF", "BW_PHOTON_STILL",
            "CHI_KE", "Y_UPDATE", "BOX_ONE_SIDED", "CURVATURE_SIGN", "AMPLITUDE", "TAU_NO_RESET", "CLAMP_GAMMA",
            "TARGET_Y", "ETA_GM", "BH_FREE_PATH", "ROW_WEIGHT", "BW_X_NODES", "REFL_SQUARED", "PIC_EX_SIGN",
-           "PIC_JY_WEIGHT", "PIC_GATHER_NODE")
+           "PIC_JY_WEIGHT", "PIC_GATHER_NODE", "PIC_BY_SIGN")
 
 
 def _mutant() -> str:

@@ -717,7 +717,11 @@ void or_pic_gather(int n_cells, double dx, const double* grid, double x, double 
     E[1] = 0.5 * (Fp + Fm);
     B[2] = 0.5 * (Fp - Fm);
     E[2] = 0.5 * (Gp + Gm);
+#ifdef OR_MUTANT_PIC_BY_SIGN
+    B[1] = 0.5 * (Gp - Gm);
+#else
     B[1] = 0.5 * (Gm - Gp);
+#endif
     B[0] = 0.0;
     /* E_x at half nodes j + 1/2 */
 #ifdef OR_MUTANT_PIC_GATHER_NODE

@@ -103,6 +103,24 @@ def test_pic_transverse_current_is_time_centred():
     assert abs(x_new - x_old) > 0.3 * DT              # the time-centring is visible: a third of a cell
 
 
+def test_pic_gather_decodes_the_waves():
+    """The grid carries the transverse fields as the waves F+- = E_y +- B_z and G+- = E_z -+ B_y: a
+    grid holding only the +x waves (F+, G+) gathers to B = x^ x E, only the -x waves to
+    B = -x^ x E, in both polarisations; E_x comes from its half nodes."""
+    n = 50
+    for waves in ("plus", "minus"):
+        grid = np.zeros(n + 5 * (n + 1))
+        ex, fp, fm, gp, gm = (grid[:n], grid[n: 2 * n + 1], grid[2 * n + 1: 3 * n + 2],
+                              grid[3 * n + 2: 4 * n + 3], grid[4 * n + 3: 5 * n + 4])
+        ex[:] = 0.3
+        (fp if waves == "plus" else fm)[:] = 1.7
+        (gp if waves == "plus" else gm)[:] = -0.9
+        E, B = O.pic_gather(grid, n, DT, 20.3 * DT)
+        sign = 1.0 if waves == "plus" else -1.0
+        assert np.allclose(E, (0.3, 0.85, -0.45), atol=1e-15)
+        assert np.allclose(B, (0.0, -sign * E[2], sign * E[1]), atol=1e-15)
+
+
 def test_pic_gauss_law():
     """The charge-conserving current keeps div E_x = rho_ion + rho_e on every interior node while a
     laser drives a warm slab (to the 2^-36 quantum of the current sums)."""
