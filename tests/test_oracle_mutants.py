@@ -67,7 +67,7 @@ CAUGHT_BY = {
 
 
 def _run_pin(mutant):
-    env = dict(os.environ, ORACLE_MUTANT=mutant, OMP_NUM_THREADS="2")
+    env = dict(os.environ, ORACLE_MUTANT=mutant, OMP_NUM_THREADS="1")
     return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", CAUGHT_BY[mutant]],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
@@ -76,7 +76,7 @@ def _run_pin(mutant):
 def pin_runs():
     """Every mutant's pin, run in child processes side by side."""
     from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
         return dict(zip(sorted(CAUGHT_BY), ex.map(_run_pin, sorted(CAUGHT_BY))))
 
 
